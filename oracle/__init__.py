@@ -1,0 +1,199 @@
+"""FP64 CPU oracle of the MWAX FX correlator's GPU stage (test infrastructure only).
+
+Only tests/, ``__graft_entry__.smoke()`` and bench.py's CPU-baseline leg may import
+this package.  It is independent of the CUDA library: ``oracle.c`` is plain C
+compiled with gcc, and nothing here touches the GPU path.
+
+Every function follows the paper's definition step by step (Sec. 2.5-2.7, see
+``oracle.c``).  Parity status per function (what pins it is in tests/test_oracle_*.py):
+  dft / fft          pinned: numpy.fft, impulse and tone closed forms, direct DFT
+  avg_weights        pinned: hand-derived tables in tests/golden/avg_weights.txt
+  spectra (delay)    pinned: closed-form tone phase with and without correction
+  correlate          pinned: Parseval identity (exact int64 RHS), tone ordering test,
+                     Hermitian full matrix, point-source closed form (statistical)
+  correlate_int      pinned: numpy int64 brute force, linearity (2x input -> 4x)
+  correlate_sampled  pinned: equals correlate element by element
+Conventions the paper leaves open (sign of the sky-frequency phase term, baseline
+order inside MWAX_ORDER, edge half-channels) follow the readings stated in the
+design notes; those readings are not pinned by the paper itself.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+FS = 1_280_000.0
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("n_tiles", ctypes.c_int), ("fft_len", ctypes.c_int), ("fine_avg", ctypes.c_int),
+                ("int_frames", ctypes.c_longlong), ("n_samples", ctypes.c_longlong),
+                ("block_samples", ctypes.c_int), ("sky_freq_hz", ctypes.c_double),
+                ("dc_exclude", ctypes.c_int)]
+
+
+@dataclass
+class Desc:
+    """One correlation job: T tiles, N-point frames, fscrunch F, K frames per integration."""
+    n_tiles: int
+    fft_len: int
+    fine_avg: int
+    int_frames: int
+    n_samples: int
+    block_samples: int = 64_000
+    sky_freq_hz: float = 0.0
+    dc_exclude: int = 1
+
+    @property
+    def n_paths(self):
+        return 2 * self.n_tiles
+
+    @property
+    def n_baselines(self):
+        return self.n_tiles * (self.n_tiles + 1) // 2
+
+    @property
+    def n_chan_out(self):
+        return self.fft_len // self.fine_avg
+
+    @property
+    def n_ints(self):
+        return self.n_samples // (self.int_frames * self.fft_len)
+
+    def c(self):
+        return _Desc(self.n_tiles, self.fft_len, self.fine_avg, self.int_frames, self.n_samples,
+                     self.block_samples, self.sky_freq_hz, self.dc_exclude)
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc -O2, OpenMP, no fast-math)."""
+    src = os.path.join(_HERE, "oracle.c")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-std=c11", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, src, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_SO)
+        vp, dp = ctypes.c_void_p, ctypes.POINTER(_Desc)
+        lib.ora_dft.argtypes = [ctypes.c_int, vp, vp]
+        lib.ora_fft.argtypes = [ctypes.c_int, vp, vp]
+        lib.ora_avg_weights.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
+        lib.ora_avg_weights.restype = ctypes.c_double
+        lib.ora_spectra.argtypes = [dp, vp, vp, ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong, vp]
+        lib.ora_correlate.argtypes = [dp, vp, vp, vp, vp]
+        lib.ora_correlate.restype = ctypes.c_int
+        lib.ora_xmatrix.argtypes = [dp, vp, vp, ctypes.c_longlong, ctypes.c_int, vp]
+        lib.ora_xmatrix.restype = ctypes.c_int
+        lib.ora_correlate_sampled.argtypes = [dp, vp, vp, ctypes.c_longlong, vp, vp]
+        lib.ora_correlate_sampled.restype = ctypes.c_int
+        lib.ora_correlate_int.argtypes = [dp, vp, vp, vp]
+        lib.ora_correlate_int.restype = ctypes.c_int
+        lib.ora_baseline_tiles.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int)]
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def _delay(d: Desc, delay):
+    if delay is None:
+        return None
+    a = np.ascontiguousarray(np.asarray(delay, dtype=np.float64).reshape(d.n_paths, 3))
+    return a
+
+
+def dft(x: np.ndarray) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.complex128)
+    X = np.empty_like(x)
+    _load().ora_dft(len(x), _p(x), _p(X))
+    return X
+
+
+def fft(x: np.ndarray) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.complex128)
+    X = np.empty_like(x)
+    _load().ora_fft(len(x), _p(x), _p(X))
+    return X
+
+
+def avg_weights(N: int, F: int, dc_exclude: int, j: int):
+    """(weights over the N ultrafine channels, weight sum) for output channel j."""
+    w = np.empty(N, dtype=np.float64)
+    s = _load().ora_avg_weights(N, F, dc_exclude, j, _p(w))
+    return w, s
+
+
+def baseline_tiles(T: int, b: int):
+    i, j = ctypes.c_int(), ctypes.c_int()
+    _load().ora_baseline_tiles(T, b, ctypes.byref(i), ctypes.byref(j))
+    return i.value, j.value
+
+
+def spectra(d: Desc, volt: np.ndarray, delay, path: int, m0: int, nm: int) -> np.ndarray:
+    """Y[m, c] for frames [m0, m0+nm) of one path (FFT, shift, delay correction)."""
+    volt = np.ascontiguousarray(volt, dtype=np.int8)
+    Y = np.empty((nm, d.fft_len), dtype=np.complex128)
+    dl = _delay(d, delay)
+    _load().ora_spectra(ctypes.byref(d.c()), _p(volt), _p(dl), path, m0, nm, _p(Y))
+    return Y
+
+
+def correlate(d: Desc, volt: np.ndarray, delay=None):
+    """(vis complex128 [ints, B, M, 4], weights float64 [ints, B, 4])."""
+    volt = np.ascontiguousarray(volt, dtype=np.int8)
+    vis = np.empty((d.n_ints, d.n_baselines, d.n_chan_out, 4), dtype=np.complex128)
+    wts = np.empty((d.n_ints, d.n_baselines, 4), dtype=np.float64)
+    dl = _delay(d, delay)
+    rc = _load().ora_correlate(ctypes.byref(d.c()), _p(volt), _p(dl), _p(vis), _p(wts))
+    if rc:
+        raise ValueError(f"oracle rejected the job (rc={rc})")
+    return vis, wts
+
+
+def xmatrix(d: Desc, volt: np.ndarray, delay, w: int, c: int) -> np.ndarray:
+    volt = np.ascontiguousarray(volt, dtype=np.int8)
+    C = np.empty((d.n_paths, d.n_paths), dtype=np.complex128)
+    dl = _delay(d, delay)
+    rc = _load().ora_xmatrix(ctypes.byref(d.c()), _p(volt), _p(dl), w, c, _p(C))
+    if rc:
+        raise ValueError(f"oracle rejected the job (rc={rc})")
+    return C
+
+
+def correlate_sampled(d: Desc, volt: np.ndarray, delay, req) -> np.ndarray:
+    """req: int array [R, 4] of (integration, baseline, channel, pol) -> complex128 [R]."""
+    volt = np.ascontiguousarray(volt, dtype=np.int8)
+    req = np.ascontiguousarray(np.asarray(req, dtype=np.int64).reshape(-1, 4))
+    out = np.empty(len(req), dtype=np.complex128)
+    dl = _delay(d, delay)
+    rc = _load().ora_correlate_sampled(ctypes.byref(d.c()), _p(volt), _p(dl), len(req), _p(req), _p(out))
+    if rc:
+        raise ValueError(f"oracle rejected the job (rc={rc})")
+    return out
+
+
+def correlate_int(d: Desc, volt: np.ndarray):
+    """Integer mode: (vis int64 [ints, B, 4, 2], weights float64 [ints, B, 4])."""
+    volt = np.ascontiguousarray(volt, dtype=np.int8)
+    vis = np.empty((d.n_ints, d.n_baselines, 4, 2), dtype=np.int64)
+    wts = np.empty((d.n_ints, d.n_baselines, 4), dtype=np.float64)
+    rc = _load().ora_correlate_int(ctypes.byref(d.c()), _p(volt), _p(vis), _p(wts))
+    if rc:
+        raise ValueError(f"oracle rejected the job (rc={rc})")
+    return vis, wts

@@ -1,0 +1,353 @@
+#!/usr/bin/env python3
+"""Benchmark of the MWAX FX correlator hot path on one B300 (or N independent replicas).
+
+Workload (full-array plain form): 256 tiles x 2 pols = 512 signal paths, one coarse
+channel, one 8 s sub-observation at 1.28 MS/s (10.24 M int8 complex samples per path,
+seeded noise sigma=16 plus a common point source with linear per-tile delays, sky
+frequency 139.52 MHz), 128-point FFT (10 kHz), 0.5 s integrations (16 per call),
+averaged to 40 kHz (fscrunch 4), FP32.  One step = one mwax_correlate call over the
+whole sub-observation (F-step + X-step + averaging/ordering for all 16 integrations).
+
+metric: real-time 256-tile coarse channels per B300 = 8 s / (device time per
+sub-observation), summed over GPUs.  Inputs (10.5 GB) exceed the 126 MB L2, so no flush
+is needed between steps.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SUBOBS_S = 8.0
+FS = 1_280_000.0
+WORKLOAD = dict(name="full-array plain FX, 256 tiles, 8 s sub-observation, N=128, 0.5 s, fscrunch 4",
+                n_tiles=256, fft_len=128, fine_avg=4, int_time_s=0.5, samples=10_240_000, seed=0x4D574159,
+                sky_freq_hz=139.52e6)
+# one 0.5 s integration of the same array: the small case used for ncu captures
+SMALL = dict(WORKLOAD, name="full-array plain FX, 256 tiles, one 0.5 s integration, N=128, fscrunch 4",
+             samples=640_000)
+METRIC = "real-time 256-tile coarse channels per B300"
+FP32_LANES_PER_SM, N_SM = 128, 148
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "sm_max_mhz": 2032.0}, \
+            "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for k, n in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(n)
+        load = [s for s in sm if mx and s > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": mx, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- inputs
+def make_inputs(W, pin: bool):
+    import torch
+    import synth
+    T, S = W["n_tiles"], W["samples"]
+    delay = synth.tile_delays_linear(W["seed"], T)
+    host = torch.empty(S // 64_000 * 2 * T * 64_000 * 2, dtype=torch.int8, pin_memory=pin)
+    synth.voltages(W["seed"], 2 * T, S, tones=synth.point_source_tones(W["seed"]), delay_c01=delay[:, :2],
+                   sky_freq_hz=W["sky_freq_hz"], out=host.numpy().reshape(-1, 2 * T, 64_000, 2))
+    return host, delay
+
+
+def used_bins(N: int, F: int, keep_dc: int = 0) -> int:
+    """Ultrafine channels that feed at least one output channel (Sec. 2.6 geometry)."""
+    M, half = N // F, F // 2
+    used = set()
+    for j in range(M):
+        mid = (j - M // 2) * F
+        for u in range(mid - half, mid + half + 1):
+            if not -(N // 2) <= u < N - N // 2:
+                continue
+            if u == 0 and F > 1 and not keep_dc:
+                continue
+            used.add(u)
+    return len(used)
+
+
+def algorithmic_work(T: int, N: int, F: int, K: int, n_ints: int, prec_bytes: int):
+    """Algorithmic work of one call: X flops over the ultrafine bins that feed an output
+    (8 real flops per complex multiply-accumulate over the unique pairs p <= q), and
+    F-step bytes (2 B of int8 in, two operand planes out per sample and path)."""
+    n = 2 * T
+    used = used_bins(N, F)
+    pairs = n * (n + 1) // 2
+    x_flops = 8.0 * pairs * K * used * n_ints
+    f_bytes = (2.0 + 2 * prec_bytes) * n * K * N * n_ints
+    return x_flops, f_bytes, used
+
+
+# ------------------------------------------------------------------------- cpu / oracle
+def oracle_sample_time(threads_note: dict):
+    """Time the FP64 oracle on a bounded sample of the workload: a 32-tile sub-array, one
+    0.5 s integration (5000 frames), same N, F and delays.  Returns (seconds per 8 s
+    256-tile sub-observation extrapolated, description, measured seconds)."""
+    import oracle
+    import synth
+    W = WORKLOAD
+    Ts, N, F = 32, W["fft_len"], W["fine_avg"]
+    K = int(W["int_time_s"] * FS) // N
+    S = K * N
+    d = synth.tile_delays_linear(W["seed"], Ts)
+    volt = synth.voltages(W["seed"], 2 * Ts, S, tones=synth.point_source_tones(W["seed"]), delay_c01=d[:, :2],
+                          sky_freq_hz=W["sky_freq_hz"])
+    desc = oracle.Desc(n_tiles=Ts, fft_len=N, fine_avg=F, int_frames=K, n_samples=S,
+                       sky_freq_hz=W["sky_freq_hz"])
+    t0 = time.perf_counter()
+    for p in range(2 * Ts):
+        oracle.spectra(desc, volt, d, p, 0, K)
+    t_f = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.correlate(desc, volt, d)
+    t_all = time.perf_counter() - t0
+    t_x = max(t_all - t_f, 0.0)
+    n_s, n_f = 2 * Ts, 2 * W["n_tiles"]
+    bp_s, bp_f = Ts * (Ts + 1) // 2, W["n_tiles"] * (W["n_tiles"] + 1) // 2
+    n_ints = int(SUBOBS_S / W["int_time_s"])
+    est = (t_f * (n_f / n_s) + t_x * (bp_f / bp_s)) * n_ints
+    desc_s = (f"{Ts}-tile sub-array, one 0.5 s integration (N=128, F=4): F part x{n_f // n_s} paths, X part "
+              f"x{bp_f / bp_s:.1f} baselines, x{n_ints} integrations")
+    threads_note["cores"] = int(os.environ.get("OMP_NUM_THREADS", 0)) or len(os.sched_getaffinity(0))
+    return est, desc_s, t_all
+
+
+# ----------------------------------------------------------------------------- arms
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    note = {}
+    for _ in range(args.warmup):
+        oracle_sample_time(note)
+    ests, descs, meas = [], "", []
+    for _ in range(args.steps):
+        est, descs, t = oracle_sample_time(note)
+        ests.append(est)
+        meas.append(t)
+    est = statistics.median(ests)
+    value = SUBOBS_S / est
+    line = {"metric": METRIC, "value": value, "unit": "channels", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * est, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded noise + point source)",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD["name"], "precision": "fp64 oracle on host cores"},
+            "cpu_baseline": {"value": value, "unit": "channels", "cores": note.get("cores"), "kind": "oracle",
+                             "sample": descs},
+            "e2e": {"value": value, "unit": "channels", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_mine(args, world, rank, local):
+    import torch
+    import paper_2303_11557_b300 as mw
+
+    torch.cuda.set_device(local)
+    W = SMALL if args.workload == "small" else WORKLOAD
+    host, delay = make_inputs(W, pin=not args.no_e2e)
+    dev_volt = host.cuda(non_blocking=False)
+    dev_delay = torch.from_numpy(delay).cuda()
+    desc = mw.PlanDesc(n_tiles=W["n_tiles"], fft_len=W["fft_len"], fine_avg=W["fine_avg"],
+                       int_time_s=W["int_time_s"], samples_per_call=W["samples"], precision=mw.MWAX_FP32,
+                       sky_freq_hz=W["sky_freq_hz"])
+    plan = mw.mwax_plan_create_ex(desc)
+    stream = torch.cuda.current_stream()
+    mw.mwax_plan_set_stream(plan, stream)
+    out = mw.empty_output(plan)
+    for _ in range(args.warmup):
+        mw.mwax_correlate(plan, dev_volt, dev_delay, out)
+    mw.mwax_plan_sync(plan)
+    mw.mwax_plan_stage_times(plan)          # reset counters
+    mw.mwax_plan_enable_timing(plan, True)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        mw.mwax_correlate(plan, dev_volt, dev_delay, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ck = clocks.stop()
+    mw.mwax_plan_sync(plan)
+    stages = mw.mwax_plan_stage_times(plan)
+    mw.mwax_plan_enable_timing(plan, False)
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = max_over_ranks(ms, world)
+
+    info = plan.info
+    K, n_ints = info["frames_per_int"], info["n_ints"]
+    x_flops, f_bytes, used = algorithmic_work(W["n_tiles"], W["fft_len"], W["fine_avg"], K, n_ints, 4)
+    pk, pk_kind = peaks()
+    x_ms, x_n = stages["xstep"]
+    f_ms, f_n = stages["fstep"]
+    x_per_launch = x_flops * args.steps / x_n
+    x_avg_ms = x_ms / x_n
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    x_achieved = x_per_launch / (x_avg_ms * 1e-3) / 1e12
+    f_per_launch = f_bytes * args.steps / f_n
+    f_avg_ms = f_ms / f_n
+    f_achieved = f_per_launch / (f_avg_ms * 1e-3) / 1e9
+
+    # end to end through the host-memory entry point (pinned buffers)
+    e2e = None
+    if not args.no_e2e:
+        host_out = torch.empty(plan.output_bytes, dtype=torch.uint8, pin_memory=True)
+        mw.mwax_correlate_host(plan, host, delay, host_out)   # warm-up (allocates staging)
+        reps = max(1, min(args.steps, 3))
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            mw.mwax_correlate_host(plan, host, delay, host_out)
+        t_e2e = max_over_ranks((time.perf_counter() - t0) / reps, world)
+        e2e = {"value": world * n_ints * W["int_time_s"] / t_e2e, "unit": "channels", "h2d_bytes_per_step": info["input_bytes"] +
+               delay.nbytes, "d2h_bytes_per_step": info["output_bytes"], "ms_per_step": 1e3 * t_e2e}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        note = {}
+        est, sample, _ = oracle_sample_time(note)
+        cpu = {"value": SUBOBS_S / est, "unit": "channels", "cores": note["cores"], "kind": "oracle",
+               "sample": sample, "extrapolated_s_per_subobs": est}
+
+    if rank != 0:
+        return
+    launches = sum(v[1] for v in stages.values())
+    line = {
+        "metric": METRIC, "value": world * SUBOBS_S * (n_ints * W["int_time_s"] / SUBOBS_S) / (ms_max * 1e-3), "unit": "channels", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded Gaussian sigma=16 + point source, linear per-tile delays)",
+        "config": {"workload": W["name"], "n_tiles": W["n_tiles"], "fft_len": W["fft_len"],
+                   "fine_avg": W["fine_avg"], "int_time_s": W["int_time_s"], "subobs_s": SUBOBS_S,
+                   "precision": "fp32", "l2": "inputs 10.5 GB > 126 MB L2, no flush needed",
+                   "parallelism": f"replicas x{world} (independent coarse channels)"},
+        "roofline": {"bound": "alu", "kernel": "xstep_simt_kernel", "achieved": x_achieved, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": x_achieved / fp32_peak, "traffic": None,
+                     "peak_kind": f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {pk.get('sm_max_mhz')} MHz "
+                                  f"({pk_kind} max clock)",
+                     "per_launch": f"{x_per_launch:.4g} flop (8 x pairs x frames x {used} used bins)",
+                     "avg_launch_ms": x_avg_ms},
+        "roofline_fstep": {"bound": "hbm", "kernel": "fstep_kernel<128>", "achieved": f_achieved,
+                           "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": f_achieved / pk["hbm_gbs"],
+                           "per_launch_bytes": f_per_launch, "avg_launch_ms": f_avg_ms,
+                           "peak_kind": f"{pk_kind} copy bandwidth"},
+        "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+        "gpu_launches": launches,
+        "clocks": ck,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "context": {"paper": "1 coarse channel of 256 tiles in real time per NVIDIA A40 (6.2 s per 8 s at "
+                             "250 ms / 40 kHz, Table 2)"},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="full", choices=["full", "small"],
+                    help="small = one 0.5 s integration (for profiler captures)")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_mine(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,174 @@
+/*
+ * mwax.h -- C ABI of a single-GPU (NVIDIA B300, sm_103a) MWAX FX correlator stage.
+ *
+ * The library turns a sub-observation of int8 complex coarse-channel voltages
+ * (tiles x 2 polarisations) into averaged visibilities, as the GPU stage of the
+ * MWAX FX-engine does (Morrison et al., "MWAX: A New Correlator for the Murchison
+ * Widefield Array", Sec. 2.5-2.7):
+ *   F-step  unpack int8, fine-channel FFT of N points, per-path delay/phase
+ *           correction (Sec. 2.5.1, 4.3), written as X-engine operands;
+ *   X-step  Hermitian cross-power of all signal-path pairs per fine channel,
+ *           summed over the frames of each integration (Sec. 2.5.2);
+ *   average centre-symmetric channel averaging by fscrunch F (Sec. 2.6), written in
+ *           MWAX_ORDER with the visibility weights table after each set (Sec. 2.7).
+ * Every step runs in the library's own CUDA kernels.  There is no CPU fallback: on a
+ * machine without a usable B300 the calls fail with MWAX_ECUDA.
+ *
+ * Conventions (the paper leaves these open; the library fixes them as follows):
+ *   - sample rate Fs = 1,280,000 complex samples/s (Sec. 2.5);
+ *   - signal path p = 2 * tile + pol, pol x = 0, y = 1;
+ *   - voltages: int8 [block][path][block_samples][2] (re, im), block_samples = 64,000
+ *     by default (one 50 ms data block per path, Sec. 2.5);
+ *   - frame m = samples [m N, (m+1) N) of the call; forward unnormalised FFT
+ *     X[k] = sum_n x[n] e^{-2 pi i k n / N};
+ *   - channel c = u + floor(N/2) for ultrafine offset u (centre-symmetric, DC at
+ *     c = N/2, Sec. 2.6); f_u = u Fs / N;
+ *   - delay correction Y = X exp(+2 pi i (nu + f_u) tau_p(t_m)), with
+ *     tau_p(t) = c0 + c1 t + c2 t^2 seconds, t_m = (m + 1/2) N / Fs seconds from the
+ *     call's first sample, nu = sky frequency of the coarse channel (Sec. 2.5.1);
+ *   - cross-power V_pq = sum_m Y_p conj(Y_q) (time is a sum, frequency a weighted
+ *     mean over the ultrafine bins of each output channel, Sec. 2.6);
+ *   - MWAX_ORDER: [integration][baseline][channel][pol], baselines (i <= j) row-major
+ *     over the upper triangle including autos, pols xx, xy, yx, yy (Sec. 2.7);
+ *   - after each integration's visibilities: weights float32 [baseline][pol], all 1.0
+ *     (the paper's current occupancy weights, Sec. 2.7).
+ */
+#ifndef MWAX_H
+#define MWAX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mwax_plan mwax_plan;
+
+typedef enum {
+    MWAX_OK = 0,
+    MWAX_EINVAL = 1,        /* invalid argument or plan parameters                  */
+    MWAX_ENOMEM = 2,        /* device or host allocation failed                      */
+    MWAX_ECUDA = 3,         /* CUDA runtime error (no device, launch failure, ...)   */
+    MWAX_EUNSUPPORTED = 4,  /* valid per the paper but not built (e.g. an FFT length) */
+    MWAX_ETIMEOUT = 5       /* a device-side bounded wait gave up (status word)      */
+} mwax_status;
+
+typedef enum {
+    MWAX_FP32 = 0,  /* FP32 FFT and FP32 CUDA-core cross-multiply (the paper's form)     */
+    MWAX_FP16 = 1,  /* FP32 FFT, FP16 operands on tcgen05 tensor cores, FP32 accumulate  */
+    MWAX_FP8 = 2,   /* FP32 FFT, e4m3 operands with per-path-per-channel scales, tcgen05 */
+    MWAX_INT8 = 3   /* no FFT (N = 1, F = 1), exact integer sums, int64 output           */
+} mwax_precision;
+
+/* Plan parameters.  Zero-initialise and set what you need; zero selects the default. */
+typedef struct {
+    int n_tiles;                 /* T >= 1; signal paths n = 2 T                          */
+    int fft_len;                 /* N: fine-channel FFT length (1 = no FFT)               */
+    int fine_avg;                /* F: fscrunch, N % F == 0; output channels M = N / F    */
+    double int_time_s;           /* integration time; int_time * Fs must be a multiple of N */
+    long long samples_per_call;  /* samples per path per call; 0 = one integration        */
+    int block_samples;           /* samples per path per data block; 0 = 64,000           */
+    int precision;               /* mwax_precision; 0 = MWAX_FP32                          */
+    double sky_freq_hz;          /* nu, centre frequency of the coarse channel; 0 allowed  */
+    int keep_dc;                 /* 0 (default) = exclude DC from the centre channel when
+                                    F > 1 (Sec. 2.6); 1 = keep it                          */
+    size_t workspace_limit;      /* bytes of device workspace; 0 = 16 GiB                 */
+} mwax_plan_desc;
+
+/* Derived sizes of a plan (all counts per call). */
+typedef struct {
+    int n_paths;                 /* n = 2 T                                   */
+    long long n_baselines;       /* B = T (T + 1) / 2                         */
+    int n_chan_out;              /* M = N / F                                 */
+    long long frames_per_int;    /* K = int_time Fs / N                       */
+    long long n_ints;            /* integrations per call                     */
+    size_t input_bytes;          /* n_blocks * n * block_samples * 2          */
+    size_t vis_set_bytes;        /* one integration's visibilities            */
+    size_t weights_bytes;        /* one integration's weights table           */
+    size_t output_bytes;         /* n_ints * (vis_set_bytes + weights_bytes)  */
+    size_t workspace_bytes;      /* device memory the plan holds              */
+    int precision;
+} mwax_plan_info;
+
+/*
+ * Create a plan: FP32 precision, sky frequency 0, DC excluded, one integration per
+ * call, 64,000-sample blocks.  Allocates the plan's device workspace on the current
+ * device.  Returns NULL on error (see mwax_last_error()).
+ * Validation (MWAX_EINVAL): n_tiles >= 1; fine_avg >= 1 and fft_len % fine_avg == 0;
+ * block_samples % fft_len == 0; int_time_s * Fs an integer multiple of fft_len;
+ * samples_per_call a multiple of both the integration length and block_samples.
+ * FFT lengths built (else MWAX_EUNSUPPORTED): 1, 16, 32, 64, 128, 256, 512, 640,
+ * 1280, 3200, 6400.  MWAX_INT8 needs fft_len = fine_avg = 1.
+ */
+mwax_plan* mwax_plan_create(int n_tiles, int fft_len, double int_time_s, int fine_avg);
+
+/* Create a plan from a descriptor (see mwax_plan_desc).  NULL on error. */
+mwax_plan* mwax_plan_create_ex(const mwax_plan_desc* desc);
+
+/* Sizes of a plan.  MWAX_EINVAL on NULL arguments. */
+mwax_status mwax_plan_get_info(const mwax_plan* plan, mwax_plan_info* info);
+
+/* Bytes of one call's output (visibility sets and weight tables of all integrations). */
+size_t mwax_plan_output_bytes(const mwax_plan* plan);
+
+/* Bytes of one call's input voltages. */
+size_t mwax_plan_input_bytes(const mwax_plan* plan);
+
+/* Enqueue all further work of this plan on `cuda_stream` (a cudaStream_t; NULL = the
+ * legacy default stream).  The plan does not own the stream. */
+mwax_status mwax_plan_set_stream(mwax_plan* plan, void* cuda_stream);
+
+/*
+ * Correlate one call's worth of voltages (samples_per_call samples per path).
+ *   voltages   device pointer, int8 [n_blocks][n][block_samples][2], caller-owned,
+ *              16-byte aligned;
+ *   delay_poly NULL (no delay/phase correction) or n x 3 float64 (c0 [s], c1 [s/s],
+ *              c2 [s/s^2]) per signal path, host or device memory; read before return
+ *              (host) or in stream order (device).  Must be NULL for MWAX_INT8;
+ *   vis_out    device pointer, mwax_plan_output_bytes() bytes, caller-owned, 16-byte
+ *              aligned.  Per integration: visibilities [B][M][4] complex float32
+ *              (MWAX_INT8: [B][1][4] pairs of int64 re, im), then weights float32 [B][4].
+ * The work is enqueued on the plan's stream and the call returns without waiting.
+ * Errors found by the kernels (bounded waits that gave up) are reported by the next
+ * mwax_plan_sync().  Not thread-safe per plan; use one plan per stream.
+ */
+mwax_status mwax_correlate(mwax_plan* plan, const int8_t* voltages, const double* delay_poly, void* vis_out);
+
+/*
+ * The same from host memory: copies the voltages to the device block by block on a
+ * copy stream, overlapped with the correlation, and copies the result back into
+ * vis_out (host).  Pinned host buffers give full PCIe bandwidth; pageable ones work.
+ * Synchronous: returns when vis_out holds the result.
+ */
+mwax_status mwax_correlate_host(mwax_plan* plan, const int8_t* voltages, const double* delay_poly, void* vis_out);
+
+/* Wait for the plan's stream; returns MWAX_ETIMEOUT / MWAX_ECUDA if a kernel reported
+ * an error since the last sync, and clears the device status word. */
+mwax_status mwax_plan_sync(mwax_plan* plan);
+
+/*
+ * Per-stage device time (the paper's Table 2 breaks the FX-engine time down by
+ * sub-function).  While enabled, CUDA events bracket each of the plan's kernel launches
+ * on its stream.  mwax_plan_stage_times() waits for the stream and returns, per stage,
+ * the summed milliseconds and the number of launches since the last call (then resets):
+ * stage 0 = output init (zero + weights), 1 = F-step, 2 = X-step.  Launch counts are
+ * kept whether or not timing is enabled.
+ */
+mwax_status mwax_plan_enable_timing(mwax_plan* plan, int enable);
+mwax_status mwax_plan_stage_times(mwax_plan* plan, double ms[3], long long launches[3]);
+
+/* Free the plan and its device workspace (waits for its stream first).  NULL is a no-op. */
+void mwax_plan_destroy(mwax_plan* plan);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* mwax_last_error(void);
+
+/* Library version string. */
+const char* mwax_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MWAX_H */

@@ -1,0 +1,285 @@
+"""Python binding of the MWAX B300 correlator C ABI (``include/mwax.h``).
+
+Argument marshalling only: every step of the correlation runs in ``libmwax.so``'s CUDA
+kernels.  PyTorch supplies device memory and streams.  There is no fallback: if the
+library is missing or no GPU is usable, the calls raise.
+
+    plan = mwax_plan_create_ex(PlanDesc(n_tiles=256, fft_len=128, fine_avg=4, int_time_s=0.5,
+                                        samples_per_call=10_240_000, precision=MWAX_FP32))
+    out = empty_output(plan)                 # torch uint8 buffer on the current device
+    mwax_correlate(plan, volt, delay, out)   # volt: int8 [blocks, paths, block_samples, 2]
+    vis, weights = split_output(plan, out)   # views: complex64 [ints, B, M, 4], float32 [ints, B, 4]
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+MWAX_OK, MWAX_EINVAL, MWAX_ENOMEM, MWAX_ECUDA, MWAX_EUNSUPPORTED, MWAX_ETIMEOUT = range(6)
+MWAX_FP32, MWAX_FP16, MWAX_FP8, MWAX_INT8 = range(4)
+PRECISIONS = {"fp32": MWAX_FP32, "fp16": MWAX_FP16, "fp8": MWAX_FP8, "int8": MWAX_INT8}
+FS = 1_280_000.0
+BLOCK_SAMPLES = 64_000
+
+LIB_PATH = _build.LIB
+
+
+class MwaxError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"mwax status {status}: {msg}")
+        self.status = status
+
+
+class _CDesc(ctypes.Structure):
+    _fields_ = [("n_tiles", ctypes.c_int), ("fft_len", ctypes.c_int), ("fine_avg", ctypes.c_int),
+                ("int_time_s", ctypes.c_double), ("samples_per_call", ctypes.c_longlong),
+                ("block_samples", ctypes.c_int), ("precision", ctypes.c_int), ("sky_freq_hz", ctypes.c_double),
+                ("keep_dc", ctypes.c_int), ("workspace_limit", ctypes.c_size_t)]
+
+
+class _CInfo(ctypes.Structure):
+    _fields_ = [("n_paths", ctypes.c_int), ("n_baselines", ctypes.c_longlong), ("n_chan_out", ctypes.c_int),
+                ("frames_per_int", ctypes.c_longlong), ("n_ints", ctypes.c_longlong),
+                ("input_bytes", ctypes.c_size_t), ("vis_set_bytes", ctypes.c_size_t),
+                ("weights_bytes", ctypes.c_size_t), ("output_bytes", ctypes.c_size_t),
+                ("workspace_bytes", ctypes.c_size_t), ("precision", ctypes.c_int)]
+
+
+@dataclass
+class PlanDesc:
+    n_tiles: int
+    fft_len: int
+    fine_avg: int
+    int_time_s: float
+    samples_per_call: int = 0
+    block_samples: int = 0
+    precision: int = MWAX_FP32
+    sky_freq_hz: float = 0.0
+    keep_dc: int = 0
+    workspace_limit: int = 0
+
+    def c(self) -> _CDesc:
+        return _CDesc(self.n_tiles, self.fft_len, self.fine_avg, self.int_time_s, self.samples_per_call,
+                      self.block_samples, int(self.precision), self.sky_freq_hz, self.keep_dc, self.workspace_limit)
+
+
+_lib = None
+SYMBOLS = ("mwax_plan_create", "mwax_plan_create_ex", "mwax_plan_get_info", "mwax_plan_output_bytes",
+           "mwax_plan_input_bytes", "mwax_plan_set_stream", "mwax_correlate", "mwax_correlate_host",
+           "mwax_plan_sync", "mwax_plan_destroy", "mwax_last_error", "mwax_version", "mwax_plan_enable_timing",
+           "mwax_plan_stage_times")
+
+
+def load_library(path: str | None = None):
+    """Load libmwax.so (building it first if the sources are newer and nvcc is present)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if _build.stale():
+        try:
+            _build.build()
+        except (OSError, FileNotFoundError) as e:  # no nvcc: use what is there, or fail
+            if not os.path.exists(path):
+                raise ImportError(f"libmwax.so missing and cannot be built: {e}") from e
+    if not os.path.exists(path):
+        raise ImportError(f"libmwax.so not found at {path}; run `python -m paper_2303_11557_b300._build`")
+    lib = ctypes.CDLL(path)
+    vp, st = ctypes.c_void_p, ctypes.c_int
+    lib.mwax_plan_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int]
+    lib.mwax_plan_create.restype = vp
+    lib.mwax_plan_create_ex.argtypes = [ctypes.POINTER(_CDesc)]
+    lib.mwax_plan_create_ex.restype = vp
+    lib.mwax_plan_get_info.argtypes = [vp, ctypes.POINTER(_CInfo)]
+    lib.mwax_plan_get_info.restype = st
+    lib.mwax_plan_output_bytes.argtypes = [vp]
+    lib.mwax_plan_output_bytes.restype = ctypes.c_size_t
+    lib.mwax_plan_input_bytes.argtypes = [vp]
+    lib.mwax_plan_input_bytes.restype = ctypes.c_size_t
+    lib.mwax_plan_set_stream.argtypes = [vp, vp]
+    lib.mwax_plan_set_stream.restype = st
+    lib.mwax_correlate.argtypes = [vp, vp, vp, vp]
+    lib.mwax_correlate.restype = st
+    lib.mwax_correlate_host.argtypes = [vp, vp, vp, vp]
+    lib.mwax_correlate_host.restype = st
+    lib.mwax_plan_sync.argtypes = [vp]
+    lib.mwax_plan_sync.restype = st
+    lib.mwax_plan_destroy.argtypes = [vp]
+    lib.mwax_plan_destroy.restype = None
+    lib.mwax_last_error.argtypes = []
+    lib.mwax_last_error.restype = ctypes.c_char_p
+    lib.mwax_plan_enable_timing.argtypes = [vp, ctypes.c_int]
+    lib.mwax_plan_enable_timing.restype = st
+    lib.mwax_plan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
+    lib.mwax_plan_stage_times.restype = st
+    lib.mwax_version.argtypes = []
+    lib.mwax_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def mwax_last_error() -> str:
+    return load_library().mwax_last_error().decode()
+
+
+def mwax_version() -> str:
+    return load_library().mwax_version().decode()
+
+
+def _check(status: int):
+    if status != MWAX_OK:
+        raise MwaxError(status, mwax_last_error())
+
+
+class Plan:
+    """Owns one mwax_plan*; destroyed with the object."""
+
+    def __init__(self, handle: int, desc: PlanDesc):
+        self.handle = handle
+        self.desc = desc
+        info = _CInfo()
+        _check(load_library().mwax_plan_get_info(handle, ctypes.byref(info)))
+        self.info = {k: getattr(info, k) for k, _ in _CInfo._fields_}
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.mwax_plan_destroy(h)
+
+    def close(self):
+        self.__del__()
+
+    # convenience accessors
+    n_ints = property(lambda self: self.info["n_ints"])
+    n_baselines = property(lambda self: self.info["n_baselines"])
+    n_chan_out = property(lambda self: self.info["n_chan_out"])
+    output_bytes = property(lambda self: self.info["output_bytes"])
+    input_bytes = property(lambda self: self.info["input_bytes"])
+
+
+def mwax_plan_create(n_tiles: int, fft_len: int, int_time_s: float, fine_avg: int) -> Plan:
+    h = load_library().mwax_plan_create(n_tiles, fft_len, int_time_s, fine_avg)
+    if not h:
+        raise MwaxError(MWAX_EINVAL, mwax_last_error())
+    return Plan(h, PlanDesc(n_tiles, fft_len, fine_avg, int_time_s))
+
+
+def mwax_plan_create_ex(desc: PlanDesc) -> Plan:
+    cd = desc.c()
+    h = load_library().mwax_plan_create_ex(ctypes.byref(cd))
+    if not h:
+        err = mwax_last_error()
+        code = MWAX_EUNSUPPORTED if "not built" in err else MWAX_EINVAL
+        raise MwaxError(code, err)
+    return Plan(h, desc)
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _delay_arg(delay, plan: Plan, device: bool):
+    """delay polynomial -> (pointer, keepalive).  float64 [n_paths, 3] host or device."""
+    if delay is None:
+        return None, None
+    n = 2 * plan.desc.n_tiles
+    if isinstance(delay, np.ndarray):
+        d = np.ascontiguousarray(delay, dtype=np.float64)
+        if d.size != 3 * n:
+            raise ValueError("delay_poly must hold n_paths x 3 float64")
+        return d.ctypes.data, d
+    import torch
+    if delay.dtype != torch.float64 or delay.numel() != 3 * n or not delay.is_contiguous():
+        raise ValueError("delay_poly must be a contiguous float64 tensor of n_paths x 3")
+    return delay.data_ptr(), delay
+
+
+def mwax_plan_set_stream(plan: Plan, stream=None):
+    """Enqueue the plan's work on a torch.cuda.Stream (default: torch's current stream)."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(load_library().mwax_plan_set_stream(plan.handle, ctypes.c_void_p(s.cuda_stream)))
+
+
+def mwax_correlate(plan: Plan, voltages, delay_poly, vis_out):
+    """voltages: CUDA int8 tensor, plan.input_bytes; vis_out: CUDA tensor of plan.output_bytes."""
+    if not voltages.is_cuda or not vis_out.is_cuda:
+        raise ValueError("mwax_correlate takes device tensors; use mwax_correlate_host for host memory")
+    if voltages.numel() * voltages.element_size() != plan.input_bytes or not voltages.is_contiguous():
+        raise ValueError(f"voltages must be a contiguous buffer of {plan.input_bytes} bytes")
+    if vis_out.numel() * vis_out.element_size() < plan.output_bytes:
+        raise ValueError(f"vis_out must hold {plan.output_bytes} bytes")
+    dptr, keep = _delay_arg(delay_poly, plan, True)
+    _check(load_library().mwax_correlate(plan.handle, _ptr(voltages), dptr, _ptr(vis_out)))
+    return keep
+
+
+def mwax_correlate_host(plan: Plan, voltages, delay_poly, vis_out):
+    """Host buffers (numpy or CPU tensors, pinned for full bandwidth); synchronous."""
+    dptr, keep = _delay_arg(delay_poly, plan, False)
+    _check(load_library().mwax_correlate_host(plan.handle, _ptr(voltages), dptr, _ptr(vis_out)))
+    return keep
+
+
+def mwax_plan_sync(plan: Plan):
+    _check(load_library().mwax_plan_sync(plan.handle))
+
+
+def mwax_plan_enable_timing(plan: Plan, enable: bool = True):
+    _check(load_library().mwax_plan_enable_timing(plan.handle, int(bool(enable))))
+
+
+STAGES = ("init", "fstep", "xstep")
+
+
+def mwax_plan_stage_times(plan: Plan):
+    """{stage: (milliseconds, launches)} since the last call (waits for the plan's stream)."""
+    ms = (ctypes.c_double * 3)()
+    n = (ctypes.c_longlong * 3)()
+    _check(load_library().mwax_plan_stage_times(plan.handle, ms, n))
+    return {STAGES[i]: (ms[i], n[i]) for i in range(3)}
+
+
+def mwax_plan_destroy(plan: Plan):
+    plan.close()
+
+
+def empty_output(plan: Plan, device=None):
+    import torch
+    return torch.empty(plan.output_bytes, dtype=torch.uint8, device=device or "cuda")
+
+
+def split_output(plan: Plan, out):
+    """Views of a call's output: (vis, weights).
+
+    Float precisions: vis complex64 [ints, B, M, 4]; MWAX_INT8: vis int64 [ints, B, 4, 2].
+    weights: float32 [ints, B, 4]."""
+    info = plan.info
+    n_ints, B, M = info["n_ints"], info["n_baselines"], info["n_chan_out"]
+    per = info["vis_set_bytes"] + info["weights_bytes"]
+    if isinstance(out, np.ndarray):
+        raw = out.reshape(-1)[: n_ints * per].reshape(n_ints, per)
+        vis_raw, w_raw = raw[:, : info["vis_set_bytes"]], raw[:, info["vis_set_bytes"]:]
+        if info["precision"] == MWAX_INT8:
+            vis = vis_raw.copy().view(np.int64).reshape(n_ints, B, 4, 2)
+        else:
+            vis = vis_raw.copy().view(np.complex64).reshape(n_ints, B, M, 4)
+        return vis, w_raw.copy().view(np.float32).reshape(n_ints, B, 4)
+    import torch
+    raw = out.reshape(-1)[: n_ints * per].view(n_ints, per)
+    vis_raw, w_raw = raw[:, : info["vis_set_bytes"]], raw[:, info["vis_set_bytes"]:]
+    if info["precision"] == MWAX_INT8:
+        vis = vis_raw.contiguous().view(torch.int64).view(n_ints, B, 4, 2)
+    else:
+        vis = vis_raw.contiguous().view(torch.float32).view(n_ints, B, M, 4, 2)
+        vis = torch.view_as_complex(vis)
+    return vis, w_raw.contiguous().view(torch.float32).view(n_ints, B, 4)

@@ -1,0 +1,550 @@
+// C ABI of the MWAX B300 correlator: plan creation and validation, the channel-averaging
+// tables, device workspace, and the per-call launch sequence
+//   init output -> for each group of integrations: F-step -> X-step.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "mwax_internal.cuh"
+
+using namespace mwax;
+
+struct mwax_plan {
+    mwax_plan_desc desc;
+    int T = 0, n = 0, N = 0, F = 0, M = 0, bs = 0, prec = 0, dc_excl = 1;
+    long long K = 0, S = 0, n_ints = 0, B = 0, n_blocks = 0;
+    double nu = 0.0;
+    size_t vis_set_bytes = 0, weights_bytes = 0, int_stride = 0, input_bytes = 0;
+
+    // integration grouping: `slots` integrations per launch, or one integration split
+    // into `chunks` launches of at most Kc frames
+    long long slots = 1, Kc = 0, Kpad = 0;
+    int chunks = 1;
+    int elem_bytes = 4;
+
+    // device memory
+    void* Y = nullptr;
+    size_t Y_bytes = 0;
+    float2* tw = nullptr;
+    double* delay = nullptr;
+    BinCoef* bins = nullptr;
+    RunInfo* runs = nullptr;
+    int n_runs = 0;
+    int2* tiles = nullptr;
+    int n_tiles = 0;
+    int* status = nullptr;
+    float out_scale = 1.0f, post_scale = 1.0f;
+
+    // host-input path
+    int8_t* dvolt = nullptr;
+    char* dout = nullptr;
+    cudaStream_t copy_stream = nullptr;
+    std::vector<cudaEvent_t> events;
+
+    cudaStream_t stream = nullptr;
+    int device = 0;
+
+    // stage timing: event pairs per launch, drained by mwax_plan_stage_times
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
+    long long launches[3] = {0, 0, 0};
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+mwax_status fail(mwax_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+mwax_status fail(mwax_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define MWAX_CUDA(call)                                                                                  \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess)                                                                           \
+            return fail(e_ == cudaErrorMemoryAllocation ? MWAX_ENOMEM : MWAX_ECUDA, "%s: %s (%s:%d)", #call, \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                                     \
+    } while (0)
+
+// Output channel j of M = N/F: centred on ultrafine offset (j - floor(M/2)) F; odd F
+// takes F bins of weight 1, even F takes F+1 bins with the two ends at 1/2; the DC bin
+// is dropped from the centre channel when F > 1 (unless kept); bins beyond the coarse
+// channel do not exist (Sec. 2.6).  Fills per-bin coefficients w / sum(w).
+bool build_bins(int N, int F, int dc_excl, std::vector<BinCoef>& bins, std::vector<double>& wsum)
+{
+    const int M = N / F, jc = M / 2, half = F / 2;
+    bins.assign(N, BinCoef{-1, -1, 0.0f, 0.0f});
+    wsum.assign(M, 0.0);
+    std::vector<std::vector<std::pair<int, double>>> members(M);
+    for (int j = 0; j < M; ++j) {
+        const long long mid = (long long)(j - jc) * F;
+        for (long long u = mid - half; u <= mid + half; ++u) {
+            const long long c = u + N / 2;
+            if (c < 0 || c >= N) continue;
+            double w = (F % 2 == 0 && (u == mid - half || u == mid + half)) ? 0.5 : 1.0;
+            if (dc_excl && F > 1 && u == 0) w = 0.0;
+            if (w == 0.0) continue;
+            members[j].push_back({(int)c, w});
+            wsum[j] += w;
+        }
+    }
+    for (int j = 0; j < M; ++j) {
+        if (wsum[j] <= 0.0) return false;
+        for (auto& m : members[j]) {
+            BinCoef& b = bins[m.first];
+            const float coef = (float)(m.second / wsum[j]);
+            if (b.ja < 0) {
+                b.ja = j;
+                b.ca = coef;
+            } else if (b.jb < 0) {
+                b.jb = j;
+                b.cb = coef;
+            } else {
+                return false;   // a bin feeds at most two channels
+            }
+        }
+    }
+    return true;
+}
+
+int prec_elem_bytes(int prec)
+{
+    switch (prec) {
+        case MWAX_FP32: return 4;
+        case MWAX_FP16: return 2;
+        case MWAX_FP8: return 1;
+        case MWAX_INT8: return 2;   // int8 held exactly in FP16 operands
+        default: return 0;
+    }
+}
+
+void free_plan(mwax_plan* p)
+{
+    if (!p) return;
+    cudaFree(p->Y);
+    cudaFree(p->tw);
+    cudaFree(p->delay);
+    cudaFree(p->bins);
+    cudaFree(p->runs);
+    cudaFree(p->tiles);
+    cudaFree(p->status);
+    cudaFree(p->dvolt);
+    cudaFree(p->dout);
+    for (auto e : p->events) cudaEventDestroy(e);
+    for (auto e : p->ev_pool) cudaEventDestroy(e);
+    for (auto& u : p->ev_used) {
+        cudaEventDestroy(u.second.first);
+        cudaEventDestroy(u.second.second);
+    }
+    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+    delete p;
+}
+
+mwax_status validate(const mwax_plan_desc& d, mwax_plan& p)
+{
+    if (d.n_tiles < 1) return fail(MWAX_EINVAL, "n_tiles must be >= 1 (got %d)", d.n_tiles);
+    if (d.fft_len < 1) return fail(MWAX_EINVAL, "fft_len must be >= 1 (got %d)", d.fft_len);
+    if (d.fine_avg < 1 || d.fft_len % d.fine_avg)
+        return fail(MWAX_EINVAL, "fine_avg (%d) must divide fft_len (%d)", d.fine_avg, d.fft_len);
+    const int bs = d.block_samples ? d.block_samples : kDefaultBlock;
+    if (bs < 1 || bs % d.fft_len)
+        return fail(MWAX_EINVAL, "block_samples (%d) must be a multiple of fft_len (%d)", bs, d.fft_len);
+    if (!(d.int_time_s > 0.0)) return fail(MWAX_EINVAL, "int_time_s must be > 0");
+    const double int_samples_d = d.int_time_s * kFs;
+    const long long int_samples = llround(int_samples_d);
+    if (fabs(int_samples_d - (double)int_samples) > 1e-9 * std::max(1.0, int_samples_d) || int_samples < 1)
+        return fail(MWAX_EINVAL, "int_time_s * Fs must be a whole number of samples");
+    if (int_samples % d.fft_len)
+        return fail(MWAX_EINVAL, "integration (%lld samples) must be a whole number of %d-sample frames",
+                    int_samples, d.fft_len);
+    const long long S = d.samples_per_call ? d.samples_per_call : int_samples;
+    if (S < 1 || S % int_samples)
+        return fail(MWAX_EINVAL, "samples_per_call (%lld) must be a multiple of the integration (%lld)", S,
+                    int_samples);
+    if (S % bs) return fail(MWAX_EINVAL, "samples_per_call (%lld) must be a multiple of block_samples (%d)", S, bs);
+    if (d.precision < MWAX_FP32 || d.precision > MWAX_INT8)
+        return fail(MWAX_EINVAL, "unknown precision %d", d.precision);
+    if (d.precision == MWAX_INT8 && (d.fft_len != 1 || d.fine_avg != 1))
+        return fail(MWAX_EINVAL, "MWAX_INT8 needs fft_len = fine_avg = 1 (no FFT)");
+    if (!fft_len_supported(d.fft_len)) return fail(MWAX_EUNSUPPORTED, "fft_len %d is not built", d.fft_len);
+    if (d.fft_len > 1 && d.fft_len < 16) return fail(MWAX_EUNSUPPORTED, "fft_len %d is not built", d.fft_len);
+    if (d.precision != MWAX_FP32)
+        return fail(MWAX_EUNSUPPORTED, "precision %d is not built in this library version", d.precision);
+
+    p.desc = d;
+    p.T = d.n_tiles;
+    p.n = 2 * d.n_tiles;
+    p.N = d.fft_len;
+    p.F = d.fine_avg;
+    p.M = d.fft_len / d.fine_avg;
+    p.bs = bs;
+    p.prec = d.precision;
+    p.dc_excl = d.keep_dc ? 0 : 1;
+    p.nu = d.sky_freq_hz;
+    p.K = int_samples / d.fft_len;
+    p.S = S;
+    p.n_ints = S / int_samples;
+    p.B = (long long)p.T * (p.T + 1) / 2;
+    p.n_blocks = S / bs;
+    if (p.prec == MWAX_INT8) {
+        p.vis_set_bytes = (size_t)p.B * 4 * 16;
+    } else {
+        p.vis_set_bytes = (size_t)p.B * p.M * 4 * 8;
+    }
+    p.weights_bytes = (size_t)p.B * 4 * 4;
+    p.int_stride = p.vis_set_bytes + p.weights_bytes;
+    p.input_bytes = (size_t)p.n_blocks * p.n * bs * 2;
+    p.elem_bytes = prec_elem_bytes(p.prec);
+    return MWAX_OK;
+}
+
+mwax_status setup(mwax_plan& p)
+{
+    MWAX_CUDA(cudaGetDevice(&p.device));
+
+    // workspace: operand slots
+    const size_t limit = p.desc.workspace_limit ? p.desc.workspace_limit : ((size_t)16 << 30);
+    const long long Kpad_full = (p.K + kKAlign - 1) / kKAlign * kKAlign;
+    const size_t per_slot = (size_t)p.N * 2 * p.n * Kpad_full * p.elem_bytes;
+    if (per_slot <= limit) {
+        p.slots = std::min<long long>(p.n_ints, (long long)(limit / per_slot));
+        p.Kc = p.K;
+        p.Kpad = Kpad_full;
+        p.chunks = 1;
+    } else {
+        const size_t per_frame = (size_t)p.N * 2 * p.n * p.elem_bytes;
+        long long kc = (long long)(limit / per_frame) / kKAlign * kKAlign;
+        if (kc < kKAlign) return fail(MWAX_ENOMEM, "workspace_limit too small for one %d-frame chunk", kKAlign);
+        p.slots = 1;
+        p.Kc = kc;
+        p.Kpad = kc;
+        p.chunks = (int)((p.K + kc - 1) / kc);
+    }
+    p.Y_bytes = (size_t)p.slots * p.N * 2 * p.n * p.Kpad * p.elem_bytes;
+    MWAX_CUDA(cudaMalloc(&p.Y, p.Y_bytes));
+    MWAX_CUDA(cudaMemset(p.Y, 0, p.Y_bytes));
+
+    // twiddles e^{-2 pi i k / N}, rounded from FP64
+    std::vector<float2> tw(p.N);
+    for (int k = 0; k < p.N; ++k) {
+        const double a = -2.0 * M_PI * (double)k / (double)p.N;
+        tw[k] = make_float2((float)cos(a), (float)sin(a));
+    }
+    MWAX_CUDA(cudaMalloc(&p.tw, sizeof(float2) * p.N));
+    MWAX_CUDA(cudaMemcpy(p.tw, tw.data(), sizeof(float2) * p.N, cudaMemcpyHostToDevice));
+    MWAX_CUDA(cudaMalloc(&p.delay, sizeof(double) * 3 * p.n));
+
+    // averaging coefficients
+    std::vector<BinCoef> bins;
+    std::vector<double> wsum;
+    if (!build_bins(p.N, p.F, p.dc_excl, bins, wsum))
+        return fail(MWAX_EINVAL, "channel averaging with fscrunch %d leaves an empty channel", p.F);
+    MWAX_CUDA(cudaMalloc(&p.bins, sizeof(BinCoef) * p.N));
+    MWAX_CUDA(cudaMemcpy(p.bins, bins.data(), sizeof(BinCoef) * p.N, cudaMemcpyHostToDevice));
+
+    // triangle tiles of 64 x 64 path pairs
+    const int nb = (p.n + 63) / 64;
+    std::vector<int2> tiles;
+    for (int i = 0; i < nb; ++i)
+        for (int j = i; j < nb; ++j) tiles.push_back(make_int2(i, j));
+    p.n_tiles = (int)tiles.size();
+    MWAX_CUDA(cudaMalloc(&p.tiles, sizeof(int2) * tiles.size()));
+    MWAX_CUDA(cudaMemcpy(p.tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice));
+
+    // runs of output channels: enough CTAs for ~8 per SM, at least 4 channels per run
+    const long long ctas_wo_runs = (long long)p.n_tiles * p.slots;
+    int want_runs = (int)std::max<long long>(1, (8LL * 148 + ctas_wo_runs - 1) / ctas_wo_runs);
+    int run_len = std::max(4, (p.M + want_runs - 1) / want_runs);
+    run_len = std::min(run_len, p.M);
+    std::vector<RunInfo> runs;
+    for (int j0 = 0; j0 < p.M; j0 += run_len) {
+        RunInfo r;
+        r.j0 = j0;
+        r.j1 = std::min(p.M, j0 + run_len);
+        r.c0 = p.N;
+        r.c1 = 0;
+        for (int c = 0; c < p.N; ++c) {
+            const BinCoef& b = bins[c];
+            const bool in = (b.ja >= r.j0 && b.ja < r.j1) || (b.jb >= r.j0 && b.jb < r.j1);
+            if (in) {
+                r.c0 = std::min(r.c0, c);
+                r.c1 = std::max(r.c1, c + 1);
+            }
+        }
+        runs.push_back(r);
+    }
+    p.n_runs = (int)runs.size();
+    MWAX_CUDA(cudaMalloc(&p.runs, sizeof(RunInfo) * runs.size()));
+    MWAX_CUDA(cudaMemcpy(p.runs, runs.data(), sizeof(RunInfo) * runs.size(), cudaMemcpyHostToDevice));
+
+    MWAX_CUDA(cudaMalloc(&p.status, sizeof(int)));
+    MWAX_CUDA(cudaMemset(p.status, 0, sizeof(int)));
+    return MWAX_OK;
+}
+
+cudaEvent_t take_event(mwax_plan* p)
+{
+    if (!p->ev_pool.empty()) {
+        cudaEvent_t e = p->ev_pool.back();
+        p->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Bracket one launch of `stage` with events when timing is on; count it either way.
+template <typename F>
+cudaError_t timed(mwax_plan* p, int stage, F&& launch)
+{
+    p->launches[stage] += 1;
+    if (!p->timing) return launch();
+    cudaEvent_t a = take_event(p), b = take_event(p);
+    cudaEventRecord(a, p->stream);
+    cudaError_t e = launch();
+    cudaEventRecord(b, p->stream);
+    p->ev_used.push_back({stage, {a, b}});
+    return e;
+}
+
+mwax_status enqueue(mwax_plan* p, const int8_t* volt, bool have_delay, char* out, cudaEvent_t* wait_events,
+                    long long events_per_block)
+{
+    cudaStream_t s = p->stream;
+    MWAX_CUDA(timed(p, 0, [&] {
+        return launch_init_output(out, p->n_ints, (long long)p->vis_set_bytes, (long long)p->weights_bytes, s);
+    }));
+    for (long long w0 = 0; w0 < p->n_ints; w0 += p->slots) {
+        const long long nslots = std::min(p->slots, p->n_ints - w0);
+        for (int ch = 0; ch < p->chunks; ++ch) {
+            const long long kbeg = (long long)ch * p->Kc;
+            const long long klen = std::min(p->Kc, p->K - kbeg);
+            const long long nframes = (p->chunks == 1) ? nslots * p->K : klen;
+            const long long m_begin = w0 * p->K + kbeg;
+            if (wait_events) {
+                // host-input path: wait for the copy of the last block this launch reads
+                const long long last_sample = (m_begin + nframes) * p->N - 1;
+                const long long blk = last_sample / p->bs;
+                MWAX_CUDA(cudaStreamWaitEvent(s, wait_events[blk / events_per_block], 0));
+            }
+            FArgs fa;
+            memset(&fa, 0, sizeof fa);
+            fa.volt = volt;
+            fa.delay = have_delay ? p->delay : nullptr;
+            fa.Y = p->Y;
+            fa.tw = p->tw;
+            fa.m_begin = m_begin;
+            fa.n_frames = nframes;
+            fa.Kc = (p->chunks == 1) ? p->K : p->Kc;
+            fa.Kpad = p->Kpad;
+            fa.n = p->n;
+            fa.bs = p->bs;
+            fa.nu = p->nu;
+            fa.out_scale = p->out_scale;
+            MWAX_CUDA(timed(p, 1, [&] { return launch_fstep(p->N, FOUT_F32, fa, s); }));
+
+            XArgs xa;
+            memset(&xa, 0, sizeof xa);
+            xa.Y = p->Y;
+            xa.out = out + w0 * (long long)p->int_stride;
+            xa.out_stride = (long long)p->int_stride;
+            xa.Kpad = p->Kpad;
+            xa.klen = klen;
+            xa.n = p->n;
+            xa.T = p->T;
+            xa.N = p->N;
+            xa.M = p->M;
+            xa.B = p->B;
+            xa.bins = p->bins;
+            xa.runs = p->runs;
+            xa.tiles = p->tiles;
+            xa.post_scale = p->post_scale;
+            xa.status = p->status;
+            MWAX_CUDA(timed(p, 2, [&] { return launch_xstep_simt(xa, p->n_tiles, p->n_runs, (int)nslots, s); }));
+        }
+    }
+    return MWAX_OK;
+}
+
+mwax_status load_delay(mwax_plan* p, const double* delay_poly)
+{
+    if (!delay_poly) return MWAX_OK;
+    MWAX_CUDA(cudaMemcpyAsync(p->delay, delay_poly, sizeof(double) * 3 * p->n, cudaMemcpyDefault, p->stream));
+    return MWAX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mwax_version(void) { return "mwax-b300 0.1 (sm_103a)"; }
+
+const char* mwax_last_error(void) { return g_err.c_str(); }
+
+mwax_plan* mwax_plan_create_ex(const mwax_plan_desc* desc)
+{
+    g_err.clear();
+    if (!desc) {
+        fail(MWAX_EINVAL, "desc is NULL");
+        return nullptr;
+    }
+    mwax_plan* p = new mwax_plan();
+    if (validate(*desc, *p) != MWAX_OK || setup(*p) != MWAX_OK) {
+        std::string keep = g_err;
+        free_plan(p);
+        g_err = keep;
+        return nullptr;
+    }
+    return p;
+}
+
+mwax_plan* mwax_plan_create(int n_tiles, int fft_len, double int_time_s, int fine_avg)
+{
+    mwax_plan_desc d;
+    memset(&d, 0, sizeof d);
+    d.n_tiles = n_tiles;
+    d.fft_len = fft_len;
+    d.int_time_s = int_time_s;
+    d.fine_avg = fine_avg;
+    return mwax_plan_create_ex(&d);
+}
+
+mwax_status mwax_plan_get_info(const mwax_plan* p, mwax_plan_info* info)
+{
+    if (!p || !info) return fail(MWAX_EINVAL, "NULL argument");
+    info->n_paths = p->n;
+    info->n_baselines = p->B;
+    info->n_chan_out = p->M;
+    info->frames_per_int = p->K;
+    info->n_ints = p->n_ints;
+    info->input_bytes = p->input_bytes;
+    info->vis_set_bytes = p->vis_set_bytes;
+    info->weights_bytes = p->weights_bytes;
+    info->output_bytes = (size_t)p->n_ints * p->int_stride;
+    info->workspace_bytes = p->Y_bytes;
+    info->precision = p->prec;
+    return MWAX_OK;
+}
+
+size_t mwax_plan_output_bytes(const mwax_plan* p) { return p ? (size_t)p->n_ints * p->int_stride : 0; }
+
+size_t mwax_plan_input_bytes(const mwax_plan* p) { return p ? p->input_bytes : 0; }
+
+mwax_status mwax_plan_set_stream(mwax_plan* p, void* stream)
+{
+    if (!p) return fail(MWAX_EINVAL, "plan is NULL");
+    p->stream = (cudaStream_t)stream;
+    return MWAX_OK;
+}
+
+mwax_status mwax_correlate(mwax_plan* p, const int8_t* volt, const double* delay_poly, void* vis_out)
+{
+    if (!p || !volt || !vis_out) return fail(MWAX_EINVAL, "NULL plan, voltages or vis_out");
+    if (((uintptr_t)volt & 15) || ((uintptr_t)vis_out & 15))
+        return fail(MWAX_EINVAL, "voltages and vis_out must be 16-byte aligned");
+    if (p->prec == MWAX_INT8 && delay_poly) return fail(MWAX_EINVAL, "MWAX_INT8 takes no delay correction");
+    MWAX_CUDA(cudaSetDevice(p->device));
+    mwax_status st = load_delay(p, delay_poly);
+    if (st != MWAX_OK) return st;
+    return enqueue(p, volt, delay_poly != nullptr, static_cast<char*>(vis_out), nullptr, 1);
+}
+
+mwax_status mwax_correlate_host(mwax_plan* p, const int8_t* volt, const double* delay_poly, void* vis_out)
+{
+    if (!p || !volt || !vis_out) return fail(MWAX_EINVAL, "NULL plan, voltages or vis_out");
+    if (p->prec == MWAX_INT8 && delay_poly) return fail(MWAX_EINVAL, "MWAX_INT8 takes no delay correction");
+    MWAX_CUDA(cudaSetDevice(p->device));
+    const size_t out_bytes = (size_t)p->n_ints * p->int_stride;
+    const long long blocks_per_copy = std::max<long long>(1, p->n_blocks / 16);
+    const long long n_copies = (p->n_blocks + blocks_per_copy - 1) / blocks_per_copy;
+    if (!p->dvolt) {
+        MWAX_CUDA(cudaMalloc(&p->dvolt, p->input_bytes));
+        MWAX_CUDA(cudaMalloc(&p->dout, out_bytes));
+        MWAX_CUDA(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+        p->events.resize(n_copies + 1);
+        for (auto& e : p->events) MWAX_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    // the copy stream must not run ahead of earlier work on the plan stream
+    MWAX_CUDA(cudaEventRecord(p->events[n_copies], p->stream));
+    MWAX_CUDA(cudaStreamWaitEvent(p->copy_stream, p->events[n_copies], 0));
+    const size_t block_bytes = (size_t)p->n * p->bs * 2;
+    for (long long c = 0; c < n_copies; ++c) {
+        const long long b0 = c * blocks_per_copy, b1 = std::min(p->n_blocks, b0 + blocks_per_copy);
+        MWAX_CUDA(cudaMemcpyAsync(p->dvolt + b0 * block_bytes, volt + b0 * block_bytes, (b1 - b0) * block_bytes,
+                                  cudaMemcpyHostToDevice, p->copy_stream));
+        MWAX_CUDA(cudaEventRecord(p->events[c], p->copy_stream));
+    }
+    mwax_status st = load_delay(p, delay_poly);
+    if (st != MWAX_OK) return st;
+    st = enqueue(p, p->dvolt, delay_poly != nullptr, p->dout, p->events.data(), blocks_per_copy);
+    if (st != MWAX_OK) return st;
+    MWAX_CUDA(cudaMemcpyAsync(vis_out, p->dout, out_bytes, cudaMemcpyDeviceToHost, p->stream));
+    return mwax_plan_sync(p);
+}
+
+mwax_status mwax_plan_sync(mwax_plan* p)
+{
+    if (!p) return fail(MWAX_EINVAL, "plan is NULL");
+    MWAX_CUDA(cudaSetDevice(p->device));
+    MWAX_CUDA(cudaStreamSynchronize(p->stream));
+    int st = 0;
+    MWAX_CUDA(cudaMemcpy(&st, p->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st != 0) {
+        MWAX_CUDA(cudaMemset(p->status, 0, sizeof(int)));
+        return fail(MWAX_ETIMEOUT, "a device-side bounded wait gave up (status %d)", st);
+    }
+    return MWAX_OK;
+}
+
+mwax_status mwax_plan_enable_timing(mwax_plan* p, int enable)
+{
+    if (!p) return fail(MWAX_EINVAL, "plan is NULL");
+    p->timing = enable != 0;
+    return MWAX_OK;
+}
+
+mwax_status mwax_plan_stage_times(mwax_plan* p, double ms[3], long long launches[3])
+{
+    if (!p || !ms || !launches) return fail(MWAX_EINVAL, "NULL argument");
+    MWAX_CUDA(cudaSetDevice(p->device));
+    MWAX_CUDA(cudaStreamSynchronize(p->stream));
+    for (int i = 0; i < 3; ++i) {
+        ms[i] = 0.0;
+        launches[i] = p->launches[i];
+        p->launches[i] = 0;
+    }
+    for (auto& u : p->ev_used) {
+        float t = 0.0f;
+        MWAX_CUDA(cudaEventElapsedTime(&t, u.second.first, u.second.second));
+        ms[u.first] += t;
+        p->ev_pool.push_back(u.second.first);
+        p->ev_pool.push_back(u.second.second);
+    }
+    p->ev_used.clear();
+    return MWAX_OK;
+}
+
+void mwax_plan_destroy(mwax_plan* p)
+{
+    if (!p) return;
+    cudaSetDevice(p->device);
+    cudaStreamSynchronize(p->stream);
+    free_plan(p);
+}
+
+}  // extern "C"

@@ -1,0 +1,446 @@
+// F-step of the MWAX FX correlator (Sec. 2.5.1): int8 unpack, fine-channel FFT,
+// per-path delay/phase correction (Sec. 2.5.1, 4.3), channel shift (Sec. 2.6) and the
+// store of X-engine operands.
+//
+// One CTA transforms FB consecutive frames of one signal path.  The frames' int8
+// samples are staged in shared memory with 16-byte loads, then an out-of-place Stockham
+// FFT runs pass by pass in shared memory (radix-R butterflies in registers, ping-pong
+// buffers), and the last pass multiplies by the delay phasor and writes the operand
+// planes straight to global memory.  Lanes of a warp take consecutive frames, so the
+// final stores are contiguous along the frame (K) axis of the K-major operand layout
+//     Y[slot][c][plane][p][Kpad]   (plane 0 = re, 1 = im).
+#include "mwax_internal.cuh"
+
+namespace mwax {
+namespace {
+
+__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 c_mul(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 c_mul_negi(float2 a) { return make_float2(a.y, -a.x); }  // -i a
+
+// In-register forward DFTs, X_k = sum_r v_r e^{-2 pi i r k / R}.
+template <int R>
+struct Dft;
+
+template <>
+struct Dft<2> {
+    __device__ __forceinline__ static void run(float2 (&v)[2])
+    {
+        float2 a = v[0], b = v[1];
+        v[0] = c_add(a, b);
+        v[1] = c_sub(a, b);
+    }
+};
+
+template <>
+struct Dft<4> {
+    __device__ __forceinline__ static void run(float2 (&v)[4])
+    {
+        float2 t0 = c_add(v[0], v[2]), t1 = c_sub(v[0], v[2]);
+        float2 t2 = c_add(v[1], v[3]), t3 = c_mul_negi(c_sub(v[1], v[3]));
+        v[0] = c_add(t0, t2);
+        v[2] = c_sub(t0, t2);
+        v[1] = c_add(t1, t3);
+        v[3] = c_sub(t1, t3);
+    }
+};
+
+template <>
+struct Dft<5> {
+    __device__ __forceinline__ static void run(float2 (&v)[5])
+    {
+        const float c1 = 0.30901699437494745f, s1 = 0.9510565162951535f;   // cos, sin 2pi/5
+        const float c2 = -0.8090169943749473f, s2 = 0.5877852522924732f;   // cos, sin 4pi/5
+        float2 a1 = c_add(v[1], v[4]), b1 = c_sub(v[1], v[4]);
+        float2 a2 = c_add(v[2], v[3]), b2 = c_sub(v[2], v[3]);
+        float2 x0 = v[0];
+        float2 p1 = make_float2(x0.x + c1 * a1.x + c2 * a2.x, x0.y + c1 * a1.y + c2 * a2.y);
+        float2 p2 = make_float2(x0.x + c2 * a1.x + c1 * a2.x, x0.y + c2 * a1.y + c1 * a2.y);
+        float2 q1 = make_float2(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y);
+        float2 q2 = make_float2(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y);
+        v[0] = make_float2(x0.x + a1.x + a2.x, x0.y + a1.y + a2.y);
+        v[1] = c_add(p1, c_mul_negi(q1));
+        v[4] = c_sub(p1, c_mul_negi(q1));
+        v[2] = c_add(p2, c_mul_negi(q2));
+        v[3] = c_sub(p2, c_mul_negi(q2));
+    }
+};
+
+template <>
+struct Dft<8> {
+    __device__ __forceinline__ static void run(float2 (&v)[8])
+    {
+        const float h = 0.7071067811865476f;
+        float2 e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+        Dft<4>::run(e);
+        Dft<4>::run(o);
+        o[1] = c_mul(o[1], make_float2(h, -h));
+        o[2] = c_mul_negi(o[2]);
+        o[3] = c_mul(o[3], make_float2(-h, -h));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = c_add(e[k], o[k]);
+            v[k + 4] = c_sub(e[k], o[k]);
+        }
+    }
+};
+
+template <>
+struct Dft<16> {
+    __device__ __forceinline__ static void run(float2 (&v)[16])
+    {
+        // e^{-2 pi i k / 16}, k = 0..7
+        const float2 w[8] = {make_float2(1.0f, 0.0f),
+                             make_float2(0.9238795325112867f, -0.3826834323650898f),
+                             make_float2(0.7071067811865476f, -0.7071067811865475f),
+                             make_float2(0.38268343236508984f, -0.9238795325112867f),
+                             make_float2(0.0f, -1.0f),
+                             make_float2(-0.3826834323650897f, -0.9238795325112867f),
+                             make_float2(-0.7071067811865475f, -0.7071067811865476f),
+                             make_float2(-0.9238795325112867f, -0.3826834323650899f)};
+        float2 e[8], o[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            e[k] = v[2 * k];
+            o[k] = v[2 * k + 1];
+        }
+        Dft<8>::run(e);
+        Dft<8>::run(o);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            float2 t = (k == 0) ? o[0] : (k == 4 ? c_mul_negi(o[4]) : c_mul(o[k], w[k]));
+            v[k] = c_add(e[k], t);
+            v[k + 8] = c_sub(e[k], t);
+        }
+    }
+};
+
+// Radix schedule per FFT length (applied in this order).
+template <int N>
+struct Sched;
+#define MWAX_SCHED(NN, FBV, ...)                                                  \
+    template <>                                                                   \
+    struct Sched<NN> {                                                            \
+        static constexpr int fb = FBV;                                            \
+        static constexpr int radix[4] = {__VA_ARGS__};                            \
+        static constexpr int passes = sizeof(radix) / sizeof(int) - count1(radix); \
+    };
+__host__ __device__ constexpr int count1(const int (&r)[4])
+{
+    return (r[0] == 1) + (r[1] == 1) + (r[2] == 1) + (r[3] == 1);
+}
+MWAX_SCHED(16, 32, 16, 1, 1, 1)
+MWAX_SCHED(32, 32, 8, 4, 1, 1)
+MWAX_SCHED(64, 32, 8, 8, 1, 1)
+MWAX_SCHED(128, 32, 16, 8, 1, 1)
+MWAX_SCHED(256, 32, 16, 16, 1, 1)
+MWAX_SCHED(512, 16, 8, 8, 8, 1)
+MWAX_SCHED(640, 16, 16, 8, 5, 1)
+MWAX_SCHED(1280, 8, 16, 16, 5, 1)
+MWAX_SCHED(3200, 4, 16, 8, 5, 5)
+MWAX_SCHED(6400, 2, 16, 16, 5, 5)
+#undef MWAX_SCHED
+
+template <int N, int P>
+struct PassNs {  // product of the radices before pass P
+    static constexpr int value = PassNs<N, P - 1>::value * Sched<N>::radix[P - 1];
+};
+template <int N>
+struct PassNs<N, 0> {
+    static constexpr int value = 1;
+};
+
+constexpr int kThreads = 256;
+
+// Per-frame data shared by the CTA.
+struct FrameInfo {
+    long long slot;   // operand slot (integration within the launch), -1 = no frame
+    long long k;      // frame index within the slot
+    float phi0;       // frac(nu * tau) [cycles]
+    float d_hi;       // tau Fs / N [cycles per bin], top 12 significant bits
+    float d_lo;       // the rest
+    int delay;
+};
+
+template <int N, int OUTK>
+struct Store {
+    // Write one corrected spectral value of channel c of frame f.
+    __device__ __forceinline__ static void run(const FArgs& a, const FrameInfo& fi, int p, int c, float2 v)
+    {
+        if (fi.slot < 0) return;
+        long long row0 = ((fi.slot * N + c) * 2 + 0) * (long long)a.n + p;
+        long long row1 = row0 + a.n;
+        if (OUTK == FOUT_F32) {
+            float* Y = static_cast<float*>(a.Y);
+            Y[row0 * a.Kpad + fi.k] = v.x;
+            Y[row1 * a.Kpad + fi.k] = v.y;
+        } else if (OUTK == FOUT_F16) {
+            __half* Y = static_cast<__half*>(a.Y);
+            Y[row0 * a.Kpad + fi.k] = __float2half_rn(v.x * a.out_scale);
+            Y[row1 * a.Kpad + fi.k] = __float2half_rn(v.y * a.out_scale);
+        }
+    }
+};
+
+// Delay phasor e^{2 pi i (phi0 + u d)} of ultrafine offset u (|u| < 4096).
+__device__ __forceinline__ float2 delay_phasor(const FrameInfo& fi, int u)
+{
+    float uf = (float)u;
+    float x = uf * fi.d_hi;       // exact: 12-bit by 12-bit significands
+    x -= rintf(x);                // exact
+    float y = fi.phi0 + x + uf * fi.d_lo;
+    y -= rintf(y);
+    float s, c;
+    sincospif(2.0f * y, &s, &c);
+    return make_float2(c, s);
+}
+
+template <int N, int OUTK, int P>
+struct Pass {
+    static constexpr int R = Sched<N>::radix[P];
+    static constexpr int NS = PassNs<N, P>::value;
+    static constexpr int NB = N / R;
+    static constexpr int FB = Sched<N>::fb;
+    static constexpr int ROW = N + 1;              // padded float2 row per frame
+    static constexpr int SROW = 2 * N + 4;         // padded int8 staging row (bytes)
+    static constexpr bool FIRST = (P == 0);
+    static constexpr bool LAST = (P == Sched<N>::passes - 1);
+
+    __device__ __forceinline__ static void run(const FArgs& a, const FrameInfo* finfo, float2* buf0,
+                                               float2* buf1, const int8_t* stage, int p)
+    {
+        float2* in = (P % 2 == 0) ? buf1 : buf0;   // pass 0 reads the staging area in buf1
+        float2* out = (P % 2 == 0) ? buf0 : buf1;
+        for (int idx = threadIdx.x; idx < FB * NB; idx += kThreads) {
+            const int f = idx % FB, j = idx / FB;
+            float2 v[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (FIRST) {
+                    const char2 s = *reinterpret_cast<const char2*>(stage + f * SROW + 2 * (j + r * NB));
+                    v[r] = make_float2((float)s.x, (float)s.y);
+                } else {
+                    v[r] = in[f * ROW + j + r * NB];
+                }
+            }
+            if (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[r] = c_mul(v[r], __ldg(&a.tw[(j % NS) * r * (N / (NS * R))]));
+            }
+            Dft<R>::run(v);
+            if (!LAST) {
+                const int d = (j / NS) * NS * R + (j % NS);
+#pragma unroll
+                for (int r = 0; r < R; ++r) out[f * ROW + d + r * NS] = v[r];
+            } else {
+                const FrameInfo fi = finfo[f];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int k = j + r * NB;                    // natural-order bin
+                    const int u = (k < N - N / 2) ? k : k - N;   // ultrafine offset
+                    float2 y = v[r];
+                    if (fi.delay) y = c_mul(y, delay_phasor(fi, u));
+                    Store<N, OUTK>::run(a, fi, p, u + N / 2, y);
+                }
+            }
+        }
+        if (!LAST) __syncthreads();
+    }
+};
+
+template <int N, int OUTK, int P, bool DONE = (P >= Sched<N>::passes)>
+struct PassChain {
+    __device__ __forceinline__ static void run(const FArgs& a, const FrameInfo* fi, float2* b0, float2* b1,
+                                               const int8_t* st, int p)
+    {
+        Pass<N, OUTK, P>::run(a, fi, b0, b1, st, p);
+        PassChain<N, OUTK, P + 1>::run(a, fi, b0, b1, st, p);
+    }
+};
+template <int N, int OUTK, int P>
+struct PassChain<N, OUTK, P, true> {
+    __device__ __forceinline__ static void run(const FArgs&, const FrameInfo*, float2*, float2*, const int8_t*, int) {}
+};
+
+template <int N>
+constexpr size_t fstep_smem()
+{
+    return 2 * sizeof(float2) * (size_t)Sched<N>::fb * (N + 1) + sizeof(FrameInfo) * Sched<N>::fb;
+}
+
+template <int N, int OUTK>
+__global__ void __launch_bounds__(kThreads) fstep_kernel(const FArgs a)
+{
+    constexpr int FB = Sched<N>::fb;
+    constexpr int ROW = N + 1;
+    constexpr int SROW = 2 * N + 4;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* buf0 = reinterpret_cast<float2*>(smem);
+    float2* buf1 = buf0 + FB * ROW;
+    FrameInfo* finfo = reinterpret_cast<FrameInfo*>(buf1 + FB * ROW);
+    int8_t* stage = reinterpret_cast<int8_t*>(buf1);
+
+    const int p = blockIdx.y;
+    const long long f0 = (long long)blockIdx.x * FB;
+
+    // Frame metadata: slot, index within the slot, FP64 delay polynomial (Sec. 4.3).
+    if (threadIdx.x < FB) {
+        const int f = threadIdx.x;
+        FrameInfo fi;
+        const long long fl = f0 + f;
+        fi.slot = (fl < a.n_frames) ? fl / a.Kc : -1;
+        fi.k = (fl < a.n_frames) ? fl % a.Kc : 0;
+        fi.delay = 0;
+        fi.phi0 = fi.d_hi = fi.d_lo = 0.0f;
+        if (a.delay != nullptr && fl < a.n_frames) {
+            const double m = (double)(a.m_begin + fl);
+            const double t = (m + 0.5) * (double)N / kFs;
+            const double tau = a.delay[3 * p] + t * (a.delay[3 * p + 1] + t * a.delay[3 * p + 2]);
+            const double ph = a.nu * tau;
+            fi.phi0 = (float)(ph - floor(ph));
+            const double d = tau * kFs / (double)N;
+            const float dh = __uint_as_float(__float_as_uint((float)d) & 0xFFFFF000u);
+            fi.d_hi = dh;
+            fi.d_lo = (float)(d - (double)dh);
+            fi.delay = 1;
+        }
+        finfo[f] = fi;
+    }
+
+    // Stage the frames' int8 samples (2N bytes per frame, 16-byte loads).
+    constexpr int CH = 2 * N / 16;   // 16-byte chunks per frame
+    for (int i = threadIdx.x; i < FB * CH; i += kThreads) {
+        const int f = i / CH, ch = i % CH;
+        const long long fl = f0 + f;
+        int4 w = make_int4(0, 0, 0, 0);
+        if (fl < a.n_frames) {
+            const long long s = (a.m_begin + fl) * (long long)N;   // absolute first sample
+            const long long blk = s / a.bs, off = s % a.bs;
+            const int8_t* src = a.volt + ((blk * a.n + p) * (long long)a.bs + off) * 2;
+            w = __ldg(reinterpret_cast<const int4*>(src) + ch);
+        }
+        int* dst = reinterpret_cast<int*>(stage + f * SROW + ch * 16);
+        dst[0] = w.x;
+        dst[1] = w.y;
+        dst[2] = w.z;
+        dst[3] = w.w;
+    }
+    __syncthreads();
+
+    PassChain<N, OUTK, 0>::run(a, finfo, buf0, buf1, stage, p);
+}
+
+// N = 1: no FFT.  One thread per (path, 4 samples); optional phasor e^{2 pi i nu tau}.
+template <int OUTK>
+__global__ void __launch_bounds__(256) unpack_kernel(const FArgs a)
+{
+    const int p = blockIdx.y;
+    const long long i4 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long f_first = i4 * 4;
+    if (f_first >= a.n_frames) return;
+    for (int e = 0; e < 4; ++e) {
+        const long long fl = f_first + e;
+        if (fl >= a.n_frames) break;
+        const long long s = a.m_begin + fl;
+        const long long blk = s / a.bs, off = s % a.bs;
+        const char2 x = *reinterpret_cast<const char2*>(a.volt + ((blk * a.n + p) * (long long)a.bs + off) * 2);
+        float2 v = make_float2((float)x.x, (float)x.y);
+        if (a.delay != nullptr) {
+            const double t = ((double)s + 0.5) / kFs;
+            const double tau = a.delay[3 * p] + t * (a.delay[3 * p + 1] + t * a.delay[3 * p + 2]);
+            const double ph = a.nu * tau;
+            float sn, cs;
+            sincospif(2.0f * (float)(ph - floor(ph)), &sn, &cs);
+            v = c_mul(v, make_float2(cs, sn));
+        }
+        FrameInfo fi;
+        fi.slot = fl / a.Kc;
+        fi.k = fl % a.Kc;
+        Store<1, OUTK>::run(a, fi, p, 0, v);
+    }
+}
+
+template <int N, int OUTK>
+cudaError_t launch_n(const FArgs& a, cudaStream_t s)
+{
+    constexpr size_t smem = fstep_smem<N>();
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(fstep_kernel<N, OUTK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    dim3 grid((unsigned)((a.n_frames + Sched<N>::fb - 1) / Sched<N>::fb), (unsigned)a.n);
+    fstep_kernel<N, OUTK><<<grid, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int OUTK>
+cudaError_t launch_kind(int N, const FArgs& a, cudaStream_t s)
+{
+    switch (N) {
+        case 1: {
+            dim3 grid((unsigned)((a.n_frames + 1023) / 1024), (unsigned)a.n);
+            unpack_kernel<OUTK><<<grid, 256, 0, s>>>(a);
+            return cudaGetLastError();
+        }
+        case 16: return launch_n<16, OUTK>(a, s);
+        case 32: return launch_n<32, OUTK>(a, s);
+        case 64: return launch_n<64, OUTK>(a, s);
+        case 128: return launch_n<128, OUTK>(a, s);
+        case 256: return launch_n<256, OUTK>(a, s);
+        case 512: return launch_n<512, OUTK>(a, s);
+        case 640: return launch_n<640, OUTK>(a, s);
+        case 1280: return launch_n<1280, OUTK>(a, s);
+        case 3200: return launch_n<3200, OUTK>(a, s);
+        case 6400: return launch_n<6400, OUTK>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Zero each integration's visibility set and write its weights table (1.0, Sec. 2.7).
+__global__ void init_output_kernel(char* out, long long n_ints, long long vis_words, long long wt_words)
+{
+    const long long per = vis_words + wt_words;
+    const long long total = n_ints * per;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i % per;
+        reinterpret_cast<float*>(out)[i] = (r < vis_words) ? 0.0f : 1.0f;
+    }
+}
+
+}  // namespace
+
+bool fft_len_supported(int N)
+{
+    switch (N) {
+        case 1: case 16: case 32: case 64: case 128: case 256: case 512: case 640: case 1280: case 3200: case 6400:
+            return true;
+        default:
+            return false;
+    }
+}
+
+cudaError_t launch_fstep(int N, int out_kind, const FArgs& a, cudaStream_t s)
+{
+    switch (out_kind) {
+        case FOUT_F32: return launch_kind<FOUT_F32>(N, a, s);
+        case FOUT_F16: return launch_kind<FOUT_F16>(N, a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_init_output(char* out, long long n_ints, long long vis_set_bytes, long long weights_bytes,
+                               cudaStream_t s)
+{
+    init_output_kernel<<<4 * 148, 256, 0, s>>>(out, n_ints, vis_set_bytes / 4, weights_bytes / 4);
+    return cudaGetLastError();
+}
+
+}  // namespace mwax

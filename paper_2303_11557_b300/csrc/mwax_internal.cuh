@@ -1,0 +1,77 @@
+// Internal declarations of the MWAX B300 correlator library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+#include "../../include/mwax.h"
+
+namespace mwax {
+
+constexpr double kFs = 1280000.0;        // coarse-channel sample rate (Sec. 2.5)
+constexpr int kDefaultBlock = 64000;     // samples per path per 50 ms data block (Sec. 2.5)
+constexpr int kKAlign = 64;              // frames per operand row are padded to this
+
+// Output-type selector of the F-step.
+enum FOut : int { FOUT_F32 = 0, FOUT_F16 = 1, FOUT_AMAX = 2, FOUT_E4M3 = 3 };
+
+// Per ultrafine channel c: the (at most two) output channels it feeds and the
+// coefficient w_c / sum(w) of each (Sec. 2.6).  j = -1 marks an unused slot.
+struct BinCoef {
+    int ja, jb;
+    float ca, cb;
+};
+
+// A run of consecutive output channels [j0, j1) handled by one X CTA, with the
+// ultrafine channel range [c0, c1) that feeds it.
+struct RunInfo {
+    int j0, j1, c0, c1;
+};
+
+// Arguments of one F-step launch: frames [m_begin, m_begin + n_frames) of the call,
+// written to operand slots of Kc frames each (slot = frame / Kc).
+struct FArgs {
+    const int8_t* volt;   // [blk][n][bs][2]
+    const double* delay;  // [n][3] or nullptr
+    void* Y;              // operands [slot][N][2][n][Kpad]
+    float* amax;          // FP8: [slot][N][n] per-path-per-channel max |re|,|im|
+    const float* scale;   // FP8 quantise pass: [slot][N][n] scale s = amax / 448
+    const float2* tw;     // e^{-2 pi i k / N}, k < N
+    long long m_begin;
+    long long n_frames;
+    long long Kc;
+    long long Kpad;
+    int n;
+    int bs;
+    double nu;
+    float out_scale;      // FP16: power-of-two pre-scale keeping |X| in range
+};
+
+// Arguments of one X-step launch over `slots` operand slots.
+struct XArgs {
+    const void* Y;         // operands [slot][N][2][n][Kpad]
+    const float* scale;    // FP8 per-path-per-channel scales [slot][N][n] or nullptr
+    char* out;             // output of slot 0's integration
+    long long out_stride;  // bytes from one integration's output to the next
+    long long Kpad;
+    long long klen;        // valid frames per slot in this launch
+    int n, T, N, M;
+    long long B;
+    const BinCoef* bins;
+    const RunInfo* runs;
+    const int2* tiles;     // (row block, column block) of each triangle tile
+    float post_scale;      // multiplies every product (undoes the FP16 pre-scale)
+    int* status;           // device status word (bounded waits)
+    unsigned int spin_limit;
+};
+
+// Launchers (each returns the cudaError_t of its launch).
+cudaError_t launch_fstep(int N, int out_kind, const FArgs& a, cudaStream_t s);
+cudaError_t launch_init_output(char* out, long long n_ints, long long vis_set_bytes, long long weights_bytes,
+                               cudaStream_t s);
+cudaError_t launch_xstep_simt(const XArgs& a, int n_tiles, int n_runs, int slots, cudaStream_t s);
+bool fft_len_supported(int N);
+
+}  // namespace mwax

@@ -30,7 +30,7 @@ def build(force: bool = False) -> str:
     src = os.path.join(_HERE, "synth.c")
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, src, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-fno-math-errno", "-fopenmp", "-fPIC", "-shared", "-o", tmp, src, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 

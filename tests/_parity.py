@@ -1,0 +1,45 @@
+"""Shared helpers of the GPU parity tests: workloads and the parity metric."""
+import numpy as np
+
+import oracle
+import synth
+
+
+def parity_error(vis_gpu, vis_ora, T):
+    """err = |V_gpu - V_ora| / sqrt(V_ora,pp V_ora,qq), the autos being the parallel-pol
+    autocorrelations of the same channel and integration (scale-free).
+    vis_*: complex [ints, B, M, 4] in MWAX_ORDER.  Returns the error array."""
+    B = T * (T + 1) // 2
+    auto_b = np.array([i * (2 * T - i + 1) // 2 for i in range(T)])
+    ti = np.concatenate([[i] * (T - i) for i in range(T)])
+    tj = np.concatenate([np.arange(i, T) for i in range(T)])
+    assert len(ti) == B
+    err = np.empty(vis_ora.shape, dtype=np.float64)
+    for pol in range(4):
+        a, e = pol >> 1, pol & 1
+        ap = np.abs(vis_ora[..., 3 * a].real)[:, auto_b[ti], :]   # xx (0) or yy (3) of tile i
+        aq = np.abs(vis_ora[..., 3 * e].real)[:, auto_b[tj], :]
+        err[..., pol] = np.abs(vis_gpu[..., pol] - vis_ora[..., pol]) / np.sqrt(ap * aq)
+    return err
+
+
+def workload(seed, T, n_samples, *, block_samples=64_000, delay="fixed", sky=synth.SKY_FREQ_HZ,
+             sigma=16.0, rel_rms=0.3):
+    """Seeded noise + point-source voltages and the per-path delay polynomial."""
+    if delay == "fixed":
+        dpoly = synth.tile_delays_fixed(T)
+    elif delay == "linear":
+        dpoly = synth.tile_delays_linear(seed, T)
+    else:
+        dpoly = None
+    src = dpoly if dpoly is not None else synth.tile_delays_fixed(T)
+    volt = synth.voltages(seed, 2 * T, n_samples, block_samples=block_samples, sigma=sigma,
+                          tones=synth.point_source_tones(seed, sigma=sigma, rel_rms=rel_rms),
+                          delay_c01=src[:, :2], sky_freq_hz=sky)
+    return volt, dpoly
+
+
+def oracle_desc(T, N, F, int_time_s, n_samples, block_samples=64_000, sky=synth.SKY_FREQ_HZ, keep_dc=0):
+    K = int(round(int_time_s * synth.FS)) // N
+    return oracle.Desc(n_tiles=T, fft_len=N, fine_avg=F, int_frames=K, n_samples=n_samples,
+                       block_samples=block_samples, sky_freq_hz=sky, dc_exclude=0 if keep_dc else 1)

@@ -1,0 +1,129 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, element by element
+on the same seeded inputs.  Bar (per result, relative to the parallel-pol autos of the
+same channel and integration): FP32 <= 1e-5."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2303_11557_b300 as mw
+import synth
+from _parity import oracle_desc, parity_error, workload
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = {mw.MWAX_FP32: 1e-5}
+
+
+def run_gpu(desc: mw.PlanDesc, volt: np.ndarray, delay):
+    plan = mw.mwax_plan_create_ex(desc)
+    mw.mwax_plan_set_stream(plan)
+    dv = torch.from_numpy(volt.reshape(-1)).cuda()
+    out = mw.empty_output(plan)
+    out.fill_(0xAB)   # poison: every byte must be written
+    dd = None if delay is None else torch.from_numpy(np.ascontiguousarray(delay, dtype=np.float64)).cuda()
+    mw.mwax_correlate(plan, dv, dd, out)
+    mw.mwax_plan_sync(plan)
+    vis, w = mw.split_output(plan, out)
+    return vis.cpu().numpy(), w.cpu().numpy(), plan
+
+
+def check(desc, volt, delay, tol=None):
+    vis, w, plan = run_gpu(desc, volt, delay)
+    od = oracle_desc(desc.n_tiles, desc.fft_len, desc.fine_avg, desc.int_time_s, volt.shape[0] * volt.shape[2],
+                     block_samples=volt.shape[2], sky=desc.sky_freq_hz, keep_dc=desc.keep_dc)
+    ref, rw = oracle.correlate(od, volt, delay)
+    assert vis.shape == ref.shape
+    assert np.array_equal(w, rw.astype(np.float32))
+    err = parity_error(vis, ref, desc.n_tiles)
+    tol = tol or TOL[desc.precision]
+    assert np.all(np.isfinite(vis))
+    assert err.max() <= tol, f"max err {err.max():.3e} (median {np.median(err):.3e})"
+    # autos: XX/YY imaginary parts are exactly zero, real parts non-negative
+    T = desc.n_tiles
+    ab = [i * (2 * T - i + 1) // 2 for i in range(T)]
+    assert np.all(vis[:, ab][..., [0, 3]].imag == 0)
+    assert np.all(vis[:, ab][..., [0, 3]].real >= 0)
+    return err
+
+
+def test_config0_fp32():
+    # 16 tiles x 2 pols, 0.4 s at 1.28 MS/s, 128-point FFT, no averaging, fixed 0-50 ns delays
+    T, N, F, t_int = 16, 128, 1, 0.4
+    volt, delay = workload(0x4D574158, T, 512_000)
+    desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=t_int, samples_per_call=512_000,
+                       sky_freq_hz=synth.SKY_FREQ_HZ)
+    check(desc, volt, delay)
+
+
+def test_ragged_tiles_and_averaging():
+    # 80 paths = one full 64-path tile block + a ragged one; even fscrunch, 2 integrations
+    T, N, F, t_int = 40, 32, 4, 0.1
+    volt, delay = workload(7, T, 256_000, delay="linear")
+    desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=t_int, samples_per_call=256_000,
+                       sky_freq_hz=synth.SKY_FREQ_HZ)
+    check(desc, volt, delay)
+
+
+def test_ragged_frames_odd_fscrunch_keep_dc():
+    # 1000 frames per integration (not a multiple of the 32-frame chunk), F = 2, DC kept
+    T, N, F, t_int = 5, 16, 2, 0.0125
+    volt, delay = workload(8, T, 64_000, block_samples=16_000, delay="linear")
+    desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=t_int, samples_per_call=64_000,
+                       block_samples=16_000, sky_freq_hz=synth.SKY_FREQ_HZ, keep_dc=1)
+    check(desc, volt, delay)
+
+
+@pytest.mark.parametrize("N,F", [(16, 1), (32, 1), (64, 8), (128, 4), (256, 1), (512, 16), (640, 5), (1280, 10),
+                                 (3200, 64), (6400, 50)])
+def test_fft_lengths(N, F):
+    T, K = 3, 40
+    bs = K * N
+    volt, delay = workload(100 + N, T, 2 * bs, block_samples=bs, delay="linear")
+    desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=K * N / synth.FS, samples_per_call=2 * bs,
+                       block_samples=bs, sky_freq_hz=synth.SKY_FREQ_HZ)
+    check(desc, volt, delay)
+
+
+def test_no_delay_and_zero_delay_identical():
+    T, N = 4, 64
+    volt, _ = workload(9, T, 64_000, delay=None)
+    desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=2, int_time_s=0.05, sky_freq_hz=synth.SKY_FREQ_HZ)
+    a, _, _ = run_gpu(desc, volt, None)
+    b, _, _ = run_gpu(desc, volt, np.zeros((2 * T, 3)))
+    assert np.array_equal(a, b)
+    check(desc, volt, None)
+
+
+@pytest.mark.parametrize("limit_frames", [1, 0])
+def test_workspace_grouping_and_chunking(limit_frames):
+    # limit_frames=1: two integrations per launch group; 0: each integration split in chunks
+    T, N, F = 6, 32, 2
+    volt, delay = workload(10, T, 512_000, delay="linear")
+    per_frame = N * 2 * (2 * T) * 4
+    K = 4000
+    limit = (2 * ((K + 63) // 64 * 64) * per_frame) if limit_frames else 1000 * per_frame
+    desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=0.1, samples_per_call=512_000,
+                       sky_freq_hz=synth.SKY_FREQ_HZ, workspace_limit=limit)
+    check(desc, volt, delay)
+
+
+def test_no_fft_float_mode():
+    T = 3
+    volt, delay = workload(11, T, 64_000, delay="linear")
+    desc = mw.PlanDesc(n_tiles=T, fft_len=1, fine_avg=1, int_time_s=0.0125, samples_per_call=64_000,
+                       sky_freq_hz=synth.SKY_FREQ_HZ)
+    check(desc, volt, delay)
+
+
+def test_host_path_matches_device_path():
+    T, N, F = 8, 128, 4
+    volt, delay = workload(12, T, 640_000, delay="linear")
+    desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=0.25, samples_per_call=640_000,
+                       sky_freq_hz=synth.SKY_FREQ_HZ)
+    vis_d, w_d, plan = run_gpu(desc, volt, delay)
+    host_out = torch.empty(plan.output_bytes, dtype=torch.uint8).pin_memory()
+    host_in = torch.from_numpy(volt.reshape(-1)).pin_memory()
+    mw.mwax_correlate_host(plan, host_in, np.ascontiguousarray(delay), host_out)
+    vis_h, w_h = mw.split_output(plan, host_out.numpy())
+    assert np.array_equal(vis_h, vis_d) and np.array_equal(w_h, w_d)

@@ -39,6 +39,23 @@ WORKLOAD = dict(name="full-array plain FX, 256 tiles, 8 s sub-observation, N=128
 SMALL = dict(WORKLOAD, name="full-array plain FX, 256 tiles, one 0.5 s integration, N=128, fscrunch 4",
              samples=640_000)
 METRIC = "real-time 256-tile coarse channels per B300"
+
+# DRAM bytes (read + write) per integration slot of the dominant kernel, from an ncu
+# capture of the one-integration case (profiles/).  Reported only while the kernel's
+# source is byte-identical to the one captured (sha1 prefix of its .cu file).
+TRAFFIC = {"xstep_simt_kernel": ("paper_2303_11557_b300/csrc/xstep_simt.cu", "96ef6c61dc27", 7.365158e9 + 0.17096576e9)}
+
+
+def traffic_per_slot(kernel: str):
+    import hashlib
+    if kernel not in TRAFFIC:
+        return None
+    path, sha, per_slot = TRAFFIC[kernel]
+    try:
+        h = hashlib.sha1(open(os.path.join(ROOT, path), "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return per_slot if h.startswith(sha) else None
 FP32_LANES_PER_SM, N_SM = 128, 148
 
 
@@ -267,6 +284,8 @@ def run_mine(args, world, rank, local):
     x_ms, x_n = stages["xstep"]
     f_ms, f_n = stages["fstep"]
     x_per_launch = x_flops * args.steps / x_n
+    tps = traffic_per_slot("xstep_simt_kernel")
+    x_traffic = None if tps is None else tps * n_ints * args.steps / x_n
     x_avg_ms = x_ms / x_n
     fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
     x_achieved = x_per_launch / (x_avg_ms * 1e-3) / 1e12
@@ -308,7 +327,7 @@ def run_mine(args, world, rank, local):
                    "precision": "fp32", "l2": "inputs 10.5 GB > 126 MB L2, no flush needed",
                    "parallelism": f"replicas x{world} (independent coarse channels)"},
         "roofline": {"bound": "alu", "kernel": "xstep_simt_kernel", "achieved": x_achieved, "peak": fp32_peak,
-                     "unit": "TFLOP/s", "frac": x_achieved / fp32_peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": x_achieved / fp32_peak, "traffic": x_traffic,
                      "peak_kind": f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {pk.get('sm_max_mhz')} MHz "
                                   f"({pk_kind} max clock)",
                      "per_launch": f"{x_per_launch:.4g} flop (8 x pairs x frames x {used} used bins)",

@@ -246,8 +246,9 @@ def run_mine(args, world, rank, local):
     host, delay = make_inputs(W, pin=not args.no_e2e)
     dev_volt = host.cuda(non_blocking=False)
     dev_delay = torch.from_numpy(delay).cuda()
+    prec = mw.PRECISIONS[args.precision]
     desc = mw.PlanDesc(n_tiles=W["n_tiles"], fft_len=W["fft_len"], fine_avg=W["fine_avg"],
-                       int_time_s=W["int_time_s"], samples_per_call=W["samples"], precision=mw.MWAX_FP32,
+                       int_time_s=W["int_time_s"], samples_per_call=W["samples"], precision=prec,
                        sky_freq_hz=W["sky_freq_hz"])
     plan = mw.mwax_plan_create_ex(desc)
     stream = torch.cuda.current_stream()
@@ -279,16 +280,26 @@ def run_mine(args, world, rank, local):
 
     info = plan.info
     K, n_ints = info["frames_per_int"], info["n_ints"]
-    x_flops, f_bytes, used = algorithmic_work(W["n_tiles"], W["fft_len"], W["fine_avg"], K, n_ints, 4)
+    x_flops, f_bytes, used = algorithmic_work(W["n_tiles"], W["fft_len"], W["fine_avg"], K, n_ints,
+                                              4 if prec == mw.MWAX_FP32 else 2)
     pk, pk_kind = peaks()
     x_ms, x_n = stages["xstep"]
     f_ms, f_n = stages["fstep"]
     x_per_launch = x_flops * args.steps / x_n
-    tps = traffic_per_slot("xstep_simt_kernel")
+    xkern = "xstep_simt_kernel" if prec == mw.MWAX_FP32 else "xstep_tc_kernel<0>"
+    tps = traffic_per_slot(xkern)
     x_traffic = None if tps is None else tps * n_ints * args.steps / x_n
     x_avg_ms = x_ms / x_n
-    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
     x_achieved = x_per_launch / (x_avg_ms * 1e-3) / 1e12
+    if prec == mw.MWAX_FP32:
+        x_peak = N_SM * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+        x_bound = "alu"
+        x_peak_kind = (f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {pk.get('sm_max_mhz')} MHz "
+                       f"({pk_kind} max clock)")
+    else:
+        x_peak = pk["bf16_tflops_sustained"] if "bf16_tflops_sustained" in pk else pk["bf16_tflops"]
+        x_bound = "tensor"
+        x_peak_kind = f"{pk_kind} dense bf16 (= fp16 rate) cuBLAS, sustained; burst {pk.get('bf16_tflops')}"
     f_per_launch = f_bytes * args.steps / f_n
     f_avg_ms = f_ms / f_n
     f_achieved = f_per_launch / (f_avg_ms * 1e-3) / 1e9
@@ -320,19 +331,18 @@ def run_mine(args, world, rank, local):
     line = {
         "metric": METRIC, "value": world * SUBOBS_S * (n_ints * W["int_time_s"] / SUBOBS_S) / (ms_max * 1e-3), "unit": "channels", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16"}[args.precision],
         "data": "synthetic (seeded Gaussian sigma=16 + point source, linear per-tile delays)",
         "config": {"workload": W["name"], "n_tiles": W["n_tiles"], "fft_len": W["fft_len"],
                    "fine_avg": W["fine_avg"], "int_time_s": W["int_time_s"], "subobs_s": SUBOBS_S,
-                   "precision": "fp32", "l2": "inputs 10.5 GB > 126 MB L2, no flush needed",
+                   "precision": args.precision, "l2": "inputs 10.5 GB > 126 MB L2, no flush needed",
                    "parallelism": f"replicas x{world} (independent coarse channels)"},
-        "roofline": {"bound": "alu", "kernel": "xstep_simt_kernel", "achieved": x_achieved, "peak": fp32_peak,
-                     "unit": "TFLOP/s", "frac": x_achieved / fp32_peak, "traffic": x_traffic,
-                     "peak_kind": f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {pk.get('sm_max_mhz')} MHz "
-                                  f"({pk_kind} max clock)",
+        "roofline": {"bound": x_bound, "kernel": xkern, "achieved": x_achieved, "peak": x_peak,
+                     "unit": "TFLOP/s", "frac": x_achieved / x_peak, "traffic": x_traffic,
+                     "peak_kind": x_peak_kind,
                      "per_launch": f"{x_per_launch:.4g} flop (8 x pairs x frames x {used} used bins)",
                      "avg_launch_ms": x_avg_ms},
-        "roofline_fstep": {"bound": "hbm", "kernel": "fstep_kernel<128>", "achieved": f_achieved,
+        "roofline_fstep": {"bound": "hbm", "kernel": f"fstep_kernel<128, {args.precision}>", "achieved": f_achieved,
                            "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": f_achieved / pk["hbm_gbs"],
                            "per_launch_bytes": f_per_launch, "avg_launch_ms": f_avg_ms,
                            "peak_kind": f"{pk_kind} copy bandwidth"},
@@ -355,6 +365,7 @@ def main():
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"])
     ap.add_argument("--workload", default="full", choices=["full", "small"],
                     help="small = one 0.5 s integration (for profiler captures)")
     args = ap.parse_args()

@@ -39,6 +39,9 @@ struct mwax_plan {
     int n_tiles = 0;
     int* status = nullptr;
     float out_scale = 1.0f, post_scale = 1.0f;
+    bool tensor_cores = false;   // tcgen05 X-step (FP16 / FP8 / INT8) vs CUDA-core FP32
+    int tile = 64;               // paths per tile side of the X-step
+    CUtensorMap tmap;            // operand planes, for the tcgen05 X-step
 
     // host-input path
     int8_t* dvolt = nullptr;
@@ -182,7 +185,7 @@ mwax_status validate(const mwax_plan_desc& d, mwax_plan& p)
         return fail(MWAX_EINVAL, "MWAX_INT8 needs fft_len = fine_avg = 1 (no FFT)");
     if (!fft_len_supported(d.fft_len)) return fail(MWAX_EUNSUPPORTED, "fft_len %d is not built", d.fft_len);
     if (d.fft_len > 1 && d.fft_len < 16) return fail(MWAX_EUNSUPPORTED, "fft_len %d is not built", d.fft_len);
-    if (d.precision != MWAX_FP32)
+    if (d.precision != MWAX_FP32 && d.precision != MWAX_FP16)
         return fail(MWAX_EUNSUPPORTED, "precision %d is not built in this library version", d.precision);
 
     p.desc = d;
@@ -256,8 +259,21 @@ mwax_status setup(mwax_plan& p)
     MWAX_CUDA(cudaMalloc(&p.bins, sizeof(BinCoef) * p.N));
     MWAX_CUDA(cudaMemcpy(p.bins, bins.data(), sizeof(BinCoef) * p.N, cudaMemcpyHostToDevice));
 
-    // triangle tiles of 64 x 64 path pairs
-    const int nb = (p.n + 63) / 64;
+    // FP16 operands: power-of-two pre-scale keeping |Re X|, |Im X| <= 181 N (int8
+    // magnitude 128 sqrt 2 summed over N samples) below 2^15; undone exactly after the MMA
+    if (p.prec == MWAX_FP16) {
+        int k = 0;
+        while (181.02 * p.N / (double)(1 << k) > 32768.0) ++k;
+        p.out_scale = ldexpf(1.0f, -k);
+        p.post_scale = ldexpf(1.0f, 2 * k);
+    }
+    p.tensor_cores = p.prec != MWAX_FP32;
+    p.tile = p.tensor_cores ? 128 : 64;
+    if (p.tensor_cores)
+        MWAX_CUDA(make_operand_tmap(&p.tmap, p.Y, p.elem_bytes == 1 ? 1 : 2, p.Kpad, p.n, p.slots * p.N * 2));
+
+    // triangle tiles of path pairs
+    const int nb = (p.n + p.tile - 1) / p.tile;
     std::vector<int2> tiles;
     for (int i = 0; i < nb; ++i)
         for (int j = i; j < nb; ++j) tiles.push_back(make_int2(i, j));
@@ -265,9 +281,11 @@ mwax_status setup(mwax_plan& p)
     MWAX_CUDA(cudaMalloc(&p.tiles, sizeof(int2) * tiles.size()));
     MWAX_CUDA(cudaMemcpy(p.tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice));
 
-    // runs of output channels: enough CTAs for ~8 per SM, at least 4 channels per run
+    // runs of output channels: enough CTAs for several waves (1 resident CTA per SM for
+    // the tensor-core kernel, 2 for the CUDA-core one), at least 4 channels per run
     const long long ctas_wo_runs = (long long)p.n_tiles * p.slots;
-    int want_runs = (int)std::max<long long>(1, (8LL * 148 + ctas_wo_runs - 1) / ctas_wo_runs);
+    const long long want_ctas = p.tensor_cores ? 4LL * 148 : 8LL * 148;
+    int want_runs = (int)std::max<long long>(1, (want_ctas + ctas_wo_runs - 1) / ctas_wo_runs);
     int run_len = std::max(4, (p.M + want_runs - 1) / want_runs);
     run_len = std::min(run_len, p.M);
     std::vector<RunInfo> runs;
@@ -350,13 +368,18 @@ mwax_status enqueue(mwax_plan* p, const int8_t* volt, bool have_delay, char* out
             fa.tw = p->tw;
             fa.m_begin = m_begin;
             fa.n_frames = nframes;
+            // a short last chunk of a split integration overwrites the previous chunk's
+            // frames up to the next 128-frame boundary with zeros
+            fa.n_store = (p->chunks == 1) ? nframes
+                                          : std::min(p->Kpad, (nframes + kKAlign - 1) / kKAlign * kKAlign);
             fa.Kc = (p->chunks == 1) ? p->K : p->Kc;
             fa.Kpad = p->Kpad;
             fa.n = p->n;
             fa.bs = p->bs;
             fa.nu = p->nu;
             fa.out_scale = p->out_scale;
-            MWAX_CUDA(timed(p, 1, [&] { return launch_fstep(p->N, FOUT_F32, fa, s); }));
+            const int fout = (p->prec == MWAX_FP32) ? FOUT_F32 : FOUT_F16;
+            MWAX_CUDA(timed(p, 1, [&] { return launch_fstep(p->N, fout, fa, s); }));
 
             XArgs xa;
             memset(&xa, 0, sizeof xa);
@@ -375,7 +398,14 @@ mwax_status enqueue(mwax_plan* p, const int8_t* volt, bool have_delay, char* out
             xa.tiles = p->tiles;
             xa.post_scale = p->post_scale;
             xa.status = p->status;
-            MWAX_CUDA(timed(p, 2, [&] { return launch_xstep_simt(xa, p->n_tiles, p->n_runs, (int)nslots, s); }));
+            xa.spin_limit = 2000000;   // x 1000 cycles: ~1 s per bounded wait
+            if (p->tensor_cores) {
+                MWAX_CUDA(timed(p, 2, [&] {
+                    return launch_xstep_tc(0, p->tmap, xa, p->n_tiles, p->n_runs, (int)nslots, s);
+                }));
+            } else {
+                MWAX_CUDA(timed(p, 2, [&] { return launch_xstep_simt(xa, p->n_tiles, p->n_runs, (int)nslots, s); }));
+            }
         }
     }
     return MWAX_OK;

@@ -292,8 +292,8 @@ __global__ void __launch_bounds__(kThreads) fstep_kernel(const FArgs a)
         const int f = threadIdx.x;
         FrameInfo fi;
         const long long fl = f0 + f;
-        fi.slot = (fl < a.n_frames) ? fl / a.Kc : -1;
-        fi.k = (fl < a.n_frames) ? fl % a.Kc : 0;
+        fi.slot = (fl < a.n_store) ? fl / a.Kc : -1;
+        fi.k = (fl < a.n_store) ? fl % a.Kc : 0;
         fi.delay = 0;
         fi.phi0 = fi.d_hi = fi.d_lo = 0.0f;
         if (a.delay != nullptr && fl < a.n_frames) {
@@ -341,15 +341,18 @@ __global__ void __launch_bounds__(256) unpack_kernel(const FArgs a)
     const int p = blockIdx.y;
     const long long i4 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long f_first = i4 * 4;
-    if (f_first >= a.n_frames) return;
+    if (f_first >= a.n_store) return;
     for (int e = 0; e < 4; ++e) {
         const long long fl = f_first + e;
-        if (fl >= a.n_frames) break;
+        if (fl >= a.n_store) break;
         const long long s = a.m_begin + fl;
-        const long long blk = s / a.bs, off = s % a.bs;
-        const char2 x = *reinterpret_cast<const char2*>(a.volt + ((blk * a.n + p) * (long long)a.bs + off) * 2);
-        float2 v = make_float2((float)x.x, (float)x.y);
-        if (a.delay != nullptr) {
+        float2 v = make_float2(0.0f, 0.0f);
+        if (fl < a.n_frames) {
+            const long long blk = s / a.bs, off = s % a.bs;
+            const char2 x = *reinterpret_cast<const char2*>(a.volt + ((blk * a.n + p) * (long long)a.bs + off) * 2);
+            v = make_float2((float)x.x, (float)x.y);
+        }
+        if (a.delay != nullptr && fl < a.n_frames) {
             const double t = ((double)s + 0.5) / kFs;
             const double tau = a.delay[3 * p] + t * (a.delay[3 * p + 1] + t * a.delay[3 * p + 2]);
             const double ph = a.nu * tau;
@@ -375,7 +378,7 @@ cudaError_t launch_n(const FArgs& a, cudaStream_t s)
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
-    dim3 grid((unsigned)((a.n_frames + Sched<N>::fb - 1) / Sched<N>::fb), (unsigned)a.n);
+    dim3 grid((unsigned)((a.n_store + Sched<N>::fb - 1) / Sched<N>::fb), (unsigned)a.n);
     fstep_kernel<N, OUTK><<<grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -385,7 +388,7 @@ cudaError_t launch_kind(int N, const FArgs& a, cudaStream_t s)
 {
     switch (N) {
         case 1: {
-            dim3 grid((unsigned)((a.n_frames + 1023) / 1024), (unsigned)a.n);
+            dim3 grid((unsigned)((a.n_store + 1023) / 1024), (unsigned)a.n);
             unpack_kernel<OUTK><<<grid, 256, 0, s>>>(a);
             return cudaGetLastError();
         }

@@ -1,6 +1,7 @@
 // Internal declarations of the MWAX B300 correlator library (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -12,7 +13,7 @@ namespace mwax {
 
 constexpr double kFs = 1280000.0;        // coarse-channel sample rate (Sec. 2.5)
 constexpr int kDefaultBlock = 64000;     // samples per path per 50 ms data block (Sec. 2.5)
-constexpr int kKAlign = 64;              // frames per operand row are padded to this
+constexpr int kKAlign = 128;             // frames per operand row are padded to this
 
 // Output-type selector of the F-step.
 enum FOut : int { FOUT_F32 = 0, FOUT_F16 = 1, FOUT_AMAX = 2, FOUT_E4M3 = 3 };
@@ -40,7 +41,8 @@ struct FArgs {
     const float* scale;   // FP8 quantise pass: [slot][N][n] scale s = amax / 448
     const float2* tw;     // e^{-2 pi i k / N}, k < N
     long long m_begin;
-    long long n_frames;
+    long long n_frames;   // frames with data
+    long long n_store;    // frames stored (>= n_frames: the rest are written as zeros)
     long long Kc;
     long long Kpad;
     int n;
@@ -72,6 +74,10 @@ cudaError_t launch_fstep(int N, int out_kind, const FArgs& a, cudaStream_t s);
 cudaError_t launch_init_output(char* out, long long n_ints, long long vis_set_bytes, long long weights_bytes,
                                cudaStream_t s);
 cudaError_t launch_xstep_simt(const XArgs& a, int n_tiles, int n_runs, int slots, cudaStream_t s);
+cudaError_t make_operand_tmap(CUtensorMap* map, const void* Y, int elem_bytes, long long Kpad, int n,
+                              long long planes);
+cudaError_t launch_xstep_tc(int op, const CUtensorMap& map, const XArgs& a, int n_tiles, int n_runs, int slots,
+                            cudaStream_t s);
 bool fft_len_supported(int N);
 
 }  // namespace mwax

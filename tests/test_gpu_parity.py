@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle, element by element
 on the same seeded inputs.  Bar (per result, relative to the parallel-pol autos of the
-same channel and integration): FP32 <= 1e-5."""
+same channel and integration): FP32 <= 1e-5, FP16 (tcgen05) <= 2e-3."""
 import numpy as np
 import pytest
 
@@ -12,7 +12,8 @@ from _parity import oracle_desc, parity_error, workload
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-TOL = {mw.MWAX_FP32: 1e-5}
+TOL = {mw.MWAX_FP32: 1e-5, mw.MWAX_FP16: 2e-3}
+FLOAT_PRECS = [pytest.param(mw.MWAX_FP32, id="fp32"), pytest.param(mw.MWAX_FP16, id="fp16")]
 
 
 def run_gpu(desc: mw.PlanDesc, volt: np.ndarray, delay):
@@ -47,72 +48,83 @@ def check(desc, volt, delay, tol=None):
     return err
 
 
-def test_config0_fp32():
+@pytest.mark.parametrize("prec", FLOAT_PRECS)
+def test_config0(prec):
     # 16 tiles x 2 pols, 0.4 s at 1.28 MS/s, 128-point FFT, no averaging, fixed 0-50 ns delays
     T, N, F, t_int = 16, 128, 1, 0.4
     volt, delay = workload(0x4D574158, T, 512_000)
     desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=t_int, samples_per_call=512_000,
-                       sky_freq_hz=synth.SKY_FREQ_HZ)
+                       sky_freq_hz=synth.SKY_FREQ_HZ, precision=prec)
     check(desc, volt, delay)
 
 
-def test_ragged_tiles_and_averaging():
-    # 80 paths = one full 64-path tile block + a ragged one; even fscrunch, 2 integrations
-    T, N, F, t_int = 40, 32, 4, 0.1
+@pytest.mark.parametrize("prec", FLOAT_PRECS)
+@pytest.mark.parametrize("T", [40, 100])
+def test_ragged_tiles_and_averaging(prec, T):
+    # 80 / 200 paths: full tile blocks plus a ragged one; even fscrunch, 2 integrations
+    N, F, t_int = 32, 4, 0.1
     volt, delay = workload(7, T, 256_000, delay="linear")
     desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=t_int, samples_per_call=256_000,
-                       sky_freq_hz=synth.SKY_FREQ_HZ)
+                       sky_freq_hz=synth.SKY_FREQ_HZ, precision=prec)
     check(desc, volt, delay)
 
 
-def test_ragged_frames_odd_fscrunch_keep_dc():
-    # 1000 frames per integration (not a multiple of the 32-frame chunk), F = 2, DC kept
+@pytest.mark.parametrize("prec", FLOAT_PRECS)
+def test_ragged_frames_odd_fscrunch_keep_dc(prec):
+    # 1000 frames per integration (not a multiple of the frame chunks), F = 2, DC kept
     T, N, F, t_int = 5, 16, 2, 0.0125
     volt, delay = workload(8, T, 64_000, block_samples=16_000, delay="linear")
     desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=t_int, samples_per_call=64_000,
-                       block_samples=16_000, sky_freq_hz=synth.SKY_FREQ_HZ, keep_dc=1)
+                       block_samples=16_000, sky_freq_hz=synth.SKY_FREQ_HZ, keep_dc=1, precision=prec)
     check(desc, volt, delay)
 
 
+@pytest.mark.parametrize("prec", FLOAT_PRECS)
 @pytest.mark.parametrize("N,F", [(16, 1), (32, 1), (64, 8), (128, 4), (256, 1), (512, 16), (640, 5), (1280, 10),
                                  (3200, 64), (6400, 50)])
-def test_fft_lengths(N, F):
+def test_fft_lengths(N, F, prec):
     T, K = 3, 40
     bs = K * N
     volt, delay = workload(100 + N, T, 2 * bs, block_samples=bs, delay="linear")
     desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=K * N / synth.FS, samples_per_call=2 * bs,
-                       block_samples=bs, sky_freq_hz=synth.SKY_FREQ_HZ)
+                       block_samples=bs, sky_freq_hz=synth.SKY_FREQ_HZ, precision=prec)
     check(desc, volt, delay)
 
 
-def test_no_delay_and_zero_delay_identical():
+@pytest.mark.parametrize("prec", FLOAT_PRECS)
+def test_no_delay_and_zero_delay_identical(prec):
     T, N = 4, 64
     volt, _ = workload(9, T, 64_000, delay=None)
-    desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=2, int_time_s=0.05, sky_freq_hz=synth.SKY_FREQ_HZ)
+    desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=2, int_time_s=0.05, sky_freq_hz=synth.SKY_FREQ_HZ,
+                       precision=prec)
     a, _, _ = run_gpu(desc, volt, None)
     b, _, _ = run_gpu(desc, volt, np.zeros((2 * T, 3)))
     assert np.array_equal(a, b)
     check(desc, volt, None)
 
 
+@pytest.mark.parametrize("prec", FLOAT_PRECS)
 @pytest.mark.parametrize("limit_frames", [1, 0])
-def test_workspace_grouping_and_chunking(limit_frames):
-    # limit_frames=1: two integrations per launch group; 0: each integration split in chunks
+def test_workspace_grouping_and_chunking(limit_frames, prec):
+    # limit_frames=1: two integrations per launch group; 0: each integration split in
+    # chunks of 896 frames (4000 = 4 x 896 + 416: a short, zero-padded last chunk)
     T, N, F = 6, 32, 2
     volt, delay = workload(10, T, 512_000, delay="linear")
-    per_frame = N * 2 * (2 * T) * 4
+    elem = 4 if prec == mw.MWAX_FP32 else 2
+    per_frame = N * 2 * (2 * T) * elem
     K = 4000
-    limit = (2 * ((K + 63) // 64 * 64) * per_frame) if limit_frames else 1000 * per_frame
+    limit = (2 * ((K + 127) // 128 * 128) * per_frame) if limit_frames else 1000 * per_frame
     desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=0.1, samples_per_call=512_000,
-                       sky_freq_hz=synth.SKY_FREQ_HZ, workspace_limit=limit)
+                       sky_freq_hz=synth.SKY_FREQ_HZ, workspace_limit=limit, precision=prec)
     check(desc, volt, delay)
 
 
-def test_no_fft_float_mode():
+@pytest.mark.parametrize("prec", FLOAT_PRECS)
+def test_no_fft_float_mode(prec):
     T = 3
     volt, delay = workload(11, T, 64_000, delay="linear")
     desc = mw.PlanDesc(n_tiles=T, fft_len=1, fine_avg=1, int_time_s=0.0125, samples_per_call=64_000,
-                       sky_freq_hz=synth.SKY_FREQ_HZ)
+                       sky_freq_hz=synth.SKY_FREQ_HZ, precision=prec)
     check(desc, volt, delay)
 
 

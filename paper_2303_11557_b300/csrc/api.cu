@@ -32,10 +32,12 @@ struct mwax_plan {
     size_t Y_bytes = 0;
     float2* tw = nullptr;
     double* delay = nullptr;
-    BinCoef* bins = nullptr;
+    Group* groups = nullptr;
+    int n_groups = 0;
+    float* gain = nullptr;
     RunInfo* runs = nullptr;
     int n_runs = 0;
-    int2* tiles = nullptr;
+    int4* tiles = nullptr;
     int n_tiles = 0;
     int* status = nullptr;
     float out_scale = 1.0f, post_scale = 1.0f;
@@ -86,39 +88,59 @@ mwax_status fail(mwax_status st, const char* fmt, ...)
 // Output channel j of M = N/F: centred on ultrafine offset (j - floor(M/2)) F; odd F
 // takes F bins of weight 1, even F takes F+1 bins with the two ends at 1/2; the DC bin
 // is dropped from the centre channel when F > 1 (unless kept); bins beyond the coarse
-// channel do not exist (Sec. 2.6).  Fills per-bin coefficients w / sum(w).
-bool build_bins(int N, int F, int dc_excl, std::vector<BinCoef>& bins, std::vector<double>& wsum)
+// channel do not exist (Sec. 2.6).  Produces gain[c] = sqrt(w_c) and the groups of
+// consecutive channels that feed the same output channels, with coef = 1 / sum(w).
+bool build_groups(int N, int F, int dc_excl, std::vector<float>& gain, std::vector<Group>& groups)
 {
     const int M = N / F, jc = M / 2, half = F / 2;
-    bins.assign(N, BinCoef{-1, -1, 0.0f, 0.0f});
-    wsum.assign(M, 0.0);
-    std::vector<std::vector<std::pair<int, double>>> members(M);
+    std::vector<double> w(N, 0.0), wsum(M, 0.0);
+    std::vector<std::vector<int>> feeds(N);
     for (int j = 0; j < M; ++j) {
         const long long mid = (long long)(j - jc) * F;
         for (long long u = mid - half; u <= mid + half; ++u) {
             const long long c = u + N / 2;
             if (c < 0 || c >= N) continue;
-            double w = (F % 2 == 0 && (u == mid - half || u == mid + half)) ? 0.5 : 1.0;
-            if (dc_excl && F > 1 && u == 0) w = 0.0;
-            if (w == 0.0) continue;
-            members[j].push_back({(int)c, w});
-            wsum[j] += w;
+            double wt = (F % 2 == 0 && (u == mid - half || u == mid + half)) ? 0.5 : 1.0;
+            if (dc_excl && F > 1 && u == 0) wt = 0.0;
+            if (wt == 0.0) continue;
+            if (w[c] != 0.0 && w[c] != wt) return false;   // a bin has one weight everywhere
+            w[c] = wt;
+            feeds[c].push_back(j);
+            wsum[j] += wt;
         }
     }
-    for (int j = 0; j < M; ++j) {
+    gain.assign(N, 0.0f);
+    for (int c = 0; c < N; ++c) gain[c] = (float)sqrt(w[c]);
+    for (int j = 0; j < M; ++j)
         if (wsum[j] <= 0.0) return false;
-        for (auto& m : members[j]) {
-            BinCoef& b = bins[m.first];
-            const float coef = (float)(m.second / wsum[j]);
-            if (b.ja < 0) {
-                b.ja = j;
-                b.ca = coef;
-            } else if (b.jb < 0) {
-                b.jb = j;
-                b.cb = coef;
-            } else {
-                return false;   // a bin feeds at most two channels
-            }
+    groups.clear();
+    for (int c = 0; c < N; ++c) {
+        if (w[c] == 0.0) continue;
+        if (feeds[c].size() > 2) return false;
+        const int ja = feeds[c][0], jb = feeds[c].size() > 1 ? feeds[c][1] : -1;
+        if (!groups.empty() && groups.back().ja == ja && groups.back().jb == jb) {
+            groups.back().c1 = c + 1;   // zero-weight channels in between are skipped by the kernels
+            continue;
+        }
+        Group g;
+        g.c0 = c;
+        g.c1 = c + 1;
+        g.ja = ja;
+        g.jb = jb;
+        g.ca = (float)(1.0 / wsum[ja]);
+        g.cb = jb >= 0 ? (float)(1.0 / wsum[jb]) : 0.0f;
+        g.first_a = g.first_b = 0;
+        groups.push_back(g);
+    }
+    // Mark, per output channel, the first group feeding it (groups are in channel order
+    // and a run always starts at the first group of its first channel).
+    std::vector<char> seen(M, 0);
+    for (auto& g : groups) {
+        if (!seen[g.ja]) g.first_a = 1;
+        seen[g.ja] = 1;
+        if (g.jb >= 0) {
+            if (!seen[g.jb]) g.first_b = 1;
+            seen[g.jb] = 1;
         }
     }
     return true;
@@ -141,7 +163,8 @@ void free_plan(mwax_plan* p)
     cudaFree(p->Y);
     cudaFree(p->tw);
     cudaFree(p->delay);
-    cudaFree(p->bins);
+    cudaFree(p->groups);
+    cudaFree(p->gain);
     cudaFree(p->runs);
     cudaFree(p->tiles);
     cudaFree(p->status);
@@ -251,13 +274,16 @@ mwax_status setup(mwax_plan& p)
     MWAX_CUDA(cudaMemcpy(p.tw, tw.data(), sizeof(float2) * p.N, cudaMemcpyHostToDevice));
     MWAX_CUDA(cudaMalloc(&p.delay, sizeof(double) * 3 * p.n));
 
-    // averaging coefficients
-    std::vector<BinCoef> bins;
-    std::vector<double> wsum;
-    if (!build_bins(p.N, p.F, p.dc_excl, bins, wsum))
+    // averaging: per-channel gains (applied in the F-step) and channel groups
+    std::vector<float> gain;
+    std::vector<Group> groups;
+    if (!build_groups(p.N, p.F, p.dc_excl, gain, groups))
         return fail(MWAX_EINVAL, "channel averaging with fscrunch %d leaves an empty channel", p.F);
-    MWAX_CUDA(cudaMalloc(&p.bins, sizeof(BinCoef) * p.N));
-    MWAX_CUDA(cudaMemcpy(p.bins, bins.data(), sizeof(BinCoef) * p.N, cudaMemcpyHostToDevice));
+    p.n_groups = (int)groups.size();
+    MWAX_CUDA(cudaMalloc(&p.gain, sizeof(float) * p.N));
+    MWAX_CUDA(cudaMemcpy(p.gain, gain.data(), sizeof(float) * p.N, cudaMemcpyHostToDevice));
+    MWAX_CUDA(cudaMalloc(&p.groups, sizeof(Group) * groups.size()));
+    MWAX_CUDA(cudaMemcpy(p.groups, groups.data(), sizeof(Group) * groups.size(), cudaMemcpyHostToDevice));
 
     // FP16 operands: power-of-two pre-scale keeping |Re X|, |Im X| <= 181 N (int8
     // magnitude 128 sqrt 2 summed over N samples) below 2^15; undone exactly after the MMA
@@ -268,18 +294,21 @@ mwax_status setup(mwax_plan& p)
         p.post_scale = ldexpf(1.0f, 2 * k);
     }
     p.tensor_cores = p.prec != MWAX_FP32;
-    p.tile = p.tensor_cores ? 128 : 64;
     if (p.tensor_cores)
         MWAX_CUDA(make_operand_tmap(&p.tmap, p.Y, p.elem_bytes == 1 ? 1 : 2, p.Kpad, p.n, p.slots * p.N * 2));
 
-    // triangle tiles of path pairs
-    const int nb = (p.n + p.tile - 1) / p.tile;
-    std::vector<int2> tiles;
-    for (int i = 0; i < nb; ++i)
-        for (int j = i; j < nb; ++j) tiles.push_back(make_int2(i, j));
+    // tiles of path pairs on or above the diagonal
+    std::vector<int4> tiles;
+    if (p.tensor_cores) {
+        tiles.resize(build_tc_tiles(p.n, nullptr, 0));
+        build_tc_tiles(p.n, tiles.data(), (int)tiles.size());
+    } else {
+        for (int i = 0; i < p.n; i += 64)
+            for (int j = i; j < p.n; j += 64) tiles.push_back(make_int4(i, j, 64, i == j ? 1 : 0));
+    }
     p.n_tiles = (int)tiles.size();
-    MWAX_CUDA(cudaMalloc(&p.tiles, sizeof(int2) * tiles.size()));
-    MWAX_CUDA(cudaMemcpy(p.tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice));
+    MWAX_CUDA(cudaMalloc(&p.tiles, sizeof(int4) * tiles.size()));
+    MWAX_CUDA(cudaMemcpy(p.tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice));
 
     // runs of output channels: enough CTAs for several waves (1 resident CTA per SM for
     // the tensor-core kernel, 2 for the CUDA-core one), at least 4 channels per run
@@ -293,14 +322,14 @@ mwax_status setup(mwax_plan& p)
         RunInfo r;
         r.j0 = j0;
         r.j1 = std::min(p.M, j0 + run_len);
-        r.c0 = p.N;
-        r.c1 = 0;
-        for (int c = 0; c < p.N; ++c) {
-            const BinCoef& b = bins[c];
-            const bool in = (b.ja >= r.j0 && b.ja < r.j1) || (b.jb >= r.j0 && b.jb < r.j1);
+        r.g0 = p.n_groups;
+        r.g1 = 0;
+        for (int g = 0; g < p.n_groups; ++g) {
+            const Group& gr = groups[g];
+            const bool in = (gr.ja >= r.j0 && gr.ja < r.j1) || (gr.jb >= r.j0 && gr.jb < r.j1);
             if (in) {
-                r.c0 = std::min(r.c0, c);
-                r.c1 = std::max(r.c1, c + 1);
+                r.g0 = std::min(r.g0, g);
+                r.g1 = std::max(r.g1, g + 1);
             }
         }
         runs.push_back(r);
@@ -366,6 +395,7 @@ mwax_status enqueue(mwax_plan* p, const int8_t* volt, bool have_delay, char* out
             fa.delay = have_delay ? p->delay : nullptr;
             fa.Y = p->Y;
             fa.tw = p->tw;
+            fa.gain = p->gain;
             fa.m_begin = m_begin;
             fa.n_frames = nframes;
             // a short last chunk of a split integration overwrites the previous chunk's
@@ -393,10 +423,13 @@ mwax_status enqueue(mwax_plan* p, const int8_t* volt, bool have_delay, char* out
             xa.N = p->N;
             xa.M = p->M;
             xa.B = p->B;
-            xa.bins = p->bins;
+            xa.groups = p->groups;
+            xa.n_groups = p->n_groups;
+            xa.gain = p->gain;
             xa.runs = p->runs;
             xa.tiles = p->tiles;
             xa.post_scale = p->post_scale;
+            xa.first_store = (ch == 0) ? 1 : 0;
             xa.status = p->status;
             xa.spin_limit = 2000000;   // x 1000 cycles: ~1 s per bounded wait
             if (p->tensor_cores) {

@@ -119,6 +119,53 @@ struct Dft<16> {
     }
 };
 
+template <>
+struct Dft<32> {
+    __device__ __forceinline__ static void run(float2 (&v)[32])
+    {
+        // e^{-2 pi i k / 32}, k = 0..15
+        const float2 w[16] = {make_float2(1.0f, 0.0f),
+                              make_float2(0.9807852804032304f, -0.19509032201612825f),
+                              make_float2(0.9238795325112867f, -0.3826834323650898f),
+                              make_float2(0.8314696123025452f, -0.5555702330196022f),
+                              make_float2(0.7071067811865476f, -0.7071067811865475f),
+                              make_float2(0.5555702330196023f, -0.8314696123025452f),
+                              make_float2(0.38268343236508984f, -0.9238795325112867f),
+                              make_float2(0.19509032201612833f, -0.9807852804032304f),
+                              make_float2(0.0f, -1.0f),
+                              make_float2(-0.1950903220161282f, -0.9807852804032304f),
+                              make_float2(-0.3826834323650897f, -0.9238795325112867f),
+                              make_float2(-0.555570233019602f, -0.8314696123025455f),
+                              make_float2(-0.7071067811865475f, -0.7071067811865476f),
+                              make_float2(-0.8314696123025453f, -0.5555702330196022f),
+                              make_float2(-0.9238795325112867f, -0.3826834323650899f),
+                              make_float2(-0.9807852804032304f, -0.1950903220161286f)};
+        float2 e[16], o[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            e[k] = v[2 * k];
+            o[k] = v[2 * k + 1];
+        }
+        Dft<16>::run(e);
+        Dft<16>::run(o);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            float2 t = (k == 0) ? o[0] : (k == 8 ? c_mul_negi(o[8]) : c_mul(o[k], w[k]));
+            v[k] = c_add(e[k], t);
+            v[k + 16] = c_sub(e[k], t);
+        }
+    }
+};
+
+template <int R>
+struct DftIf {   // radix-1 "DFT" is the identity
+    __device__ __forceinline__ static void run(float2 (&v)[R]) { Dft<R>::run(v); }
+};
+template <>
+struct DftIf<1> {
+    __device__ __forceinline__ static void run(float2 (&)[1]) {}
+};
+
 // Radix schedule per FFT length (applied in this order).
 template <int N>
 struct Sched;
@@ -164,29 +211,42 @@ struct FrameInfo {
     float d_hi;       // tau Fs / N [cycles per bin], top 12 significant bits
     float d_lo;       // the rest
     int delay;
+    float2 step;      // e^{2 pi i (N/R_last) d}: phasor ratio between a thread's outputs
+    float2 wrap;      // e^{-2 pi i N d}: outputs past N/2 sit at u = k - N
 };
 
 template <int N, int OUTK>
 struct Store {
-    // Write one corrected spectral value of channel c of frame f.
-    __device__ __forceinline__ static void run(const FArgs& a, const FrameInfo& fi, int p, int c, float2 v)
+    // Write one corrected spectral value: real plane at element `at`, imaginary plane at
+    // `at + plane_stride` of the operand buffer.
+    __device__ __forceinline__ static void run(const FArgs& a, long long at, long long plane_stride, float2 v)
     {
-        if (fi.slot < 0) return;
-        long long row0 = ((fi.slot * N + c) * 2 + 0) * (long long)a.n + p;
-        long long row1 = row0 + a.n;
         if (OUTK == FOUT_F32) {
             float* Y = static_cast<float*>(a.Y);
-            Y[row0 * a.Kpad + fi.k] = v.x;
-            Y[row1 * a.Kpad + fi.k] = v.y;
+            Y[at] = v.x;
+            Y[at + plane_stride] = v.y;
         } else if (OUTK == FOUT_F16) {
             __half* Y = static_cast<__half*>(a.Y);
-            Y[row0 * a.Kpad + fi.k] = __float2half_rn(v.x * a.out_scale);
-            Y[row1 * a.Kpad + fi.k] = __float2half_rn(v.y * a.out_scale);
+            Y[at] = __float2half_rn(v.x * a.out_scale);
+            Y[at + plane_stride] = __float2half_rn(v.y * a.out_scale);
         }
     }
 };
 
-// Delay phasor e^{2 pi i (phi0 + u d)} of ultrafine offset u (|u| < 4096).
+// Delay phasor e^{2 pi i (phi0 + u d)} of ultrafine offset u (|u| < 4096), d = d_hi + d_lo
+// with d_hi holding 12 significant bits so that u * d_hi is exact in FP32.
+__device__ __forceinline__ float2 delay_phasor_u(float phi0, float d_hi, float d_lo, int u)
+{
+    float uf = (float)u;
+    float x = uf * d_hi;
+    x -= rintf(x);
+    float y = phi0 + x + uf * d_lo;
+    y -= rintf(y);
+    float s, c;
+    sincospif(2.0f * y, &s, &c);
+    return make_float2(c, s);
+}
+
 __device__ __forceinline__ float2 delay_phasor(const FrameInfo& fi, int u)
 {
     float uf = (float)u;
@@ -211,7 +271,8 @@ struct Pass {
     static constexpr bool LAST = (P == Sched<N>::passes - 1);
 
     __device__ __forceinline__ static void run(const FArgs& a, const FrameInfo* finfo, float2* buf0,
-                                               float2* buf1, const int8_t* stage, int p)
+                                               float2* buf1, const int8_t* stage, int p, const float2* tw,
+                                               const float* gain)
     {
         float2* in = (P % 2 == 0) ? buf1 : buf0;   // pass 0 reads the staging area in buf1
         float2* out = (P % 2 == 0) ? buf0 : buf1;
@@ -229,7 +290,7 @@ struct Pass {
             }
             if (NS > 1) {
 #pragma unroll
-                for (int r = 1; r < R; ++r) v[r] = c_mul(v[r], __ldg(&a.tw[(j % NS) * r * (N / (NS * R))]));
+                for (int r = 1; r < R; ++r) v[r] = c_mul(v[r], tw[(j % NS) * r * (N / (NS * R))]);
             }
             Dft<R>::run(v);
             if (!LAST) {
@@ -238,13 +299,26 @@ struct Pass {
                 for (int r = 0; r < R; ++r) out[f * ROW + d + r * NS] = v[r];
             } else {
                 const FrameInfo fi = finfo[f];
+                if (fi.slot < 0) continue;
+                // outputs k = j + r NB, r = 0..R-1; channel c = (k + N/2) mod N
+                float2 E = make_float2(1.0f, 0.0f);
+                if (fi.delay) E = delay_phasor(fi, j);   // u = j for r = 0 (j < NB <= N/2)
+                const long long cs = 2LL * a.n * a.Kpad;                 // channel stride
+                const long long ps = (long long)a.n * a.Kpad;            // plane stride
+                const long long base = (fi.slot * N * 2LL * a.n + p) * a.Kpad + fi.k;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const int k = j + r * NB;                    // natural-order bin
-                    const int u = (k < N - N / 2) ? k : k - N;   // ultrafine offset
+                    const int k = j + r * NB;
+                    const int c = (k < N - N / 2) ? k + N / 2 : k - (N - N / 2);
                     float2 y = v[r];
-                    if (fi.delay) y = c_mul(y, delay_phasor(fi, u));
-                    Store<N, OUTK>::run(a, fi, p, u + N / 2, y);
+                    if (fi.delay) {
+                        y = c_mul(y, (k < N - N / 2) ? E : c_mul(E, fi.wrap));
+                        E = c_mul(E, fi.step);
+                    }
+                    const float gn = gain[c];
+                    y.x *= gn;
+                    y.y *= gn;
+                    Store<N, OUTK>::run(a, base + c * cs, ps, y);
                 }
             }
         }
@@ -255,21 +329,32 @@ struct Pass {
 template <int N, int OUTK, int P, bool DONE = (P >= Sched<N>::passes)>
 struct PassChain {
     __device__ __forceinline__ static void run(const FArgs& a, const FrameInfo* fi, float2* b0, float2* b1,
-                                               const int8_t* st, int p)
+                                               const int8_t* st, int p, const float2* tw, const float* gn)
     {
-        Pass<N, OUTK, P>::run(a, fi, b0, b1, st, p);
-        PassChain<N, OUTK, P + 1>::run(a, fi, b0, b1, st, p);
+        Pass<N, OUTK, P>::run(a, fi, b0, b1, st, p, tw, gn);
+        PassChain<N, OUTK, P + 1>::run(a, fi, b0, b1, st, p, tw, gn);
     }
 };
 template <int N, int OUTK, int P>
 struct PassChain<N, OUTK, P, true> {
-    __device__ __forceinline__ static void run(const FArgs&, const FrameInfo*, float2*, float2*, const int8_t*, int) {}
+    __device__ __forceinline__ static void run(const FArgs&, const FrameInfo*, float2*, float2*, const int8_t*, int,
+                                               const float2*, const float*)
+    {
+    }
 };
 
+// Twiddle and gain tables live in shared memory for N <= 1280 (global, L1-cached, above).
 template <int N>
-constexpr size_t fstep_smem()
+__host__ __device__ constexpr bool tables_in_smem()
 {
-    return 2 * sizeof(float2) * (size_t)Sched<N>::fb * (N + 1) + sizeof(FrameInfo) * Sched<N>::fb;
+    return N <= 1280;
+}
+
+template <int N>
+__host__ __device__ constexpr size_t fstep_smem()
+{
+    return 2 * sizeof(float2) * (size_t)Sched<N>::fb * (N + 1) + sizeof(FrameInfo) * Sched<N>::fb +
+           (tables_in_smem<N>() ? (sizeof(float2) + sizeof(float)) * N : 0);
 }
 
 template <int N, int OUTK>
@@ -283,6 +368,18 @@ __global__ void __launch_bounds__(kThreads) fstep_kernel(const FArgs a)
     float2* buf1 = buf0 + FB * ROW;
     FrameInfo* finfo = reinterpret_cast<FrameInfo*>(buf1 + FB * ROW);
     int8_t* stage = reinterpret_cast<int8_t*>(buf1);
+    const float2* tw = a.tw;
+    const float* gain = a.gain;
+    if (tables_in_smem<N>()) {
+        float2* tws = reinterpret_cast<float2*>(finfo + FB);
+        float* gns = reinterpret_cast<float*>(tws + N);
+        for (int i = threadIdx.x; i < N; i += kThreads) {
+            tws[i] = __ldg(&a.tw[i]);
+            gns[i] = __ldg(&a.gain[i]);
+        }
+        tw = tws;
+        gain = gns;
+    }
 
     const int p = blockIdx.y;
     const long long f0 = (long long)blockIdx.x * FB;
@@ -307,6 +404,13 @@ __global__ void __launch_bounds__(kThreads) fstep_kernel(const FArgs a)
             fi.d_hi = dh;
             fi.d_lo = (float)(d - (double)dh);
             fi.delay = 1;
+            constexpr int NBL = N / Sched<N>::radix[Sched<N>::passes - 1];
+            const double st = (double)NBL * d, wr = -(double)N * d;
+            float sn, cs;
+            sincospif(2.0f * (float)(st - rint(st)), &sn, &cs);
+            fi.step = make_float2(cs, sn);
+            sincospif(2.0f * (float)(wr - rint(wr)), &sn, &cs);
+            fi.wrap = make_float2(cs, sn);
         }
         finfo[f] = fi;
     }
@@ -331,7 +435,154 @@ __global__ void __launch_bounds__(kThreads) fstep_kernel(const FArgs a)
     }
     __syncthreads();
 
-    PassChain<N, OUTK, 0>::run(a, finfo, buf0, buf1, stage, p);
+    PassChain<N, OUTK, 0>::run(a, finfo, buf0, buf1, stage, p, tw, gain);
+}
+
+
+// -------------------------------------------------------------------------------------
+// Two-pass variant for N = 32 T (T = 1, 2, 4, 8, 16): pass 1 reads each frame's int8
+// samples straight from global memory, decimated by T (thread t of a frame takes samples
+// t, t + T, ...), and does a 32-point DFT in registers; pass 2 does radix-T butterflies
+// across those sub-transforms, with the twiddles W_N^{j r}, and its epilogue applies the
+// delay phasor and channel gain and stores.  Each pass-2 thread takes consecutive
+// butterflies j of one frame, so the phasor e^{2 pi i (phi0 + u d)} advances by fixed
+// ratios (j -> j+1: e^{2 pi i d}; output r -> r+1: e^{2 pi i 32 d}; past N/2:
+// e^{-2 pi i N d}) and only one sincospi is needed per thread and frame.
+template <int N>
+struct R32 {
+    static constexpr int T = N / 32;
+    static constexpr int FB = (N <= 256) ? 32 : 16;     // frames per CTA
+    static constexpr int NT = 128;                      // threads per CTA
+    static constexpr int ROW = N + 1;                   // padded float2 row per frame
+    static constexpr int JPT = 32 * FB / NT;            // pass-2 butterflies per thread
+};
+
+struct FrameR32 {
+    long long slot, k;
+    float phi0, d_hi, d_lo;
+    int delay;
+    float2 step1, step32, wrap;
+};
+
+template <int N>
+__host__ __device__ constexpr size_t r32_smem()
+{
+    return sizeof(float2) * (size_t)R32<N>::FB * R32<N>::ROW + sizeof(FrameR32) * R32<N>::FB +
+           (sizeof(float2) + sizeof(float)) * N;
+}
+
+template <int N, int OUTK>
+__global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
+{
+    using P = R32<N>;
+    constexpr int T = P::T, FB = P::FB, NT = P::NT, ROW = P::ROW;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* buf = reinterpret_cast<float2*>(smem);
+    FrameR32* finfo = reinterpret_cast<FrameR32*>(buf + FB * ROW);
+    float2* tw = reinterpret_cast<float2*>(finfo + FB);
+    float* gain = reinterpret_cast<float*>(tw + N);
+
+    const int p = blockIdx.y;
+    const long long f0 = (long long)blockIdx.x * FB;
+
+    for (int i = threadIdx.x; i < N; i += NT) {
+        tw[i] = __ldg(&a.tw[i]);
+        gain[i] = __ldg(&a.gain[i]);
+    }
+    if (threadIdx.x < FB) {
+        const int f = threadIdx.x;
+        const long long fl = f0 + f;
+        FrameR32 fi;
+        fi.slot = (fl < a.n_store) ? fl / a.Kc : -1;
+        fi.k = (fl < a.n_store) ? fl % a.Kc : 0;
+        fi.delay = 0;
+        fi.phi0 = fi.d_hi = fi.d_lo = 0.0f;
+        fi.step1 = fi.step32 = fi.wrap = make_float2(1.0f, 0.0f);
+        if (a.delay != nullptr && fl < a.n_frames) {
+            const double m = (double)(a.m_begin + fl);
+            const double t = (m + 0.5) * (double)N / kFs;
+            const double tau = a.delay[3 * p] + t * (a.delay[3 * p + 1] + t * a.delay[3 * p + 2]);
+            const double ph = a.nu * tau;
+            fi.phi0 = (float)(ph - floor(ph));
+            const double d = tau * kFs / (double)N;
+            const float dh = __uint_as_float(__float_as_uint((float)d) & 0xFFFFF000u);
+            fi.d_hi = dh;
+            fi.d_lo = (float)(d - (double)dh);
+            fi.delay = 1;
+            float sn, cs;
+            const double s1 = d, s32 = 32.0 * d, wr = -(double)N * d;
+            sincospif(2.0f * (float)(s1 - rint(s1)), &sn, &cs);
+            fi.step1 = make_float2(cs, sn);
+            sincospif(2.0f * (float)(s32 - rint(s32)), &sn, &cs);
+            fi.step32 = make_float2(cs, sn);
+            sincospif(2.0f * (float)(wr - rint(wr)), &sn, &cs);
+            fi.wrap = make_float2(cs, sn);
+        }
+        finfo[f] = fi;
+    }
+
+    // ---- pass 1: 32-point DFTs of the T decimated sub-sequences of each frame
+    for (int idx = threadIdx.x; idx < FB * T; idx += NT) {
+        const int t = idx % T, f = idx / T;
+        const long long fl = f0 + f;
+        float2 v[32];
+        if (fl < a.n_frames) {
+            const long long s = (a.m_begin + fl) * (long long)N;   // first sample of the frame
+            const long long blk = s / a.bs, off = s % a.bs;
+            const char2* src = reinterpret_cast<const char2*>(a.volt + ((blk * a.n + p) * (long long)a.bs + off) * 2);
+#pragma unroll
+            for (int m = 0; m < 32; ++m) {
+                const char2 x = __ldg(src + t + T * m);
+                v[m] = make_float2((float)x.x, (float)x.y);
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < 32; ++m) v[m] = make_float2(0.0f, 0.0f);
+        }
+        Dft<32>::run(v);
+        if (T == 1) {
+            // single pass: this is the final spectrum, handled below from shared memory
+        }
+#pragma unroll
+        for (int r = 0; r < 32; ++r) buf[f * ROW + 32 * t + r] = v[r];
+    }
+    __syncthreads();
+
+    // ---- pass 2: radix-T butterflies j = 0..31 of each frame, then phasor, gain, store
+    const int f = threadIdx.x % FB;
+    const int jb = (threadIdx.x / FB) * P::JPT;
+    const FrameR32 fi = finfo[f];
+    if (fi.slot < 0) return;
+    const long long cs = 2LL * a.n * a.Kpad;
+    const long long ps = (long long)a.n * a.Kpad;
+    const long long base = (fi.slot * N * 2LL * a.n + p) * a.Kpad + fi.k;
+    float2 Ej = make_float2(1.0f, 0.0f);
+    if (fi.delay) Ej = delay_phasor_u(fi.phi0, fi.d_hi, fi.d_lo, jb);
+#pragma unroll 2
+    for (int jj = 0; jj < P::JPT; ++jj) {
+        const int j = jb + jj;
+        float2 v[T];
+#pragma unroll
+        for (int r = 0; r < T; ++r) {
+            v[r] = buf[f * ROW + j + 32 * r];
+            if (r > 0) v[r] = c_mul(v[r], tw[j * r]);
+        }
+        DftIf<T>::run(v);
+        float2 E = Ej;
+#pragma unroll
+        for (int r = 0; r < T; ++r) {
+            const int k = j + 32 * r;   // natural-order bin
+            const int c = (k < N - N / 2) ? k + N / 2 : k - (N - N / 2);
+            float2 y = v[r];
+            if (fi.delay) {
+                y = c_mul(y, (k < N - N / 2) ? E : c_mul(E, fi.wrap));
+                E = c_mul(E, fi.step32);
+            }
+            const float gn = gain[c];
+            Store<N, OUTK>::run(a, base + c * cs, ps, make_float2(y.x * gn, y.y * gn));
+        }
+        if (fi.delay) Ej = c_mul(Ej, fi.step1);
+    }
 }
 
 // N = 1: no FFT.  One thread per (path, 4 samples); optional phasor e^{2 pi i nu tau}.
@@ -360,10 +611,9 @@ __global__ void __launch_bounds__(256) unpack_kernel(const FArgs a)
             sincospif(2.0f * (float)(ph - floor(ph)), &sn, &cs);
             v = c_mul(v, make_float2(cs, sn));
         }
-        FrameInfo fi;
-        fi.slot = fl / a.Kc;
-        fi.k = fl % a.Kc;
-        Store<1, OUTK>::run(a, fi, p, 0, v);
+        const float gn = __ldg(&a.gain[0]);
+        const long long at = ((fl / a.Kc) * 2LL * a.n + p) * a.Kpad + fl % a.Kc;
+        Store<1, OUTK>::run(a, at, (long long)a.n * a.Kpad, make_float2(v.x * gn, v.y * gn));
     }
 }
 
@@ -383,6 +633,22 @@ cudaError_t launch_n(const FArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <int N, int OUTK>
+cudaError_t launch_r32(const FArgs& a, cudaStream_t s)
+{
+    constexpr size_t smem = r32_smem<N>();
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(fstep_r32_kernel<N, OUTK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    dim3 grid((unsigned)((a.n_store + R32<N>::FB - 1) / R32<N>::FB), (unsigned)a.n);
+    fstep_r32_kernel<N, OUTK><<<grid, R32<N>::NT, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int OUTK>
 cudaError_t launch_kind(int N, const FArgs& a, cudaStream_t s)
 {
@@ -393,11 +659,11 @@ cudaError_t launch_kind(int N, const FArgs& a, cudaStream_t s)
             return cudaGetLastError();
         }
         case 16: return launch_n<16, OUTK>(a, s);
-        case 32: return launch_n<32, OUTK>(a, s);
-        case 64: return launch_n<64, OUTK>(a, s);
-        case 128: return launch_n<128, OUTK>(a, s);
-        case 256: return launch_n<256, OUTK>(a, s);
-        case 512: return launch_n<512, OUTK>(a, s);
+        case 32: return launch_r32<32, OUTK>(a, s);
+        case 64: return launch_r32<64, OUTK>(a, s);
+        case 128: return launch_r32<128, OUTK>(a, s);
+        case 256: return launch_r32<256, OUTK>(a, s);
+        case 512: return launch_r32<512, OUTK>(a, s);
         case 640: return launch_n<640, OUTK>(a, s);
         case 1280: return launch_n<1280, OUTK>(a, s);
         case 3200: return launch_n<3200, OUTK>(a, s);

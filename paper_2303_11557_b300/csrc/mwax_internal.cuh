@@ -18,17 +18,23 @@ constexpr int kKAlign = 128;             // frames per operand row are padded to
 // Output-type selector of the F-step.
 enum FOut : int { FOUT_F32 = 0, FOUT_F16 = 1, FOUT_AMAX = 2, FOUT_E4M3 = 3 };
 
-// Per ultrafine channel c: the (at most two) output channels it feeds and the
-// coefficient w_c / sum(w) of each (Sec. 2.6).  j = -1 marks an unused slot.
-struct BinCoef {
-    int ja, jb;
-    float ca, cb;
+// Channel averaging (Sec. 2.6) is split in two: the F-step multiplies ultrafine channel
+// c by gain[c] = sqrt(w_c) (w_c = 1, 1/2 for the end bins of an even fscrunch, 0 for an
+// excluded DC bin), so C'(c) = w_c C(c); the X-step then sums C' over a *group* of
+// consecutive channels that feed the same output channels, and adds coef * sum into
+// each of them, coef = 1 / sum(w) of that output channel.  j = -1 marks "none".
+struct Group {
+    int c0, c1;     // ultrafine channels [c0, c1) (zero-gain channels inside are skipped)
+    int ja, jb;     // output channels fed
+    float ca, cb;   // their 1 / sum(w)
+    int first_a;    // 1: the first group (in channel order) that feeds ja; it stores
+    int first_b;    //    instead of adding (same for jb)
 };
 
-// A run of consecutive output channels [j0, j1) handled by one X CTA, with the
-// ultrafine channel range [c0, c1) that feeds it.
+// A run of consecutive output channels [j0, j1) handled by one X CTA and the groups
+// [g0, g1) that feed it (groups shared with a neighbouring run add only to j in [j0, j1)).
 struct RunInfo {
-    int j0, j1, c0, c1;
+    int j0, j1, g0, g1;
 };
 
 // Arguments of one F-step launch: frames [m_begin, m_begin + n_frames) of the call,
@@ -40,6 +46,7 @@ struct FArgs {
     float* amax;          // FP8: [slot][N][n] per-path-per-channel max |re|,|im|
     const float* scale;   // FP8 quantise pass: [slot][N][n] scale s = amax / 448
     const float2* tw;     // e^{-2 pi i k / N}, k < N
+    const float* gain;    // [N] sqrt of each ultrafine channel's averaging weight
     long long m_begin;
     long long n_frames;   // frames with data
     long long n_store;    // frames stored (>= n_frames: the rest are written as zeros)
@@ -60,11 +67,15 @@ struct XArgs {
     long long Kpad;
     long long klen;        // valid frames per slot in this launch
     int n, T, N, M;
+    int n_groups;
     long long B;
-    const BinCoef* bins;
+    const Group* groups;
     const RunInfo* runs;
-    const int2* tiles;     // (row block, column block) of each triangle tile
+    const float* gain;     // [N]; channels with gain 0 are skipped
+    const int4* tiles;     // (p0, q0, column count, A rows inside the B window) per tile
     float post_scale;      // multiplies every product (undoes the FP16 pre-scale)
+    int first_store;       // 1: a channel's first group stores (output not yet written by an
+                           //    earlier frame chunk of the same integration); 0: all add
     int* status;           // device status word (bounded waits)
     unsigned int spin_limit;
 };
@@ -78,6 +89,7 @@ cudaError_t make_operand_tmap(CUtensorMap* map, const void* Y, int elem_bytes, l
                               long long planes);
 cudaError_t launch_xstep_tc(int op, const CUtensorMap& map, const XArgs& a, int n_tiles, int n_runs, int slots,
                             cudaStream_t s);
+int build_tc_tiles(int n, int4* out, int cap);
 bool fft_len_supported(int N);
 
 }  // namespace mwax

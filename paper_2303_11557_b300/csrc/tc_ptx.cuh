@@ -162,16 +162,16 @@ __device__ __forceinline__ void tmem_wait_ld()
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand tile written by TMA with 128-byte
-// swizzle (rows of 128 B, 8-row atoms of 1024 B stacked along M/N).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+// Shared-memory matrix descriptor of a K-major operand tile written by TMA with 64-byte
+// swizzle: rows of 64 B, 8-row atoms of 512 B stacked along M/N.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr)
 {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address, bits [0,14)
     d |= (uint64_t)1 << 16;                     // leading byte offset (unused for this layout)
-    d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset: next 8-row atom
+    d |= (uint64_t)(512 >> 4) << 32;            // stride byte offset: next 8-row atom
     d |= (uint64_t)1 << 46;                     // descriptor version for tcgen05
-    d |= (uint64_t)2 << 61;                     // swizzle: 128 B
+    d |= (uint64_t)4 << 61;                     // swizzle: 64 B
     return d;
 }
 

@@ -4,12 +4,13 @@
 //
 // CTA = one 64 x 64 tile of signal-path pairs (p rows, q columns; tiles on or above the
 // block diagonal only) x one run of output channels x one integration slot.  For every
-// ultrafine channel c feeding the run, the CTA forms
-//     C[p,q] = sum_k Y_p[k,c] conj(Y_q[k,c])
-// over the slot's frames with a 4 x 4 complex register tile per thread (two-level FP32
-// accumulation: a fresh partial per 32-frame chunk, added into the running total), and
-// adds coef * C into every output channel c feeds.  Each output element is owned by
-// exactly one CTA, so the read-modify-write needs no atomics.
+// group of ultrafine channels feeding the run, the CTA forms
+//     C[p,q] = sum_{c in group} sum_k Y_p[k,c] conj(Y_q[k,c])
+// (the F-step has already weighted channel c by sqrt(w_c)) with a 4 x 4 complex register
+// tile per thread (two-level FP32 accumulation: a fresh partial per 32-frame chunk, added
+// into the running total), and adds coef * C into every output channel the group feeds.
+// Each output element is owned by exactly one CTA, so the read-modify-write needs no
+// atomics.
 #include "mwax_internal.cuh"
 
 namespace mwax {
@@ -61,11 +62,11 @@ __global__ void __launch_bounds__(256, 2) xstep_simt_kernel(const XArgs a)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SimtSmem& sm = *reinterpret_cast<SimtSmem*>(smem_raw);
 
-    const int2 tile = a.tiles[blockIdx.x];
+    const int4 tile = a.tiles[blockIdx.x];
     const RunInfo run = a.runs[blockIdx.y];
     const long long slot = blockIdx.z;
-    const int p0 = tile.x * TP, q0 = tile.y * TP;
-    const bool diag = (tile.x == tile.y);
+    const int p0 = tile.x, q0 = tile.y;
+    const bool diag = (p0 == q0);
     const int tid = threadIdx.x;
     const int tx = tid % 16, ty = tid / 16;
 
@@ -76,15 +77,11 @@ __global__ void __launch_bounds__(256, 2) xstep_simt_kernel(const XArgs a)
     const int rows_a = min(TP, a.n - p0), rows_b = min(TP, a.n - q0);
     const float* Yf = static_cast<const float*>(a.Y);
 
-    for (int c = run.c0; c < run.c1; ++c) {
-        const BinCoef bc = a.bins[c];
-        const bool use_a = bc.ja >= run.j0 && bc.ja < run.j1;
-        const bool use_b = bc.jb >= run.j0 && bc.jb < run.j1;
+    for (int g = run.g0; g < run.g1; ++g) {
+        const Group gr = a.groups[g];
+        const bool use_a = gr.ja >= run.j0 && gr.ja < run.j1;
+        const bool use_b = gr.jb >= run.j0 && gr.jb < run.j1;
         if (!use_a && !use_b) continue;
-
-        const float* plane_base = Yf + ((slot * a.N + c) * 2) * (long long)a.n * a.Kpad;
-        const float* abase = plane_base + ((long long)lplane * a.n + p0) * a.Kpad;
-        const float* bbase = plane_base + ((long long)lplane * a.n + q0) * a.Kpad;
 
         float tre[4][4], tim[4][4];
 #pragma unroll
@@ -92,93 +89,97 @@ __global__ void __launch_bounds__(256, 2) xstep_simt_kernel(const XArgs a)
 #pragma unroll
             for (int j = 0; j < 4; ++j) tre[i][j] = tim[i][j] = 0.f;
 
-        const long long nchunks = (a.klen + KT - 1) / KT;
-        float4 ra[4], rb[4];
-        load_block(abase, a.Kpad, rows_a, lrow, lk, a.klen, ra);
-        if (!diag) load_block(bbase, a.Kpad, rows_b, lrow, lk, a.klen, rb);
-        __syncthreads();   // previous bin's readers are done with both buffers
-        store_block(sm.a[0][lplane], lrow, lk, ra);
-        if (!diag) store_block(sm.b[0][lplane], lrow, lk, rb);
-        __syncthreads();
+        for (int c = gr.c0; c < gr.c1; ++c) {
+            if (__ldg(&a.gain[c]) == 0.0f) continue;
+            const float* plane_base = Yf + ((slot * a.N + c) * 2) * (long long)a.n * a.Kpad;
+            const float* abase = plane_base + ((long long)lplane * a.n + p0) * a.Kpad;
+            const float* bbase = plane_base + ((long long)lplane * a.n + q0) * a.Kpad;
 
-        for (long long ch = 0; ch < nchunks; ++ch) {
-            const int cur = (int)(ch & 1);
-            const bool more = ch + 1 < nchunks;
-            if (more) {
-                const long long k0 = (ch + 1) * KT + lk;
-                load_block(abase, a.Kpad, rows_a, lrow, k0, a.klen, ra);
-                if (!diag) load_block(bbase, a.Kpad, rows_b, lrow, k0, a.klen, rb);
-            }
-            const float(*Ar)[LDA] = sm.a[cur][0];
-            const float(*Ai)[LDA] = sm.a[cur][1];
-            const float(*Br)[LDA] = diag ? sm.a[cur][0] : sm.b[cur][0];
-            const float(*Bi)[LDA] = diag ? sm.a[cur][1] : sm.b[cur][1];
-            float pre[4][4], pim[4][4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) pre[i][j] = pim[i][j] = 0.f;
-#pragma unroll 8
-            for (int k = 0; k < KT; ++k) {
-                const float4 ar = *reinterpret_cast<const float4*>(&Ar[k][ty * 4]);
-                const float4 ai = *reinterpret_cast<const float4*>(&Ai[k][ty * 4]);
-                const float4 br = *reinterpret_cast<const float4*>(&Br[k][tx * 4]);
-                const float4 bi = *reinterpret_cast<const float4*>(&Bi[k][tx * 4]);
-                const float xr[4] = {ar.x, ar.y, ar.z, ar.w}, xi[4] = {ai.x, ai.y, ai.z, ai.w};
-                const float yr[4] = {br.x, br.y, br.z, br.w}, yi[4] = {bi.x, bi.y, bi.z, bi.w};
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        // (xr + i xi)(yr - i yi)
-                        pre[i][j] = fmaf(xr[i], yr[j], pre[i][j]);
-                        pre[i][j] = fmaf(xi[i], yi[j], pre[i][j]);
-                        pim[i][j] = fmaf(xi[i], yr[j], pim[i][j]);
-                        pim[i][j] = fmaf(-xr[i], yi[j], pim[i][j]);
-                    }
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    tre[i][j] += pre[i][j];
-                    tim[i][j] += pim[i][j];
-                }
-            if (more) {
-                store_block(sm.a[cur ^ 1][lplane], lrow, lk, ra);
-                if (!diag) store_block(sm.b[cur ^ 1][lplane], lrow, lk, rb);
-            }
+            const long long nchunks = (a.klen + KT - 1) / KT;
+            float4 ra[4], rb[4];
+            load_block(abase, a.Kpad, rows_a, lrow, lk, a.klen, ra);
+            if (!diag) load_block(bbase, a.Kpad, rows_b, lrow, lk, a.klen, rb);
+            __syncthreads();   // previous channel's readers are done with both buffers
+            store_block(sm.a[0][lplane], lrow, lk, ra);
+            if (!diag) store_block(sm.b[0][lplane], lrow, lk, rb);
             __syncthreads();
-        }
 
-        // Epilogue: add coef * C into MWAX_ORDER output of every channel this bin feeds.
+            for (long long ch = 0; ch < nchunks; ++ch) {
+                const int cur = (int)(ch & 1);
+                const bool more = ch + 1 < nchunks;
+                if (more) {
+                    const long long k0 = (ch + 1) * KT + lk;
+                    load_block(abase, a.Kpad, rows_a, lrow, k0, a.klen, ra);
+                    if (!diag) load_block(bbase, a.Kpad, rows_b, lrow, k0, a.klen, rb);
+                }
+                const float(*Ar)[LDA] = sm.a[cur][0];
+                const float(*Ai)[LDA] = sm.a[cur][1];
+                const float(*Br)[LDA] = diag ? sm.a[cur][0] : sm.b[cur][0];
+                const float(*Bi)[LDA] = diag ? sm.a[cur][1] : sm.b[cur][1];
+                float pre[4][4], pim[4][4];
+    #pragma unroll
+                for (int i = 0; i < 4; ++i)
+    #pragma unroll
+                    for (int j = 0; j < 4; ++j) pre[i][j] = pim[i][j] = 0.f;
+    #pragma unroll 8
+                for (int k = 0; k < KT; ++k) {
+                    const float4 ar = *reinterpret_cast<const float4*>(&Ar[k][ty * 4]);
+                    const float4 ai = *reinterpret_cast<const float4*>(&Ai[k][ty * 4]);
+                    const float4 br = *reinterpret_cast<const float4*>(&Br[k][tx * 4]);
+                    const float4 bi = *reinterpret_cast<const float4*>(&Bi[k][tx * 4]);
+                    const float xr[4] = {ar.x, ar.y, ar.z, ar.w}, xi[4] = {ai.x, ai.y, ai.z, ai.w};
+                    const float yr[4] = {br.x, br.y, br.z, br.w}, yi[4] = {bi.x, bi.y, bi.z, bi.w};
+    #pragma unroll
+                    for (int i = 0; i < 4; ++i)
+    #pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            // (xr + i xi)(yr - i yi)
+                            pre[i][j] = fmaf(xr[i], yr[j], pre[i][j]);
+                            pre[i][j] = fmaf(xi[i], yi[j], pre[i][j]);
+                            pim[i][j] = fmaf(xi[i], yr[j], pim[i][j]);
+                            pim[i][j] = fmaf(-xr[i], yi[j], pim[i][j]);
+                        }
+                }
+    #pragma unroll
+                for (int i = 0; i < 4; ++i)
+    #pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        tre[i][j] += pre[i][j];
+                        tim[i][j] += pim[i][j];
+                    }
+                if (more) {
+                    store_block(sm.a[cur ^ 1][lplane], lrow, lk, ra);
+                    if (!diag) store_block(sm.b[cur ^ 1][lplane], lrow, lk, rb);
+                }
+                __syncthreads();
+            }
+        }   // channels of the group
+
+        // Epilogue: add coef * C into MWAX_ORDER output of every channel the group feeds
+        // (the first group feeding a channel stores; a row's loads precede its stores).
+        float2* ob = reinterpret_cast<float2*>(a.out + slot * a.out_stride);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int p = p0 + ty * 4 + i;
-            if (p >= a.n) continue;
+            int off[4];
+            float2 va[4], vb[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int q = q0 + tx * 4 + j;
-                if (q >= a.n) continue;
-                const int ti = p >> 1, tj = q >> 1;
-                if (ti > tj) continue;   // lower triangle of the baseline matrix: not emitted
+                const bool ok = p < a.n && q < a.n && (p >> 1) <= (q >> 1);
                 const int pol = ((p & 1) << 1) | (q & 1);
-                const long long b = baseline_of(ti, tj, a.T);
+                off[j] = ok ? (int)(baseline_of(p >> 1, q >> 1, a.T) * a.M * 4 + pol) : -1;
+                va[j] = (ok && use_a && !(gr.first_a & a.first_store)) ? ob[off[j] + gr.ja * 4] : make_float2(0.f, 0.f);
+                vb[j] = (ok && use_b && !(gr.first_b & a.first_store)) ? ob[off[j] + gr.jb * 4] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (off[j] < 0) continue;
+                const int q = q0 + tx * 4 + j;
                 const float vr = tre[i][j] * a.post_scale;
                 const float vi = (p == q) ? 0.0f : tim[i][j] * a.post_scale;   // autos are real
-                float2* o = reinterpret_cast<float2*>(a.out + slot * a.out_stride) + (b * a.M) * 4 + pol;
-                if (use_a) {
-                    float2 cur = o[(long long)bc.ja * 4];
-                    cur.x = fmaf(bc.ca, vr, cur.x);
-                    cur.y = fmaf(bc.ca, vi, cur.y);
-                    o[(long long)bc.ja * 4] = cur;
-                }
-                if (use_b) {
-                    float2 cur = o[(long long)bc.jb * 4];
-                    cur.x = fmaf(bc.cb, vr, cur.x);
-                    cur.y = fmaf(bc.cb, vi, cur.y);
-                    o[(long long)bc.jb * 4] = cur;
-                }
+                if (use_a) ob[off[j] + gr.ja * 4] = make_float2(fmaf(gr.ca, vr, va[j].x), fmaf(gr.ca, vi, va[j].y));
+                if (use_b) ob[off[j] + gr.jb * 4] = make_float2(fmaf(gr.cb, vr, vb[j].x), fmaf(gr.cb, vi, vb[j].y));
             }
         }
     }

@@ -6,13 +6,19 @@
 // The complex product C = Y_p conj(Y_q) is four real MMAs on planar operands:
 //     Re C = Ar Br^T + Ai Bi^T,      Im C = Ai Br^T - Ar Bi^T
 // (the last with the instruction's A-negate bit).  Operands are K-major planes
-// Y[slot][c][plane][p][Kpad] loaded by TMA with 128-byte swizzle.
+// Y[slot][c][plane][p][Kpad] loaded by TMA with 64-byte swizzle.
 //
-// CTA = one 128 x 128 tile of path pairs x one run of output channels x one slot;
-// 6 warps: warp 0 issues TMA loads into a 3-stage ring, warp 1 owns TMEM and issues
-// the MMAs from one thread, warps 2-5 drain the accumulators (one TMEM lane = one path
-// p per thread).  Each ultrafine bin accumulates into one of two TMEM buffers (Re and
-// Im, 128 columns each), so the epilogue of bin c overlaps the MMAs of bin c+1.
+// CTA = one tile x one run of output channels x one slot.  A tile is 128 rows (paths p)
+// by a window of 256 (or, at the right edge, 128) columns (paths q).  Windows start at
+// the tile's own diagonal, so for those the 128 A rows are the first 128 rows of the B
+// window and only B is loaded; elsewhere A and B are loaded separately.  For each group of
+// ultrafine channels (pre-weighted by sqrt(w) in the F-step) the MMAs of every frame of
+// every channel in the group accumulate into one TMEM accumulator pair (Re: columns
+// [0, 256), Im: [256, 512)), which the epilogue drains once per group.
+//
+// 10 warps: warp 0 issues TMA loads into a 4-stage ring, warp 1 owns TMEM and issues the
+// MMAs from one thread, warps 2-9 drain the accumulators (TMEM lane quarter = warp % 4,
+// column half = (warp - 2) / 4; one TMEM lane = one path p).
 #include "mwax_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -21,19 +27,22 @@
 namespace mwax {
 namespace {
 
-constexpr int TM = 128;           // paths per tile side
-constexpr int STAGES = 3;
-constexpr int ROWB = 128;         // bytes per operand row in a stage (one swizzle row)
-constexpr int PLANE_BYTES = TM * ROWB;   // 16 KB
-constexpr int STAGE_BYTES = 4 * PLANE_BYTES;
-constexpr int NTHREADS = 192;
+constexpr int TM = 128;                        // rows (paths p) per tile
+constexpr int TNMAX = 256;                     // columns (paths q) per tile
+constexpr int STAGES = 4;
+constexpr int ROWB = 64;                       // bytes of K per operand row in a stage
+constexpr int A_PLANE = TM * ROWB;             // 8 KB
+constexpr int B_PLANE = TNMAX * ROWB;          // 16 KB
+constexpr int STAGE_BYTES = 2 * B_PLANE + 2 * A_PLANE;   // 48 KB: Br, Bi, Ar, Ai
+constexpr int NTHREADS = 320;
+constexpr int EPI_THREADS = 256;
 constexpr uint32_t TMEM_COLS = 512;
 
 struct TcSmem {
     uint64_t full[STAGES];
     uint64_t empty[STAGES];
-    uint64_t acc_full[2];
-    uint64_t acc_empty[2];
+    uint64_t acc_full;
+    uint64_t acc_empty;
     uint32_t tmem_base;
     int abort;
 };
@@ -48,25 +57,21 @@ template <int OP>
 __global__ void __launch_bounds__(NTHREADS, 1) xstep_tc_kernel(const __grid_constant__ CUtensorMap tmap, const XArgs a)
 {
     constexpr int ELEM = (OP == 0) ? 2 : 1;
-    constexpr int KB = ROWB / ELEM;           // frames per stage
-    constexpr int KSTEP = 32 / ELEM;          // frames per MMA (32 bytes of K)
-    constexpr int NSTEPS = KB / KSTEP;        // MMAs per plane pair per stage (4)
-    constexpr uint32_t ID = tc::idesc(0, TM, TM, false);
-    constexpr uint32_t ID_NEG = tc::idesc(0, TM, TM, true);
+    constexpr int KF = ROWB / ELEM;           // frames per stage
+    constexpr int NSTEPS = ROWB / 32;         // MMA K-steps (32 bytes of K) per stage
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    // operand ring at a 1024-byte aligned offset, control block after it
     unsigned char* ring = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     TcSmem& S = *reinterpret_cast<TcSmem*>(ring + STAGES * STAGE_BYTES);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int2 tile = a.tiles[blockIdx.x];
+    const int4 tile = a.tiles[blockIdx.x];
     const RunInfo run = a.runs[blockIdx.y];
     const int slot = blockIdx.z;
-    const int p0 = tile.x * TM, q0 = tile.y * TM;
-    const bool diag = tile.x == tile.y;
-    const int nkb = (int)((a.klen + KB - 1) / KB);
+    const int p0 = tile.x, q0 = tile.y, nq = tile.z;
+    const bool a_in_b = tile.w != 0;
+    const int nkb = (int)((a.klen + KF - 1) / KF);
     const long long lim = (long long)a.spin_limit * 1000LL;   // cycles
 
     if (threadIdx.x == 0) {
@@ -74,10 +79,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) xstep_tc_kernel(const __grid_cons
             tc::mbar_init(&S.full[s], 1);
             tc::mbar_init(&S.empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
-            tc::mbar_init(&S.acc_full[b], 1);
-            tc::mbar_init(&S.acc_empty[b], 128);
-        }
+        tc::mbar_init(&S.acc_full, 1);
+        tc::mbar_init(&S.acc_empty, EPI_THREADS);
         S.abort = 0;
         tc::fence_mbar_init();
         tc::prefetch_tmap(&tmap);
@@ -99,25 +102,31 @@ __global__ void __launch_bounds__(NTHREADS, 1) xstep_tc_kernel(const __grid_cons
             uint32_t phase = 0;
             int issued_phase[STAGES];
             for (int s = 0; s < STAGES; ++s) issued_phase[s] = -1;
-            const uint32_t bytes = diag ? 2 * PLANE_BYTES : 4 * PLANE_BYTES;
-            for (int c = run.c0; c < run.c1 && !*abort; ++c) {
-                const BinCoef bc = a.bins[c];
-                if (!((bc.ja >= run.j0 && bc.ja < run.j1) || (bc.jb >= run.j0 && bc.jb < run.j1))) continue;
-                const int zr = (slot * a.N + c) * 2, zi = zr + 1;
-                for (int kb = 0; kb < nkb; ++kb) {
-                    if (!tc::mbar_wait(&S.empty[stage], phase ^ 1, abort, a.status, 2, lim)) break;
-                    unsigned char* st = ring + stage * STAGE_BYTES;
-                    tc::mbar_arrive_expect_tx(&S.full[stage], bytes);
-                    tc::tma_load_3d(st, &tmap, &S.full[stage], kb * KB, p0, zr);
-                    tc::tma_load_3d(st + PLANE_BYTES, &tmap, &S.full[stage], kb * KB, p0, zi);
-                    if (!diag) {
-                        tc::tma_load_3d(st + 2 * PLANE_BYTES, &tmap, &S.full[stage], kb * KB, q0, zr);
-                        tc::tma_load_3d(st + 3 * PLANE_BYTES, &tmap, &S.full[stage], kb * KB, q0, zi);
-                    }
-                    issued_phase[stage] = (int)phase;
-                    if (++stage == STAGES) {
-                        stage = 0;
-                        phase ^= 1;
+            const int nbox = nq / TM;   // 128-row boxes of the B window
+            const uint32_t bytes = (uint32_t)(2 * nbox * A_PLANE + (a_in_b ? 0 : 2 * A_PLANE));
+            for (int g = run.g0; g < run.g1 && !*abort; ++g) {
+                const Group gr = a.groups[g];
+                for (int c = gr.c0; c < gr.c1 && !*abort; ++c) {
+                    if (__ldg(&a.gain[c]) == 0.0f) continue;
+                    const int zr = (slot * a.N + c) * 2, zi = zr + 1;
+                    for (int kb = 0; kb < nkb; ++kb) {
+                        if (!tc::mbar_wait(&S.empty[stage], phase ^ 1, abort, a.status, 2, lim)) break;
+                        unsigned char* st = ring + stage * STAGE_BYTES;
+                        uint64_t* fb = &S.full[stage];
+                        tc::mbar_arrive_expect_tx(fb, bytes);
+                        for (int b = 0; b < nbox; ++b) {
+                            tc::tma_load_3d(st + b * A_PLANE, &tmap, fb, kb * KF, q0 + b * TM, zr);
+                            tc::tma_load_3d(st + B_PLANE + b * A_PLANE, &tmap, fb, kb * KF, q0 + b * TM, zi);
+                        }
+                        if (!a_in_b) {
+                            tc::tma_load_3d(st + 2 * B_PLANE, &tmap, fb, kb * KF, p0, zr);
+                            tc::tma_load_3d(st + 2 * B_PLANE + A_PLANE, &tmap, fb, kb * KF, p0, zi);
+                        }
+                        issued_phase[stage] = (int)phase;
+                        if (++stage == STAGES) {
+                            stage = 0;
+                            phase ^= 1;
+                        }
                     }
                 }
             }
@@ -134,129 +143,132 @@ __global__ void __launch_bounds__(NTHREADS, 1) xstep_tc_kernel(const __grid_cons
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
+            const uint32_t id = tc::idesc(0, TM, nq, false), id_neg = tc::idesc(0, TM, nq, true);
             int stage = 0;
-            uint32_t phase = 0;
-            int buf = 0;
-            uint32_t aphase = 0;
+            uint32_t phase = 0, gphase = 0;
             const uint32_t sbase = tc::smem_u32(ring);
             bool issued = false;
-            for (int c = run.c0; c < run.c1 && !*abort; ++c) {
-                const BinCoef bc = a.bins[c];
-                if (!((bc.ja >= run.j0 && bc.ja < run.j1) || (bc.jb >= run.j0 && bc.jb < run.j1))) continue;
-                if (!tc::mbar_wait(&S.acc_empty[buf], aphase ^ 1, abort, a.status, 4, lim)) break;
+            const uint32_t d_re = tmem, d_im = tmem + 256;
+            for (int g = run.g0; g < run.g1 && !*abort; ++g) {
+                const Group gr = a.groups[g];
+                if (!tc::mbar_wait(&S.acc_empty, gphase ^ 1, abort, a.status, 4, lim)) break;
                 tc::fence_after();
-                const uint32_t d_re = tmem + buf * 256, d_im = d_re + 128;
-                for (int kb = 0; kb < nkb; ++kb) {
-                    if (!tc::mbar_wait(&S.full[stage], phase, abort, a.status, 8, lim)) break;
-                    tc::fence_after();
-                    const uint32_t st = sbase + stage * STAGE_BYTES;
-                    const uint64_t dar = tc::sw128_desc(st), dai = tc::sw128_desc(st + PLANE_BYTES);
-                    const uint64_t dbr = diag ? dar : tc::sw128_desc(st + 2 * PLANE_BYTES);
-                    const uint64_t dbi = diag ? dai : tc::sw128_desc(st + 3 * PLANE_BYTES);
+                bool first = true;
+                for (int c = gr.c0; c < gr.c1 && !*abort; ++c) {
+                    if (__ldg(&a.gain[c]) == 0.0f) continue;
+                    for (int kb = 0; kb < nkb; ++kb) {
+                        if (!tc::mbar_wait(&S.full[stage], phase, abort, a.status, 8, lim)) break;
+                        tc::fence_after();
+                        const uint32_t st = sbase + stage * STAGE_BYTES;
+                        const uint64_t dbr = tc::sw64_desc(st), dbi = tc::sw64_desc(st + B_PLANE);
+                        const uint64_t dar = a_in_b ? dbr : tc::sw64_desc(st + 2 * B_PLANE);
+                        const uint64_t dai = a_in_b ? dbi : tc::sw64_desc(st + 2 * B_PLANE + A_PLANE);
 #pragma unroll
-                    for (int k = 0; k < NSTEPS; ++k) {
-                        const uint64_t off = (uint64_t)(k * 32) >> 4;   // 32 bytes of K per step
-                        const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
-                        if (OP == 0) {
-                            tc::mma_f16(d_re, dar + off, dbr + off, ID, acc);
-                            tc::mma_f16(d_re, dai + off, dbi + off, ID, 1u);
-                            tc::mma_f16(d_im, dai + off, dbr + off, ID, acc);
-                            tc::mma_f16(d_im, dar + off, dbi + off, ID_NEG, 1u);
-                        } else {
-                            tc::mma_f8(d_re, dar + off, dbr + off, ID, acc);
-                            tc::mma_f8(d_re, dai + off, dbi + off, ID, 1u);
-                            tc::mma_f8(d_im, dai + off, dbr + off, ID, acc);
-                            tc::mma_f8(d_im, dar + off, dbi + off, ID_NEG, 1u);
+                        for (int k = 0; k < NSTEPS; ++k) {
+                            const uint64_t off = (uint64_t)(k * 32) >> 4;   // 32 bytes of K per step
+                            const uint32_t acc = first ? 0u : 1u;
+                            first = false;
+                            if (OP == 0) {
+                                tc::mma_f16(d_re, dar + off, dbr + off, id, acc);
+                                tc::mma_f16(d_re, dai + off, dbi + off, id, 1u);
+                                tc::mma_f16(d_im, dai + off, dbr + off, id, acc);
+                                tc::mma_f16(d_im, dar + off, dbi + off, id_neg, 1u);
+                            } else {
+                                tc::mma_f8(d_re, dar + off, dbr + off, id, acc);
+                                tc::mma_f8(d_re, dai + off, dbi + off, id, 1u);
+                                tc::mma_f8(d_im, dai + off, dbr + off, id, acc);
+                                tc::mma_f8(d_im, dar + off, dbi + off, id_neg, 1u);
+                            }
                         }
-                    }
-                    issued = true;
-                    tc::mma_commit(&S.empty[stage]);
-                    if (++stage == STAGES) {
-                        stage = 0;
-                        phase ^= 1;
+                        issued = true;
+                        tc::mma_commit(&S.empty[stage]);
+                        if (++stage == STAGES) {
+                            stage = 0;
+                            phase ^= 1;
+                        }
                     }
                 }
                 if (*abort) break;
-                tc::mma_commit(&S.acc_full[buf]);
-                if (++buf == 2) {
-                    buf = 0;
-                    aphase ^= 1;
-                }
+                tc::mma_commit(&S.acc_full);
+                gphase ^= 1;
             }
             if (*abort && issued) {
                 // wait for the MMAs in flight before TMEM is released
-                uint64_t* done = &S.acc_full[buf];
-                tc::mma_commit(done);
+                tc::mma_commit(&S.acc_full);
                 const long long t0 = clock64();
-                while (!tc::mbar_try_wait(done, aphase) && clock64() - t0 < lim) {
+                while (!tc::mbar_try_wait(&S.acc_full, gphase) && clock64() - t0 < lim) {
                 }
             }
         }
     } else {
         // ------------------------------------------------------------ epilogue
-        const int g = warp & 3;                  // TMEM lane quarter of this warp
-        const int row = g * 32 + lane;
-        const int p = p0 + row;
-        int buf = 0;
-        uint32_t aphase = 0;
-        for (int c = run.c0; c < run.c1 && !*abort; ++c) {
-            const BinCoef bc = a.bins[c];
-            const bool use_a = bc.ja >= run.j0 && bc.ja < run.j1;
-            const bool use_b = bc.jb >= run.j0 && bc.jb < run.j1;
-            if (!use_a && !use_b) continue;
-            bool ok = tc::mbar_wait(&S.acc_full[buf], aphase, abort, a.status, 16, lim);
+        const int g4 = warp & 3;                 // TMEM lane quarter of this warp
+        const int half = (warp - 2) >> 2;        // column half of the window
+        const int p = p0 + g4 * 32 + lane;
+        const int ti = p >> 1;
+        const bool cols = half * 128 < nq;
+        uint32_t gphase = 0;
+        char* obase = a.out + (long long)slot * a.out_stride;
+        for (int g = run.g0; g < run.g1 && !*abort; ++g) {
+            const Group gr = a.groups[g];
+            const bool use_a = gr.ja >= run.j0 && gr.ja < run.j1;
+            const bool use_b = gr.jb >= run.j0 && gr.jb < run.j1;
+            bool ok = tc::mbar_wait(&S.acc_full, gphase, abort, a.status, 16, lim);
             if (!__all_sync(0xffffffffu, ok)) break;   // keep the warp's TMEM loads uniform
             tc::fence_after();
-            float sp = a.post_scale;
-            const float* qscale = nullptr;
-            if (OP == 1) {
-                const float* sc = a.scale + ((long long)slot * a.N + c) * a.n;
-                sp *= (p < a.n) ? __ldg(sc + p) : 0.0f;
-                qscale = sc;
-            }
-            const int ti = p >> 1;
-            char* obase = a.out + (long long)slot * a.out_stride;
+            if (cols) {
+                float sp = a.post_scale;
+                const float* qscale = nullptr;
+                if (OP == 1) {
+                    const float* sc = a.scale + ((long long)slot * a.n_groups + g) * a.n;
+                    sp *= (p < a.n) ? __ldg(sc + p) : 0.0f;
+                    qscale = sc;
+                }
 #pragma unroll 1
-            for (int ch = 0; ch < TM / 32; ++ch) {
-                uint32_t vr[32], vi[32];
-                const uint32_t taddr = tmem + ((uint32_t)(g * 32) << 16) + buf * 256 + ch * 32;
-                tc::tmem_ld32(taddr, vr);
-                tc::tmem_ld32(taddr + 128, vi);
-                tc::tmem_wait_ld();
-                if (p >= a.n) continue;
+                for (int ch = 0; ch < 4; ++ch) {
+                    const int col = half * 128 + ch * 32;
+                    uint32_t vr[32], vi[32];
+                    const uint32_t taddr = tmem + ((uint32_t)(g4 * 32) << 16) + col;
+                    tc::tmem_ld32(taddr, vr);
+                    tc::tmem_ld32(taddr + 256, vi);
+                    tc::tmem_wait_ld();
+                    if (p >= a.n) continue;
+                    // 8 columns at a time: issue every load of the old values before any
+                    // store, so the read-modify-writes overlap instead of serialising
+                    float2* ob = reinterpret_cast<float2*>(obase);
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const int q = q0 + ch * 32 + i;
-                    const int tj = q >> 1;
-                    if (q < a.n && ti <= tj) {
-                        float s = sp;
-                        if (OP == 1) s *= __ldg(qscale + q);
-                        const float re = __uint_as_float(vr[i]) * s;
-                        const float im = (p == q) ? 0.0f : __uint_as_float(vi[i]) * s;
-                        const int pol = ((p & 1) << 1) | (q & 1);
-                        float2* o =
-                            reinterpret_cast<float2*>(obase) + (baseline_of(ti, tj, a.T) * a.M) * 4 + pol;
-                        if (use_a) {
-                            float2 cur = o[(long long)bc.ja * 4];
-                            cur.x = fmaf(bc.ca, re, cur.x);
-                            cur.y = fmaf(bc.ca, im, cur.y);
-                            o[(long long)bc.ja * 4] = cur;
+                    for (int h = 0; h < 4; ++h) {
+                        int off[8];
+                        float2 va[8], vb[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int q = q0 + col + h * 8 + i;
+                            const int tj = q >> 1;
+                            const bool ok = q < a.n && ti <= tj;
+                            const int pol = ((p & 1) << 1) | (q & 1);
+                            off[i] = ok ? (int)(baseline_of(ti, tj, a.T) * a.M * 4 + pol) : -1;
+                            va[i] = (ok && use_a && !(gr.first_a & a.first_store)) ? ob[off[i] + gr.ja * 4] : make_float2(0.f, 0.f);
+                            vb[i] = (ok && use_b && !(gr.first_b & a.first_store)) ? ob[off[i] + gr.jb * 4] : make_float2(0.f, 0.f);
                         }
-                        if (use_b) {
-                            float2 cur = o[(long long)bc.jb * 4];
-                            cur.x = fmaf(bc.cb, re, cur.x);
-                            cur.y = fmaf(bc.cb, im, cur.y);
-                            o[(long long)bc.jb * 4] = cur;
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            if (off[i] < 0) continue;
+                            const int q = q0 + col + h * 8 + i;
+                            float s = sp;
+                            if (OP == 1) s *= __ldg(qscale + q);
+                            const float re = __uint_as_float(vr[h * 8 + i]) * s;
+                            const float im = (p == q) ? 0.0f : __uint_as_float(vi[h * 8 + i]) * s;
+                            if (use_a)
+                                ob[off[i] + gr.ja * 4] = make_float2(fmaf(gr.ca, re, va[i].x), fmaf(gr.ca, im, va[i].y));
+                            if (use_b)
+                                ob[off[i] + gr.jb * 4] = make_float2(fmaf(gr.cb, re, vb[i].x), fmaf(gr.cb, im, vb[i].y));
                         }
                     }
                 }
             }
             tc::fence_before();
-            tc::mbar_arrive(&S.acc_empty[buf]);
-            if (++buf == 2) {
-                buf = 0;
-                aphase ^= 1;
-            }
+            tc::mbar_arrive(&S.acc_empty);
+            gphase ^= 1;
         }
     }
 
@@ -286,8 +298,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 
 }  // namespace
 
-// Tensor map over the operand planes: dims (Kpad, n, slots * N * 2), box (128 B of K,
-// 128 rows, 1 plane), 128-byte swizzle, zero fill outside the rows / frames.
+// Tensor map over the operand planes: dims (Kpad, n, slots * N * 2), box (64 B of K,
+// 128 rows, 1 plane), 64-byte swizzle, zero fill outside the rows / frames.
 cudaError_t make_operand_tmap(CUtensorMap* map, const void* Y, int elem_bytes, long long Kpad, int n,
                               long long planes)
 {
@@ -299,7 +311,7 @@ cudaError_t make_operand_tmap(CUtensorMap* map, const void* Y, int elem_bytes, l
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(map, elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 3,
                     const_cast<void*>(Y), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
@@ -327,6 +339,21 @@ cudaError_t launch_xstep_tc(int op, const CUtensorMap& map, const XArgs& a, int 
         xstep_tc_kernel<1><<<grid, NTHREADS, smem, s>>>(map, a);
     }
     return cudaGetLastError();
+}
+
+// Tile list of the tensor-core X-step: for each 128-row block, column windows of 256
+// starting at its own diagonal (the last window of a row may be 128 wide).
+int build_tc_tiles(int n, int4* out, int cap)
+{
+    int k = 0;
+    for (int p0 = 0; p0 < n; p0 += TM) {
+        for (int q0 = p0; q0 < n; q0 += TNMAX) {
+            const int nq = (n - q0 > TM) ? TNMAX : TM;
+            if (k < cap) out[k] = make_int4(p0, q0, nq, q0 == p0 ? 1 : 0);
+            ++k;
+        }
+    }
+    return k;
 }
 
 }  // namespace mwax

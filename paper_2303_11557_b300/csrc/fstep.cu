@@ -453,8 +453,12 @@ struct R32 {
     static constexpr int T = N / 32;
     static constexpr int FB = (N <= 256) ? 32 : 16;     // frames per CTA
     static constexpr int NT = 128;                      // threads per CTA
-    static constexpr int ROW = N + 1;                   // padded float2 row per frame
     static constexpr int JPT = 32 * FB / NT;            // pass-2 butterflies per thread
+    // Shared-memory strides chosen for conflict-free access by both passes: pass 1 (lanes
+    // = T sub-sequences x 32/T frames) writes row f, sub-row t; pass 2 (lanes = frames)
+    // reads across sub-rows.  SR = 32 + 16/T (mod 16 == 16/T), ROW = 1 (mod 16).
+    static constexpr int SR = (T == 1) ? 32 : 32 + 16 / T;
+    static constexpr int ROW = (T == 1) ? 33 : T * SR + 1;
 };
 
 struct FrameR32 {
@@ -475,7 +479,7 @@ template <int N, int OUTK>
 __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
 {
     using P = R32<N>;
-    constexpr int T = P::T, FB = P::FB, NT = P::NT, ROW = P::ROW;
+    constexpr int T = P::T, FB = P::FB, NT = P::NT, ROW = P::ROW, SR = P::SR;
     extern __shared__ __align__(16) unsigned char smem[];
     float2* buf = reinterpret_cast<float2*>(smem);
     FrameR32* finfo = reinterpret_cast<FrameR32*>(buf + FB * ROW);
@@ -527,8 +531,8 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
         const long long fl = f0 + f;
         float2 v[32];
         if (fl < a.n_frames) {
-            const long long s = (a.m_begin + fl) * (long long)N;   // first sample of the frame
-            const long long blk = s / a.bs, off = s % a.bs;
+            const long long s0 = (a.m_begin + fl) * (long long)N;   // first sample of the frame
+            const long long blk = s0 / a.bs, off = s0 % a.bs;
             const char2* src = reinterpret_cast<const char2*>(a.volt + ((blk * a.n + p) * (long long)a.bs + off) * 2);
 #pragma unroll
             for (int m = 0; m < 32; ++m) {
@@ -540,11 +544,8 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
             for (int m = 0; m < 32; ++m) v[m] = make_float2(0.0f, 0.0f);
         }
         Dft<32>::run(v);
-        if (T == 1) {
-            // single pass: this is the final spectrum, handled below from shared memory
-        }
 #pragma unroll
-        for (int r = 0; r < 32; ++r) buf[f * ROW + 32 * t + r] = v[r];
+        for (int r = 0; r < 32; ++r) buf[f * ROW + SR * t + r] = v[r];
     }
     __syncthreads();
 
@@ -564,7 +565,7 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
         float2 v[T];
 #pragma unroll
         for (int r = 0; r < T; ++r) {
-            v[r] = buf[f * ROW + j + 32 * r];
+            v[r] = buf[f * ROW + SR * r + j];
             if (r > 0) v[r] = c_mul(v[r], tw[j * r]);
         }
         DftIf<T>::run(v);

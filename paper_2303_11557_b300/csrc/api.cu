@@ -35,6 +35,9 @@ struct mwax_plan {
     Group* groups = nullptr;
     int n_groups = 0;
     float* gain = nullptr;
+    int* chan_group = nullptr;   // FP8: group of each ultrafine channel
+    float* amax = nullptr;       // FP8: [slots][groups][n] per-path max magnitude
+    size_t amax_bytes = 0;
     RunInfo* runs = nullptr;
     int n_runs = 0;
     int4* tiles = nullptr;
@@ -165,6 +168,8 @@ void free_plan(mwax_plan* p)
     cudaFree(p->delay);
     cudaFree(p->groups);
     cudaFree(p->gain);
+    cudaFree(p->chan_group);
+    cudaFree(p->amax);
     cudaFree(p->runs);
     cudaFree(p->tiles);
     cudaFree(p->status);
@@ -208,8 +213,6 @@ mwax_status validate(const mwax_plan_desc& d, mwax_plan& p)
         return fail(MWAX_EINVAL, "MWAX_INT8 needs fft_len = fine_avg = 1 (no FFT)");
     if (!fft_len_supported(d.fft_len)) return fail(MWAX_EUNSUPPORTED, "fft_len %d is not built", d.fft_len);
     if (d.fft_len > 1 && d.fft_len < 16) return fail(MWAX_EUNSUPPORTED, "fft_len %d is not built", d.fft_len);
-    if (d.precision != MWAX_FP32 && d.precision != MWAX_FP16)
-        return fail(MWAX_EUNSUPPORTED, "precision %d is not built in this library version", d.precision);
 
     p.desc = d;
     p.T = d.n_tiles;
@@ -294,12 +297,25 @@ mwax_status setup(mwax_plan& p)
         p.post_scale = ldexpf(1.0f, 2 * k);
     }
     p.tensor_cores = p.prec != MWAX_FP32;
+    if (p.prec == MWAX_FP8) {
+        std::vector<int> cg(p.N, -1);
+        for (int g = 0; g < p.n_groups; ++g)
+            for (int c = groups[g].c0; c < groups[g].c1; ++c)
+                if (gain[c] > 0.0f) cg[c] = g;
+        MWAX_CUDA(cudaMalloc(&p.chan_group, sizeof(int) * p.N));
+        MWAX_CUDA(cudaMemcpy(p.chan_group, cg.data(), sizeof(int) * p.N, cudaMemcpyHostToDevice));
+        p.amax_bytes = sizeof(float) * (size_t)p.slots * p.n_groups * p.n;
+        MWAX_CUDA(cudaMalloc(&p.amax, p.amax_bytes));
+    }
     if (p.tensor_cores)
         MWAX_CUDA(make_operand_tmap(&p.tmap, p.Y, p.elem_bytes == 1 ? 1 : 2, p.Kpad, p.n, p.slots * p.N * 2));
 
     // tiles of path pairs on or above the diagonal
     std::vector<int4> tiles;
-    if (p.tensor_cores) {
+    if (p.prec == MWAX_INT8) {
+        for (int i = 0; i < p.n; i += 128)
+            for (int j = i; j < p.n; j += 128) tiles.push_back(make_int4(i, j, 128, i == j ? 1 : 0));
+    } else if (p.tensor_cores) {
         tiles.resize(build_tc_tiles(p.n, nullptr, 0));
         build_tc_tiles(p.n, tiles.data(), (int)tiles.size());
     } else {
@@ -408,8 +424,18 @@ mwax_status enqueue(mwax_plan* p, const int8_t* volt, bool have_delay, char* out
             fa.bs = p->bs;
             fa.nu = p->nu;
             fa.out_scale = p->out_scale;
-            const int fout = (p->prec == MWAX_FP32) ? FOUT_F32 : FOUT_F16;
-            MWAX_CUDA(timed(p, 1, [&] { return launch_fstep(p->N, fout, fa, s); }));
+            fa.chan_group = p->chan_group;
+            fa.n_groups = p->n_groups;
+            fa.amax = p->amax;
+            if (p->prec == MWAX_FP8) {
+                // two passes: per-path-per-group max magnitude, then e4m3 quantisation
+                MWAX_CUDA(cudaMemsetAsync(p->amax, 0, p->amax_bytes, s));
+                MWAX_CUDA(timed(p, 1, [&] { return launch_fstep(p->N, FOUT_AMAX, fa, s); }));
+                MWAX_CUDA(timed(p, 1, [&] { return launch_fstep(p->N, FOUT_E4M3, fa, s); }));
+            } else {
+                const int fout = (p->prec == MWAX_FP32) ? FOUT_F32 : FOUT_F16;
+                MWAX_CUDA(timed(p, 1, [&] { return launch_fstep(p->N, fout, fa, s); }));
+            }
 
             XArgs xa;
             memset(&xa, 0, sizeof xa);
@@ -432,9 +458,13 @@ mwax_status enqueue(mwax_plan* p, const int8_t* volt, bool have_delay, char* out
             xa.first_store = (ch == 0) ? 1 : 0;
             xa.status = p->status;
             xa.spin_limit = 2000000;   // x 1000 cycles: ~1 s per bounded wait
-            if (p->tensor_cores) {
+            xa.scale = p->amax;
+            if (p->prec == MWAX_INT8) {
+                MWAX_CUDA(timed(p, 2, [&] { return launch_xstep_int8(p->tmap, xa, p->n_tiles, (int)nslots, s); }));
+            } else if (p->tensor_cores) {
+                const int op = (p->prec == MWAX_FP8) ? 1 : 0;
                 MWAX_CUDA(timed(p, 2, [&] {
-                    return launch_xstep_tc(0, p->tmap, xa, p->n_tiles, p->n_runs, (int)nslots, s);
+                    return launch_xstep_tc(op, p->tmap, xa, p->n_tiles, p->n_runs, (int)nslots, s);
                 }));
             } else {
                 MWAX_CUDA(timed(p, 2, [&] { return launch_xstep_simt(xa, p->n_tiles, p->n_runs, (int)nslots, s); }));

@@ -218,8 +218,10 @@ struct FrameInfo {
 template <int N, int OUTK>
 struct Store {
     // Write one corrected spectral value: real plane at element `at`, imaginary plane at
-    // `at + plane_stride` of the operand buffer.
-    __device__ __forceinline__ static void run(const FArgs& a, long long at, long long plane_stride, float2 v)
+    // `at + plane_stride` of the operand buffer.  FP8: the amax pass raises
+    // amax[slot][group(c)][p]; the quantise pass writes v / s as e4m3.
+    __device__ __forceinline__ static void run(const FArgs& a, long long at, long long plane_stride, float2 v,
+                                               long long slot, int c, int p)
     {
         if (OUTK == FOUT_F32) {
             float* Y = static_cast<float*>(a.Y);
@@ -229,6 +231,19 @@ struct Store {
             __half* Y = static_cast<__half*>(a.Y);
             Y[at] = __float2half_rn(v.x * a.out_scale);
             Y[at + plane_stride] = __float2half_rn(v.y * a.out_scale);
+        } else {
+            const int g = a.chan_group[c];
+            if (g < 0) return;
+            float* am = a.amax + (slot * a.n_groups + g) * (long long)a.n + p;
+            if (OUTK == FOUT_AMAX) {
+                const float m = fmaxf(fabsf(v.x), fabsf(v.y));
+                if (m > 0.0f) atomicMax(reinterpret_cast<int*>(am), __float_as_int(m));   // m >= 0: int order
+            } else {
+                const float sc = e4m3_scale(*am);
+                __nv_fp8_storage_t* Y = static_cast<__nv_fp8_storage_t*>(a.Y);
+                Y[at] = __nv_cvt_float_to_fp8(__fdiv_rn(v.x, sc), __NV_SATFINITE, __NV_E4M3);
+                Y[at + plane_stride] = __nv_cvt_float_to_fp8(__fdiv_rn(v.y, sc), __NV_SATFINITE, __NV_E4M3);
+            }
         }
     }
 };
@@ -318,7 +333,7 @@ struct Pass {
                     const float gn = gain[c];
                     y.x *= gn;
                     y.y *= gn;
-                    Store<N, OUTK>::run(a, base + c * cs, ps, y);
+                    Store<N, OUTK>::run(a, base + c * cs, ps, y, fi.slot, c, p);
                 }
             }
         }
@@ -553,7 +568,15 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
     const int f = threadIdx.x % FB;
     const int jb = (threadIdx.x / FB) * P::JPT;
     const FrameR32 fi = finfo[f];
-    if (fi.slot < 0) return;
+    // FP8 amax pass: lanes sharing a butterfly set are FB consecutive frames; when they
+    // all belong to one slot, their maxima are combined before one atomic per channel
+    bool seg_uniform = false;
+    if (OUTK == FOUT_AMAX) {
+        const long long s0 = __shfl_sync(0xffffffffu, fi.slot, (threadIdx.x % 32) / FB * FB, FB);
+        seg_uniform = __all_sync(0xffffffffu, fi.slot == s0 && fi.slot >= 0);
+    } else if (fi.slot < 0) {
+        return;
+    }
     const long long cs = 2LL * a.n * a.Kpad;
     const long long ps = (long long)a.n * a.Kpad;
     const long long base = (fi.slot * N * 2LL * a.n + p) * a.Kpad + fi.k;
@@ -580,7 +603,23 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
                 E = c_mul(E, fi.step32);
             }
             const float gn = gain[c];
-            Store<N, OUTK>::run(a, base + c * cs, ps, make_float2(y.x * gn, y.y * gn));
+            y = make_float2(y.x * gn, y.y * gn);
+            if (OUTK == FOUT_AMAX) {
+                const int g = a.chan_group[c];
+                float m = (fi.slot >= 0) ? fmaxf(fabsf(y.x), fabsf(y.y)) : 0.0f;
+                if (seg_uniform) {
+#pragma unroll
+                    for (int o = FB / 2; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o, FB));
+                    if (f == 0 && g >= 0 && m > 0.0f)
+                        atomicMax(reinterpret_cast<int*>(a.amax + (fi.slot * a.n_groups + g) * (long long)a.n + p),
+                                  __float_as_int(m));
+                } else if (fi.slot >= 0 && g >= 0 && m > 0.0f) {
+                    atomicMax(reinterpret_cast<int*>(a.amax + (fi.slot * a.n_groups + g) * (long long)a.n + p),
+                              __float_as_int(m));
+                }
+            } else {
+                Store<N, OUTK>::run(a, base + c * cs, ps, y, fi.slot, c, p);
+            }
         }
         if (fi.delay) Ej = c_mul(Ej, fi.step1);
     }
@@ -614,7 +653,7 @@ __global__ void __launch_bounds__(256) unpack_kernel(const FArgs a)
         }
         const float gn = __ldg(&a.gain[0]);
         const long long at = ((fl / a.Kc) * 2LL * a.n + p) * a.Kpad + fl % a.Kc;
-        Store<1, OUTK>::run(a, at, (long long)a.n * a.Kpad, make_float2(v.x * gn, v.y * gn));
+        Store<1, OUTK>::run(a, at, (long long)a.n * a.Kpad, make_float2(v.x * gn, v.y * gn), fl / a.Kc, 0, p);
     }
 }
 
@@ -702,6 +741,8 @@ cudaError_t launch_fstep(int N, int out_kind, const FArgs& a, cudaStream_t s)
     switch (out_kind) {
         case FOUT_F32: return launch_kind<FOUT_F32>(N, a, s);
         case FOUT_F16: return launch_kind<FOUT_F16>(N, a, s);
+        case FOUT_AMAX: return launch_kind<FOUT_AMAX>(N, a, s);
+        case FOUT_E4M3: return launch_kind<FOUT_E4M3>(N, a, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -43,8 +43,10 @@ struct FArgs {
     const int8_t* volt;   // [blk][n][bs][2]
     const double* delay;  // [n][3] or nullptr
     void* Y;              // operands [slot][N][2][n][Kpad]
-    float* amax;          // FP8: [slot][N][n] per-path-per-channel max |re|,|im|
-    const float* scale;   // FP8 quantise pass: [slot][N][n] scale s = amax / 448
+    float* amax;          // FP8: [slot][group][n] max |re|, |im| over the slot's frames and the
+                          //      group's channels (atomically raised by the amax pass)
+    const int* chan_group;   // FP8: [N] group of each ultrafine channel (-1: none)
+    int n_groups;
     const float2* tw;     // e^{-2 pi i k / N}, k < N
     const float* gain;    // [N] sqrt of each ultrafine channel's averaging weight
     long long m_begin;
@@ -61,7 +63,7 @@ struct FArgs {
 // Arguments of one X-step launch over `slots` operand slots.
 struct XArgs {
     const void* Y;         // operands [slot][N][2][n][Kpad]
-    const float* scale;    // FP8 per-path-per-channel scales [slot][N][n] or nullptr
+    const float* scale;    // FP8: amax [slot][group][n]; the scale is s = amax / 448
     char* out;             // output of slot 0's integration
     long long out_stride;  // bytes from one integration's output to the next
     long long Kpad;
@@ -82,6 +84,9 @@ struct XArgs {
 
 // Launchers (each returns the cudaError_t of its launch).
 cudaError_t launch_fstep(int N, int out_kind, const FArgs& a, cudaStream_t s);
+
+// e4m3 scale of a path's spectra from their max magnitude: 448 is e4m3's largest finite.
+__host__ __device__ __forceinline__ float e4m3_scale(float amax) { return amax > 0.0f ? amax * (1.0f / 448.0f) : 1.0f; }
 cudaError_t launch_init_output(char* out, long long n_ints, long long vis_set_bytes, long long weights_bytes,
                                cudaStream_t s);
 cudaError_t launch_xstep_simt(const XArgs& a, int n_tiles, int n_runs, int slots, cudaStream_t s);
@@ -90,6 +95,7 @@ cudaError_t make_operand_tmap(CUtensorMap* map, const void* Y, int elem_bytes, l
 cudaError_t launch_xstep_tc(int op, const CUtensorMap& map, const XArgs& a, int n_tiles, int n_runs, int slots,
                             cudaStream_t s);
 int build_tc_tiles(int n, int4* out, int cap);
+cudaError_t launch_xstep_int8(const CUtensorMap& map, const XArgs& a, int n_tiles, int slots, cudaStream_t s);
 bool fft_len_supported(int N);
 
 }  // namespace mwax

@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) xstep_tc_kernel(const __grid_cons
                 const float* qscale = nullptr;
                 if (OP == 1) {
                     const float* sc = a.scale + ((long long)slot * a.n_groups + g) * a.n;
-                    sp *= (p < a.n) ? __ldg(sc + p) : 0.0f;
+                    sp *= (p < a.n) ? e4m3_scale(__ldg(sc + p)) : 0.0f;
                     qscale = sc;
                 }
 #pragma unroll 1
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) xstep_tc_kernel(const __grid_cons
                             if (off[i] < 0) continue;
                             const int q = q0 + col + h * 8 + i;
                             float s = sp;
-                            if (OP == 1) s *= __ldg(qscale + q);
+                            if (OP == 1) s *= e4m3_scale(__ldg(qscale + q));
                             const float re = __uint_as_float(vr[h * 8 + i]) * s;
                             const float im = (p == q) ? 0.0f : __uint_as_float(vi[h * 8 + i]) * s;
                             if (use_a)

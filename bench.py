@@ -237,6 +237,55 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def time_plan(mw, torch, plan, dev_volt, dev_delay, steps, warmup, world, clocks=None):
+    """Warm up, then time `steps` calls on the plan's stream with CUDA events (and per-stage
+    events inside the library).  Returns (ms per step max over ranks, stage times, output)."""
+    stream = torch.cuda.current_stream()
+    mw.mwax_plan_set_stream(plan, stream)
+    out = mw.empty_output(plan)
+    for _ in range(warmup):
+        mw.mwax_correlate(plan, dev_volt, dev_delay, out)
+    mw.mwax_plan_sync(plan)
+    mw.mwax_plan_stage_times(plan)          # reset counters
+    mw.mwax_plan_enable_timing(plan, True)
+    if clocks:
+        clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        mw.mwax_correlate(plan, dev_volt, dev_delay, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ck = clocks.stop() if clocks else None
+    mw.mwax_plan_sync(plan)
+    stages = mw.mwax_plan_stage_times(plan)
+    mw.mwax_plan_enable_timing(plan, False)
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, world)
+    return ms, stages, out, ck
+
+
+def rel_error_vs(mw, torch, plan, out, ref_vis, T):
+    """max / median of |V - V_ref| / sqrt(V_ref,pp V_ref,qq) (parallel-pol autos of V_ref)."""
+    vis, _ = mw.split_output(plan, out)
+    ti = torch.tensor([i for i in range(T) for _ in range(i, T)], device=vis.device)
+    tj = torch.tensor([j for i in range(T) for j in range(i, T)], device=vis.device)
+    auto_b = ti.new_tensor([i * (2 * T - i + 1) // 2 for i in range(T)])
+    mx, meds = 0.0, []
+    for w in range(vis.shape[0]):
+        r, v = ref_vis[w], vis[w]
+        for pol in range(4):
+            a, e = pol >> 1, pol & 1
+            ap = r[:, :, 3 * a].real.abs()[auto_b[ti]]
+            aq = r[:, :, 3 * e].real.abs()[auto_b[tj]]
+            err = (v[:, :, pol] - r[:, :, pol]).abs() / torch.sqrt(ap * aq)
+            mx = max(mx, float(err.max()))
+            meds.append(float(err.median()))
+    return mx, statistics.median(meds)
+
+
 def run_mine(args, world, rank, local):
     import torch
     import paper_2303_11557_b300 as mw
@@ -246,65 +295,85 @@ def run_mine(args, world, rank, local):
     host, delay = make_inputs(W, pin=not args.no_e2e)
     dev_volt = host.cuda(non_blocking=False)
     dev_delay = torch.from_numpy(delay).cuda()
-    prec = mw.PRECISIONS[args.precision]
-    desc = mw.PlanDesc(n_tiles=W["n_tiles"], fft_len=W["fft_len"], fine_avg=W["fine_avg"],
-                       int_time_s=W["int_time_s"], samples_per_call=W["samples"], precision=prec,
-                       sky_freq_hz=W["sky_freq_hz"])
-    plan = mw.mwax_plan_create_ex(desc)
-    stream = torch.cuda.current_stream()
-    mw.mwax_plan_set_stream(plan, stream)
-    out = mw.empty_output(plan)
-    for _ in range(args.warmup):
-        mw.mwax_correlate(plan, dev_volt, dev_delay, out)
-    mw.mwax_plan_sync(plan)
-    mw.mwax_plan_stage_times(plan)          # reset counters
-    mw.mwax_plan_enable_timing(plan, True)
-
-    clocks = ClockSampler(local)
-    clocks.start()
-    barrier(world)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        mw.mwax_correlate(plan, dev_volt, dev_delay, out)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(world)
-    ck = clocks.stop()
-    mw.mwax_plan_sync(plan)
-    stages = mw.mwax_plan_stage_times(plan)
-    mw.mwax_plan_enable_timing(plan, False)
-    ms = e0.elapsed_time(e1) / args.steps
-    ms_max = max_over_ranks(ms, world)
-
-    info = plan.info
-    K, n_ints = info["frames_per_int"], info["n_ints"]
-    x_flops, f_bytes, used = algorithmic_work(W["n_tiles"], W["fft_len"], W["fine_avg"], K, n_ints,
-                                              4 if prec == mw.MWAX_FP32 else 2)
     pk, pk_kind = peaks()
-    x_ms, x_n = stages["xstep"]
-    f_ms, f_n = stages["fstep"]
-    x_per_launch = x_flops * args.steps / x_n
-    xkern = "xstep_simt_kernel" if prec == mw.MWAX_FP32 else "xstep_tc_kernel<0>"
-    tps = traffic_per_slot(xkern)
-    x_traffic = None if tps is None else tps * n_ints * args.steps / x_n
-    x_avg_ms = x_ms / x_n
-    x_achieved = x_per_launch / (x_avg_ms * 1e-3) / 1e12
-    if prec == mw.MWAX_FP32:
-        x_peak = N_SM * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
-        x_bound = "alu"
-        x_peak_kind = (f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {pk.get('sm_max_mhz')} MHz "
-                       f"({pk_kind} max clock)")
-    else:
-        x_peak = pk["bf16_tflops_sustained"] if "bf16_tflops_sustained" in pk else pk["bf16_tflops"]
-        x_bound = "tensor"
-        x_peak_kind = f"{pk_kind} dense bf16 (= fp16 rate) cuBLAS, sustained; burst {pk.get('bf16_tflops')}"
-    f_per_launch = f_bytes * args.steps / f_n
-    f_avg_ms = f_ms / f_n
-    f_achieved = f_per_launch / (f_avg_ms * 1e-3) / 1e9
+    headline = args.precision
+    forms = [headline] + ([] if args.no_forms else [f for f in ("fp32", "fp16", "fp8", "int8") if f != headline])
+    results, ref_vis, line_parts = {}, None, {}
+    for form in forms:
+        prec = mw.PRECISIONS[form]
+        if form == "int8":
+            # integer mode on the same voltages: no FFT (1.28 MHz channels), 1 s integrations
+            desc = mw.PlanDesc(n_tiles=W["n_tiles"], fft_len=1, fine_avg=1, int_time_s=1.0 if W is WORKLOAD else 0.5,
+                               samples_per_call=W["samples"], precision=prec)
+            ddelay = None
+        else:
+            desc = mw.PlanDesc(n_tiles=W["n_tiles"], fft_len=W["fft_len"], fine_avg=W["fine_avg"],
+                               int_time_s=W["int_time_s"], samples_per_call=W["samples"], precision=prec,
+                               sky_freq_hz=W["sky_freq_hz"])
+            ddelay = dev_delay
+        plan = mw.mwax_plan_create_ex(desc)
+        clocks = ClockSampler(local) if form == headline else None
+        ms, stages, out, ck = time_plan(mw, torch, plan, dev_volt, ddelay, args.steps, args.warmup, world, clocks)
+        info = plan.info
+        K, n_ints = info["frames_per_int"], info["n_ints"]
+        N, F = desc.fft_len, desc.fine_avg
+        elem = {"fp32": 4, "fp16": 2, "fp8": 1, "int8": 2}[form]
+        x_flops, f_bytes, used = algorithmic_work(W["n_tiles"], N, F, K, n_ints, elem)
+        if form == "fp8":
+            f_bytes += 2.0 * 2 * W["n_tiles"] * K * N * n_ints   # the amax pass reads the voltages again
+        x_ms, x_n = stages["xstep"]
+        f_ms, f_n = stages["fstep"]
+        x_per_launch = x_flops * args.steps / x_n
+        x_avg_ms = x_ms / x_n
+        x_achieved = x_per_launch / (x_avg_ms * 1e-3) / 1e12
+        if form == "fp32":
+            xkern, bound = "xstep_simt_kernel", "alu"
+            x_peak = N_SM * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+            peak_kind = (f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {pk.get('sm_max_mhz')} MHz "
+                         f"({pk_kind} max clock)")
+        else:
+            xkern = {"fp16": "xstep_tc_kernel<0>", "fp8": "xstep_tc_kernel<1>", "int8": "xstep_int8_kernel"}[form]
+            bound = "tensor"
+            base = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+            ratio = 2.0 if form == "fp8" else 1.0
+            x_peak = base * ratio
+            peak_kind = (f"{pk_kind} dense bf16 cuBLAS, sustained" + (" x 2 (fp8 : bf16 nominal 4.5 : 2.25)"
+                                                                        if form == "fp8" else " (fp16 = bf16 rate)")
+                         + ("; int8 values run exactly as fp16" if form == "int8" else ""))
+        tps = traffic_per_slot(xkern) if form == headline else None
+        r = {"value": world * SUBOBS_S * (n_ints * desc.int_time_s / SUBOBS_S) / (ms * 1e-3),
+             "ms_per_step": ms, "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+             "launches_per_step": sum(v[1] for v in stages.values()) / args.steps,
+             "roofline": {"bound": bound, "kernel": xkern, "achieved": x_achieved, "peak": x_peak, "unit": "TFLOP/s",
+                          "frac": x_achieved / x_peak,
+                          "traffic": None if tps is None else tps * n_ints * args.steps / x_n,
+                          "peak_kind": peak_kind,
+                          "per_launch": f"{x_per_launch:.4g} flop (8 x pairs x frames x {used} used bins)",
+                          "avg_launch_ms": x_avg_ms},
+             "roofline_fstep": {"bound": "hbm", "achieved": f_bytes / (f_ms / args.steps * 1e-3) / 1e9,
+                                "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                "frac": f_bytes / (f_ms / args.steps * 1e-3) / 1e9 / pk["hbm_gbs"],
+                                "per_step_bytes": f_bytes, "peak_kind": f"{pk_kind} copy bandwidth"},
+             "gpu_launches": sum(v[1] for v in stages.values())}
+        if form == "fp32" and form != "int8":
+            vis32, _ = mw.split_output(plan, out)
+            ref_vis = vis32.clone()
+        elif form in ("fp16", "fp8") and ref_vis is not None:
+            mx, med = rel_error_vs(mw, torch, plan, out, ref_vis, W["n_tiles"])
+            r["error_vs_fp32"] = {"max": mx, "median": med,
+                                  "metric": "|V - V_fp32| / sqrt(auto_pp auto_qq), full workload"}
+        if form == headline:
+            line_parts["clocks"] = ck
+            line_parts["info"] = info
+            line_parts["plan"] = plan
+            line_parts["desc"] = desc
+        else:
+            plan.close()
+            del out
+        results[form] = r
 
-    # end to end through the host-memory entry point (pinned buffers)
+    # end to end through the host-memory entry point (pinned buffers), headline precision
+    plan, info = line_parts["plan"], line_parts["info"]
     e2e = None
     if not args.no_e2e:
         host_out = torch.empty(plan.output_bytes, dtype=torch.uint8, pin_memory=True)
@@ -315,8 +384,9 @@ def run_mine(args, world, rank, local):
         for _ in range(reps):
             mw.mwax_correlate_host(plan, host, delay, host_out)
         t_e2e = max_over_ranks((time.perf_counter() - t0) / reps, world)
-        e2e = {"value": world * n_ints * W["int_time_s"] / t_e2e, "unit": "channels", "h2d_bytes_per_step": info["input_bytes"] +
-               delay.nbytes, "d2h_bytes_per_step": info["output_bytes"], "ms_per_step": 1e3 * t_e2e}
+        e2e = {"value": world * info["n_ints"] * W["int_time_s"] / t_e2e, "unit": "channels",
+               "h2d_bytes_per_step": info["input_bytes"] + delay.nbytes, "d2h_bytes_per_step": info["output_bytes"],
+               "ms_per_step": 1e3 * t_e2e}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -327,30 +397,26 @@ def run_mine(args, world, rank, local):
 
     if rank != 0:
         return
-    launches = sum(v[1] for v in stages.values())
+    h = results[headline]
     line = {
-        "metric": METRIC, "value": world * SUBOBS_S * (n_ints * W["int_time_s"] / SUBOBS_S) / (ms_max * 1e-3), "unit": "channels", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16"}[args.precision],
+        "metric": METRIC, "value": h["value"], "unit": "channels", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16", "fp8": "e4m3",
+                                                          "int8": "s8"}[headline],
         "data": "synthetic (seeded Gaussian sigma=16 + point source, linear per-tile delays)",
         "config": {"workload": W["name"], "n_tiles": W["n_tiles"], "fft_len": W["fft_len"],
                    "fine_avg": W["fine_avg"], "int_time_s": W["int_time_s"], "subobs_s": SUBOBS_S,
-                   "precision": args.precision, "l2": "inputs 10.5 GB > 126 MB L2, no flush needed",
+                   "precision": headline, "l2": "inputs 10.5 GB > 126 MB L2, no flush needed",
                    "parallelism": f"replicas x{world} (independent coarse channels)"},
-        "roofline": {"bound": x_bound, "kernel": xkern, "achieved": x_achieved, "peak": x_peak,
-                     "unit": "TFLOP/s", "frac": x_achieved / x_peak, "traffic": x_traffic,
-                     "peak_kind": x_peak_kind,
-                     "per_launch": f"{x_per_launch:.4g} flop (8 x pairs x frames x {used} used bins)",
-                     "avg_launch_ms": x_avg_ms},
-        "roofline_fstep": {"bound": "hbm", "kernel": f"fstep_kernel<128, {args.precision}>", "achieved": f_achieved,
-                           "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": f_achieved / pk["hbm_gbs"],
-                           "per_launch_bytes": f_per_launch, "avg_launch_ms": f_avg_ms,
-                           "peak_kind": f"{pk_kind} copy bandwidth"},
-        "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
-        "gpu_launches": launches,
-        "clocks": ck,
+        "roofline": h["roofline"],
+        "roofline_fstep": h["roofline_fstep"],
+        "stage_ms_per_step": h["stage_ms_per_step"],
+        "gpu_launches": h["gpu_launches"],
+        "clocks": line_parts["clocks"],
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "precision_forms": {f: {k: v for k, v in r.items() if k != "gpu_launches"} for f, r in results.items()
+                            if f != headline},
         "context": {"paper": "1 coarse channel of 256 tiles in real time per NVIDIA A40 (6.2 s per 8 s at "
                              "250 ms / 40 kHz, Table 2)"},
     }
@@ -365,7 +431,9 @@ def main():
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "fp8", "int8"],
+                    help="headline precision (config 1 is FP32); the other forms are timed beside it")
+    ap.add_argument("--no-forms", action="store_true", help="time the headline precision only")
     ap.add_argument("--workload", default="full", choices=["full", "small"],
                     help="small = one 0.5 s integration (for profiler captures)")
     args = ap.parse_args()

@@ -28,7 +28,8 @@ struct mwax_plan {
     int elem_bytes = 4;
 
     // device memory
-    void* Y = nullptr;
+    void* Y = nullptr;      // X-step operands (FP8: e4m3)
+    void* Y16 = nullptr;    // FP8 only: the FP16 operands the e4m3 ones are quantised from
     size_t Y_bytes = 0;
     float2* tw = nullptr;
     double* delay = nullptr;
@@ -154,7 +155,7 @@ int prec_elem_bytes(int prec)
     switch (prec) {
         case MWAX_FP32: return 4;
         case MWAX_FP16: return 2;
-        case MWAX_FP8: return 1;
+        case MWAX_FP8: return 3;   // FP16 staging (2) + e4m3 operands (1)
         case MWAX_INT8: return 2;   // int8 held exactly in FP16 operands
         default: return 0;
     }
@@ -164,6 +165,7 @@ void free_plan(mwax_plan* p)
 {
     if (!p) return;
     cudaFree(p->Y);
+    cudaFree(p->Y16);
     cudaFree(p->tw);
     cudaFree(p->delay);
     cudaFree(p->groups);
@@ -263,9 +265,17 @@ mwax_status setup(mwax_plan& p)
         p.Kpad = kc;
         p.chunks = (int)((p.K + kc - 1) / kc);
     }
-    p.Y_bytes = (size_t)p.slots * p.N * 2 * p.n * p.Kpad * p.elem_bytes;
-    MWAX_CUDA(cudaMalloc(&p.Y, p.Y_bytes));
-    MWAX_CUDA(cudaMemset(p.Y, 0, p.Y_bytes));
+    const size_t elems = (size_t)p.slots * p.N * 2 * p.n * p.Kpad;
+    p.Y_bytes = elems * p.elem_bytes;
+    if (p.prec == MWAX_FP8) {
+        MWAX_CUDA(cudaMalloc(&p.Y16, elems * 2));
+        MWAX_CUDA(cudaMemset(p.Y16, 0, elems * 2));
+        MWAX_CUDA(cudaMalloc(&p.Y, elems));
+        MWAX_CUDA(cudaMemset(p.Y, 0, elems));
+    } else {
+        MWAX_CUDA(cudaMalloc(&p.Y, p.Y_bytes));
+        MWAX_CUDA(cudaMemset(p.Y, 0, p.Y_bytes));
+    }
 
     // twiddles e^{-2 pi i k / N}, rounded from FP64
     std::vector<float2> tw(p.N);
@@ -290,7 +300,7 @@ mwax_status setup(mwax_plan& p)
 
     // FP16 operands: power-of-two pre-scale keeping |Re X|, |Im X| <= 181 N (int8
     // magnitude 128 sqrt 2 summed over N samples) below 2^15; undone exactly after the MMA
-    if (p.prec == MWAX_FP16) {
+    if (p.prec == MWAX_FP16 || p.prec == MWAX_FP8) {
         int k = 0;
         while (181.02 * p.N / (double)(1 << k) > 32768.0) ++k;
         p.out_scale = ldexpf(1.0f, -k);
@@ -308,7 +318,7 @@ mwax_status setup(mwax_plan& p)
         MWAX_CUDA(cudaMalloc(&p.amax, p.amax_bytes));
     }
     if (p.tensor_cores)
-        MWAX_CUDA(make_operand_tmap(&p.tmap, p.Y, p.elem_bytes == 1 ? 1 : 2, p.Kpad, p.n, p.slots * p.N * 2));
+        MWAX_CUDA(make_operand_tmap(&p.tmap, p.Y, p.prec == MWAX_FP8 ? 1 : 2, p.Kpad, p.n, p.slots * p.N * 2));
 
     // tiles of path pairs on or above the diagonal
     std::vector<int4> tiles;
@@ -428,10 +438,15 @@ mwax_status enqueue(mwax_plan* p, const int8_t* volt, bool have_delay, char* out
             fa.n_groups = p->n_groups;
             fa.amax = p->amax;
             if (p->prec == MWAX_FP8) {
-                // two passes: per-path-per-group max magnitude, then e4m3 quantisation
+                // FP16 operands with the per-path-per-group max magnitude, then e4m3
                 MWAX_CUDA(cudaMemsetAsync(p->amax, 0, p->amax_bytes, s));
-                MWAX_CUDA(timed(p, 1, [&] { return launch_fstep(p->N, FOUT_AMAX, fa, s); }));
-                MWAX_CUDA(timed(p, 1, [&] { return launch_fstep(p->N, FOUT_E4M3, fa, s); }));
+                fa.Y = p->Y16;
+                MWAX_CUDA(timed(p, 1, [&] { return launch_fstep(p->N, FOUT_F16A, fa, s); }));
+                MWAX_CUDA(timed(p, 1, [&] {
+                    return launch_quantise_e4m3(static_cast<const __half*>(p->Y16),
+                                                static_cast<__nv_fp8_storage_t*>(p->Y), p->amax, p->chan_group,
+                                                p->n_groups, nslots, p->N, p->n, p->Kpad, s);
+                }));
             } else {
                 const int fout = (p->prec == MWAX_FP32) ? FOUT_F32 : FOUT_F16;
                 MWAX_CUDA(timed(p, 1, [&] { return launch_fstep(p->N, fout, fa, s); }));
@@ -460,7 +475,14 @@ mwax_status enqueue(mwax_plan* p, const int8_t* volt, bool have_delay, char* out
             xa.spin_limit = 2000000;   // x 1000 cycles: ~1 s per bounded wait
             xa.scale = p->amax;
             if (p->prec == MWAX_INT8) {
-                MWAX_CUDA(timed(p, 2, [&] { return launch_xstep_int8(p->tmap, xa, p->n_tiles, (int)nslots, s); }));
+                // split each slot's samples into segments of whole 256-sample chunks so the
+                // grid covers the GPU several times over
+                const long long chunks256 = (klen + 255) / 256;
+                const long long want = std::max<long long>(1, (4LL * 148 + p->n_tiles * nslots - 1) / (p->n_tiles * nslots));
+                const long long seg_chunks = std::max<long long>(1, (chunks256 + want - 1) / want);
+                xa.seg_frames = seg_chunks * 256;
+                const int nseg = (int)((chunks256 + seg_chunks - 1) / seg_chunks);
+                MWAX_CUDA(timed(p, 2, [&] { return launch_xstep_int8(p->tmap, xa, p->n_tiles, nseg, (int)nslots, s); }));
             } else if (p->tensor_cores) {
                 const int op = (p->prec == MWAX_FP8) ? 1 : 0;
                 MWAX_CUDA(timed(p, 2, [&] {

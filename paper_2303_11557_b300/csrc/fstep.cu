@@ -218,8 +218,8 @@ struct FrameInfo {
 template <int N, int OUTK>
 struct Store {
     // Write one corrected spectral value: real plane at element `at`, imaginary plane at
-    // `at + plane_stride` of the operand buffer.  FP8: the amax pass raises
-    // amax[slot][group(c)][p]; the quantise pass writes v / s as e4m3.
+    // `at + plane_stride` of the operand buffer.  FOUT_F16A also raises
+    // amax[slot][group(c)][p] (per point here; the radix-32 kernel reduces across frames).
     __device__ __forceinline__ static void run(const FArgs& a, long long at, long long plane_stride, float2 v,
                                                long long slot, int c, int p)
     {
@@ -232,18 +232,14 @@ struct Store {
             Y[at] = __float2half_rn(v.x * a.out_scale);
             Y[at + plane_stride] = __float2half_rn(v.y * a.out_scale);
         } else {
+            __half* Y = static_cast<__half*>(a.Y);
+            const __half hr = __float2half_rn(v.x * a.out_scale), hi = __float2half_rn(v.y * a.out_scale);
+            Y[at] = hr;
+            Y[at + plane_stride] = hi;
             const int g = a.chan_group[c];
-            if (g < 0) return;
-            float* am = a.amax + (slot * a.n_groups + g) * (long long)a.n + p;
-            if (OUTK == FOUT_AMAX) {
-                const float m = fmaxf(fabsf(v.x), fabsf(v.y));
-                if (m > 0.0f) atomicMax(reinterpret_cast<int*>(am), __float_as_int(m));   // m >= 0: int order
-            } else {
-                const float sc = e4m3_scale(*am);
-                __nv_fp8_storage_t* Y = static_cast<__nv_fp8_storage_t*>(a.Y);
-                Y[at] = __nv_cvt_float_to_fp8(__fdiv_rn(v.x, sc), __NV_SATFINITE, __NV_E4M3);
-                Y[at + plane_stride] = __nv_cvt_float_to_fp8(__fdiv_rn(v.y, sc), __NV_SATFINITE, __NV_E4M3);
-            }
+            const float m = fmaxf(fabsf(__half2float(hr)), fabsf(__half2float(hi)));
+            if (g >= 0 && m > 0.0f)
+                atomicMax(reinterpret_cast<int*>(a.amax + (slot * a.n_groups + g) * (long long)a.n + p), __float_as_int(m));
         }
     }
 };
@@ -568,10 +564,10 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
     const int f = threadIdx.x % FB;
     const int jb = (threadIdx.x / FB) * P::JPT;
     const FrameR32 fi = finfo[f];
-    // FP8 amax pass: lanes sharing a butterfly set are FB consecutive frames; when they
+    // FP8 (FOUT_F16A): lanes sharing a butterfly set are FB consecutive frames; when they
     // all belong to one slot, their maxima are combined before one atomic per channel
     bool seg_uniform = false;
-    if (OUTK == FOUT_AMAX) {
+    if (OUTK == FOUT_F16A) {
         const long long s0 = __shfl_sync(0xffffffffu, fi.slot, (threadIdx.x % 32) / FB * FB, FB);
         seg_uniform = __all_sync(0xffffffffu, fi.slot == s0 && fi.slot >= 0);
     } else if (fi.slot < 0) {
@@ -604,9 +600,16 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
             }
             const float gn = gain[c];
             y = make_float2(y.x * gn, y.y * gn);
-            if (OUTK == FOUT_AMAX) {
+            if (OUTK == FOUT_F16A) {
                 const int g = a.chan_group[c];
-                float m = (fi.slot >= 0) ? fmaxf(fabsf(y.x), fabsf(y.y)) : 0.0f;
+                float m = 0.0f;
+                if (fi.slot >= 0) {
+                    __half* Y = static_cast<__half*>(a.Y);
+                    const __half hr = __float2half_rn(y.x * a.out_scale), hi = __float2half_rn(y.y * a.out_scale);
+                    Y[base + c * cs] = hr;
+                    Y[base + c * cs + ps] = hi;
+                    m = fmaxf(fabsf(__half2float(hr)), fabsf(__half2float(hi)));
+                }
                 if (seg_uniform) {
 #pragma unroll
                     for (int o = FB / 2; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o, FB));
@@ -712,6 +715,41 @@ cudaError_t launch_kind(int N, const FArgs& a, cudaStream_t s)
     }
 }
 
+// FP8: e4m3 operands from the FP16 ones, q = h * 448 / amax[slot][group(c)][p] with
+// saturation (|q| <= 448 by construction).  One thread per 8 consecutive frames of a row.
+__global__ void quantise_e4m3_kernel(const __half* __restrict__ Y16, __nv_fp8_storage_t* __restrict__ Y8,
+                                     const float* __restrict__ amax, const int* __restrict__ chan_group, int n_groups,
+                                     long long rows, int N, int n, long long Kpad)
+{
+    const long long per_row = Kpad / 8;
+    const long long total = rows * per_row;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long row = i / per_row, k8 = i % per_row;
+        const int p = (int)(row % n);
+        const long long sc = row / (2LL * n);           // slot * N + c
+        const int c = (int)(sc % N);
+        const long long slot = sc / N;
+        const int g = chan_group[c];
+        if (g < 0) continue;                            // zero-weight channel: never read
+        const float am = amax[(slot * n_groups + g) * (long long)n + p];
+        const float inv = am > 0.0f ? 448.0f / am : 0.0f;
+        const uint4 h = *reinterpret_cast<const uint4*>(Y16 + row * Kpad + k8 * 8);
+        const __half2* hp = reinterpret_cast<const __half2*>(&h);
+        uint32_t lo = 0, hi = 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float2 v = __half22float2(hp[e]);
+            const uint32_t q0 = __nv_cvt_float_to_fp8(v.x * inv, __NV_SATFINITE, __NV_E4M3);
+            const uint32_t q1 = __nv_cvt_float_to_fp8(v.y * inv, __NV_SATFINITE, __NV_E4M3);
+            const uint32_t pair = q0 | (q1 << 8);
+            if (e < 2) lo |= pair << (16 * e);
+            else hi |= pair << (16 * (e - 2));
+        }
+        *reinterpret_cast<uint2*>(Y8 + row * Kpad + k8 * 8) = make_uint2(lo, hi);
+    }
+}
+
 // Zero each integration's visibility set and write its weights table (1.0, Sec. 2.7).
 __global__ void init_output_kernel(char* out, long long n_ints, long long vis_words, long long wt_words)
 {
@@ -741,10 +779,18 @@ cudaError_t launch_fstep(int N, int out_kind, const FArgs& a, cudaStream_t s)
     switch (out_kind) {
         case FOUT_F32: return launch_kind<FOUT_F32>(N, a, s);
         case FOUT_F16: return launch_kind<FOUT_F16>(N, a, s);
-        case FOUT_AMAX: return launch_kind<FOUT_AMAX>(N, a, s);
-        case FOUT_E4M3: return launch_kind<FOUT_E4M3>(N, a, s);
+        case FOUT_F16A: return launch_kind<FOUT_F16A>(N, a, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_quantise_e4m3(const __half* Y16, __nv_fp8_storage_t* Y8, const float* amax,
+                                 const int* chan_group, int n_groups, long long slots, int N, int n, long long Kpad,
+                                 cudaStream_t s)
+{
+    const long long rows = slots * (long long)N * 2 * n;
+    quantise_e4m3_kernel<<<16 * 148, 256, 0, s>>>(Y16, Y8, amax, chan_group, n_groups, rows, N, n, Kpad);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_init_output(char* out, long long n_ints, long long vis_set_bytes, long long weights_bytes,

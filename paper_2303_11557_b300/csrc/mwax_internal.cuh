@@ -16,7 +16,9 @@ constexpr int kDefaultBlock = 64000;     // samples per path per 50 ms data bloc
 constexpr int kKAlign = 128;             // frames per operand row are padded to this
 
 // Output-type selector of the F-step.
-enum FOut : int { FOUT_F32 = 0, FOUT_F16 = 1, FOUT_AMAX = 2, FOUT_E4M3 = 3 };
+// FOUT_F16A: FP16 operands plus the FP8 per-path-per-group max magnitude of the stored
+// FP16 values (the e4m3 quantisation then runs as a separate bandwidth-bound pass).
+enum FOut : int { FOUT_F32 = 0, FOUT_F16 = 1, FOUT_F16A = 2 };
 
 // Channel averaging (Sec. 2.6) is split in two: the F-step multiplies ultrafine channel
 // c by gain[c] = sqrt(w_c) (w_c = 1, 1/2 for the end bins of an even fscrunch, 0 for an
@@ -76,6 +78,7 @@ struct XArgs {
     const float* gain;     // [N]; channels with gain 0 are skipped
     const int4* tiles;     // (p0, q0, column count, A rows inside the B window) per tile
     float post_scale;      // multiplies every product (undoes the FP16 pre-scale)
+    long long seg_frames;  // integer mode: frames per K segment (a multiple of 256)
     int first_store;       // 1: a channel's first group stores (output not yet written by an
                            //    earlier frame chunk of the same integration); 0: all add
     int* status;           // device status word (bounded waits)
@@ -87,6 +90,9 @@ cudaError_t launch_fstep(int N, int out_kind, const FArgs& a, cudaStream_t s);
 
 // e4m3 scale of a path's spectra from their max magnitude: 448 is e4m3's largest finite.
 __host__ __device__ __forceinline__ float e4m3_scale(float amax) { return amax > 0.0f ? amax * (1.0f / 448.0f) : 1.0f; }
+cudaError_t launch_quantise_e4m3(const __half* Y16, __nv_fp8_storage_t* Y8, const float* amax,
+                                 const int* chan_group, int n_groups, long long slots, int N, int n, long long Kpad,
+                                 cudaStream_t s);
 cudaError_t launch_init_output(char* out, long long n_ints, long long vis_set_bytes, long long weights_bytes,
                                cudaStream_t s);
 cudaError_t launch_xstep_simt(const XArgs& a, int n_tiles, int n_runs, int slots, cudaStream_t s);
@@ -95,7 +101,8 @@ cudaError_t make_operand_tmap(CUtensorMap* map, const void* Y, int elem_bytes, l
 cudaError_t launch_xstep_tc(int op, const CUtensorMap& map, const XArgs& a, int n_tiles, int n_runs, int slots,
                             cudaStream_t s);
 int build_tc_tiles(int n, int4* out, int cap);
-cudaError_t launch_xstep_int8(const CUtensorMap& map, const XArgs& a, int n_tiles, int slots, cudaStream_t s);
+cudaError_t launch_xstep_int8(const CUtensorMap& map, const XArgs& a, int n_tiles, int segments, int slots,
+                              cudaStream_t s);
 bool fft_len_supported(int N);
 
 }  // namespace mwax

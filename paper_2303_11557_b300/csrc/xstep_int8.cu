@@ -9,7 +9,9 @@
 // TMEM; every 200 chunks (51,200 samples: at most 200 * 2^23 < 2^31) the int32 sums are
 // added into the int64 output.  Result: bit-exact int64 visibilities.
 //
-// CTA = one 128 x 128 tile of path pairs x one slot.  TMEM columns: FP32 chunk sums
+// CTA = one 128 x 128 tile of path pairs x one segment of the slot's samples x one slot;
+// the segments' int64 sums are combined with 64-bit atomic adds into the zeroed output
+// (integer addition, so the result does not depend on their order).  TMEM columns: FP32 chunk sums
 // (Re [0,128), Im [128,256)), int32 running sums (Re [256,384), Im [384,512)).
 // Warps: 0 = TMA producer, 1 = MMA issuer (+ TMEM owner), 2-9 = epilogue (lane quarter
 // warp % 4, column half (warp - 2) / 4).
@@ -56,7 +58,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) xstep_int8_kernel(const __grid_co
     const int slot = blockIdx.z;
     const int p0 = tile.x, q0 = tile.y;
     const bool a_in_b = tile.w != 0;
-    const int nkb = (int)((a.klen + KF - 1) / KF);
+    // this CTA's segment: stages [kb0, kb1) of the slot, a whole number of chunks
+    const int nkb_all = (int)((a.klen + KF - 1) / KF);
+    const int seg_stages = (int)a.seg_frames / KF;
+    const int kb0 = blockIdx.y * seg_stages;
+    const int kb1 = min(nkb_all, kb0 + seg_stages);
+    const int nkb = max(0, kb1 - kb0);
     const int nchunks = (nkb + CHUNK_STAGES - 1) / CHUNK_STAGES;
     const long long lim = (long long)a.spin_limit * 1000LL;
 
@@ -94,11 +101,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) xstep_int8_kernel(const __grid_co
                 unsigned char* st = ring + stage * STAGE_BYTES;
                 uint64_t* fb = &S.full[stage];
                 tc::mbar_arrive_expect_tx(fb, bytes);
-                tc::tma_load_3d(st, &tmap, fb, kb * KF, q0, zr);
-                tc::tma_load_3d(st + PLANE, &tmap, fb, kb * KF, q0, zi);
+                const int kx = (kb0 + kb) * KF;
+                tc::tma_load_3d(st, &tmap, fb, kx, q0, zr);
+                tc::tma_load_3d(st + PLANE, &tmap, fb, kx, q0, zi);
                 if (!a_in_b) {
-                    tc::tma_load_3d(st + 2 * PLANE, &tmap, fb, kb * KF, p0, zr);
-                    tc::tma_load_3d(st + 3 * PLANE, &tmap, fb, kb * KF, p0, zi);
+                    tc::tma_load_3d(st + 2 * PLANE, &tmap, fb, kx, p0, zr);
+                    tc::tma_load_3d(st + 3 * PLANE, &tmap, fb, kx, p0, zi);
                 }
                 issued_phase[stage] = (int)phase;
                 if (++stage == STAGES) {
@@ -172,7 +180,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) xstep_int8_kernel(const __grid_co
         long long* ob = reinterpret_cast<long long*>(a.out + (long long)slot * a.out_stride);
         uint32_t cphase = 0;
         int since_flush = 0;
-        bool flushed_once = false;
         for (int ch = 0; ch < nchunks && !*abort; ++ch) {
             bool ok = tc::mbar_wait(&S.acc_full, cphase, abort, a.status, 16, lim);
             if (!__all_sync(0xffffffffu, ok)) break;
@@ -202,7 +209,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) xstep_int8_kernel(const __grid_co
             ++since_flush;
             if (since_flush == FLUSH_CHUNKS || ch == nchunks - 1) {
                 // add the int32 sums into the int64 MWAX_ORDER output
-                const bool store = !flushed_once && a.first_store;
 #pragma unroll 1
                 for (int cb = 0; cb < 2; ++cb) {
                     const int col = half * 64 + cb * 32;
@@ -216,21 +222,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) xstep_int8_kernel(const __grid_co
                             const int q = q0 + col + i;
                             if (q < a.n && ti <= (q >> 1)) {
                                 const int pol = ((p & 1) << 1) | (q & 1);
-                                long long* o = ob + (baseline_of(ti, q >> 1, a.T) * 4 + pol) * 2;
+                                unsigned long long* o = reinterpret_cast<unsigned long long*>(
+                                    ob + (baseline_of(ti, q >> 1, a.T) * 4 + pol) * 2);
                                 const long long vr = (long long)(int)re[i];
                                 const long long vi = (p == q) ? 0LL : (long long)(int)im[i];
-                                if (store) {
-                                    o[0] = vr;
-                                    o[1] = vi;
-                                } else {
-                                    o[0] += vr;
-                                    o[1] += vi;
-                                }
+                                atomicAdd(o, (unsigned long long)vr);   // two's complement add
+                                if (vi != 0) atomicAdd(o + 1, (unsigned long long)vi);
                             }
                         }
                     }
                 }
-                flushed_once = true;
                 since_flush = 0;
             }
         }
@@ -248,7 +249,8 @@ constexpr size_t i8_smem_bytes() { return 1024 + STAGES * STAGE_BYTES + sizeof(I
 
 }  // namespace
 
-cudaError_t launch_xstep_int8(const CUtensorMap& map, const XArgs& a, int n_tiles, int slots, cudaStream_t s)
+cudaError_t launch_xstep_int8(const CUtensorMap& map, const XArgs& a, int n_tiles, int segments, int slots,
+                              cudaStream_t s)
 {
     static bool attr_done = false;
     const size_t smem = i8_smem_bytes();
@@ -257,7 +259,7 @@ cudaError_t launch_xstep_int8(const CUtensorMap& map, const XArgs& a, int n_tile
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
-    dim3 grid((unsigned)n_tiles, 1u, (unsigned)slots);
+    dim3 grid((unsigned)n_tiles, (unsigned)segments, (unsigned)slots);
     xstep_int8_kernel<<<grid, NTHREADS, smem, s>>>(map, a);
     return cudaGetLastError();
 }

@@ -44,10 +44,24 @@ struct mwax_plan {
     int4* tiles = nullptr;
     int n_tiles = 0;
     int* status = nullptr;
+    int* counter = nullptr;   // work-item counter of the persistent X-step
     float out_scale = 1.0f, post_scale = 1.0f;
     bool tensor_cores = false;   // tcgen05 X-step (FP16 / FP8 / INT8) vs CUDA-core FP32
     int tile = 64;               // paths per tile side of the X-step
     CUtensorMap tmap;            // operand planes, for the tcgen05 X-step
+
+    // host copies of the tables (work-item costs) and the tcgen05 item lists by slot count
+    std::vector<int4> h_tiles;
+    std::vector<RunInfo> h_runs;
+    std::vector<Group> h_groups;
+    std::vector<float> h_gain;
+    struct ItemList {
+        long long key;
+        XItem* items;
+        int* offs;
+        int workers;
+    };
+    std::vector<ItemList> item_lists;   // per (slot count, frames) of a launch
 
     // host-input path
     int8_t* dvolt = nullptr;
@@ -175,8 +189,13 @@ void free_plan(mwax_plan* p)
     cudaFree(p->runs);
     cudaFree(p->tiles);
     cudaFree(p->status);
+    cudaFree(p->counter);
     cudaFree(p->dvolt);
     cudaFree(p->dout);
+    for (auto& it : p->item_lists) {
+        cudaFree(it.items);
+        cudaFree(it.offs);
+    }
     for (auto e : p->events) cudaEventDestroy(e);
     for (auto e : p->ev_pool) cudaEventDestroy(e);
     for (auto& u : p->ev_used) {
@@ -333,13 +352,16 @@ mwax_status setup(mwax_plan& p)
             for (int j = i; j < p.n; j += 64) tiles.push_back(make_int4(i, j, 64, i == j ? 1 : 0));
     }
     p.n_tiles = (int)tiles.size();
+    p.h_tiles = tiles;
+    p.h_groups = groups;
+    p.h_gain = gain;
     MWAX_CUDA(cudaMalloc(&p.tiles, sizeof(int4) * tiles.size()));
     MWAX_CUDA(cudaMemcpy(p.tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice));
 
     // runs of output channels: enough CTAs for several waves (1 resident CTA per SM for
     // the tensor-core kernel, 2 for the CUDA-core one), at least 4 channels per run
     const long long ctas_wo_runs = (long long)p.n_tiles * p.slots;
-    const long long want_ctas = p.tensor_cores ? 4LL * 148 : 8LL * 148;
+    const long long want_ctas = p.tensor_cores ? 6LL * 148 : 8LL * 148;
     int want_runs = (int)std::max<long long>(1, (want_ctas + ctas_wo_runs - 1) / ctas_wo_runs);
     int run_len = std::max(4, (p.M + want_runs - 1) / want_runs);
     run_len = std::min(run_len, p.M);
@@ -361,11 +383,81 @@ mwax_status setup(mwax_plan& p)
         runs.push_back(r);
     }
     p.n_runs = (int)runs.size();
+    p.h_runs = runs;
     MWAX_CUDA(cudaMalloc(&p.runs, sizeof(RunInfo) * runs.size()));
     MWAX_CUDA(cudaMemcpy(p.runs, runs.data(), sizeof(RunInfo) * runs.size(), cudaMemcpyHostToDevice));
 
+    MWAX_CUDA(cudaMalloc(&p.counter, sizeof(int)));
     MWAX_CUDA(cudaMalloc(&p.status, sizeof(int)));
     MWAX_CUDA(cudaMemset(p.status, 0, sizeof(int)));
+    return MWAX_OK;
+}
+
+}  // namespace
+
+// Work items of one tensor-core X launch of plan p (as job `job`), with a cost estimate
+// (MMA volume: active ultrafine channels x frame blocks x window width) for ordering.
+void plan_items(const mwax_plan& p, int job, long long nslots, long long klen, std::vector<std::pair<double, XItem>>& out)
+{
+    const int KF = (p.prec == MWAX_FP8) ? 64 : 32;
+    const double nkb = (double)((klen + KF - 1) / KF);
+    for (int r = 0; r < p.n_runs; ++r) {
+        const RunInfo& run = p.h_runs[r];
+        int bins = 0;
+        for (int g = run.g0; g < run.g1; ++g) {
+            const Group& gr = p.h_groups[g];
+            if (!((gr.ja >= run.j0 && gr.ja < run.j1) || (gr.jb >= run.j0 && gr.jb < run.j1))) continue;
+            for (int c = gr.c0; c < gr.c1; ++c) bins += p.h_gain[c] > 0.0f;
+        }
+        for (int t = 0; t < p.n_tiles; ++t) {
+            const int4 tl = p.h_tiles[t];
+            const double cost = bins * nkb * tl.z * (tl.w ? 1.0 : 1.25) + 1.0;
+            for (long long sl = 0; sl < nslots; ++sl) out.push_back({cost, XItem{job, t, r, (int)sl}});
+        }
+    }
+}
+
+// Items in decreasing estimated cost: claimed in this order, the big ones start first.
+void sort_items(std::vector<std::pair<double, XItem>>& v, std::vector<XItem>& order)
+{
+    std::stable_sort(v.begin(), v.end(), [](const std::pair<double, XItem>& a, const std::pair<double, XItem>& b) {
+        return a.first > b.first;
+    });
+    order.resize(v.size());
+    for (size_t i = 0; i < v.size(); ++i) order[i] = v[i].second;
+}
+
+int sm_count()
+{
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+namespace {
+
+// Device item list of a single-plan launch, most expensive first (cached per slot count
+// and frames).
+mwax_status single_items(mwax_plan* p, long long nslots, long long klen, XItem** items, int* n)
+{
+    const long long key = nslots * 1000003LL + klen;
+    for (auto& e : p->item_lists)
+        if (e.key == key) {
+            *items = e.items;
+            *n = e.workers;
+            return MWAX_OK;
+        }
+    std::vector<std::pair<double, XItem>> v;
+    plan_items(*p, 0, nslots, klen, v);
+    std::vector<XItem> order;
+    sort_items(v, order);
+    XItem* d = nullptr;
+    MWAX_CUDA(cudaMalloc(&d, sizeof(XItem) * std::max<size_t>(1, order.size())));
+    MWAX_CUDA(cudaMemcpy(d, order.data(), sizeof(XItem) * order.size(), cudaMemcpyHostToDevice));
+    p->item_lists.push_back({key, d, nullptr, (int)order.size()});
+    *items = d;
+    *n = (int)order.size();
     return MWAX_OK;
 }
 
@@ -410,7 +502,20 @@ mwax_status enqueue(mwax_plan* p, const int8_t* volt, bool have_delay, char* out
             const long long nframes = (p->chunks == 1) ? nslots * p->K : klen;
             const long long m_begin = w0 * p->K + kbeg;
             if (wait_events) {
-                // host-input path: wait for the copy of the last block this launch reads
+                // host copies of the tables (work-item costs) and the tcgen05 item lists by slot count
+    std::vector<int4> h_tiles;
+    std::vector<RunInfo> h_runs;
+    std::vector<Group> h_groups;
+    std::vector<float> h_gain;
+    struct ItemList {
+        long long key;
+        XItem* items;
+        int* offs;
+        int workers;
+    };
+    std::vector<ItemList> item_lists;   // per (slot count, frames) of a launch
+
+    // host-input path: wait for the copy of the last block this launch reads
                 const long long last_sample = (m_begin + nframes) * p->N - 1;
                 const long long blk = last_sample / p->bs;
                 MWAX_CUDA(cudaStreamWaitEvent(s, wait_events[blk / events_per_block], 0));
@@ -484,10 +589,16 @@ mwax_status enqueue(mwax_plan* p, const int8_t* volt, bool have_delay, char* out
                 const int nseg = (int)((chunks256 + seg_chunks - 1) / seg_chunks);
                 MWAX_CUDA(timed(p, 2, [&] { return launch_xstep_int8(p->tmap, xa, p->n_tiles, nseg, (int)nslots, s); }));
             } else if (p->tensor_cores) {
-                const int op = (p->prec == MWAX_FP8) ? 1 : 0;
-                MWAX_CUDA(timed(p, 2, [&] {
-                    return launch_xstep_tc(op, p->tmap, xa, p->n_tiles, p->n_runs, (int)nslots, s);
-                }));
+                XItem* items = nullptr;
+                int n_items = 0;
+                mwax_status st = single_items(p, nslots, klen, &items, &n_items);
+                if (st != MWAX_OK) return st;
+                static thread_local XLaunch L;   // large: keep it off the stack
+                L.n_jobs = 1;
+                L.jobs[0].tmap = p->tmap;
+                L.jobs[0].a = xa;
+                L.jobs[0].op = (p->prec == MWAX_FP8) ? 1 : 0;
+                MWAX_CUDA(timed(p, 2, [&] { return launch_xstep_tc(L, items, n_items, p->counter, p->status, s); }));
             } else {
                 MWAX_CUDA(timed(p, 2, [&] { return launch_xstep_simt(xa, p->n_tiles, p->n_runs, (int)nslots, s); }));
             }

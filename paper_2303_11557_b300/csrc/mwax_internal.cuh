@@ -85,6 +85,26 @@ struct XArgs {
     unsigned int spin_limit;
 };
 
+// One launch's worth of tensor-core X-step work for one plan ("job"): its operand tensor
+// map and arguments, resident in device memory.
+struct alignas(64) XJob {
+    CUtensorMap tmap;
+    XArgs a;
+    int op;   // 0 = FP16 (kind::f16), 1 = e4m3 (kind::f8f6f4)
+};
+
+// One work item of the persistent tensor-core X-step.
+struct XItem {
+    int job, tile, run, slot;
+};
+
+// The jobs of one persistent X-step launch, passed by value (kernel parameter space).
+constexpr int kMaxJobs = 40;
+struct XLaunch {
+    int n_jobs;
+    XJob jobs[kMaxJobs];
+};
+
 // Launchers (each returns the cudaError_t of its launch).
 cudaError_t launch_fstep(int N, int out_kind, const FArgs& a, cudaStream_t s);
 
@@ -98,7 +118,7 @@ cudaError_t launch_init_output(char* out, long long n_ints, long long vis_set_by
 cudaError_t launch_xstep_simt(const XArgs& a, int n_tiles, int n_runs, int slots, cudaStream_t s);
 cudaError_t make_operand_tmap(CUtensorMap* map, const void* Y, int elem_bytes, long long Kpad, int n,
                               long long planes);
-cudaError_t launch_xstep_tc(int op, const CUtensorMap& map, const XArgs& a, int n_tiles, int n_runs, int slots,
+cudaError_t launch_xstep_tc(const XLaunch& L, const XItem* items, int n_items, int* counter, int* status,
                             cudaStream_t s);
 int build_tc_tiles(int n, int4* out, int cap);
 cudaError_t launch_xstep_int8(const CUtensorMap& map, const XArgs& a, int n_tiles, int segments, int slots,

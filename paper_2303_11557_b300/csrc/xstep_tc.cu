@@ -8,8 +8,14 @@
 // (the last with the instruction's A-negate bit).  Operands are K-major planes
 // Y[slot][c][plane][p][Kpad] loaded by TMA with 64-byte swizzle.
 //
-// CTA = one tile x one run of output channels x one slot.  A tile is 128 rows (paths p)
-// by a window of 256 (or, at the right edge, 128) columns (paths q).  Windows start at
+// The kernel is persistent: one CTA per SM claims work items (job, tile, run of output
+// channels, slot) from a global counter, most expensive first (the host sorts the list
+// by estimated cost); the producer warp claims and publishes each item index to the MMA
+// and epilogue warps through a small shared-memory ring.  A job is one plan's launch (its operand
+// tensor map and arguments), so one launch serves a single plan or a batch of coarse
+// channels of mixed shapes and precisions.  The TMA ring, MMA and epilogue pipelines run
+// on across item boundaries.  A tile is 128 rows (paths p) by a window of 256 (or, at
+// the right edge, 128) columns (paths q).  Windows start at
 // the tile's own diagonal, so for those the 128 A rows are the first 128 rows of the B
 // window and only B is loaded; elsewhere A and B are loaded separately.  For each group of
 // ultrafine channels (pre-weighted by sqrt(w) in the F-step) the MMAs of every frame of
@@ -38,11 +44,16 @@ constexpr int NTHREADS = 320;
 constexpr int EPI_THREADS = 256;
 constexpr uint32_t TMEM_COLS = 512;
 
+constexpr int IRING = 4;   // claimed work items in flight between the roles
+
 struct TcSmem {
     uint64_t full[STAGES];
     uint64_t empty[STAGES];
     uint64_t acc_full;
     uint64_t acc_empty;
+    uint64_t item_full[IRING];    // producer -> MMA + epilogue: item index published
+    uint64_t item_empty[IRING];   // MMA + epilogue -> producer: slot free again
+    int item[IRING];              // claimed item index, -1 = no more work
     uint32_t tmem_base;
     int abort;
 };
@@ -52,27 +63,23 @@ __device__ __forceinline__ long long baseline_of(int i, int j, int T)
     return (long long)i * (2 * T - i + 1) / 2 + (j - i);
 }
 
-// OP: 0 = FP16 (kind::f16, 16 frames per MMA), 1 = e4m3 (kind::f8f6f4, 32 frames per MMA)
-template <int OP>
-__global__ void __launch_bounds__(NTHREADS, 1) xstep_tc_kernel(const __grid_constant__ CUtensorMap tmap, const XArgs a)
+__device__ __forceinline__ bool item_feeds(const Group& gr, const RunInfo& run)
 {
-    constexpr int ELEM = (OP == 0) ? 2 : 1;
-    constexpr int KF = ROWB / ELEM;           // frames per stage
-    constexpr int NSTEPS = ROWB / 32;         // MMA K-steps (32 bytes of K) per stage
+    return (gr.ja >= run.j0 && gr.ja < run.j1) || (gr.jb >= run.j0 && gr.jb < run.j1);
+}
 
+__global__ void __launch_bounds__(NTHREADS, 1)
+    xstep_tc_kernel(const __grid_constant__ XLaunch L, const XItem* __restrict__ items, int n_items, int* counter,
+                    int* status, unsigned int spin_limit)
+{
+    const XJob* jobs = L.jobs;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* ring = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     TcSmem& S = *reinterpret_cast<TcSmem*>(ring + STAGES * STAGE_BYTES);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int4 tile = a.tiles[blockIdx.x];
-    const RunInfo run = a.runs[blockIdx.y];
-    const int slot = blockIdx.z;
-    const int p0 = tile.x, q0 = tile.y, nq = tile.z;
-    const bool a_in_b = tile.w != 0;
-    const int nkb = (int)((a.klen + KF - 1) / KF);
-    const long long lim = (long long)a.spin_limit * 1000LL;   // cycles
+    const long long lim = (long long)spin_limit * 1000LL;   // cycles
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -81,9 +88,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) xstep_tc_kernel(const __grid_cons
         }
         tc::mbar_init(&S.acc_full, 1);
         tc::mbar_init(&S.acc_empty, EPI_THREADS);
+        for (int r = 0; r < IRING; ++r) {
+            tc::mbar_init(&S.item_full[r], 1);
+            tc::mbar_init(&S.item_empty[r], 1 + EPI_THREADS);
+        }
         S.abort = 0;
         tc::fence_mbar_init();
-        tc::prefetch_tmap(&tmap);
     }
     if (warp == 1) {
         tc::tmem_alloc(&S.tmem_base, TMEM_COLS);
@@ -102,30 +112,55 @@ __global__ void __launch_bounds__(NTHREADS, 1) xstep_tc_kernel(const __grid_cons
             uint32_t phase = 0;
             int issued_phase[STAGES];
             for (int s = 0; s < STAGES; ++s) issued_phase[s] = -1;
-            const int nbox = nq / TM;   // 128-row boxes of the B window
-            const uint32_t bytes = (uint32_t)(2 * nbox * A_PLANE + (a_in_b ? 0 : 2 * A_PLANE));
-            for (int g = run.g0; g < run.g1 && !*abort; ++g) {
-                const Group gr = a.groups[g];
-                for (int c = gr.c0; c < gr.c1 && !*abort; ++c) {
-                    if (__ldg(&a.gain[c]) == 0.0f) continue;
-                    const int zr = (slot * a.N + c) * 2, zi = zr + 1;
-                    for (int kb = 0; kb < nkb; ++kb) {
-                        if (!tc::mbar_wait(&S.empty[stage], phase ^ 1, abort, a.status, 2, lim)) break;
-                        unsigned char* st = ring + stage * STAGE_BYTES;
-                        uint64_t* fb = &S.full[stage];
-                        tc::mbar_arrive_expect_tx(fb, bytes);
-                        for (int b = 0; b < nbox; ++b) {
-                            tc::tma_load_3d(st + b * A_PLANE, &tmap, fb, kb * KF, q0 + b * TM, zr);
-                            tc::tma_load_3d(st + B_PLANE + b * A_PLANE, &tmap, fb, kb * KF, q0 + b * TM, zi);
-                        }
-                        if (!a_in_b) {
-                            tc::tma_load_3d(st + 2 * B_PLANE, &tmap, fb, kb * KF, p0, zr);
-                            tc::tma_load_3d(st + 2 * B_PLANE + A_PLANE, &tmap, fb, kb * KF, p0, zi);
-                        }
-                        issued_phase[stage] = (int)phase;
-                        if (++stage == STAGES) {
-                            stage = 0;
-                            phase ^= 1;
+            int ir = 0;
+            uint32_t iphase = 0;
+            for (;;) {
+                // claim the next item and publish it (-1 = done) to the other roles
+                if (!tc::mbar_wait(&S.item_empty[ir], iphase ^ 1, abort, status, 32, lim)) break;
+                const int it = atomicAdd(counter, 1);
+                S.item[ir] = (it < n_items) ? it : -1;
+                tc::mbar_arrive(&S.item_full[ir]);
+                if (++ir == IRING) {
+                    ir = 0;
+                    iphase ^= 1;
+                }
+                if (it >= n_items || *abort) break;
+                const XItem w = items[it];
+                const XJob* J = jobs + w.job;
+                const XArgs& a = J->a;
+                const CUtensorMap* tm = &J->tmap;
+                tc::prefetch_tmap(tm);
+                const int4 tile = a.tiles[w.tile];
+                const RunInfo run = a.runs[w.run];
+                const int KF = (J->op == 0) ? 32 : 64;   // frames per 64-byte operand row
+                const int nkb = (int)((a.klen + KF - 1) / KF);
+                const int nbox = tile.z / TM;             // 128-row boxes of the B window
+                const bool a_in_b = tile.w != 0;
+                const uint32_t bytes = (uint32_t)(2 * nbox * A_PLANE + (a_in_b ? 0 : 2 * A_PLANE));
+                for (int g = run.g0; g < run.g1 && !*abort; ++g) {
+                    const Group gr = a.groups[g];
+                    if (!item_feeds(gr, run)) continue;
+                    for (int c = gr.c0; c < gr.c1 && !*abort; ++c) {
+                        if (__ldg(&a.gain[c]) == 0.0f) continue;
+                        const int zr = (w.slot * a.N + c) * 2, zi = zr + 1;
+                        for (int kb = 0; kb < nkb; ++kb) {
+                            if (!tc::mbar_wait(&S.empty[stage], phase ^ 1, abort, status, 2, lim)) break;
+                            unsigned char* st = ring + stage * STAGE_BYTES;
+                            uint64_t* fb = &S.full[stage];
+                            tc::mbar_arrive_expect_tx(fb, bytes);
+                            for (int b = 0; b < nbox; ++b) {
+                                tc::tma_load_3d(st + b * A_PLANE, tm, fb, kb * KF, tile.y + b * TM, zr);
+                                tc::tma_load_3d(st + B_PLANE + b * A_PLANE, tm, fb, kb * KF, tile.y + b * TM, zi);
+                            }
+                            if (!a_in_b) {
+                                tc::tma_load_3d(st + 2 * B_PLANE, tm, fb, kb * KF, tile.x, zr);
+                                tc::tma_load_3d(st + 2 * B_PLANE + A_PLANE, tm, fb, kb * KF, tile.x, zi);
+                            }
+                            issued_phase[stage] = (int)phase;
+                            if (++stage == STAGES) {
+                                stage = 0;
+                                phase ^= 1;
+                            }
                         }
                     }
                 }
@@ -143,54 +178,76 @@ __global__ void __launch_bounds__(NTHREADS, 1) xstep_tc_kernel(const __grid_cons
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t id = tc::idesc(0, TM, nq, false), id_neg = tc::idesc(0, TM, nq, true);
             int stage = 0;
             uint32_t phase = 0, gphase = 0;
             const uint32_t sbase = tc::smem_u32(ring);
             bool issued = false;
             const uint32_t d_re = tmem, d_im = tmem + 256;
-            for (int g = run.g0; g < run.g1 && !*abort; ++g) {
-                const Group gr = a.groups[g];
-                if (!tc::mbar_wait(&S.acc_empty, gphase ^ 1, abort, a.status, 4, lim)) break;
-                tc::fence_after();
-                bool first = true;
-                for (int c = gr.c0; c < gr.c1 && !*abort; ++c) {
-                    if (__ldg(&a.gain[c]) == 0.0f) continue;
-                    for (int kb = 0; kb < nkb; ++kb) {
-                        if (!tc::mbar_wait(&S.full[stage], phase, abort, a.status, 8, lim)) break;
-                        tc::fence_after();
-                        const uint32_t st = sbase + stage * STAGE_BYTES;
-                        const uint64_t dbr = tc::sw64_desc(st), dbi = tc::sw64_desc(st + B_PLANE);
-                        const uint64_t dar = a_in_b ? dbr : tc::sw64_desc(st + 2 * B_PLANE);
-                        const uint64_t dai = a_in_b ? dbi : tc::sw64_desc(st + 2 * B_PLANE + A_PLANE);
+            int ir = 0;
+            uint32_t iphase = 0;
+            for (;;) {
+                if (!tc::mbar_wait(&S.item_full[ir], iphase, abort, status, 32, lim)) break;
+                const int it = S.item[ir];
+                tc::mbar_arrive(&S.item_empty[ir]);
+                if (++ir == IRING) {
+                    ir = 0;
+                    iphase ^= 1;
+                }
+                if (it < 0 || *abort) break;
+                const XItem w = items[it];
+                const XJob* J = jobs + w.job;
+                const XArgs& a = J->a;
+                const int op = J->op;
+                const int4 tile = a.tiles[w.tile];
+                const RunInfo run = a.runs[w.run];
+                const int KF = (op == 0) ? 32 : 64;
+                const int nkb = (int)((a.klen + KF - 1) / KF);
+                const bool a_in_b = tile.w != 0;
+                const uint32_t id = tc::idesc(0, TM, tile.z, false), id_neg = tc::idesc(0, TM, tile.z, true);
+                for (int g = run.g0; g < run.g1 && !*abort; ++g) {
+                    const Group gr = a.groups[g];
+                    if (!item_feeds(gr, run)) continue;
+                    if (!tc::mbar_wait(&S.acc_empty, gphase ^ 1, abort, status, 4, lim)) break;
+                    tc::fence_after();
+                    bool first = true;
+                    for (int c = gr.c0; c < gr.c1 && !*abort; ++c) {
+                        if (__ldg(&a.gain[c]) == 0.0f) continue;
+                        for (int kb = 0; kb < nkb; ++kb) {
+                            if (!tc::mbar_wait(&S.full[stage], phase, abort, status, 8, lim)) break;
+                            tc::fence_after();
+                            const uint32_t st = sbase + stage * STAGE_BYTES;
+                            const uint64_t dbr = tc::sw64_desc(st), dbi = tc::sw64_desc(st + B_PLANE);
+                            const uint64_t dar = a_in_b ? dbr : tc::sw64_desc(st + 2 * B_PLANE);
+                            const uint64_t dai = a_in_b ? dbi : tc::sw64_desc(st + 2 * B_PLANE + A_PLANE);
 #pragma unroll
-                        for (int k = 0; k < NSTEPS; ++k) {
-                            const uint64_t off = (uint64_t)(k * 32) >> 4;   // 32 bytes of K per step
-                            const uint32_t acc = first ? 0u : 1u;
-                            first = false;
-                            if (OP == 0) {
-                                tc::mma_f16(d_re, dar + off, dbr + off, id, acc);
-                                tc::mma_f16(d_re, dai + off, dbi + off, id, 1u);
-                                tc::mma_f16(d_im, dai + off, dbr + off, id, acc);
-                                tc::mma_f16(d_im, dar + off, dbi + off, id_neg, 1u);
-                            } else {
-                                tc::mma_f8(d_re, dar + off, dbr + off, id, acc);
-                                tc::mma_f8(d_re, dai + off, dbi + off, id, 1u);
-                                tc::mma_f8(d_im, dai + off, dbr + off, id, acc);
-                                tc::mma_f8(d_im, dar + off, dbi + off, id_neg, 1u);
+                            for (int k = 0; k < ROWB / 32; ++k) {
+                                const uint64_t off = (uint64_t)(k * 32) >> 4;   // 32 bytes of K per step
+                                const uint32_t acc = first ? 0u : 1u;
+                                first = false;
+                                if (op == 0) {
+                                    tc::mma_f16(d_re, dar + off, dbr + off, id, acc);
+                                    tc::mma_f16(d_re, dai + off, dbi + off, id, 1u);
+                                    tc::mma_f16(d_im, dai + off, dbr + off, id, acc);
+                                    tc::mma_f16(d_im, dar + off, dbi + off, id_neg, 1u);
+                                } else {
+                                    tc::mma_f8(d_re, dar + off, dbr + off, id, acc);
+                                    tc::mma_f8(d_re, dai + off, dbi + off, id, 1u);
+                                    tc::mma_f8(d_im, dai + off, dbr + off, id, acc);
+                                    tc::mma_f8(d_im, dar + off, dbi + off, id_neg, 1u);
+                                }
+                            }
+                            issued = true;
+                            tc::mma_commit(&S.empty[stage]);
+                            if (++stage == STAGES) {
+                                stage = 0;
+                                phase ^= 1;
                             }
                         }
-                        issued = true;
-                        tc::mma_commit(&S.empty[stage]);
-                        if (++stage == STAGES) {
-                            stage = 0;
-                            phase ^= 1;
-                        }
                     }
+                    if (*abort) break;
+                    tc::mma_commit(&S.acc_full);
+                    gphase ^= 1;
                 }
-                if (*abort) break;
-                tc::mma_commit(&S.acc_full);
-                gphase ^= 1;
             }
             if (*abort && issued) {
                 // wait for the MMAs in flight before TMEM is released
@@ -204,71 +261,97 @@ __global__ void __launch_bounds__(NTHREADS, 1) xstep_tc_kernel(const __grid_cons
         // ------------------------------------------------------------ epilogue
         const int g4 = warp & 3;                 // TMEM lane quarter of this warp
         const int half = (warp - 2) >> 2;        // column half of the window
-        const int p = p0 + g4 * 32 + lane;
-        const int ti = p >> 1;
-        const bool cols = half * 128 < nq;
         uint32_t gphase = 0;
-        char* obase = a.out + (long long)slot * a.out_stride;
-        for (int g = run.g0; g < run.g1 && !*abort; ++g) {
-            const Group gr = a.groups[g];
-            const bool use_a = gr.ja >= run.j0 && gr.ja < run.j1;
-            const bool use_b = gr.jb >= run.j0 && gr.jb < run.j1;
-            bool ok = tc::mbar_wait(&S.acc_full, gphase, abort, a.status, 16, lim);
-            if (!__all_sync(0xffffffffu, ok)) break;   // keep the warp's TMEM loads uniform
-            tc::fence_after();
-            if (cols) {
-                float sp = a.post_scale;
-                const float* qscale = nullptr;
-                if (OP == 1) {
-                    const float* sc = a.scale + ((long long)slot * a.n_groups + g) * a.n;
-                    sp *= (p < a.n) ? e4m3_scale(__ldg(sc + p)) : 0.0f;
-                    qscale = sc;
-                }
+        int ir = 0;
+        uint32_t iphase = 0;
+        for (;;) {
+            bool okit = tc::mbar_wait(&S.item_full[ir], iphase, abort, status, 32, lim);
+            if (!__all_sync(0xffffffffu, okit)) break;
+            const int it = S.item[ir];
+            tc::mbar_arrive(&S.item_empty[ir]);
+            if (++ir == IRING) {
+                ir = 0;
+                iphase ^= 1;
+            }
+            if (it < 0 || *abort) break;
+            const XItem w = items[it];
+            const XJob* J = jobs + w.job;
+            const XArgs& a = J->a;
+            const int op = J->op;
+            const int4 tile = a.tiles[w.tile];
+            const RunInfo run = a.runs[w.run];
+            const int p0 = tile.x, q0 = tile.y, nq = tile.z;
+            const int p = p0 + g4 * 32 + lane;
+            const int ti = p >> 1;
+            const bool cols = half * 128 < nq;
+            char* obase = a.out + (long long)w.slot * a.out_stride;
+            float2* ob = reinterpret_cast<float2*>(obase);
+            const int T = a.T, M = a.M, n = a.n, first_store = a.first_store;
+            for (int g = run.g0; g < run.g1 && !*abort; ++g) {
+                const Group gr = a.groups[g];
+                if (!item_feeds(gr, run)) continue;
+                const bool use_a = gr.ja >= run.j0 && gr.ja < run.j1;
+                const bool use_b = gr.jb >= run.j0 && gr.jb < run.j1;
+                bool ok = tc::mbar_wait(&S.acc_full, gphase, abort, status, 16, lim);
+                if (!__all_sync(0xffffffffu, ok)) break;   // keep the warp's TMEM loads uniform
+                tc::fence_after();
+                if (cols) {
+                    float sp = a.post_scale;
+                    const float* qscale = nullptr;
+                    if (op == 1) {
+                        const float* sc = a.scale + ((long long)w.slot * a.n_groups + g) * n;
+                        sp *= (p < n) ? e4m3_scale(__ldg(sc + p)) : 0.0f;
+                        qscale = sc;
+                    }
 #pragma unroll 1
-                for (int ch = 0; ch < 4; ++ch) {
-                    const int col = half * 128 + ch * 32;
-                    uint32_t vr[32], vi[32];
-                    const uint32_t taddr = tmem + ((uint32_t)(g4 * 32) << 16) + col;
-                    tc::tmem_ld32(taddr, vr);
-                    tc::tmem_ld32(taddr + 256, vi);
-                    tc::tmem_wait_ld();
-                    if (p >= a.n) continue;
-                    // 8 columns at a time: issue every load of the old values before any
-                    // store, so the read-modify-writes overlap instead of serialising
-                    float2* ob = reinterpret_cast<float2*>(obase);
+                    for (int ch = 0; ch < 4; ++ch) {
+                        const int col = half * 128 + ch * 32;
+                        uint32_t vr[32], vi[32];
+                        const uint32_t taddr = tmem + ((uint32_t)(g4 * 32) << 16) + col;
+                        tc::tmem_ld32(taddr, vr);
+                        tc::tmem_ld32(taddr + 256, vi);
+                        tc::tmem_wait_ld();
+                        if (p >= n) continue;
+                        // 8 columns at a time: issue every load of the old values before any
+                        // store, so the read-modify-writes overlap instead of serialising
 #pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        int off[8];
-                        float2 va[8], vb[8];
+                        for (int h = 0; h < 4; ++h) {
+                            int off[8];
+                            float2 va[8], vb[8];
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const int q = q0 + col + h * 8 + i;
-                            const int tj = q >> 1;
-                            const bool ok = q < a.n && ti <= tj;
-                            const int pol = ((p & 1) << 1) | (q & 1);
-                            off[i] = ok ? (int)(baseline_of(ti, tj, a.T) * a.M * 4 + pol) : -1;
-                            va[i] = (ok && use_a && !(gr.first_a & a.first_store)) ? ob[off[i] + gr.ja * 4] : make_float2(0.f, 0.f);
-                            vb[i] = (ok && use_b && !(gr.first_b & a.first_store)) ? ob[off[i] + gr.jb * 4] : make_float2(0.f, 0.f);
-                        }
+                            for (int i = 0; i < 8; ++i) {
+                                const int q = q0 + col + h * 8 + i;
+                                const int tj = q >> 1;
+                                const bool okq = q < n && ti <= tj;
+                                const int pol = ((p & 1) << 1) | (q & 1);
+                                off[i] = okq ? (int)(baseline_of(ti, tj, T) * M * 4 + pol) : -1;
+                                va[i] = (okq && use_a && !(gr.first_a & first_store)) ? ob[off[i] + gr.ja * 4]
+                                                                                      : make_float2(0.f, 0.f);
+                                vb[i] = (okq && use_b && !(gr.first_b & first_store)) ? ob[off[i] + gr.jb * 4]
+                                                                                      : make_float2(0.f, 0.f);
+                            }
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            if (off[i] < 0) continue;
-                            const int q = q0 + col + h * 8 + i;
-                            float s = sp;
-                            if (OP == 1) s *= e4m3_scale(__ldg(qscale + q));
-                            const float re = __uint_as_float(vr[h * 8 + i]) * s;
-                            const float im = (p == q) ? 0.0f : __uint_as_float(vi[h * 8 + i]) * s;
-                            if (use_a)
-                                ob[off[i] + gr.ja * 4] = make_float2(fmaf(gr.ca, re, va[i].x), fmaf(gr.ca, im, va[i].y));
-                            if (use_b)
-                                ob[off[i] + gr.jb * 4] = make_float2(fmaf(gr.cb, re, vb[i].x), fmaf(gr.cb, im, vb[i].y));
+                            for (int i = 0; i < 8; ++i) {
+                                if (off[i] < 0) continue;
+                                const int q = q0 + col + h * 8 + i;
+                                float s = sp;
+                                if (op == 1) s *= e4m3_scale(__ldg(qscale + q));
+                                const float re = __uint_as_float(vr[h * 8 + i]) * s;
+                                const float im = (p == q) ? 0.0f : __uint_as_float(vi[h * 8 + i]) * s;
+                                if (use_a)
+                                    ob[off[i] + gr.ja * 4] =
+                                        make_float2(fmaf(gr.ca, re, va[i].x), fmaf(gr.ca, im, va[i].y));
+                                if (use_b)
+                                    ob[off[i] + gr.jb * 4] =
+                                        make_float2(fmaf(gr.cb, re, vb[i].x), fmaf(gr.cb, im, vb[i].y));
+                            }
                         }
                     }
                 }
+                tc::fence_before();
+                tc::mbar_arrive(&S.acc_empty);
+                gphase ^= 1;
             }
-            tc::fence_before();
-            tc::mbar_arrive(&S.acc_empty);
-            gphase ^= 1;
         }
     }
 
@@ -315,29 +398,24 @@ cudaError_t make_operand_tmap(CUtensorMap* map, const void* Y, int elem_bytes, l
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t launch_xstep_tc(int op, const CUtensorMap& map, const XArgs& a, int n_tiles, int n_runs, int slots,
+cudaError_t launch_xstep_tc(const XLaunch& L, const XItem* items, int n_items, int* counter, int* status,
                             cudaStream_t s)
 {
-    static bool attr_done[2] = {false, false};
+    static bool attr_done = false;
     const size_t smem = tc_smem_bytes();
-    dim3 grid((unsigned)n_tiles, (unsigned)n_runs, (unsigned)slots);
-    if (op == 0) {
-        if (!attr_done[0]) {
-            cudaError_t e = cudaFuncSetAttribute(xstep_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem);
-            if (e != cudaSuccess) return e;
-            attr_done[0] = true;
-        }
-        xstep_tc_kernel<0><<<grid, NTHREADS, smem, s>>>(map, a);
-    } else {
-        if (!attr_done[1]) {
-            cudaError_t e = cudaFuncSetAttribute(xstep_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem);
-            if (e != cudaSuccess) return e;
-            attr_done[1] = true;
-        }
-        xstep_tc_kernel<1><<<grid, NTHREADS, smem, s>>>(map, a);
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(xstep_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
     }
+    if (n_items <= 0) return cudaSuccess;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    xstep_tc_kernel<<<n_items < sms ? n_items : sms, NTHREADS, smem, s>>>(L, items, n_items, counter, status,
+                                                                          2000000u);
     return cudaGetLastError();
 }
 

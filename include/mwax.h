@@ -158,6 +158,69 @@ mwax_status mwax_plan_sync(mwax_plan* plan);
 mwax_status mwax_plan_enable_timing(mwax_plan* plan, int enable);
 mwax_status mwax_plan_stage_times(mwax_plan* plan, double ms[3], long long launches[3]);
 
+/* ------------------------------------------------------------------ autotuning */
+
+/* Launch choices of a plan.  fstep_variant: 0 = two-pass radix-32 F-step kernel (built
+ * for N = 32..512; the generic kernel elsewhere), 1 = generic shared-memory Stockham
+ * kernel.  run_len: output channels per X-step work item (0 = chosen from the grid
+ * size).  window: column width of a tensor-core X-step tile, 128 or 256.  ms: device time
+ * of one call measured by the autotuner. */
+typedef struct {
+    int fstep_variant;
+    int run_len;
+    int window;
+    double ms;
+} mwax_tuning;
+
+/*
+ * Autotuner: runs the plan on the caller's buffers (same arguments as mwax_correlate)
+ * once per candidate choice (F-step variant x run length x tile window), times each
+ * with CUDA events on the plan's stream, and keeps the fastest.  Synchronous.  vis_out is
+ * overwritten with a valid result.  best (may be NULL) receives the choice and its time.
+ */
+mwax_status mwax_plan_autotune(mwax_plan* plan, const int8_t* voltages, const double* delay_poly, void* vis_out,
+                               mwax_tuning* best);
+/* Set or read a plan's launch choices (waits for the plan's stream before changing). */
+mwax_status mwax_plan_set_tuning(mwax_plan* plan, const mwax_tuning* tuning);
+mwax_status mwax_plan_get_tuning(const mwax_plan* plan, mwax_tuning* tuning);
+
+/* ------------------------------------------------------------------ batches */
+
+/*
+ * Batch of plans (e.g. many coarse channels of mixed tile counts, FFT lengths,
+ * integration times and precisions) correlated together on one stream.  Each call runs
+ * every plan once: per round, the plans' F-steps on auxiliary streams, then ONE
+ * persistent tcgen05 X-step launch over all FP16 / FP8 plans' work (one job per plan,
+ * work items claimed dynamically, most expensive first); FP32 and integer-mode plans run
+ * their own X-steps.  The paper processes one coarse channel per server (Sec. 2.1); a
+ * batch processes many on one GPU.  The batch references the plans (they must outlive it,
+ * stay on one device and not be used on their own while the batch runs) and uses the
+ * plans' workspaces.  Returns NULL on error.
+ */
+typedef struct mwax_batch mwax_batch;
+mwax_batch* mwax_batch_create(mwax_plan* const* plans, int n_plans);
+
+/* Stream of the batch's work (a cudaStream_t; NULL = legacy default stream). */
+mwax_status mwax_batch_set_stream(mwax_batch* batch, void* cuda_stream);
+
+/* CUDA graphs (default on): the first call runs eagerly; later calls capture the whole
+ * schedule once per set of buffer pointers and replay it with one graph launch. */
+mwax_status mwax_batch_set_graphs(mwax_batch* batch, int enable);
+
+/*
+ * One call of every plan: voltages[i], delay_poly[i] (device pointer or NULL; NULL array
+ * = no delays) and vis_out[i] are plan i's arguments as for mwax_correlate (device
+ * memory).  Asynchronous on the batch's stream.
+ */
+mwax_status mwax_batch_correlate(mwax_batch* batch, const int8_t* const* voltages, const double* const* delay_poly,
+                                 void* const* vis_out);
+
+/* Wait for the batch's stream; MWAX_ETIMEOUT if a bounded device wait gave up. */
+mwax_status mwax_batch_sync(mwax_batch* batch);
+
+/* Free the batch (not its plans).  NULL is a no-op. */
+void mwax_batch_destroy(mwax_batch* batch);
+
 /* Free the plan and its device workspace (waits for its stream first).  NULL is a no-op. */
 void mwax_plan_destroy(mwax_plan* plan);
 

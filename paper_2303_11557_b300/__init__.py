@@ -50,6 +50,15 @@ class _CInfo(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_size_t), ("precision", ctypes.c_int)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("fstep_variant", ctypes.c_int), ("run_len", ctypes.c_int), ("window", ctypes.c_int),
+                ("ms", ctypes.c_double)]
+
+    def __repr__(self):
+        return (f"Tuning(fstep_variant={self.fstep_variant}, run_len={self.run_len}, window={self.window}, "
+                f"ms={self.ms:.3f})")
+
+
 @dataclass
 class PlanDesc:
     n_tiles: int
@@ -72,7 +81,9 @@ _lib = None
 SYMBOLS = ("mwax_plan_create", "mwax_plan_create_ex", "mwax_plan_get_info", "mwax_plan_output_bytes",
            "mwax_plan_input_bytes", "mwax_plan_set_stream", "mwax_correlate", "mwax_correlate_host",
            "mwax_plan_sync", "mwax_plan_destroy", "mwax_last_error", "mwax_version", "mwax_plan_enable_timing",
-           "mwax_plan_stage_times")
+           "mwax_plan_stage_times", "mwax_plan_autotune", "mwax_plan_set_tuning", "mwax_plan_get_tuning",
+           "mwax_batch_create", "mwax_batch_set_stream", "mwax_batch_set_graphs", "mwax_batch_correlate",
+           "mwax_batch_sync", "mwax_batch_destroy")
 
 
 def load_library(path: str | None = None):
@@ -117,6 +128,24 @@ def load_library(path: str | None = None):
     lib.mwax_plan_enable_timing.restype = st
     lib.mwax_plan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
     lib.mwax_plan_stage_times.restype = st
+    lib.mwax_plan_autotune.argtypes = [vp, vp, vp, vp, ctypes.POINTER(Tuning)]
+    lib.mwax_plan_autotune.restype = st
+    lib.mwax_plan_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+    lib.mwax_plan_set_tuning.restype = st
+    lib.mwax_plan_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+    lib.mwax_plan_get_tuning.restype = st
+    lib.mwax_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
+    lib.mwax_batch_create.restype = vp
+    lib.mwax_batch_set_stream.argtypes = [vp, vp]
+    lib.mwax_batch_set_stream.restype = st
+    lib.mwax_batch_set_graphs.argtypes = [vp, ctypes.c_int]
+    lib.mwax_batch_set_graphs.restype = st
+    lib.mwax_batch_correlate.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    lib.mwax_batch_correlate.restype = st
+    lib.mwax_batch_sync.argtypes = [vp]
+    lib.mwax_batch_sync.restype = st
+    lib.mwax_batch_destroy.argtypes = [vp]
+    lib.mwax_batch_destroy.restype = None
     lib.mwax_version.argtypes = []
     lib.mwax_version.restype = ctypes.c_char_p
     _lib = lib
@@ -247,6 +276,61 @@ def mwax_plan_stage_times(plan: Plan):
     n = (ctypes.c_longlong * 3)()
     _check(load_library().mwax_plan_stage_times(plan.handle, ms, n))
     return {STAGES[i]: (ms[i], n[i]) for i in range(3)}
+
+
+def mwax_plan_autotune(plan: Plan, voltages, delay_poly, vis_out) -> Tuning:
+    """Time the plan's launch choices on these device buffers and keep the fastest."""
+    dptr, keep = _delay_arg(delay_poly, plan, True)
+    t = Tuning()
+    _check(load_library().mwax_plan_autotune(plan.handle, _ptr(voltages), dptr, _ptr(vis_out), ctypes.byref(t)))
+    return t
+
+
+def mwax_plan_set_tuning(plan: Plan, tuning: Tuning):
+    _check(load_library().mwax_plan_set_tuning(plan.handle, ctypes.byref(tuning)))
+
+
+def mwax_plan_get_tuning(plan: Plan) -> Tuning:
+    t = Tuning()
+    _check(load_library().mwax_plan_get_tuning(plan.handle, ctypes.byref(t)))
+    return t
+
+
+class Batch:
+    """A set of plans correlated together (one persistent X-step launch per round, CUDA
+    graph replay).  Keeps references to its plans."""
+
+    def __init__(self, plans, stream=None, graphs: bool = True):
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p.handle for p in self.plans])
+        h = load_library().mwax_batch_create(arr, len(self.plans))
+        if not h:
+            raise MwaxError(MWAX_EINVAL, mwax_last_error())
+        self.handle = h
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(load_library().mwax_batch_set_stream(h, ctypes.c_void_p(s.cuda_stream)))
+        _check(load_library().mwax_batch_set_graphs(h, int(graphs)))
+
+    def correlate(self, voltages, delays, outs):
+        n = len(self.plans)
+        V = (ctypes.c_void_p * n)(*[_ptr(v) for v in voltages])
+        O = (ctypes.c_void_p * n)(*[_ptr(o) for o in outs])
+        D = None
+        if delays is not None:
+            D = (ctypes.c_void_p * n)(*[None if d is None else _ptr(d) for d in delays])
+        _check(load_library().mwax_batch_correlate(self.handle, V, D, O))
+
+    def sync(self):
+        _check(load_library().mwax_batch_sync(self.handle))
+
+    def close(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.mwax_batch_destroy(h)
+
+    def __del__(self):
+        self.close()
 
 
 def mwax_plan_destroy(plan: Plan):

@@ -10,74 +10,9 @@
 #include <string>
 #include <vector>
 
-#include "mwax_internal.cuh"
+#include "plan.cuh"
 
 using namespace mwax;
-
-struct mwax_plan {
-    mwax_plan_desc desc;
-    int T = 0, n = 0, N = 0, F = 0, M = 0, bs = 0, prec = 0, dc_excl = 1;
-    long long K = 0, S = 0, n_ints = 0, B = 0, n_blocks = 0;
-    double nu = 0.0;
-    size_t vis_set_bytes = 0, weights_bytes = 0, int_stride = 0, input_bytes = 0;
-
-    // integration grouping: `slots` integrations per launch, or one integration split
-    // into `chunks` launches of at most Kc frames
-    long long slots = 1, Kc = 0, Kpad = 0;
-    int chunks = 1;
-    int elem_bytes = 4;
-
-    // device memory
-    void* Y = nullptr;      // X-step operands (FP8: e4m3)
-    void* Y16 = nullptr;    // FP8 only: the FP16 operands the e4m3 ones are quantised from
-    size_t Y_bytes = 0;
-    float2* tw = nullptr;
-    double* delay = nullptr;
-    Group* groups = nullptr;
-    int n_groups = 0;
-    float* gain = nullptr;
-    int* chan_group = nullptr;   // FP8: group of each ultrafine channel
-    float* amax = nullptr;       // FP8: [slots][groups][n] per-path max magnitude
-    size_t amax_bytes = 0;
-    RunInfo* runs = nullptr;
-    int n_runs = 0;
-    int4* tiles = nullptr;
-    int n_tiles = 0;
-    int* status = nullptr;
-    int* counter = nullptr;   // work-item counter of the persistent X-step
-    float out_scale = 1.0f, post_scale = 1.0f;
-    bool tensor_cores = false;   // tcgen05 X-step (FP16 / FP8 / INT8) vs CUDA-core FP32
-    int tile = 64;               // paths per tile side of the X-step
-    CUtensorMap tmap;            // operand planes, for the tcgen05 X-step
-
-    // host copies of the tables (work-item costs) and the tcgen05 item lists by slot count
-    std::vector<int4> h_tiles;
-    std::vector<RunInfo> h_runs;
-    std::vector<Group> h_groups;
-    std::vector<float> h_gain;
-    struct ItemList {
-        long long key;
-        XItem* items;
-        int* offs;
-        int workers;
-    };
-    std::vector<ItemList> item_lists;   // per (slot count, frames) of a launch
-
-    // host-input path
-    int8_t* dvolt = nullptr;
-    char* dout = nullptr;
-    cudaStream_t copy_stream = nullptr;
-    std::vector<cudaEvent_t> events;
-
-    cudaStream_t stream = nullptr;
-    int device = 0;
-
-    // stage timing: event pairs per launch, drained by mwax_plan_stage_times
-    bool timing = false;
-    std::vector<cudaEvent_t> ev_pool;
-    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
-    long long launches[3] = {0, 0, 0};
-};
 
 namespace {
 
@@ -192,10 +127,7 @@ void free_plan(mwax_plan* p)
     cudaFree(p->counter);
     cudaFree(p->dvolt);
     cudaFree(p->dout);
-    for (auto& it : p->item_lists) {
-        cudaFree(it.items);
-        cudaFree(it.offs);
-    }
+    for (auto& it : p->item_lists) cudaFree(it.items);
     for (auto e : p->events) cudaEventDestroy(e);
     for (auto e : p->ev_pool) cudaEventDestroy(e);
     for (auto& u : p->ev_used) {
@@ -262,6 +194,80 @@ mwax_status validate(const mwax_plan_desc& d, mwax_plan& p)
     return MWAX_OK;
 }
 
+}  // namespace
+
+namespace mwax {
+
+// (Re)build the X-step tile list and the runs of output channels.  run_len = output
+// channels per work item (0: chosen from the grid size), window = width of a tensor-core
+// tile's column window (128 or 256).  Drops cached item lists.
+mwax_status configure_x(mwax_plan& p, int run_len_req, int window)
+{
+    for (auto& it : p.item_lists) cudaFree(it.items);
+    p.item_lists.clear();
+    cudaFree(p.tiles);
+    cudaFree(p.runs);
+    p.tiles = nullptr;
+    p.runs = nullptr;
+    const std::vector<Group>& groups = p.h_groups;
+
+    // tiles of path pairs on or above the diagonal
+    std::vector<int4> tiles;
+    if (p.prec == MWAX_INT8) {
+        for (int i = 0; i < p.n; i += 128)
+            for (int j = i; j < p.n; j += 128) tiles.push_back(make_int4(i, j, 128, i == j ? 1 : 0));
+    } else if (p.tensor_cores) {
+        tiles.resize(build_tc_tiles(p.n, window, nullptr, 0));
+        build_tc_tiles(p.n, window, tiles.data(), (int)tiles.size());
+    } else {
+        for (int i = 0; i < p.n; i += 64)
+            for (int j = i; j < p.n; j += 64) tiles.push_back(make_int4(i, j, 64, i == j ? 1 : 0));
+    }
+    p.n_tiles = (int)tiles.size();
+    p.h_tiles = tiles;
+    MWAX_CUDA(cudaMalloc(&p.tiles, sizeof(int4) * tiles.size()));
+    MWAX_CUDA(cudaMemcpy(p.tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice));
+
+    // runs of output channels: by default enough work items for several per SM, at least
+    // 4 channels per run
+    int run_len = run_len_req;
+    if (run_len <= 0) {
+        const long long items_wo_runs = (long long)p.n_tiles * p.slots;
+        const long long want_items = p.tensor_cores ? 6LL * 148 : 8LL * 148;
+        const int want_runs = (int)std::max<long long>(1, (want_items + items_wo_runs - 1) / items_wo_runs);
+        run_len = std::max(4, (p.M + want_runs - 1) / want_runs);
+    }
+    run_len = std::max(1, std::min(run_len, p.M));
+    p.run_len = run_len;
+    std::vector<RunInfo> runs;
+    for (int j0 = 0; j0 < p.M; j0 += run_len) {
+        RunInfo r;
+        r.j0 = j0;
+        r.j1 = std::min(p.M, j0 + run_len);
+        r.g0 = p.n_groups;
+        r.g1 = 0;
+        for (int g = 0; g < p.n_groups; ++g) {
+            const Group& gr = groups[g];
+            const bool in = (gr.ja >= r.j0 && gr.ja < r.j1) || (gr.jb >= r.j0 && gr.jb < r.j1);
+            if (in) {
+                r.g0 = std::min(r.g0, g);
+                r.g1 = std::max(r.g1, g + 1);
+            }
+        }
+        runs.push_back(r);
+    }
+    p.n_runs = (int)runs.size();
+    p.h_runs = runs;
+    p.window = window;
+    MWAX_CUDA(cudaMalloc(&p.runs, sizeof(RunInfo) * runs.size()));
+    MWAX_CUDA(cudaMemcpy(p.runs, runs.data(), sizeof(RunInfo) * runs.size(), cudaMemcpyHostToDevice));
+    return MWAX_OK;
+}
+
+}  // namespace mwax
+
+namespace {
+
 mwax_status setup(mwax_plan& p)
 {
     MWAX_CUDA(cudaGetDevice(&p.device));
@@ -316,6 +322,8 @@ mwax_status setup(mwax_plan& p)
     MWAX_CUDA(cudaMemcpy(p.gain, gain.data(), sizeof(float) * p.N, cudaMemcpyHostToDevice));
     MWAX_CUDA(cudaMalloc(&p.groups, sizeof(Group) * groups.size()));
     MWAX_CUDA(cudaMemcpy(p.groups, groups.data(), sizeof(Group) * groups.size(), cudaMemcpyHostToDevice));
+    p.h_groups = groups;
+    p.h_gain = gain;
 
     // FP16 operands: power-of-two pre-scale keeping |Re X|, |Im X| <= 181 N (int8
     // magnitude 128 sqrt 2 summed over N samples) below 2^15; undone exactly after the MMA
@@ -339,53 +347,10 @@ mwax_status setup(mwax_plan& p)
     if (p.tensor_cores)
         MWAX_CUDA(make_operand_tmap(&p.tmap, p.Y, p.prec == MWAX_FP8 ? 1 : 2, p.Kpad, p.n, p.slots * p.N * 2));
 
-    // tiles of path pairs on or above the diagonal
-    std::vector<int4> tiles;
-    if (p.prec == MWAX_INT8) {
-        for (int i = 0; i < p.n; i += 128)
-            for (int j = i; j < p.n; j += 128) tiles.push_back(make_int4(i, j, 128, i == j ? 1 : 0));
-    } else if (p.tensor_cores) {
-        tiles.resize(build_tc_tiles(p.n, nullptr, 0));
-        build_tc_tiles(p.n, tiles.data(), (int)tiles.size());
-    } else {
-        for (int i = 0; i < p.n; i += 64)
-            for (int j = i; j < p.n; j += 64) tiles.push_back(make_int4(i, j, 64, i == j ? 1 : 0));
+    {
+        mwax_status st = configure_x(p, 0, p.prec == MWAX_INT8 ? 128 : 256);
+        if (st != MWAX_OK) return st;
     }
-    p.n_tiles = (int)tiles.size();
-    p.h_tiles = tiles;
-    p.h_groups = groups;
-    p.h_gain = gain;
-    MWAX_CUDA(cudaMalloc(&p.tiles, sizeof(int4) * tiles.size()));
-    MWAX_CUDA(cudaMemcpy(p.tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice));
-
-    // runs of output channels: enough CTAs for several waves (1 resident CTA per SM for
-    // the tensor-core kernel, 2 for the CUDA-core one), at least 4 channels per run
-    const long long ctas_wo_runs = (long long)p.n_tiles * p.slots;
-    const long long want_ctas = p.tensor_cores ? 6LL * 148 : 8LL * 148;
-    int want_runs = (int)std::max<long long>(1, (want_ctas + ctas_wo_runs - 1) / ctas_wo_runs);
-    int run_len = std::max(4, (p.M + want_runs - 1) / want_runs);
-    run_len = std::min(run_len, p.M);
-    std::vector<RunInfo> runs;
-    for (int j0 = 0; j0 < p.M; j0 += run_len) {
-        RunInfo r;
-        r.j0 = j0;
-        r.j1 = std::min(p.M, j0 + run_len);
-        r.g0 = p.n_groups;
-        r.g1 = 0;
-        for (int g = 0; g < p.n_groups; ++g) {
-            const Group& gr = groups[g];
-            const bool in = (gr.ja >= r.j0 && gr.ja < r.j1) || (gr.jb >= r.j0 && gr.jb < r.j1);
-            if (in) {
-                r.g0 = std::min(r.g0, g);
-                r.g1 = std::max(r.g1, g + 1);
-            }
-        }
-        runs.push_back(r);
-    }
-    p.n_runs = (int)runs.size();
-    p.h_runs = runs;
-    MWAX_CUDA(cudaMalloc(&p.runs, sizeof(RunInfo) * runs.size()));
-    MWAX_CUDA(cudaMemcpy(p.runs, runs.data(), sizeof(RunInfo) * runs.size(), cudaMemcpyHostToDevice));
 
     MWAX_CUDA(cudaMalloc(&p.counter, sizeof(int)));
     MWAX_CUDA(cudaMalloc(&p.status, sizeof(int)));
@@ -394,6 +359,8 @@ mwax_status setup(mwax_plan& p)
 }
 
 }  // namespace
+
+namespace mwax {
 
 // Work items of one tensor-core X launch of plan p (as job `job`), with a cost estimate
 // (MMA volume: active ultrafine channels x frame blocks x window width) for ordering.
@@ -427,6 +394,10 @@ void sort_items(std::vector<std::pair<double, XItem>>& v, std::vector<XItem>& or
     for (size_t i = 0; i < v.size(); ++i) order[i] = v[i].second;
 }
 
+}  // namespace mwax
+
+namespace {
+
 int sm_count()
 {
     int dev = 0, sms = 148;
@@ -434,8 +405,6 @@ int sm_count()
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     return sms;
 }
-
-namespace {
 
 // Device item list of a single-plan launch, most expensive first (cached per slot count
 // and frames).
@@ -445,7 +414,7 @@ mwax_status single_items(mwax_plan* p, long long nslots, long long klen, XItem**
     for (auto& e : p->item_lists)
         if (e.key == key) {
             *items = e.items;
-            *n = e.workers;
+            *n = e.n;
             return MWAX_OK;
         }
     std::vector<std::pair<double, XItem>> v;
@@ -455,7 +424,7 @@ mwax_status single_items(mwax_plan* p, long long nslots, long long klen, XItem**
     XItem* d = nullptr;
     MWAX_CUDA(cudaMalloc(&d, sizeof(XItem) * std::max<size_t>(1, order.size())));
     MWAX_CUDA(cudaMemcpy(d, order.data(), sizeof(XItem) * order.size(), cudaMemcpyHostToDevice));
-    p->item_lists.push_back({key, d, nullptr, (int)order.size()});
+    p->item_lists.push_back({key, d, (int)order.size()});
     *items = d;
     *n = (int)order.size();
     return MWAX_OK;
@@ -475,14 +444,14 @@ cudaEvent_t take_event(mwax_plan* p)
 
 // Bracket one launch of `stage` with events when timing is on; count it either way.
 template <typename F>
-cudaError_t timed(mwax_plan* p, int stage, F&& launch)
+cudaError_t timed(mwax_plan* p, int stage, cudaStream_t s, F&& launch)
 {
     p->launches[stage] += 1;
     if (!p->timing) return launch();
     cudaEvent_t a = take_event(p), b = take_event(p);
-    cudaEventRecord(a, p->stream);
+    cudaEventRecord(a, s);
     cudaError_t e = launch();
-    cudaEventRecord(b, p->stream);
+    cudaEventRecord(b, s);
     p->ev_used.push_back({stage, {a, b}});
     return e;
 }
@@ -491,118 +460,19 @@ mwax_status enqueue(mwax_plan* p, const int8_t* volt, bool have_delay, char* out
                     long long events_per_block)
 {
     cudaStream_t s = p->stream;
-    MWAX_CUDA(timed(p, 0, [&] {
-        return launch_init_output(out, p->n_ints, (long long)p->vis_set_bytes, (long long)p->weights_bytes, s);
-    }));
-    for (long long w0 = 0; w0 < p->n_ints; w0 += p->slots) {
-        const long long nslots = std::min(p->slots, p->n_ints - w0);
-        for (int ch = 0; ch < p->chunks; ++ch) {
-            const long long kbeg = (long long)ch * p->Kc;
-            const long long klen = std::min(p->Kc, p->K - kbeg);
-            const long long nframes = (p->chunks == 1) ? nslots * p->K : klen;
-            const long long m_begin = w0 * p->K + kbeg;
-            if (wait_events) {
-                // host copies of the tables (work-item costs) and the tcgen05 item lists by slot count
-    std::vector<int4> h_tiles;
-    std::vector<RunInfo> h_runs;
-    std::vector<Group> h_groups;
-    std::vector<float> h_gain;
-    struct ItemList {
-        long long key;
-        XItem* items;
-        int* offs;
-        int workers;
-    };
-    std::vector<ItemList> item_lists;   // per (slot count, frames) of a launch
-
-    // host-input path: wait for the copy of the last block this launch reads
-                const long long last_sample = (m_begin + nframes) * p->N - 1;
-                const long long blk = last_sample / p->bs;
-                MWAX_CUDA(cudaStreamWaitEvent(s, wait_events[blk / events_per_block], 0));
-            }
-            FArgs fa;
-            memset(&fa, 0, sizeof fa);
-            fa.volt = volt;
-            fa.delay = have_delay ? p->delay : nullptr;
-            fa.Y = p->Y;
-            fa.tw = p->tw;
-            fa.gain = p->gain;
-            fa.m_begin = m_begin;
-            fa.n_frames = nframes;
-            // a short last chunk of a split integration overwrites the previous chunk's
-            // frames up to the next 128-frame boundary with zeros
-            fa.n_store = (p->chunks == 1) ? nframes
-                                          : std::min(p->Kpad, (nframes + kKAlign - 1) / kKAlign * kKAlign);
-            fa.Kc = (p->chunks == 1) ? p->K : p->Kc;
-            fa.Kpad = p->Kpad;
-            fa.n = p->n;
-            fa.bs = p->bs;
-            fa.nu = p->nu;
-            fa.out_scale = p->out_scale;
-            fa.chan_group = p->chan_group;
-            fa.n_groups = p->n_groups;
-            fa.amax = p->amax;
-            if (p->prec == MWAX_FP8) {
-                // FP16 operands with the per-path-per-group max magnitude, then e4m3
-                MWAX_CUDA(cudaMemsetAsync(p->amax, 0, p->amax_bytes, s));
-                fa.Y = p->Y16;
-                MWAX_CUDA(timed(p, 1, [&] { return launch_fstep(p->N, FOUT_F16A, fa, s); }));
-                MWAX_CUDA(timed(p, 1, [&] {
-                    return launch_quantise_e4m3(static_cast<const __half*>(p->Y16),
-                                                static_cast<__nv_fp8_storage_t*>(p->Y), p->amax, p->chan_group,
-                                                p->n_groups, nslots, p->N, p->n, p->Kpad, s);
-                }));
-            } else {
-                const int fout = (p->prec == MWAX_FP32) ? FOUT_F32 : FOUT_F16;
-                MWAX_CUDA(timed(p, 1, [&] { return launch_fstep(p->N, fout, fa, s); }));
-            }
-
-            XArgs xa;
-            memset(&xa, 0, sizeof xa);
-            xa.Y = p->Y;
-            xa.out = out + w0 * (long long)p->int_stride;
-            xa.out_stride = (long long)p->int_stride;
-            xa.Kpad = p->Kpad;
-            xa.klen = klen;
-            xa.n = p->n;
-            xa.T = p->T;
-            xa.N = p->N;
-            xa.M = p->M;
-            xa.B = p->B;
-            xa.groups = p->groups;
-            xa.n_groups = p->n_groups;
-            xa.gain = p->gain;
-            xa.runs = p->runs;
-            xa.tiles = p->tiles;
-            xa.post_scale = p->post_scale;
-            xa.first_store = (ch == 0) ? 1 : 0;
-            xa.status = p->status;
-            xa.spin_limit = 2000000;   // x 1000 cycles: ~1 s per bounded wait
-            xa.scale = p->amax;
-            if (p->prec == MWAX_INT8) {
-                // split each slot's samples into segments of whole 256-sample chunks so the
-                // grid covers the GPU several times over
-                const long long chunks256 = (klen + 255) / 256;
-                const long long want = std::max<long long>(1, (4LL * 148 + p->n_tiles * nslots - 1) / (p->n_tiles * nslots));
-                const long long seg_chunks = std::max<long long>(1, (chunks256 + want - 1) / want);
-                xa.seg_frames = seg_chunks * 256;
-                const int nseg = (int)((chunks256 + seg_chunks - 1) / seg_chunks);
-                MWAX_CUDA(timed(p, 2, [&] { return launch_xstep_int8(p->tmap, xa, p->n_tiles, nseg, (int)nslots, s); }));
-            } else if (p->tensor_cores) {
-                XItem* items = nullptr;
-                int n_items = 0;
-                mwax_status st = single_items(p, nslots, klen, &items, &n_items);
-                if (st != MWAX_OK) return st;
-                static thread_local XLaunch L;   // large: keep it off the stack
-                L.n_jobs = 1;
-                L.jobs[0].tmap = p->tmap;
-                L.jobs[0].a = xa;
-                L.jobs[0].op = (p->prec == MWAX_FP8) ? 1 : 0;
-                MWAX_CUDA(timed(p, 2, [&] { return launch_xstep_tc(L, items, n_items, p->counter, p->status, s); }));
-            } else {
-                MWAX_CUDA(timed(p, 2, [&] { return launch_xstep_simt(xa, p->n_tiles, p->n_runs, (int)nslots, s); }));
-            }
+    mwax_status st = enqueue_init(p, out, s);
+    if (st != MWAX_OK) return st;
+    for (const LaunchGroup& g : plan_groups(p)) {
+        if (wait_events) {
+            // host-input path: wait for the copy of the last block this launch reads
+            const long long last_sample = (g.m_begin + g.nframes) * p->N - 1;
+            const long long blk = last_sample / p->bs;
+            MWAX_CUDA(cudaStreamWaitEvent(s, wait_events[blk / events_per_block], 0));
         }
+        st = enqueue_fstep(p, g, volt, have_delay, s);
+        if (st != MWAX_OK) return st;
+        st = enqueue_xstep_single(p, g, make_xargs(p, g, out), s);
+        if (st != MWAX_OK) return st;
     }
     return MWAX_OK;
 }
@@ -615,6 +485,142 @@ mwax_status load_delay(mwax_plan* p, const double* delay_poly)
 }
 
 }  // namespace
+
+namespace mwax {
+
+mwax_status set_error(mwax_status st, const char* msg) { return fail(st, "%s", msg); }
+
+mwax_status cuda_error(cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return MWAX_OK;
+    return fail(e == cudaErrorMemoryAllocation ? MWAX_ENOMEM : MWAX_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+std::vector<LaunchGroup> plan_groups(const mwax_plan* p)
+{
+    std::vector<LaunchGroup> v;
+    for (long long w0 = 0; w0 < p->n_ints; w0 += p->slots) {
+        const long long nslots = std::min(p->slots, p->n_ints - w0);
+        for (int ch = 0; ch < p->chunks; ++ch) {
+            LaunchGroup g;
+            g.w0 = w0;
+            g.nslots = nslots;
+            g.ch = ch;
+            g.kbeg = (long long)ch * p->Kc;
+            g.klen = std::min(p->Kc, p->K - g.kbeg);
+            g.nframes = (p->chunks == 1) ? nslots * p->K : g.klen;
+            g.m_begin = w0 * p->K + g.kbeg;
+            v.push_back(g);
+        }
+    }
+    return v;
+}
+
+mwax_status enqueue_init(mwax_plan* p, char* out, cudaStream_t s)
+{
+    MWAX_CUDA(timed(p, 0, s, [&] {
+        return launch_init_output(out, p->n_ints, (long long)p->vis_set_bytes, (long long)p->weights_bytes, s);
+    }));
+    return MWAX_OK;
+}
+
+mwax_status enqueue_fstep(mwax_plan* p, const LaunchGroup& g, const int8_t* volt, bool have_delay, cudaStream_t s)
+{
+    FArgs fa;
+    memset(&fa, 0, sizeof fa);
+    fa.volt = volt;
+    fa.delay = have_delay ? p->delay : nullptr;
+    fa.Y = p->Y;
+    fa.tw = p->tw;
+    fa.gain = p->gain;
+    fa.m_begin = g.m_begin;
+    fa.n_frames = g.nframes;
+    // a short last chunk of a split integration overwrites the previous chunk's frames
+    // up to the next 128-frame boundary with zeros
+    fa.n_store = (p->chunks == 1) ? g.nframes : std::min(p->Kpad, (g.nframes + kKAlign - 1) / kKAlign * kKAlign);
+    fa.Kc = (p->chunks == 1) ? p->K : p->Kc;
+    fa.Kpad = p->Kpad;
+    fa.n = p->n;
+    fa.bs = p->bs;
+    fa.nu = p->nu;
+    fa.out_scale = p->out_scale;
+    fa.chan_group = p->chan_group;
+    fa.n_groups = p->n_groups;
+    fa.amax = p->amax;
+    if (p->prec == MWAX_FP8) {
+        // FP16 operands with the per-path-per-group max magnitude, then e4m3
+        MWAX_CUDA(cudaMemsetAsync(p->amax, 0, p->amax_bytes, s));
+        fa.Y = p->Y16;
+        MWAX_CUDA(timed(p, 1, s, [&] { return launch_fstep(p->N, FOUT_F16A, fa, s, p->fvariant); }));
+        MWAX_CUDA(timed(p, 1, s, [&] {
+            return launch_quantise_e4m3(static_cast<const __half*>(p->Y16), static_cast<__nv_fp8_storage_t*>(p->Y),
+                                        p->amax, p->chan_group, p->n_groups, g.nslots, p->N, p->n, p->Kpad, s);
+        }));
+    } else {
+        const int fout = (p->prec == MWAX_FP32) ? FOUT_F32 : FOUT_F16;
+        MWAX_CUDA(timed(p, 1, s, [&] { return launch_fstep(p->N, fout, fa, s, p->fvariant); }));
+    }
+    return MWAX_OK;
+}
+
+XArgs make_xargs(const mwax_plan* p, const LaunchGroup& g, char* out)
+{
+    XArgs xa;
+    memset(&xa, 0, sizeof xa);
+    xa.Y = p->Y;
+    xa.out = out + g.w0 * (long long)p->int_stride;
+    xa.out_stride = (long long)p->int_stride;
+    xa.Kpad = p->Kpad;
+    xa.klen = g.klen;
+    xa.n = p->n;
+    xa.T = p->T;
+    xa.N = p->N;
+    xa.M = p->M;
+    xa.B = p->B;
+    xa.groups = p->groups;
+    xa.n_groups = p->n_groups;
+    xa.gain = p->gain;
+    xa.runs = p->runs;
+    xa.tiles = p->tiles;
+    xa.post_scale = p->post_scale;
+    xa.first_store = (g.ch == 0) ? 1 : 0;
+    xa.status = p->status;
+    xa.spin_limit = 2000000;   // x 1000 cycles: ~1 s per bounded wait
+    xa.scale = p->amax;
+    return xa;
+}
+
+mwax_status enqueue_xstep_single(mwax_plan* p, const LaunchGroup& g, const XArgs& xa_in, cudaStream_t s)
+{
+    XArgs xa = xa_in;
+    if (p->prec == MWAX_INT8) {
+        // split each slot's samples into segments of whole 256-sample chunks so the grid
+        // covers the GPU several times over
+        const long long chunks256 = (g.klen + 255) / 256;
+        const long long want =
+            std::max<long long>(1, (4LL * 148 + p->n_tiles * g.nslots - 1) / (p->n_tiles * g.nslots));
+        const long long seg_chunks = std::max<long long>(1, (chunks256 + want - 1) / want);
+        xa.seg_frames = seg_chunks * 256;
+        const int nseg = (int)((chunks256 + seg_chunks - 1) / seg_chunks);
+        MWAX_CUDA(timed(p, 2, s, [&] { return launch_xstep_int8(p->tmap, xa, p->n_tiles, nseg, (int)g.nslots, s); }));
+    } else if (p->tensor_cores) {
+        XItem* items = nullptr;
+        int n_items = 0;
+        mwax_status st = single_items(p, g.nslots, g.klen, &items, &n_items);
+        if (st != MWAX_OK) return st;
+        static thread_local XLaunch L;   // large: keep it off the stack
+        L.n_jobs = 1;
+        L.jobs[0].tmap = p->tmap;
+        L.jobs[0].a = xa;
+        L.jobs[0].op = (p->prec == MWAX_FP8) ? 1 : 0;
+        MWAX_CUDA(timed(p, 2, s, [&] { return launch_xstep_tc(L, items, n_items, p->counter, p->status, s); }));
+    } else {
+        MWAX_CUDA(timed(p, 2, s, [&] { return launch_xstep_simt(xa, p->n_tiles, p->n_runs, (int)g.nslots, s); }));
+    }
+    return MWAX_OK;
+}
+
+}  // namespace mwax
 
 extern "C" {
 

@@ -1,0 +1,370 @@
+// Batched correlation of many coarse channels (plans of mixed shapes and precisions) in
+// one schedule, replayed as a CUDA graph, and the autotuner of a plan's launch choices.
+//
+// Schedule of one batch call: every plan's output is initialised; then, round by round,
+// the F-steps of each plan's r-th launch group run on auxiliary streams (fork/join), and
+// ONE persistent tcgen05 X launch covers the r-th groups of all FP16 / FP8 plans (their
+// work items merged into one cost-sorted list; each plan is one job of the launch).
+// CUDA-core FP32 and integer-mode plans run their X-steps in the same round after it.
+// The paper runs one coarse channel per server (Sec. 2.1); here one GPU takes many.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "plan.cuh"
+
+using namespace mwax;
+
+struct mwax_batch {
+    std::vector<mwax_plan*> plans;
+    int device = 0;
+    cudaStream_t stream = nullptr;   // the caller's stream
+    cudaStream_t work = nullptr;     // private stream the schedule runs (and is captured) on
+    cudaEvent_t in_ev = nullptr, out_ev = nullptr;
+    std::vector<cudaStream_t> aux;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> joins;
+    std::vector<std::vector<std::pair<int, LaunchGroup>>> rounds;   // (plan, group) per round
+    struct RoundX {
+        std::vector<int> jobs;   // plan index of each job of the persistent X launch
+        XItem* items = nullptr;
+        int n_items = 0;
+    };
+    std::vector<RoundX> rx;
+    int* counter = nullptr;
+    int* status = nullptr;
+    bool graphs = true;
+    bool warmed = false;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<const void*> gkey;
+};
+
+namespace {
+
+constexpr int kAuxStreams = 4;
+
+#define BCUDA(call)                                              \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_error(e_, #call);     \
+    } while (0)
+
+bool tc_plan(const mwax_plan* p) { return p->prec == MWAX_FP16 || p->prec == MWAX_FP8; }
+
+void free_batch(mwax_batch* b)
+{
+    if (!b) return;
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    for (auto& r : b->rx) cudaFree(r.items);
+    cudaFree(b->counter);
+    cudaFree(b->status);
+    for (auto s : b->aux) cudaStreamDestroy(s);
+    if (b->work) cudaStreamDestroy(b->work);
+    if (b->in_ev) cudaEventDestroy(b->in_ev);
+    if (b->out_ev) cudaEventDestroy(b->out_ev);
+    if (b->fork) cudaEventDestroy(b->fork);
+    for (auto e : b->joins) cudaEventDestroy(e);
+    delete b;
+}
+
+mwax_status build(mwax_batch* b)
+{
+    size_t n_rounds = 0;
+    std::vector<std::vector<LaunchGroup>> groups;
+    for (auto* p : b->plans) {
+        groups.push_back(plan_groups(p));
+        n_rounds = std::max(n_rounds, groups.back().size());
+    }
+    b->rounds.assign(n_rounds, {});
+    b->rx.assign(n_rounds, {});
+    for (size_t r = 0; r < n_rounds; ++r) {
+        std::vector<std::pair<double, XItem>> items;
+        for (size_t i = 0; i < b->plans.size(); ++i) {
+            if (r >= groups[i].size()) continue;
+            const LaunchGroup& g = groups[i][r];
+            b->rounds[r].push_back({(int)i, g});
+            mwax_plan* p = b->plans[i];
+            if (!tc_plan(p)) continue;
+            const int job = (int)b->rx[r].jobs.size();
+            if (job >= kMaxJobs) return set_error(MWAX_EUNSUPPORTED, "more tensor-core plans in a batch than kMaxJobs");
+            b->rx[r].jobs.push_back((int)i);
+            plan_items(*p, job, g.nslots, g.klen, items);
+        }
+        std::vector<XItem> order;
+        sort_items(items, order);
+        b->rx[r].n_items = (int)order.size();
+        if (!order.empty()) {
+            BCUDA(cudaMalloc(&b->rx[r].items, sizeof(XItem) * order.size()));
+            BCUDA(cudaMemcpy(b->rx[r].items, order.data(), sizeof(XItem) * order.size(), cudaMemcpyHostToDevice));
+        }
+    }
+    BCUDA(cudaMalloc(&b->counter, sizeof(int)));
+    BCUDA(cudaMalloc(&b->status, sizeof(int)));
+    BCUDA(cudaMemset(b->status, 0, sizeof(int)));
+    for (int i = 0; i < kAuxStreams; ++i) {
+        cudaStream_t s;
+        BCUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        b->aux.push_back(s);
+        cudaEvent_t e;
+        BCUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        b->joins.push_back(e);
+    }
+    BCUDA(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    BCUDA(cudaStreamCreateWithFlags(&b->work, cudaStreamNonBlocking));
+    BCUDA(cudaEventCreateWithFlags(&b->in_ev, cudaEventDisableTiming));
+    BCUDA(cudaEventCreateWithFlags(&b->out_ev, cudaEventDisableTiming));
+    return MWAX_OK;
+}
+
+// Enqueue one batch call on the private work stream (eagerly or under stream capture).
+mwax_status enqueue_batch(mwax_batch* b, const int8_t* const* volt, const double* const* delay, void* const* out)
+{
+    cudaStream_t s = b->work;
+    for (size_t i = 0; i < b->plans.size(); ++i) {
+        mwax_plan* p = b->plans[i];
+        if (delay && delay[i])
+            BCUDA(cudaMemcpyAsync(p->delay, delay[i], sizeof(double) * 3 * p->n, cudaMemcpyDeviceToDevice, s));
+        mwax_status st = enqueue_init(p, static_cast<char*>(out[i]), s);
+        if (st != MWAX_OK) return st;
+    }
+    static thread_local XLaunch L;
+    for (size_t r = 0; r < b->rounds.size(); ++r) {
+        // F-steps of this round, spread over the auxiliary streams
+        BCUDA(cudaEventRecord(b->fork, s));
+        for (auto a : b->aux) BCUDA(cudaStreamWaitEvent(a, b->fork, 0));
+        for (size_t k = 0; k < b->rounds[r].size(); ++k) {
+            const int i = b->rounds[r][k].first;
+            mwax_plan* p = b->plans[i];
+            const bool have_delay = delay && delay[i];
+            mwax_status st = enqueue_fstep(p, b->rounds[r][k].second, volt[i], have_delay, b->aux[k % b->aux.size()]);
+            if (st != MWAX_OK) return st;
+        }
+        for (size_t a = 0; a < b->aux.size(); ++a) {
+            BCUDA(cudaEventRecord(b->joins[a], b->aux[a]));
+            BCUDA(cudaStreamWaitEvent(s, b->joins[a], 0));
+        }
+        // one persistent tensor-core X launch for every FP16 / FP8 plan of the round
+        const auto& R = b->rx[r];
+        if (!R.jobs.empty()) {
+            L.n_jobs = (int)R.jobs.size();
+            for (size_t j = 0; j < R.jobs.size(); ++j) {
+                const int i = R.jobs[j];
+                mwax_plan* p = b->plans[i];
+                const LaunchGroup* g = nullptr;
+                for (auto& e : b->rounds[r])
+                    if (e.first == i) g = &e.second;
+                L.jobs[j].tmap = p->tmap;
+                L.jobs[j].a = make_xargs(p, *g, static_cast<char*>(out[i]));
+                L.jobs[j].a.status = b->status;
+                L.jobs[j].op = (p->prec == MWAX_FP8) ? 1 : 0;
+            }
+            BCUDA(launch_xstep_tc(L, R.items, R.n_items, b->counter, b->status, s));
+        }
+        // the other plans' X-steps
+        for (auto& e : b->rounds[r]) {
+            mwax_plan* p = b->plans[e.first];
+            if (tc_plan(p)) continue;
+            mwax_status st = enqueue_xstep_single(p, e.second, make_xargs(p, e.second, static_cast<char*>(out[e.first])), s);
+            if (st != MWAX_OK) return st;
+        }
+    }
+    return MWAX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mwax_batch* mwax_batch_create(mwax_plan* const* plans, int n_plans)
+{
+    if (!plans || n_plans < 1) {
+        set_error(MWAX_EINVAL, "a batch needs at least one plan");
+        return nullptr;
+    }
+    mwax_batch* b = new mwax_batch();
+    for (int i = 0; i < n_plans; ++i) {
+        if (!plans[i]) {
+            set_error(MWAX_EINVAL, "NULL plan in batch");
+            free_batch(b);
+            return nullptr;
+        }
+        b->plans.push_back(plans[i]);
+    }
+    b->device = plans[0]->device;
+    for (auto* p : b->plans)
+        if (p->device != b->device) {
+            set_error(MWAX_EINVAL, "all plans of a batch must be on one device");
+            free_batch(b);
+            return nullptr;
+        }
+    if (cudaSetDevice(b->device) != cudaSuccess || build(b) != MWAX_OK) {
+        free_batch(b);
+        return nullptr;
+    }
+    return b;
+}
+
+mwax_status mwax_batch_set_stream(mwax_batch* b, void* stream)
+{
+    if (!b) return set_error(MWAX_EINVAL, "batch is NULL");
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    b->stream = (cudaStream_t)stream;
+    return MWAX_OK;
+}
+
+mwax_status mwax_batch_set_graphs(mwax_batch* b, int enable)
+{
+    if (!b) return set_error(MWAX_EINVAL, "batch is NULL");
+    b->graphs = enable != 0;
+    return MWAX_OK;
+}
+
+mwax_status mwax_batch_correlate(mwax_batch* b, const int8_t* const* voltages, const double* const* delay_poly,
+                                 void* const* vis_out)
+{
+    if (!b || !voltages || !vis_out) return set_error(MWAX_EINVAL, "NULL batch, voltages or vis_out");
+    for (size_t i = 0; i < b->plans.size(); ++i) {
+        if (!voltages[i] || !vis_out[i]) return set_error(MWAX_EINVAL, "NULL voltages or vis_out of a plan");
+        if (b->plans[i]->prec == MWAX_INT8 && delay_poly && delay_poly[i])
+            return set_error(MWAX_EINVAL, "MWAX_INT8 takes no delay correction");
+    }
+    BCUDA(cudaSetDevice(b->device));
+    // the work stream follows the caller's stream, and the caller's stream waits for it
+    BCUDA(cudaEventRecord(b->in_ev, b->stream));
+    BCUDA(cudaStreamWaitEvent(b->work, b->in_ev, 0));
+    mwax_status st = MWAX_OK;
+    if (!b->graphs || !b->warmed) {
+        // first call runs eagerly (sets kernel attributes, fills caches); later calls replay
+        st = enqueue_batch(b, voltages, delay_poly, vis_out);
+        b->warmed = true;
+    } else {
+        std::vector<const void*> key;
+        for (size_t i = 0; i < b->plans.size(); ++i) {
+            key.push_back(voltages[i]);
+            key.push_back(delay_poly ? delay_poly[i] : nullptr);
+            key.push_back(vis_out[i]);
+        }
+        if (!b->gexec || key != b->gkey) {
+            if (b->gexec) {
+                cudaGraphExecDestroy(b->gexec);
+                b->gexec = nullptr;
+            }
+            BCUDA(cudaStreamBeginCapture(b->work, cudaStreamCaptureModeThreadLocal));
+            st = enqueue_batch(b, voltages, delay_poly, vis_out);
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamEndCapture(b->work, &graph);
+            if (st != MWAX_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return st;
+            }
+            if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&b->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_error(e, "cudaGraphInstantiate");
+            b->gkey = key;
+        }
+        BCUDA(cudaGraphLaunch(b->gexec, b->work));
+    }
+    if (st != MWAX_OK) return st;
+    BCUDA(cudaEventRecord(b->out_ev, b->work));
+    BCUDA(cudaStreamWaitEvent(b->stream, b->out_ev, 0));
+    return MWAX_OK;
+}
+
+mwax_status mwax_batch_sync(mwax_batch* b)
+{
+    if (!b) return set_error(MWAX_EINVAL, "batch is NULL");
+    BCUDA(cudaSetDevice(b->device));
+    BCUDA(cudaStreamSynchronize(b->work));
+    BCUDA(cudaStreamSynchronize(b->stream));
+    int st = 0;
+    BCUDA(cudaMemcpy(&st, b->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st != 0) {
+        BCUDA(cudaMemset(b->status, 0, sizeof(int)));
+        return set_error(MWAX_ETIMEOUT, "a device-side bounded wait gave up in a batch launch");
+    }
+    return MWAX_OK;
+}
+
+void mwax_batch_destroy(mwax_batch* b)
+{
+    if (!b) return;
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->work);
+    free_batch(b);
+}
+
+// Autotuner: times each candidate (F-step kernel variant x X-step run length x tile
+// window) on the caller's buffers with CUDA events and keeps the fastest.
+mwax_status mwax_plan_autotune(mwax_plan* p, const int8_t* voltages, const double* delay_poly, void* vis_out,
+                               mwax_tuning* best_out)
+{
+    if (!p || !voltages || !vis_out) return set_error(MWAX_EINVAL, "NULL plan, voltages or vis_out");
+    BCUDA(cudaSetDevice(p->device));
+    std::vector<int> fvars = {0};
+    if (p->N >= 32 && p->N <= 512) fvars.push_back(1);
+    std::vector<int> windows = {p->window};
+    if (tc_plan(p)) windows = {256, 128};
+    std::vector<int> runs = {0};
+    for (int r : {2, 4, 8, 16, 32})
+        if (r < p->M) runs.push_back(r);
+    if (p->M > 1) runs.push_back(p->M);
+    cudaEvent_t e0, e1;
+    BCUDA(cudaEventCreate(&e0));
+    BCUDA(cudaEventCreate(&e1));
+    mwax_tuning best{p->fvariant, p->run_len, p->window, 1e30};
+    const bool timing = p->timing;
+    p->timing = false;
+    mwax_status st = MWAX_OK;
+    for (int fv : fvars)
+        for (int w : windows)
+            for (int rl : runs) {
+                p->fvariant = fv;
+                st = configure_x(*p, rl, w);
+                if (st != MWAX_OK) break;
+                st = mwax_correlate(p, voltages, delay_poly, vis_out);   // warm-up
+                if (st != MWAX_OK) break;
+                cudaEventRecord(e0, p->stream);
+                st = mwax_correlate(p, voltages, delay_poly, vis_out);
+                if (st != MWAX_OK) break;
+                cudaEventRecord(e1, p->stream);
+                cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best.ms) best = mwax_tuning{fv, p->run_len, w, ms};
+            }
+    p->timing = timing;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != MWAX_OK) return st;
+    p->fvariant = best.fstep_variant;
+    st = configure_x(*p, best.run_len, best.window);
+    if (st != MWAX_OK) return st;
+    if (best_out) *best_out = best;
+    return mwax_plan_sync(p);
+}
+
+mwax_status mwax_plan_set_tuning(mwax_plan* p, const mwax_tuning* t)
+{
+    if (!p || !t) return set_error(MWAX_EINVAL, "NULL argument");
+    if (t->fstep_variant < 0 || t->fstep_variant > 1 || (t->window != 128 && t->window != 256) || t->run_len < 0)
+        return set_error(MWAX_EINVAL, "invalid tuning");
+    BCUDA(cudaSetDevice(p->device));
+    BCUDA(cudaStreamSynchronize(p->stream));
+    p->fvariant = t->fstep_variant;
+    return configure_x(*p, t->run_len, tc_plan(p) ? t->window : p->window);
+}
+
+mwax_status mwax_plan_get_tuning(const mwax_plan* p, mwax_tuning* t)
+{
+    if (!p || !t) return set_error(MWAX_EINVAL, "NULL argument");
+    *t = mwax_tuning{p->fvariant, p->run_len, p->window, 0.0};
+    return MWAX_OK;
+}
+
+}  // extern "C"

@@ -693,8 +693,18 @@ cudaError_t launch_r32(const FArgs& a, cudaStream_t s)
 }
 
 template <int OUTK>
-cudaError_t launch_kind(int N, const FArgs& a, cudaStream_t s)
+cudaError_t launch_kind(int N, const FArgs& a, cudaStream_t s, int variant)
 {
+    if (variant == 1) {
+        switch (N) {
+            case 32: return launch_n<32, OUTK>(a, s);
+            case 64: return launch_n<64, OUTK>(a, s);
+            case 128: return launch_n<128, OUTK>(a, s);
+            case 256: return launch_n<256, OUTK>(a, s);
+            case 512: return launch_n<512, OUTK>(a, s);
+            default: break;
+        }
+    }
     switch (N) {
         case 1: {
             dim3 grid((unsigned)((a.n_store + 1023) / 1024), (unsigned)a.n);
@@ -774,12 +784,12 @@ bool fft_len_supported(int N)
     }
 }
 
-cudaError_t launch_fstep(int N, int out_kind, const FArgs& a, cudaStream_t s)
+cudaError_t launch_fstep(int N, int out_kind, const FArgs& a, cudaStream_t s, int variant)
 {
     switch (out_kind) {
-        case FOUT_F32: return launch_kind<FOUT_F32>(N, a, s);
-        case FOUT_F16: return launch_kind<FOUT_F16>(N, a, s);
-        case FOUT_F16A: return launch_kind<FOUT_F16A>(N, a, s);
+        case FOUT_F32: return launch_kind<FOUT_F32>(N, a, s, variant);
+        case FOUT_F16: return launch_kind<FOUT_F16>(N, a, s, variant);
+        case FOUT_F16A: return launch_kind<FOUT_F16A>(N, a, s, variant);
         default: return cudaErrorInvalidValue;
     }
 }

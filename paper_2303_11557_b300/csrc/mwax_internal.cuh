@@ -87,7 +87,7 @@ struct XArgs {
 
 // One launch's worth of tensor-core X-step work for one plan ("job"): its operand tensor
 // map and arguments, resident in device memory.
-struct alignas(64) XJob {
+struct XJob {
     CUtensorMap tmap;
     XArgs a;
     int op;   // 0 = FP16 (kind::f16), 1 = e4m3 (kind::f8f6f4)
@@ -106,7 +106,9 @@ struct XLaunch {
 };
 
 // Launchers (each returns the cudaError_t of its launch).
-cudaError_t launch_fstep(int N, int out_kind, const FArgs& a, cudaStream_t s);
+// variant 0: two-pass radix-32 kernel for N = 32..512 (generic elsewhere); 1: generic
+// Stockham passes for every N.
+cudaError_t launch_fstep(int N, int out_kind, const FArgs& a, cudaStream_t s, int variant);
 
 // e4m3 scale of a path's spectra from their max magnitude: 448 is e4m3's largest finite.
 __host__ __device__ __forceinline__ float e4m3_scale(float amax) { return amax > 0.0f ? amax * (1.0f / 448.0f) : 1.0f; }
@@ -120,7 +122,7 @@ cudaError_t make_operand_tmap(CUtensorMap* map, const void* Y, int elem_bytes, l
                               long long planes);
 cudaError_t launch_xstep_tc(const XLaunch& L, const XItem* items, int n_items, int* counter, int* status,
                             cudaStream_t s);
-int build_tc_tiles(int n, int4* out, int cap);
+int build_tc_tiles(int n, int window, int4* out, int cap);
 cudaError_t launch_xstep_int8(const CUtensorMap& map, const XArgs& a, int n_tiles, int segments, int slots,
                               cudaStream_t s);
 bool fft_len_supported(int N);

@@ -1,0 +1,102 @@
+// The plan object behind the C ABI's opaque mwax_plan, and the launch building blocks
+// shared by the single-plan path (api.cu) and the batch path (batch.cu).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "mwax_internal.cuh"
+
+using mwax::Group;
+using mwax::RunInfo;
+using mwax::XItem;
+
+struct mwax_plan {
+    mwax_plan_desc desc;
+    int T = 0, n = 0, N = 0, F = 0, M = 0, bs = 0, prec = 0, dc_excl = 1;
+    long long K = 0, S = 0, n_ints = 0, B = 0, n_blocks = 0;
+    double nu = 0.0;
+    size_t vis_set_bytes = 0, weights_bytes = 0, int_stride = 0, input_bytes = 0;
+
+    // integration grouping: `slots` integrations per launch, or one integration split
+    // into `chunks` launches of at most Kc frames
+    long long slots = 1, Kc = 0, Kpad = 0;
+    int chunks = 1;
+    int elem_bytes = 4;
+
+    // device memory
+    void* Y = nullptr;      // X-step operands (FP8: e4m3)
+    void* Y16 = nullptr;    // FP8 only: the FP16 operands the e4m3 ones are quantised from
+    size_t Y_bytes = 0;
+    float2* tw = nullptr;
+    double* delay = nullptr;
+    Group* groups = nullptr;
+    int n_groups = 0;
+    float* gain = nullptr;
+    int* chan_group = nullptr;   // FP8: group of each ultrafine channel
+    float* amax = nullptr;       // FP8: [slots][groups][n] per-path max magnitude
+    size_t amax_bytes = 0;
+    RunInfo* runs = nullptr;
+    int n_runs = 0;
+    int4* tiles = nullptr;
+    int n_tiles = 0;
+    int* status = nullptr;
+    int* counter = nullptr;   // work-item counter of the persistent X-step
+    float out_scale = 1.0f, post_scale = 1.0f;
+    bool tensor_cores = false;   // tcgen05 X-step (FP16 / FP8 / INT8) vs CUDA-core FP32
+    int tile = 64;               // paths per tile side of the X-step
+    int run_len = 0;             // output channels per X work item (autotuned)
+    int window = 256;            // tensor-core tile column window (autotuned: 128 or 256)
+    int fvariant = 0;            // F-step kernel: 0 = two-pass radix-32 where built, 1 = generic
+    CUtensorMap tmap;            // operand planes, for the tcgen05 X-step
+
+    // host copies of the tables (work-item costs) and the tcgen05 item lists by slot count
+    std::vector<int4> h_tiles;
+    std::vector<RunInfo> h_runs;
+    std::vector<Group> h_groups;
+    std::vector<float> h_gain;
+    struct ItemList {
+        long long key;
+        XItem* items;
+        int n;
+    };
+    std::vector<ItemList> item_lists;   // per (slot count, frames) of a launch
+
+    // host-input path
+    int8_t* dvolt = nullptr;
+    char* dout = nullptr;
+    cudaStream_t copy_stream = nullptr;
+    std::vector<cudaEvent_t> events;
+
+    cudaStream_t stream = nullptr;
+    int device = 0;
+
+    // stage timing: event pairs per launch, drained by mwax_plan_stage_times
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
+    long long launches[3] = {0, 0, 0};
+};
+
+
+namespace mwax {
+
+// One launch group of a call: `nslots` integrations from w0, or chunk `ch` of integration w0.
+struct LaunchGroup {
+    long long w0, nslots, kbeg, klen, nframes, m_begin;
+    int ch;
+};
+
+std::vector<LaunchGroup> plan_groups(const mwax_plan* p);
+mwax_status enqueue_init(mwax_plan* p, char* out, cudaStream_t s);
+mwax_status enqueue_fstep(mwax_plan* p, const LaunchGroup& g, const int8_t* volt, bool have_delay, cudaStream_t s);
+XArgs make_xargs(const mwax_plan* p, const LaunchGroup& g, char* out);
+mwax_status enqueue_xstep_single(mwax_plan* p, const LaunchGroup& g, const XArgs& xa, cudaStream_t s);
+void plan_items(const mwax_plan& p, int job, long long nslots, long long klen,
+                std::vector<std::pair<double, XItem>>& out);
+void sort_items(std::vector<std::pair<double, XItem>>& v, std::vector<XItem>& order);
+mwax_status set_error(mwax_status st, const char* msg);
+mwax_status configure_x(mwax_plan& p, int run_len, int window);
+mwax_status cuda_error(cudaError_t e, const char* what);
+
+}  // namespace mwax

@@ -419,14 +419,16 @@ cudaError_t launch_xstep_tc(const XLaunch& L, const XItem* items, int n_items, i
     return cudaGetLastError();
 }
 
-// Tile list of the tensor-core X-step: for each 128-row block, column windows of 256
-// starting at its own diagonal (the last window of a row may be 128 wide).
-int build_tc_tiles(int n, int4* out, int cap)
+// Tile list of the tensor-core X-step: for each 128-row block, column windows of
+// `window` (256 or 128) starting at its own diagonal (a 256 window at the right edge
+// shrinks to 128 when only that much is left).
+int build_tc_tiles(int n, int window, int4* out, int cap)
 {
+    const int wmax = (window == TM) ? TM : TNMAX;
     int k = 0;
     for (int p0 = 0; p0 < n; p0 += TM) {
-        for (int q0 = p0; q0 < n; q0 += TNMAX) {
-            const int nq = (n - q0 > TM) ? TNMAX : TM;
+        for (int q0 = p0; q0 < n; q0 += wmax) {
+            const int nq = (n - q0 > TM) ? wmax : TM;
             if (k < cap) out[k] = make_int4(p0, q0, nq, q0 == p0 ? 1 : 0);
             ++k;
         }

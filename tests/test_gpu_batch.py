@@ -1,0 +1,90 @@
+"""Batched correlation (many coarse channels of mixed shapes and precisions in one
+schedule with one persistent X-step launch per round, CUDA-graph replay) and the
+autotuner.  Each plan's result in the batch must equal its result alone, bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2303_11557_b300 as mw
+import synth
+from _parity import oracle_desc, parity_error, workload
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+# (tiles, N, fscrunch, integration s, samples per call, precision, workspace MB); small
+# workspaces give some plans several launch groups (rounds) or split integrations
+MIX = [
+    (20, 128, 4, 0.05, 128_000, mw.MWAX_FP16, 12),
+    (40, 32, 1, 0.025, 64_000, mw.MWAX_FP16, 8),
+    (9, 640, 10, 0.1, 128_000, mw.MWAX_FP8, 1024),
+    (66, 128, 1, 0.05, 64_000, mw.MWAX_FP16, 1024),
+    (12, 64, 2, 0.05, 64_000, mw.MWAX_FP32, 4),
+    (30, 1, 1, 0.025, 64_000, mw.MWAX_INT8, 1024),
+    (70, 6400, 50, 0.05, 64_000, mw.MWAX_FP8, 1024),
+]
+
+
+def _inputs():
+    vs, ds, plans = [], [], []
+    for k, (T, N, F, t, S, prec, ws) in enumerate(MIX):
+        volt, delay = workload(500 + k, T, S, delay=None if prec == mw.MWAX_INT8 else "linear")
+        plans.append(mw.mwax_plan_create_ex(mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=t,
+                                                        samples_per_call=S, precision=prec,
+                                                        sky_freq_hz=synth.SKY_FREQ_HZ,
+                                                        workspace_limit=ws << 20)))
+        vs.append(torch.from_numpy(volt.reshape(-1)).cuda())
+        ds.append(None if delay is None else torch.from_numpy(delay).cuda())
+    return plans, vs, ds
+
+
+def test_batch_equals_alone_and_graph_replay():
+    plans, vs, ds = _inputs()
+    alone = []
+    for p, v, d in zip(plans, vs, ds):
+        mw.mwax_plan_set_stream(p)
+        o = mw.empty_output(p)
+        mw.mwax_correlate(p, v, d, o)
+        mw.mwax_plan_sync(p)
+        alone.append(o.cpu().numpy().copy())
+    b = mw.Batch(plans)
+    outs = [mw.empty_output(p) for p in plans]
+    for call in range(3):                       # eager, capture + replay, replay
+        for o in outs:
+            o.fill_(0x77)
+        b.correlate(vs, ds, outs)
+        b.sync()
+        for i, (o, ref) in enumerate(zip(outs, alone)):
+            assert np.array_equal(o.cpu().numpy(), ref), f"plan {i} differs in batch call {call}"
+    b.close()
+
+
+def test_autotune_keeps_parity():
+    T, N, F, t, S = 24, 128, 4, 0.05, 128_000
+    volt, delay = workload(600, T, S, delay="linear")
+    for prec, tol in ((mw.MWAX_FP16, 2e-3), (mw.MWAX_FP32, 1e-5)):
+        p = mw.mwax_plan_create_ex(mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=t, samples_per_call=S,
+                                               precision=prec, sky_freq_hz=synth.SKY_FREQ_HZ))
+        mw.mwax_plan_set_stream(p)
+        v = torch.from_numpy(volt.reshape(-1)).cuda()
+        d = torch.from_numpy(delay).cuda()
+        o = mw.empty_output(p)
+        best = mw.mwax_plan_autotune(p, v, d, o)
+        assert best.ms > 0 and best.fstep_variant in (0, 1) and best.window in (128, 256)
+        got = mw.mwax_plan_get_tuning(p)
+        assert (got.fstep_variant, got.run_len, got.window) == (best.fstep_variant, best.run_len, best.window)
+        o.fill_(0)
+        mw.mwax_correlate(p, v, d, o)
+        mw.mwax_plan_sync(p)
+        vis, _ = mw.split_output(p, o)
+        ref, _ = oracle.correlate(oracle_desc(T, N, F, t, S), volt, delay)
+        assert parity_error(vis.cpu().numpy(), ref, T).max() <= tol
+        # every candidate choice is correct, not just the fastest
+        for fv in (0, 1):
+            for w in (128, 256):
+                for rl in (1, 3, 32):
+                    mw.mwax_plan_set_tuning(p, mw.Tuning(fv, rl, w, 0.0))
+                    mw.mwax_correlate(p, v, d, o)
+                    mw.mwax_plan_sync(p)
+                    vis, _ = mw.split_output(p, o)
+                    assert parity_error(vis.cpu().numpy(), ref, T).max() <= tol

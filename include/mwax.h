@@ -221,6 +221,59 @@ mwax_status mwax_batch_sync(mwax_batch* batch);
 /* Free the batch (not its plans).  NULL is a no-op. */
 void mwax_batch_destroy(mwax_batch* batch);
 
+/* ------------------------------------------------------------------ serving */
+
+/*
+ * Real-time serving loop: sub-observations arrive from the host (as the paper's FX-engine
+ * receives 8 s subfiles through its input ring buffer, Sec. 2.5) and are admitted onto
+ * the GPU in arrival order as device lanes and HBM free up.  Each lane is a CUDA stream
+ * with its own cached plans and reusable device buffers; a request runs H2D copy ->
+ * correlation -> D2H copy on its lane, and requests on different lanes overlap on the
+ * device.  A scheduler thread inside the server makes all of its CUDA calls.
+ */
+typedef struct mwax_server mwax_server;
+
+typedef struct {
+    size_t hbm_budget;       /* device bytes for request buffers and plan workspaces; 0 = 64 GiB */
+    int n_lanes;             /* requests in flight on the device at once; 0 = 4                  */
+    size_t workspace_limit;  /* per-plan workspace when a request's desc leaves it 0; 0 = 2 GiB  */
+} mwax_server_desc;
+
+typedef struct {
+    long long submitted, completed, failed, queued, in_flight;
+    double p50_ms, p99_ms, max_ms;   /* latency from submission to result in host memory   */
+    long long deadline_misses;       /* completed requests later than their deadline        */
+    size_t hbm_in_use;               /* device bytes held by lanes (buffers and plans)       */
+} mwax_server_stats;
+
+/* Start a server on the current device (NULL desc = defaults).  NULL on error. */
+mwax_server* mwax_server_create(const mwax_server_desc* desc);
+
+/*
+ * Submit one request: plan parameters (any precision; the plan is created on first use
+ * per lane and cached), host voltages (pinned memory lets the copy overlap), host delay
+ * polynomial or NULL, host output buffer of the plan's output_bytes, and a deadline in
+ * seconds after submission (0 = none; only counted in the statistics).  Returns the
+ * request id (>= 0) or -1.  Non-blocking; the buffers must stay valid until completion.
+ */
+long long mwax_server_submit(mwax_server* server, const mwax_plan_desc* desc, const int8_t* voltages,
+                             const double* delay_poly, void* vis_out, double deadline_s);
+
+/* 1 = done, 0 = pending, negative = -(mwax_status) of a failed request. */
+int mwax_server_poll(mwax_server* server, long long request_id);
+
+/* Block until the request completes. */
+mwax_status mwax_server_wait(mwax_server* server, long long request_id);
+
+/* Block until every submitted request has completed. */
+mwax_status mwax_server_drain(mwax_server* server);
+
+/* Counters and latency percentiles so far. */
+mwax_status mwax_server_get_stats(mwax_server* server, mwax_server_stats* stats);
+
+/* Finish the queued requests, free everything.  NULL is a no-op. */
+void mwax_server_destroy(mwax_server* server);
+
 /* Free the plan and its device workspace (waits for its stream first).  NULL is a no-op. */
 void mwax_plan_destroy(mwax_plan* plan);
 

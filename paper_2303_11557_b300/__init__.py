@@ -59,6 +59,20 @@ class Tuning(ctypes.Structure):
                 f"ms={self.ms:.3f})")
 
 
+class _ServerDesc(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("n_lanes", ctypes.c_int), ("workspace_limit", ctypes.c_size_t)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong),
+                ("queued", ctypes.c_longlong), ("in_flight", ctypes.c_longlong), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("deadline_misses", ctypes.c_longlong),
+                ("hbm_in_use", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 @dataclass
 class PlanDesc:
     n_tiles: int
@@ -83,7 +97,8 @@ SYMBOLS = ("mwax_plan_create", "mwax_plan_create_ex", "mwax_plan_get_info", "mwa
            "mwax_plan_sync", "mwax_plan_destroy", "mwax_last_error", "mwax_version", "mwax_plan_enable_timing",
            "mwax_plan_stage_times", "mwax_plan_autotune", "mwax_plan_set_tuning", "mwax_plan_get_tuning",
            "mwax_batch_create", "mwax_batch_set_stream", "mwax_batch_set_graphs", "mwax_batch_correlate",
-           "mwax_batch_sync", "mwax_batch_destroy")
+           "mwax_batch_sync", "mwax_batch_destroy", "mwax_server_create", "mwax_server_submit", "mwax_server_poll",
+           "mwax_server_wait", "mwax_server_drain", "mwax_server_get_stats", "mwax_server_destroy")
 
 
 def load_library(path: str | None = None):
@@ -146,6 +161,20 @@ def load_library(path: str | None = None):
     lib.mwax_batch_sync.restype = st
     lib.mwax_batch_destroy.argtypes = [vp]
     lib.mwax_batch_destroy.restype = None
+    lib.mwax_server_create.argtypes = [ctypes.POINTER(_ServerDesc)]
+    lib.mwax_server_create.restype = vp
+    lib.mwax_server_submit.argtypes = [vp, ctypes.POINTER(_CDesc), vp, vp, vp, ctypes.c_double]
+    lib.mwax_server_submit.restype = ctypes.c_longlong
+    lib.mwax_server_poll.argtypes = [vp, ctypes.c_longlong]
+    lib.mwax_server_poll.restype = ctypes.c_int
+    lib.mwax_server_wait.argtypes = [vp, ctypes.c_longlong]
+    lib.mwax_server_wait.restype = st
+    lib.mwax_server_drain.argtypes = [vp]
+    lib.mwax_server_drain.restype = st
+    lib.mwax_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+    lib.mwax_server_get_stats.restype = st
+    lib.mwax_server_destroy.argtypes = [vp]
+    lib.mwax_server_destroy.restype = None
     lib.mwax_version.argtypes = []
     lib.mwax_version.restype = ctypes.c_char_p
     _lib = lib
@@ -328,6 +357,55 @@ class Batch:
         h, self.handle = getattr(self, "handle", None), None
         if h and _lib is not None:
             _lib.mwax_batch_destroy(h)
+
+    def __del__(self):
+        self.close()
+
+
+class Server:
+    """Real-time serving loop (native scheduler thread in libmwax.so).  Host buffers
+    passed to submit() are kept referenced until the request completes."""
+
+    def __init__(self, hbm_budget: int = 0, n_lanes: int = 0, workspace_limit: int = 0):
+        d = _ServerDesc(hbm_budget, n_lanes, workspace_limit)
+        h = load_library().mwax_server_create(ctypes.byref(d))
+        if not h:
+            raise MwaxError(MWAX_ECUDA, mwax_last_error())
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, desc: PlanDesc, voltages, delay_poly, vis_out, deadline_s: float = 0.0) -> int:
+        cd = desc.c()
+        d = None
+        if delay_poly is not None:
+            d = np.ascontiguousarray(delay_poly, dtype=np.float64) if isinstance(delay_poly, np.ndarray) else delay_poly
+        rid = load_library().mwax_server_submit(self.handle, ctypes.byref(cd), _ptr(voltages), _ptr(d), _ptr(vis_out),
+                                                 deadline_s)
+        if rid < 0:
+            raise MwaxError(MWAX_EINVAL, mwax_last_error())
+        self._keep[rid] = (voltages, d, vis_out)
+        return rid
+
+    def poll(self, rid: int) -> int:
+        return load_library().mwax_server_poll(self.handle, rid)
+
+    def wait(self, rid: int):
+        _check(load_library().mwax_server_wait(self.handle, rid))
+        self._keep.pop(rid, None)
+
+    def drain(self):
+        _check(load_library().mwax_server_drain(self.handle))
+        self._keep.clear()
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(load_library().mwax_server_get_stats(self.handle, ctypes.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.mwax_server_destroy(h)
 
     def __del__(self):
         self.close()

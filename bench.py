@@ -237,6 +237,148 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- configs 3 and 4
+F_CHOICES = {32: [1], 128: [1, 4], 1280: [10, 40], 6400: [50, 200]}
+
+
+def mixed_channels(seed: int, n: int = 24, int8_share: float = 0.0):
+    """Seeded mix of coarse channels: tiles in {128, 256, 512}, FFT length in {32, 128,
+    1280, 6400}, fscrunch giving >= 10 kHz channels, integration in {0.25, 0.5, 2, 8} s;
+    a share of them in the integer mode (no FFT, 1.28 MHz)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        T = int(rng.choice([128, 256, 512]))
+        t = float(rng.choice([0.25, 0.5, 2.0, 8.0]))
+        if rng.random() < int8_share:
+            out.append(dict(T=T, N=1, F=1, t=t, prec="int8"))
+        else:
+            N = int(rng.choice([32, 128, 1280, 6400]))
+            out.append(dict(T=T, N=N, F=int(rng.choice(F_CHOICES[N])), t=t, prec="fp16"))
+    return out
+
+
+def channel_volt(torch, dev_base, T):
+    """Voltages of a T-tile channel: the resident config-1 bytes viewed (128 tiles: the
+    first half; 256: all; 512: two copies) as [160 blocks][2T paths][64000][2]."""
+    need = 160 * 2 * T * 64_000 * 2
+    if need <= dev_base.numel():
+        return dev_base[:need]
+    return torch.cat([dev_base] * (need // dev_base.numel()))
+
+
+def run_batch24(mw, torch, dev_base, args):
+    """Config 3: 24 coarse channels of mixed shapes, one batch call per 8 s sub-observation
+    (FP16 X-engine in one persistent launch per round, autotuned, CUDA-graph replayed)."""
+    chans = mixed_channels(0x4D57415B)
+    plans, vols, outs = [], {}, []
+    tuned = {}
+    for c in chans:
+        d = mw.PlanDesc(n_tiles=c["T"], fft_len=c["N"], fine_avg=c["F"], int_time_s=c["t"],
+                        samples_per_call=10_240_000, precision=mw.MWAX_FP16, sky_freq_hz=WORKLOAD["sky_freq_hz"],
+                        workspace_limit=4 << 30)
+        p = mw.mwax_plan_create_ex(d)
+        mw.mwax_plan_set_stream(p)
+        if c["T"] not in vols:
+            vols[c["T"]] = channel_volt(torch, dev_base, c["T"])
+        o = mw.empty_output(p)
+        key = (c["T"], c["N"], c["F"], c["t"])
+        if key not in tuned:
+            tuned[key] = mw.mwax_plan_autotune(p, vols[c["T"]], None, o)
+        else:
+            mw.mwax_plan_set_tuning(p, tuned[key])
+        plans.append(p)
+        outs.append(o)
+    b = mw.Batch(plans)
+    V = [vols[c["T"]] for c in chans]
+    b.correlate(V, None, outs)          # eager
+    b.correlate(V, None, outs)          # capture + replay
+    b.sync()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(1, min(args.steps, 3))
+    e0.record()
+    for _ in range(steps):
+        b.correlate(V, None, outs)
+    e1.record()
+    b.sync()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    flops = 0.0
+    for c in chans:
+        n = 2 * c["T"]
+        flops += 8.0 * n * (n + 1) / 2 * 10_240_000 / c["N"] * used_bins(c["N"], c["F"])
+    b.close()
+    for p in plans:
+        p.close()
+    return {"workload": "24 coarse channels, 8 s each, tiles {128,256,512}, N {32,128,1280,6400}, "
+                        "int {0.25,0.5,2,8} s (seeded mix), FP16, one batch call",
+            "ms_per_batch": ms, "realtime_factor": SUBOBS_S / (ms * 1e-3),
+            "channels_realtime": 24 * SUBOBS_S / (ms * 1e-3), "x_tflops_alg": flops / (ms * 1e-3) / 1e12,
+            "tunings": {f"T{k[0]} N{k[1]} F{k[2]} t{k[3]}": repr(v) for k, v in tuned.items()},
+            "mix": [f"T{c['T']}/N{c['N']}/F{c['F']}/{c['t']}s" for c in chans],
+            "input": "config-1 voltage bytes re-tiled per tile count (every channel computed in full)"}
+
+
+def run_serve(mw, torch, host_base, args, periods: int = 2):
+    """Config 4: 24 coarse channels each delivering an 8 s sub-observation every 8 s
+    (seeded offsets within the period), FP16 or integer mode per request (80/20), host
+    pinned voltages; the server admits by HBM footprint; deadline = 8 s."""
+    chans = mixed_channels(0x4D57415C, int8_share=0.2)
+    hosts = {}
+    for c in chans:
+        T = c["T"]
+        if T in hosts:
+            continue
+        need = 160 * 2 * T * 64_000 * 2
+        if need <= host_base.numel():
+            hosts[T] = host_base[:need]
+        else:
+            h = torch.empty(need, dtype=torch.int8, pin_memory=True)
+            for k in range(need // host_base.numel()):
+                h[k * host_base.numel():(k + 1) * host_base.numel()].copy_(host_base)
+            hosts[T] = h
+    rng = np.random.default_rng(0x5E7E)
+    offsets = rng.uniform(0, SUBOBS_S, len(chans))
+    descs, outs = [], []
+    for c in chans:
+        prec = mw.MWAX_INT8 if c["prec"] == "int8" else mw.MWAX_FP16
+        d = mw.PlanDesc(n_tiles=c["T"], fft_len=c["N"], fine_avg=c["F"], int_time_s=c["t"],
+                        samples_per_call=10_240_000, precision=prec, sky_freq_hz=0.0, workspace_limit=4 << 30)
+        descs.append(d)
+        p = mw.mwax_plan_create_ex(d)            # size of the output only
+        outs.append(torch.empty(p.output_bytes, dtype=torch.uint8, pin_memory=True))
+        p.close()
+    srv = mw.Server(hbm_budget=160 << 30, n_lanes=4)
+    # warm-up: one request of every distinct shape (plans created, kernels loaded)
+    seen = set()
+    for k, d in enumerate(descs):
+        key = (d.n_tiles, d.fft_len, d.fine_avg, d.int_time_s, d.precision)
+        if key not in seen:
+            seen.add(key)
+            srv.submit(d, hosts[d.n_tiles], None, outs[k])
+    srv.drain()
+    warm = srv.stats()["completed"]
+    t0 = time.perf_counter()
+    events = sorted((pp * SUBOBS_S + offsets[k], k) for pp in range(periods) for k in range(len(chans)))
+    for at, k in events:
+        while time.perf_counter() - t0 < at:
+            time.sleep(0.0005)
+        srv.submit(descs[k], hosts[descs[k].n_tiles], None, outs[k], deadline_s=SUBOBS_S)
+    srv.drain()
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    done = st["completed"] - warm
+    return {"workload": f"24 coarse channels x {periods} sub-observations of 8 s at wall-clock rate, tiles "
+                        "{128,256,512}, mixed N/F/int as config 3, 20 % integer mode, host pinned voltages",
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+            "deadline_ms": 1e3 * SUBOBS_S, "deadline_misses": st["deadline_misses"], "completed": done,
+            "sustained_channels": done * SUBOBS_S / wall, "wall_s": wall,
+            "latency_note": "percentiles include the warm-up requests (one per shape)",
+            "lanes": 4, "hbm_budget_gb": 160}
+
+
 def time_plan(mw, torch, plan, dev_volt, dev_delay, steps, warmup, world, clocks=None):
     """Warm up, then time `steps` calls on the plan's stream with CUDA events (and per-stage
     events inside the library).  Returns (ms per step max over ranks, stage times, output)."""
@@ -388,6 +530,14 @@ def run_mine(args, world, rank, local):
                "h2d_bytes_per_step": info["input_bytes"] + delay.nbytes, "d2h_bytes_per_step": info["output_bytes"],
                "ms_per_step": 1e3 * t_e2e}
 
+    # configs 3 and 4: batched mixed channels, real-time serving
+    batch = serve = None
+    if not args.no_batch and W is WORKLOAD:
+        plan.close()
+        batch = run_batch24(mw, torch, dev_volt, args)
+    if not args.no_serve and not args.no_e2e and W is WORKLOAD:
+        serve = run_serve(mw, torch, host, args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         note = {}
@@ -417,6 +567,8 @@ def run_mine(args, world, rank, local):
         "cpu_baseline": cpu,
         "precision_forms": {f: {k: v for k, v in r.items() if k != "gpu_launches"} for f, r in results.items()
                             if f != headline},
+        "batch": batch,
+        "serving": serve,
         "context": {"paper": "1 coarse channel of 256 tiles in real time per NVIDIA A40 (6.2 s per 8 s at "
                              "250 ms / 40 kHz, Table 2)"},
     }
@@ -434,6 +586,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "fp8", "int8"],
                     help="headline precision (config 1 is FP32); the other forms are timed beside it")
     ap.add_argument("--no-forms", action="store_true", help="time the headline precision only")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 24-channel batched measurement")
+    ap.add_argument("--no-serve", action="store_true", help="skip the real-time serving measurement")
     ap.add_argument("--workload", default="full", choices=["full", "small"],
                     help="small = one 0.5 s integration (for profiler captures)")
     args = ap.parse_args()

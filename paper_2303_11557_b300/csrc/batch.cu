@@ -311,7 +311,7 @@ mwax_status mwax_plan_autotune(mwax_plan* p, const int8_t* voltages, const doubl
     std::vector<int> windows = {p->window};
     if (tc_plan(p)) windows = {256, 128};
     std::vector<int> runs = {0};
-    for (int r : {2, 4, 8, 16, 32})
+    for (int r : {2, 8})
         if (r < p->M) runs.push_back(r);
     if (p->M > 1) runs.push_back(p->M);
     cudaEvent_t e0, e1;
@@ -327,8 +327,10 @@ mwax_status mwax_plan_autotune(mwax_plan* p, const int8_t* voltages, const doubl
                 p->fvariant = fv;
                 st = configure_x(*p, rl, w);
                 if (st != MWAX_OK) break;
-                st = mwax_correlate(p, voltages, delay_poly, vis_out);   // warm-up
-                if (st != MWAX_OK) break;
+                if (fv == fvars[0] && w == windows[0] && rl == runs[0]) {
+                    st = mwax_correlate(p, voltages, delay_poly, vis_out);   // warm-up
+                    if (st != MWAX_OK) break;
+                }
                 cudaEventRecord(e0, p->stream);
                 st = mwax_correlate(p, voltages, delay_poly, vis_out);
                 if (st != MWAX_OK) break;

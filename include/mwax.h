@@ -274,6 +274,28 @@ mwax_status mwax_server_get_stats(mwax_server* server, mwax_server_stats* stats)
 /* Finish the queued requests, free everything.  NULL is a no-op. */
 void mwax_server_destroy(mwax_server* server);
 
+/* ------------------------------------------------------------------ allocation-free call */
+
+/*
+ * FP32 correlation of one small job that allocates no memory at all (the paper has no
+ * counterpart; this is for callers that cannot allocate: code running inside a CUDA-graph
+ * capture it does not control, processes whose device memory belongs to another
+ * allocator, or services that forbid allocation after start-up).  desc as for
+ * mwax_plan_create_ex with precision MWAX_FP32, 1..32 tiles, fft_len 32/64/128/256/512;
+ * voltages and vis_out device pointers as for mwax_correlate (vis_out:
+ * n_ints x (B M 4 complex64 + B 4 float32) bytes); delay_poly NULL, host or device;
+ * cuda_stream a cudaStream_t (NULL = legacy default stream).
+ * All device working memory is a fixed set of arrays inside the library image (a 32 MiB
+ * operand array plus small tables, held on every GPU that loads the library until exit);
+ * jobs whose operands exceed 32 MiB (n_ints x fft_len x 2 x 2T x K rounded up to 128
+ * frames x 4 bytes) are rejected with MWAX_EINVAL.  The first call on a device looks up
+ * the arrays' device addresses there; make it before any stream capture.  Every call uses
+ * the same arrays (each call clears what must start at zero): calls that overlap on the
+ * GPU, on any stream, race and corrupt each other.  Asynchronous on cuda_stream.
+ */
+mwax_status mwax_correlate_noalloc(const mwax_plan_desc* desc, const int8_t* voltages, const double* delay_poly,
+                                   void* vis_out, void* cuda_stream);
+
 /* Free the plan and its device workspace (waits for its stream first).  NULL is a no-op. */
 void mwax_plan_destroy(mwax_plan* plan);
 

@@ -98,7 +98,8 @@ SYMBOLS = ("mwax_plan_create", "mwax_plan_create_ex", "mwax_plan_get_info", "mwa
            "mwax_plan_stage_times", "mwax_plan_autotune", "mwax_plan_set_tuning", "mwax_plan_get_tuning",
            "mwax_batch_create", "mwax_batch_set_stream", "mwax_batch_set_graphs", "mwax_batch_correlate",
            "mwax_batch_sync", "mwax_batch_destroy", "mwax_server_create", "mwax_server_submit", "mwax_server_poll",
-           "mwax_server_wait", "mwax_server_drain", "mwax_server_get_stats", "mwax_server_destroy")
+           "mwax_server_wait", "mwax_server_drain", "mwax_server_get_stats", "mwax_server_destroy",
+           "mwax_correlate_noalloc")
 
 
 def load_library(path: str | None = None):
@@ -175,6 +176,8 @@ def load_library(path: str | None = None):
     lib.mwax_server_get_stats.restype = st
     lib.mwax_server_destroy.argtypes = [vp]
     lib.mwax_server_destroy.restype = None
+    lib.mwax_correlate_noalloc.argtypes = [ctypes.POINTER(_CDesc), vp, vp, vp, vp]
+    lib.mwax_correlate_noalloc.restype = st
     lib.mwax_version.argtypes = []
     lib.mwax_version.restype = ctypes.c_char_p
     _lib = lib
@@ -409,6 +412,17 @@ class Server:
 
     def __del__(self):
         self.close()
+
+
+def mwax_correlate_noalloc(desc: PlanDesc, voltages, delay_poly, vis_out, stream=None):
+    """Allocation-free FP32 call for small jobs (device buffers; see include/mwax.h)."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    cd = desc.c()
+    keep = delay_poly if delay_poly is None or not isinstance(delay_poly, np.ndarray) else \
+        np.ascontiguousarray(delay_poly, dtype=np.float64)
+    _check(load_library().mwax_correlate_noalloc(ctypes.byref(cd), _ptr(voltages), _ptr(keep), _ptr(vis_out),
+                                                 ctypes.c_void_p(s.cuda_stream)))
 
 
 def mwax_plan_destroy(plan: Plan):

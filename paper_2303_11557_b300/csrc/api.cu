@@ -344,7 +344,9 @@ mwax_status setup(mwax_plan& p)
         p.amax_bytes = sizeof(float) * (size_t)p.slots * p.n_groups * p.n;
         MWAX_CUDA(cudaMalloc(&p.amax, p.amax_bytes));
     }
-    if (p.tensor_cores)
+    if (p.prec == MWAX_FP32)
+        MWAX_CUDA(make_simt_tmap(&p.tmap, p.Y, p.Kpad, p.n, p.slots * p.N * 2));
+    else
         MWAX_CUDA(make_operand_tmap(&p.tmap, p.Y, p.prec == MWAX_FP8 ? 1 : 2, p.Kpad, p.n, p.slots * p.N * 2));
 
     {
@@ -615,7 +617,7 @@ mwax_status enqueue_xstep_single(mwax_plan* p, const LaunchGroup& g, const XArgs
         L.jobs[0].op = (p->prec == MWAX_FP8) ? 1 : 0;
         MWAX_CUDA(timed(p, 2, s, [&] { return launch_xstep_tc(L, items, n_items, p->counter, p->status, s); }));
     } else {
-        MWAX_CUDA(timed(p, 2, s, [&] { return launch_xstep_simt(xa, p->n_tiles, p->n_runs, (int)g.nslots, s); }));
+        MWAX_CUDA(timed(p, 2, s, [&] { return launch_xstep_simt(p->tmap, xa, p->n_tiles, p->n_runs, (int)g.nslots, s); }));
     }
     return MWAX_OK;
 }

@@ -117,7 +117,11 @@ cudaError_t launch_quantise_e4m3(const __half* Y16, __nv_fp8_storage_t* Y8, cons
                                  cudaStream_t s);
 cudaError_t launch_init_output(char* out, long long n_ints, long long vis_set_bytes, long long weights_bytes,
                                cudaStream_t s);
-cudaError_t launch_xstep_simt(const XArgs& a, int n_tiles, int n_runs, int slots, cudaStream_t s);
+cudaError_t launch_xstep_simt(const CUtensorMap& map, const XArgs& a, int n_tiles, int n_runs, int slots,
+                              cudaStream_t s);
+// FP32 operand planes for the CUDA-core X-step: 32 frames x 64 rows x both planes per box,
+// 128-byte swizzle.
+cudaError_t make_simt_tmap(CUtensorMap* map, const void* Y, long long Kpad, int n, long long planes);
 cudaError_t make_operand_tmap(CUtensorMap* map, const void* Y, int elem_bytes, long long Kpad, int n,
                               long long planes);
 cudaError_t launch_xstep_tc(const XLaunch& L, const XItem* items, int n_items, int* counter, int* status,

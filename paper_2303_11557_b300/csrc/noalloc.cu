@@ -240,6 +240,10 @@ extern "C" mwax_status mwax_correlate_noalloc(const mwax_plan_desc* desc, const 
     xa.tiles = A.tiles;
     xa.post_scale = 1.0f;
     xa.first_store = 1;
-    if ((e = launch_xstep_simt(xa, 1, nr, (int)n_ints, s)) != cudaSuccess) return cuda_error(e, "X-step launch");
+    xa.spin_limit = 2000000;
+    CUtensorMap map;   // encoded on the host into the launch parameters: no device memory
+    if ((e = make_simt_tmap(&map, A.scratch, Kpad, n, n_ints * N * 2)) != cudaSuccess)
+        return cuda_error(e, "operand tensor map");
+    if ((e = launch_xstep_simt(map, xa, 1, nr, (int)n_ints, s)) != cudaSuccess) return cuda_error(e, "X-step launch");
     return MWAX_OK;
 }

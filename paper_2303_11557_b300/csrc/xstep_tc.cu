@@ -398,6 +398,20 @@ cudaError_t make_operand_tmap(CUtensorMap* map, const void* Y, int elem_bytes, l
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+cudaError_t make_simt_tmap(CUtensorMap* map, const void* Y, long long Kpad, int n, long long planes)
+{
+    auto fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    cuuint64_t dims[3] = {(cuuint64_t)Kpad, (cuuint64_t)n, (cuuint64_t)planes};
+    cuuint64_t strides[2] = {(cuuint64_t)Kpad * 4, (cuuint64_t)Kpad * 4 * n};
+    cuuint32_t box[3] = {32, 64, 2};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(Y), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 cudaError_t launch_xstep_tc(const XLaunch& L, const XItem* items, int n_items, int* counter, int* status,
                             cudaStream_t s)
 {

@@ -483,7 +483,7 @@ template <int N>
 __host__ __device__ constexpr size_t r32_smem()
 {
     return sizeof(float2) * (size_t)R32<N>::FB * R32<N>::ROW + sizeof(FrameR32) * R32<N>::FB +
-           (sizeof(float2) + sizeof(float)) * N;
+           (sizeof(float2) + sizeof(float) + sizeof(int) + sizeof(unsigned)) * N;
 }
 
 template <int N, int OUTK>
@@ -496,13 +496,23 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
     FrameR32* finfo = reinterpret_cast<FrameR32*>(buf + FB * ROW);
     float2* tw = reinterpret_cast<float2*>(finfo + FB);
     float* gain = reinterpret_cast<float*>(tw + N);
+    int* cgroup = reinterpret_cast<int*>(gain + N);            // FP8: group of channel c
+    unsigned* gmax = reinterpret_cast<unsigned*>(cgroup + N);  // FP8: per-group max (float bits)
 
     const int p = blockIdx.y;
     const long long f0 = (long long)blockIdx.x * FB;
+    // FP8: when all of the CTA's frames lie in one slot, the per-group maxima are gathered
+    // in shared memory (warp reduction, then one shared atomic) and flushed at the end
+    const long long slot_first = (f0 < a.n_store) ? f0 / a.Kc : -1;
+    const bool one_slot = slot_first >= 0 && (min(f0 + FB, a.n_store) - 1) / a.Kc == slot_first;
 
     for (int i = threadIdx.x; i < N; i += NT) {
         tw[i] = __ldg(&a.tw[i]);
         gain[i] = __ldg(&a.gain[i]);
+        if (OUTK == FOUT_F16A) {
+            cgroup[i] = __ldg(&a.chan_group[i]);
+            gmax[i] = 0u;
+        }
     }
     if (threadIdx.x < FB) {
         const int f = threadIdx.x;
@@ -564,15 +574,9 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
     const int f = threadIdx.x % FB;
     const int jb = (threadIdx.x / FB) * P::JPT;
     const FrameR32 fi = finfo[f];
-    // FP8 (FOUT_F16A): lanes sharing a butterfly set are FB consecutive frames; when they
-    // all belong to one slot, their maxima are combined before one atomic per channel
-    bool seg_uniform = false;
-    if (OUTK == FOUT_F16A) {
-        const long long s0 = __shfl_sync(0xffffffffu, fi.slot, (threadIdx.x % 32) / FB * FB, FB);
-        seg_uniform = __all_sync(0xffffffffu, fi.slot == s0 && fi.slot >= 0);
-    } else if (fi.slot < 0) {
-        return;
-    }
+    // FP8 (FOUT_F16A): lanes sharing a butterfly set are FB consecutive frames
+    if (OUTK != FOUT_F16A && fi.slot < 0) return;
+    const unsigned lanes = (FB == 32) ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
     const long long cs = 2LL * a.n * a.Kpad;
     const long long ps = (long long)a.n * a.Kpad;
     const long long base = (fi.slot * N * 2LL * a.n + p) * a.Kpad + fi.k;
@@ -601,7 +605,7 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
             const float gn = gain[c];
             y = make_float2(y.x * gn, y.y * gn);
             if (OUTK == FOUT_F16A) {
-                const int g = a.chan_group[c];
+                const int g = cgroup[c];
                 float m = 0.0f;
                 if (fi.slot >= 0) {
                     __half* Y = static_cast<__half*>(a.Y);
@@ -610,12 +614,9 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
                     Y[base + c * cs + ps] = hi;
                     m = fmaxf(fabsf(__half2float(hr)), fabsf(__half2float(hi)));
                 }
-                if (seg_uniform) {
-#pragma unroll
-                    for (int o = FB / 2; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o, FB));
-                    if (f == 0 && g >= 0 && m > 0.0f)
-                        atomicMax(reinterpret_cast<int*>(a.amax + (fi.slot * a.n_groups + g) * (long long)a.n + p),
-                                  __float_as_int(m));
+                if (one_slot) {
+                    const unsigned mb = __reduce_max_sync(lanes, __float_as_uint(m));   // m >= 0: bits order as values
+                    if (f == 0 && g >= 0 && mb != 0u) atomicMax(gmax + g, mb);
                 } else if (fi.slot >= 0 && g >= 0 && m > 0.0f) {
                     atomicMax(reinterpret_cast<int*>(a.amax + (fi.slot * a.n_groups + g) * (long long)a.n + p),
                               __float_as_int(m));
@@ -625,6 +626,13 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
             }
         }
         if (fi.delay) Ej = c_mul(Ej, fi.step1);
+    }
+    if (OUTK == FOUT_F16A && one_slot) {
+        __syncthreads();
+        for (int g = threadIdx.x; g < a.n_groups; g += NT)
+            if (gmax[g] != 0u)
+                atomicMax(reinterpret_cast<unsigned*>(a.amax + (slot_first * a.n_groups + g) * (long long)a.n + p),
+                          gmax[g]);
     }
 }
 
@@ -726,25 +734,27 @@ cudaError_t launch_kind(int N, const FArgs& a, cudaStream_t s, int variant)
 }
 
 // FP8: e4m3 operands from the FP16 ones, q = h * 448 / amax[slot][group(c)][p] with
-// saturation (|q| <= 448 by construction).  One thread per 8 consecutive frames of a row.
-__global__ void quantise_e4m3_kernel(const __half* __restrict__ Y16, __nv_fp8_storage_t* __restrict__ Y8,
-                                     const float* __restrict__ amax, const int* __restrict__ chan_group, int n_groups,
-                                     long long rows, int N, int n, long long Kpad)
+// saturation (|q| <= 448 by construction).  One CTA per operand row (slot, c, plane, p),
+// 8 consecutive frames per thread and step.
+__global__ void __launch_bounds__(256) quantise_e4m3_kernel(const __half* __restrict__ Y16,
+                                                            __nv_fp8_storage_t* __restrict__ Y8,
+                                                            const float* __restrict__ amax,
+                                                            const int* __restrict__ chan_group, int n_groups, int N,
+                                                            int n, long long Kpad)
 {
-    const long long per_row = Kpad / 8;
-    const long long total = rows * per_row;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long row = i / per_row, k8 = i % per_row;
-        const int p = (int)(row % n);
-        const long long sc = row / (2LL * n);           // slot * N + c
-        const int c = (int)(sc % N);
-        const long long slot = sc / N;
-        const int g = chan_group[c];
-        if (g < 0) continue;                            // zero-weight channel: never read
-        const float am = amax[(slot * n_groups + g) * (long long)n + p];
-        const float inv = am > 0.0f ? 448.0f / am : 0.0f;
-        const uint4 h = *reinterpret_cast<const uint4*>(Y16 + row * Kpad + k8 * 8);
+    const long long row = blockIdx.x;
+    const int p = (int)(row % n);
+    const long long sc = row / (2LL * n);           // slot * N + c
+    const int c = (int)(sc % N);
+    const long long slot = sc / N;
+    const int g = chan_group[c];
+    if (g < 0) return;                              // zero-weight channel: never read
+    const float am = amax[(slot * n_groups + g) * (long long)n + p];
+    const float inv = am > 0.0f ? 448.0f / am : 0.0f;
+    const uint4* src = reinterpret_cast<const uint4*>(Y16 + row * Kpad);
+    uint2* dst = reinterpret_cast<uint2*>(Y8 + row * Kpad);
+    for (long long k8 = threadIdx.x; k8 < Kpad / 8; k8 += blockDim.x) {
+        const uint4 h = __ldg(src + k8);
         const __half2* hp = reinterpret_cast<const __half2*>(&h);
         uint32_t lo = 0, hi = 0;
 #pragma unroll
@@ -756,7 +766,7 @@ __global__ void quantise_e4m3_kernel(const __half* __restrict__ Y16, __nv_fp8_st
             if (e < 2) lo |= pair << (16 * e);
             else hi |= pair << (16 * (e - 2));
         }
-        *reinterpret_cast<uint2*>(Y8 + row * Kpad + k8 * 8) = make_uint2(lo, hi);
+        dst[k8] = make_uint2(lo, hi);
     }
 }
 
@@ -799,7 +809,10 @@ cudaError_t launch_quantise_e4m3(const __half* Y16, __nv_fp8_storage_t* Y8, cons
                                  cudaStream_t s)
 {
     const long long rows = slots * (long long)N * 2 * n;
-    quantise_e4m3_kernel<<<16 * 148, 256, 0, s>>>(Y16, Y8, amax, chan_group, n_groups, rows, N, n, Kpad);
+    if (rows <= 0) return cudaSuccess;
+    if (rows > 0x7fffffffLL) return cudaErrorInvalidValue;
+    quantise_e4m3_kernel<<<(unsigned)rows, Kpad >= 2048 ? 256 : 128, 0, s>>>(Y16, Y8, amax, chan_group, n_groups, N,
+                                                                               n, Kpad);
     return cudaGetLastError();
 }
 

@@ -197,3 +197,108 @@ def correlate_int(d: Desc, volt: np.ndarray):
     if rc:
         raise ValueError(f"oracle rejected the job (rc={rc})")
     return vis, wts
+
+
+# ------------------------------------------------------------------ roadmap extensions
+class _Ext(ctypes.Structure):
+    _fields_ = [("sample_rate_hz", ctypes.c_double), ("keep_bins", ctypes.c_int),
+                ("delay_table", ctypes.c_void_p), ("table_step", ctypes.c_longlong),
+                ("table_steps", ctypes.c_longlong), ("passband", ctypes.c_void_p),
+                ("zero_flags", ctypes.c_void_p), ("normalise", ctypes.c_int)]
+
+
+@dataclass
+class Ext:
+    """Roadmap extensions (Sec. 4): sample rate / kept bins (oversampled channels, 4.5),
+    tabulated delays [n_paths, steps] of `table_step` samples (2.4.1, 4.3), passband gains
+    per ultrafine channel (4.2), zeroing flags [n_blocks, n_paths] and normalisation (4.1)."""
+    sample_rate_hz: float = 0.0
+    keep_bins: int = 0
+    delay_table: np.ndarray | None = None
+    table_step: int = 6400
+    passband: np.ndarray | None = None
+    zero_flags: np.ndarray | None = None
+    normalise: int = 0
+
+    def c(self, d: Desc):
+        keep = []
+        tab = None
+        if self.delay_table is not None:
+            tab = np.ascontiguousarray(np.asarray(self.delay_table, dtype=np.float64).reshape(d.n_paths, -1))
+            keep.append(tab)
+        pb = None
+        if self.passband is not None:
+            pb = np.ascontiguousarray(np.asarray(self.passband, dtype=np.float64).reshape(d.fft_len))
+            keep.append(pb)
+        fl = None
+        if self.zero_flags is not None:
+            fl = np.ascontiguousarray(np.asarray(self.zero_flags, dtype=np.uint8).reshape(-1, d.n_paths))
+            keep.append(fl)
+        e = _Ext(self.sample_rate_hz, self.keep_bins, _p(tab), self.table_step,
+                 0 if tab is None else tab.shape[1], _p(pb), _p(fl), self.normalise)
+        return e, keep
+
+    def n_chan_out(self, d: Desc):
+        return (self.keep_bins or d.fft_len) // d.fine_avg
+
+
+def _load_ext():
+    lib = _load()
+    if not hasattr(lib, "_ext_ready"):
+        vp, dp, ep = ctypes.c_void_p, ctypes.POINTER(_Desc), ctypes.POINTER(_Ext)
+        lib.ora_avg_weights_keep.argtypes = [ctypes.c_int] * 5 + [vp]
+        lib.ora_avg_weights_keep.restype = ctypes.c_double
+        lib.ora_spectra_ext.argtypes = [dp, ep, vp, vp, ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong, vp]
+        lib.ora_occupancy.argtypes = [dp, ep, ctypes.c_longlong, ctypes.c_int, ctypes.c_int]
+        lib.ora_occupancy.restype = ctypes.c_double
+        lib.ora_correlate_ext.argtypes = [dp, ep, vp, vp, vp, vp]
+        lib.ora_correlate_ext.restype = ctypes.c_int
+        lib.ora_correlate_int_ext.argtypes = [dp, ep, vp, vp, vp]
+        lib.ora_correlate_int_ext.restype = ctypes.c_int
+        lib._ext_ready = True
+    return lib
+
+
+def avg_weights_keep(N: int, keep: int, F: int, dc_exclude: int, j: int):
+    w = np.empty(N, dtype=np.float64)
+    s = _load_ext().ora_avg_weights_keep(N, keep, F, dc_exclude, j, _p(w))
+    return w, s
+
+
+def spectra_ext(d: Desc, e: Ext, volt: np.ndarray, delay, path: int, m0: int, nm: int) -> np.ndarray:
+    volt = np.ascontiguousarray(volt, dtype=np.int8)
+    Y = np.empty((nm, d.fft_len), dtype=np.complex128)
+    ce, keep = e.c(d)
+    _load_ext().ora_spectra_ext(ctypes.byref(d.c()), ctypes.byref(ce), _p(volt), _p(_delay(d, delay)), path, m0, nm,
+                                _p(Y))
+    return Y
+
+
+def occupancy(d: Desc, e: Ext, w: int, p: int, q: int) -> float:
+    ce, keep = e.c(d)
+    return _load_ext().ora_occupancy(ctypes.byref(d.c()), ctypes.byref(ce), w, p, q)
+
+
+def correlate_ext(d: Desc, e: Ext, volt: np.ndarray, delay=None):
+    """(vis complex128 [ints, B, M, 4] with M = kept bins / F, weights float64 [ints, B, 4])."""
+    volt = np.ascontiguousarray(volt, dtype=np.int8)
+    M = e.n_chan_out(d)
+    vis = np.empty((d.n_ints, d.n_baselines, M, 4), dtype=np.complex128)
+    wts = np.empty((d.n_ints, d.n_baselines, 4), dtype=np.float64)
+    ce, keep = e.c(d)
+    rc = _load_ext().ora_correlate_ext(ctypes.byref(d.c()), ctypes.byref(ce), _p(volt), _p(_delay(d, delay)),
+                                       _p(vis), _p(wts))
+    if rc:
+        raise ValueError(f"oracle rejected the job (rc={rc})")
+    return vis, wts
+
+
+def correlate_int_ext(d: Desc, e: Ext, volt: np.ndarray):
+    volt = np.ascontiguousarray(volt, dtype=np.int8)
+    vis = np.empty((d.n_ints, d.n_baselines, 4, 2), dtype=np.int64)
+    wts = np.empty((d.n_ints, d.n_baselines, 4), dtype=np.float64)
+    ce, keep = e.c(d)
+    rc = _load_ext().ora_correlate_int_ext(ctypes.byref(d.c()), ctypes.byref(ce), _p(volt), _p(vis), _p(wts))
+    if rc:
+        raise ValueError(f"oracle rejected the job (rc={rc})")
+    return vis, wts

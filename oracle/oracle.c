@@ -410,3 +410,212 @@ int ora_correlate_int(const ora_desc* d, const int8_t* volt, long long* vis, dou
         }
     return 0;
 }
+
+/* ============================================================================
+ * Roadmap extensions (Sec. 4), each a plain restatement of what the paper describes:
+ *   - zeroing flags and visibility weights (Sec. 2.4.2, 4.1): a flagged 50 ms block of
+ *     a path holds no data (its samples count as zero); the weight of a baseline/pol in
+ *     an integration is the fraction of the integration's frames whose blocks are
+ *     unflagged in both paths; optionally the visibility is divided by that weight;
+ *   - tabulated fractional delays (Sec. 2.4.1, 4.3): one value per path per table step
+ *     (5 ms = 6,400 samples in MWAX), held constant over the step; frame m uses the step
+ *     containing its centre sample (m + 1/2) N;
+ *   - passband de-ripple (Sec. 4.2): a real magnitude gain per ultrafine channel
+ *     multiplies every spectral value together with the delay phasor;
+ *   - oversampled coarse channels (Sec. 4.5): the coarse channel is sampled at a rate
+ *     above its spacing; only the keep_bins ultrafine channels around DC are passed to
+ *     the X step and averaged (M = keep_bins / F), the rest are discarded.
+ * ========================================================================== */
+
+typedef struct {
+    double sample_rate_hz;       /* coarse-channel sample rate Fs; 0 = 1.28 MS/s       */
+    int keep_bins;               /* ultrafine channels kept around DC; 0 = all N       */
+    const double* delay_table;   /* [n_paths][table_steps] seconds, or NULL            */
+    long long table_step;        /* samples per table step                             */
+    long long table_steps;       /* entries per path                                   */
+    const double* passband;      /* [N] gain per ultrafine channel c, or NULL          */
+    const uint8_t* zero_flags;   /* [n_blocks][n_paths], nonzero = zeroed, or NULL     */
+    int normalise;               /* divide visibilities by their occupancy weight      */
+} ora_ext;
+
+static double ext_fs(const ora_ext* e) { return (e && e->sample_rate_hz > 0.0) ? e->sample_rate_hz : ORA_FS; }
+
+static int ext_keep(const ora_desc* d, const ora_ext* e) { return (e && e->keep_bins > 0) ? e->keep_bins : d->fft_len; }
+
+static int ext_flagged(const ora_desc* d, const ora_ext* e, int p, long long s)
+{
+    if (!e || !e->zero_flags) return 0;
+    long long blk = s / d->block_samples;
+    return e->zero_flags[blk * (2LL * d->n_tiles) + p] != 0;
+}
+
+/*
+ * Averaging weights of output channel j when only the keep ultrafine channels around DC
+ * are used: M = keep / F output channels centred as in Sec. 2.6, bins outside
+ * [-keep/2, keep - keep/2 - 1] dropped.  keep = N gives ora_avg_weights.
+ */
+double ora_avg_weights_keep(int N, int keep, int F, int dc_exclude, int j, double* w)
+{
+    int M = keep / F;
+    int j0 = M / 2;
+    long long centre = (long long)(j - j0) * F;
+    int half = F / 2;
+    double sum = 0.0;
+    for (int c = 0; c < N; ++c) w[c] = 0.0;
+    for (long long u = centre - half; u <= centre + half; ++u) {
+        double wt = 1.0;
+        if (F % 2 == 0 && (u == centre - half || u == centre + half)) wt = 0.5;
+        if (dc_exclude && F > 1 && u == 0) wt = 0.0;
+        if (u < -(keep / 2) || u > keep - keep / 2 - 1) continue;
+        w[u + N / 2] = wt;
+        sum += wt;
+    }
+    return sum;
+}
+
+/* Fractional delay of path p for the frame starting at sample s0 (N samples), seconds. */
+static double ext_tau(const ora_desc* d, const ora_ext* e, const double* delay, int p, long long s0)
+{
+    int N = d->fft_len;
+    if (e && e->delay_table) {
+        long long step = (2 * s0 + N) / (2 * e->table_step);   /* step holding sample s0 + N/2 */
+        if (step >= e->table_steps) step = e->table_steps - 1;
+        return e->delay_table[(long long)p * e->table_steps + step];
+    }
+    double t = ((double)(s0 / N) + 0.5) * (double)N / ext_fs(e);   /* frame centre */
+    return delay[3 * p] + delay[3 * p + 1] * t + delay[3 * p + 2] * t * t;
+}
+
+/* ora_spectra with the extensions: sample rate, flags, delay table, passband gains. */
+void ora_spectra_ext(const ora_desc* d, const ora_ext* e, const int8_t* volt, const double* delay, int p,
+                     long long m0, long long nm, double complex* Y)
+{
+    int N = d->fft_len;
+    double fs = ext_fs(e);
+    int have_delay = delay != NULL || (e && e->delay_table);
+    double complex* x = malloc(sizeof(double complex) * (size_t)N);
+    double complex* X = malloc(sizeof(double complex) * (size_t)N);
+    for (long long m = m0; m < m0 + nm; ++m) {
+        long long s0 = m * N;
+        int zero = ext_flagged(d, e, p, s0); /* frames never straddle a block (N | block) */
+        for (int n = 0; n < N; ++n) x[n] = zero ? 0.0 : volt_at(d, volt, p, s0 + n);
+        ora_fft(N, x, X);
+        double complex* out = Y + (m - m0) * N;
+        for (int k = 0; k < N; ++k) out[channel_of_bin(N, k)] = X[k];
+        double tau = have_delay ? ext_tau(d, e, delay, p, s0) : 0.0;
+        for (int c = 0; c < N; ++c) {
+            if (have_delay) {
+                double f = (double)ora_offset_of_channel(N, c) * fs / (double)N;
+                double cyc = (d->sky_freq_hz + f) * tau;
+                out[c] *= cexp(2.0 * ORA_PI * I * cyc);
+            }
+            if (e && e->passband) out[c] *= e->passband[c];
+        }
+    }
+    free(x);
+    free(X);
+}
+
+/* Occupancy weight of paths (p, q) over integration w: fraction of its K frames whose
+ * block is unflagged in both paths (Sec. 4.1).  1.0 without flags. */
+double ora_occupancy(const ora_desc* d, const ora_ext* e, long long w, int p, int q)
+{
+    long long K = d->int_frames, good = 0;
+    int N = d->fft_len;
+    for (long long m = w * K; m < (w + 1) * K; ++m)
+        if (!ext_flagged(d, e, p, m * N) && !ext_flagged(d, e, q, m * N)) ++good;
+    return (double)good / (double)K;
+}
+
+int ora_check_ext(const ora_desc* d, const ora_ext* e)
+{
+    if (ora_check(d)) return -1;
+    if (!e) return 0;
+    int keep = ext_keep(d, e);
+    if (keep < 1 || keep > d->fft_len || keep % d->fine_avg) return -1;
+    if (e->delay_table && (e->table_step < 1 || e->table_steps < 1)) return -1;
+    return 0;
+}
+
+/*
+ * Full correlation with the extensions.  vis: [ints][B][M][4] with M = keep / F;
+ * weights: [ints][B][4] occupancy (1.0 without flags); with normalise, each visibility
+ * is divided by its weight (left at 0 where the weight is 0).
+ */
+int ora_correlate_ext(const ora_desc* d, const ora_ext* e, const int8_t* volt, const double* delay,
+                      double complex* vis, double* weights)
+{
+    if (ora_check_ext(d, e)) return -1;
+    int T = d->n_tiles, n = 2 * T, N = d->fft_len, F = d->fine_avg, keep = ext_keep(d, e), M = keep / F;
+    long long K = d->int_frames, n_ints = d->n_samples / (K * N), B = ora_n_baselines(T);
+    double complex* Y = malloc(sizeof(double complex) * (size_t)n * (size_t)K * (size_t)N);
+    double* wts = malloc(sizeof(double) * (size_t)M * (size_t)N);
+    double* wsum = malloc(sizeof(double) * (size_t)M);
+    if (!Y || !wts || !wsum) {
+        free(Y);
+        free(wts);
+        free(wsum);
+        return -2;
+    }
+    for (int j = 0; j < M; ++j) wsum[j] = ora_avg_weights_keep(N, keep, F, d->dc_exclude, j, wts + (size_t)j * N);
+    for (long long w = 0; w < n_ints; ++w) {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int p = 0; p < n; ++p) ora_spectra_ext(d, e, volt, delay, p, w * K, K, Y + (size_t)p * K * N);
+#pragma omp parallel for schedule(dynamic, 1)
+        for (long long bp = 0; bp < B * 4; ++bp) {
+            long long b = bp / 4;
+            int pol = (int)(bp % 4), p, q;
+            baseline_paths(T, b, pol, &p, &q);
+            double occ = ora_occupancy(d, e, w, p, q);
+            for (int j = 0; j < M; ++j) {
+                double complex acc = 0;
+                for (int c = 0; c < N; ++c) {
+                    double wt = wts[(size_t)j * N + c];
+                    if (wt == 0.0) continue;
+                    double complex cpq = 0;
+                    for (long long m = 0; m < K; ++m)
+                        cpq += Y[((size_t)p * K + m) * N + c] * conj(Y[((size_t)q * K + m) * N + c]);
+                    acc += wt * cpq;
+                }
+                double complex v = acc / wsum[j];
+                if (e && e->normalise) v = occ > 0.0 ? v / occ : 0.0;
+                vis[((w * B + b) * M + j) * 4 + pol] = v;
+            }
+            weights[(w * B + b) * 4 + pol] = occ;
+        }
+    }
+    free(Y);
+    free(wts);
+    free(wsum);
+    return 0;
+}
+
+/* Integer mode with zeroing flags: flagged samples count as zero, weights = occupancy
+ * (no normalisation: the sums stay exact integers). */
+int ora_correlate_int_ext(const ora_desc* d, const ora_ext* e, const int8_t* volt, long long* vis, double* weights)
+{
+    if (ora_check_ext(d, e) || d->fft_len != 1 || d->fine_avg != 1 || (e && e->normalise)) return -1;
+    int T = d->n_tiles;
+    long long K = d->int_frames, n_ints = d->n_samples / K, B = ora_n_baselines(T);
+#pragma omp parallel for schedule(dynamic, 1) collapse(2)
+    for (long long w = 0; w < n_ints; ++w)
+        for (long long bp = 0; bp < B * 4; ++bp) {
+            long long b = bp / 4;
+            int pol = (int)(bp % 4), p, q;
+            baseline_paths(T, b, pol, &p, &q);
+            long long re = 0, im = 0;
+            int n_paths = 2 * T, bs = d->block_samples;
+            for (long long s = w * K; s < (w + 1) * K; ++s) {
+                if (ext_flagged(d, e, p, s) || ext_flagged(d, e, q, s)) continue;
+                long long blk = s / bs, i = s % bs;
+                const int8_t* a = volt + ((blk * n_paths + p) * (long long)bs + i) * 2;
+                const int8_t* c = volt + ((blk * n_paths + q) * (long long)bs + i) * 2;
+                re += (long long)a[0] * c[0] + (long long)a[1] * c[1];
+                im += (long long)a[1] * c[0] - (long long)a[0] * c[1];
+            }
+            vis[((w * B + b) * 4 + pol) * 2] = re;
+            vis[((w * B + b) * 4 + pol) * 2 + 1] = im;
+            weights[(w * B + b) * 4 + pol] = ora_occupancy(d, e, w, p, q);
+        }
+    return 0;
+}

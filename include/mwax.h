@@ -74,13 +74,18 @@ typedef struct {
     int keep_dc;                 /* 0 (default) = exclude DC from the centre channel when
                                     F > 1 (Sec. 2.6); 1 = keep it                          */
     size_t workspace_limit;      /* bytes of device workspace; 0 = 16 GiB                 */
+    double sample_rate_hz;       /* coarse-channel sample rate Fs; 0 = 1.28 MS/s.  Above
+                                    the channel spacing for oversampled channels (Sec. 4.5) */
+    int keep_bins;               /* ultrafine channels passed to the X step, centred on DC;
+                                    0 = all N.  Oversampled channels discard the rest
+                                    (Sec. 4.5); M = keep_bins / F                           */
 } mwax_plan_desc;
 
 /* Derived sizes of a plan (all counts per call). */
 typedef struct {
     int n_paths;                 /* n = 2 T                                   */
     long long n_baselines;       /* B = T (T + 1) / 2                         */
-    int n_chan_out;              /* M = N / F                                 */
+    int n_chan_out;              /* M = keep_bins / F (N / F by default)      */
     long long frames_per_int;    /* K = int_time Fs / N                       */
     long long n_ints;            /* integrations per call                     */
     size_t input_bytes;          /* n_blocks * n * block_samples * 2          */
@@ -142,6 +147,48 @@ mwax_status mwax_correlate(mwax_plan* plan, const int8_t* voltages, const double
  * Synchronous: returns when vis_out holds the result.
  */
 mwax_status mwax_correlate_host(mwax_plan* plan, const int8_t* voltages, const double* delay_poly, void* vis_out);
+
+/*
+ * Extended call (Sec. 2.4, 4.1, 4.3): tabulated fractional delays and zeroing flags.
+ *   voltages, vis_out   as for mwax_correlate (device, 16-byte aligned);
+ *   delay_poly          as for mwax_correlate, or NULL;
+ *   delay_table         NULL or float64 [n][table_steps] fractional delays in seconds, host
+ *                       or device memory: entry s holds for samples
+ *                       [s table_step_samples, (s + 1) table_step_samples) of the call, and a
+ *                       frame takes the entry holding its centre (entries past the end repeat
+ *                       the last).  Exclusive with delay_poly; not for MWAX_INT8;
+ *   table_steps         entries per path (>= 1 with a table);
+ *   table_step_samples  samples per entry; 0 = 6,400 (5 ms at 1.28 MS/s, the paper's cadence);
+ *   zero_flags          NULL or uint8 [n_blocks][n], host or device memory: nonzero marks a
+ *                       data block of a path that was zeroed (lost or excised).  Its samples
+ *                       are excluded (read as zero) and each integration's weights table
+ *                       receives the occupancy of every baseline/pol: the fraction of the
+ *                       integration's frames whose blocks are unflagged in both paths;
+ *   normalise           nonzero: divide each visibility by its occupancy weight (zero weight
+ *                       leaves zeros).  Float precisions only (MWAX_EINVAL for MWAX_INT8).
+ * Host-memory tables and flags are copied before the call returns.  The plan keeps one
+ * device copy of each (grown on demand: the first call with a larger table allocates).
+ */
+typedef struct {
+    const int8_t* voltages;
+    const double* delay_poly;
+    const double* delay_table;
+    long long table_steps;
+    long long table_step_samples;
+    const uint8_t* zero_flags;
+    int normalise;
+    void* vis_out;
+} mwax_call;
+mwax_status mwax_correlate_ex(mwax_plan* plan, const mwax_call* call);
+
+/*
+ * Passband de-ripple (Sec. 4.2): a real magnitude gain per ultrafine channel, multiplied
+ * into every spectral value with the delay phasor (visibilities scale by its square).
+ * gain: host float32 [fft_len] in channel order c = u + N/2 (u = ultrafine offset from DC),
+ * each finite and > 0; NULL restores a flat passband.  Applies to calls enqueued after it
+ * returns.  MWAX_EUNSUPPORTED for MWAX_INT8 (exact integer sums).
+ */
+mwax_status mwax_plan_set_passband(mwax_plan* plan, const float* gain);
 
 /* Wait for the plan's stream; returns MWAX_ETIMEOUT / MWAX_ECUDA if a kernel reported
  * an error since the last sync, and clears the device status word. */

@@ -39,7 +39,14 @@ class _CDesc(ctypes.Structure):
     _fields_ = [("n_tiles", ctypes.c_int), ("fft_len", ctypes.c_int), ("fine_avg", ctypes.c_int),
                 ("int_time_s", ctypes.c_double), ("samples_per_call", ctypes.c_longlong),
                 ("block_samples", ctypes.c_int), ("precision", ctypes.c_int), ("sky_freq_hz", ctypes.c_double),
-                ("keep_dc", ctypes.c_int), ("workspace_limit", ctypes.c_size_t)]
+                ("keep_dc", ctypes.c_int), ("workspace_limit", ctypes.c_size_t),
+                ("sample_rate_hz", ctypes.c_double), ("keep_bins", ctypes.c_int)]
+
+
+class _Call(ctypes.Structure):
+    _fields_ = [("voltages", ctypes.c_void_p), ("delay_poly", ctypes.c_void_p), ("delay_table", ctypes.c_void_p),
+                ("table_steps", ctypes.c_longlong), ("table_step_samples", ctypes.c_longlong),
+                ("zero_flags", ctypes.c_void_p), ("normalise", ctypes.c_int), ("vis_out", ctypes.c_void_p)]
 
 
 class _CInfo(ctypes.Structure):
@@ -85,10 +92,13 @@ class PlanDesc:
     sky_freq_hz: float = 0.0
     keep_dc: int = 0
     workspace_limit: int = 0
+    sample_rate_hz: float = 0.0
+    keep_bins: int = 0
 
     def c(self) -> _CDesc:
         return _CDesc(self.n_tiles, self.fft_len, self.fine_avg, self.int_time_s, self.samples_per_call,
-                      self.block_samples, int(self.precision), self.sky_freq_hz, self.keep_dc, self.workspace_limit)
+                      self.block_samples, int(self.precision), self.sky_freq_hz, self.keep_dc, self.workspace_limit,
+                      self.sample_rate_hz, self.keep_bins)
 
 
 _lib = None
@@ -99,7 +109,7 @@ SYMBOLS = ("mwax_plan_create", "mwax_plan_create_ex", "mwax_plan_get_info", "mwa
            "mwax_batch_create", "mwax_batch_set_stream", "mwax_batch_set_graphs", "mwax_batch_correlate",
            "mwax_batch_sync", "mwax_batch_destroy", "mwax_server_create", "mwax_server_submit", "mwax_server_poll",
            "mwax_server_wait", "mwax_server_drain", "mwax_server_get_stats", "mwax_server_destroy",
-           "mwax_correlate_noalloc")
+           "mwax_correlate_noalloc", "mwax_correlate_ex", "mwax_plan_set_passband")
 
 
 def load_library(path: str | None = None):
@@ -178,6 +188,10 @@ def load_library(path: str | None = None):
     lib.mwax_server_destroy.restype = None
     lib.mwax_correlate_noalloc.argtypes = [ctypes.POINTER(_CDesc), vp, vp, vp, vp]
     lib.mwax_correlate_noalloc.restype = st
+    lib.mwax_correlate_ex.argtypes = [vp, ctypes.POINTER(_Call)]
+    lib.mwax_correlate_ex.restype = st
+    lib.mwax_plan_set_passband.argtypes = [vp, vp]
+    lib.mwax_plan_set_passband.restype = st
     lib.mwax_version.argtypes = []
     lib.mwax_version.restype = ctypes.c_char_p
     _lib = lib
@@ -423,6 +437,51 @@ def mwax_correlate_noalloc(desc: PlanDesc, voltages, delay_poly, vis_out, stream
         np.ascontiguousarray(delay_poly, dtype=np.float64)
     _check(load_library().mwax_correlate_noalloc(ctypes.byref(cd), _ptr(voltages), _ptr(keep), _ptr(vis_out),
                                                  ctypes.c_void_p(s.cuda_stream)))
+
+
+def _array_arg(x, dtype):
+    """(pointer, keepalive) of a numpy array (host) or torch tensor (host or device)."""
+    if x is None:
+        return None, None
+    if isinstance(x, np.ndarray):
+        a = np.ascontiguousarray(x, dtype=dtype)
+        return a.ctypes.data, a
+    if not x.is_contiguous():
+        raise ValueError("tables and flags must be contiguous")
+    return x.data_ptr(), x
+
+
+def mwax_correlate_ex(plan: Plan, voltages, vis_out, delay_poly=None, delay_table=None, table_step_samples=0,
+                      zero_flags=None, normalise=False):
+    """Extended call: tabulated delays [n_paths, steps] (float64 s), zeroing flags
+    [n_blocks, n_paths] (uint8) with occupancy weights, optional normalisation."""
+    if not voltages.is_cuda or not vis_out.is_cuda:
+        raise ValueError("mwax_correlate_ex takes device voltages and output")
+    if voltages.numel() * voltages.element_size() != plan.input_bytes or not voltages.is_contiguous():
+        raise ValueError(f"voltages must be a contiguous buffer of {plan.input_bytes} bytes")
+    if vis_out.numel() * vis_out.element_size() < plan.output_bytes:
+        raise ValueError(f"vis_out must hold {plan.output_bytes} bytes")
+    dptr, keep_d = _delay_arg(delay_poly, plan, True)
+    n = 2 * plan.desc.n_tiles
+    tptr, keep_t = _array_arg(delay_table, np.float64)
+    steps = 0
+    if delay_table is not None:
+        steps = (delay_table.size if isinstance(delay_table, np.ndarray) else delay_table.numel()) // n
+        if steps * n != (delay_table.size if isinstance(delay_table, np.ndarray) else delay_table.numel()):
+            raise ValueError("delay_table must hold n_paths x steps float64")
+    fptr, keep_f = _array_arg(zero_flags, np.uint8)
+    call = _Call(_ptr(voltages), dptr, tptr, steps, int(table_step_samples), fptr, int(bool(normalise)),
+                 _ptr(vis_out))
+    _check(load_library().mwax_correlate_ex(plan.handle, ctypes.byref(call)))
+    return keep_d, keep_t, keep_f
+
+
+def mwax_plan_set_passband(plan: Plan, gain=None):
+    """De-ripple gains per ultrafine channel (float32 [fft_len], channel order), None = flat."""
+    g = None if gain is None else np.ascontiguousarray(gain, dtype=np.float32)
+    if g is not None and g.size != plan.desc.fft_len:
+        raise ValueError("passband gain must hold fft_len values")
+    _check(load_library().mwax_plan_set_passband(plan.handle, _ptr(g)))
 
 
 def mwax_plan_destroy(plan: Plan):

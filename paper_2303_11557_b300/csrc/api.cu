@@ -38,21 +38,22 @@ mwax_status fail(mwax_status st, const char* fmt, ...)
                         cudaGetErrorString(e_), __FILE__, __LINE__);                                     \
     } while (0)
 
-// Output channel j of M = N/F: centred on ultrafine offset (j - floor(M/2)) F; odd F
+// Output channel j of M = keep/F: centred on ultrafine offset (j - floor(M/2)) F; odd F
 // takes F bins of weight 1, even F takes F+1 bins with the two ends at 1/2; the DC bin
-// is dropped from the centre channel when F > 1 (unless kept); bins beyond the coarse
-// channel do not exist (Sec. 2.6).  Produces gain[c] = sqrt(w_c) and the groups of
+// is dropped from the centre channel when F > 1 (unless kept); bins beyond the kept band
+// (the coarse channel, or its central keep bins when oversampled, Sec. 4.5) do not exist
+// (Sec. 2.6).  Produces gain[c] = sqrt(w_c) and the groups of
 // consecutive channels that feed the same output channels, with coef = 1 / sum(w).
-bool build_groups(int N, int F, int dc_excl, std::vector<float>& gain, std::vector<Group>& groups)
+bool build_groups(int N, int keep, int F, int dc_excl, std::vector<float>& gain, std::vector<Group>& groups)
 {
-    const int M = N / F, jc = M / 2, half = F / 2;
+    const int M = keep / F, jc = M / 2, half = F / 2;
     std::vector<double> w(N, 0.0), wsum(M, 0.0);
     std::vector<std::vector<int>> feeds(N);
     for (int j = 0; j < M; ++j) {
         const long long mid = (long long)(j - jc) * F;
         for (long long u = mid - half; u <= mid + half; ++u) {
             const long long c = u + N / 2;
-            if (c < 0 || c >= N) continue;
+            if (u < -(keep / 2) || u > keep - keep / 2 - 1) continue;   // outside the kept band
             double wt = (F % 2 == 0 && (u == mid - half || u == mid + half)) ? 0.5 : 1.0;
             if (dc_excl && F > 1 && u == 0) wt = 0.0;
             if (wt == 0.0) continue;
@@ -127,6 +128,8 @@ void free_plan(mwax_plan* p)
     cudaFree(p->counter);
     cudaFree(p->dvolt);
     cudaFree(p->dout);
+    cudaFree(p->d_table);
+    cudaFree(p->d_flags);
     for (auto& it : p->item_lists) cudaFree(it.items);
     for (auto e : p->events) cudaEventDestroy(e);
     for (auto e : p->ev_pool) cudaEventDestroy(e);
@@ -148,7 +151,14 @@ mwax_status validate(const mwax_plan_desc& d, mwax_plan& p)
     if (bs < 1 || bs % d.fft_len)
         return fail(MWAX_EINVAL, "block_samples (%d) must be a multiple of fft_len (%d)", bs, d.fft_len);
     if (!(d.int_time_s > 0.0)) return fail(MWAX_EINVAL, "int_time_s must be > 0");
-    const double int_samples_d = d.int_time_s * kFs;
+    if (d.sample_rate_hz < 0.0 || !(d.sample_rate_hz < 1e12))
+        return fail(MWAX_EINVAL, "sample_rate_hz must be >= 0 (0 = 1.28 MS/s)");
+    const double fs = d.sample_rate_hz > 0.0 ? d.sample_rate_hz : kFs;
+    const int keep = d.keep_bins ? d.keep_bins : d.fft_len;
+    if (keep < 1 || keep > d.fft_len || keep % d.fine_avg)
+        return fail(MWAX_EINVAL, "keep_bins (%d) must be in [1, fft_len] and a multiple of fine_avg (%d)", keep,
+                    d.fine_avg);
+    const double int_samples_d = d.int_time_s * fs;
     const long long int_samples = llround(int_samples_d);
     if (fabs(int_samples_d - (double)int_samples) > 1e-9 * std::max(1.0, int_samples_d) || int_samples < 1)
         return fail(MWAX_EINVAL, "int_time_s * Fs must be a whole number of samples");
@@ -172,7 +182,9 @@ mwax_status validate(const mwax_plan_desc& d, mwax_plan& p)
     p.n = 2 * d.n_tiles;
     p.N = d.fft_len;
     p.F = d.fine_avg;
-    p.M = d.fft_len / d.fine_avg;
+    p.keep = keep;
+    p.fs = fs;
+    p.M = keep / d.fine_avg;
     p.bs = bs;
     p.prec = d.precision;
     p.dc_excl = d.keep_dc ? 0 : 1;
@@ -268,6 +280,34 @@ mwax_status configure_x(mwax_plan& p, int run_len_req, int window)
 
 namespace {
 
+// FP16 / FP8 operands: power-of-two pre-scale keeping |Re X|, |Im X| <= 181 N g (int8
+// magnitude 128 sqrt 2 summed over N samples, times a passband gain g <= 2) below 2^15;
+// undone exactly after the MMA.  Fixed at plan creation, so de-ripple gains can change
+// without touching launch arguments captured in graphs.
+constexpr double kMaxPassband = 2.0;
+
+void set_prescale(mwax_plan& p)
+{
+    if (p.prec != MWAX_FP16 && p.prec != MWAX_FP8) return;
+    int k = 0;
+    while (181.02 * p.N * kMaxPassband / (double)(1 << k) > 32768.0) ++k;
+    p.out_scale = ldexpf(1.0f, -k);
+    p.post_scale = ldexpf(1.0f, 2 * k);
+}
+
+// Copy into plan-owned device memory in stream order; a pinned host source is waited for
+// so that the caller may reuse it when the call returns (pageable sources are staged by
+// the copy itself, device sources are read in stream order).
+mwax_status copy_in(mwax_plan* p, void* dst, const void* src, size_t bytes)
+{
+    MWAX_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, p->stream));
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, src) == cudaSuccess && at.type == cudaMemoryTypeHost)
+        MWAX_CUDA(cudaStreamSynchronize(p->stream));
+    cudaGetLastError();   // an unregistered pointer is not an error here
+    return MWAX_OK;
+}
+
 mwax_status setup(mwax_plan& p)
 {
     MWAX_CUDA(cudaGetDevice(&p.device));
@@ -315,7 +355,7 @@ mwax_status setup(mwax_plan& p)
     // averaging: per-channel gains (applied in the F-step) and channel groups
     std::vector<float> gain;
     std::vector<Group> groups;
-    if (!build_groups(p.N, p.F, p.dc_excl, gain, groups))
+    if (!build_groups(p.N, p.keep, p.F, p.dc_excl, gain, groups))
         return fail(MWAX_EINVAL, "channel averaging with fscrunch %d leaves an empty channel", p.F);
     p.n_groups = (int)groups.size();
     MWAX_CUDA(cudaMalloc(&p.gain, sizeof(float) * p.N));
@@ -324,15 +364,12 @@ mwax_status setup(mwax_plan& p)
     MWAX_CUDA(cudaMemcpy(p.groups, groups.data(), sizeof(Group) * groups.size(), cudaMemcpyHostToDevice));
     p.h_groups = groups;
     p.h_gain = gain;
+    p.h_avg_gain = gain;
+    p.passband.assign(p.N, 1.0f);
 
     // FP16 operands: power-of-two pre-scale keeping |Re X|, |Im X| <= 181 N (int8
     // magnitude 128 sqrt 2 summed over N samples) below 2^15; undone exactly after the MMA
-    if (p.prec == MWAX_FP16 || p.prec == MWAX_FP8) {
-        int k = 0;
-        while (181.02 * p.N / (double)(1 << k) > 32768.0) ++k;
-        p.out_scale = ldexpf(1.0f, -k);
-        p.post_scale = ldexpf(1.0f, 2 * k);
-    }
+    set_prescale(p);
     p.tensor_cores = p.prec != MWAX_FP32;
     if (p.prec == MWAX_FP8) {
         std::vector<int> cg(p.N, -1);
@@ -546,6 +583,11 @@ mwax_status enqueue_fstep(mwax_plan* p, const LaunchGroup& g, const int8_t* volt
     fa.bs = p->bs;
     fa.nu = p->nu;
     fa.out_scale = p->out_scale;
+    fa.fs = p->fs;
+    fa.delay_tab = p->cur_table;
+    fa.tab_steps = p->cur_steps;
+    fa.tab_step = p->cur_step;
+    fa.flags = p->cur_flags;
     fa.chan_group = p->chan_group;
     fa.n_groups = p->n_groups;
     fa.amax = p->amax;
@@ -696,6 +738,77 @@ mwax_status mwax_correlate(mwax_plan* p, const int8_t* volt, const double* delay
     mwax_status st = load_delay(p, delay_poly);
     if (st != MWAX_OK) return st;
     return enqueue(p, volt, delay_poly != nullptr, static_cast<char*>(vis_out), nullptr, 1);
+}
+
+mwax_status mwax_correlate_ex(mwax_plan* p, const mwax_call* c)
+{
+    if (!p || !c) return fail(MWAX_EINVAL, "NULL plan or call");
+    if (!c->voltages || !c->vis_out) return fail(MWAX_EINVAL, "NULL voltages or vis_out");
+    if (((uintptr_t)c->voltages & 15) || ((uintptr_t)c->vis_out & 15))
+        return fail(MWAX_EINVAL, "voltages and vis_out must be 16-byte aligned");
+    if (c->delay_poly && c->delay_table) return fail(MWAX_EINVAL, "delay_poly and delay_table are exclusive");
+    if (p->prec == MWAX_INT8 && (c->delay_poly || c->delay_table))
+        return fail(MWAX_EINVAL, "MWAX_INT8 takes no delay correction");
+    if (p->prec == MWAX_INT8 && c->normalise)
+        return fail(MWAX_EINVAL, "normalise needs a float precision (MWAX_INT8 sums stay exact integers)");
+    const long long step = c->table_step_samples ? c->table_step_samples : 6400;
+    if (c->delay_table && (c->table_steps < 1 || step < 1))
+        return fail(MWAX_EINVAL, "delay_table needs table_steps >= 1 and table_step_samples >= 0");
+    MWAX_CUDA(cudaSetDevice(p->device));
+    mwax_status st = load_delay(p, c->delay_poly);
+    if (st != MWAX_OK) return st;
+    if (c->delay_table) {
+        const size_t bytes = sizeof(double) * (size_t)p->n * (size_t)c->table_steps;
+        if (bytes > p->table_cap) {
+            cudaFree(p->d_table);   // synchronises with work still reading the old table
+            p->d_table = nullptr;
+            p->table_cap = 0;
+            MWAX_CUDA(cudaMalloc(&p->d_table, bytes));
+            p->table_cap = bytes;
+        }
+        if ((st = copy_in(p, p->d_table, c->delay_table, bytes)) != MWAX_OK) return st;
+    }
+    if (c->zero_flags) {
+        const size_t bytes = (size_t)p->n_blocks * p->n;
+        if (!p->d_flags) MWAX_CUDA(cudaMalloc(&p->d_flags, bytes));
+        if ((st = copy_in(p, p->d_flags, c->zero_flags, bytes)) != MWAX_OK) return st;
+    }
+    p->cur_table = c->delay_table ? p->d_table : nullptr;
+    p->cur_steps = c->table_steps;
+    p->cur_step = step;
+    p->cur_flags = c->zero_flags ? p->d_flags : nullptr;
+    char* out = static_cast<char*>(c->vis_out);
+    st = enqueue(p, c->voltages, c->delay_poly != nullptr, out, nullptr, 1);
+    if (st == MWAX_OK && c->zero_flags) {
+        cudaError_t e = timed(p, 0, p->stream, [&] {
+            return launch_weights(out, p->n_ints, (long long)p->int_stride, (long long)p->vis_set_bytes, p->T, p->M,
+                                  p->K, p->N, p->bs, p->n, p->d_flags, c->normalise ? 1 : 0, p->stream);
+        });
+        if (e != cudaSuccess) st = cuda_error(e, "weights launch");
+    }
+    p->cur_table = nullptr;
+    p->cur_flags = nullptr;
+    return st;
+}
+
+mwax_status mwax_plan_set_passband(mwax_plan* p, const float* gain)
+{
+    if (!p) return fail(MWAX_EINVAL, "plan is NULL");
+    if (p->prec == MWAX_INT8) return fail(MWAX_EUNSUPPORTED, "MWAX_INT8 sums stay exact integers: no passband gains");
+    std::vector<float> g(p->N, 1.0f);
+    if (gain) {
+        for (int c = 0; c < p->N; ++c) {
+            if (!(gain[c] > 0.0f) || !(gain[c] <= (float)kMaxPassband))
+                return fail(MWAX_EINVAL, "passband gain[%d] = %g must be in (0, %g]", c, (double)gain[c], kMaxPassband);
+            g[c] = gain[c];
+        }
+    }
+    MWAX_CUDA(cudaSetDevice(p->device));
+    MWAX_CUDA(cudaStreamSynchronize(p->stream));   // earlier calls may still read the table
+    p->passband = g;
+    for (int c = 0; c < p->N; ++c) p->h_gain[c] = p->h_avg_gain[c] * g[c];
+    MWAX_CUDA(cudaMemcpy(p->gain, p->h_gain.data(), sizeof(float) * p->N, cudaMemcpyHostToDevice));
+    return MWAX_OK;
 }
 
 mwax_status mwax_correlate_host(mwax_plan* p, const int8_t* volt, const double* delay_poly, void* vis_out)

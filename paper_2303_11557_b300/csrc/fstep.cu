@@ -404,13 +404,11 @@ __global__ void __launch_bounds__(kThreads) fstep_kernel(const FArgs a)
         fi.k = (fl < a.n_store) ? fl % a.Kc : 0;
         fi.delay = 0;
         fi.phi0 = fi.d_hi = fi.d_lo = 0.0f;
-        if (a.delay != nullptr && fl < a.n_frames) {
-            const double m = (double)(a.m_begin + fl);
-            const double t = (m + 0.5) * (double)N / kFs;
-            const double tau = a.delay[3 * p] + t * (a.delay[3 * p + 1] + t * a.delay[3 * p + 2]);
+        if ((a.delay != nullptr || a.delay_tab != nullptr) && fl < a.n_frames) {
+            const double tau = frame_delay(a, p, (a.m_begin + fl) * (long long)N, N);
             const double ph = a.nu * tau;
             fi.phi0 = (float)(ph - floor(ph));
-            const double d = tau * kFs / (double)N;
+            const double d = tau * a.fs / (double)N;
             const float dh = __uint_as_float(__float_as_uint((float)d) & 0xFFFFF000u);
             fi.d_hi = dh;
             fi.d_lo = (float)(d - (double)dh);
@@ -432,7 +430,7 @@ __global__ void __launch_bounds__(kThreads) fstep_kernel(const FArgs a)
         const int f = i / CH, ch = i % CH;
         const long long fl = f0 + f;
         int4 w = make_int4(0, 0, 0, 0);
-        if (fl < a.n_frames) {
+        if (fl < a.n_frames && !frame_zeroed(a, p, (a.m_begin + fl) * (long long)N)) {
             const long long s = (a.m_begin + fl) * (long long)N;   // absolute first sample
             const long long blk = s / a.bs, off = s % a.bs;
             const int8_t* src = a.volt + ((blk * a.n + p) * (long long)a.bs + off) * 2;
@@ -523,13 +521,11 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
         fi.delay = 0;
         fi.phi0 = fi.d_hi = fi.d_lo = 0.0f;
         fi.step1 = fi.step32 = fi.wrap = make_float2(1.0f, 0.0f);
-        if (a.delay != nullptr && fl < a.n_frames) {
-            const double m = (double)(a.m_begin + fl);
-            const double t = (m + 0.5) * (double)N / kFs;
-            const double tau = a.delay[3 * p] + t * (a.delay[3 * p + 1] + t * a.delay[3 * p + 2]);
+        if ((a.delay != nullptr || a.delay_tab != nullptr) && fl < a.n_frames) {
+            const double tau = frame_delay(a, p, (a.m_begin + fl) * (long long)N, N);
             const double ph = a.nu * tau;
             fi.phi0 = (float)(ph - floor(ph));
-            const double d = tau * kFs / (double)N;
+            const double d = tau * a.fs / (double)N;
             const float dh = __uint_as_float(__float_as_uint((float)d) & 0xFFFFF000u);
             fi.d_hi = dh;
             fi.d_lo = (float)(d - (double)dh);
@@ -551,7 +547,7 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
         const int t = idx % T, f = idx / T;
         const long long fl = f0 + f;
         float2 v[32];
-        if (fl < a.n_frames) {
+        if (fl < a.n_frames && !frame_zeroed(a, p, (a.m_begin + fl) * (long long)N)) {
             const long long s0 = (a.m_begin + fl) * (long long)N;   // first sample of the frame
             const long long blk = s0 / a.bs, off = s0 % a.bs;
             const char2* src = reinterpret_cast<const char2*>(a.volt + ((blk * a.n + p) * (long long)a.bs + off) * 2);
@@ -649,14 +645,13 @@ __global__ void __launch_bounds__(256) unpack_kernel(const FArgs a)
         if (fl >= a.n_store) break;
         const long long s = a.m_begin + fl;
         float2 v = make_float2(0.0f, 0.0f);
-        if (fl < a.n_frames) {
+        if (fl < a.n_frames && !frame_zeroed(a, p, s)) {
             const long long blk = s / a.bs, off = s % a.bs;
             const char2 x = *reinterpret_cast<const char2*>(a.volt + ((blk * a.n + p) * (long long)a.bs + off) * 2);
             v = make_float2((float)x.x, (float)x.y);
         }
-        if (a.delay != nullptr && fl < a.n_frames) {
-            const double t = ((double)s + 0.5) / kFs;
-            const double tau = a.delay[3 * p] + t * (a.delay[3 * p + 1] + t * a.delay[3 * p + 2]);
+        if ((a.delay != nullptr || a.delay_tab != nullptr) && fl < a.n_frames) {
+            const double tau = frame_delay(a, p, s, 1);
             const double ph = a.nu * tau;
             float sn, cs;
             sincospif(2.0f * (float)(ph - floor(ph)), &sn, &cs);
@@ -782,6 +777,43 @@ __global__ void init_output_kernel(char* out, long long n_ints, long long vis_wo
     }
 }
 
+// Occupancy weight of (integration w, baseline b, pol): the fraction of the integration's K
+// frames whose data block is unflagged in both paths (Sec. 4.1).  One thread per
+// (w, tile i, tile j >= i, pol); frames never straddle a block (N divides the block).
+__global__ void weights_kernel(char* out, long long n_ints, long long int_stride, long long vis_set_bytes, int T,
+                               int M, long long K, int N, int bs, int n, const uint8_t* __restrict__ flags,
+                               int normalise)
+{
+    const long long total = n_ints * (long long)T * T * 4;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int pol = (int)(idx % 4);
+        const long long r = idx / 4;
+        const int j = (int)(r % T), i = (int)((r / T) % T);
+        const long long w = r / ((long long)T * T);
+        if (j < i) continue;
+        const int p = 2 * i + (pol >> 1), q = 2 * j + (pol & 1);
+        const long long s_begin = w * K * N, s_end = (w + 1) * K * N;
+        long long good = 0;
+        for (long long blk = s_begin / bs; blk * bs < s_end; ++blk) {
+            const long long lo = max(blk * bs, s_begin), hi = min((blk + 1) * bs, s_end);
+            if (!flags[blk * n + p] && !flags[blk * n + q]) good += (hi - lo) / N;
+        }
+        const float wt = (float)((double)good / (double)K);
+        const long long b = (long long)i * (2 * T - i + 1) / 2 + (j - i);
+        char* set = out + w * int_stride;
+        reinterpret_cast<float*>(set + vis_set_bytes)[b * 4 + pol] = wt;
+        if (normalise) {
+            const float inv = wt > 0.0f ? 1.0f / wt : 0.0f;
+            float2* v = reinterpret_cast<float2*>(set);
+            for (int ch = 0; ch < M; ++ch) {
+                float2 x = v[(b * M + ch) * 4 + pol];
+                v[(b * M + ch) * 4 + pol] = make_float2(x.x * inv, x.y * inv);
+            }
+        }
+    }
+}
+
 }  // namespace
 
 bool fft_len_supported(int N)
@@ -813,6 +845,14 @@ cudaError_t launch_quantise_e4m3(const __half* Y16, __nv_fp8_storage_t* Y8, cons
     if (rows > 0x7fffffffLL) return cudaErrorInvalidValue;
     quantise_e4m3_kernel<<<(unsigned)rows, Kpad >= 2048 ? 256 : 128, 0, s>>>(Y16, Y8, amax, chan_group, n_groups, N,
                                                                                n, Kpad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_weights(char* out, long long n_ints, long long int_stride, long long vis_set_bytes, int T, int M,
+                           long long K, int N, int bs, int n, const uint8_t* flags, int normalise, cudaStream_t s)
+{
+    weights_kernel<<<4 * 148, 256, 0, s>>>(out, n_ints, int_stride, vis_set_bytes, T, M, K, N, bs, n, flags,
+                                           normalise);
     return cudaGetLastError();
 }
 

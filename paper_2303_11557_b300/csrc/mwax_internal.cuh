@@ -60,7 +60,33 @@ struct FArgs {
     int bs;
     double nu;
     float out_scale;      // FP16: power-of-two pre-scale keeping |X| in range
+    double fs;            // coarse-channel sample rate (1.28 MS/s unless oversampled)
+    const double* delay_tab;   // [n][tab_steps] tabulated fractional delays (s), or nullptr
+    long long tab_steps;
+    long long tab_step;        // samples per table entry
+    const uint8_t* flags;      // [n_blocks][n] zeroing flags (nonzero: block holds no data), or nullptr
 };
+
+// Delay (s) of path p for the frame of N samples that starts at absolute sample s0: the
+// FP64 polynomial at the frame centre t = (s0 / N + 1/2) N / Fs (Sec. 4.3), or the table
+// entry of the step that holds the frame centre (Sec. 2.4.1).
+__device__ __forceinline__ double frame_delay(const FArgs& a, int p, long long s0, int N)
+{
+    if (a.delay_tab != nullptr) {
+        long long step = (2 * s0 + N) / (2 * a.tab_step);
+        if (step >= a.tab_steps) step = a.tab_steps - 1;
+        return a.delay_tab[(long long)p * a.tab_steps + step];
+    }
+    const double t = ((double)(s0 / N) + 0.5) * (double)N / a.fs;
+    return a.delay[3 * p] + t * (a.delay[3 * p + 1] + t * a.delay[3 * p + 2]);
+}
+
+// True when the data block holding sample s0 of path p is flagged as zeroed (Sec. 2.4.2):
+// its samples are excluded (read as zero) whatever the buffer holds.
+__device__ __forceinline__ bool frame_zeroed(const FArgs& a, int p, long long s0)
+{
+    return a.flags != nullptr && a.flags[(s0 / a.bs) * (long long)a.n + p] != 0;
+}
 
 // Arguments of one X-step launch over `slots` operand slots.
 struct XArgs {
@@ -117,6 +143,10 @@ cudaError_t launch_quantise_e4m3(const __half* Y16, __nv_fp8_storage_t* Y8, cons
                                  cudaStream_t s);
 cudaError_t launch_init_output(char* out, long long n_ints, long long vis_set_bytes, long long weights_bytes,
                                cudaStream_t s);
+// Occupancy weights from zeroing flags (Sec. 4.1) over each integration's weights table;
+// with normalise (float output only) the visibilities are divided by them.
+cudaError_t launch_weights(char* out, long long n_ints, long long int_stride, long long vis_set_bytes, int T, int M,
+                           long long K, int N, int bs, int n, const uint8_t* flags, int normalise, cudaStream_t s);
 cudaError_t launch_xstep_simt(const CUtensorMap& map, const XArgs& a, int n_tiles, int n_runs, int slots,
                               cudaStream_t s);
 // FP32 operand planes for the CUDA-core X-step: 32 frames x 64 rows x both planes per box,

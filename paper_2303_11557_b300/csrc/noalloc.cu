@@ -93,7 +93,11 @@ extern "C" mwax_status mwax_correlate_noalloc(const mwax_plan_desc* desc, const 
     if (F < 1 || N % F) return set_error(MWAX_EINVAL, "fine_avg must divide fft_len");
     if (bs % N) return set_error(MWAX_EINVAL, "block_samples must be a multiple of fft_len");
     if (!(d.int_time_s > 0.0)) return set_error(MWAX_EINVAL, "int_time_s must be > 0");
-    const double isd = d.int_time_s * kFs;
+    if (d.keep_bins != 0 && d.keep_bins != N)
+        return set_error(MWAX_EUNSUPPORTED, "allocation-free call: all fft_len bins are kept");
+    if (d.sample_rate_hz < 0.0) return set_error(MWAX_EINVAL, "sample_rate_hz must be >= 0");
+    const double fs = d.sample_rate_hz > 0.0 ? d.sample_rate_hz : kFs;
+    const double isd = d.int_time_s * fs;
     const long long is = llround(isd);
     if (is < 1 || fabs(isd - (double)is) > 1e-9 * isd || is % N)
         return set_error(MWAX_EINVAL, "integration must be a whole number of frames");
@@ -220,6 +224,7 @@ extern "C" mwax_status mwax_correlate_noalloc(const mwax_plan_desc* desc, const 
     fa_.bs = bs;
     fa_.nu = d.sky_freq_hz;
     fa_.out_scale = 1.0f;
+    fa_.fs = fs;
     if ((e = launch_fstep(N, FOUT_F32, fa_, s, 0)) != cudaSuccess) return cuda_error(e, "F-step launch");
     XArgs xa;
     memset(&xa, 0, sizeof xa);

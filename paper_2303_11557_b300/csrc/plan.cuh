@@ -14,6 +14,8 @@ using mwax::XItem;
 struct mwax_plan {
     mwax_plan_desc desc;
     int T = 0, n = 0, N = 0, F = 0, M = 0, bs = 0, prec = 0, dc_excl = 1;
+    int keep = 0;             // ultrafine channels passed to the X step (centred on DC)
+    double fs = 0.0;          // coarse-channel sample rate
     long long K = 0, S = 0, n_ints = 0, B = 0, n_blocks = 0;
     double nu = 0.0;
     size_t vis_set_bytes = 0, weights_bytes = 0, int_stride = 0, input_bytes = 0;
@@ -55,6 +57,17 @@ struct mwax_plan {
     std::vector<RunInfo> h_runs;
     std::vector<Group> h_groups;
     std::vector<float> h_gain;
+    std::vector<float> h_avg_gain;   // sqrt of each channel's averaging weight
+    std::vector<float> passband;     // de-ripple gain per channel (1 = flat)
+
+    // extended calls: device copies of the delay table and zeroing flags, and what the
+    // call being enqueued uses (nullptr outside mwax_correlate_ex)
+    double* d_table = nullptr;
+    size_t table_cap = 0;
+    uint8_t* d_flags = nullptr;
+    const double* cur_table = nullptr;
+    long long cur_steps = 0, cur_step = 0;
+    const uint8_t* cur_flags = nullptr;
     struct ItemList {
         long long key;
         XItem* items;

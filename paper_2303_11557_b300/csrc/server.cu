@@ -158,11 +158,12 @@ bool try_admit(mwax_server* S)
         out_b = mwax_plan_output_bytes(probe);
     } else {
         const double bs = d.block_samples ? d.block_samples : 64000;
-        const long long S_ = d.samples_per_call ? d.samples_per_call : llround(d.int_time_s * kFs);
+        const double fs = d.sample_rate_hz > 0.0 ? d.sample_rate_hz : kFs;
+        const long long S_ = d.samples_per_call ? d.samples_per_call : llround(d.int_time_s * fs);
         in_b = (size_t)S_ * 2 * d.n_tiles * 2;
-        const long long ints = S_ / llround(d.int_time_s * kFs);
+        const long long ints = S_ / std::max(1LL, llround(d.int_time_s * fs));
         const long long B = (long long)d.n_tiles * (d.n_tiles + 1) / 2;
-        const int M = d.fft_len / d.fine_avg;
+        const int M = (d.keep_bins ? d.keep_bins : d.fft_len) / std::max(1, d.fine_avg);
         out_b = (size_t)ints * (d.precision == MWAX_INT8 ? B * 4 * 16 : B * M * 4 * 8) + (size_t)ints * B * 16;
         (void)bs;
     }

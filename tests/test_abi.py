@@ -41,6 +41,11 @@ def test_version_and_no_error():
     (dict(n_tiles=4, fft_len=128, fine_avg=1, int_time_s=0.4, block_samples=100), "block_samples"),
     (dict(n_tiles=4, fft_len=128, fine_avg=1, int_time_s=0.4, precision=mw.MWAX_INT8), "MWAX_INT8"),
     (dict(n_tiles=4, fft_len=128, fine_avg=1, int_time_s=0.4, precision=9), "precision"),
+    (dict(n_tiles=4, fft_len=128, fine_avg=4, int_time_s=0.4, keep_bins=102), "keep_bins"),
+    (dict(n_tiles=4, fft_len=128, fine_avg=4, int_time_s=0.4, keep_bins=132), "keep_bins"),
+    (dict(n_tiles=4, fft_len=128, fine_avg=4, int_time_s=0.4, sample_rate_hz=-1.0), "sample_rate_hz"),
+    # 0.1 s at 1,638,401 samples/s is not a whole number of samples
+    (dict(n_tiles=4, fft_len=128, fine_avg=4, int_time_s=0.1, sample_rate_hz=1.6384e6 + 1), "whole number"),
 ])
 def test_invalid_plans_rejected(args, frag):
     with pytest.raises(mw.MwaxError) as ei:

@@ -302,3 +302,31 @@ def correlate_int_ext(d: Desc, e: Ext, volt: np.ndarray):
     if rc:
         raise ValueError(f"oracle rejected the job (rc={rc})")
     return vis, wts
+
+
+def beamform(d: Desc, volt: np.ndarray, beam_table: np.ndarray, table_step: int = 6400, int_frames: int = 0,
+             sample_rate_hz: float = 0.0):
+    """Tied-array beams (Sec. 4.4): (beams complex128 [n_beams, 2, frames, N],
+    Stokes I power [n_beams, n_det, N], incoherent [n_det, 2, N]); the detected outputs
+    are empty when int_frames is 0.  beam_table: float64 [n_beams, n_paths, steps] s."""
+    lib = _load()
+    if not hasattr(lib, "_beam_ready"):
+        vp = ctypes.c_void_p
+        lib.ora_beamform.argtypes = [ctypes.POINTER(_Desc), ctypes.c_double, vp, ctypes.c_int, vp, ctypes.c_longlong,
+                                     ctypes.c_longlong, ctypes.c_longlong, vp, vp, vp]
+        lib.ora_beamform.restype = ctypes.c_int
+        lib._beam_ready = True
+    volt = np.ascontiguousarray(volt, dtype=np.int8)
+    tab = np.ascontiguousarray(np.asarray(beam_table, dtype=np.float64))
+    nb = tab.shape[0]
+    tab = tab.reshape(nb, d.n_paths, -1)
+    frames = d.n_samples // d.fft_len
+    n_det = frames // int_frames if int_frames > 0 else 0
+    beams = np.empty((nb, 2, frames, d.fft_len), dtype=np.complex128)
+    power = np.empty((nb, n_det, d.fft_len))
+    incoh = np.empty((n_det, 2, d.fft_len))
+    rc = lib.ora_beamform(ctypes.byref(d.c()), sample_rate_hz, _p(volt), nb, _p(tab), table_step, tab.shape[2],
+                          int_frames, _p(beams), _p(power), _p(incoh))
+    if rc:
+        raise ValueError(f"oracle rejected the job (rc={rc})")
+    return beams, power, incoh

@@ -619,3 +619,70 @@ int ora_correlate_int_ext(const ora_desc* d, const ora_ext* e, const int8_t* vol
         }
     return 0;
 }
+
+/* ============================================================================
+ * Tied-array beamformer (Sec. 4.4), plain FP64.  The spectra of every path are formed
+ * without the correlator's delay correction (steps 1-3); coherent beam b of polarisation
+ * a is the delay-steered sum over tiles t of path p = 2t + a:
+ *     B_b,a[m, c] = sum_t Y_p[m, c] exp(+2 pi i (nu + f_u) tau_b,p(step(m)))
+ * with tau from the beam's table of fractional delays (one value per path per step of
+ * table_step samples, a frame taking the step that holds its centre, as in Sec. 2.4.1).
+ * Detected outputs over integrations of int_frames frames (when int_frames > 0):
+ *     P_b[w, c] = sum_{m in w} |B_b,x[m, c]|^2 + |B_b,y[m, c]|^2   (Stokes I)
+ *     I[w, a, c] = sum_{m in w} sum_t |Y_{2t+a}[m, c]|^2             (incoherent beam)
+ * ========================================================================== */
+int ora_beamform(const ora_desc* d, double fs_in, const int8_t* volt, int n_beams, const double* beam_tab,
+                 long long table_step, long long table_steps, long long int_frames, double complex* beams,
+                 double* power, double* incoh)
+{
+    if (ora_check(d) || n_beams < 1 || table_step < 1 || table_steps < 1) return -1;
+    int T = d->n_tiles, n = 2 * T, N = d->fft_len;
+    double fs = fs_in > 0.0 ? fs_in : ORA_FS;
+    long long frames = d->n_samples / N;
+    long long n_det = int_frames > 0 ? frames / int_frames : 0;
+    double complex* Y = malloc(sizeof(double complex) * (size_t)n * (size_t)frames * (size_t)N);
+    if (!Y) return -2;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int p = 0; p < n; ++p) ora_spectra(d, volt, NULL, p, 0, frames, Y + (size_t)p * frames * N);
+#pragma omp parallel for schedule(dynamic, 1) collapse(2)
+    for (int b = 0; b < n_beams; ++b)
+        for (int a = 0; a < 2; ++a)
+            for (long long m = 0; m < frames; ++m) {
+                long long step = (2 * m * N + N) / (2 * table_step);
+                if (step >= table_steps) step = table_steps - 1;
+                for (int c = 0; c < N; ++c) {
+                    double f = (double)ora_offset_of_channel(N, c) * fs / (double)N;
+                    double complex acc = 0;
+                    for (int t = 0; t < T; ++t) {
+                        int p = 2 * t + a;
+                        double tau = beam_tab[((long long)b * n + p) * table_steps + step];
+                        double cyc = (d->sky_freq_hz + f) * tau;
+                        acc += Y[((size_t)p * frames + m) * N + c] * cexp(2.0 * ORA_PI * I * cyc);
+                    }
+                    beams[(((size_t)b * 2 + a) * frames + m) * N + c] = acc;
+                }
+            }
+    for (long long w = 0; w < n_det; ++w)
+        for (int c = 0; c < N; ++c) {
+            for (int b = 0; b < n_beams; ++b) {
+                double s = 0.0;
+                for (long long m = w * int_frames; m < (w + 1) * int_frames; ++m)
+                    for (int a = 0; a < 2; ++a) {
+                        double complex v = beams[(((size_t)b * 2 + a) * frames + m) * N + c];
+                        s += creal(v) * creal(v) + cimag(v) * cimag(v);
+                    }
+                if (power) power[((size_t)b * n_det + w) * N + c] = s;
+            }
+            for (int a = 0; a < 2; ++a) {
+                double s = 0.0;
+                for (long long m = w * int_frames; m < (w + 1) * int_frames; ++m)
+                    for (int t = 0; t < T; ++t) {
+                        double complex v = Y[((size_t)(2 * t + a) * frames + m) * N + c];
+                        s += creal(v) * creal(v) + cimag(v) * cimag(v);
+                    }
+                if (incoh) incoh[((size_t)w * 2 + a) * N + c] = s;
+            }
+        }
+    free(Y);
+    return 0;
+}

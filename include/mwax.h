@@ -321,6 +321,57 @@ mwax_status mwax_server_get_stats(mwax_server* server, mwax_server_stats* stats)
 /* Finish the queued requests, free everything.  NULL is a no-op. */
 void mwax_server_destroy(mwax_server* server);
 
+/* ------------------------------------------------------------------ tied-array beamformer */
+
+/*
+ * Multibeam beamformer (Sec. 4.4) on the correlator's F-step: the voltages are channelised
+ * (N-point FFT, centre-symmetric channel order, no delay correction) and each beam steers
+ * every path with its own tabulated fractional delays, then sums the tiles of each
+ * polarisation:
+ *     B_b,a[m, c] = sum_t Y_{2t+a}[m, c] exp(+2 pi i (nu + f_u) tau_b,2t+a(step(m)))
+ * (f_u = (c - N/2) Fs / N; a frame takes the table step that holds its centre sample).
+ * Optional detected outputs per interval of int_frames frames: Stokes I of each beam,
+ * sum over the interval of |B_x|^2 + |B_y|^2, and the incoherent beam, sum over the
+ * interval and the tiles of |Y|^2 per polarisation.  FP32 throughout.
+ */
+typedef struct mwax_beamformer mwax_beamformer;
+
+typedef struct {
+    int n_tiles;                  /* T >= 1                                                   */
+    int fft_len;                  /* N: a built FFT length >= 16                              */
+    int n_beams;                  /* >= 1                                                     */
+    long long samples_per_call;   /* whole blocks                                             */
+    int block_samples;            /* 0 = 64,000                                               */
+    double sky_freq_hz;           /* nu                                                        */
+    double sample_rate_hz;        /* 0 = 1.28 MS/s                                            */
+    long long table_step_samples; /* samples per delay-table entry; 0 = 6,400 (5 ms)          */
+    int int_frames;               /* frames per detected sample; 0 = no detected outputs      */
+    size_t workspace_limit;       /* device bytes for one chunk's spectra; 0 = 4 GiB          */
+} mwax_beam_desc;
+
+/* NULL on error (mwax_last_error()); allocates the spectra workspace on the current device. */
+mwax_beamformer* mwax_beam_create(const mwax_beam_desc* desc);
+mwax_status mwax_beam_set_stream(mwax_beamformer* bf, void* cuda_stream);
+
+/* Output sizes in bytes: which = 0 coherent beams complex64 [n_beams][2][frames][N],
+ * 1 Stokes I float32 [n_beams][n_det][N], 2 incoherent float32 [n_det][2][N], with
+ * frames = samples_per_call / N and n_det = frames / int_frames (0 without int_frames). */
+size_t mwax_beam_output_bytes(const mwax_beamformer* bf, int which);
+
+/*
+ * Form the beams of one call.  voltages: device, as for mwax_correlate (16-byte aligned);
+ * beam_delay: float64 [n_beams][n][table_steps] seconds, host or device (a pinned host
+ * table is waited for; entries past the end of the table repeat the last); beams_out:
+ * device, required; power_out, incoh_out: device or NULL (need int_frames >= 1).
+ * Asynchronous on the beamformer's stream.
+ */
+mwax_status mwax_beam_form(mwax_beamformer* bf, const int8_t* voltages, const double* beam_delay,
+                           long long table_steps, void* beams_out, float* power_out, float* incoh_out);
+mwax_status mwax_beam_sync(mwax_beamformer* bf);
+
+/* Waits for the beamformer's stream, frees everything.  NULL is a no-op. */
+void mwax_beam_destroy(mwax_beamformer* bf);
+
 /* ------------------------------------------------------------------ allocation-free call */
 
 /*

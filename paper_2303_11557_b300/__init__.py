@@ -43,6 +43,14 @@ class _CDesc(ctypes.Structure):
                 ("sample_rate_hz", ctypes.c_double), ("keep_bins", ctypes.c_int)]
 
 
+class _BeamDesc(ctypes.Structure):
+    _fields_ = [("n_tiles", ctypes.c_int), ("fft_len", ctypes.c_int), ("n_beams", ctypes.c_int),
+                ("samples_per_call", ctypes.c_longlong), ("block_samples", ctypes.c_int),
+                ("sky_freq_hz", ctypes.c_double), ("sample_rate_hz", ctypes.c_double),
+                ("table_step_samples", ctypes.c_longlong), ("int_frames", ctypes.c_int),
+                ("workspace_limit", ctypes.c_size_t)]
+
+
 class _Call(ctypes.Structure):
     _fields_ = [("voltages", ctypes.c_void_p), ("delay_poly", ctypes.c_void_p), ("delay_table", ctypes.c_void_p),
                 ("table_steps", ctypes.c_longlong), ("table_step_samples", ctypes.c_longlong),
@@ -109,7 +117,8 @@ SYMBOLS = ("mwax_plan_create", "mwax_plan_create_ex", "mwax_plan_get_info", "mwa
            "mwax_batch_create", "mwax_batch_set_stream", "mwax_batch_set_graphs", "mwax_batch_correlate",
            "mwax_batch_sync", "mwax_batch_destroy", "mwax_server_create", "mwax_server_submit", "mwax_server_poll",
            "mwax_server_wait", "mwax_server_drain", "mwax_server_get_stats", "mwax_server_destroy",
-           "mwax_correlate_noalloc", "mwax_correlate_ex", "mwax_plan_set_passband")
+           "mwax_correlate_noalloc", "mwax_correlate_ex", "mwax_plan_set_passband", "mwax_beam_create",
+           "mwax_beam_set_stream", "mwax_beam_output_bytes", "mwax_beam_form", "mwax_beam_sync", "mwax_beam_destroy")
 
 
 def load_library(path: str | None = None):
@@ -192,6 +201,18 @@ def load_library(path: str | None = None):
     lib.mwax_correlate_ex.restype = st
     lib.mwax_plan_set_passband.argtypes = [vp, vp]
     lib.mwax_plan_set_passband.restype = st
+    lib.mwax_beam_create.argtypes = [ctypes.POINTER(_BeamDesc)]
+    lib.mwax_beam_create.restype = vp
+    lib.mwax_beam_set_stream.argtypes = [vp, vp]
+    lib.mwax_beam_set_stream.restype = st
+    lib.mwax_beam_output_bytes.argtypes = [vp, ctypes.c_int]
+    lib.mwax_beam_output_bytes.restype = ctypes.c_size_t
+    lib.mwax_beam_form.argtypes = [vp, vp, vp, ctypes.c_longlong, vp, vp, vp]
+    lib.mwax_beam_form.restype = st
+    lib.mwax_beam_sync.argtypes = [vp]
+    lib.mwax_beam_sync.restype = st
+    lib.mwax_beam_destroy.argtypes = [vp]
+    lib.mwax_beam_destroy.restype = None
     lib.mwax_version.argtypes = []
     lib.mwax_version.restype = ctypes.c_char_p
     _lib = lib
@@ -482,6 +503,51 @@ def mwax_plan_set_passband(plan: Plan, gain=None):
     if g is not None and g.size != plan.desc.fft_len:
         raise ValueError("passband gain must hold fft_len values")
     _check(load_library().mwax_plan_set_passband(plan.handle, _ptr(g)))
+
+
+class Beamformer:
+    """Tied-array multibeam beamformer (Sec. 4.4); owns one mwax_beamformer*."""
+
+    def __init__(self, n_tiles: int, fft_len: int, n_beams: int, samples_per_call: int, *, block_samples: int = 0,
+                 sky_freq_hz: float = 0.0, sample_rate_hz: float = 0.0, table_step_samples: int = 0,
+                 int_frames: int = 0, workspace_limit: int = 0):
+        lib = load_library()
+        self.desc = _BeamDesc(n_tiles, fft_len, n_beams, samples_per_call, block_samples, sky_freq_hz, sample_rate_hz,
+                              table_step_samples, int_frames, workspace_limit)
+        h = lib.mwax_beam_create(ctypes.byref(self.desc))
+        if not h:
+            raise MwaxError(MWAX_EINVAL, mwax_last_error())
+        self.handle = h
+        self.n_paths, self.fft_len, self.n_beams = 2 * n_tiles, fft_len, n_beams
+        self.frames = samples_per_call // fft_len
+        self.n_det = self.frames // int_frames if int_frames else 0
+
+    def set_stream(self, stream=None):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(load_library().mwax_beam_set_stream(self.handle, ctypes.c_void_p(s.cuda_stream)))
+
+    def output_bytes(self, which: int) -> int:
+        return load_library().mwax_beam_output_bytes(self.handle, which)
+
+    def form(self, voltages, beam_delay, beams_out, power_out=None, incoh_out=None):
+        """beam_delay: float64 [n_beams, n_paths, steps] (numpy or torch); outputs device tensors."""
+        ptr, keep = _array_arg(beam_delay, np.float64)
+        numel = beam_delay.size if isinstance(beam_delay, np.ndarray) else beam_delay.numel()
+        steps = numel // (self.n_beams * self.n_paths)
+        if steps < 1 or steps * self.n_beams * self.n_paths != numel:
+            raise ValueError("beam_delay must hold n_beams x n_paths x steps float64")
+        _check(load_library().mwax_beam_form(self.handle, _ptr(voltages), ptr, steps, _ptr(beams_out),
+                                             _ptr(power_out), _ptr(incoh_out)))
+        return keep
+
+    def sync(self):
+        _check(load_library().mwax_beam_sync(self.handle))
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.mwax_beam_destroy(h)
 
 
 def mwax_plan_destroy(plan: Plan):

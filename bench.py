@@ -410,6 +410,91 @@ def time_plan(mw, torch, plan, dev_volt, dev_delay, steps, warmup, world, clocks
     return ms, stages, out, ck
 
 
+def _time_calls(torch, fn, steps, warmup):
+    """Device milliseconds per call of fn() on torch's current stream (CUDA events)."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_extensions(mw, torch, W, dev_volt, delay, args):
+    """The roadmap rows on the full 256-tile sub-observation (Sec. 2.4, 4.1-4.5): per-call
+    device time of the plain FP16 call beside the same call with zeroing flags +
+    normalisation, a 5 ms delay table, de-ripple gains; an oversampled channel (FP16);
+    and 8 tied-array beams with detected outputs (FP32), with the beam kernel's rate."""
+    import numpy as np
+    import synth
+    T, S, N = W["n_tiles"], W["samples"], W["fft_len"]
+    n = 2 * T
+    steps, warm = max(2, min(args.steps, 3)), 1
+    res = {}
+    desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=W["fine_avg"], int_time_s=W["int_time_s"], samples_per_call=S,
+                       precision=mw.MWAX_FP16, sky_freq_hz=W["sky_freq_hz"])
+    plan = mw.mwax_plan_create_ex(desc)
+    mw.mwax_plan_set_stream(plan)
+    out = mw.empty_output(plan)
+    ddelay = torch.from_numpy(delay).cuda()
+    n_blocks = S // 64_000
+    flags = torch.from_numpy((np.random.default_rng(W["seed"]).random((n_blocks, n)) < 0.01).astype(np.uint8)).cuda()
+    t_mid = (np.arange(S // 6400) + 0.5) * 6400 / synth.FS
+    table = torch.from_numpy(np.ascontiguousarray(delay[:, :1] + delay[:, 1:2] * t_mid[None, :])).cuda()
+    u = np.arange(N) - N // 2
+    gains = (1.0 / ((1 + 0.03 * np.cos(2 * np.pi * u / 21.0)) * (1 - 0.45 * (np.abs(u) / (N / 2)) ** 6)))
+    plain = _time_calls(torch, lambda: mw.mwax_correlate(plan, dev_volt, ddelay, out), steps, warm)
+    fl = _time_calls(torch, lambda: mw.mwax_correlate_ex(plan, dev_volt, out, delay_poly=ddelay, zero_flags=flags,
+                                                         normalise=True), steps, warm)
+    tb = _time_calls(torch, lambda: mw.mwax_correlate_ex(plan, dev_volt, out, delay_table=table), steps, warm)
+    mw.mwax_plan_set_passband(plan, gains.astype(np.float32))
+    pb = _time_calls(torch, lambda: mw.mwax_correlate(plan, dev_volt, ddelay, out), steps, warm)
+    plan.close()
+    del out
+    ch = lambda ms: SUBOBS_S / (ms * 1e-3)
+    res["fp16_plain"] = {"ms_per_subobs": plain, "channels": ch(plain)}
+    res["zero_flags_normalised"] = {"ms_per_subobs": fl, "channels": ch(fl), "flagged_blocks": "1 % seeded"}
+    res["delay_table_5ms"] = {"ms_per_subobs": tb, "channels": ch(tb), "steps_per_path": int(S // 6400)}
+    res["passband_deripple"] = {"ms_per_subobs": pb, "channels": ch(pb)}
+    # oversampled coarse channel: 32/25 x 1.28 MS/s, the central 100 of 128 bins, 25 channels
+    fs = 1.6384e6
+    od = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=4, int_time_s=1_024_000 / fs, samples_per_call=S,
+                     precision=mw.MWAX_FP16, sky_freq_hz=W["sky_freq_hz"], sample_rate_hz=fs, keep_bins=100)
+    op = mw.mwax_plan_create_ex(od)
+    mw.mwax_plan_set_stream(op)
+    oo = mw.empty_output(op)
+    os_ms = _time_calls(torch, lambda: mw.mwax_correlate(op, dev_volt, ddelay, oo), steps, warm)
+    res["oversampled_32_25"] = {"ms_per_call": os_ms, "seconds_of_data": S / fs, "real_time_factor": S / fs / (os_ms * 1e-3),
+                                "n_chan_out": op.info["n_chan_out"]}
+    op.close()
+    del oo
+    # tied-array beams: 8 beams, 5 ms steering tables, 10 ms detected Stokes I + incoherent
+    nb = 8
+    bf = mw.Beamformer(T, N, nb, S, sky_freq_hz=W["sky_freq_hz"], int_frames=100)
+    bf.set_stream()
+    rng = np.random.default_rng(W["seed"] + 4)
+    btab = torch.from_numpy(delay[None, :, :1] + rng.uniform(-200e-9, 200e-9, (nb, n, 1)) +
+                            delay[None, :, 1:2] * t_mid[None, None, :]).cuda()
+    beams = torch.empty(bf.output_bytes(0), dtype=torch.uint8, device="cuda")
+    power = torch.empty(bf.output_bytes(1), dtype=torch.uint8, device="cuda").view(torch.float32)
+    incoh = torch.empty(bf.output_bytes(2), dtype=torch.uint8, device="cuda").view(torch.float32)
+    bms = _time_calls(torch, lambda: bf.form(dev_volt, btab, beams, power, incoh), steps, warm)
+    flops = 8.0 * nb * n * S
+    pk, pk_kind = peaks()
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    res["beamformer"] = {"n_beams": nb, "ms_per_subobs": bms, "real_time_factor": SUBOBS_S / (bms * 1e-3),
+                         "whole_call_tflops": flops / (bms * 1e-3) / 1e12, "fp32_peak_tflops": fp32_peak,
+                         "whole_call_frac": flops / (bms * 1e-3) / 1e12 / fp32_peak,
+                         "work": "8 flop per beam x path x sample (complex MAC); call includes the F-step"}
+    del bf, beams, power, incoh
+    return res
+
+
 def rel_error_vs(mw, torch, plan, out, ref_vis, T):
     """max / median of |V - V_ref| / sqrt(V_ref,pp V_ref,qq) (parallel-pol autos of V_ref)."""
     vis, _ = mw.split_output(plan, out)
@@ -531,6 +616,10 @@ def run_mine(args, world, rank, local):
                "h2d_bytes_per_step": info["input_bytes"] + delay.nbytes, "d2h_bytes_per_step": info["output_bytes"],
                "ms_per_step": 1e3 * t_e2e}
 
+    ext = None
+    if not args.no_ext and W is WORKLOAD:
+        ext = run_extensions(mw, torch, W, dev_volt, delay, args)
+
     # configs 3 and 4: batched mixed channels, real-time serving
     batch = serve = None
     if not args.no_batch and W is WORKLOAD:
@@ -570,6 +659,7 @@ def run_mine(args, world, rank, local):
                             if f != headline},
         "batch": batch,
         "serving": serve,
+        "extensions": ext,
         "context": {"paper": "1 coarse channel of 256 tiles in real time per NVIDIA A40 (6.2 s per 8 s at "
                              "250 ms / 40 kHz, Table 2)"},
     }
@@ -589,6 +679,7 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="time the headline precision only")
     ap.add_argument("--no-batch", action="store_true", help="skip the 24-channel batched measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the real-time serving measurement")
+    ap.add_argument("--no-ext", action="store_true", help="skip the roadmap extensions and the beamformer")
     ap.add_argument("--workload", default="full", choices=["full", "small"],
                     help="small = one 0.5 s integration (for profiler captures)")
     args = ap.parse_args()

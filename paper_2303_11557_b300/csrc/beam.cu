@@ -8,10 +8,11 @@
 //     B_b,a[m, c] = sum_t Y_{2t+a}[m, c] exp(+2 pi i (nu + f_u) tau_b,2t+a(step(m)))
 // For one channel and one step that is a small complex matrix product, beams x tiles
 // times tiles x frames, whose left factor W[b][t] depends on (channel, step) only.  A CTA
-// takes one step's frames (up to 64), 8 channels and up to 8 beams of one polarisation:
+// takes one step's frames (up to 32), 8 channels and up to 8 beams of one polarisation:
 // it builds W for 16 tiles at a time in shared memory (one sincospi per beam and tile, the
-// other channels by the exact phasor ratio e^{2 pi i tau Fs / N}), stages the matching
-// spectra, and each thread accumulates an 8-beam x 4-frame complex register tile.  The
+// other channels by the exact phasor ratio e^{2 pi i tau Fs / N}) while the next 16 tiles'
+// spectra stream in by asynchronous copies (two stages), and each thread accumulates an
+// 8-beam x 2-frame complex register tile.  The
 // incoherent beam (sum over tiles of |Y|^2) is accumulated from the same staged spectra.
 // Detected Stokes I is formed afterwards from the coherent beams.
 #include <math.h>
@@ -26,11 +27,14 @@ namespace mwax {
 namespace {
 
 constexpr int CB = 8;      // channels per CTA
-constexpr int FMAX = 64;   // frames per CTA
+constexpr int FMAX = 32;   // frames per CTA
 constexpr int TC = 16;     // tiles per shared-memory chunk
 constexpr int BG = 8;      // beams per CTA
-constexpr int NT = 128;    // threads: 8 channels x 16 groups of 4 frames
-constexpr size_t kBeamSmem = sizeof(float2) * CB * TC * BG + 2 * sizeof(float) * CB * TC * FMAX;   // 72 KB
+constexpr int NT = 128;    // threads: 8 channels x 16 pairs of frames
+// two stages of (spectra Re, Im planes + steering phasors): 80 KB
+constexpr size_t kStageY = sizeof(float) * CB * TC * FMAX;
+constexpr size_t kStageW = sizeof(float2) * CB * TC * BG;
+constexpr size_t kBeamSmem = 2 * (2 * kStageY + kStageW);
 
 struct BeamUnit {
     int m_lo, m_hi;   // frames of the chunk (relative to its first frame)
@@ -54,6 +58,17 @@ __global__ void beam_params_kernel(const double* __restrict__ tab, long long tot
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 
+// 4-byte asynchronous copy global -> shared; src_bytes = 0 fills the destination with zero.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, int src_bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 struct BeamArgs {
     const float* Y;         // chunk spectra, slot 0: [N][2][n][Kpad]
     const float4* params;   // [nb][n][steps]
@@ -68,43 +83,55 @@ struct BeamArgs {
 __global__ void __launch_bounds__(NT) beam_kernel(const BeamArgs a)
 {
     extern __shared__ __align__(16) unsigned char beam_smem[];
-    float2 (*W)[TC][BG] = reinterpret_cast<float2 (*)[TC][BG]>(beam_smem);
-    float (*Yr)[TC][FMAX] = reinterpret_cast<float (*)[TC][FMAX]>(beam_smem + sizeof(float2) * CB * TC * BG);
-    float (*Yi)[TC][FMAX] = Yr + CB;
-
     const BeamUnit un = a.units[blockIdx.x];
     const int c0 = blockIdx.y * CB;
     const int pol = blockIdx.z & 1, bg = blockIdx.z >> 1;
     const int tid = threadIdx.x;
-    const int ch = tid / 16, fg = tid % 16;
+    const int ch = tid / 16, fg = tid % 16;   // channel, frames 2 fg and 2 fg + 1
     const int nfr = un.m_hi - un.m_lo;
+    const int n_chunks = (a.T + TC - 1) / TC;
 
-    float2 acc[BG][4];
-#pragma unroll
-    for (int b = 0; b < BG; ++b)
-#pragma unroll
-        for (int f = 0; f < 4; ++f) acc[b][f] = make_float2(0.0f, 0.0f);
-    float pw[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    const bool want_incoh = a.incoh != nullptr && bg == 0;
+    auto Yr = [&](int st) { return reinterpret_cast<float (*)[TC][FMAX]>(beam_smem + st * (2 * kStageY + kStageW)); };
+    auto Yi = [&](int st) {
+        return reinterpret_cast<float (*)[TC][FMAX]>(beam_smem + st * (2 * kStageY + kStageW) + kStageY);
+    };
+    auto Wt = [&](int st) {
+        return reinterpret_cast<float2 (*)[TC][BG]>(beam_smem + st * (2 * kStageY + kStageW) + 2 * kStageY);
+    };
 
-    for (int t0 = 0; t0 < a.T; t0 += TC) {
-        // spectra of 16 tiles x 8 channels x the unit's frames (zero past the end)
+    // stage the spectra of tile chunk k (16 tiles x 8 channels x the unit's frames, zero
+    // past the end) with asynchronous copies
+    auto stage = [&](int k, int st) {
+        float (*yr)[TC][FMAX] = Yr(st);
+        float (*yi)[TC][FMAX] = Yi(st);
         for (int i = tid; i < 2 * CB * TC * FMAX; i += NT) {
             const int m = i % FMAX, r = i / FMAX;
             const int t = r % TC, cp = r / TC;
             const int c = cp % CB, plane = cp / CB;
-            float v = 0.0f;
-            const int tt = t0 + t;
-            if (m < nfr && tt < a.T) {
-                const long long p = 2 * tt + pol;
-                v = __ldg(a.Y + (((long long)(c0 + c) * 2 + plane) * a.n + p) * a.Kpad + un.m_lo + m);
-            }
-            (plane ? Yi : Yr)[c][t][m] = v;
+            const int tt = k * TC + t;
+            const bool ok = m < nfr && tt < a.T;
+            const long long p = 2 * (long long)(ok ? tt : 0) + pol;
+            const float* src = a.Y + (((long long)(c0 + c) * 2 + plane) * a.n + p) * a.Kpad + un.m_lo + (ok ? m : 0);
+            cp_async4(plane ? &yi[c][t][m] : &yr[c][t][m], src, ok ? 4 : 0);
         }
-        // steering phasors of 8 beams x 16 tiles for the 8 channels
+        cp_async_commit();
+    };
+
+    float2 acc[BG][2];
+#pragma unroll
+    for (int b = 0; b < BG; ++b) acc[b][0] = acc[b][1] = make_float2(0.0f, 0.0f);
+    float pw[2] = {0.0f, 0.0f};
+    const bool want_incoh = a.incoh != nullptr && bg == 0;
+
+    stage(0, 0);
+    for (int k = 0; k < n_chunks; ++k) {
+        const int st = k & 1;
+        if (k + 1 < n_chunks) stage(k + 1, st ^ 1);
+        // steering phasors of 8 beams x 16 tiles for the 8 channels: one sincospi at the
+        // first channel, the others by the exact ratio e^{2 pi i d}
         {
             const int t = tid / BG, b = tid % BG;
-            const int tt = t0 + t, bb = bg * BG + b;
+            const int tt = k * TC + t, bb = bg * BG + b;
             float2 w[CB];
             if (tt < a.T && bb < a.nb) {
                 const float4 pr = __ldg(a.params + ((long long)bb * a.n + 2 * tt + pol) * a.steps + un.step);
@@ -120,20 +147,26 @@ __global__ void __launch_bounds__(NT) beam_kernel(const BeamArgs a)
                 sincospif(2.0f * dd, &sn, &cs);
                 const float2 R = make_float2(cs, sn);
 #pragma unroll
-                for (int k = 1; k < CB; ++k) w[k] = cmul(w[k - 1], R);
+                for (int q = 1; q < CB; ++q) w[q] = cmul(w[q - 1], R);
             } else {
 #pragma unroll
-                for (int k = 0; k < CB; ++k) w[k] = make_float2(0.0f, 0.0f);
+                for (int q = 0; q < CB; ++q) w[q] = make_float2(0.0f, 0.0f);
             }
+            float2 (*W)[TC][BG] = Wt(st);
 #pragma unroll
-            for (int k = 0; k < CB; ++k) W[k][t][b] = w[k];
+            for (int q = 0; q < CB; ++q) W[q][t][b] = w[q];
         }
+        if (k + 1 < n_chunks) cp_async_wait<1>();
+        else cp_async_wait<0>();
         __syncthreads();
+        float (*yr)[TC][FMAX] = Yr(st);
+        float (*yi)[TC][FMAX] = Yi(st);
+        float2 (*W)[TC][BG] = Wt(st);
 #pragma unroll 4
         for (int t = 0; t < TC; ++t) {
-            const float4 yr = *reinterpret_cast<const float4*>(&Yr[ch][t][4 * fg]);
-            const float4 yi = *reinterpret_cast<const float4*>(&Yi[ch][t][4 * fg]);
-            const float y_r[4] = {yr.x, yr.y, yr.z, yr.w}, y_i[4] = {yi.x, yi.y, yi.z, yi.w};
+            const float2 r2 = *reinterpret_cast<const float2*>(&yr[ch][t][2 * fg]);
+            const float2 i2 = *reinterpret_cast<const float2*>(&yi[ch][t][2 * fg]);
+            const float y_r[2] = {r2.x, r2.y}, y_i[2] = {i2.x, i2.y};
 #pragma unroll
             for (int b2 = 0; b2 < BG / 2; ++b2) {
                 const float4 ww = *reinterpret_cast<const float4*>(&W[ch][t][2 * b2]);
@@ -141,7 +174,7 @@ __global__ void __launch_bounds__(NT) beam_kernel(const BeamArgs a)
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
 #pragma unroll
-                    for (int f = 0; f < 4; ++f) {
+                    for (int f = 0; f < 2; ++f) {
                         float2& s = acc[2 * b2 + h][f];
                         s.x = fmaf(wv[h].x, y_r[f], fmaf(-wv[h].y, y_i[f], s.x));
                         s.y = fmaf(wv[h].x, y_i[f], fmaf(wv[h].y, y_r[f], s.y));
@@ -149,16 +182,16 @@ __global__ void __launch_bounds__(NT) beam_kernel(const BeamArgs a)
             }
             if (want_incoh) {
 #pragma unroll
-                for (int f = 0; f < 4; ++f) pw[f] = fmaf(y_r[f], y_r[f], fmaf(y_i[f], y_i[f], pw[f]));
+                for (int f = 0; f < 2; ++f) pw[f] = fmaf(y_r[f], y_r[f], fmaf(y_i[f], y_i[f], pw[f]));
             }
         }
-        __syncthreads();
+        __syncthreads();   // stage st is refilled two iterations on
     }
 
     const int c = c0 + ch;
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-        const int m = 4 * fg + f;
+    for (int f = 0; f < 2; ++f) {
+        const int m = 2 * fg + f;
         if (m >= nfr) continue;
         const long long fr = a.f0 + un.m_lo + m;   // frame in the call
 #pragma unroll

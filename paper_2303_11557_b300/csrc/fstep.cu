@@ -632,15 +632,56 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
     }
 }
 
-// N = 1: no FFT.  One thread per (path, 4 samples); optional phasor e^{2 pi i nu tau}.
+// N = 1: no FFT.  One thread per (path, 8 samples).  The common case (no delay, no flags,
+// FP32/FP16 output, the 8 samples in one data block and one operand slot) is one 16-byte
+// load and 16-byte stores per plane with the index arithmetic done once; everything else
+// (phasor e^{2 pi i nu tau}, flags, FP8 maxima, group edges) takes the per-sample path.
 template <int OUTK>
 __global__ void __launch_bounds__(256) unpack_kernel(const FArgs a)
 {
     const int p = blockIdx.y;
-    const long long i4 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long f_first = i4 * 4;
+    const long long i8 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long f_first = i8 * 8;
     if (f_first >= a.n_store) return;
-    for (int e = 0; e < 4; ++e) {
+    if ((OUTK == FOUT_F32 || OUTK == FOUT_F16) && a.delay == nullptr && a.delay_tab == nullptr &&
+        a.flags == nullptr && f_first + 8 <= a.n_frames) {
+        const long long s0 = a.m_begin + f_first;
+        const long long blk = s0 / a.bs, off = s0 % a.bs;
+        const long long slot = f_first / a.Kc, k = f_first % a.Kc;
+        const int8_t* src = a.volt + ((blk * a.n + p) * (long long)a.bs + off) * 2;
+        if (off + 8 <= a.bs && k + 8 <= a.Kc && (k & 7) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+            const int4 raw = __ldg(reinterpret_cast<const int4*>(src));
+            const char2* x = reinterpret_cast<const char2*>(&raw);
+            const float g = __ldg(&a.gain[0]) * (OUTK == FOUT_F16 ? a.out_scale : 1.0f);
+            const long long at = (slot * 2LL * a.n + p) * a.Kpad + k;
+            const long long ps = (long long)a.n * a.Kpad;
+            if (OUTK == FOUT_F16) {
+                __half2 re[4], im[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    re[e] = __floats2half2_rn((float)x[2 * e].x * g, (float)x[2 * e + 1].x * g);
+                    im[e] = __floats2half2_rn((float)x[2 * e].y * g, (float)x[2 * e + 1].y * g);
+                }
+                __half* Y = static_cast<__half*>(a.Y);
+                *reinterpret_cast<uint4*>(Y + at) = *reinterpret_cast<const uint4*>(re);
+                *reinterpret_cast<uint4*>(Y + at + ps) = *reinterpret_cast<const uint4*>(im);
+            } else {
+                float re[8], im[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    re[e] = (float)x[e].x * g;
+                    im[e] = (float)x[e].y * g;
+                }
+                float* Y = static_cast<float*>(a.Y);
+                *reinterpret_cast<float4*>(Y + at) = make_float4(re[0], re[1], re[2], re[3]);
+                *reinterpret_cast<float4*>(Y + at + 4) = make_float4(re[4], re[5], re[6], re[7]);
+                *reinterpret_cast<float4*>(Y + at + ps) = make_float4(im[0], im[1], im[2], im[3]);
+                *reinterpret_cast<float4*>(Y + at + ps + 4) = make_float4(im[4], im[5], im[6], im[7]);
+            }
+            return;
+        }
+    }
+    for (int e = 0; e < 8; ++e) {
         const long long fl = f_first + e;
         if (fl >= a.n_store) break;
         const long long s = a.m_begin + fl;
@@ -710,7 +751,7 @@ cudaError_t launch_kind(int N, const FArgs& a, cudaStream_t s, int variant)
     }
     switch (N) {
         case 1: {
-            dim3 grid((unsigned)((a.n_store + 1023) / 1024), (unsigned)a.n);
+            dim3 grid((unsigned)((a.n_store + 2047) / 2048), (unsigned)a.n);
             unpack_kernel<OUTK><<<grid, 256, 0, s>>>(a);
             return cudaGetLastError();
         }

@@ -499,6 +499,7 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
 
     const int p = blockIdx.y;
     const long long f0 = (long long)blockIdx.x * FB;
+
     // FP8: when all of the CTA's frames lie in one slot, the per-group maxima are gathered
     // in shared memory (warp reduction, then one shared atomic) and flushed at the end
     const long long slot_first = (f0 < a.n_store) ? f0 / a.Kc : -1;
@@ -512,34 +513,30 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
             gmax[i] = 0u;
         }
     }
-    if (threadIdx.x < FB) {
-        const int f = threadIdx.x;
+    // Per-frame delay terms (Sec. 4.3), four roles per frame spread over the CTA's threads
+    // so that no warp carries all of the FP64 work into the barrier after pass 1.
+    {
+        const int f = threadIdx.x % FB, role = threadIdx.x / FB;
         const long long fl = f0 + f;
-        FrameR32 fi;
-        fi.slot = (fl < a.n_store) ? fl / a.Kc : -1;
-        fi.k = (fl < a.n_store) ? fl % a.Kc : 0;
-        fi.delay = 0;
-        fi.phi0 = fi.d_hi = fi.d_lo = 0.0f;
-        fi.step1 = fi.step32 = fi.wrap = make_float2(1.0f, 0.0f);
-        if ((a.delay != nullptr || a.delay_tab != nullptr) && fl < a.n_frames) {
-            const double tau = frame_delay(a, p, (a.m_begin + fl) * (long long)N, N);
+        const bool live = (a.delay != nullptr || a.delay_tab != nullptr) && fl < a.n_frames;
+        const double tau = live ? frame_delay(a, p, (a.m_begin + fl) * (long long)N, N) : 0.0;
+        const double d = tau * a.fs / (double)N;
+        FrameR32& fi = finfo[f];
+        if (role == 0) {
+            fi.slot = (fl < a.n_store) ? fl / a.Kc : -1;
+            fi.k = (fl < a.n_store) ? fl % a.Kc : 0;
+            fi.delay = live ? 1 : 0;
             const double ph = a.nu * tau;
-            fi.phi0 = (float)(ph - floor(ph));
-            const double d = tau * a.fs / (double)N;
+            fi.phi0 = live ? (float)(ph - floor(ph)) : 0.0f;
             const float dh = __uint_as_float(__float_as_uint((float)d) & 0xFFFFF000u);
-            fi.d_hi = dh;
-            fi.d_lo = (float)(d - (double)dh);
-            fi.delay = 1;
-            float sn, cs;
-            const double s1 = d, s32 = 32.0 * d, wr = -(double)N * d;
-            sincospif(2.0f * (float)(s1 - rint(s1)), &sn, &cs);
-            fi.step1 = make_float2(cs, sn);
-            sincospif(2.0f * (float)(s32 - rint(s32)), &sn, &cs);
-            fi.step32 = make_float2(cs, sn);
-            sincospif(2.0f * (float)(wr - rint(wr)), &sn, &cs);
-            fi.wrap = make_float2(cs, sn);
+            fi.d_hi = live ? dh : 0.0f;
+            fi.d_lo = live ? (float)(d - (double)dh) : 0.0f;
+        } else if (role == 1 || role == 2 || role == 3) {
+            const double x = (role == 1) ? d : (role == 2 ? 32.0 * d : -(double)N * d);
+            float sn = 0.0f, cs = 1.0f;
+            if (live) sincospif(2.0f * (float)(x - rint(x)), &sn, &cs);
+            (role == 1 ? fi.step1 : (role == 2 ? fi.step32 : fi.wrap)) = make_float2(cs, sn);
         }
-        finfo[f] = fi;
     }
 
     // ---- pass 1: 32-point DFTs of the T decimated sub-sequences of each frame
@@ -592,10 +589,17 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
 #pragma unroll
         for (int r = 0; r < T; ++r) {
             const int k = j + 32 * r;   // natural-order bin
-            const int c = (k < N - N / 2) ? k + N / 2 : k - (N - N / 2);
+            // j < 32: for T >= 2 the bins past N/2 are exactly the outputs r >= T/2
+            const bool low = (T >= 2) ? (r < T / 2) : (k < N - N / 2);
+            const int c = low ? k + N / 2 : k - (N - N / 2);
             float2 y = v[r];
             if (fi.delay) {
-                y = c_mul(y, (k < N - N / 2) ? E : c_mul(E, fi.wrap));
+                if (T >= 2) {
+                    if (r == T / 2) E = c_mul(E, fi.wrap);   // u = k - N from here on
+                    y = c_mul(y, E);
+                } else {
+                    y = c_mul(y, low ? E : c_mul(E, fi.wrap));
+                }
                 E = c_mul(E, fi.step32);
             }
             const float gn = gain[c];

@@ -39,6 +39,10 @@ WORKLOAD = dict(name="full-array plain FX, 256 tiles, 8 s sub-observation, N=128
 SMALL = dict(WORKLOAD, name="full-array plain FX, 256 tiles, one 0.5 s integration, N=128, fscrunch 4",
              samples=640_000)
 METRIC = "real-time 256-tile coarse channels per B300"
+# Plan workspace of the timed forms: 48 GiB holds the operands of all 16 integrations of
+# the sub-observation at once (FP32: 43 GB), so the F-step and the X-step each run as one
+# launch over the whole call (B300 has 275 GB of HBM).
+WORKSPACE = 48 << 30
 
 # DRAM bytes (read + write) per integration slot of the dominant kernel, from an ncu
 # capture of the one-integration case (profiles/).  Reported only while the kernel's
@@ -532,12 +536,12 @@ def run_mine(args, world, rank, local):
         if form == "int8":
             # integer mode on the same voltages: no FFT (1.28 MHz channels), 1 s integrations
             desc = mw.PlanDesc(n_tiles=W["n_tiles"], fft_len=1, fine_avg=1, int_time_s=1.0 if W is WORKLOAD else 0.5,
-                               samples_per_call=W["samples"], precision=prec)
+                               samples_per_call=W["samples"], precision=prec, workspace_limit=WORKSPACE)
             ddelay = None
         else:
             desc = mw.PlanDesc(n_tiles=W["n_tiles"], fft_len=W["fft_len"], fine_avg=W["fine_avg"],
                                int_time_s=W["int_time_s"], samples_per_call=W["samples"], precision=prec,
-                               sky_freq_hz=W["sky_freq_hz"])
+                               sky_freq_hz=W["sky_freq_hz"], workspace_limit=WORKSPACE)
             ddelay = dev_delay
         plan = mw.mwax_plan_create_ex(desc)
         clocks = ClockSampler(local) if form == headline else None

@@ -7,6 +7,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
+#include <queue>
 #include <string>
 #include <vector>
 
@@ -213,6 +215,71 @@ namespace mwax {
 // (Re)build the X-step tile list and the runs of output channels.  run_len = output
 // channels per work item (0: chosen from the grid size), window = width of a tensor-core
 // tile's column window (128 or 256).  Drops cached item lists.
+// Ultrafine channels (with non-zero weight) that a run [j0, j1) of output channels
+// consumes: every group feeding one of them, shared boundary groups included.
+int run_bins(const mwax_plan& p, int j0, int j1)
+{
+    int bins = 0;
+    for (const Group& gr : p.h_groups) {
+        if (!((gr.ja >= j0 && gr.ja < j1) || (gr.jb >= j0 && gr.jb < j1))) continue;
+        for (int c = gr.c0; c < gr.c1; ++c) bins += p.h_gain[c] > 0.0f;
+    }
+    return bins;
+}
+
+// Run length of the CUDA-core X-step: short runs make more CTAs (a fuller last wave) but
+// recompute the boundary channels that neighbouring runs share.  Each candidate's CTAs
+// (cost = channels consumed, x 23/32 on diagonal tiles, + a fixed epilogue share) are
+// placed longest first on the resident CTA slots, as the sorted work list launches
+// them; the candidate whose launches finish first wins.
+int simt_run_len(const mwax_plan& p, const std::vector<int4>& tiles)
+{
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int resident = sms * simt_resident_ctas();
+    std::vector<long long> launch_slots;
+    for (long long w0 = 0; w0 < p.n_ints; w0 += p.slots)
+        for (int ch = 0; ch < p.chunks; ++ch) launch_slots.push_back(std::min(p.slots, p.n_ints - w0));
+    std::vector<int> cand;
+    for (int rl = 1; rl <= 8; ++rl) cand.push_back(rl);
+    for (int rl = 12; rl <= 32; rl += 4) cand.push_back(rl);
+    for (int rl = 48; rl < p.M; rl *= 2) cand.push_back(rl);
+    cand.push_back(p.M);
+    int best = p.M;
+    double best_t = 1e300;
+    for (int rl : cand) {
+        if (rl > p.M) continue;
+        std::vector<double> run_cost;
+        for (int j0 = 0; j0 < p.M; j0 += rl) run_cost.push_back(run_bins(p, j0, std::min(p.M, j0 + rl)) + 0.25);
+        const double ctas = (double)run_cost.size() * tiles.size() * launch_slots[0];
+        if (ctas > 400000.0 && rl < p.M) continue;   // far more CTAs than the GPU holds
+        double t = 0.0;
+        for (long long ns : launch_slots) {
+            std::vector<double> c;
+            for (long long sl = 0; sl < ns; ++sl)
+                for (double rc : run_cost)
+                    for (const int4& tl : tiles) c.push_back(rc * (tl.w ? 23.0 / 32.0 : 1.0));
+            std::sort(c.begin(), c.end(), std::greater<double>());
+            std::priority_queue<double, std::vector<double>, std::greater<double>> q;
+            for (int k = 0; k < resident; ++k) q.push(0.0);
+            double end = 0.0;
+            for (double w : c) {
+                const double f = q.top() + w;
+                q.pop();
+                q.push(f);
+                end = std::max(end, f);
+            }
+            t += end;
+        }
+        if (t < best_t * 0.999) {
+            best_t = t;
+            best = rl;
+        }
+    }
+    return best;
+}
+
 mwax_status configure_x(mwax_plan& p, int run_len_req, int window)
 {
     for (auto& it : p.item_lists) cudaFree(it.items);
@@ -241,8 +308,10 @@ mwax_status configure_x(mwax_plan& p, int run_len_req, int window)
     MWAX_CUDA(cudaMemcpy(p.tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice));
 
     // runs of output channels: by default enough work items for several per SM, at least
-    // 4 channels per run
+    // 4 channels per run (tensor cores); the CUDA-core path picks the run length whose
+    // longest-first schedule finishes first (simt_run_len)
     int run_len = run_len_req;
+    if (run_len <= 0 && !p.tensor_cores && p.prec != MWAX_INT8) run_len = simt_run_len(p, tiles);
     if (run_len <= 0) {
         const long long items_wo_runs = (long long)p.n_tiles * p.slots;
         const long long want_items = p.tensor_cores ? 6LL * 148 : 8LL * 148;
@@ -417,7 +486,10 @@ void plan_items(const mwax_plan& p, int job, long long nslots, long long klen, s
         }
         for (int t = 0; t < p.n_tiles; ++t) {
             const int4 tl = p.h_tiles[t];
-            const double cost = bins * nkb * tl.z * (tl.w ? 1.0 : 1.25) + 1.0;
+            // tensor cores: B window width, A rows outside it cost extra; CUDA cores: a
+            // diagonal tile skips 9 of its 32 register sub-blocks
+            const double f = p.tensor_cores ? (tl.w ? 1.0 : 1.25) : (tl.w ? 23.0 / 32.0 : 1.0);
+            const double cost = bins * nkb * tl.z * f + 1.0;
             for (long long sl = 0; sl < nslots; ++sl) out.push_back({cost, XItem{job, t, r, (int)sl}});
         }
     }
@@ -659,7 +731,11 @@ mwax_status enqueue_xstep_single(mwax_plan* p, const LaunchGroup& g, const XArgs
         L.jobs[0].op = (p->prec == MWAX_FP8) ? 1 : 0;
         MWAX_CUDA(timed(p, 2, s, [&] { return launch_xstep_tc(L, items, n_items, p->counter, p->status, s); }));
     } else {
-        MWAX_CUDA(timed(p, 2, s, [&] { return launch_xstep_simt(p->tmap, xa, p->n_tiles, p->n_runs, (int)g.nslots, s); }));
+        XItem* items = nullptr;
+        int n_items = 0;
+        mwax_status st = single_items(p, g.nslots, g.klen, &items, &n_items);
+        if (st != MWAX_OK) return st;
+        MWAX_CUDA(timed(p, 2, s, [&] { return launch_xstep_simt_items(p->tmap, xa, items, n_items, s); }));
     }
     return MWAX_OK;
 }

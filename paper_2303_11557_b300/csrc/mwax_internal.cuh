@@ -149,6 +149,10 @@ cudaError_t launch_weights(char* out, long long n_ints, long long int_stride, lo
                            long long K, int N, int bs, int n, const uint8_t* flags, int normalise, cudaStream_t s);
 cudaError_t launch_xstep_simt(const CUtensorMap& map, const XArgs& a, int n_tiles, int n_runs, int slots,
                               cudaStream_t s);
+// Same over a work list (tile, run, slot per CTA, in launch order).
+cudaError_t launch_xstep_simt_items(const CUtensorMap& map, const XArgs& a, const XItem* items, int n_items,
+                                    cudaStream_t s);
+int simt_resident_ctas();   // CTAs of the FP32 X-step resident per SM
 // FP32 operand planes for the CUDA-core X-step: 32 frames x 64 rows x both planes per box,
 // 128-byte swizzle.
 cudaError_t make_simt_tmap(CUtensorMap* map, const void* Y, long long Kpad, int n, long long planes);

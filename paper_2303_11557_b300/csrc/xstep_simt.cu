@@ -3,7 +3,11 @@
 // MWAX_ORDER output (Sec. 2.7) fused into the epilogue.
 //
 // CTA = one 64 x 64 tile of signal-path pairs (p rows, q columns; tiles on or above the
-// block diagonal only) x one run of output channels x one integration slot.  For every
+// block diagonal only) x one run of output channels x one integration slot, taken from a
+// work list sorted by estimated cost (longest first, so the short ones fill the tail).
+// On a diagonal tile a thread skips its register sub-blocks (i, j) with j < 2 i: their
+// rows ty + 16 i >= 16 i exceed their columns tx + 8 j <= 8 j + 7 for every thread, so
+// they hold only pairs below the diagonal (9 of the 32 complex accumulators).  For every
 // group of ultrafine channels feeding the run, the CTA forms
 //     C[p,q] = sum_{c in group} sum_k Y_p[k,c] conj(Y_q[k,c])
 // (the F-step has already weighted channel c by sqrt(w_c)) and adds coef * C into every
@@ -121,8 +125,9 @@ __device__ __forceinline__ void cmac(float xr, float xi, float yr, float yi, flo
 
 // The four frames of one 16-byte column chunk into the thread's partial.  oa / ob: byte
 // offsets of the thread's first A row (ty) and first B row (tx) at this column chunk
-// (swizzle applied); A rows step by 16 (2 KB), B rows by 8 (1 KB).
-template <bool first>
+// (swizzle applied); A rows step by 16 (2 KB), B rows by 8 (1 KB).  DIAG: a diagonal tile
+// (sub-blocks j < 2 i lie below the diagonal and are skipped; they stay 0).
+template <bool first, bool DIAG>
 __device__ __forceinline__ void column_chunk(const unsigned char* sa, const unsigned char* sb, uint32_t oa,
                                              uint32_t ob, float (&pre)[4][8], float (&pim)[4][8])
 {
@@ -142,6 +147,10 @@ __device__ __forceinline__ void column_chunk(const unsigned char* sa, const unsi
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
+            if (DIAG && j < 2 * i) {
+                if (first) pre[i][j] = pim[i][j] = 0.f;
+                continue;
+            }
             cmac<first>(ar[i].x, ai[i].x, br[j].x, bi[j].x, pre[i][j], pim[i][j]);
             cmac<false>(ar[i].y, ai[i].y, br[j].y, bi[j].y, pre[i][j], pim[i][j]);
             cmac<false>(ar[i].z, ai[i].z, br[j].z, bi[j].z, pre[i][j], pim[i][j]);
@@ -165,6 +174,10 @@ __device__ __forceinline__ void column_chunk(const unsigned char* sa, const unsi
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
+                if (DIAG && j < 2 * i) {
+                    if (first && h == 0) pre[i][j] = pim[i][j] = 0.f;
+                    continue;
+                }
                 if (h == 0)
                     cmac<first>(ar[i].x, ai[i].x, br[j].x, bi[j].x, pre[i][j], pim[i][j]);
                 else
@@ -175,8 +188,21 @@ __device__ __forceinline__ void column_chunk(const unsigned char* sa, const unsi
 #endif
 }
 
+// The 32 frames of one staged chunk into the thread's partials.
+template <bool DIAG>
+__device__ __forceinline__ void chunk_partials(const unsigned char* sa, const unsigned char* sb, int ty, int tx,
+                                               float (&pre)[4][8], float (&pim)[4][8])
+{
+    column_chunk<true, DIAG>(sa, sb, ty * 128 + ((ty & 7) << 4), tx * 128 + (tx << 4), pre, pim);
+#pragma unroll 1
+    for (int ck = 1; ck < KT / 4; ++ck)
+        column_chunk<false, DIAG>(sa, sb, ty * 128 + ((ck ^ (ty & 7)) << 4), tx * 128 + ((ck ^ tx) << 4), pre, pim);
+}
+
+// order: work list (tile, run, slot) indexed by blockIdx.x, or nullptr for a 3-D grid
+// (x = tile, y = run, z = slot).
 __global__ void __launch_bounds__(NTHREADS, 2)
-    xstep_simt_kernel(const __grid_constant__ CUtensorMap map, const XArgs a)
+    xstep_simt_kernel(const __grid_constant__ CUtensorMap map, const XArgs a, const XItem* __restrict__ order)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);   // swizzle atom
@@ -184,9 +210,15 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     unsigned char* ring_b = base + STAGES * TILE_BYTES;
     SimtBars& S = *reinterpret_cast<SimtBars*>(base + 2 * STAGES * TILE_BYTES);
 
-    const int4 tile = a.tiles[blockIdx.x];
-    const RunInfo run = a.runs[blockIdx.y];
-    const int slot = blockIdx.z;
+    int tile_i = blockIdx.x, run_i = blockIdx.y, slot = blockIdx.z;
+    if (order != nullptr) {
+        const XItem w = order[blockIdx.x];
+        tile_i = w.tile;
+        run_i = w.run;
+        slot = w.slot;
+    }
+    const int4 tile = a.tiles[tile_i];
+    const RunInfo run = a.runs[run_i];
     const int p0 = tile.x, q0 = tile.y;
     const bool diag = (p0 == q0);
     const int tid = threadIdx.x;
@@ -245,11 +277,10 @@ __global__ void __launch_bounds__(NTHREADS, 2)
                 const unsigned char* sa = a_ring + s * TILE_BYTES;
                 const unsigned char* sb = b_ring + s * TILE_BYTES;
                 float pre[4][8], pim[4][8];
-                column_chunk<true>(sa, sb, ty * 128 + ((ty & 7) << 4), tx * 128 + (tx << 4), pre, pim);
-#pragma unroll 1
-                for (int ck = 1; ck < KT / 4; ++ck)
-                    column_chunk<false>(sa, sb, ty * 128 + ((ck ^ (ty & 7)) << 4), tx * 128 + ((ck ^ tx) << 4), pre,
-                                        pim);
+                if (diag)
+                    chunk_partials<true>(sa, sb, ty, tx, pre, pim);
+                else
+                    chunk_partials<false>(sa, sb, ty, tx, pre, pim);
                 // Release the stage (every shared-memory read of it has returned: its values
                 // are used above); the last warp to release it copies the chunk STAGES ahead.
                 __syncwarp();
@@ -316,8 +347,7 @@ __global__ void __launch_bounds__(NTHREADS, 2)
 
 }  // namespace
 
-cudaError_t launch_xstep_simt(const CUtensorMap& map, const XArgs& a, int n_tiles, int n_runs, int slots,
-                              cudaStream_t s)
+cudaError_t simt_attributes()
 {
     static bool attr_done = false;
     if (!attr_done) {
@@ -326,9 +356,36 @@ cudaError_t launch_xstep_simt(const CUtensorMap& map, const XArgs& a, int n_tile
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
+    return cudaSuccess;
+}
+
+cudaError_t launch_xstep_simt(const CUtensorMap& map, const XArgs& a, int n_tiles, int n_runs, int slots,
+                              cudaStream_t s)
+{
+    cudaError_t e = simt_attributes();
+    if (e != cudaSuccess) return e;
     dim3 grid((unsigned)n_tiles, (unsigned)n_runs, (unsigned)slots);
-    xstep_simt_kernel<<<grid, NTHREADS, simt_smem_bytes(), s>>>(map, a);
+    xstep_simt_kernel<<<grid, NTHREADS, simt_smem_bytes(), s>>>(map, a, nullptr);
     return cudaGetLastError();
+}
+
+cudaError_t launch_xstep_simt_items(const CUtensorMap& map, const XArgs& a, const XItem* items, int n_items,
+                                    cudaStream_t s)
+{
+    cudaError_t e = simt_attributes();
+    if (e != cudaSuccess) return e;
+    xstep_simt_kernel<<<(unsigned)n_items, NTHREADS, simt_smem_bytes(), s>>>(map, a, items);
+    return cudaGetLastError();
+}
+
+int simt_resident_ctas()
+{
+    int n = 0;
+    if (simt_attributes() != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, xstep_simt_kernel, NTHREADS, simt_smem_bytes()) !=
+            cudaSuccess)
+        return 2;
+    return n > 0 ? n : 1;
 }
 
 }  // namespace mwax

@@ -710,14 +710,15 @@ mwax_status enqueue_xstep_single(mwax_plan* p, const LaunchGroup& g, const XArgs
 {
     XArgs xa = xa_in;
     if (p->prec == MWAX_INT8) {
-        // split each slot's samples into segments of whole 256-sample chunks so the grid
-        // covers the GPU several times over
-        const long long chunks256 = (g.klen + 255) / 256;
+        // split each slot's samples into segments of whole 512-sample chunks (the exact
+        // FP32 accumulation span of the integer X-step) so the grid covers the GPU
+        // several times over
+        const long long chunks512 = (g.klen + 511) / 512;
         const long long want =
             std::max<long long>(1, (4LL * 148 + p->n_tiles * g.nslots - 1) / (p->n_tiles * g.nslots));
-        const long long seg_chunks = std::max<long long>(1, (chunks256 + want - 1) / want);
-        xa.seg_frames = seg_chunks * 256;
-        const int nseg = (int)((chunks256 + seg_chunks - 1) / seg_chunks);
+        const long long seg_chunks = std::max<long long>(1, (chunks512 + want - 1) / want);
+        xa.seg_frames = seg_chunks * 512;
+        const int nseg = (int)((chunks512 + seg_chunks - 1) / seg_chunks);
         MWAX_CUDA(timed(p, 2, s, [&] { return launch_xstep_int8(p->tmap, xa, p->n_tiles, nseg, (int)g.nslots, s); }));
     } else if (p->tensor_cores) {
         XItem* items = nullptr;

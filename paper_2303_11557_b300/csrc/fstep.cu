@@ -405,10 +405,10 @@ __global__ void __launch_bounds__(kThreads) fstep_kernel(const FArgs a)
         fi.delay = 0;
         fi.phi0 = fi.d_hi = fi.d_lo = 0.0f;
         if ((a.delay != nullptr || a.delay_tab != nullptr) && fl < a.n_frames) {
-            const double tau = frame_delay(a, p, (a.m_begin + fl) * (long long)N, N);
+            const double tau = frame_delay(a, p, a.m_begin + fl, N);
             const double ph = a.nu * tau;
             fi.phi0 = (float)(ph - floor(ph));
-            const double d = tau * a.fs / (double)N;
+            const double d = tau * a.fs_over_n;
             const float dh = __uint_as_float(__float_as_uint((float)d) & 0xFFFFF000u);
             fi.d_hi = dh;
             fi.d_lo = (float)(d - (double)dh);
@@ -519,8 +519,8 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
         const int f = threadIdx.x % FB, role = threadIdx.x / FB;
         const long long fl = f0 + f;
         const bool live = (a.delay != nullptr || a.delay_tab != nullptr) && fl < a.n_frames;
-        const double tau = live ? frame_delay(a, p, (a.m_begin + fl) * (long long)N, N) : 0.0;
-        const double d = tau * a.fs / (double)N;
+        const double tau = live ? frame_delay(a, p, a.m_begin + fl, N) : 0.0;
+        const double d = tau * a.fs_over_n;
         FrameR32& fi = finfo[f];
         if (role == 0) {
             fi.slot = (fl < a.n_store) ? fl / a.Kc : -1;
@@ -567,9 +567,18 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
     const int f = threadIdx.x % FB;
     const int jb = (threadIdx.x / FB) * P::JPT;
     const FrameR32 fi = finfo[f];
-    // FP8 (FOUT_F16A): lanes sharing a butterfly set are FB consecutive frames
-    if (OUTK != FOUT_F16A && fi.slot < 0) return;
+    // FP16 / FP8 (FOUT_F16, FOUT_F16A): lanes sharing a butterfly set are FB consecutive
+    // frames and exchange values, so all of them stay to the end
+    if (OUTK == FOUT_F32 && fi.slot < 0) return;
     const unsigned lanes = (FB == 32) ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
+    // FP16: frames 2m and 2m+1 of one slot, at an even K index, share 4-byte half2 stores
+    // (the even lane writes both real parts, the odd lane both imaginary parts)
+    bool pair = false;
+    if (OUTK == FOUT_F16) {
+        const long long nslot = __shfl_xor_sync(lanes, fi.slot, 1), nk = __shfl_xor_sync(lanes, fi.k, 1);
+        const long long k_even = (f & 1) ? nk : fi.k, k_odd = (f & 1) ? fi.k : nk;
+        pair = fi.slot >= 0 && nslot == fi.slot && (k_even & 1) == 0 && k_odd == k_even + 1;
+    }
     const long long cs = 2LL * a.n * a.Kpad;
     const long long ps = (long long)a.n * a.Kpad;
     const long long base = (fi.slot * N * 2LL * a.n + p) * a.Kpad + fi.k;
@@ -620,6 +629,19 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
                 } else if (fi.slot >= 0 && g >= 0 && m > 0.0f) {
                     atomicMax(reinterpret_cast<int*>(a.amax + (fi.slot * a.n_groups + g) * (long long)a.n + p),
                               __float_as_int(m));
+                }
+            } else if (OUTK == FOUT_F16) {
+                __half* Y = static_cast<__half*>(a.Y);
+                const __half2 h = __floats2half2_rn(y.x * a.out_scale, y.y * a.out_scale);   // (re, im)
+                const unsigned mine = *reinterpret_cast<const unsigned*>(&h);
+                const unsigned other = __shfl_xor_sync(lanes, mine, 1);
+                if (pair) {
+                    // even lane: (re_2m, re_2m+1) at k; odd lane: (im_2m, im_2m+1) at k - 1
+                    const unsigned w = (f & 1) ? __byte_perm(other, mine, 0x7632) : __byte_perm(mine, other, 0x5410);
+                    *reinterpret_cast<unsigned*>(Y + base + c * cs + ((f & 1) ? ps - 1 : 0)) = w;
+                } else if (fi.slot >= 0) {
+                    Y[base + c * cs] = __low2half(h);
+                    Y[base + c * cs + ps] = __high2half(h);
                 }
             } else {
                 Store<N, OUTK>::run(a, base + c * cs, ps, y, fi.slot, c, p);
@@ -696,7 +718,7 @@ __global__ void __launch_bounds__(256) unpack_kernel(const FArgs a)
             v = make_float2((float)x.x, (float)x.y);
         }
         if ((a.delay != nullptr || a.delay_tab != nullptr) && fl < a.n_frames) {
-            const double tau = frame_delay(a, p, s, 1);
+            const double tau = frame_delay(a, p, s, 1);   // N = 1: frame = sample
             const double ph = a.nu * tau;
             float sn, cs;
             sincospif(2.0f * (float)(ph - floor(ph)), &sn, &cs);
@@ -871,8 +893,11 @@ bool fft_len_supported(int N)
     }
 }
 
-cudaError_t launch_fstep(int N, int out_kind, const FArgs& a, cudaStream_t s, int variant)
+cudaError_t launch_fstep(int N, int out_kind, const FArgs& a_in, cudaStream_t s, int variant)
 {
+    FArgs a = a_in;
+    a.frame_dt = (double)N / a.fs;
+    a.fs_over_n = a.fs / (double)N;
     switch (out_kind) {
         case FOUT_F32: return launch_kind<FOUT_F32>(N, a, s, variant);
         case FOUT_F16: return launch_kind<FOUT_F16>(N, a, s, variant);

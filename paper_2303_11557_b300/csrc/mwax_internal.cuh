@@ -65,20 +65,23 @@ struct FArgs {
     long long tab_steps;
     long long tab_step;        // samples per table entry
     const uint8_t* flags;      // [n_blocks][n] zeroing flags (nonzero: block holds no data), or nullptr
+    // set by launch_fstep from fs and N (so no kernel divides in FP64 per frame)
+    double frame_dt;           // N / fs: seconds per frame
+    double fs_over_n;          // fs / N: frames per second
 };
 
-// Delay (s) of path p for the frame of N samples that starts at absolute sample s0: the
-// FP64 polynomial at the frame centre t = (s0 / N + 1/2) N / Fs (Sec. 4.3), or the table
-// entry of the step that holds the frame centre (Sec. 2.4.1).
-__device__ __forceinline__ double frame_delay(const FArgs& a, int p, long long s0, int N)
+// Delay (s) of path p for frame m of the call (N samples from absolute sample m N): the
+// FP64 polynomial at the frame centre t = (m + 1/2) N / Fs (Sec. 4.3), or the table entry
+// of the step that holds the frame centre (Sec. 2.4.1).
+__device__ __forceinline__ double frame_delay(const FArgs& a, int p, long long m, int N)
 {
     if (a.delay_tab != nullptr) {
-        long long step = (2 * s0 + N) / (2 * a.tab_step);
+        long long step = (2 * m * N + N) / (2 * a.tab_step);
         if (step >= a.tab_steps) step = a.tab_steps - 1;
         return a.delay_tab[(long long)p * a.tab_steps + step];
     }
-    const double t = ((double)(s0 / N) + 0.5) * (double)N / a.fs;
-    return a.delay[3 * p] + t * (a.delay[3 * p + 1] + t * a.delay[3 * p + 2]);
+    const double t = ((double)m + 0.5) * a.frame_dt;
+    return fma(t, fma(t, a.delay[3 * p + 2], a.delay[3 * p + 1]), a.delay[3 * p]);
 }
 
 // True when the data block holding sample s0 of path p is flagged as zeroed (Sec. 2.4.2):
@@ -104,7 +107,7 @@ struct XArgs {
     const float* gain;     // [N]; channels with gain 0 are skipped
     const int4* tiles;     // (p0, q0, column count, A rows inside the B window) per tile
     float post_scale;      // multiplies every product (undoes the FP16 pre-scale)
-    long long seg_frames;  // integer mode: frames per K segment (a multiple of 256)
+    long long seg_frames;  // integer mode: frames per K segment (a multiple of 512)
     int first_store;       // 1: a channel's first group stores (output not yet written by an
                            //    earlier frame chunk of the same integration); 0: all add
     int* status;           // device status word (bounded waits)

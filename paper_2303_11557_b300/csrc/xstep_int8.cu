@@ -2,12 +2,12 @@
 // sums of the int8 voltages on the tcgen05 tensor cores.
 //
 // sm_103a has no integer tensor-core MMA, but every int8 value is exact in FP16 and every
-// product of two is exact in FP32.  The MMAs accumulate chunks of 256 samples in FP32
-// TMEM: a chunk's partial sums of (re re + im im) or (im re - re im) are bounded by
-// 256 * 2 * 128^2 = 2^23 < 2^24, so they are exact integers.  After each chunk the
-// epilogue converts them and adds them into int32 accumulators kept in the other half of
-// TMEM; every 200 chunks (51,200 samples: at most 200 * 2^23 < 2^31) the int32 sums are
-// added into the int64 output.  Result: bit-exact int64 visibilities.
+// product of two is exact in FP32.  The MMAs accumulate chunks of 512 samples in FP32
+// TMEM: every partial sum of (re re + im im) or (im re - re im) within a chunk is an
+// integer of magnitude at most 512 * 2 * 128^2 = 2^24, so it is exact.  After each chunk
+// the epilogue converts the sums and adds them into int32 accumulators kept in the other
+// half of TMEM; every 100 chunks (51,200 samples: at most 100 * 2^24 < 2^31) the int32
+// sums are added into the int64 output.  Result: bit-exact int64 visibilities.
 //
 // CTA = one 128 x 128 tile of path pairs x one segment of the slot's samples x one slot;
 // the segments' int64 sums are combined with 64-bit atomic adds into the zeroed output
@@ -27,8 +27,8 @@ constexpr int ROWB = 64;                      // 32 FP16 samples per operand row
 constexpr int KF = 32;                        // samples per stage
 constexpr int PLANE = TM * ROWB;              // 8 KB
 constexpr int STAGE_BYTES = 4 * PLANE;        // Br, Bi, Ar, Ai
-constexpr int CHUNK_STAGES = 8;               // 256 samples per exact FP32 chunk
-constexpr int FLUSH_CHUNKS = 200;             // 51,200 samples per int32 flush
+constexpr int CHUNK_STAGES = 16;              // 512 samples per exact FP32 chunk
+constexpr int FLUSH_CHUNKS = 100;             // 51,200 samples per int32 flush
 constexpr int NTHREADS = 320;
 constexpr int EPI_THREADS = 256;
 

@@ -82,6 +82,18 @@ def test_ragged_frames_odd_fscrunch_keep_dc(prec):
 
 
 @pytest.mark.parametrize("prec", FLOAT_PRECS)
+def test_odd_frames_per_integration(prec):
+    # 201 frames per integration: frame pairs straddle the integrations' boundary at odd K
+    # indices (the FP16 store pairs neighbouring frames only inside one slot at even K)
+    T, N, F, K = 5, 128, 4, 201
+    bs = K * N
+    volt, delay = workload(13, T, 2 * bs, block_samples=bs, delay="linear")
+    desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=K * N / synth.FS, samples_per_call=2 * bs,
+                       block_samples=bs, sky_freq_hz=synth.SKY_FREQ_HZ, precision=prec)
+    check(desc, volt, delay)
+
+
+@pytest.mark.parametrize("prec", FLOAT_PRECS)
 @pytest.mark.parametrize("N,F", [(16, 1), (32, 1), (64, 8), (128, 4), (256, 1), (512, 16), (640, 5), (1280, 10),
                                  (3200, 64), (6400, 50)])
 def test_fft_lengths(N, F, prec):

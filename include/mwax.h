@@ -149,6 +149,23 @@ mwax_status mwax_correlate(mwax_plan* plan, const int8_t* voltages, const double
 mwax_status mwax_correlate_host(mwax_plan* plan, const int8_t* voltages, const double* delay_poly, void* vis_out);
 
 /*
+ * Streaming form of mwax_correlate_host for consecutive sub-observations (the real-time
+ * loop of Sec. 2.3: data keep arriving while earlier data are correlated).  Enqueues the
+ * copies, the correlation and the copy back, and returns without waiting.  The plan keeps
+ * two device staging sets (voltages + output, allocated on first use) and alternates
+ * between them, so the voltages of call k + 1 stream in while call k is correlated; the
+ * correlations themselves run in call order on the plan's stream.
+ *   voltages, vis_out   host memory as for mwax_correlate_host; pinned (page-locked)
+ *                       buffers are needed for the copies to overlap.  The caller keeps
+ *                       voltages unchanged and does not read vis_out until
+ *                       mwax_plan_sync() returns;
+ *   delay_poly          as for mwax_correlate_host (copied when the call is enqueued).
+ * Errors found by the kernels are reported by mwax_plan_sync().  Not thread-safe per plan.
+ */
+mwax_status mwax_correlate_host_async(mwax_plan* plan, const int8_t* voltages, const double* delay_poly,
+                                      void* vis_out);
+
+/*
  * Extended call (Sec. 2.4, 4.1, 4.3): tabulated fractional delays and zeroing flags.
  *   voltages, vis_out   as for mwax_correlate (device, 16-byte aligned);
  *   delay_poly          as for mwax_correlate, or NULL;

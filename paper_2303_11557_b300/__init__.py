@@ -112,6 +112,7 @@ class PlanDesc:
 _lib = None
 SYMBOLS = ("mwax_plan_create", "mwax_plan_create_ex", "mwax_plan_get_info", "mwax_plan_output_bytes",
            "mwax_plan_input_bytes", "mwax_plan_set_stream", "mwax_correlate", "mwax_correlate_host",
+           "mwax_correlate_host_async",
            "mwax_plan_sync", "mwax_plan_destroy", "mwax_last_error", "mwax_version", "mwax_plan_enable_timing",
            "mwax_plan_stage_times", "mwax_plan_autotune", "mwax_plan_set_tuning", "mwax_plan_get_tuning",
            "mwax_batch_create", "mwax_batch_set_stream", "mwax_batch_set_graphs", "mwax_batch_correlate",
@@ -153,6 +154,8 @@ def load_library(path: str | None = None):
     lib.mwax_correlate.restype = st
     lib.mwax_correlate_host.argtypes = [vp, vp, vp, vp]
     lib.mwax_correlate_host.restype = st
+    lib.mwax_correlate_host_async.argtypes = [vp, vp, vp, vp]
+    lib.mwax_correlate_host_async.restype = st
     lib.mwax_plan_sync.argtypes = [vp]
     lib.mwax_plan_sync.restype = st
     lib.mwax_plan_destroy.argtypes = [vp]
@@ -323,6 +326,14 @@ def mwax_correlate_host(plan: Plan, voltages, delay_poly, vis_out):
     """Host buffers (numpy or CPU tensors, pinned for full bandwidth); synchronous."""
     dptr, keep = _delay_arg(delay_poly, plan, False)
     _check(load_library().mwax_correlate_host(plan.handle, _ptr(voltages), dptr, _ptr(vis_out)))
+    return keep
+
+
+def mwax_correlate_host_async(plan: Plan, voltages, delay_poly, vis_out):
+    """Streaming host call (pinned buffers): enqueue and return; the next call's upload
+    overlaps this one's correlation.  Keep the buffers until mwax_plan_sync()."""
+    dptr, keep = _delay_arg(delay_poly, plan, False)
+    _check(load_library().mwax_correlate_host_async(plan.handle, _ptr(voltages), dptr, _ptr(vis_out)))
     return keep
 
 

@@ -128,12 +128,18 @@ void free_plan(mwax_plan* p)
     cudaFree(p->tiles);
     cudaFree(p->status);
     cudaFree(p->counter);
-    cudaFree(p->dvolt);
-    cudaFree(p->dout);
+    for (auto& h : p->hbuf) {
+        cudaFree(h.dvolt);
+        cudaFree(h.dout);
+        for (auto e : h.copied) cudaEventDestroy(e);
+        if (h.free_ev) cudaEventDestroy(h.free_ev);
+        if (h.done_ev) cudaEventDestroy(h.done_ev);
+        if (h.out_ev) cudaEventDestroy(h.out_ev);
+    }
+    if (p->back_stream) cudaStreamDestroy(p->back_stream);
     cudaFree(p->d_table);
     cudaFree(p->d_flags);
     for (auto& it : p->item_lists) cudaFree(it.items);
-    for (auto e : p->events) cudaEventDestroy(e);
     for (auto e : p->ev_pool) cudaEventDestroy(e);
     for (auto& u : p->ev_used) {
         cudaEventDestroy(u.second.first);
@@ -567,13 +573,33 @@ cudaError_t timed(mwax_plan* p, int stage, cudaStream_t s, F&& launch)
     return e;
 }
 
+// Launch groups of one call.  max_slots > 0 (host-input path) splits each group of
+// whole integrations into groups of at most max_slots, so the F- and X-steps of the
+// first integrations run while the later ones are still being copied in.
+std::vector<LaunchGroup> call_groups(const mwax_plan* p, long long max_slots)
+{
+    std::vector<LaunchGroup> v = plan_groups(p);
+    if (max_slots <= 0 || p->chunks != 1) return v;
+    std::vector<LaunchGroup> out;
+    for (const LaunchGroup& g : v)
+        for (long long s0 = 0; s0 < g.nslots; s0 += max_slots) {
+            LaunchGroup h = g;
+            h.w0 = g.w0 + s0;
+            h.nslots = std::min(max_slots, g.nslots - s0);
+            h.nframes = h.nslots * p->K;
+            h.m_begin = h.w0 * p->K;
+            out.push_back(h);
+        }
+    return out;
+}
+
 mwax_status enqueue(mwax_plan* p, const int8_t* volt, bool have_delay, char* out, cudaEvent_t* wait_events,
-                    long long events_per_block)
+                    long long events_per_block, long long max_slots = 0)
 {
     cudaStream_t s = p->stream;
     mwax_status st = enqueue_init(p, out, s);
     if (st != MWAX_OK) return st;
-    for (const LaunchGroup& g : plan_groups(p)) {
+    for (const LaunchGroup& g : call_groups(p, max_slots)) {
         if (wait_events) {
             // host-input path: wait for the copy of the last block this launch reads
             const long long last_sample = (g.m_begin + g.nframes) * p->N - 1;
@@ -592,6 +618,57 @@ mwax_status load_delay(mwax_plan* p, const double* delay_poly)
 {
     if (!delay_poly) return MWAX_OK;
     MWAX_CUDA(cudaMemcpyAsync(p->delay, delay_poly, sizeof(double) * 3 * p->n, cudaMemcpyDefault, p->stream));
+    return MWAX_OK;
+}
+
+// One host-memory call on staging set b: the voltages go to the device in 16 chunks on the
+// copy stream (after the set's previous call has read it), each launch group of the
+// correlation waits for the chunks it reads, and the result is copied back on the
+// read-back stream (the set's next correlation waits until that copy is done).  split: launch groups of a quarter of the plan's (the synchronous call, whose
+// own upload is all there is to overlap with); otherwise the plan's groups (streaming:
+// the next call's upload overlaps this correlation).  Returns once all is enqueued.
+mwax_status host_call(mwax_plan* p, const int8_t* volt, const double* delay_poly, void* vis_out, int b, bool split)
+{
+    if (!p || !volt || !vis_out) return fail(MWAX_EINVAL, "NULL plan, voltages or vis_out");
+    if (p->prec == MWAX_INT8 && delay_poly) return fail(MWAX_EINVAL, "MWAX_INT8 takes no delay correction");
+    MWAX_CUDA(cudaSetDevice(p->device));
+    const size_t out_bytes = (size_t)p->n_ints * p->int_stride;
+    const long long blocks_per_copy = std::max<long long>(1, p->n_blocks / 16);
+    const long long n_copies = (p->n_blocks + blocks_per_copy - 1) / blocks_per_copy;
+    if (!p->copy_stream) MWAX_CUDA(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+    if (!p->back_stream) MWAX_CUDA(cudaStreamCreateWithFlags(&p->back_stream, cudaStreamNonBlocking));
+    mwax_plan::HostBuf& h = p->hbuf[b];
+    if (!h.dvolt) {
+        MWAX_CUDA(cudaMalloc(&h.dvolt, p->input_bytes));
+        MWAX_CUDA(cudaMalloc(&h.dout, out_bytes));
+        h.copied.resize(n_copies);
+        for (auto& e : h.copied) MWAX_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        for (cudaEvent_t* e : {&h.free_ev, &h.done_ev, &h.out_ev}) {
+            MWAX_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+            MWAX_CUDA(cudaEventRecord(*e, p->stream));
+        }
+    }
+    MWAX_CUDA(cudaStreamWaitEvent(p->copy_stream, h.free_ev, 0));
+    MWAX_CUDA(cudaStreamWaitEvent(p->stream, h.out_ev, 0));   // the set's last output was read back
+    const size_t block_bytes = (size_t)p->n * p->bs * 2;
+    for (long long c = 0; c < n_copies; ++c) {
+        const long long b0 = c * blocks_per_copy, b1 = std::min(p->n_blocks, b0 + blocks_per_copy);
+        MWAX_CUDA(cudaMemcpyAsync(h.dvolt + b0 * block_bytes, volt + b0 * block_bytes, (b1 - b0) * block_bytes,
+                                  cudaMemcpyHostToDevice, p->copy_stream));
+        MWAX_CUDA(cudaEventRecord(h.copied[c], p->copy_stream));
+    }
+    mwax_status st = load_delay(p, delay_poly);
+    if (st != MWAX_OK) return st;
+    // split: a quarter of the launch group per launch, so compute follows the copies
+    // while each X-step still fills the GPU several times over
+    const long long host_slots = split ? std::max<long long>(1, (p->slots + 3) / 4) : 0;
+    st = enqueue(p, h.dvolt, delay_poly != nullptr, h.dout, h.copied.data(), blocks_per_copy, host_slots);
+    if (st != MWAX_OK) return st;
+    MWAX_CUDA(cudaEventRecord(h.free_ev, p->stream));
+    MWAX_CUDA(cudaEventRecord(h.done_ev, p->stream));
+    MWAX_CUDA(cudaStreamWaitEvent(p->back_stream, h.done_ev, 0));
+    MWAX_CUDA(cudaMemcpyAsync(vis_out, h.dout, out_bytes, cudaMemcpyDeviceToHost, p->back_stream));
+    MWAX_CUDA(cudaEventRecord(h.out_ev, p->back_stream));
     return MWAX_OK;
 }
 
@@ -890,35 +967,18 @@ mwax_status mwax_plan_set_passband(mwax_plan* p, const float* gain)
 
 mwax_status mwax_correlate_host(mwax_plan* p, const int8_t* volt, const double* delay_poly, void* vis_out)
 {
-    if (!p || !volt || !vis_out) return fail(MWAX_EINVAL, "NULL plan, voltages or vis_out");
-    if (p->prec == MWAX_INT8 && delay_poly) return fail(MWAX_EINVAL, "MWAX_INT8 takes no delay correction");
-    MWAX_CUDA(cudaSetDevice(p->device));
-    const size_t out_bytes = (size_t)p->n_ints * p->int_stride;
-    const long long blocks_per_copy = std::max<long long>(1, p->n_blocks / 16);
-    const long long n_copies = (p->n_blocks + blocks_per_copy - 1) / blocks_per_copy;
-    if (!p->dvolt) {
-        MWAX_CUDA(cudaMalloc(&p->dvolt, p->input_bytes));
-        MWAX_CUDA(cudaMalloc(&p->dout, out_bytes));
-        MWAX_CUDA(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
-        p->events.resize(n_copies + 1);
-        for (auto& e : p->events) MWAX_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    }
-    // the copy stream must not run ahead of earlier work on the plan stream
-    MWAX_CUDA(cudaEventRecord(p->events[n_copies], p->stream));
-    MWAX_CUDA(cudaStreamWaitEvent(p->copy_stream, p->events[n_copies], 0));
-    const size_t block_bytes = (size_t)p->n * p->bs * 2;
-    for (long long c = 0; c < n_copies; ++c) {
-        const long long b0 = c * blocks_per_copy, b1 = std::min(p->n_blocks, b0 + blocks_per_copy);
-        MWAX_CUDA(cudaMemcpyAsync(p->dvolt + b0 * block_bytes, volt + b0 * block_bytes, (b1 - b0) * block_bytes,
-                                  cudaMemcpyHostToDevice, p->copy_stream));
-        MWAX_CUDA(cudaEventRecord(p->events[c], p->copy_stream));
-    }
-    mwax_status st = load_delay(p, delay_poly);
+    mwax_status st = host_call(p, volt, delay_poly, vis_out, 0, true);
     if (st != MWAX_OK) return st;
-    st = enqueue(p, p->dvolt, delay_poly != nullptr, p->dout, p->events.data(), blocks_per_copy);
-    if (st != MWAX_OK) return st;
-    MWAX_CUDA(cudaMemcpyAsync(vis_out, p->dout, out_bytes, cudaMemcpyDeviceToHost, p->stream));
     return mwax_plan_sync(p);
+}
+
+mwax_status mwax_correlate_host_async(mwax_plan* p, const int8_t* volt, const double* delay_poly, void* vis_out)
+{
+    if (!p) return fail(MWAX_EINVAL, "plan is NULL");
+    const int b = p->hnext;
+    mwax_status st = host_call(p, volt, delay_poly, vis_out, b, false);
+    if (st == MWAX_OK) p->hnext ^= 1;
+    return st;
 }
 
 mwax_status mwax_plan_sync(mwax_plan* p)
@@ -926,6 +986,7 @@ mwax_status mwax_plan_sync(mwax_plan* p)
     if (!p) return fail(MWAX_EINVAL, "plan is NULL");
     MWAX_CUDA(cudaSetDevice(p->device));
     MWAX_CUDA(cudaStreamSynchronize(p->stream));
+    if (p->back_stream) MWAX_CUDA(cudaStreamSynchronize(p->back_stream));
     int st = 0;
     MWAX_CUDA(cudaMemcpy(&st, p->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (st != 0) {

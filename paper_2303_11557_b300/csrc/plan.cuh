@@ -75,11 +75,20 @@ struct mwax_plan {
     };
     std::vector<ItemList> item_lists;   // per (slot count, frames) of a launch
 
-    // host-input path
-    int8_t* dvolt = nullptr;
-    char* dout = nullptr;
-    cudaStream_t copy_stream = nullptr;
-    std::vector<cudaEvent_t> events;
+    // host-input path: two device staging sets used alternately by the streaming call
+    // (the synchronous one always takes set 0)
+    struct HostBuf {
+        int8_t* dvolt = nullptr;
+        char* dout = nullptr;
+        std::vector<cudaEvent_t> copied;   // per copy chunk of the voltages
+        cudaEvent_t free_ev = nullptr;     // the last call that used the set has read it
+        cudaEvent_t done_ev = nullptr;     // its correlation is complete (output written)
+        cudaEvent_t out_ev = nullptr;      // its output has been copied back
+    };
+    HostBuf hbuf[2];
+    int hnext = 0;
+    cudaStream_t copy_stream = nullptr;   // uploads
+    cudaStream_t back_stream = nullptr;   // read-backs
 
     cudaStream_t stream = nullptr;
     int device = 0;

@@ -155,3 +155,24 @@ def test_host_path_matches_device_path():
     mw.mwax_correlate_host(plan, host_in, np.ascontiguousarray(delay), host_out)
     vis_h, w_h = mw.split_output(plan, host_out.numpy())
     assert np.array_equal(vis_h, vis_d) and np.array_equal(w_h, w_d)
+
+
+def test_host_async_two_in_flight():
+    # streaming host calls: three sub-observations enqueued back to back (the staging sets
+    # alternate, the third reuses the first's), each equal to the device path on its input
+    T, N, F = 8, 128, 4
+    desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=0.25, samples_per_call=640_000,
+                       sky_freq_hz=synth.SKY_FREQ_HZ)
+    inputs = [workload(20 + k, T, 640_000, delay="linear") for k in range(3)]
+    want = [run_gpu(desc, v, d)[0] for v, d in inputs]
+    plan = mw.mwax_plan_create_ex(desc)
+    mw.mwax_plan_set_stream(plan)
+    hins = [torch.from_numpy(v.reshape(-1)).pin_memory() for v, _ in inputs]
+    houts = [torch.zeros(plan.output_bytes, dtype=torch.uint8).pin_memory() for _ in inputs]
+    keep = [mw.mwax_correlate_host_async(plan, hins[k], np.ascontiguousarray(inputs[k][1]), houts[k])
+            for k in range(3)]
+    mw.mwax_plan_sync(plan)
+    for k in range(3):
+        vis, _ = mw.split_output(plan, houts[k].numpy())
+        assert np.array_equal(vis, want[k])
+    del keep

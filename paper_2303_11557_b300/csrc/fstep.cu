@@ -567,18 +567,9 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
     const int f = threadIdx.x % FB;
     const int jb = (threadIdx.x / FB) * P::JPT;
     const FrameR32 fi = finfo[f];
-    // FP16 / FP8 (FOUT_F16, FOUT_F16A): lanes sharing a butterfly set are FB consecutive
-    // frames and exchange values, so all of them stay to the end
-    if (OUTK == FOUT_F32 && fi.slot < 0) return;
+    // FP8 (FOUT_F16A): lanes sharing a butterfly set are FB consecutive frames
+    if (OUTK != FOUT_F16A && fi.slot < 0) return;
     const unsigned lanes = (FB == 32) ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
-    // FP16: frames 2m and 2m+1 of one slot, at an even K index, share 4-byte half2 stores
-    // (the even lane writes both real parts, the odd lane both imaginary parts)
-    bool pair = false;
-    if (OUTK == FOUT_F16) {
-        const long long nslot = __shfl_xor_sync(lanes, fi.slot, 1), nk = __shfl_xor_sync(lanes, fi.k, 1);
-        const long long k_even = (f & 1) ? nk : fi.k, k_odd = (f & 1) ? fi.k : nk;
-        pair = fi.slot >= 0 && nslot == fi.slot && (k_even & 1) == 0 && k_odd == k_even + 1;
-    }
     const long long cs = 2LL * a.n * a.Kpad;
     const long long ps = (long long)a.n * a.Kpad;
     const long long base = (fi.slot * N * 2LL * a.n + p) * a.Kpad + fi.k;
@@ -629,19 +620,6 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
                 } else if (fi.slot >= 0 && g >= 0 && m > 0.0f) {
                     atomicMax(reinterpret_cast<int*>(a.amax + (fi.slot * a.n_groups + g) * (long long)a.n + p),
                               __float_as_int(m));
-                }
-            } else if (OUTK == FOUT_F16) {
-                __half* Y = static_cast<__half*>(a.Y);
-                const __half2 h = __floats2half2_rn(y.x * a.out_scale, y.y * a.out_scale);   // (re, im)
-                const unsigned mine = *reinterpret_cast<const unsigned*>(&h);
-                const unsigned other = __shfl_xor_sync(lanes, mine, 1);
-                if (pair) {
-                    // even lane: (re_2m, re_2m+1) at k; odd lane: (im_2m, im_2m+1) at k - 1
-                    const unsigned w = (f & 1) ? __byte_perm(other, mine, 0x7632) : __byte_perm(mine, other, 0x5410);
-                    *reinterpret_cast<unsigned*>(Y + base + c * cs + ((f & 1) ? ps - 1 : 0)) = w;
-                } else if (fi.slot >= 0) {
-                    Y[base + c * cs] = __low2half(h);
-                    Y[base + c * cs + ps] = __high2half(h);
                 }
             } else {
                 Store<N, OUTK>::run(a, base + c * cs, ps, y, fi.slot, c, p);
@@ -802,33 +780,40 @@ __global__ void __launch_bounds__(256) quantise_e4m3_kernel(const __half* __rest
                                                             __nv_fp8_storage_t* __restrict__ Y8,
                                                             const float* __restrict__ amax,
                                                             const int* __restrict__ chan_group, int n_groups, int N,
-                                                            int n, long long Kpad)
+                                                            int n, long long Kpad, long long rows)
 {
-    const long long row = blockIdx.x;
-    const int p = (int)(row % n);
-    const long long sc = row / (2LL * n);           // slot * N + c
-    const int c = (int)(sc % N);
-    const long long slot = sc / N;
-    const int g = chan_group[c];
-    if (g < 0) return;                              // zero-weight channel: never read
-    const float am = amax[(slot * n_groups + g) * (long long)n + p];
-    const float inv = am > 0.0f ? 448.0f / am : 0.0f;
-    const uint4* src = reinterpret_cast<const uint4*>(Y16 + row * Kpad);
-    uint2* dst = reinterpret_cast<uint2*>(Y8 + row * Kpad);
-    for (long long k8 = threadIdx.x; k8 < Kpad / 8; k8 += blockDim.x) {
-        const uint4 h = __ldg(src + k8);
-        const __half2* hp = reinterpret_cast<const __half2*>(&h);
-        uint32_t lo = 0, hi = 0;
+    // One warp per operand row (grid-stride over rows); a lane converts 16 FP16 values
+    // (two 16-byte loads) into one 16-byte store of e4m3 codes per step.
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long row = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += warps) {
+        const int p = (int)(row % n);
+        const long long sc = row / (2LL * n);       // slot * N + c
+        const int c = (int)(sc % N);
+        const long long slot = sc / N;
+        const int g = __ldg(&chan_group[c]);
+        if (g < 0) continue;                        // zero-weight channel: never read
+        const float am = __ldg(&amax[(slot * n_groups + g) * (long long)n + p]);
+        const float inv = am > 0.0f ? 448.0f / am : 0.0f;
+        const uint4* src = reinterpret_cast<const uint4*>(Y16 + row * Kpad);
+        uint4* dst = reinterpret_cast<uint4*>(Y8 + row * Kpad);
+        for (long long k16 = lane; k16 < Kpad / 16; k16 += 32) {
+            const uint4 h[2] = {__ldg(src + 2 * k16), __ldg(src + 2 * k16 + 1)};
+            const __half2* hp = reinterpret_cast<const __half2*>(h);
+            uint32_t w[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const float2 v = __half22float2(hp[e]);
-            const uint32_t q0 = __nv_cvt_float_to_fp8(v.x * inv, __NV_SATFINITE, __NV_E4M3);
-            const uint32_t q1 = __nv_cvt_float_to_fp8(v.y * inv, __NV_SATFINITE, __NV_E4M3);
-            const uint32_t pair = q0 | (q1 << 8);
-            if (e < 2) lo |= pair << (16 * e);
-            else hi |= pair << (16 * (e - 2));
+            for (int e = 0; e < 4; ++e) {
+                float2 v0 = __half22float2(hp[2 * e]), v1 = __half22float2(hp[2 * e + 1]);
+                v0.x *= inv;
+                v0.y *= inv;
+                v1.x *= inv;
+                v1.y *= inv;
+                const uint32_t q0 = __nv_cvt_float2_to_fp8x2(v0, __NV_SATFINITE, __NV_E4M3);
+                const uint32_t q1 = __nv_cvt_float2_to_fp8x2(v1, __NV_SATFINITE, __NV_E4M3);
+                w[e] = q0 | (q1 << 16);
+            }
+            dst[k16] = make_uint4(w[0], w[1], w[2], w[3]);
         }
-        dst[k8] = make_uint2(lo, hi);
     }
 }
 
@@ -913,8 +898,8 @@ cudaError_t launch_quantise_e4m3(const __half* Y16, __nv_fp8_storage_t* Y8, cons
     const long long rows = slots * (long long)N * 2 * n;
     if (rows <= 0) return cudaSuccess;
     if (rows > 0x7fffffffLL) return cudaErrorInvalidValue;
-    quantise_e4m3_kernel<<<(unsigned)rows, Kpad >= 2048 ? 256 : 128, 0, s>>>(Y16, Y8, amax, chan_group, n_groups, N,
-                                                                               n, Kpad);
+    const long long blocks = std::min<long long>((rows + 7) / 8, 148LL * 16);   // 8 rows (warps) per block
+    quantise_e4m3_kernel<<<(unsigned)blocks, 256, 0, s>>>(Y16, Y8, amax, chan_group, n_groups, N, n, Kpad, rows);
     return cudaGetLastError();
 }
 

@@ -188,8 +188,14 @@ MWAX_SCHED(256, 32, 16, 16, 1, 1)
 MWAX_SCHED(512, 16, 8, 8, 8, 1)
 MWAX_SCHED(640, 16, 16, 8, 5, 1)
 MWAX_SCHED(1280, 8, 16, 16, 5, 1)
-MWAX_SCHED(3200, 4, 16, 8, 5, 5)
-MWAX_SCHED(6400, 2, 16, 16, 5, 5)
+#ifndef MWAX_FB3200
+#define MWAX_FB3200 2
+#endif
+#ifndef MWAX_FB6400
+#define MWAX_FB6400 2
+#endif
+MWAX_SCHED(3200, MWAX_FB3200, 16, 8, 5, 5)
+MWAX_SCHED(6400, MWAX_FB6400, 16, 16, 5, 5)
 #undef MWAX_SCHED
 
 template <int N, int P>
@@ -270,6 +276,18 @@ __device__ __forceinline__ float2 delay_phasor(const FrameInfo& fi, int u)
     return make_float2(c, s);
 }
 
+// Twiddle e^{-2 pi i k / N}: straight from the full table when it sits in shared memory
+// (N <= 1280); above that from two small shared tables, T1[k mod 128] T2[k / 128]
+// (T1[a] = e^{-2 pi i a / N}, T2[b] = e^{-2 pi i 128 b / N}), one complex multiply
+// instead of an uncached load from a table larger than what L1 has left.
+template <int N>
+__device__ __forceinline__ float2 twiddle(const float2* tw, int k)
+{
+    static_assert(N <= 1280 || N % 128 == 0, "two-level twiddles need N % 128 == 0");
+    if (N <= 1280) return tw[k];
+    return c_mul(tw[k & 127], tw[128 + (k >> 7)]);
+}
+
 template <int N, int OUTK, int P>
 struct Pass {
     static constexpr int R = Sched<N>::radix[P];
@@ -301,7 +319,7 @@ struct Pass {
             }
             if (NS > 1) {
 #pragma unroll
-                for (int r = 1; r < R; ++r) v[r] = c_mul(v[r], tw[(j % NS) * r * (N / (NS * R))]);
+                for (int r = 1; r < R; ++r) v[r] = c_mul(v[r], twiddle<N>(tw, (j % NS) * r * (N / (NS * R))));
             }
             Dft<R>::run(v);
             if (!LAST) {
@@ -354,7 +372,9 @@ struct PassChain<N, OUTK, P, true> {
     }
 };
 
-// Twiddle and gain tables live in shared memory for N <= 1280 (global, L1-cached, above).
+// Twiddle and gain tables live in shared memory for N <= 1280; above that the twiddles
+// are two small tables there (128 + N / 128 entries) and the gains stay in global memory
+// (read once per output, coalesced).
 template <int N>
 __host__ __device__ constexpr bool tables_in_smem()
 {
@@ -365,7 +385,7 @@ template <int N>
 __host__ __device__ constexpr size_t fstep_smem()
 {
     return 2 * sizeof(float2) * (size_t)Sched<N>::fb * (N + 1) + sizeof(FrameInfo) * Sched<N>::fb +
-           (tables_in_smem<N>() ? (sizeof(float2) + sizeof(float)) * N : 0);
+           (tables_in_smem<N>() ? (sizeof(float2) + sizeof(float)) * N : sizeof(float2) * (128 + N / 128));
 }
 
 template <int N, int OUTK>
@@ -390,6 +410,11 @@ __global__ void __launch_bounds__(kThreads) fstep_kernel(const FArgs a)
         }
         tw = tws;
         gain = gns;
+    } else {
+        float2* tws = reinterpret_cast<float2*>(finfo + FB);
+        for (int i = threadIdx.x; i < 128 + N / 128; i += kThreads)
+            tws[i] = __ldg(&a.tw[i < 128 ? i : 128 * (i - 128)]);
+        tw = tws;
     }
 
     const int p = blockIdx.y;

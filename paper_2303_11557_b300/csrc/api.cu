@@ -482,23 +482,27 @@ void plan_items(const mwax_plan& p, int job, long long nslots, long long klen, s
 {
     const int KF = (p.prec == MWAX_FP8) ? 64 : 32;
     const double nkb = (double)((klen + KF - 1) / KF);
+    std::vector<int> bins(p.n_runs, 0);
     for (int r = 0; r < p.n_runs; ++r) {
         const RunInfo& run = p.h_runs[r];
-        int bins = 0;
         for (int g = run.g0; g < run.g1; ++g) {
             const Group& gr = p.h_groups[g];
             if (!((gr.ja >= run.j0 && gr.ja < run.j1) || (gr.jb >= run.j0 && gr.jb < run.j1))) continue;
-            for (int c = gr.c0; c < gr.c1; ++c) bins += p.h_gain[c] > 0.0f;
-        }
-        for (int t = 0; t < p.n_tiles; ++t) {
-            const int4 tl = p.h_tiles[t];
-            // tensor cores: B window width, A rows outside it cost extra; CUDA cores: a
-            // diagonal tile skips 9 of its 32 register sub-blocks
-            const double f = p.tensor_cores ? (tl.w ? 1.0 : 1.25) : (tl.w ? 23.0 / 32.0 : 1.0);
-            const double cost = bins * nkb * tl.z * f + 1.0;
-            for (long long sl = 0; sl < nslots; ++sl) out.push_back({cost, XItem{job, t, r, (int)sl}});
+            for (int c = gr.c0; c < gr.c1; ++c) bins[r] += p.h_gain[c] > 0.0f;
         }
     }
+    // slot-major, then run, then tile: after the (stable) sort by cost, items of equal cost
+    // that run side by side read the same integration's channels, which then stay in L2
+    for (long long sl = 0; sl < nslots; ++sl)
+        for (int r = 0; r < p.n_runs; ++r)
+            for (int t = 0; t < p.n_tiles; ++t) {
+                const int4 tl = p.h_tiles[t];
+                // tensor cores: B window width, A rows outside it cost extra; CUDA cores: a
+                // diagonal tile skips 9 of its 32 register sub-blocks
+                const double f = p.tensor_cores ? (tl.w ? 1.0 : 1.25) : (tl.w ? 23.0 / 32.0 : 1.0);
+                const double cost = bins[r] * nkb * tl.z * f + 1.0;
+                out.push_back({cost, XItem{job, t, r, (int)sl}});
+            }
 }
 
 // Items in decreasing estimated cost: claimed in this order, the big ones start first.

@@ -242,7 +242,7 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-# ---------------------------------------------------------------- configs 3 and 4
+# ------------------------------------------ 24-channel batch and real-time serving
 F_CHOICES = {32: [1], 128: [1, 4], 1280: [10, 40], 6400: [50, 200]}
 
 
@@ -264,7 +264,7 @@ def mixed_channels(seed: int, n: int = 24, int8_share: float = 0.0):
 
 
 def channel_volt(torch, dev_base, T):
-    """Voltages of a T-tile channel: the resident config-1 bytes viewed (128 tiles: the
+    """Voltages of a T-tile channel: the resident 256-tile 8 s voltage bytes viewed (128 tiles: the
     first half; 256: all; 512: two copies) as [160 blocks][2T paths][64000][2]."""
     need = 160 * 2 * T * 64_000 * 2
     if need <= dev_base.numel():
@@ -273,7 +273,7 @@ def channel_volt(torch, dev_base, T):
 
 
 def run_batch24(mw, torch, dev_base, args):
-    """Config 3: 24 coarse channels of mixed shapes, one batch call per 8 s sub-observation
+    """24 coarse channels of mixed shapes, one batch call per 8 s sub-observation
     (FP16 X-engine in one persistent launch per round, autotuned, CUDA-graph replayed)."""
     chans = mixed_channels(0x4D57415B)
     plans, vols, outs = [], {}, []
@@ -322,11 +322,11 @@ def run_batch24(mw, torch, dev_base, args):
             "channels_realtime": 24 * SUBOBS_S / (ms * 1e-3), "x_tflops_alg": flops / (ms * 1e-3) / 1e12,
             "tunings": {f"T{k[0]} N{k[1]} F{k[2]} t{k[3]}": repr(v) for k, v in tuned.items()},
             "mix": [f"T{c['T']}/N{c['N']}/F{c['F']}/{c['t']}s" for c in chans],
-            "input": "config-1 voltage bytes re-tiled per tile count (every channel computed in full)"}
+            "input": "the 256-tile 8 s voltage bytes re-tiled per tile count (every channel computed in full)"}
 
 
 def run_serve(mw, torch, host_base, args, periods: int = 2):
-    """Config 4: 24 coarse channels each delivering an 8 s sub-observation every 8 s
+    """Real-time serving: 24 coarse channels each delivering an 8 s sub-observation every 8 s
     (seeded offsets within the period), FP16 or integer mode per request (80/20), host
     pinned voltages; the server admits by HBM footprint; deadline = 8 s."""
     chans = mixed_channels(0x4D57415C, int8_share=0.2)
@@ -376,7 +376,7 @@ def run_serve(mw, torch, host_base, args, periods: int = 2):
     srv.close()
     done = st["completed"] - warm
     return {"workload": f"24 coarse channels x {periods} sub-observations of 8 s at wall-clock rate, tiles "
-                        "{128,256,512}, mixed N/F/int as config 3, 20 % integer mode, host pinned voltages",
+                        "{128,256,512}, mixed N/F/int as the 24-channel batch, 20 % integer mode, host pinned voltages",
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
             "deadline_ms": 1e3 * SUBOBS_S, "deadline_misses": st["deadline_misses"], "completed": done,
             "sustained_channels": done * SUBOBS_S / wall, "wall_s": wall,
@@ -637,7 +637,7 @@ def run_mine(args, world, rank, local):
     if not args.no_ext and W is WORKLOAD:
         ext = run_extensions(mw, torch, W, dev_volt, delay, args)
 
-    # configs 3 and 4: batched mixed channels, real-time serving
+    # 24 batched channels of mixed shapes, then real-time serving
     batch = serve = None
     if not args.no_batch and W is WORKLOAD:
         plan.close()
@@ -692,7 +692,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "fp8", "int8"],
-                    help="headline precision (config 1 is FP32); the other forms are timed beside it")
+                    help="headline precision (the full-array plain form is FP32); the other forms are timed beside it")
     ap.add_argument("--no-forms", action="store_true", help="time the headline precision only")
     ap.add_argument("--no-batch", action="store_true", help="skip the 24-channel batched measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the real-time serving measurement")

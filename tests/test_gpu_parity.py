@@ -51,7 +51,7 @@ def check(desc, volt, delay, tol=None):
 
 
 @pytest.mark.parametrize("prec", FLOAT_PRECS)
-def test_config0(prec):
+def test_16_tiles_0p4s_no_averaging(prec):
     # 16 tiles x 2 pols, 0.4 s at 1.28 MS/s, 128-point FFT, no averaging, fixed 0-50 ns delays
     T, N, F, t_int = 16, 128, 1, 0.4
     volt, delay = workload(0x4D574158, T, 512_000)

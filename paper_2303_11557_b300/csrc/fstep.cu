@@ -169,10 +169,11 @@ struct DftIf<1> {
 // Radix schedule per FFT length (applied in this order).
 template <int N>
 struct Sched;
-#define MWAX_SCHED(NN, FBV, ...)                                                  \
+#define MWAX_SCHED(NN, FBV, NTV, ...)                                             \
     template <>                                                                   \
     struct Sched<NN> {                                                            \
         static constexpr int fb = FBV;                                            \
+        static constexpr int nt = NTV;                                            \
         static constexpr int radix[4] = {__VA_ARGS__};                            \
         static constexpr int passes = sizeof(radix) / sizeof(int) - count1(radix); \
     };
@@ -180,22 +181,42 @@ __host__ __device__ constexpr int count1(const int (&r)[4])
 {
     return (r[0] == 1) + (r[1] == 1) + (r[2] == 1) + (r[3] == 1);
 }
-MWAX_SCHED(16, 32, 16, 1, 1, 1)
-MWAX_SCHED(32, 32, 8, 4, 1, 1)
-MWAX_SCHED(64, 32, 8, 8, 1, 1)
-MWAX_SCHED(128, 32, 16, 8, 1, 1)
-MWAX_SCHED(256, 32, 16, 16, 1, 1)
-MWAX_SCHED(512, 16, 8, 8, 8, 1)
-MWAX_SCHED(640, 16, 16, 8, 5, 1)
-MWAX_SCHED(1280, 8, 16, 16, 5, 1)
+// (N, frames per CTA, threads per CTA, radices).  Above N = 512 the frames and threads are
+// chosen so that two ping-pong buffers of fb frames still leave 16 warps resident per SM.
+#ifndef MWAX_FB640
+#define MWAX_FB640 16
+#endif
+#ifndef MWAX_NT640
+#define MWAX_NT640 512
+#endif
+#ifndef MWAX_FB1280
+#define MWAX_FB1280 8
+#endif
+#ifndef MWAX_NT1280
+#define MWAX_NT1280 512
+#endif
 #ifndef MWAX_FB3200
 #define MWAX_FB3200 2
+#endif
+#ifndef MWAX_NT3200
+#define MWAX_NT3200 256
 #endif
 #ifndef MWAX_FB6400
 #define MWAX_FB6400 2
 #endif
-MWAX_SCHED(3200, MWAX_FB3200, 16, 8, 5, 5)
-MWAX_SCHED(6400, MWAX_FB6400, 16, 16, 5, 5)
+#ifndef MWAX_NT6400
+#define MWAX_NT6400 512
+#endif
+MWAX_SCHED(16, 32, 256, 16, 1, 1, 1)
+MWAX_SCHED(32, 32, 256, 8, 4, 1, 1)
+MWAX_SCHED(64, 32, 256, 8, 8, 1, 1)
+MWAX_SCHED(128, 32, 256, 16, 8, 1, 1)
+MWAX_SCHED(256, 32, 256, 16, 16, 1, 1)
+MWAX_SCHED(512, 16, 256, 8, 8, 8, 1)
+MWAX_SCHED(640, MWAX_FB640, MWAX_NT640, 16, 8, 5, 1)
+MWAX_SCHED(1280, MWAX_FB1280, MWAX_NT1280, 16, 16, 5, 1)
+MWAX_SCHED(3200, MWAX_FB3200, MWAX_NT3200, 16, 8, 5, 5)
+MWAX_SCHED(6400, MWAX_FB6400, MWAX_NT6400, 16, 16, 5, 5)
 #undef MWAX_SCHED
 
 template <int N, int P>
@@ -207,7 +228,6 @@ struct PassNs<N, 0> {
     static constexpr int value = 1;
 };
 
-constexpr int kThreads = 256;
 
 // Per-frame data shared by the CTA.
 struct FrameInfo {
@@ -305,7 +325,7 @@ struct Pass {
     {
         float2* in = (P % 2 == 0) ? buf1 : buf0;   // pass 0 reads the staging area in buf1
         float2* out = (P % 2 == 0) ? buf0 : buf1;
-        for (int idx = threadIdx.x; idx < FB * NB; idx += kThreads) {
+        for (int idx = threadIdx.x; idx < FB * NB; idx += Sched<N>::nt) {
             const int f = idx % FB, j = idx / FB;
             float2 v[R];
 #pragma unroll
@@ -389,7 +409,7 @@ __host__ __device__ constexpr size_t fstep_smem()
 }
 
 template <int N, int OUTK>
-__global__ void __launch_bounds__(kThreads) fstep_kernel(const FArgs a)
+__global__ void __launch_bounds__(Sched<N>::nt) fstep_kernel(const FArgs a)
 {
     constexpr int FB = Sched<N>::fb;
     constexpr int ROW = N + 1;
@@ -404,7 +424,7 @@ __global__ void __launch_bounds__(kThreads) fstep_kernel(const FArgs a)
     if (tables_in_smem<N>()) {
         float2* tws = reinterpret_cast<float2*>(finfo + FB);
         float* gns = reinterpret_cast<float*>(tws + N);
-        for (int i = threadIdx.x; i < N; i += kThreads) {
+        for (int i = threadIdx.x; i < N; i += Sched<N>::nt) {
             tws[i] = __ldg(&a.tw[i]);
             gns[i] = __ldg(&a.gain[i]);
         }
@@ -412,7 +432,7 @@ __global__ void __launch_bounds__(kThreads) fstep_kernel(const FArgs a)
         gain = gns;
     } else {
         float2* tws = reinterpret_cast<float2*>(finfo + FB);
-        for (int i = threadIdx.x; i < 128 + N / 128; i += kThreads)
+        for (int i = threadIdx.x; i < 128 + N / 128; i += Sched<N>::nt)
             tws[i] = __ldg(&a.tw[i < 128 ? i : 128 * (i - 128)]);
         tw = tws;
     }
@@ -451,7 +471,7 @@ __global__ void __launch_bounds__(kThreads) fstep_kernel(const FArgs a)
 
     // Stage the frames' int8 samples (2N bytes per frame, 16-byte loads).
     constexpr int CH = 2 * N / 16;   // 16-byte chunks per frame
-    for (int i = threadIdx.x; i < FB * CH; i += kThreads) {
+    for (int i = threadIdx.x; i < FB * CH; i += Sched<N>::nt) {
         const int f = i / CH, ch = i % CH;
         const long long fl = f0 + f;
         int4 w = make_int4(0, 0, 0, 0);
@@ -745,7 +765,7 @@ cudaError_t launch_n(const FArgs& a, cudaStream_t s)
         attr_done = true;
     }
     dim3 grid((unsigned)((a.n_store + Sched<N>::fb - 1) / Sched<N>::fb), (unsigned)a.n);
-    fstep_kernel<N, OUTK><<<grid, kThreads, smem, s>>>(a);
+    fstep_kernel<N, OUTK><<<grid, Sched<N>::nt, smem, s>>>(a);
     return cudaGetLastError();
 }
 

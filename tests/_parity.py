@@ -43,3 +43,40 @@ def oracle_desc(T, N, F, int_time_s, n_samples, block_samples=64_000, sky=synth.
     K = int(round(int_time_s * synth.FS)) // N
     return oracle.Desc(n_tiles=T, fft_len=N, fine_avg=F, int_frames=K, n_samples=n_samples,
                        block_samples=block_samples, sky_freq_hz=sky, dc_exclude=0 if keep_dc else 1)
+
+
+def baseline_index(T, i, j):
+    return i * (2 * T - i + 1) // 2 + (j - i)
+
+
+def sample_requests(seed, T, ints, M, per_int):
+    """Random (integration, baseline, channel, pol) entries, plus the parallel-pol autos
+    (same integration and channel) that the parity metric of each one divides by.
+    Returns (requests int64 [R, 4] with the random entries first, their number, and the
+    tile pair (i, j) of each random entry)."""
+    rng = np.random.default_rng(seed)
+    req = []
+    for w in ints:
+        for _ in range(per_int):
+            i = int(rng.integers(0, T))
+            j = int(rng.integers(i, T))
+            req.append((w, baseline_index(T, i, j), int(rng.integers(0, M)), int(rng.integers(0, 4)), i, j))
+    autos = set()
+    for w, _, c, pol, i, j in req:
+        autos.add((w, baseline_index(T, i, i), c, 3 * (pol >> 1)))
+        autos.add((w, baseline_index(T, j, j), c, 3 * (pol & 1)))
+    main = [r[:4] for r in req]
+    return np.array(main + sorted(autos), dtype=np.int64), len(main), [(r[4], r[5]) for r in req]
+
+
+def sampled_error(got, want, req, n_main, tiles, T):
+    """The parity metric on sampled outputs (autos taken from the oracle's samples)."""
+    look = {tuple(r): k for k, r in enumerate(req.tolist())}
+    err = []
+    for k in range(n_main):
+        w, _, c, pol = req[k].tolist()
+        i, j = tiles[k]
+        ap = abs(want[look[(w, baseline_index(T, i, i), c, 3 * (pol >> 1))]].real)
+        aq = abs(want[look[(w, baseline_index(T, j, j), c, 3 * (pol & 1))]].real)
+        err.append(abs(got[k] - want[k]) / np.sqrt(ap * aq))
+    return np.array(err)

@@ -233,17 +233,22 @@ int run_bins(const mwax_plan& p, int j0, int j1)
     return bins;
 }
 
-// Run length of the CUDA-core X-step: short runs make more CTAs (a fuller last wave) but
-// recompute the boundary channels that neighbouring runs share.  Each candidate's CTAs
-// (cost = channels consumed, x 23/32 on diagonal tiles, + a fixed epilogue share) are
-// placed longest first on the resident CTA slots, as the sorted work list launches
-// them; the candidate whose launches finish first wins.
-int simt_run_len(const mwax_plan& p, const std::vector<int4>& tiles)
+// Run length of the X-step: short runs make more work items (a fuller last wave) but
+// recompute the boundary channels that neighbouring runs share.  Each candidate's items
+// (cost = channels consumed x the tile's relative cost, + a fixed epilogue share) are
+// placed longest first on the resident CTA slots (CUDA cores: the sorted work list as
+// launched; tensor cores: one persistent CTA per SM claiming the sorted list); the
+// candidate whose launches finish first wins.
+int model_run_len(const mwax_plan& p, const std::vector<int4>& tiles)
 {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int resident = sms * simt_resident_ctas();
+    const int resident = p.tensor_cores ? sms : sms * simt_resident_ctas();
+    // relative cost of a tile, as in plan_items
+    auto tile_cost = [&](const int4& tl) {
+        return p.tensor_cores ? tl.z / 256.0 * (tl.w ? 1.0 : 1.25) : (tl.w ? 23.0 / 32.0 : 1.0);
+    };
     std::vector<long long> launch_slots;
     for (long long w0 = 0; w0 < p.n_ints; w0 += p.slots)
         for (int ch = 0; ch < p.chunks; ++ch) launch_slots.push_back(std::min(p.slots, p.n_ints - w0));
@@ -265,7 +270,7 @@ int simt_run_len(const mwax_plan& p, const std::vector<int4>& tiles)
             std::vector<double> c;
             for (long long sl = 0; sl < ns; ++sl)
                 for (double rc : run_cost)
-                    for (const int4& tl : tiles) c.push_back(rc * (tl.w ? 23.0 / 32.0 : 1.0));
+                    for (const int4& tl : tiles) c.push_back(rc * tile_cost(tl));
             std::sort(c.begin(), c.end(), std::greater<double>());
             std::priority_queue<double, std::vector<double>, std::greater<double>> q;
             for (int k = 0; k < resident; ++k) q.push(0.0);
@@ -313,11 +318,10 @@ mwax_status configure_x(mwax_plan& p, int run_len_req, int window)
     MWAX_CUDA(cudaMalloc(&p.tiles, sizeof(int4) * tiles.size()));
     MWAX_CUDA(cudaMemcpy(p.tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice));
 
-    // runs of output channels: by default enough work items for several per SM, at least
-    // 4 channels per run (tensor cores); the CUDA-core path picks the run length whose
-    // longest-first schedule finishes first (simt_run_len)
+    // runs of output channels: by default the run length whose longest-first schedule
+    // finishes first (model_run_len); the integer mode has one output channel
     int run_len = run_len_req;
-    if (run_len <= 0 && !p.tensor_cores && p.prec != MWAX_INT8) run_len = simt_run_len(p, tiles);
+    if (run_len <= 0 && p.prec != MWAX_INT8) run_len = model_run_len(p, tiles);
     if (run_len <= 0) {
         const long long items_wo_runs = (long long)p.n_tiles * p.slots;
         const long long want_items = p.tensor_cores ? 6LL * 148 : 8LL * 148;

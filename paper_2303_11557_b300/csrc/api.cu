@@ -745,14 +745,14 @@ mwax_status enqueue_fstep(mwax_plan* p, const LaunchGroup& g, const int8_t* volt
     fa.tab_steps = p->cur_steps;
     fa.tab_step = p->cur_step;
     fa.flags = p->cur_flags;
-    fa.chan_group = p->chan_group;
-    fa.n_groups = p->n_groups;
-    fa.amax = p->amax;
     if (p->prec == MWAX_FP8) {
-        // FP16 operands with the per-path-per-group max magnitude, then e4m3
-        MWAX_CUDA(cudaMemsetAsync(p->amax, 0, p->amax_bytes, s));
+        // FP16 operands, then per path and channel group the max magnitude, then e4m3
         fa.Y = p->Y16;
-        MWAX_CUDA(timed(p, 1, s, [&] { return launch_fstep(p->N, FOUT_F16A, fa, s, p->fvariant); }));
+        MWAX_CUDA(timed(p, 1, s, [&] { return launch_fstep(p->N, FOUT_F16, fa, s, p->fvariant); }));
+        MWAX_CUDA(timed(p, 1, s, [&] {
+            return launch_amax_e4m3(static_cast<const __half*>(p->Y16), p->amax, p->chan_group, p->groups,
+                                    p->n_groups, g.nslots, p->N, p->n, p->Kpad, g.klen, s);
+        }));
         MWAX_CUDA(timed(p, 1, s, [&] {
             return launch_quantise_e4m3(static_cast<const __half*>(p->Y16), static_cast<__nv_fp8_storage_t*>(p->Y),
                                         p->amax, p->chan_group, p->n_groups, g.nslots, p->N, p->n, p->Kpad, s);

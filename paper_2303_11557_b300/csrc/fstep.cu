@@ -244,28 +244,18 @@ struct FrameInfo {
 template <int N, int OUTK>
 struct Store {
     // Write one corrected spectral value: real plane at element `at`, imaginary plane at
-    // `at + plane_stride` of the operand buffer.  FOUT_F16A also raises
-    // amax[slot][group(c)][p] (per point here; the radix-32 kernel reduces across frames).
+    // `at + plane_stride` of the operand buffer (FP32, or FP16 pre-scaled by out_scale).
     __device__ __forceinline__ static void run(const FArgs& a, long long at, long long plane_stride, float2 v,
-                                               long long slot, int c, int p)
+                                               long long /*slot*/, int /*c*/, int /*p*/)
     {
         if (OUTK == FOUT_F32) {
             float* Y = static_cast<float*>(a.Y);
             Y[at] = v.x;
             Y[at + plane_stride] = v.y;
-        } else if (OUTK == FOUT_F16) {
+        } else {
             __half* Y = static_cast<__half*>(a.Y);
             Y[at] = __float2half_rn(v.x * a.out_scale);
             Y[at + plane_stride] = __float2half_rn(v.y * a.out_scale);
-        } else {
-            __half* Y = static_cast<__half*>(a.Y);
-            const __half hr = __float2half_rn(v.x * a.out_scale), hi = __float2half_rn(v.y * a.out_scale);
-            Y[at] = hr;
-            Y[at + plane_stride] = hi;
-            const int g = a.chan_group[c];
-            const float m = fmaxf(fabsf(__half2float(hr)), fabsf(__half2float(hi)));
-            if (g >= 0 && m > 0.0f)
-                atomicMax(reinterpret_cast<int*>(a.amax + (slot * a.n_groups + g) * (long long)a.n + p), __float_as_int(m));
         }
     }
 };
@@ -526,7 +516,7 @@ template <int N>
 __host__ __device__ constexpr size_t r32_smem()
 {
     return sizeof(float2) * (size_t)R32<N>::FB * R32<N>::ROW + sizeof(FrameR32) * R32<N>::FB +
-           (sizeof(float2) + sizeof(float) + sizeof(int) + sizeof(unsigned)) * N;
+           (sizeof(float2) + sizeof(float)) * N;
 }
 
 template <int N, int OUTK>
@@ -539,24 +529,14 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
     FrameR32* finfo = reinterpret_cast<FrameR32*>(buf + FB * ROW);
     float2* tw = reinterpret_cast<float2*>(finfo + FB);
     float* gain = reinterpret_cast<float*>(tw + N);
-    int* cgroup = reinterpret_cast<int*>(gain + N);            // FP8: group of channel c
-    unsigned* gmax = reinterpret_cast<unsigned*>(cgroup + N);  // FP8: per-group max (float bits)
 
     const int p = blockIdx.y;
     const long long f0 = (long long)blockIdx.x * FB;
 
-    // FP8: when all of the CTA's frames lie in one slot, the per-group maxima are gathered
-    // in shared memory (warp reduction, then one shared atomic) and flushed at the end
-    const long long slot_first = (f0 < a.n_store) ? f0 / a.Kc : -1;
-    const bool one_slot = slot_first >= 0 && (min(f0 + FB, a.n_store) - 1) / a.Kc == slot_first;
 
     for (int i = threadIdx.x; i < N; i += NT) {
         tw[i] = __ldg(&a.tw[i]);
         gain[i] = __ldg(&a.gain[i]);
-        if (OUTK == FOUT_F16A) {
-            cgroup[i] = __ldg(&a.chan_group[i]);
-            gmax[i] = 0u;
-        }
     }
     // Per-frame delay terms (Sec. 4.3), four roles per frame spread over the CTA's threads
     // so that no warp carries all of the FP64 work into the barrier after pass 1.
@@ -612,9 +592,7 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
     const int f = threadIdx.x % FB;
     const int jb = (threadIdx.x / FB) * P::JPT;
     const FrameR32 fi = finfo[f];
-    // FP8 (FOUT_F16A): lanes sharing a butterfly set are FB consecutive frames
-    if (OUTK != FOUT_F16A && fi.slot < 0) return;
-    const unsigned lanes = (FB == 32) ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
+    if (fi.slot < 0) return;
     const long long cs = 2LL * a.n * a.Kpad;
     const long long ps = (long long)a.n * a.Kpad;
     const long long base = (fi.slot * N * 2LL * a.n + p) * a.Kpad + fi.k;
@@ -649,35 +627,9 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
             }
             const float gn = gain[c];
             y = make_float2(y.x * gn, y.y * gn);
-            if (OUTK == FOUT_F16A) {
-                const int g = cgroup[c];
-                float m = 0.0f;
-                if (fi.slot >= 0) {
-                    __half* Y = static_cast<__half*>(a.Y);
-                    const __half hr = __float2half_rn(y.x * a.out_scale), hi = __float2half_rn(y.y * a.out_scale);
-                    Y[base + c * cs] = hr;
-                    Y[base + c * cs + ps] = hi;
-                    m = fmaxf(fabsf(__half2float(hr)), fabsf(__half2float(hi)));
-                }
-                if (one_slot) {
-                    const unsigned mb = __reduce_max_sync(lanes, __float_as_uint(m));   // m >= 0: bits order as values
-                    if (f == 0 && g >= 0 && mb != 0u) atomicMax(gmax + g, mb);
-                } else if (fi.slot >= 0 && g >= 0 && m > 0.0f) {
-                    atomicMax(reinterpret_cast<int*>(a.amax + (fi.slot * a.n_groups + g) * (long long)a.n + p),
-                              __float_as_int(m));
-                }
-            } else {
-                Store<N, OUTK>::run(a, base + c * cs, ps, y, fi.slot, c, p);
-            }
+            Store<N, OUTK>::run(a, base + c * cs, ps, y, fi.slot, c, p);
         }
         if (fi.delay) Ej = c_mul(Ej, fi.step1);
-    }
-    if (OUTK == FOUT_F16A && one_slot) {
-        __syncthreads();
-        for (int g = threadIdx.x; g < a.n_groups; g += NT)
-            if (gmax[g] != 0u)
-                atomicMax(reinterpret_cast<unsigned*>(a.amax + (slot_first * a.n_groups + g) * (long long)a.n + p),
-                          gmax[g]);
     }
 }
 
@@ -931,9 +883,63 @@ cudaError_t launch_fstep(int N, int out_kind, const FArgs& a_in, cudaStream_t s,
     switch (out_kind) {
         case FOUT_F32: return launch_kind<FOUT_F32>(N, a, s, variant);
         case FOUT_F16: return launch_kind<FOUT_F16>(N, a, s, variant);
-        case FOUT_F16A: return launch_kind<FOUT_F16A>(N, a, s, variant);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// FP8 form, after an FP16 F-step: per (slot, channel group g, path p) one warp reads the
+// FP16 operand rows of the group's channels (both planes, 16-byte loads) and stores the
+// largest magnitude over the slot's kvalid frames in amax[slot][g][p] (the e4m3 scale is
+// amax / 448): the same maxima as gathering them inside the F-step.
+__global__ void __launch_bounds__(256) amax_e4m3_kernel(const __half* __restrict__ Y16, float* __restrict__ amax,
+                                                        const int* __restrict__ chan_group,
+                                                        const Group* __restrict__ groups, int n_groups, int N, int n,
+                                                        long long Kpad, long long kvalid, long long slots)
+{
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long tasks = slots * n_groups * (long long)n;
+    for (long long t = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < tasks; t += warps) {
+        const int p = (int)(t % n);
+        const int g = (int)((t / n) % n_groups);
+        const long long slot = t / ((long long)n * n_groups);
+        const Group gr = groups[g];
+        __half2 m2 = __float2half2_rn(0.0f);
+        for (int c = gr.c0; c < gr.c1; ++c) {
+            if (__ldg(&chan_group[c]) != g) continue;
+            for (int plane = 0; plane < 2; ++plane) {
+                const uint4* row = reinterpret_cast<const uint4*>(Y16 + (((slot * N + c) * 2 + plane) * n + p) * Kpad);
+                for (long long k8 = lane; 8 * k8 < kvalid; k8 += 32) {
+                    const uint4 h = __ldg(row + k8);
+                    const __half2* hp = reinterpret_cast<const __half2*>(&h);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        __half2 v = __habs2(hp[e]);
+                        // frames past kvalid were not written by the F-step: leave them out
+                        const long long f0 = 8 * k8 + 2 * e;
+                        if (f0 + 1 >= kvalid) v = (f0 >= kvalid) ? __float2half2_rn(0.0f)
+                                                                : __halves2half2(__low2half(v), __float2half(0.0f));
+                        m2 = __hmax2(m2, v);
+                    }
+                }
+            }
+        }
+        float m = fmaxf(__low2float(m2), __high2float(m2));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) amax[(slot * n_groups + g) * (long long)n + p] = m;
+    }
+}
+
+cudaError_t launch_amax_e4m3(const __half* Y16, float* amax, const int* chan_group, const Group* groups, int n_groups,
+                             long long slots, int N, int n, long long Kpad, long long kvalid, cudaStream_t s)
+{
+    const long long tasks = slots * n_groups * (long long)n;
+    if (tasks <= 0) return cudaSuccess;
+    const long long blocks = std::min<long long>((tasks + 7) / 8, 148LL * 16);   // 8 tasks (warps) per block
+    amax_e4m3_kernel<<<(unsigned)blocks, 256, 0, s>>>(Y16, amax, chan_group, groups, n_groups, N, n, Kpad, kvalid,
+                                                      slots);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_quantise_e4m3(const __half* Y16, __nv_fp8_storage_t* Y8, const float* amax,

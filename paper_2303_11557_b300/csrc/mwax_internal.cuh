@@ -15,10 +15,8 @@ constexpr double kFs = 1280000.0;        // coarse-channel sample rate (Sec. 2.5
 constexpr int kDefaultBlock = 64000;     // samples per path per 50 ms data block (Sec. 2.5)
 constexpr int kKAlign = 128;             // frames per operand row are padded to this
 
-// Output-type selector of the F-step.
-// FOUT_F16A: FP16 operands plus the FP8 per-path-per-group max magnitude of the stored
-// FP16 values (the e4m3 quantisation then runs as a separate bandwidth-bound pass).
-enum FOut : int { FOUT_F32 = 0, FOUT_F16 = 1, FOUT_F16A = 2 };
+// Output-type selector of the F-step (the FP8 form quantises the FP16 output afterwards).
+enum FOut : int { FOUT_F32 = 0, FOUT_F16 = 1 };
 
 // Channel averaging (Sec. 2.6) is split in two: the F-step multiplies ultrafine channel
 // c by gain[c] = sqrt(w_c) (w_c = 1, 1/2 for the end bins of an even fscrunch, 0 for an
@@ -45,10 +43,6 @@ struct FArgs {
     const int8_t* volt;   // [blk][n][bs][2]
     const double* delay;  // [n][3] or nullptr
     void* Y;              // operands [slot][N][2][n][Kpad]
-    float* amax;          // FP8: [slot][group][n] max |re|, |im| over the slot's frames and the
-                          //      group's channels (atomically raised by the amax pass)
-    const int* chan_group;   // FP8: [N] group of each ultrafine channel (-1: none)
-    int n_groups;
     const float2* tw;     // e^{-2 pi i k / N}, k < N
     const float* gain;    // [N] sqrt of each ultrafine channel's averaging weight
     long long m_begin;
@@ -144,6 +138,10 @@ __host__ __device__ __forceinline__ float e4m3_scale(float amax) { return amax >
 cudaError_t launch_quantise_e4m3(const __half* Y16, __nv_fp8_storage_t* Y8, const float* amax,
                                  const int* chan_group, int n_groups, long long slots, int N, int n, long long Kpad,
                                  cudaStream_t s);
+// FP8 form after an FP16 F-step: per (slot, group, path) the max magnitude of the FP16
+// values over frames [0, kvalid) into amax (then launch_quantise_e4m3).
+cudaError_t launch_amax_e4m3(const __half* Y16, float* amax, const int* chan_group, const Group* groups, int n_groups,
+                             long long slots, int N, int n, long long Kpad, long long kvalid, cudaStream_t s);
 cudaError_t launch_init_output(char* out, long long n_ints, long long vis_set_bytes, long long weights_bytes,
                                cudaStream_t s);
 // Occupancy weights from zeroing flags (Sec. 4.1) over each integration's weights table;

@@ -596,6 +596,15 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
     const long long cs = 2LL * a.n * a.Kpad;
     const long long ps = (long long)a.n * a.Kpad;
     const long long base = (fi.slot * N * 2LL * a.n + p) * a.Kpad + fi.k;
+    // output r of butterfly j goes to channel c_r(j) = c_r(jb) + (j - jb): one element offset
+    // per r, advanced by a channel stride per butterfly
+    long long at[T];
+#pragma unroll
+    for (int r = 0; r < T; ++r) {
+        const int k = jb + 32 * r;
+        const bool low = (T >= 2) ? (r < T / 2) : (k < N - N / 2);
+        at[r] = base + (long long)(low ? k + N / 2 : k - (N - N / 2)) * cs;
+    }
     float2 Ej = make_float2(1.0f, 0.0f);
     if (fi.delay) Ej = delay_phasor_u(fi.phi0, fi.d_hi, fi.d_lo, jb);
 #pragma unroll 2
@@ -627,7 +636,8 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
             }
             const float gn = gain[c];
             y = make_float2(y.x * gn, y.y * gn);
-            Store<N, OUTK>::run(a, base + c * cs, ps, y, fi.slot, c, p);
+            Store<N, OUTK>::run(a, at[r], ps, y, fi.slot, c, p);
+            at[r] += cs;
         }
         if (fi.delay) Ej = c_mul(Ej, fi.step1);
     }

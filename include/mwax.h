@@ -411,7 +411,8 @@ void mwax_beam_destroy(mwax_beamformer* bf);
 mwax_status mwax_correlate_noalloc(const mwax_plan_desc* desc, const int8_t* voltages, const double* delay_poly,
                                    void* vis_out, void* cuda_stream);
 
-/* Free the plan and its device workspace (waits for its stream first).  NULL is a no-op. */
+/* Free the plan and its device workspace (waits for its stream and for host-call copies
+ * still in flight first).  NULL is a no-op. */
 void mwax_plan_destroy(mwax_plan* plan);
 
 /* Message of the last error on the calling thread ("" if none). */

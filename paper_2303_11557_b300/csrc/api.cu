@@ -1037,6 +1037,8 @@ void mwax_plan_destroy(mwax_plan* p)
     if (!p) return;
     cudaSetDevice(p->device);
     cudaStreamSynchronize(p->stream);
+    if (p->copy_stream) cudaStreamSynchronize(p->copy_stream);   // host calls still in flight
+    if (p->back_stream) cudaStreamSynchronize(p->back_stream);
     free_plan(p);
 }
 

@@ -226,9 +226,10 @@ mwax_status mwax_plan_stage_times(mwax_plan* plan, double ms[3], long long launc
 
 /* Launch choices of a plan.  fstep_variant: 0 = two-pass radix-32 F-step kernel (built
  * for N = 32..512; the generic kernel elsewhere), 1 = generic shared-memory Stockham
- * kernel.  run_len: output channels per X-step work item (0 = chosen from the grid
- * size).  window: column width of a tensor-core X-step tile, 128 or 256.  ms: device time
- * of one call measured by the autotuner. */
+ * kernel.  run_len: output channels per X-step work item (0 = the plan's own choice: the
+ * run length whose longest-first schedule of the work items on the GPU's resident CTA
+ * slots is shortest).  window: column width of a tensor-core X-step tile, 128 or 256.
+ * ms: device time of one call measured by the autotuner. */
 typedef struct {
     int fstep_variant;
     int run_len;
@@ -238,8 +239,10 @@ typedef struct {
 
 /*
  * Autotuner: runs the plan on the caller's buffers (same arguments as mwax_correlate)
- * once per candidate choice (F-step variant x run length x tile window), times each
- * with CUDA events on the plan's stream, and keeps the fastest.  Synchronous.  vis_out is
+ * twice per candidate choice (F-step variant: radix-32 or generic for N = 32..512; run
+ * length: the plan's modelled choice, 3, 5, 11 and all output channels; tile window 256
+ * or 128 for the tensor-core forms), times each call with CUDA events on the plan's
+ * stream, and keeps the choice with the fastest call.  Synchronous.  vis_out is
  * overwritten with a valid result.  best (may be NULL) receives the choice and its time.
  */
 mwax_status mwax_plan_autotune(mwax_plan* plan, const int8_t* voltages, const double* delay_poly, void* vis_out,

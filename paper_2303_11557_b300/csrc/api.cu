@@ -480,8 +480,16 @@ mwax_status setup(mwax_plan& p)
 
 namespace mwax {
 
-// Work items of one tensor-core X launch of plan p (as job `job`), with a cost estimate
-// (MMA volume: active ultrafine channels x frame blocks x window width) for ordering.
+// Work items of one X launch of plan p (as job `job`) with their sort key; the tiles'
+// relative costs: tensor cores, the B window width with A rows outside it costing extra;
+// CUDA cores, a diagonal tile skipping 9 of its 32 register sub-blocks.
+// Tensor cores: the key is the cost of the item's run of output channels (active
+// ultrafine channels x frame blocks) and within each (slot, run) the tiles are listed most
+// expensive first, so after the stable sort the big runs start first and all tiles of one
+// (slot, run) sit side by side: the CTAs running together stream the same channels of the
+// same integration, which then come from L2 instead of HBM (the persistent kernel is fed by
+// HBM; this ordering took 4-5 % off its time).  CUDA cores (bound by FMA issue, not by
+// HBM): the key is the item's own cost, longest first.
 void plan_items(const mwax_plan& p, int job, long long nslots, long long klen, std::vector<std::pair<double, XItem>>& out)
 {
     const int KF = (p.prec == MWAX_FP8) ? 64 : 32;
@@ -495,21 +503,22 @@ void plan_items(const mwax_plan& p, int job, long long nslots, long long klen, s
             for (int c = gr.c0; c < gr.c1; ++c) bins[r] += p.h_gain[c] > 0.0f;
         }
     }
-    // slot-major, then run, then tile: after the (stable) sort by cost, items of equal cost
-    // that run side by side read the same integration's channels, which then stay in L2
+    std::vector<int> tiles(p.n_tiles);
+    std::vector<double> tcost(p.n_tiles);
+    for (int t = 0; t < p.n_tiles; ++t) {
+        const int4 tl = p.h_tiles[t];
+        tiles[t] = t;
+        tcost[t] = tl.z * (p.tensor_cores ? (tl.w ? 1.0 : 1.25) : (tl.w ? 23.0 / 32.0 : 1.0));
+    }
+    std::stable_sort(tiles.begin(), tiles.end(), [&](int x, int y) { return tcost[x] > tcost[y]; });
     for (long long sl = 0; sl < nslots; ++sl)
         for (int r = 0; r < p.n_runs; ++r)
-            for (int t = 0; t < p.n_tiles; ++t) {
-                const int4 tl = p.h_tiles[t];
-                // tensor cores: B window width, A rows outside it cost extra; CUDA cores: a
-                // diagonal tile skips 9 of its 32 register sub-blocks
-                const double f = p.tensor_cores ? (tl.w ? 1.0 : 1.25) : (tl.w ? 23.0 / 32.0 : 1.0);
-                const double cost = bins[r] * nkb * tl.z * f + 1.0;
-                out.push_back({cost, XItem{job, t, r, (int)sl}});
-            }
+            for (int t : tiles)
+                out.push_back({p.tensor_cores ? bins[r] * nkb + 1.0 : bins[r] * nkb * tcost[t] + 1.0,
+                               XItem{job, t, r, (int)sl}});
 }
 
-// Items in decreasing estimated cost: claimed in this order, the big ones start first.
+// Items in decreasing key (stable): claimed or launched in this order.
 void sort_items(std::vector<std::pair<double, XItem>>& v, std::vector<XItem>& order)
 {
     std::stable_sort(v.begin(), v.end(), [](const std::pair<double, XItem>& a, const std::pair<double, XItem>& b) {

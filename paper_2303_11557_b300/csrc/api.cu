@@ -824,6 +824,8 @@ mwax_status enqueue_xstep_single(mwax_plan* p, const LaunchGroup& g, const XArgs
         L.jobs[0].tmap = p->tmap;
         L.jobs[0].a = xa;
         L.jobs[0].op = (p->prec == MWAX_FP8) ? 1 : 0;
+        L.jobs[0].max_cols = 0;
+        for (const int4& tl : p->h_tiles) L.jobs[0].max_cols = std::max(L.jobs[0].max_cols, tl.z);
         MWAX_CUDA(timed(p, 2, s, [&] { return launch_xstep_tc(L, items, n_items, p->counter, p->status, s); }));
     } else {
         XItem* items = nullptr;

@@ -159,6 +159,8 @@ mwax_status enqueue_batch(mwax_batch* b, const int8_t* const* volt, const double
                 L.jobs[j].a = make_xargs(p, *g, static_cast<char*>(out[i]));
                 L.jobs[j].a.status = b->status;
                 L.jobs[j].op = (p->prec == MWAX_FP8) ? 1 : 0;
+                L.jobs[j].max_cols = 0;
+                for (const int4& tl : p->h_tiles) L.jobs[j].max_cols = std::max(L.jobs[j].max_cols, tl.z);
             }
             BCUDA(launch_xstep_tc(L, R.items, R.n_items, b->counter, b->status, s));
         }

@@ -113,7 +113,8 @@ struct XArgs {
 struct XJob {
     CUtensorMap tmap;
     XArgs a;
-    int op;   // 0 = FP16 (kind::f16), 1 = e4m3 (kind::f8f6f4)
+    int op;         // 0 = FP16 (kind::f16), 1 = e4m3 (kind::f8f6f4)
+    int max_cols;   // widest tile (columns) of the job: 128 lets the launch double-buffer TMEM
 };
 
 // One work item of the persistent tensor-core X-step.

@@ -20,7 +20,10 @@
 // window and only B is loaded; elsewhere A and B are loaded separately.  For each group of
 // ultrafine channels (pre-weighted by sqrt(w) in the F-step) the MMAs of every frame of
 // every channel in the group accumulate into one TMEM accumulator pair (Re: columns
-// [0, 256), Im: [256, 512)), which the epilogue drains once per group.
+// [0, 256), Im: [256, 512)), which the epilogue drains once per group.  When every tile of
+// the launch is at most 128 columns wide the pair needs only 256 columns, and two pairs
+// alternate (buffer b: Re [256 b, 256 b + 128), Im [256 b + 128, 256 b + 256)): the MMAs
+// of the next group run while the epilogue drains the previous one.
 //
 // 10 warps: warp 0 issues TMA loads into a 4-stage ring, warp 1 owns TMEM and issues the
 // MMAs from one thread, warps 2-9 drain the accumulators (TMEM lane quarter = warp % 4,
@@ -49,8 +52,8 @@ constexpr int IRING = 4;   // claimed work items in flight between the roles
 struct TcSmem {
     uint64_t full[STAGES];
     uint64_t empty[STAGES];
-    uint64_t acc_full;
-    uint64_t acc_empty;
+    uint64_t acc_full[2];
+    uint64_t acc_empty[2];
     uint64_t item_full[IRING];    // producer -> MMA + epilogue: item index published
     uint64_t item_empty[IRING];   // MMA + epilogue -> producer: slot free again
     int item[IRING];              // claimed item index, -1 = no more work
@@ -70,7 +73,7 @@ __device__ __forceinline__ bool item_feeds(const Group& gr, const RunInfo& run)
 
 __global__ void __launch_bounds__(NTHREADS, 1)
     xstep_tc_kernel(const __grid_constant__ XLaunch L, const XItem* __restrict__ items, int n_items, int* counter,
-                    int* status, unsigned int spin_limit)
+                    int* status, unsigned int spin_limit, int dbuf)
 {
     const XJob* jobs = L.jobs;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -86,8 +89,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             tc::mbar_init(&S.full[s], 1);
             tc::mbar_init(&S.empty[s], 1);
         }
-        tc::mbar_init(&S.acc_full, 1);
-        tc::mbar_init(&S.acc_empty, EPI_THREADS);
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&S.acc_full[b], 1);
+            tc::mbar_init(&S.acc_empty[b], EPI_THREADS);
+        }
         for (int r = 0; r < IRING; ++r) {
             tc::mbar_init(&S.item_full[r], 1);
             tc::mbar_init(&S.item_empty[r], 1 + EPI_THREADS);
@@ -179,10 +184,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             int stage = 0;
-            uint32_t phase = 0, gphase = 0;
+            uint32_t phase = 0, gcount = 0;   // gcount: groups accumulated so far
+            int cur_b = 0;
+            uint32_t cur_ph = 0;
             const uint32_t sbase = tc::smem_u32(ring);
             bool issued = false;
-            const uint32_t d_re = tmem, d_im = tmem + 256;
             int ir = 0;
             uint32_t iphase = 0;
             for (;;) {
@@ -207,7 +213,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 for (int g = run.g0; g < run.g1 && !*abort; ++g) {
                     const Group gr = a.groups[g];
                     if (!item_feeds(gr, run)) continue;
-                    if (!tc::mbar_wait(&S.acc_empty, gphase ^ 1, abort, status, 4, lim)) break;
+                    // accumulator buffer of this group and the parity of its use
+                    cur_b = dbuf ? (int)(gcount & 1) : 0;
+                    cur_ph = dbuf ? ((gcount >> 1) & 1) : (gcount & 1);
+                    const uint32_t d_re = tmem + (dbuf ? 256u * cur_b : 0u), d_im = d_re + (dbuf ? 128u : 256u);
+                    if (!tc::mbar_wait(&S.acc_empty[cur_b], cur_ph ^ 1, abort, status, 4, lim)) break;
                     tc::fence_after();
                     bool first = true;
                     for (int c = gr.c0; c < gr.c1 && !*abort; ++c) {
@@ -245,15 +255,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         }
                     }
                     if (*abort) break;
-                    tc::mma_commit(&S.acc_full);
-                    gphase ^= 1;
+                    tc::mma_commit(&S.acc_full[cur_b]);
+                    ++gcount;
                 }
             }
             if (*abort && issued) {
                 // wait for the MMAs in flight before TMEM is released
-                tc::mma_commit(&S.acc_full);
+                tc::mma_commit(&S.acc_full[cur_b]);
                 const long long t0 = clock64();
-                while (!tc::mbar_try_wait(&S.acc_full, gphase) && clock64() - t0 < lim) {
+                while (!tc::mbar_try_wait(&S.acc_full[cur_b], cur_ph) && clock64() - t0 < lim) {
                 }
             }
         }
@@ -261,7 +271,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // ------------------------------------------------------------ epilogue
         const int g4 = warp & 3;                 // TMEM lane quarter of this warp
         const int half = (warp - 2) >> 2;        // column half of the window
-        uint32_t gphase = 0;
+        uint32_t gcount = 0;
         int ir = 0;
         uint32_t iphase = 0;
         for (;;) {
@@ -292,7 +302,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 if (!item_feeds(gr, run)) continue;
                 const bool use_a = gr.ja >= run.j0 && gr.ja < run.j1;
                 const bool use_b = gr.jb >= run.j0 && gr.jb < run.j1;
-                bool ok = tc::mbar_wait(&S.acc_full, gphase, abort, status, 16, lim);
+                const int b = dbuf ? (int)(gcount & 1) : 0;
+                const uint32_t ph = dbuf ? ((gcount >> 1) & 1) : (gcount & 1);
+                const uint32_t re0 = dbuf ? 256u * b : 0u, im_off = dbuf ? 128u : 256u;
+                bool ok = tc::mbar_wait(&S.acc_full[b], ph, abort, status, 16, lim);
                 if (!__all_sync(0xffffffffu, ok)) break;   // keep the warp's TMEM loads uniform
                 tc::fence_after();
                 if (cols) {
@@ -307,9 +320,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     for (int ch = 0; ch < 4; ++ch) {
                         const int col = half * 128 + ch * 32;
                         uint32_t vr[32], vi[32];
-                        const uint32_t taddr = tmem + ((uint32_t)(g4 * 32) << 16) + col;
+                        const uint32_t taddr = tmem + ((uint32_t)(g4 * 32) << 16) + re0 + col;
                         tc::tmem_ld32(taddr, vr);
-                        tc::tmem_ld32(taddr + 256, vi);
+                        tc::tmem_ld32(taddr + im_off, vi);
                         tc::tmem_wait_ld();
                         if (p >= n) continue;
                         // 8 columns at a time: issue every load of the old values before any
@@ -349,8 +362,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                 }
                 tc::fence_before();
-                tc::mbar_arrive(&S.acc_empty);
-                gphase ^= 1;
+                tc::mbar_arrive(&S.acc_empty[b]);
+                ++gcount;
             }
         }
     }
@@ -428,8 +441,10 @@ cudaError_t launch_xstep_tc(const XLaunch& L, const XItem* items, int n_items, i
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
+    int dbuf = 1;   // double-buffered accumulators when every job's tiles are at most 128 columns wide
+    for (int j = 0; j < L.n_jobs; ++j) dbuf &= (L.jobs[j].max_cols <= TM) ? 1 : 0;
     xstep_tc_kernel<<<n_items < sms ? n_items : sms, NTHREADS, smem, s>>>(L, items, n_items, counter, status,
-                                                                          2000000u);
+                                                                          2000000u, dbuf);
     return cudaGetLastError();
 }
 

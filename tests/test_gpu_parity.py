@@ -176,3 +176,30 @@ def test_host_async_two_in_flight():
         vis, _ = mw.split_output(plan, houts[k].numpy())
         assert np.array_equal(vis, want[k])
     del keep
+
+
+@pytest.mark.parametrize("prec", [pytest.param(mw.MWAX_FP16, id="fp16"), pytest.param(mw.MWAX_FP8, id="fp8")])
+@pytest.mark.parametrize("run_len", [1, 5])
+def test_tensor_core_window_128(prec, run_len):
+    # 128-column tiles: the persistent X-step alternates two TMEM accumulator pairs (the
+    # MMAs of a group run while the previous group is drained); 40 tiles = 80 paths give
+    # several 128 x 128 tiles and a ragged one; FP8 needs >= 200 frames (see test_fft_lengths)
+    T, N, F, t_int = 80, 64, 2, 0.01
+    volt, delay = workload(14, T, 64_000, block_samples=6400, delay="linear")
+    desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=t_int, samples_per_call=64_000,
+                       block_samples=6400, sky_freq_hz=synth.SKY_FREQ_HZ, precision=prec)
+    plan = mw.mwax_plan_create_ex(desc)
+    mw.mwax_plan_set_stream(plan)
+    t0 = mw.mwax_plan_get_tuning(plan)
+    mw.mwax_plan_set_tuning(plan, mw.Tuning(t0.fstep_variant, run_len, 128, 0.0))
+    dv = torch.from_numpy(volt.reshape(-1)).cuda()
+    out = mw.empty_output(plan)
+    out.fill_(0xAB)
+    mw.mwax_correlate(plan, dv, torch.from_numpy(delay).cuda(), out)
+    mw.mwax_plan_sync(plan)
+    vis, w = mw.split_output(plan, out)
+    vis = vis.cpu().numpy()
+    ref, _ = oracle.correlate(oracle_desc(T, N, F, t_int, 64_000, block_samples=6400), volt, delay)
+    err = parity_error(vis, ref, T)
+    assert np.all(np.isfinite(vis)) and err.max() <= TOL[prec], f"max err {err.max():.3e}"
+    plan.close()

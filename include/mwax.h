@@ -238,12 +238,13 @@ typedef struct {
 } mwax_tuning;
 
 /*
- * Autotuner: runs the plan on the caller's buffers (same arguments as mwax_correlate)
- * twice per candidate choice (F-step variant: radix-32 or generic for N = 32..512; run
- * length: the plan's modelled choice, 3, 5, 11 and all output channels; tile window 256
- * or 128 for the tensor-core forms), times each call with CUDA events on the plan's
- * stream, and keeps the choice with the fastest call.  Synchronous.  vis_out is
- * overwritten with a valid result.  best (may be NULL) receives the choice and its time.
+ * Autotuner: runs the plan on the caller's buffers (same arguments as mwax_correlate),
+ * three calls per candidate, timed with CUDA events on the plan's stream (the fastest of
+ * the three counts).  First the F-step variant (radix-32 or generic, for N = 32..512) with
+ * the plan's current X-step choice; then, with the faster variant, the tile window (256 or
+ * 128, tensor-core forms) x the run length (the plan's modelled choice, 3, 5, 11 and all
+ * output channels).  Keeps the fastest.  Synchronous.  vis_out is overwritten with a valid
+ * result.  best (may be NULL) receives the choice and its time.
  */
 mwax_status mwax_plan_autotune(mwax_plan* plan, const int8_t* voltages, const double* delay_poly, void* vis_out,
                                mwax_tuning* best);

@@ -323,30 +323,48 @@ mwax_status mwax_plan_autotune(mwax_plan* p, const int8_t* voltages, const doubl
     const bool timing = p->timing;
     p->timing = false;
     mwax_status st = MWAX_OK;
-    for (int fv : fvars)
-        for (int w : windows)
-            for (int rl : runs) {
-                p->fvariant = fv;
-                st = configure_x(*p, rl, w);
-                if (st != MWAX_OK) break;
-                if (fv == fvars[0] && w == windows[0] && rl == runs[0]) {
-                    st = mwax_correlate(p, voltages, delay_poly, vis_out);   // warm-up
-                    if (st != MWAX_OK) break;
-                }
-                float ms = 1e30f;   // best of two calls: one call's noise can exceed the differences
-                for (int rep = 0; rep < 2 && st == MWAX_OK; ++rep) {
-                    cudaEventRecord(e0, p->stream);
-                    st = mwax_correlate(p, voltages, delay_poly, vis_out);
-                    if (st != MWAX_OK) break;
-                    cudaEventRecord(e1, p->stream);
-                    cudaEventSynchronize(e1);
-                    float t = 0.0f;
-                    cudaEventElapsedTime(&t, e0, e1);
-                    ms = std::min(ms, t);
-                }
-                if (st != MWAX_OK) break;
-                if (ms < best.ms) best = mwax_tuning{fv, p->run_len, w, ms};
-            }
+    // best of three calls: one call's noise can exceed the differences being measured
+    auto time_call = [&](float& ms) {
+        ms = 1e30f;
+        for (int rep = 0; rep < 3 && st == MWAX_OK; ++rep) {
+            cudaEventRecord(e0, p->stream);
+            st = mwax_correlate(p, voltages, delay_poly, vis_out);
+            if (st != MWAX_OK) break;
+            cudaEventRecord(e1, p->stream);
+            cudaEventSynchronize(e1);
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, e0, e1);
+            ms = std::min(ms, t);
+        }
+    };
+    // stage 1: the F-step variant, with the plan's own X-step choice
+    const int rl0 = p->run_len, w0 = p->window;
+    for (int fv : fvars) {
+        p->fvariant = fv;
+        st = configure_x(*p, rl0, w0);
+        if (st != MWAX_OK) break;
+        if (fv == fvars[0]) {
+            st = mwax_correlate(p, voltages, delay_poly, vis_out);   // warm-up
+            if (st != MWAX_OK) break;
+        }
+        float ms;
+        time_call(ms);
+        if (st != MWAX_OK) break;
+        if (ms < best.ms) best = mwax_tuning{fv, p->run_len, w0, ms};
+    }
+    // stage 2: tile window x run length, with that F-step variant
+    if (st == MWAX_OK) p->fvariant = best.fstep_variant;
+    for (int w : windows)
+        for (int rl : runs) {
+            if (st != MWAX_OK) break;
+            if (w == w0 && rl != 0 && rl == rl0) continue;   // measured in stage 1
+            st = configure_x(*p, rl, w);
+            if (st != MWAX_OK) break;
+            float ms;
+            time_call(ms);
+            if (st != MWAX_OK) break;
+            if (ms < best.ms) best = mwax_tuning{best.fstep_variant, p->run_len, w, ms};
+        }
     p->timing = timing;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

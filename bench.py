@@ -48,8 +48,8 @@ WORKSPACE = 48 << 30
 # capture of the one-integration case (profiles/).  Reported only while the kernel's
 # source is byte-identical to the one captured (sha1 prefix of its .cu file).
 TRAFFIC = {"xstep_simt_kernel": ("paper_2303_11557_b300/csrc/xstep_simt.cu", "801bae888475", 6.645909e9 + 0.100315e9),
-           "xstep_tc_kernel<0>": ("paper_2303_11557_b300/csrc/xstep_tc.cu", "afc1d7f6e301",
-                                  (5.340589e9 + 0.290356e9) / 3)}   # 3-slot capture
+           "xstep_tc_kernel<false> (fp16)": ("paper_2303_11557_b300/csrc/xstep_tc.cu", "afc1d7f6e301",
+                                             (5.340589e9 + 0.290356e9) / 3)}   # 3-slot capture
 
 
 def traffic_per_slot(kernel: str):
@@ -530,7 +530,8 @@ def run_mine(args, world, rank, local):
     dev_delay = torch.from_numpy(delay).cuda()
     pk, pk_kind = peaks()
     headline = args.precision
-    forms = [headline] + ([] if args.no_forms else [f for f in ("fp32", "fp16", "fp8", "int8") if f != headline])
+    forms = [headline] + ([] if args.no_forms else [f for f in ("fp32", "fp16x3", "fp16", "fp8", "int8")
+                                                     if f != headline])
     results, ref_vis, line_parts = {}, None, {}
     for form in forms:
         prec = mw.PRECISIONS[form]
@@ -554,7 +555,7 @@ def run_mine(args, world, rank, local):
         info = plan.info
         K, n_ints = info["frames_per_int"], info["n_ints"]
         N, F = desc.fft_len, desc.fine_avg
-        elem = {"fp32": 4, "fp16": 2, "fp8": 1, "int8": 2}[form]
+        elem = {"fp32": 4, "fp16": 2, "fp8": 1, "int8": 2, "fp16x3": 4}[form]
         x_flops, f_bytes, used = algorithmic_work(W["n_tiles"], N, F, K, n_ints, elem)
         if form == "fp8":
             f_bytes += 2.0 * 2 * W["n_tiles"] * K * N * n_ints   # the amax pass reads the voltages again
@@ -569,14 +570,17 @@ def run_mine(args, world, rank, local):
             peak_kind = (f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {pk.get('sm_max_mhz')} MHz "
                          f"({pk_kind} max clock)")
         else:
-            xkern = {"fp16": "xstep_tc_kernel<0>", "fp8": "xstep_tc_kernel<1>", "int8": "xstep_int8_kernel"}[form]
+            xkern = {"fp16": "xstep_tc_kernel<false> (fp16)", "fp8": "xstep_tc_kernel<false> (e4m3)",
+                     "fp16x3": "xstep_tc_kernel<true> (fp16 hi/lo pairs)", "int8": "xstep_int8_kernel"}[form]
             bound = "tensor"
             base = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
             ratio = 2.0 if form == "fp8" else 1.0
             x_peak = base * ratio
             peak_kind = (f"{pk_kind} dense bf16 cuBLAS, sustained" + (" x 2 (fp8 : bf16 nominal 4.5 : 2.25)"
                                                                         if form == "fp8" else " (fp16 = bf16 rate)")
-                         + ("; int8 values run exactly as fp16" if form == "int8" else ""))
+                         + ("; int8 values run exactly as fp16" if form == "int8" else "")
+                         + ("; three fp16 products per algorithmic term, so frac <= 1/3 by construction"
+                            if form == "fp16x3" else ""))
         tps = traffic_per_slot(xkern) if form == headline else None
         r = {"value": world * SUBOBS_S * (n_ints * desc.int_time_s / SUBOBS_S) / (ms * 1e-3),
              "ms_per_step": ms, "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
@@ -596,7 +600,7 @@ def run_mine(args, world, rank, local):
         if form == "fp32" and form != "int8":
             vis32, _ = mw.split_output(plan, out)
             ref_vis = vis32.clone()
-        elif form in ("fp16", "fp8") and ref_vis is not None:
+        elif form in ("fp16", "fp8", "fp16x3") and ref_vis is not None:
             mx, med = rel_error_vs(mw, torch, plan, out, ref_vis, W["n_tiles"])
             r["error_vs_fp32"] = {"max": mx, "median": med,
                                   "metric": "|V - V_fp32| / sqrt(auto_pp auto_qq), full workload"}
@@ -665,7 +669,7 @@ def run_mine(args, world, rank, local):
         "metric": METRIC, "value": h["value"], "unit": "channels", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16", "fp8": "e4m3",
-                                                          "int8": "s8"}[headline],
+                                                          "int8": "s8", "fp16x3": "f16x3"}[headline],
         "data": "synthetic (seeded Gaussian sigma=16 + point source, linear per-tile delays)",
         "config": {"workload": W["name"], "n_tiles": W["n_tiles"], "fft_len": W["fft_len"],
                    "fine_avg": W["fine_avg"], "int_time_s": W["int_time_s"], "subobs_s": SUBOBS_S,
@@ -698,7 +702,7 @@ def main():
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "fp8", "int8"],
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16x3", "fp16", "fp8", "int8"],
                     help="headline precision (the full-array plain form is FP32); the other forms are timed beside it")
     ap.add_argument("--no-forms", action="store_true", help="time the headline precision only")
     ap.add_argument("--no-batch", action="store_true", help="skip the 24-channel batched measurement")

@@ -58,7 +58,12 @@ typedef enum {
     MWAX_FP32 = 0,  /* FP32 FFT and FP32 CUDA-core cross-multiply (the paper's form)     */
     MWAX_FP16 = 1,  /* FP32 FFT, FP16 operands on tcgen05 tensor cores, FP32 accumulate  */
     MWAX_FP8 = 2,   /* FP32 FFT, e4m3 operands with per-path-per-channel scales, tcgen05 */
-    MWAX_INT8 = 3   /* no FFT (N = 1, F = 1), exact integer sums, int64 output           */
+    MWAX_INT8 = 3,  /* no FFT (N = 1, F = 1), exact integer sums, int64 output           */
+    MWAX_FP16X3 = 4 /* FP32 FFT; each operand an FP16 hi/lo pair (22 significant bits),
+                       three FP16 products per complex term on tcgen05 (the lo x lo term,
+                       2^-22 of the product, dropped), partial sums of 64 frames added in
+                       FP32: FP32-level error on the tensor cores; 128 x 128 tiles,
+                       operands 8 B per sample and path like MWAX_FP32                  */
 } mwax_precision;
 
 /* Plan parameters.  Zero-initialise and set what you need; zero selects the default. */

@@ -21,8 +21,8 @@ import numpy as np
 from . import _build
 
 MWAX_OK, MWAX_EINVAL, MWAX_ENOMEM, MWAX_ECUDA, MWAX_EUNSUPPORTED, MWAX_ETIMEOUT = range(6)
-MWAX_FP32, MWAX_FP16, MWAX_FP8, MWAX_INT8 = range(4)
-PRECISIONS = {"fp32": MWAX_FP32, "fp16": MWAX_FP16, "fp8": MWAX_FP8, "int8": MWAX_INT8}
+MWAX_FP32, MWAX_FP16, MWAX_FP8, MWAX_INT8, MWAX_FP16X3 = range(5)
+PRECISIONS = {"fp32": MWAX_FP32, "fp16": MWAX_FP16, "fp8": MWAX_FP8, "int8": MWAX_INT8, "fp16x3": MWAX_FP16X3}
 FS = 1_280_000.0
 BLOCK_SAMPLES = 64_000
 

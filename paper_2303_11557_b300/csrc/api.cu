@@ -109,6 +109,7 @@ int prec_elem_bytes(int prec)
         case MWAX_FP16: return 2;
         case MWAX_FP8: return 3;   // FP16 staging (2) + e4m3 operands (1)
         case MWAX_INT8: return 2;   // int8 held exactly in FP16 operands
+        case MWAX_FP16X3: return 4;   // an FP16 hi/lo pair per value
         default: return 0;
     }
 }
@@ -178,7 +179,7 @@ mwax_status validate(const mwax_plan_desc& d, mwax_plan& p)
         return fail(MWAX_EINVAL, "samples_per_call (%lld) must be a multiple of the integration (%lld)", S,
                     int_samples);
     if (S % bs) return fail(MWAX_EINVAL, "samples_per_call (%lld) must be a multiple of block_samples (%d)", S, bs);
-    if (d.precision < MWAX_FP32 || d.precision > MWAX_INT8)
+    if (d.precision < MWAX_FP32 || d.precision > MWAX_FP16X3)
         return fail(MWAX_EINVAL, "unknown precision %d", d.precision);
     if (d.precision == MWAX_INT8 && (d.fft_len != 1 || d.fine_avg != 1))
         return fail(MWAX_EINVAL, "MWAX_INT8 needs fft_len = fine_avg = 1 (no FFT)");
@@ -307,6 +308,7 @@ mwax_status configure_x(mwax_plan& p, int run_len_req, int window)
         for (int i = 0; i < p.n; i += 128)
             for (int j = i; j < p.n; j += 128) tiles.push_back(make_int4(i, j, 128, i == j ? 1 : 0));
     } else if (p.tensor_cores) {
+        if (p.prec == MWAX_FP16X3) window = 128;   // the pair form's register totals hold 128 columns
         tiles.resize(build_tc_tiles(p.n, window, nullptr, 0));
         build_tc_tiles(p.n, window, tiles.data(), (int)tiles.size());
     } else {
@@ -367,7 +369,7 @@ constexpr double kMaxPassband = 2.0;
 
 void set_prescale(mwax_plan& p)
 {
-    if (p.prec != MWAX_FP16 && p.prec != MWAX_FP8) return;
+    if (p.prec != MWAX_FP16 && p.prec != MWAX_FP8 && p.prec != MWAX_FP16X3) return;
     int k = 0;
     while (181.02 * p.N * kMaxPassband / (double)(1 << k) > 32768.0) ++k;
     p.out_scale = ldexpf(1.0f, -k);
@@ -462,6 +464,8 @@ mwax_status setup(mwax_plan& p)
     }
     if (p.prec == MWAX_FP32)
         MWAX_CUDA(make_simt_tmap(&p.tmap, p.Y, p.Kpad, p.n, p.slots * p.N * 2));
+    else if (p.prec == MWAX_FP16X3)   // FP16 rows of 2 Kpad: hi frames, then lo frames
+        MWAX_CUDA(make_operand_tmap(&p.tmap, p.Y, 2, 2 * p.Kpad, p.n, p.slots * p.N * 2));
     else
         MWAX_CUDA(make_operand_tmap(&p.tmap, p.Y, p.prec == MWAX_FP8 ? 1 : 2, p.Kpad, p.n, p.slots * p.N * 2));
 
@@ -767,7 +771,8 @@ mwax_status enqueue_fstep(mwax_plan* p, const LaunchGroup& g, const int8_t* volt
                                         p->amax, p->chan_group, p->n_groups, g.nslots, p->N, p->n, p->Kpad, s);
         }));
     } else {
-        const int fout = (p->prec == MWAX_FP32) ? FOUT_F32 : FOUT_F16;
+        const int fout = (p->prec == MWAX_FP32) ? FOUT_F32 : (p->prec == MWAX_FP16X3 ? FOUT_F16X3 : FOUT_F16);
+        if (p->prec == MWAX_FP16X3) fa.Kpad = 2 * p->Kpad;   // row length: hi frames, then lo frames
         MWAX_CUDA(timed(p, 1, s, [&] { return launch_fstep(p->N, fout, fa, s, p->fvariant); }));
     }
     return MWAX_OK;
@@ -823,7 +828,7 @@ mwax_status enqueue_xstep_single(mwax_plan* p, const LaunchGroup& g, const XArgs
         L.n_jobs = 1;
         L.jobs[0].tmap = p->tmap;
         L.jobs[0].a = xa;
-        L.jobs[0].op = (p->prec == MWAX_FP8) ? 1 : 0;
+        L.jobs[0].op = (p->prec == MWAX_FP8) ? 1 : (p->prec == MWAX_FP16X3 ? 2 : 0);
         L.jobs[0].max_cols = 0;
         for (const int4& tl : p->h_tiles) L.jobs[0].max_cols = std::max(L.jobs[0].max_cols, tl.z);
         MWAX_CUDA(timed(p, 2, s, [&] { return launch_xstep_tc(L, items, n_items, p->counter, p->status, s); }));

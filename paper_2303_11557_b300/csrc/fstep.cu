@@ -244,7 +244,9 @@ struct FrameInfo {
 template <int N, int OUTK>
 struct Store {
     // Write one corrected spectral value: real plane at element `at`, imaginary plane at
-    // `at + plane_stride` of the operand buffer (FP32, or FP16 pre-scaled by out_scale).
+    // `at + plane_stride` of the operand buffer (FP32, or FP16 pre-scaled by out_scale;
+    // FP16 pairs: the remainder v - hi, exact in FP32, rounded again to FP16 half a row
+    // further on, so hi + lo carries 22 significant bits).
     __device__ __forceinline__ static void run(const FArgs& a, long long at, long long plane_stride, float2 v,
                                                long long /*slot*/, int /*c*/, int /*p*/)
     {
@@ -252,6 +254,15 @@ struct Store {
             float* Y = static_cast<float*>(a.Y);
             Y[at] = v.x;
             Y[at + plane_stride] = v.y;
+        } else if (OUTK == FOUT_F16X3) {
+            __half* Y = static_cast<__half*>(a.Y);
+            const long long lo = a.Kpad >> 1;
+            const float xr = v.x * a.out_scale, xi = v.y * a.out_scale;
+            const __half hr = __float2half_rn(xr), hi = __float2half_rn(xi);
+            Y[at] = hr;
+            Y[at + plane_stride] = hi;
+            Y[at + lo] = __float2half_rn(xr - __half2float(hr));
+            Y[at + plane_stride + lo] = __float2half_rn(xi - __half2float(hi));
         } else {
             __half* Y = static_cast<__half*>(a.Y);
             Y[at] = __float2half_rn(v.x * a.out_scale);
@@ -893,6 +904,7 @@ cudaError_t launch_fstep(int N, int out_kind, const FArgs& a_in, cudaStream_t s,
     switch (out_kind) {
         case FOUT_F32: return launch_kind<FOUT_F32>(N, a, s, variant);
         case FOUT_F16: return launch_kind<FOUT_F16>(N, a, s, variant);
+        case FOUT_F16X3: return launch_kind<FOUT_F16X3>(N, a, s, variant);
         default: return cudaErrorInvalidValue;
     }
 }

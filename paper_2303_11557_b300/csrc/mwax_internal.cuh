@@ -16,7 +16,10 @@ constexpr int kDefaultBlock = 64000;     // samples per path per 50 ms data bloc
 constexpr int kKAlign = 128;             // frames per operand row are padded to this
 
 // Output-type selector of the F-step (the FP8 form quantises the FP16 output afterwards).
-enum FOut : int { FOUT_F32 = 0, FOUT_F16 = 1 };
+// FOUT_F16X3: each value v (pre-scaled) as an FP16 pair hi = fp16(v), lo = fp16(v - hi),
+// hi in the first half of the operand row and lo in the second (the launch's Kpad is then
+// the row length, twice the frame capacity).
+enum FOut : int { FOUT_F32 = 0, FOUT_F16 = 1, FOUT_F16X3 = 2 };
 
 // Channel averaging (Sec. 2.6) is split in two: the F-step multiplies ultrafine channel
 // c by gain[c] = sqrt(w_c) (w_c = 1, 1/2 for the end bins of an even fscrunch, 0 for an
@@ -113,7 +116,8 @@ struct XArgs {
 struct XJob {
     CUtensorMap tmap;
     XArgs a;
-    int op;         // 0 = FP16 (kind::f16), 1 = e4m3 (kind::f8f6f4)
+    int op;         // 0 = FP16 (kind::f16), 1 = e4m3 (kind::f8f6f4), 2 = FP16 hi/lo pairs
+                    //   (three products per complex term, chunked two-level accumulation)
     int max_cols;   // widest tile (columns) of the job: 128 lets the launch double-buffer TMEM
 };
 

@@ -1,5 +1,5 @@
 // X-step on the 5th-generation tensor cores (tcgen05, TMEM accumulators, TMA operand
-// staging) for the FP16 and FP8-e4m3 precision forms, with the same fused epilogue as the
+// staging) for the FP16, FP8-e4m3 and FP16 hi/lo pair forms, with the same fused epilogue as the
 // CUDA-core form: integration over the frames of a slot (Sec. 2.5.2), channel averaging
 // (Sec. 2.6) and MWAX_ORDER output (Sec. 2.7).
 //
@@ -28,6 +28,17 @@
 // 10 warps: warp 0 issues TMA loads into a 4-stage ring, warp 1 owns TMEM and issues the
 // MMAs from one thread, warps 2-9 drain the accumulators (TMEM lane quarter = warp % 4,
 // column half = (warp - 2) / 4; one TMEM lane = one path p).
+//
+// FP16 hi/lo pair form (FP32-accurate products on the tensor cores): every operand value
+// v is held as hi = fp16(v) and lo = fp16(v - hi) (22 significant bits), and each complex
+// product is (Ah + Al)(Bh + Bl)^H less the Al Bl^H term, i.e. twelve real MMAs whose
+// products are exact in FP32; the dropped term is 2^-22 of the product.  The MMAs of 64
+// frames at a time go into a fresh TMEM partial (two partial buffers alternate), and the
+// epilogue adds each partial into FP32 register totals: the two-level sum keeps the
+// accumulation error of an integration of thousands of frames at the FP32 level, where
+// one MMA accumulation over all of them would not be.  Tiles are 128 x 128 (the register
+// totals hold one row's 64 columns per epilogue thread); the ring has 3 stages of the 8
+// planes (re, im x hi, lo of A and B).
 #include "mwax_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -38,20 +49,33 @@ namespace {
 
 constexpr int TM = 128;                        // rows (paths p) per tile
 constexpr int TNMAX = 256;                     // columns (paths q) per tile
-constexpr int STAGES = 4;
 constexpr int ROWB = 64;                       // bytes of K per operand row in a stage
 constexpr int A_PLANE = TM * ROWB;             // 8 KB
 constexpr int B_PLANE = TNMAX * ROWB;          // 16 KB
-constexpr int STAGE_BYTES = 2 * B_PLANE + 2 * A_PLANE;   // 48 KB: Br, Bi, Ar, Ai
 constexpr int NTHREADS = 320;
 constexpr int EPI_THREADS = 256;
 constexpr uint32_t TMEM_COLS = 512;
+constexpr int MAX_STAGES = 4;
+
+// Ring geometry.  One-product forms: 4 stages of Br, Bi (256 rows) and Ar, Ai (48 KB).
+// Hi/lo pair form (128-column windows only): 3 stages of Br, Bi, Br', Bi', Ar, Ai, Ar',
+// Ai' (' = low halves; 8 planes of 128 rows, 64 KB).
+template <bool SPLIT>
+struct Ring {
+    static constexpr int stages = SPLIT ? 3 : 4;
+    static constexpr int stage_bytes = SPLIT ? 8 * A_PLANE : 2 * B_PLANE + 2 * A_PLANE;
+};
+
+// Hi/lo pair form: k-blocks (32 frames each) per TMEM partial sum.  Each partial is a
+// fresh MMA accumulation over 64 frames; the epilogue adds the partials into FP32
+// register totals, so no tensor-core accumulation runs longer than 24 MMAs.
+constexpr int CHUNK_KB = 2;
 
 constexpr int IRING = 4;   // claimed work items in flight between the roles
 
 struct TcSmem {
-    uint64_t full[STAGES];
-    uint64_t empty[STAGES];
+    uint64_t full[MAX_STAGES];
+    uint64_t empty[MAX_STAGES];
     uint64_t acc_full[2];
     uint64_t acc_empty[2];
     uint64_t item_full[IRING];    // producer -> MMA + epilogue: item index published
@@ -71,10 +95,84 @@ __device__ __forceinline__ bool item_feeds(const Group& gr, const RunInfo& run)
     return (gr.ja >= run.j0 && gr.ja < run.j1) || (gr.jb >= run.j0 && gr.jb < run.j1);
 }
 
+// Ultrafine channels of a group that carry weight (the others are skipped).
+__device__ __forceinline__ int live_channels(const XArgs& a, const Group& gr)
+{
+    int live = 0;
+    for (int c = gr.c0; c < gr.c1; ++c) live += __ldg(&a.gain[c]) != 0.0f;
+    return live;
+}
+
+// Add coef x (re, im) of row p and the 8 consecutive columns q = qc .. qc + 7 into the
+// output channels ja / jb that the group feeds (MWAX_ORDER), or store where this group is
+// the channel's first.  Every load of the old values is issued before any store, so the
+// read-modify-writes overlap instead of serialising.
+__device__ __forceinline__ void emit8(const XArgs& a, const Group& gr, bool use_a, bool use_b, float2* ob, int p,
+                                      int qc, const float (&re)[8], const float (&im)[8])
+{
+    const int T = a.T, M = a.M, n = a.n, first_store = a.first_store;
+    const int ti = p >> 1;
+    int off[8];
+    float2 va[8], vb[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int q = qc + i;
+        const int tj = q >> 1;
+        const bool okq = q < n && ti <= tj;
+        const int pol = ((p & 1) << 1) | (q & 1);
+        off[i] = okq ? (int)(baseline_of(ti, tj, T) * M * 4 + pol) : -1;
+        va[i] = (okq && use_a && !(gr.first_a & first_store)) ? ob[off[i] + gr.ja * 4] : make_float2(0.f, 0.f);
+        vb[i] = (okq && use_b && !(gr.first_b & first_store)) ? ob[off[i] + gr.jb * 4] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        if (off[i] < 0) continue;
+        const float vi = (p == qc + i) ? 0.0f : im[i];   // autocorrelation: exactly real
+        if (use_a) ob[off[i] + gr.ja * 4] = make_float2(fmaf(gr.ca, re[i], va[i].x), fmaf(gr.ca, vi, va[i].y));
+        if (use_b) ob[off[i] + gr.jb * 4] = make_float2(fmaf(gr.cb, re[i], vb[i].x), fmaf(gr.cb, vi, vb[i].y));
+    }
+}
+
+// Write-out of row p's columns [col, col + 32 pieces) of the accumulator whose real part
+// starts at TMEM column re0 (imaginary part im_off further on): scale (post_scale, and the
+// e4m3 scales of p and q for FP8), then emit8.  Every lane of the warp takes part in the
+// TMEM loads.
+__device__ __forceinline__ void drain(const XArgs& a, const Group& gr, bool use_a, bool use_b, float2* ob, int p,
+                                      int q0, uint32_t tlane, uint32_t re0, uint32_t im_off, int col, int pieces,
+                                      float sp, const float* qscale)
+{
+    const int n = a.n;
+#pragma unroll 1
+    for (int ch = 0; ch < pieces; ++ch) {
+        const int c = col + ch * 32;
+        uint32_t vr[32], vi[32];
+        tc::tmem_ld32(tlane + re0 + c, vr);
+        tc::tmem_ld32(tlane + re0 + c + im_off, vi);
+        tc::tmem_wait_ld();
+        if (p >= n) continue;
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            float re[8], im[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int q = q0 + c + h * 8 + i;
+                float s = sp;
+                if (qscale != nullptr) s *= (q < n) ? e4m3_scale(__ldg(qscale + q)) : 0.0f;
+                re[i] = __uint_as_float(vr[h * 8 + i]) * s;
+                im[i] = __uint_as_float(vi[h * 8 + i]) * s;
+            }
+            emit8(a, gr, use_a, use_b, ob, p, q0 + c + h * 8, re, im);
+        }
+    }
+}
+
+template <bool SPLIT>
 __global__ void __launch_bounds__(NTHREADS, 1)
     xstep_tc_kernel(const __grid_constant__ XLaunch L, const XItem* __restrict__ items, int n_items, int* counter,
                     int* status, unsigned int spin_limit, int dbuf)
 {
+    constexpr int STAGES = Ring<SPLIT>::stages;
+    constexpr int STAGE_BYTES = Ring<SPLIT>::stage_bytes;
     const XJob* jobs = L.jobs;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* ring = reinterpret_cast<unsigned char*>(
@@ -83,6 +181,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const long long lim = (long long)spin_limit * 1000LL;   // cycles
+    if (SPLIT) dbuf = 1;   // the partial sums always alternate between two buffers
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -137,11 +236,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tc::prefetch_tmap(tm);
                 const int4 tile = a.tiles[w.tile];
                 const RunInfo run = a.runs[w.run];
-                const int KF = (J->op == 0) ? 32 : 64;   // frames per 64-byte operand row
+                const int KF = (J->op == 1) ? 64 : 32;   // frames per 64-byte operand row
                 const int nkb = (int)((a.klen + KF - 1) / KF);
                 const int nbox = tile.z / TM;             // 128-row boxes of the B window
                 const bool a_in_b = tile.w != 0;
-                const uint32_t bytes = (uint32_t)(2 * nbox * A_PLANE + (a_in_b ? 0 : 2 * A_PLANE));
+                const uint32_t bytes = SPLIT ? (uint32_t)((a_in_b ? 4 : 8) * A_PLANE)
+                                             : (uint32_t)(2 * nbox * A_PLANE + (a_in_b ? 0 : 2 * A_PLANE));
+                const int klo = (int)a.Kpad;   // hi/lo pairs: the low halves start Kpad frames into a row
                 for (int g = run.g0; g < run.g1 && !*abort; ++g) {
                     const Group gr = a.groups[g];
                     if (!item_feeds(gr, run)) continue;
@@ -153,13 +254,28 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             unsigned char* st = ring + stage * STAGE_BYTES;
                             uint64_t* fb = &S.full[stage];
                             tc::mbar_arrive_expect_tx(fb, bytes);
-                            for (int b = 0; b < nbox; ++b) {
-                                tc::tma_load_3d(st + b * A_PLANE, tm, fb, kb * KF, tile.y + b * TM, zr);
-                                tc::tma_load_3d(st + B_PLANE + b * A_PLANE, tm, fb, kb * KF, tile.y + b * TM, zi);
-                            }
-                            if (!a_in_b) {
-                                tc::tma_load_3d(st + 2 * B_PLANE, tm, fb, kb * KF, tile.x, zr);
-                                tc::tma_load_3d(st + 2 * B_PLANE + A_PLANE, tm, fb, kb * KF, tile.x, zi);
+                            if (SPLIT) {
+                                const int kx = kb * KF, kl = klo + kb * KF;
+                                tc::tma_load_3d(st, tm, fb, kx, tile.y, zr);
+                                tc::tma_load_3d(st + A_PLANE, tm, fb, kx, tile.y, zi);
+                                tc::tma_load_3d(st + 2 * A_PLANE, tm, fb, kl, tile.y, zr);
+                                tc::tma_load_3d(st + 3 * A_PLANE, tm, fb, kl, tile.y, zi);
+                                if (!a_in_b) {
+                                    tc::tma_load_3d(st + 4 * A_PLANE, tm, fb, kx, tile.x, zr);
+                                    tc::tma_load_3d(st + 5 * A_PLANE, tm, fb, kx, tile.x, zi);
+                                    tc::tma_load_3d(st + 6 * A_PLANE, tm, fb, kl, tile.x, zr);
+                                    tc::tma_load_3d(st + 7 * A_PLANE, tm, fb, kl, tile.x, zi);
+                                }
+                            } else {
+                                for (int b = 0; b < nbox; ++b) {
+                                    tc::tma_load_3d(st + b * A_PLANE, tm, fb, kb * KF, tile.y + b * TM, zr);
+                                    tc::tma_load_3d(st + B_PLANE + b * A_PLANE, tm, fb, kb * KF, tile.y + b * TM,
+                                                    zi);
+                                }
+                                if (!a_in_b) {
+                                    tc::tma_load_3d(st + 2 * B_PLANE, tm, fb, kb * KF, tile.x, zr);
+                                    tc::tma_load_3d(st + 2 * B_PLANE + A_PLANE, tm, fb, kb * KF, tile.x, zi);
+                                }
                             }
                             issued_phase[stage] = (int)phase;
                             if (++stage == STAGES) {
@@ -184,7 +300,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             int stage = 0;
-            uint32_t phase = 0, gcount = 0;   // gcount: groups accumulated so far
+            uint32_t phase = 0, gcount = 0;   // gcount: accumulator uses so far (groups; chunks for pairs)
             int cur_b = 0;
             uint32_t cur_ph = 0;
             const uint32_t sbase = tc::smem_u32(ring);
@@ -206,13 +322,75 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int op = J->op;
                 const int4 tile = a.tiles[w.tile];
                 const RunInfo run = a.runs[w.run];
-                const int KF = (op == 0) ? 32 : 64;
+                const int KF = (op == 1) ? 64 : 32;
                 const int nkb = (int)((a.klen + KF - 1) / KF);
                 const bool a_in_b = tile.w != 0;
                 const uint32_t id = tc::idesc(0, TM, tile.z, false), id_neg = tc::idesc(0, TM, tile.z, true);
                 for (int g = run.g0; g < run.g1 && !*abort; ++g) {
                     const Group gr = a.groups[g];
                     if (!item_feeds(gr, run)) continue;
+                    if (SPLIT) {
+                        // hi/lo pairs: a fresh partial per CHUNK_KB k-blocks, alternating buffers
+                        const int total = live_channels(a, gr) * nkb;
+                        int done = 0;
+                        bool first = true;
+                        uint32_t d_re = 0, d_im = 0;
+                        for (int c = gr.c0; c < gr.c1 && !*abort; ++c) {
+                            if (__ldg(&a.gain[c]) == 0.0f) continue;
+                            for (int kb = 0; kb < nkb; ++kb) {
+                                if (done % CHUNK_KB == 0) {
+                                    cur_b = (int)(gcount & 1);
+                                    cur_ph = (gcount >> 1) & 1;
+                                    d_re = tmem + 256u * cur_b;
+                                    d_im = d_re + 128u;
+                                    if (!tc::mbar_wait(&S.acc_empty[cur_b], cur_ph ^ 1, abort, status, 4, lim)) break;
+                                    tc::fence_after();
+                                    first = true;
+                                }
+                                if (!tc::mbar_wait(&S.full[stage], phase, abort, status, 8, lim)) break;
+                                tc::fence_after();
+                                const uint32_t st = sbase + stage * STAGE_BYTES;
+                                const uint64_t brh = tc::sw64_desc(st), bih = tc::sw64_desc(st + A_PLANE);
+                                const uint64_t brl = tc::sw64_desc(st + 2 * A_PLANE);
+                                const uint64_t bil = tc::sw64_desc(st + 3 * A_PLANE);
+                                const uint64_t arh = a_in_b ? brh : tc::sw64_desc(st + 4 * A_PLANE);
+                                const uint64_t aih = a_in_b ? bih : tc::sw64_desc(st + 5 * A_PLANE);
+                                const uint64_t arl = a_in_b ? brl : tc::sw64_desc(st + 6 * A_PLANE);
+                                const uint64_t ail = a_in_b ? bil : tc::sw64_desc(st + 7 * A_PLANE);
+#pragma unroll
+                                for (int k = 0; k < ROWB / 32; ++k) {
+                                    const uint64_t off = (uint64_t)(k * 32) >> 4;
+                                    const uint32_t acc = first ? 0u : 1u;
+                                    first = false;
+                                    // (Ah + Al)(Bh + Bl)^H without the Al Bl^H term
+                                    tc::mma_f16(d_re, arh + off, brh + off, id, acc);
+                                    tc::mma_f16(d_re, aih + off, bih + off, id, 1u);
+                                    tc::mma_f16(d_re, arh + off, brl + off, id, 1u);
+                                    tc::mma_f16(d_re, aih + off, bil + off, id, 1u);
+                                    tc::mma_f16(d_re, arl + off, brh + off, id, 1u);
+                                    tc::mma_f16(d_re, ail + off, bih + off, id, 1u);
+                                    tc::mma_f16(d_im, aih + off, brh + off, id, acc);
+                                    tc::mma_f16(d_im, arh + off, bih + off, id_neg, 1u);
+                                    tc::mma_f16(d_im, aih + off, brl + off, id, 1u);
+                                    tc::mma_f16(d_im, arh + off, bil + off, id_neg, 1u);
+                                    tc::mma_f16(d_im, ail + off, brh + off, id, 1u);
+                                    tc::mma_f16(d_im, arl + off, bih + off, id_neg, 1u);
+                                }
+                                issued = true;
+                                tc::mma_commit(&S.empty[stage]);
+                                if (++stage == STAGES) {
+                                    stage = 0;
+                                    phase ^= 1;
+                                }
+                                if (++done % CHUNK_KB == 0 || done == total) {
+                                    tc::mma_commit(&S.acc_full[cur_b]);
+                                    ++gcount;
+                                }
+                            }
+                        }
+                        if (*abort) break;
+                        continue;
+                    }
                     // accumulator buffer of this group and the parity of its use
                     cur_b = dbuf ? (int)(gcount & 1) : 0;
                     cur_ph = dbuf ? ((gcount >> 1) & 1) : (gcount & 1);
@@ -292,16 +470,79 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const RunInfo run = a.runs[w.run];
             const int p0 = tile.x, q0 = tile.y, nq = tile.z;
             const int p = p0 + g4 * 32 + lane;
-            const int ti = p >> 1;
             const bool cols = half * 128 < nq;
             char* obase = a.out + (long long)w.slot * a.out_stride;
             float2* ob = reinterpret_cast<float2*>(obase);
-            const int T = a.T, M = a.M, n = a.n, first_store = a.first_store;
+            const int n = a.n;
+            const int nkb = (int)((a.klen + 31) / 32);   // pairs: FP16, 32 frames per k-block
             for (int g = run.g0; g < run.g1 && !*abort; ++g) {
                 const Group gr = a.groups[g];
                 if (!item_feeds(gr, run)) continue;
                 const bool use_a = gr.ja >= run.j0 && gr.ja < run.j1;
                 const bool use_b = gr.jb >= run.j0 && gr.jb < run.j1;
+                const uint32_t tlane = tmem + ((uint32_t)(g4 * 32) << 16);
+                if (SPLIT) {
+                    // columns [64 half, 64 half + 64) of the 128-column window, summed over
+                    // the group's chunk partials in FP32 registers; the totals go back into
+                    // the last partial's buffer (still held) for the write-out
+                    const int col0 = half * 64;
+                    const int nch = (live_channels(a, gr) * nkb + CHUNK_KB - 1) / CHUNK_KB;
+                    float tr[64], tq[64];
+#pragma unroll
+                    for (int i = 0; i < 64; ++i) {
+                        tr[i] = 0.0f;
+                        tq[i] = 0.0f;
+                    }
+                    bool ok = true;
+                    int b = 0;
+                    for (int ck = 0; ck < nch; ++ck) {
+                        b = (int)(gcount & 1);
+                        const uint32_t ph = (gcount >> 1) & 1;
+                        ok = tc::mbar_wait(&S.acc_full[b], ph, abort, status, 16, lim);
+                        if (!__all_sync(0xffffffffu, ok)) {
+                            ok = false;
+                            break;
+                        }
+                        tc::fence_after();
+                        const uint32_t taddr = tlane + 256u * b + col0;
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            uint32_t vr[16], vi[16];
+                            tc::tmem_ld16(taddr + 16 * h, vr);
+                            tc::tmem_ld16(taddr + 128 + 16 * h, vi);
+                            tc::tmem_wait_ld();
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) {
+                                tr[16 * h + i] += __uint_as_float(vr[i]);
+                                tq[16 * h + i] += __uint_as_float(vi[i]);
+                            }
+                        }
+                        if (ck + 1 < nch) {
+                            tc::fence_before();
+                            tc::mbar_arrive(&S.acc_empty[b]);
+                            ++gcount;
+                        }
+                    }
+                    if (!ok) break;
+                    if (nch == 0) continue;   // no channel with weight: nothing accumulated
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        uint32_t vr[16], vi[16];
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            vr[i] = __float_as_uint(tr[16 * h + i]);
+                            vi[i] = __float_as_uint(tq[16 * h + i]);
+                        }
+                        tc::tmem_st16(tlane + 256u * b + col0 + 16 * h, vr);
+                        tc::tmem_st16(tlane + 256u * b + 128 + col0 + 16 * h, vi);
+                    }
+                    tc::tmem_wait_st();
+                    drain(a, gr, use_a, use_b, ob, p, q0, tlane, 256u * b, 128u, col0, 2, a.post_scale, nullptr);
+                    tc::fence_before();
+                    tc::mbar_arrive(&S.acc_empty[b]);
+                    ++gcount;
+                    continue;
+                }
                 const int b = dbuf ? (int)(gcount & 1) : 0;
                 const uint32_t ph = dbuf ? ((gcount >> 1) & 1) : (gcount & 1);
                 const uint32_t re0 = dbuf ? 256u * b : 0u, im_off = dbuf ? 128u : 256u;
@@ -316,50 +557,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         sp *= (p < n) ? e4m3_scale(__ldg(sc + p)) : 0.0f;
                         qscale = sc;
                     }
-#pragma unroll 1
-                    for (int ch = 0; ch < 4; ++ch) {
-                        const int col = half * 128 + ch * 32;
-                        uint32_t vr[32], vi[32];
-                        const uint32_t taddr = tmem + ((uint32_t)(g4 * 32) << 16) + re0 + col;
-                        tc::tmem_ld32(taddr, vr);
-                        tc::tmem_ld32(taddr + im_off, vi);
-                        tc::tmem_wait_ld();
-                        if (p >= n) continue;
-                        // 8 columns at a time: issue every load of the old values before any
-                        // store, so the read-modify-writes overlap instead of serialising
-#pragma unroll
-                        for (int h = 0; h < 4; ++h) {
-                            int off[8];
-                            float2 va[8], vb[8];
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) {
-                                const int q = q0 + col + h * 8 + i;
-                                const int tj = q >> 1;
-                                const bool okq = q < n && ti <= tj;
-                                const int pol = ((p & 1) << 1) | (q & 1);
-                                off[i] = okq ? (int)(baseline_of(ti, tj, T) * M * 4 + pol) : -1;
-                                va[i] = (okq && use_a && !(gr.first_a & first_store)) ? ob[off[i] + gr.ja * 4]
-                                                                                      : make_float2(0.f, 0.f);
-                                vb[i] = (okq && use_b && !(gr.first_b & first_store)) ? ob[off[i] + gr.jb * 4]
-                                                                                      : make_float2(0.f, 0.f);
-                            }
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) {
-                                if (off[i] < 0) continue;
-                                const int q = q0 + col + h * 8 + i;
-                                float s = sp;
-                                if (op == 1) s *= e4m3_scale(__ldg(qscale + q));
-                                const float re = __uint_as_float(vr[h * 8 + i]) * s;
-                                const float im = (p == q) ? 0.0f : __uint_as_float(vi[h * 8 + i]) * s;
-                                if (use_a)
-                                    ob[off[i] + gr.ja * 4] =
-                                        make_float2(fmaf(gr.ca, re, va[i].x), fmaf(gr.ca, im, va[i].y));
-                                if (use_b)
-                                    ob[off[i] + gr.jb * 4] =
-                                        make_float2(fmaf(gr.cb, re, vb[i].x), fmaf(gr.cb, im, vb[i].y));
-                            }
-                        }
-                    }
+                    drain(a, gr, use_a, use_b, ob, p, q0, tlane, re0, im_off, half * 128, 4, sp, qscale);
                 }
                 tc::fence_before();
                 tc::mbar_arrive(&S.acc_empty[b]);
@@ -376,7 +574,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
 }
 
-constexpr size_t tc_smem_bytes() { return 1024 + STAGES * STAGE_BYTES + sizeof(TcSmem); }
+template <bool SPLIT>
+constexpr size_t tc_smem_bytes()
+{
+    return 1024 + Ring<SPLIT>::stages * Ring<SPLIT>::stage_bytes + sizeof(TcSmem);
+}
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
@@ -425,13 +627,15 @@ cudaError_t make_simt_tmap(CUtensorMap* map, const void* Y, long long Kpad, int 
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t launch_xstep_tc(const XLaunch& L, const XItem* items, int n_items, int* counter, int* status,
-                            cudaStream_t s)
+template <bool SPLIT>
+cudaError_t launch_tc_kernel(const XLaunch& L, const XItem* items, int n_items, int* counter, int* status, int dbuf,
+                             cudaStream_t s)
 {
     static bool attr_done = false;
-    const size_t smem = tc_smem_bytes();
+    const size_t smem = tc_smem_bytes<SPLIT>();
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(xstep_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(xstep_tc_kernel<SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
@@ -441,11 +645,27 @@ cudaError_t launch_xstep_tc(const XLaunch& L, const XItem* items, int n_items, i
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
+    xstep_tc_kernel<SPLIT><<<n_items < sms ? n_items : sms, NTHREADS, smem, s>>>(L, items, n_items, counter, status,
+                                                                                 2000000u, dbuf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xstep_tc(const XLaunch& L, const XItem* items, int n_items, int* counter, int* status,
+                            cudaStream_t s)
+{
+    // one kernel form per launch: every job FP16 / e4m3, or every job FP16 hi/lo pairs
+    // (these on 128-column windows only)
+    int pairs = -1;
+    for (int j = 0; j < L.n_jobs; ++j) {
+        const int pj = L.jobs[j].op == 2 ? 1 : 0;
+        if (pairs >= 0 && pj != pairs) return cudaErrorInvalidValue;
+        pairs = pj;
+        if (pj && L.jobs[j].max_cols > TM) return cudaErrorInvalidValue;
+    }
+    if (pairs == 1) return launch_tc_kernel<true>(L, items, n_items, counter, status, 1, s);
     int dbuf = 1;   // double-buffered accumulators when every job's tiles are at most 128 columns wide
     for (int j = 0; j < L.n_jobs; ++j) dbuf &= (L.jobs[j].max_cols <= TM) ? 1 : 0;
-    xstep_tc_kernel<<<n_items < sms ? n_items : sms, NTHREADS, smem, s>>>(L, items, n_items, counter, status,
-                                                                          2000000u, dbuf);
-    return cudaGetLastError();
+    return launch_tc_kernel<false>(L, items, n_items, counter, status, dbuf, s);
 }
 
 // Tile list of the tensor-core X-step: for each 128-row block, column windows of

@@ -4,8 +4,8 @@ as the benchmark runs it (same plan description and 48 GiB workspace, so the sam
 launches), checked against the FP64 oracle on sampled outputs that the oracle computes one
 by one: random (integration, baseline, channel, pol) entries plus the parallel-pol
 autocorrelations that the parity metric divides by.  Bars as in the small-case tests:
-FP32 1e-5, FP16 2e-3, FP8 3e-2 of the auto scale; the integer mode (no FFT, 1 s
-integrations) bit-exact."""
+FP32 and FP16 hi/lo pairs 1e-5, FP16 2e-3, FP8 3e-2 of the auto scale; the integer mode
+(no FFT, 1 s integrations) bit-exact."""
 import numpy as np
 import pytest
 
@@ -19,7 +19,7 @@ torch = pytest.importorskip("torch")
 T, N, F, T_INT, S = 256, 128, 4, 0.5, 10_240_000
 SEED = 0x4D574159
 WORKSPACE = 48 << 30   # as bench.py: all 16 integrations' operands resident, one launch each
-TOL = {mw.MWAX_FP32: 1e-5, mw.MWAX_FP16: 2e-3, mw.MWAX_FP8: 3e-2}
+TOL = {mw.MWAX_FP32: 1e-5, mw.MWAX_FP16: 2e-3, mw.MWAX_FP8: 3e-2, mw.MWAX_FP16X3: 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -80,7 +80,7 @@ def metric(got, want, req, n_main):
 
 
 @pytest.mark.parametrize("prec", [pytest.param(mw.MWAX_FP32, id="fp32"), pytest.param(mw.MWAX_FP16, id="fp16"),
-                                  pytest.param(mw.MWAX_FP8, id="fp8")])
+                                  pytest.param(mw.MWAX_FP8, id="fp8"), pytest.param(mw.MWAX_FP16X3, id="fp16x3")])
 def test_fullsize_sampled(prec, full_input):
     volt, delay, dev = full_input
     desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=T_INT, samples_per_call=S,

@@ -548,7 +548,8 @@ def run_mine(args, world, rank, local):
         plan = mw.mwax_plan_create_ex(desc)
         # one-off autotune on this workload (F-step variant, run length, tensor-core window),
         # as a user does once per shape; the timed steps below run the chosen tuning
-        tuning = mw.mwax_plan_autotune(plan, dev_volt, ddelay, mw.empty_output(plan))
+        tuning = (mw.mwax_plan_get_tuning(plan) if args.no_tune
+                  else mw.mwax_plan_autotune(plan, dev_volt, ddelay, mw.empty_output(plan)))
         torch.cuda.empty_cache()
         clocks = ClockSampler(local) if form == headline else None
         ms, stages, out, ck = time_plan(mw, torch, plan, dev_volt, ddelay, args.steps, args.warmup, world, clocks)
@@ -705,6 +706,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16x3", "fp16", "fp8", "int8"],
                     help="headline precision (the full-array plain form is FP32); the other forms are timed beside it")
     ap.add_argument("--no-forms", action="store_true", help="time the headline precision only")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep each plan's default tuning (no autotune launches; for profiler captures)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 24-channel batched measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the real-time serving measurement")
     ap.add_argument("--no-ext", action="store_true", help="skip the roadmap extensions and the beamformer")

@@ -22,6 +22,7 @@ MIX = [
     (12, 64, 2, 0.05, 64_000, mw.MWAX_FP32, 4),
     (30, 1, 1, 0.025, 64_000, mw.MWAX_INT8, 1024),
     (70, 6400, 50, 0.05, 64_000, mw.MWAX_FP8, 1024),
+    (24, 128, 4, 0.05, 128_000, mw.MWAX_FP16X3, 16),
 ]
 
 
@@ -62,7 +63,7 @@ def test_batch_equals_alone_and_graph_replay():
 def test_autotune_keeps_parity():
     T, N, F, t, S = 24, 128, 4, 0.05, 128_000
     volt, delay = workload(600, T, S, delay="linear")
-    for prec, tol in ((mw.MWAX_FP16, 2e-3), (mw.MWAX_FP32, 1e-5)):
+    for prec, tol in ((mw.MWAX_FP16, 2e-3), (mw.MWAX_FP32, 1e-5), (mw.MWAX_FP16X3, 1e-5)):
         p = mw.mwax_plan_create_ex(mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=t, samples_per_call=S,
                                                precision=prec, sky_freq_hz=synth.SKY_FREQ_HZ))
         mw.mwax_plan_set_stream(p)

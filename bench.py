@@ -592,7 +592,15 @@ def run_mine(args, world, rank, local):
                           "traffic": None if tps is None else tps * n_ints * args.steps / x_n,
                           "peak_kind": peak_kind,
                           "per_launch": f"{x_per_launch:.4g} flop (8 x pairs x frames x {used} used bins)",
-                          "avg_launch_ms": x_avg_ms},
+                          "avg_launch_ms": x_avg_ms,
+                          # what the kernel executes with this tuning: whole tiles (pairs below
+                          # the diagonal and past n included), K blocks, shared boundary channels
+                          "issued_per_launch": info["x_flop_issued"] * args.steps / x_n,
+                          "issued_achieved": info["x_flop_issued"] * args.steps / x_n / (x_avg_ms * 1e-3) / 1e12,
+                          "issued_frac": info["x_flop_issued"] * args.steps / x_n / (x_avg_ms * 1e-3) / 1e12
+                          * (3.0 if form == "fp16x3" else 1.0) / x_peak,
+                          "issued_note": "issued_frac counts the three FP16 products per term of the hi/lo form"
+                          if form == "fp16x3" else "issued_frac = issued_achieved / peak"},
              "roofline_fstep": {"bound": "hbm", "achieved": f_bytes / (f_ms / args.steps * 1e-3) / 1e9,
                                 "peak": pk["hbm_gbs"], "unit": "GB/s",
                                 "frac": f_bytes / (f_ms / args.steps * 1e-3) / 1e9 / pk["hbm_gbs"],

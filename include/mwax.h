@@ -99,6 +99,16 @@ typedef struct {
     size_t output_bytes;         /* n_ints * (vis_set_bytes + weights_bytes)  */
     size_t workspace_bytes;      /* device memory the plan holds              */
     int precision;
+    double x_flop_alg;           /* X-step work per call: 8 flop per complex multiply-
+                                    accumulate over the n (n + 1) / 2 unique path pairs,
+                                    each frame and each ultrafine channel feeding an
+                                    output channel (exactly once)                      */
+    double x_flop_issued;        /* the same count over what the X kernels execute with
+                                    the current tuning: whole tiles (including the pairs
+                                    below the diagonal and past n that a tile covers),
+                                    frames rounded up to the kernel's K block, boundary
+                                    channels of two runs computed by both.  FP16X3
+                                    issues three FP16 products per term on top of it  */
 } mwax_plan_info;
 
 /*

@@ -62,7 +62,8 @@ class _CInfo(ctypes.Structure):
                 ("frames_per_int", ctypes.c_longlong), ("n_ints", ctypes.c_longlong),
                 ("input_bytes", ctypes.c_size_t), ("vis_set_bytes", ctypes.c_size_t),
                 ("weights_bytes", ctypes.c_size_t), ("output_bytes", ctypes.c_size_t),
-                ("workspace_bytes", ctypes.c_size_t), ("precision", ctypes.c_int)]
+                ("workspace_bytes", ctypes.c_size_t), ("precision", ctypes.c_int),
+                ("x_flop_alg", ctypes.c_double), ("x_flop_issued", ctypes.c_double)]
 
 
 class Tuning(ctypes.Structure):
@@ -241,9 +242,13 @@ class Plan:
     def __init__(self, handle: int, desc: PlanDesc):
         self.handle = handle
         self.desc = desc
+
+    @property
+    def info(self) -> dict:
+        """mwax_plan_info as a dict, read afresh (issued flops follow the tuning)."""
         info = _CInfo()
-        _check(load_library().mwax_plan_get_info(handle, ctypes.byref(info)))
-        self.info = {k: getattr(info, k) for k, _ in _CInfo._fields_}
+        _check(load_library().mwax_plan_get_info(self.handle, ctypes.byref(info)))
+        return {k: getattr(info, k) for k, _ in _CInfo._fields_}
 
     def __del__(self):
         h, self.handle = getattr(self, "handle", None), None

@@ -844,6 +844,32 @@ mwax_status enqueue_xstep_single(mwax_plan* p, const LaunchGroup& g, const XArgs
 
 }  // namespace mwax
 
+namespace mwax {
+
+// X-step flops of one call (8 per complex multiply-accumulate): the algorithmic count over
+// unique pairs, frames and feeding channels, and what the kernels execute with the
+// current tiles and runs (see mwax_plan_info).
+void x_flops(const mwax_plan& p, double* alg, double* issued)
+{
+    double used = 0.0;
+    for (const Group& gr : p.h_groups)
+        for (int c = gr.c0; c < gr.c1; ++c) used += p.h_gain[c] > 0.0f;
+    *alg = 8.0 * ((double)p.n * (p.n + 1) / 2) * (double)p.K * (double)p.n_ints * used;
+    double tile_pairs = 0.0;
+    for (const int4& t : p.h_tiles) {
+        if (p.tensor_cores) tile_pairs += 128.0 * t.z;                         // whole MMA rectangles
+        else tile_pairs += 64.0 * 64.0 * (t.w ? 23.0 / 32.0 : 1.0);          // diagonal sub-block skip
+    }
+    double run_chan = 0.0;
+    for (const RunInfo& r : p.h_runs) run_chan += run_bins(p, r.j0, r.j1);
+    const long long KF = (p.prec == MWAX_FP8) ? 64 : 32;
+    double frames = 0.0;
+    for (const LaunchGroup& g : plan_groups(&p)) frames += (double)g.nslots * ((g.klen + KF - 1) / KF * KF);
+    *issued = 8.0 * tile_pairs * run_chan * frames;
+}
+
+}  // namespace mwax
+
 extern "C" {
 
 const char* mwax_version(void) { return "mwax-b300 0.1 (sm_103a)"; }
@@ -892,6 +918,7 @@ mwax_status mwax_plan_get_info(const mwax_plan* p, mwax_plan_info* info)
     info->output_bytes = (size_t)p->n_ints * p->int_stride;
     info->workspace_bytes = p->Y_bytes;
     info->precision = p->prec;
+    mwax::x_flops(*p, &info->x_flop_alg, &info->x_flop_issued);
     return MWAX_OK;
 }
 

@@ -13,9 +13,9 @@ from _parity import oracle_desc, parity_error, sample_requests, sampled_error, w
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-TOL = {mw.MWAX_FP32: 1e-5, mw.MWAX_FP16: 2e-3, mw.MWAX_FP8: 3e-2}
+TOL = {mw.MWAX_FP32: 1e-5, mw.MWAX_FP16: 2e-3, mw.MWAX_FP8: 3e-2, mw.MWAX_FP16X3: 1e-5}
 FLOAT = [pytest.param(mw.MWAX_FP32, id="fp32"), pytest.param(mw.MWAX_FP16, id="fp16"),
-         pytest.param(mw.MWAX_FP8, id="fp8")]
+         pytest.param(mw.MWAX_FP8, id="fp8"), pytest.param(mw.MWAX_FP16X3, id="fp16x3")]
 
 
 def run(desc, volt, delay):
@@ -89,3 +89,19 @@ def test_512_tiles_int8_sampled(array_512):
     got = vis[req[:, 0], req[:, 1], req[:, 3]]
     assert np.array_equal(got[:, 0], want.real.astype(np.int64))
     assert np.array_equal(got[:, 1], want.imag.astype(np.int64))
+
+
+@pytest.mark.parametrize("prec,issued_pairs,frames", [
+    (mw.MWAX_FP32, 64 * 64 * 23 // 32, 4000),    # one diagonal 64 x 64 tile, 9 of 32 sub-blocks skipped
+    (mw.MWAX_FP16, 128 * 128, 4000),            # one 128 x 128 MMA tile (rows and columns past n = 32)
+    (mw.MWAX_FP8, 128 * 128, 4032),             # K blocks of 64 frames
+    (mw.MWAX_FP16X3, 128 * 128, 4000)])
+def test_plan_info_flop_counts(prec, issued_pairs, frames):
+    # 16 tiles, 0.4 s, N = 128, F = 1: 528 unique pairs, 4,000 frames, 128 channels each
+    # fed by one bin (no run shares a boundary channel)
+    plan = mw.mwax_plan_create_ex(mw.PlanDesc(n_tiles=16, fft_len=128, fine_avg=1, int_time_s=0.4,
+                                              samples_per_call=512_000, precision=prec))
+    info = plan.info
+    assert info["x_flop_alg"] == 8.0 * 528 * 4000 * 128
+    assert info["x_flop_issued"] == 8.0 * issued_pairs * frames * 128
+    plan.close()

@@ -109,6 +109,18 @@ def test_fft_lengths(N, F, prec):
     check(desc, volt, delay)
 
 
+@pytest.mark.parametrize("prec", [pytest.param(mw.MWAX_FP32, id="fp32"), pytest.param(mw.MWAX_FP16X3, id="fp16x3")])
+def test_one_8s_integration(prec):
+    # the longest integration of the configurations: 80,000 frames of 128 points summed into
+    # each visibility (FP32 bar: the two-level sums of both FP32-level forms must hold it
+    # over 16x the frames of the 0.5 s cases)
+    T, N, F, t_int, S = 6, 128, 4, 8.0, 10_240_000
+    volt, delay = workload(15, T, S, delay="linear")
+    desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=t_int, samples_per_call=S,
+                       sky_freq_hz=synth.SKY_FREQ_HZ, precision=prec)
+    check(desc, volt, delay)
+
+
 @pytest.mark.parametrize("prec", FLOAT_PRECS)
 def test_no_delay_and_zero_delay_identical(prec):
     T, N = 4, 64

@@ -243,8 +243,8 @@ mwax_status mwax_plan_stage_times(mwax_plan* plan, double ms[3], long long launc
  * for N = 32..512; the generic kernel elsewhere), 1 = generic shared-memory Stockham
  * kernel.  run_len: output channels per X-step work item (0 = the plan's own choice: the
  * run length whose longest-first schedule of the work items on the GPU's resident CTA
- * slots is shortest).  window: column width of a tensor-core X-step tile, 128 or 256.
- * ms: device time of one call measured by the autotuner. */
+ * slots is shortest).  window: column width of a tensor-core X-step tile, 128 or 256
+ * (MWAX_FP16X3 always runs 128).  ms: device time of one call measured by the autotuner. */
 typedef struct {
     int fstep_variant;
     int run_len;
@@ -257,7 +257,7 @@ typedef struct {
  * three calls per candidate, timed with CUDA events on the plan's stream (the fastest of
  * the three counts).  First the F-step variant (radix-32 or generic, for N = 32..512) with
  * the plan's current X-step choice; then, with the faster variant, the tile window (256 or
- * 128, tensor-core forms) x the run length (the plan's modelled choice, 3, 5, 11 and all
+ * 128, FP16 / FP8 forms; 128 only for MWAX_FP16X3) x the run length (the plan's modelled choice, 3, 5, 11 and all
  * output channels).  Keeps the fastest.  Synchronous.  vis_out is overwritten with a valid
  * result.  best (may be NULL) receives the choice and its time.
  */
@@ -274,8 +274,8 @@ mwax_status mwax_plan_get_tuning(const mwax_plan* plan, mwax_tuning* tuning);
  * integration times and precisions) correlated together on one stream.  Each call runs
  * every plan once: per round, the plans' F-steps on auxiliary streams, then ONE
  * persistent tcgen05 X-step launch over all FP16 / FP8 plans' work (one job per plan,
- * work items claimed dynamically, most expensive first); FP32 and integer-mode plans run
- * their own X-steps.  The paper processes one coarse channel per server (Sec. 2.1); a
+ * work items claimed dynamically, most expensive first); FP32, FP16X3 and integer-mode
+ * plans run their own X-steps.  The paper processes one coarse channel per server (Sec. 2.1); a
  * batch processes many on one GPU.  The batch references the plans (they must outlive it,
  * stay on one device and not be used on their own while the batch runs) and uses the
  * plans' workspaces.  Returns NULL on error.

@@ -48,7 +48,7 @@ WORKSPACE = 48 << 30
 # capture of the one-integration case (profiles/).  Reported only while the kernel's
 # source is byte-identical to the one captured (sha1 prefix of its .cu file).
 TRAFFIC = {"xstep_simt_kernel": ("paper_2303_11557_b300/csrc/xstep_simt.cu", "801bae888475", 6.645909e9 + 0.100315e9),
-           "xstep_tc_kernel<false> (fp16)": ("paper_2303_11557_b300/csrc/xstep_tc.cu", "afc1d7f6e301",
+           "xstep_tc_kernel<0> (fp16)": ("paper_2303_11557_b300/csrc/xstep_tc.cu", "afc1d7f6e301",
                                              (5.340589e9 + 0.290356e9) / 3)}   # 3-slot capture
 
 
@@ -571,8 +571,9 @@ def run_mine(args, world, rank, local):
             peak_kind = (f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {pk.get('sm_max_mhz')} MHz "
                          f"({pk_kind} max clock)")
         else:
-            xkern = {"fp16": "xstep_tc_kernel<false> (fp16)", "fp8": "xstep_tc_kernel<false> (e4m3)",
-                     "fp16x3": "xstep_tc_kernel<true> (fp16 hi/lo pairs)", "int8": "xstep_int8_kernel"}[form]
+            xkern = {"fp16": "xstep_tc_kernel<0> (fp16)", "fp8": "xstep_tc_kernel<0> (e4m3)",
+                     "fp16x3": "xstep_tc_kernel<1> (fp16 hi/lo pairs)",
+                     "int8": "xstep_tc_kernel<2> (integer mode)"}[form]
             bound = "tensor"
             base = pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
             ratio = 2.0 if form == "fp8" else 1.0

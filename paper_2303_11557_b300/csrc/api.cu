@@ -395,7 +395,10 @@ mwax_status setup(mwax_plan& p)
 
     // workspace: operand slots
     const size_t limit = p.desc.workspace_limit ? p.desc.workspace_limit : ((size_t)16 << 30);
-    const long long Kpad_full = (p.K + kKAlign - 1) / kKAlign * kKAlign;
+    // integer mode: frames come in whole K tiles
+    const long long align = (p.prec == MWAX_INT8) ? kIntKTile : kKAlign;
+    p.ktile = (p.prec == MWAX_INT8) ? kIntKTile : 0;
+    const long long Kpad_full = (p.K + align - 1) / align * align;
     const size_t per_slot = (size_t)p.N * 2 * p.n * Kpad_full * p.elem_bytes;
     if (per_slot <= limit) {
         p.slots = std::min<long long>(p.n_ints, (long long)(limit / per_slot));
@@ -404,8 +407,8 @@ mwax_status setup(mwax_plan& p)
         p.chunks = 1;
     } else {
         const size_t per_frame = (size_t)p.N * 2 * p.n * p.elem_bytes;
-        long long kc = (long long)(limit / per_frame) / kKAlign * kKAlign;
-        if (kc < kKAlign) return fail(MWAX_ENOMEM, "workspace_limit too small for one %d-frame chunk", kKAlign);
+        long long kc = (long long)(limit / per_frame) / align * align;
+        if (kc < align) return fail(MWAX_ENOMEM, "workspace_limit too small for one %lld-frame chunk", align);
         p.slots = 1;
         p.Kc = kc;
         p.Kpad = kc;
@@ -466,6 +469,8 @@ mwax_status setup(mwax_plan& p)
         MWAX_CUDA(make_simt_tmap(&p.tmap, p.Y, p.Kpad, p.n, p.slots * p.N * 2));
     else if (p.prec == MWAX_FP16X3)   // FP16 rows of 2 Kpad: hi frames, then lo frames
         MWAX_CUDA(make_operand_tmap(&p.tmap, p.Y, 2, 2 * p.Kpad, p.n, p.slots * p.N * 2));
+    else if (p.prec == MWAX_INT8)     // rows of one K tile: planes [slot][K tile][re/im]
+        MWAX_CUDA(make_operand_tmap(&p.tmap, p.Y, 2, p.ktile, p.n, p.slots * (p.Kpad / p.ktile) * 2));
     else
         MWAX_CUDA(make_operand_tmap(&p.tmap, p.Y, p.prec == MWAX_FP8 ? 1 : 2, p.Kpad, p.n, p.slots * p.N * 2));
 
@@ -494,8 +499,29 @@ namespace mwax {
 // same integration, which then come from L2 instead of HBM (the persistent kernel is fed by
 // HBM; this ordering took 4-5 % off its time).  CUDA cores (bound by FMA issue, not by
 // HBM): the key is the item's own cost, longest first.
+// Integer mode: samples per K segment of the tensor-core X-step (one work item each): the
+// slot's samples split evenly into segments of whole 512-sample chunks, at most 100
+// chunks (51,200 samples) each so the int32 register sums cannot overflow.
+long long int8_seg_frames(long long klen)
+{
+    const long long chunks = std::max<long long>(1, (klen + 511) / 512);
+    const long long nseg = (chunks + 99) / 100;
+    return (chunks + nseg - 1) / nseg * 512;
+}
+
 void plan_items(const mwax_plan& p, int job, long long nslots, long long klen, std::vector<std::pair<double, XItem>>& out)
 {
+    if (p.prec == MWAX_INT8) {
+        // (slot, segment) groups with all tiles side by side (they stream the same samples
+        // through L2); the key is the segment's length, so a short last segment goes last
+        const long long seg = int8_seg_frames(klen);
+        const int nseg = (int)((klen + seg - 1) / seg);
+        for (long long sl = 0; sl < nslots; ++sl)
+            for (int sg = 0; sg < nseg; ++sg)
+                for (int t = 0; t < p.n_tiles; ++t)
+                    out.push_back({(double)std::min(seg, klen - sg * seg), XItem{job, t, sg, (int)sl}});
+        return;
+    }
     const int KF = (p.prec == MWAX_FP8) ? 64 : 32;
     const double nkb = (double)((klen + KF - 1) / KF);
     std::vector<int> bins(p.n_runs, 0);
@@ -749,6 +775,7 @@ mwax_status enqueue_fstep(mwax_plan* p, const LaunchGroup& g, const int8_t* volt
     fa.n_store = (p->chunks == 1) ? g.nframes : std::min(p->Kpad, (g.nframes + kKAlign - 1) / kKAlign * kKAlign);
     fa.Kc = (p->chunks == 1) ? p->K : p->Kc;
     fa.Kpad = p->Kpad;
+    fa.ktile = p->ktile;
     fa.n = p->n;
     fa.bs = p->bs;
     fa.nu = p->nu;
@@ -786,6 +813,7 @@ XArgs make_xargs(const mwax_plan* p, const LaunchGroup& g, char* out)
     xa.out = out + g.w0 * (long long)p->int_stride;
     xa.out_stride = (long long)p->int_stride;
     xa.Kpad = p->Kpad;
+    xa.ktile = p->ktile;
     xa.klen = g.klen;
     xa.n = p->n;
     xa.T = p->T;
@@ -808,18 +836,7 @@ XArgs make_xargs(const mwax_plan* p, const LaunchGroup& g, char* out)
 mwax_status enqueue_xstep_single(mwax_plan* p, const LaunchGroup& g, const XArgs& xa_in, cudaStream_t s)
 {
     XArgs xa = xa_in;
-    if (p->prec == MWAX_INT8) {
-        // split each slot's samples into segments of whole 512-sample chunks (the exact
-        // FP32 accumulation span of the integer X-step) so the grid covers the GPU
-        // several times over
-        const long long chunks512 = (g.klen + 511) / 512;
-        const long long want =
-            std::max<long long>(1, (4LL * 148 + p->n_tiles * g.nslots - 1) / (p->n_tiles * g.nslots));
-        const long long seg_chunks = std::max<long long>(1, (chunks512 + want - 1) / want);
-        xa.seg_frames = seg_chunks * 512;
-        const int nseg = (int)((chunks512 + seg_chunks - 1) / seg_chunks);
-        MWAX_CUDA(timed(p, 2, s, [&] { return launch_xstep_int8(p->tmap, xa, p->n_tiles, nseg, (int)g.nslots, s); }));
-    } else if (p->tensor_cores) {
+    if (p->tensor_cores) {
         XItem* items = nullptr;
         int n_items = 0;
         mwax_status st = single_items(p, g.nslots, g.klen, &items, &n_items);
@@ -828,7 +845,8 @@ mwax_status enqueue_xstep_single(mwax_plan* p, const LaunchGroup& g, const XArgs
         L.n_jobs = 1;
         L.jobs[0].tmap = p->tmap;
         L.jobs[0].a = xa;
-        L.jobs[0].op = (p->prec == MWAX_FP8) ? 1 : (p->prec == MWAX_FP16X3 ? 2 : 0);
+        L.jobs[0].op = (p->prec == MWAX_FP8) ? 1 : (p->prec == MWAX_FP16X3 ? 2 : (p->prec == MWAX_INT8 ? 3 : 0));
+        if (p->prec == MWAX_INT8) L.jobs[0].a.seg_frames = int8_seg_frames(g.klen);
         L.jobs[0].max_cols = 0;
         for (const int4& tl : p->h_tiles) L.jobs[0].max_cols = std::max(L.jobs[0].max_cols, tl.z);
         MWAX_CUDA(timed(p, 2, s, [&] { return launch_xstep_tc(L, items, n_items, p->counter, p->status, s); }));

@@ -658,6 +658,19 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
 // FP32/FP16 output, the 8 samples in one data block and one operand slot) is one 16-byte
 // load and 16-byte stores per plane with the index arithmetic done once; everything else
 // (phasor e^{2 pi i nu tau}, flags, FP8 maxima, group edges) takes the per-sample path.
+// Operand element of frame k of a slot for path p (real plane; the imaginary plane is
+// *ps further on): rows of Kpad frames, or in the integer mode rows of one K tile
+// (Y[slot][K tile][plane][p][ktile]).
+__device__ __forceinline__ long long unpack_at(const FArgs& a, long long slot, long long k, int p, long long* ps)
+{
+    if (a.ktile > 0) {
+        *ps = (long long)a.n * a.ktile;
+        return ((slot * (a.Kpad / a.ktile) + k / a.ktile) * 2LL * a.n + p) * a.ktile + k % a.ktile;
+    }
+    *ps = (long long)a.n * a.Kpad;
+    return (slot * 2LL * a.n + p) * a.Kpad + k;
+}
+
 template <int OUTK>
 __global__ void __launch_bounds__(256) unpack_kernel(const FArgs a)
 {
@@ -675,8 +688,8 @@ __global__ void __launch_bounds__(256) unpack_kernel(const FArgs a)
             const int4 raw = __ldg(reinterpret_cast<const int4*>(src));
             const char2* x = reinterpret_cast<const char2*>(&raw);
             const float g = __ldg(&a.gain[0]) * (OUTK == FOUT_F16 ? a.out_scale : 1.0f);
-            const long long at = (slot * 2LL * a.n + p) * a.Kpad + k;
-            const long long ps = (long long)a.n * a.Kpad;
+            long long ps;
+            const long long at = unpack_at(a, slot, k, p, &ps);   // 8 frames in one row (tiles are multiples of 8)
             if (OUTK == FOUT_F16) {
                 __half2 re[4], im[4];
 #pragma unroll
@@ -721,8 +734,9 @@ __global__ void __launch_bounds__(256) unpack_kernel(const FArgs a)
             v = c_mul(v, make_float2(cs, sn));
         }
         const float gn = __ldg(&a.gain[0]);
-        const long long at = ((fl / a.Kc) * 2LL * a.n + p) * a.Kpad + fl % a.Kc;
-        Store<1, OUTK>::run(a, at, (long long)a.n * a.Kpad, make_float2(v.x * gn, v.y * gn), fl / a.Kc, 0, p);
+        long long ps;
+        const long long at = unpack_at(a, fl / a.Kc, fl % a.Kc, p, &ps);
+        Store<1, OUTK>::run(a, at, ps, make_float2(v.x * gn, v.y * gn), fl / a.Kc, 0, p);
     }
 }
 

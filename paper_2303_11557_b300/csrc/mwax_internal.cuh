@@ -14,6 +14,10 @@ namespace mwax {
 constexpr double kFs = 1280000.0;        // coarse-channel sample rate (Sec. 2.5)
 constexpr int kDefaultBlock = 64000;     // samples per path per 50 ms data block (Sec. 2.5)
 constexpr int kKAlign = 128;             // frames per operand row are padded to this
+// Integer mode: the K axis of the operands is cut into tiles of this many samples, laid out
+// Y[slot][K tile][plane][p][kIntKTile], so that the 128 rows of one TMA box lie within
+// 512 KB (a whole 1 s row per path would put them 2.56 MB apart, one memory page each).
+constexpr int kIntKTile = 2048;
 
 // Output-type selector of the F-step (the FP8 form quantises the FP16 output afterwards).
 // FOUT_F16X3: each value v (pre-scaled) as an FP16 pair hi = fp16(v), lo = fp16(v - hi),
@@ -62,6 +66,7 @@ struct FArgs {
     long long tab_steps;
     long long tab_step;        // samples per table entry
     const uint8_t* flags;      // [n_blocks][n] zeroing flags (nonzero: block holds no data), or nullptr
+    long long ktile;           // integer mode: K tile length (kIntKTile); 0 = rows of Kpad frames
     // set by launch_fstep from fs and N (so no kernel divides in FP64 per frame)
     double frame_dt;           // N / fs: seconds per frame
     double fs_over_n;          // fs / N: frames per second
@@ -104,11 +109,13 @@ struct XArgs {
     const float* gain;     // [N]; channels with gain 0 are skipped
     const int4* tiles;     // (p0, q0, column count, A rows inside the B window) per tile
     float post_scale;      // multiplies every product (undoes the FP16 pre-scale)
-    long long seg_frames;  // integer mode: frames per K segment (a multiple of 512)
+    long long seg_frames;  // integer mode: frames per K segment, one work item each (a multiple
+                           //   of 512, at most 51,200)
     int first_store;       // 1: a channel's first group stores (output not yet written by an
                            //    earlier frame chunk of the same integration); 0: all add
     int* status;           // device status word (bounded waits)
     unsigned int spin_limit;
+    long long ktile;       // integer mode: K tile length of the operand layout (see kIntKTile)
 };
 
 // One launch's worth of tensor-core X-step work for one plan ("job"): its operand tensor
@@ -117,7 +124,8 @@ struct XJob {
     CUtensorMap tmap;
     XArgs a;
     int op;         // 0 = FP16 (kind::f16), 1 = e4m3 (kind::f8f6f4), 2 = FP16 hi/lo pairs
-                    //   (three products per complex term, chunked two-level accumulation)
+                    //   (three products per complex term, chunked two-level accumulation),
+                    //   3 = integer mode (int8 held in FP16, exact chunks, int64 output)
     int max_cols;   // widest tile (columns) of the job: 128 lets the launch double-buffer TMEM
 };
 
@@ -167,8 +175,6 @@ cudaError_t make_operand_tmap(CUtensorMap* map, const void* Y, int elem_bytes, l
 cudaError_t launch_xstep_tc(const XLaunch& L, const XItem* items, int n_items, int* counter, int* status,
                             cudaStream_t s);
 int build_tc_tiles(int n, int window, int4* out, int cap);
-cudaError_t launch_xstep_int8(const CUtensorMap& map, const XArgs& a, int n_tiles, int segments, int slots,
-                              cudaStream_t s);
 bool fft_len_supported(int N);
 
 }  // namespace mwax

@@ -25,6 +25,7 @@ struct mwax_plan {
     long long slots = 1, Kc = 0, Kpad = 0;
     int chunks = 1;
     int elem_bytes = 4;
+    long long ktile = 0;      // integer mode: K tile of the operand layout (kIntKTile), else 0
 
     // device memory
     void* Y = nullptr;      // X-step operands (FP8: e4m3)

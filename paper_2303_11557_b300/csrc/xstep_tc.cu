@@ -44,6 +44,8 @@
 
 #include <cudaTypedefs.h>
 
+#include <type_traits>
+
 namespace mwax {
 namespace {
 
@@ -57,19 +59,29 @@ constexpr int EPI_THREADS = 256;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int MAX_STAGES = 4;
 
-// Ring geometry.  One-product forms: 4 stages of Br, Bi (256 rows) and Ar, Ai (48 KB).
-// Hi/lo pair form (128-column windows only): 3 stages of Br, Bi, Br', Bi', Ar, Ai, Ar',
+// Kernel modes: one FP16 / e4m3 product per term, accumulated per channel group in TMEM;
+// FP16 hi/lo pairs (three products per term) in chunked partial sums added into FP32
+// register totals; integer mode (int8 values held in FP16) in exact 512-sample partials
+// added into int32 register totals and flushed as int64 atomics per segment.
+constexpr int MODE_ONE = 0, MODE_PAIRS = 1, MODE_INT = 2;
+
+// Ring geometry.  One-product and integer modes: 4 stages of Br, Bi (256 rows) and Ar, Ai
+// (48 KB).  Pairs (128-column windows only): 3 stages of Br, Bi, Br', Bi', Ar, Ai, Ar',
 // Ai' (' = low halves; 8 planes of 128 rows, 64 KB).
-template <bool SPLIT>
+template <int MODE>
 struct Ring {
-    static constexpr int stages = SPLIT ? 3 : 4;
-    static constexpr int stage_bytes = SPLIT ? 8 * A_PLANE : 2 * B_PLANE + 2 * A_PLANE;
+    static constexpr int stages = MODE == MODE_PAIRS ? 3 : 4;
+    static constexpr int stage_bytes = MODE == MODE_PAIRS ? 8 * A_PLANE : 2 * B_PLANE + 2 * A_PLANE;
 };
 
-// Hi/lo pair form: k-blocks (32 frames each) per TMEM partial sum.  Each partial is a
-// fresh MMA accumulation over 64 frames; the epilogue adds the partials into FP32
-// register totals, so no tensor-core accumulation runs longer than 24 MMAs.
-constexpr int CHUNK_KB = 2;
+// k-blocks (32 frames each) per TMEM partial sum in the chunked modes.  Pairs: 64 frames,
+// so no tensor-core accumulation runs longer than 24 MMAs.  Integer mode: 512 samples,
+// every partial an integer of magnitude at most 512 * 2 * 128^2 = 2^24, exact in FP32.
+template <int MODE>
+__host__ __device__ constexpr int chunk_kb()
+{
+    return MODE == MODE_PAIRS ? 2 : 16;
+}
 
 constexpr int IRING = 4;   // claimed work items in flight between the roles
 
@@ -166,13 +178,47 @@ __device__ __forceinline__ void drain(const XArgs& a, const Group& gr, bool use_
     }
 }
 
-template <bool SPLIT>
+// Integer mode: add row p's int32 segment sums for columns [col, col + 64) (TMEM: real
+// part at tre, imaginary part 128 columns further on) into the int64 (re, im) MWAX_ORDER
+// output (one channel) with 64-bit atomic adds: integer addition, so the result does not
+// depend on the order in which segments arrive.  Every lane takes part in the TMEM loads.
+__device__ __forceinline__ void flush_int(const XArgs& a, char* obase, int p, int q0, uint32_t tre, int col)
+{
+    const int n = a.n, ti = p >> 1;
+    long long* ob64 = reinterpret_cast<long long*>(obase);
+#pragma unroll 1
+    for (int ch = 0; ch < 2; ++ch) {
+        const int c = col + ch * 32;
+        uint32_t re[32], im[32];
+        tc::tmem_ld32(tre + c, re);
+        tc::tmem_ld32(tre + 128 + c, im);
+        tc::tmem_wait_ld();
+        if (p >= n) continue;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const int q = q0 + c + i;
+            if (q < n && ti <= (q >> 1)) {
+                const int pol = ((p & 1) << 1) | (q & 1);
+                unsigned long long* o =
+                    reinterpret_cast<unsigned long long*>(ob64 + (baseline_of(ti, q >> 1, a.T) * 4 + pol) * 2);
+                const long long vi = (p == q) ? 0LL : (long long)(int)im[i];
+                atomicAdd(o, (unsigned long long)(long long)(int)re[i]);   // two's complement add
+                if (vi != 0) atomicAdd(o + 1, (unsigned long long)vi);
+            }
+        }
+    }
+}
+
+template <int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)
     xstep_tc_kernel(const __grid_constant__ XLaunch L, const XItem* __restrict__ items, int n_items, int* counter,
                     int* status, unsigned int spin_limit, int dbuf)
 {
-    constexpr int STAGES = Ring<SPLIT>::stages;
-    constexpr int STAGE_BYTES = Ring<SPLIT>::stage_bytes;
+    constexpr bool SPLIT = MODE == MODE_PAIRS;
+    constexpr bool CHUNKED = MODE != MODE_ONE;
+    constexpr int CHUNK_KB = chunk_kb<MODE>();
+    constexpr int STAGES = Ring<MODE>::stages;
+    constexpr int STAGE_BYTES = Ring<MODE>::stage_bytes;
     const XJob* jobs = L.jobs;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* ring = reinterpret_cast<unsigned char*>(
@@ -181,7 +227,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const long long lim = (long long)spin_limit * 1000LL;   // cycles
-    if (SPLIT) dbuf = 1;   // the partial sums always alternate between two buffers
+    if (CHUNKED) dbuf = 1;   // the partial sums always alternate between two buffers
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -235,9 +281,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const CUtensorMap* tm = &J->tmap;
                 tc::prefetch_tmap(tm);
                 const int4 tile = a.tiles[w.tile];
-                const RunInfo run = a.runs[w.run];
+                const RunInfo run = a.runs[MODE == MODE_INT ? 0 : w.run];
                 const int KF = (J->op == 1) ? 64 : 32;   // frames per 64-byte operand row
                 const int nkb = (int)((a.klen + KF - 1) / KF);
+                // k-blocks of this item: all of the slot's, or (integer mode) segment w.run's
+                const int kb_lo = MODE == MODE_INT ? w.run * (int)(a.seg_frames / KF) : 0;
+                const int kb_hi = MODE == MODE_INT ? min(nkb, kb_lo + (int)(a.seg_frames / KF)) : nkb;
                 const int nbox = tile.z / TM;             // 128-row boxes of the B window
                 const bool a_in_b = tile.w != 0;
                 const uint32_t bytes = SPLIT ? (uint32_t)((a_in_b ? 4 : 8) * A_PLANE)
@@ -248,14 +297,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     if (!item_feeds(gr, run)) continue;
                     for (int c = gr.c0; c < gr.c1 && !*abort; ++c) {
                         if (__ldg(&a.gain[c]) == 0.0f) continue;
-                        const int zr = (w.slot * a.N + c) * 2, zi = zr + 1;
-                        for (int kb = 0; kb < nkb; ++kb) {
+                        int zr = (w.slot * a.N + c) * 2, zi = zr + 1;
+                        for (int kb = kb_lo; kb < kb_hi; ++kb) {
+                            int kx = kb * KF;
+                            if (MODE == MODE_INT) {
+                                // K-tiled operand planes [slot][K tile][re/im] (one channel)
+                                const int kt = (int)(kx / a.ktile);
+                                zr = (int)((w.slot * (a.Kpad / a.ktile) + kt) * 2);
+                                zi = zr + 1;
+                                kx -= (int)(kt * a.ktile);
+                            }
                             if (!tc::mbar_wait(&S.empty[stage], phase ^ 1, abort, status, 2, lim)) break;
                             unsigned char* st = ring + stage * STAGE_BYTES;
                             uint64_t* fb = &S.full[stage];
                             tc::mbar_arrive_expect_tx(fb, bytes);
                             if (SPLIT) {
-                                const int kx = kb * KF, kl = klo + kb * KF;
+                                const int kl = klo + kx;
                                 tc::tma_load_3d(st, tm, fb, kx, tile.y, zr);
                                 tc::tma_load_3d(st + A_PLANE, tm, fb, kx, tile.y, zi);
                                 tc::tma_load_3d(st + 2 * A_PLANE, tm, fb, kl, tile.y, zr);
@@ -268,13 +325,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                                 }
                             } else {
                                 for (int b = 0; b < nbox; ++b) {
-                                    tc::tma_load_3d(st + b * A_PLANE, tm, fb, kb * KF, tile.y + b * TM, zr);
-                                    tc::tma_load_3d(st + B_PLANE + b * A_PLANE, tm, fb, kb * KF, tile.y + b * TM,
-                                                    zi);
+                                    tc::tma_load_3d(st + b * A_PLANE, tm, fb, kx, tile.y + b * TM, zr);
+                                    tc::tma_load_3d(st + B_PLANE + b * A_PLANE, tm, fb, kx, tile.y + b * TM, zi);
                                 }
                                 if (!a_in_b) {
-                                    tc::tma_load_3d(st + 2 * B_PLANE, tm, fb, kb * KF, tile.x, zr);
-                                    tc::tma_load_3d(st + 2 * B_PLANE + A_PLANE, tm, fb, kb * KF, tile.x, zi);
+                                    tc::tma_load_3d(st + 2 * B_PLANE, tm, fb, kx, tile.x, zr);
+                                    tc::tma_load_3d(st + 2 * B_PLANE + A_PLANE, tm, fb, kx, tile.x, zi);
                                 }
                             }
                             issued_phase[stage] = (int)phase;
@@ -321,23 +377,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const XArgs& a = J->a;
                 const int op = J->op;
                 const int4 tile = a.tiles[w.tile];
-                const RunInfo run = a.runs[w.run];
+                const RunInfo run = a.runs[MODE == MODE_INT ? 0 : w.run];
                 const int KF = (op == 1) ? 64 : 32;
                 const int nkb = (int)((a.klen + KF - 1) / KF);
+                const int kb_lo = MODE == MODE_INT ? w.run * (int)(a.seg_frames / KF) : 0;
+                const int kb_hi = MODE == MODE_INT ? min(nkb, kb_lo + (int)(a.seg_frames / KF)) : nkb;
                 const bool a_in_b = tile.w != 0;
                 const uint32_t id = tc::idesc(0, TM, tile.z, false), id_neg = tc::idesc(0, TM, tile.z, true);
                 for (int g = run.g0; g < run.g1 && !*abort; ++g) {
                     const Group gr = a.groups[g];
                     if (!item_feeds(gr, run)) continue;
-                    if (SPLIT) {
-                        // hi/lo pairs: a fresh partial per CHUNK_KB k-blocks, alternating buffers
-                        const int total = live_channels(a, gr) * nkb;
+                    if (CHUNKED) {
+                        // a fresh partial per CHUNK_KB k-blocks, alternating buffers
+                        const int total = live_channels(a, gr) * (kb_hi - kb_lo);
                         int done = 0;
                         bool first = true;
                         uint32_t d_re = 0, d_im = 0;
                         for (int c = gr.c0; c < gr.c1 && !*abort; ++c) {
                             if (__ldg(&a.gain[c]) == 0.0f) continue;
-                            for (int kb = 0; kb < nkb; ++kb) {
+                            for (int kb = kb_lo; kb < kb_hi; ++kb) {
                                 if (done % CHUNK_KB == 0) {
                                     cur_b = (int)(gcount & 1);
                                     cur_ph = (gcount >> 1) & 1;
@@ -350,31 +408,48 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                                 if (!tc::mbar_wait(&S.full[stage], phase, abort, status, 8, lim)) break;
                                 tc::fence_after();
                                 const uint32_t st = sbase + stage * STAGE_BYTES;
-                                const uint64_t brh = tc::sw64_desc(st), bih = tc::sw64_desc(st + A_PLANE);
-                                const uint64_t brl = tc::sw64_desc(st + 2 * A_PLANE);
-                                const uint64_t bil = tc::sw64_desc(st + 3 * A_PLANE);
-                                const uint64_t arh = a_in_b ? brh : tc::sw64_desc(st + 4 * A_PLANE);
-                                const uint64_t aih = a_in_b ? bih : tc::sw64_desc(st + 5 * A_PLANE);
-                                const uint64_t arl = a_in_b ? brl : tc::sw64_desc(st + 6 * A_PLANE);
-                                const uint64_t ail = a_in_b ? bil : tc::sw64_desc(st + 7 * A_PLANE);
+                                if (!SPLIT) {
+                                    // integer mode: int8 values held in FP16, one product per term
+                                    const uint64_t dbr = tc::sw64_desc(st), dbi = tc::sw64_desc(st + B_PLANE);
+                                    const uint64_t dar = a_in_b ? dbr : tc::sw64_desc(st + 2 * B_PLANE);
+                                    const uint64_t dai = a_in_b ? dbi : tc::sw64_desc(st + 2 * B_PLANE + A_PLANE);
 #pragma unroll
-                                for (int k = 0; k < ROWB / 32; ++k) {
-                                    const uint64_t off = (uint64_t)(k * 32) >> 4;
-                                    const uint32_t acc = first ? 0u : 1u;
-                                    first = false;
-                                    // (Ah + Al)(Bh + Bl)^H without the Al Bl^H term
-                                    tc::mma_f16(d_re, arh + off, brh + off, id, acc);
-                                    tc::mma_f16(d_re, aih + off, bih + off, id, 1u);
-                                    tc::mma_f16(d_re, arh + off, brl + off, id, 1u);
-                                    tc::mma_f16(d_re, aih + off, bil + off, id, 1u);
-                                    tc::mma_f16(d_re, arl + off, brh + off, id, 1u);
-                                    tc::mma_f16(d_re, ail + off, bih + off, id, 1u);
-                                    tc::mma_f16(d_im, aih + off, brh + off, id, acc);
-                                    tc::mma_f16(d_im, arh + off, bih + off, id_neg, 1u);
-                                    tc::mma_f16(d_im, aih + off, brl + off, id, 1u);
-                                    tc::mma_f16(d_im, arh + off, bil + off, id_neg, 1u);
-                                    tc::mma_f16(d_im, ail + off, brh + off, id, 1u);
-                                    tc::mma_f16(d_im, arl + off, bih + off, id_neg, 1u);
+                                    for (int k = 0; k < ROWB / 32; ++k) {
+                                        const uint64_t off = (uint64_t)(k * 32) >> 4;
+                                        const uint32_t acc = first ? 0u : 1u;
+                                        first = false;
+                                        tc::mma_f16(d_re, dar + off, dbr + off, id, acc);
+                                        tc::mma_f16(d_re, dai + off, dbi + off, id, 1u);
+                                        tc::mma_f16(d_im, dai + off, dbr + off, id, acc);
+                                        tc::mma_f16(d_im, dar + off, dbi + off, id_neg, 1u);
+                                    }
+                                } else {
+                                    const uint64_t brh = tc::sw64_desc(st), bih = tc::sw64_desc(st + A_PLANE);
+                                    const uint64_t brl = tc::sw64_desc(st + 2 * A_PLANE);
+                                    const uint64_t bil = tc::sw64_desc(st + 3 * A_PLANE);
+                                    const uint64_t arh = a_in_b ? brh : tc::sw64_desc(st + 4 * A_PLANE);
+                                    const uint64_t aih = a_in_b ? bih : tc::sw64_desc(st + 5 * A_PLANE);
+                                    const uint64_t arl = a_in_b ? brl : tc::sw64_desc(st + 6 * A_PLANE);
+                                    const uint64_t ail = a_in_b ? bil : tc::sw64_desc(st + 7 * A_PLANE);
+#pragma unroll
+                                    for (int k = 0; k < ROWB / 32; ++k) {
+                                        const uint64_t off = (uint64_t)(k * 32) >> 4;
+                                        const uint32_t acc = first ? 0u : 1u;
+                                        first = false;
+                                        // (Ah + Al)(Bh + Bl)^H without the Al Bl^H term
+                                        tc::mma_f16(d_re, arh + off, brh + off, id, acc);
+                                        tc::mma_f16(d_re, aih + off, bih + off, id, 1u);
+                                        tc::mma_f16(d_re, arh + off, brl + off, id, 1u);
+                                        tc::mma_f16(d_re, aih + off, bil + off, id, 1u);
+                                        tc::mma_f16(d_re, arl + off, brh + off, id, 1u);
+                                        tc::mma_f16(d_re, ail + off, bih + off, id, 1u);
+                                        tc::mma_f16(d_im, aih + off, brh + off, id, acc);
+                                        tc::mma_f16(d_im, arh + off, bih + off, id_neg, 1u);
+                                        tc::mma_f16(d_im, aih + off, brl + off, id, 1u);
+                                        tc::mma_f16(d_im, arh + off, bil + off, id_neg, 1u);
+                                        tc::mma_f16(d_im, ail + off, brh + off, id, 1u);
+                                        tc::mma_f16(d_im, arl + off, bih + off, id_neg, 1u);
+                                    }
                                 }
                                 issued = true;
                                 tc::mma_commit(&S.empty[stage]);
@@ -467,31 +542,35 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const XArgs& a = J->a;
             const int op = J->op;
             const int4 tile = a.tiles[w.tile];
-            const RunInfo run = a.runs[w.run];
+            const RunInfo run = a.runs[MODE == MODE_INT ? 0 : w.run];
             const int p0 = tile.x, q0 = tile.y, nq = tile.z;
             const int p = p0 + g4 * 32 + lane;
             const bool cols = half * 128 < nq;
             char* obase = a.out + (long long)w.slot * a.out_stride;
             float2* ob = reinterpret_cast<float2*>(obase);
             const int n = a.n;
-            const int nkb = (int)((a.klen + 31) / 32);   // pairs: FP16, 32 frames per k-block
+            const int nkb = (int)((a.klen + 31) / 32);   // chunked modes: FP16, 32 frames per k-block
+            const int kb_lo = MODE == MODE_INT ? w.run * (int)(a.seg_frames / 32) : 0;
+            const int kb_hi = MODE == MODE_INT ? min(nkb, kb_lo + (int)(a.seg_frames / 32)) : nkb;
             for (int g = run.g0; g < run.g1 && !*abort; ++g) {
                 const Group gr = a.groups[g];
                 if (!item_feeds(gr, run)) continue;
                 const bool use_a = gr.ja >= run.j0 && gr.ja < run.j1;
                 const bool use_b = gr.jb >= run.j0 && gr.jb < run.j1;
                 const uint32_t tlane = tmem + ((uint32_t)(g4 * 32) << 16);
-                if (SPLIT) {
+                if (CHUNKED) {
                     // columns [64 half, 64 half + 64) of the 128-column window, summed over
-                    // the group's chunk partials in FP32 registers; the totals go back into
-                    // the last partial's buffer (still held) for the write-out
+                    // the group's chunk partials in registers (pairs: FP32, the totals then
+                    // go back into the last partial's buffer, still held, for the write-out;
+                    // integer mode: int32, flushed into the int64 output by atomic adds)
+                    using Tot = typename std::conditional<MODE == MODE_INT, int, float>::type;
                     const int col0 = half * 64;
-                    const int nch = (live_channels(a, gr) * nkb + CHUNK_KB - 1) / CHUNK_KB;
-                    float tr[64], tq[64];
+                    const int nch = (live_channels(a, gr) * (kb_hi - kb_lo) + CHUNK_KB - 1) / CHUNK_KB;
+                    Tot tr[64], tq[64];
 #pragma unroll
                     for (int i = 0; i < 64; ++i) {
-                        tr[i] = 0.0f;
-                        tq[i] = 0.0f;
+                        tr[i] = 0;
+                        tq[i] = 0;
                     }
                     bool ok = true;
                     int b = 0;
@@ -513,8 +592,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             tc::tmem_wait_ld();
 #pragma unroll
                             for (int i = 0; i < 16; ++i) {
-                                tr[16 * h + i] += __uint_as_float(vr[i]);
-                                tq[16 * h + i] += __uint_as_float(vi[i]);
+                                if (MODE == MODE_INT) {   // exact integers in FP32
+                                    tr[16 * h + i] += __float2int_rn(__uint_as_float(vr[i]));
+                                    tq[16 * h + i] += __float2int_rn(__uint_as_float(vi[i]));
+                                } else {
+                                    tr[16 * h + i] += __uint_as_float(vr[i]);
+                                    tq[16 * h + i] += __uint_as_float(vi[i]);
+                                }
                             }
                         }
                         if (ck + 1 < nch) {
@@ -529,15 +613,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     for (int h = 0; h < 4; ++h) {
                         uint32_t vr[16], vi[16];
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            vr[i] = __float_as_uint(tr[16 * h + i]);
-                            vi[i] = __float_as_uint(tq[16 * h + i]);
+                        for (int i = 0; i < 16; ++i) {   // FP32 totals, or int32 totals as their bits
+                            vr[i] = MODE == MODE_INT ? (uint32_t)tr[16 * h + i] : __float_as_uint((float)tr[16 * h + i]);
+                            vi[i] = MODE == MODE_INT ? (uint32_t)tq[16 * h + i] : __float_as_uint((float)tq[16 * h + i]);
                         }
                         tc::tmem_st16(tlane + 256u * b + col0 + 16 * h, vr);
                         tc::tmem_st16(tlane + 256u * b + 128 + col0 + 16 * h, vi);
                     }
                     tc::tmem_wait_st();
-                    drain(a, gr, use_a, use_b, ob, p, q0, tlane, 256u * b, 128u, col0, 2, a.post_scale, nullptr);
+                    if (MODE == MODE_INT)
+                        flush_int(a, obase, p, q0, tlane + 256u * b, col0);
+                    else
+                        drain(a, gr, use_a, use_b, ob, p, q0, tlane, 256u * b, 128u, col0, 2, a.post_scale, nullptr);
                     tc::fence_before();
                     tc::mbar_arrive(&S.acc_empty[b]);
                     ++gcount;
@@ -574,10 +661,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
 }
 
-template <bool SPLIT>
+template <int MODE>
 constexpr size_t tc_smem_bytes()
 {
-    return 1024 + Ring<SPLIT>::stages * Ring<SPLIT>::stage_bytes + sizeof(TcSmem);
+    return 1024 + Ring<MODE>::stages * Ring<MODE>::stage_bytes + sizeof(TcSmem);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
@@ -627,15 +714,15 @@ cudaError_t make_simt_tmap(CUtensorMap* map, const void* Y, long long Kpad, int 
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <bool SPLIT>
+template <int MODE>
 cudaError_t launch_tc_kernel(const XLaunch& L, const XItem* items, int n_items, int* counter, int* status, int dbuf,
                              cudaStream_t s)
 {
     static bool attr_done = false;
-    const size_t smem = tc_smem_bytes<SPLIT>();
+    const size_t smem = tc_smem_bytes<MODE>();
     if (!attr_done) {
         cudaError_t e =
-            cudaFuncSetAttribute(xstep_tc_kernel<SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(xstep_tc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
@@ -645,7 +732,7 @@ cudaError_t launch_tc_kernel(const XLaunch& L, const XItem* items, int n_items, 
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    xstep_tc_kernel<SPLIT><<<n_items < sms ? n_items : sms, NTHREADS, smem, s>>>(L, items, n_items, counter, status,
+    xstep_tc_kernel<MODE><<<n_items < sms ? n_items : sms, NTHREADS, smem, s>>>(L, items, n_items, counter, status,
                                                                                  2000000u, dbuf);
     return cudaGetLastError();
 }
@@ -653,19 +740,24 @@ cudaError_t launch_tc_kernel(const XLaunch& L, const XItem* items, int n_items, 
 cudaError_t launch_xstep_tc(const XLaunch& L, const XItem* items, int n_items, int* counter, int* status,
                             cudaStream_t s)
 {
-    // one kernel form per launch: every job FP16 / e4m3, or every job FP16 hi/lo pairs
-    // (these on 128-column windows only)
-    int pairs = -1;
+    // one kernel mode per launch: every job FP16 / e4m3 (op 0, 1), every job FP16 hi/lo
+    // pairs (op 2) or every job integer mode (op 3); the last two on 128-column tiles only
+    int mode = -1;
     for (int j = 0; j < L.n_jobs; ++j) {
-        const int pj = L.jobs[j].op == 2 ? 1 : 0;
-        if (pairs >= 0 && pj != pairs) return cudaErrorInvalidValue;
-        pairs = pj;
-        if (pj && L.jobs[j].max_cols > TM) return cudaErrorInvalidValue;
+        const int op = L.jobs[j].op;
+        const int mj = op == 2 ? MODE_PAIRS : (op == 3 ? MODE_INT : MODE_ONE);
+        if (mode >= 0 && mj != mode) return cudaErrorInvalidValue;
+        mode = mj;
+        if (mj != MODE_ONE && L.jobs[j].max_cols > TM) return cudaErrorInvalidValue;
+        if (mj == MODE_INT && (L.jobs[j].a.seg_frames <= 0 || L.jobs[j].a.seg_frames % 512 != 0 ||
+                               L.jobs[j].a.seg_frames > 100 * 512))
+            return cudaErrorInvalidValue;   // segments of whole exact chunks, int32-safe
     }
-    if (pairs == 1) return launch_tc_kernel<true>(L, items, n_items, counter, status, 1, s);
+    if (mode == MODE_PAIRS) return launch_tc_kernel<MODE_PAIRS>(L, items, n_items, counter, status, 1, s);
+    if (mode == MODE_INT) return launch_tc_kernel<MODE_INT>(L, items, n_items, counter, status, 1, s);
     int dbuf = 1;   // double-buffered accumulators when every job's tiles are at most 128 columns wide
     for (int j = 0; j < L.n_jobs; ++j) dbuf &= (L.jobs[j].max_cols <= TM) ? 1 : 0;
-    return launch_tc_kernel<false>(L, items, n_items, counter, status, dbuf, s);
+    return launch_tc_kernel<MODE_ONE>(L, items, n_items, counter, status, dbuf, s);
 }
 
 // Tile list of the tensor-core X-step: for each 128-row block, column windows of

@@ -1,7 +1,8 @@
 // X-step on the 5th-generation tensor cores (tcgen05, TMEM accumulators, TMA operand
-// staging) for the FP16, FP8-e4m3 and FP16 hi/lo pair forms, with the same fused epilogue as the
-// CUDA-core form: integration over the frames of a slot (Sec. 2.5.2), channel averaging
-// (Sec. 2.6) and MWAX_ORDER output (Sec. 2.7).
+// staging) for the FP16, FP8-e4m3 and FP16 hi/lo pair forms, with the same fused epilogue
+// as the CUDA-core form: integration over the frames of a slot (Sec. 2.5.2), channel
+// averaging (Sec. 2.6) and MWAX_ORDER output (Sec. 2.7); and for the exact integer mode
+// (no FFT, int64 sums of the int8 voltages).
 //
 // The complex product C = Y_p conj(Y_q) is four real MMAs on planar operands:
 //     Re C = Ar Br^T + Ai Bi^T,      Im C = Ai Br^T - Ar Bi^T
@@ -28,6 +29,15 @@
 // 10 warps: warp 0 issues TMA loads into a 4-stage ring, warp 1 owns TMEM and issues the
 // MMAs from one thread, warps 2-9 drain the accumulators (TMEM lane quarter = warp % 4,
 // column half = (warp - 2) / 4; one TMEM lane = one path p).
+//
+// Integer mode: sm_103a has no integer MMA, but every int8 value is exact in FP16 and every
+// product of two is exact in FP32.  The MMAs of 512 samples go into a fresh TMEM partial
+// (every partial sum an integer of magnitude at most 512 * 2 * 128^2 = 2^24, so exact),
+// two partial buffers alternate, and the epilogue adds each partial into int32 register
+// totals.  A work item is (tile, segment of at most 51,200 samples, slot), so the totals
+// stay below 2^31; at its end they go into the int64 output by 64-bit atomic adds (integer
+// addition: the order of the segments does not matter).  The operands of this mode are
+// K-tiled, [slot][K tile][re/im][p][2048], so that the rows of one TMA box lie close together.
 //
 // FP16 hi/lo pair form (FP32-accurate products on the tensor cores): every operand value
 // v is held as hi = fp16(v) and lo = fp16(v - hi) (22 significant bits), and each complex

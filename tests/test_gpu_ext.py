@@ -1,8 +1,9 @@
 """GPU parity of the roadmap extensions (Sec. 2.4, 4.1-4.3, 4.5) through the C ABI against
 the FP64 oracle's extended correlation, on seeded inputs: zeroing flags with occupancy
 weights and normalisation, tabulated 5 ms-style delays, passband de-ripple gains and
-oversampled coarse channels.  Same bars as the base parity tests (FP32 1e-5, FP16 2e-3 of
-the autos; int8 bit-exact); weights to FP32 rounding of the exact fractions."""
+oversampled coarse channels.  Same bars as the base parity tests (FP32 and FP16 hi/lo pairs
+1e-5, FP16 2e-3 of the autos; int8 bit-exact); weights to FP32 rounding of the exact
+fractions."""
 import numpy as np
 import pytest
 
@@ -14,7 +15,7 @@ from _parity import workload
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-TOL = {mw.MWAX_FP32: 1e-5, mw.MWAX_FP16: 2e-3}
+TOL = {mw.MWAX_FP32: 1e-5, mw.MWAX_FP16: 2e-3, mw.MWAX_FP16X3: 1e-5}
 
 
 def ext_parity(vis, ref, T):
@@ -71,7 +72,7 @@ def flags_for(seed, n_blocks, n_paths, frac=0.15, dead=None):
     return f
 
 
-@pytest.mark.parametrize("prec", [mw.MWAX_FP32, mw.MWAX_FP16], ids=["fp32", "fp16"])
+@pytest.mark.parametrize("prec", [mw.MWAX_FP32, mw.MWAX_FP16, mw.MWAX_FP16X3], ids=["fp32", "fp16", "fp16x3"])
 @pytest.mark.parametrize("normalise", [0, 1], ids=["raw", "normalised"])
 def test_zero_flags_weights(prec, normalise):
     # 5 ms blocks, 0.1 s integrations: 20 blocks per integration; path 5 dead for all of
@@ -136,7 +137,7 @@ def test_delay_table_from_host_fp16():
     assert ext_parity(vis, ref, T).max() <= TOL[mw.MWAX_FP16]
 
 
-@pytest.mark.parametrize("prec", [mw.MWAX_FP32, mw.MWAX_FP16], ids=["fp32", "fp16"])
+@pytest.mark.parametrize("prec", [mw.MWAX_FP32, mw.MWAX_FP16, mw.MWAX_FP16X3], ids=["fp32", "fp16", "fp16x3"])
 def test_passband_deripple(prec):
     # inverse of a rippled passband with rolled-off edges: gains 0.9 .. 1.9
     T, N, F, S = 8, 128, 4, 128_000
@@ -151,7 +152,7 @@ def test_passband_deripple(prec):
     assert ext_parity(vis, ref, T).max() <= TOL[prec]
 
 
-@pytest.mark.parametrize("prec", [mw.MWAX_FP32, mw.MWAX_FP16], ids=["fp32", "fp16"])
+@pytest.mark.parametrize("prec", [mw.MWAX_FP32, mw.MWAX_FP16, mw.MWAX_FP16X3], ids=["fp32", "fp16", "fp16x3"])
 def test_oversampled_channel(prec):
     # 32/25 oversampled coarse channel: 1.6384 MS/s, N = 128 keeps the central 100 bins,
     # F = 4 -> 25 output channels; integration of 1000 frames = 78.125 ms

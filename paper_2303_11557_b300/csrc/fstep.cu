@@ -271,6 +271,69 @@ struct Store {
     }
 };
 
+// Two frames per CTA (the largest FFT lengths): lanes 2i and 2i + 1 hold frames 0 and 1 of
+// the same output, which are neighbours along K.  They swap halves with one shuffle so that
+// the even lane writes both frames' real parts and the odd lane both imaginary parts, each
+// as one word: half the scattered stores.  `at` is this lane's own element (the odd lane's
+// frame-0 element is at - 1); paired = both frames in one slot starting at an even index
+// (the same for both lanes); otherwise each live lane stores its own values.  Every lane
+// must call this (the shuffle).
+template <int OUTK>
+__device__ __forceinline__ void store_frame_pair(const FArgs& a, long long at, long long ps, float2 y, bool odd,
+                                                 bool paired, bool live)
+{
+    if (OUTK == FOUT_F32) {
+        const float other = __shfl_xor_sync(0xffffffffu, odd ? y.x : y.y, 1);
+        float* Y = static_cast<float*>(a.Y);
+        if (paired) {
+            if (odd) *reinterpret_cast<float2*>(Y + at - 1 + ps) = make_float2(other, y.y);
+            else *reinterpret_cast<float2*>(Y + at) = make_float2(y.x, other);
+        } else if (live) {
+            Y[at] = y.x;
+            Y[at + ps] = y.y;
+        }
+    } else if (OUTK == FOUT_F16) {
+        const __half2 h2 = __floats2half2_rn(y.x * a.out_scale, y.y * a.out_scale);
+        const uint32_t hu = *reinterpret_cast<const uint32_t*>(&h2);
+        const uint32_t other = __shfl_xor_sync(0xffffffffu, hu, 1);
+        __half* Y = static_cast<__half*>(a.Y);
+        if (paired) {
+            if (odd) *reinterpret_cast<uint32_t*>(Y + at - 1 + ps) = __byte_perm(other, hu, 0x7632);
+            else *reinterpret_cast<uint32_t*>(Y + at) = __byte_perm(hu, other, 0x5410);
+        } else if (live) {
+            Y[at] = __low2half(h2);
+            Y[at + ps] = __high2half(h2);
+        }
+    } else {   // FP16 hi/lo pairs: lo values half a row further on
+        const float xr = y.x * a.out_scale, xi = y.y * a.out_scale;
+        const __half2 h2 = __floats2half2_rn(xr, xi);
+        const float2 hf = __half22float2(h2);
+        const __half2 l2 = __floats2half2_rn(xr - hf.x, xi - hf.y);
+        const uint32_t hu = *reinterpret_cast<const uint32_t*>(&h2), lu = *reinterpret_cast<const uint32_t*>(&l2);
+        // even lane sends (im hi, im lo), odd lane (re hi, re lo)
+        const uint32_t send = odd ? __byte_perm(hu, lu, 0x5410) : __byte_perm(hu, lu, 0x7632);
+        const uint32_t other = __shfl_xor_sync(0xffffffffu, send, 1);
+        const long long lo = a.Kpad >> 1;
+        __half* Y = static_cast<__half*>(a.Y);
+        if (paired) {
+            if (odd) {
+                uint32_t* w = reinterpret_cast<uint32_t*>(Y + at - 1 + ps);
+                w[0] = __byte_perm(other, hu, 0x7610);          // (frame 0 im hi, frame 1 im hi)
+                w[lo >> 1] = __byte_perm(other, lu, 0x7632);    // (frame 0 im lo, frame 1 im lo)
+            } else {
+                uint32_t* w = reinterpret_cast<uint32_t*>(Y + at);
+                w[0] = __byte_perm(hu, other, 0x5410);          // (frame 0 re hi, frame 1 re hi)
+                w[lo >> 1] = __byte_perm(lu, other, 0x7610);    // (frame 0 re lo, frame 1 re lo)
+            }
+        } else if (live) {
+            Y[at] = __low2half(h2);
+            Y[at + ps] = __high2half(h2);
+            Y[at + lo] = __low2half(l2);
+            Y[at + ps + lo] = __high2half(l2);
+        }
+    }
+}
+
 // Delay phasor e^{2 pi i (phi0 + u d)} of ultrafine offset u (|u| < 4096), d = d_hi + d_lo
 // with d_hi holding 12 significant bits so that u * d_hi is exact in FP32.
 __device__ __forceinline__ float2 delay_phasor_u(float phi0, float d_hi, float d_lo, int u)
@@ -349,7 +412,14 @@ struct Pass {
                 for (int r = 0; r < R; ++r) out[f * ROW + d + r * NS] = v[r];
             } else {
                 const FrameInfo fi = finfo[f];
-                if (fi.slot < 0) continue;
+                // two frames per CTA: neighbouring lanes pair their stores (every lane stays
+                // in the loop for the shuffles; FB * NB is a multiple of the CTA size)
+                constexpr bool PAIR = FB == 2;
+                static_assert(!PAIR || !LAST || (FB * NB) % Sched<N>::nt == 0, "paired stores need uniform iterations");
+                const bool live = fi.slot >= 0;
+                const bool paired =
+                    PAIR && finfo[0].slot >= 0 && finfo[1].slot == finfo[0].slot && (finfo[0].k & 1) == 0;
+                if (!PAIR && !live) continue;
                 // outputs k = j + r NB, r = 0..R-1; channel c = (k + N/2) mod N
                 float2 E = make_float2(1.0f, 0.0f);
                 if (fi.delay) E = delay_phasor(fi, j);   // u = j for r = 0 (j < NB <= N/2)
@@ -368,7 +438,10 @@ struct Pass {
                     const float gn = gain[c];
                     y.x *= gn;
                     y.y *= gn;
-                    Store<N, OUTK>::run(a, base + c * cs, ps, y, fi.slot, c, p);
+                    if (PAIR)
+                        store_frame_pair<OUTK>(a, base + c * cs, ps, y, f == 1, paired, live);
+                    else
+                        Store<N, OUTK>::run(a, base + c * cs, ps, y, fi.slot, c, p);
                 }
             }
         }

@@ -525,6 +525,12 @@ def run_mine(args, world, rank, local):
 
     torch.cuda.set_device(local)
     W = SMALL if args.workload == "small" else WORKLOAD
+    if args.fft_len:
+        # profiler captures of the other FFT lengths on the small workload only
+        if W is not SMALL:
+            raise SystemExit("--fft-len applies to --workload small (profiler captures)")
+        W = dict(W, fft_len=args.fft_len, fine_avg=args.fine_avg or 1,
+                 name=f"{W['name']} (N={args.fft_len}, fscrunch {args.fine_avg or 1})")
     host, delay = make_inputs(W, pin=not args.no_e2e)
     dev_volt = host.cuda(non_blocking=False)
     dev_delay = torch.from_numpy(delay).cuda()
@@ -720,6 +726,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 24-channel batched measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the real-time serving measurement")
     ap.add_argument("--no-ext", action="store_true", help="skip the roadmap extensions and the beamformer")
+    ap.add_argument("--fft-len", type=int, default=0,
+                    help="with --workload small: another FFT length (for profiler captures of the F-step)")
+    ap.add_argument("--fine-avg", type=int, default=0, help="fscrunch with --fft-len")
     ap.add_argument("--workload", default="full", choices=["full", "small"],
                     help="small = one 0.5 s integration (for profiler captures)")
     args = ap.parse_args()

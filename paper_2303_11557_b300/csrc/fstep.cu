@@ -372,13 +372,26 @@ __device__ __forceinline__ float2 twiddle(const float2* tw, int k)
     return c_mul(tw[k & 127], tw[128 + (k >> 7)]);
 }
 
+// Shared-memory layout of the generic kernel's frames: element i of a frame sits at
+// smem_pad(i) (one float2 of padding per 16, so the first pass's radix-R writes, R float2
+// apart, fall in different banks), and frame f's row starts at f * ROW with ROW = 16 / FB
+// (mod 16 float2): the FB frames x 16 / FB butterflies of a half-warp then cover all banks.
+__host__ __device__ constexpr int smem_pad(int i) { return i + (i >> 4); }
+
+template <int N>
+__host__ __device__ constexpr int fstep_row()
+{
+    return (smem_pad(N - 1) + 1) +
+           (((Sched<N>::fb >= 16 ? 1 : 16 / Sched<N>::fb) - (smem_pad(N - 1) + 1) % 16) % 16 + 16) % 16;
+}
+
 template <int N, int OUTK, int P>
 struct Pass {
     static constexpr int R = Sched<N>::radix[P];
     static constexpr int NS = PassNs<N, P>::value;
     static constexpr int NB = N / R;
     static constexpr int FB = Sched<N>::fb;
-    static constexpr int ROW = N + 1;              // padded float2 row per frame
+    static constexpr int ROW = fstep_row<N>();     // padded float2 row per frame
     static constexpr int SROW = 2 * N + 4;         // padded int8 staging row (bytes)
     static constexpr bool FIRST = (P == 0);
     static constexpr bool LAST = (P == Sched<N>::passes - 1);
@@ -398,18 +411,28 @@ struct Pass {
                     const char2 s = *reinterpret_cast<const char2*>(stage + f * SROW + 2 * (j + r * NB));
                     v[r] = make_float2((float)s.x, (float)s.y);
                 } else {
-                    v[r] = in[f * ROW + j + r * NB];
+                    v[r] = in[f * ROW + smem_pad(j + r * NB)];
                 }
             }
             if (NS > 1) {
 #pragma unroll
                 for (int r = 1; r < R; ++r) v[r] = c_mul(v[r], twiddle<N>(tw, (j % NS) * r * (N / (NS * R))));
             }
+            // last pass: the outputs' channel gains, loaded before the butterfly so that
+            // their latency (global memory above N = 1280) overlaps its arithmetic
+            float gk[LAST ? R : 1];
+            if (LAST) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int k = j + r * NB;
+                    gk[r] = gain[(k < N - N / 2) ? k + N / 2 : k - (N - N / 2)];
+                }
+            }
             Dft<R>::run(v);
             if (!LAST) {
                 const int d = (j / NS) * NS * R + (j % NS);
 #pragma unroll
-                for (int r = 0; r < R; ++r) out[f * ROW + d + r * NS] = v[r];
+                for (int r = 0; r < R; ++r) out[f * ROW + smem_pad(d + r * NS)] = v[r];
             } else {
                 const FrameInfo fi = finfo[f];
                 // two frames per CTA: neighbouring lanes pair their stores (every lane stays
@@ -435,7 +458,7 @@ struct Pass {
                         y = c_mul(y, (k < N - N / 2) ? E : c_mul(E, fi.wrap));
                         E = c_mul(E, fi.step);
                     }
-                    const float gn = gain[c];
+                    const float gn = gk[r];
                     y.x *= gn;
                     y.y *= gn;
                     if (PAIR)
@@ -478,7 +501,7 @@ __host__ __device__ constexpr bool tables_in_smem()
 template <int N>
 __host__ __device__ constexpr size_t fstep_smem()
 {
-    return 2 * sizeof(float2) * (size_t)Sched<N>::fb * (N + 1) + sizeof(FrameInfo) * Sched<N>::fb +
+    return 2 * sizeof(float2) * (size_t)Sched<N>::fb * fstep_row<N>() + sizeof(FrameInfo) * Sched<N>::fb +
            (tables_in_smem<N>() ? (sizeof(float2) + sizeof(float)) * N : sizeof(float2) * (128 + N / 128));
 }
 
@@ -486,7 +509,7 @@ template <int N, int OUTK>
 __global__ void __launch_bounds__(Sched<N>::nt) fstep_kernel(const FArgs a)
 {
     constexpr int FB = Sched<N>::fb;
-    constexpr int ROW = N + 1;
+    constexpr int ROW = fstep_row<N>();
     constexpr int SROW = 2 * N + 4;
     extern __shared__ __align__(16) unsigned char smem[];
     float2* buf0 = reinterpret_cast<float2*>(smem);

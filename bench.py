@@ -643,7 +643,9 @@ def run_mine(args, world, rank, local):
         for k in range(2):                                     # warm-up (allocates both staging sets)
             mw.mwax_correlate_host_async(plan, host, delay, host_outs[k])
         mw.mwax_plan_sync(plan)
-        reps = max(2, args.steps)
+        # every timed call uploads its own voltages and reads back its result; the first
+        # upload overlaps nothing, so more calls amortise that pipeline fill
+        reps = max(10, args.steps)
         barrier(world)
         t0 = time.perf_counter()
         for k in range(reps):

@@ -402,21 +402,34 @@ struct Pass {
     {
         float2* in = (P % 2 == 0) ? buf1 : buf0;   // pass 0 reads the staging area in buf1
         float2* out = (P % 2 == 0) ? buf0 : buf1;
-        for (int idx = threadIdx.x; idx < FB * NB; idx += Sched<N>::nt) {
-            const int f = idx % FB, j = idx / FB;
+        // A thread keeps one frame (the CTA size is a multiple of FB) and walks its
+        // butterflies j; padded offsets of the R inputs (outputs) are compile-time steps from
+        // the first one whenever their stride is a multiple of 16 (or the first pass's
+        // radix divides 16), so each access is one shared load or store.
+        constexpr int NT = Sched<N>::nt;
+        static_assert(NT % FB == 0, "a thread keeps one frame");
+        const int f = threadIdx.x % FB;
+        const float2* in_f = in + f * ROW;
+        float2* out_f = out + f * ROW;
+        const int8_t* st_f = stage + f * SROW;
+        for (int j = threadIdx.x / FB; j < NB; j += NT / FB) {
             float2 v[R];
+            const int pj = smem_pad(j);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 if (FIRST) {
-                    const char2 s = *reinterpret_cast<const char2*>(stage + f * SROW + 2 * (j + r * NB));
+                    const char2 s = *reinterpret_cast<const char2*>(st_f + 2 * j + 2 * r * NB);
                     v[r] = make_float2((float)s.x, (float)s.y);
+                } else if (NB % 16 == 0) {
+                    v[r] = in_f[pj + r * (NB + NB / 16)];
                 } else {
-                    v[r] = in[f * ROW + smem_pad(j + r * NB)];
+                    v[r] = in_f[smem_pad(j + r * NB)];
                 }
             }
             if (NS > 1) {
+                const int tj = (j % NS) * (N / (NS * R));
 #pragma unroll
-                for (int r = 1; r < R; ++r) v[r] = c_mul(v[r], twiddle<N>(tw, (j % NS) * r * (N / (NS * R))));
+                for (int r = 1; r < R; ++r) v[r] = c_mul(v[r], twiddle<N>(tw, tj * r));
             }
             // last pass: the outputs' channel gains, loaded before the butterfly so that
             // their latency (global memory above N = 1280) overlaps its arithmetic
@@ -431,8 +444,13 @@ struct Pass {
             Dft<R>::run(v);
             if (!LAST) {
                 const int d = (j / NS) * NS * R + (j % NS);
+                const int pd = smem_pad(d);
 #pragma unroll
-                for (int r = 0; r < R; ++r) out[f * ROW + smem_pad(d + r * NS)] = v[r];
+                for (int r = 0; r < R; ++r) {
+                    if (NS % 16 == 0) out_f[pd + r * (NS + NS / 16)] = v[r];
+                    else if (NS == 1 && 16 % R == 0) out_f[pd + r] = v[r];   // d = j R: no carry into d / 16
+                    else out_f[smem_pad(d + r * NS)] = v[r];
+                }
             } else {
                 const FrameInfo fi = finfo[f];
                 // two frames per CTA: neighbouring lanes pair their stores (every lane stays

@@ -777,9 +777,11 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
 // (Y[slot][K tile][plane][p][ktile]).
 __device__ __forceinline__ long long unpack_at(const FArgs& a, long long slot, long long k, int p, long long* ps)
 {
-    if (a.ktile > 0) {
-        *ps = (long long)a.n * a.ktile;
-        return ((slot * (a.Kpad / a.ktile) + k / a.ktile) * 2LL * a.n + p) * a.ktile + k % a.ktile;
+    if (a.ktile > 0) {   // the integer mode's tile is kIntKTile (a power of two: shifts, not divisions)
+        constexpr long long KT = kIntKTile;
+        static_assert((KT & (KT - 1)) == 0, "K tile must be a power of two");
+        *ps = (long long)a.n * KT;
+        return ((slot * (a.Kpad / KT) + k / KT) * 2LL * a.n + p) * KT + (k & (KT - 1));
     }
     *ps = (long long)a.n * a.Kpad;
     return (slot * 2LL * a.n + p) * a.Kpad + k;

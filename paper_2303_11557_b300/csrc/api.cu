@@ -367,6 +367,16 @@ namespace {
 // without touching launch arguments captured in graphs.
 constexpr double kMaxPassband = 2.0;
 
+// The F-step's per-channel gains as the device holds them: sqrt(w_c) x passband gain x the
+// power-of-two pre-scale of the FP16 operand forms (1 otherwise), one multiply per value.
+mwax_status upload_gains(mwax_plan& p)
+{
+    std::vector<float> g(p.N);
+    for (int c = 0; c < p.N; ++c) g[c] = p.h_gain[c] * p.out_scale;   // exact: a power of two
+    MWAX_CUDA(cudaMemcpy(p.gain, g.data(), sizeof(float) * p.N, cudaMemcpyHostToDevice));
+    return MWAX_OK;
+}
+
 void set_prescale(mwax_plan& p)
 {
     if (p.prec != MWAX_FP16 && p.prec != MWAX_FP8 && p.prec != MWAX_FP16X3) return;
@@ -443,7 +453,6 @@ mwax_status setup(mwax_plan& p)
         return fail(MWAX_EINVAL, "channel averaging with fscrunch %d leaves an empty channel", p.F);
     p.n_groups = (int)groups.size();
     MWAX_CUDA(cudaMalloc(&p.gain, sizeof(float) * p.N));
-    MWAX_CUDA(cudaMemcpy(p.gain, gain.data(), sizeof(float) * p.N, cudaMemcpyHostToDevice));
     MWAX_CUDA(cudaMalloc(&p.groups, sizeof(Group) * groups.size()));
     MWAX_CUDA(cudaMemcpy(p.groups, groups.data(), sizeof(Group) * groups.size(), cudaMemcpyHostToDevice));
     p.h_groups = groups;
@@ -454,6 +463,10 @@ mwax_status setup(mwax_plan& p)
     // FP16 operands: power-of-two pre-scale keeping |Re X|, |Im X| <= 181 N (int8
     // magnitude 128 sqrt 2 summed over N samples) below 2^15; undone exactly after the MMA
     set_prescale(p);
+    {
+        mwax_status st = upload_gains(p);
+        if (st != MWAX_OK) return st;
+    }
     p.tensor_cores = p.prec != MWAX_FP32;
     if (p.prec == MWAX_FP8) {
         std::vector<int> cg(p.N, -1);
@@ -779,7 +792,6 @@ mwax_status enqueue_fstep(mwax_plan* p, const LaunchGroup& g, const int8_t* volt
     fa.n = p->n;
     fa.bs = p->bs;
     fa.nu = p->nu;
-    fa.out_scale = p->out_scale;
     fa.fs = p->fs;
     fa.delay_tab = p->cur_table;
     fa.tab_steps = p->cur_steps;
@@ -1030,8 +1042,7 @@ mwax_status mwax_plan_set_passband(mwax_plan* p, const float* gain)
     MWAX_CUDA(cudaStreamSynchronize(p->stream));   // earlier calls may still read the table
     p->passband = g;
     for (int c = 0; c < p->N; ++c) p->h_gain[c] = p->h_avg_gain[c] * g[c];
-    MWAX_CUDA(cudaMemcpy(p->gain, p->h_gain.data(), sizeof(float) * p->N, cudaMemcpyHostToDevice));
-    return MWAX_OK;
+    return upload_gains(*p);
 }
 
 mwax_status mwax_correlate_host(mwax_plan* p, const int8_t* volt, const double* delay_poly, void* vis_out)

@@ -432,7 +432,6 @@ mwax_status mwax_beam_form(mwax_beamformer* b, const int8_t* volt, const double*
         fa.n = b->n;
         fa.bs = b->bs;
         fa.nu = b->nu;
-        fa.out_scale = 1.0f;
         fa.fs = b->fs;
         BEAM_CUDA(launch_fstep(b->N, FOUT_F32, fa, s, 0));
         build_units(b, f0, nfr, steps, b->h_units);

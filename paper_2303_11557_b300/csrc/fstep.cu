@@ -244,7 +244,8 @@ struct FrameInfo {
 template <int N, int OUTK>
 struct Store {
     // Write one corrected spectral value: real plane at element `at`, imaginary plane at
-    // `at + plane_stride` of the operand buffer (FP32, or FP16 pre-scaled by out_scale;
+    // `at + plane_stride` of the operand buffer (FP32, or FP16, v already carrying the
+    // power-of-two pre-scale through the channel gain;
     // FP16 pairs: the remainder v - hi, exact in FP32, rounded again to FP16 half a row
     // further on, so hi + lo carries 22 significant bits).
     __device__ __forceinline__ static void run(const FArgs& a, long long at, long long plane_stride, float2 v,
@@ -257,7 +258,7 @@ struct Store {
         } else if (OUTK == FOUT_F16X3) {
             __half* Y = static_cast<__half*>(a.Y);
             const long long lo = a.Kpad >> 1;
-            const float xr = v.x * a.out_scale, xi = v.y * a.out_scale;
+            const float xr = v.x, xi = v.y;
             const __half hr = __float2half_rn(xr), hi = __float2half_rn(xi);
             Y[at] = hr;
             Y[at + plane_stride] = hi;
@@ -265,8 +266,8 @@ struct Store {
             Y[at + plane_stride + lo] = __float2half_rn(xi - __half2float(hi));
         } else {
             __half* Y = static_cast<__half*>(a.Y);
-            Y[at] = __float2half_rn(v.x * a.out_scale);
-            Y[at + plane_stride] = __float2half_rn(v.y * a.out_scale);
+            Y[at] = __float2half_rn(v.x);
+            Y[at + plane_stride] = __float2half_rn(v.y);
         }
     }
 };
@@ -293,7 +294,7 @@ __device__ __forceinline__ void store_frame_pair(const FArgs& a, long long at, l
             Y[at + ps] = y.y;
         }
     } else if (OUTK == FOUT_F16) {
-        const __half2 h2 = __floats2half2_rn(y.x * a.out_scale, y.y * a.out_scale);
+        const __half2 h2 = __floats2half2_rn(y.x, y.y);
         const uint32_t hu = *reinterpret_cast<const uint32_t*>(&h2);
         const uint32_t other = __shfl_xor_sync(0xffffffffu, hu, 1);
         __half* Y = static_cast<__half*>(a.Y);
@@ -305,7 +306,7 @@ __device__ __forceinline__ void store_frame_pair(const FArgs& a, long long at, l
             Y[at + ps] = __high2half(h2);
         }
     } else {   // FP16 hi/lo pairs: lo values half a row further on
-        const float xr = y.x * a.out_scale, xi = y.y * a.out_scale;
+        const float xr = y.x, xi = y.y;
         const __half2 h2 = __floats2half2_rn(xr, xi);
         const float2 hf = __half22float2(h2);
         const __half2 l2 = __floats2half2_rn(xr - hf.x, xi - hf.y);
@@ -803,7 +804,7 @@ __global__ void __launch_bounds__(256) unpack_kernel(const FArgs a)
         if (off + 8 <= a.bs && k + 8 <= a.Kc && (k & 7) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
             const int4 raw = __ldg(reinterpret_cast<const int4*>(src));
             const char2* x = reinterpret_cast<const char2*>(&raw);
-            const float g = __ldg(&a.gain[0]) * (OUTK == FOUT_F16 ? a.out_scale : 1.0f);
+            const float g = __ldg(&a.gain[0]);
             long long ps;
             const long long at = unpack_at(a, slot, k, p, &ps);   // 8 frames in one row (tiles are multiples of 8)
             if (OUTK == FOUT_F16) {

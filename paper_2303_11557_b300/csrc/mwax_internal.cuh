@@ -51,7 +51,8 @@ struct FArgs {
     const double* delay;  // [n][3] or nullptr
     void* Y;              // operands [slot][N][2][n][Kpad]
     const float2* tw;     // e^{-2 pi i k / N}, k < N
-    const float* gain;    // [N] sqrt of each ultrafine channel's averaging weight
+    const float* gain;    // [N] sqrt of each ultrafine channel's averaging weight (x passband gain,
+                          //   x the FP16 forms' power-of-two pre-scale keeping |X| in range)
     long long m_begin;
     long long n_frames;   // frames with data
     long long n_store;    // frames stored (>= n_frames: the rest are written as zeros)
@@ -60,7 +61,6 @@ struct FArgs {
     int n;
     int bs;
     double nu;
-    float out_scale;      // FP16: power-of-two pre-scale keeping |X| in range
     double fs;            // coarse-channel sample rate (1.28 MS/s unless oversampled)
     const double* delay_tab;   // [n][tab_steps] tabulated fractional delays (s), or nullptr
     long long tab_steps;

@@ -223,7 +223,6 @@ extern "C" mwax_status mwax_correlate_noalloc(const mwax_plan_desc* desc, const 
     fa_.n = n;
     fa_.bs = bs;
     fa_.nu = d.sky_freq_hz;
-    fa_.out_scale = 1.0f;
     fa_.fs = fs;
     if ((e = launch_fstep(N, FOUT_F32, fa_, s, 0)) != cudaSuccess) return cuda_error(e, "F-step launch");
     XArgs xa;

@@ -380,7 +380,11 @@ def run_serve(mw, torch, host_base, args, periods: int = 2):
                         "{128,256,512}, mixed N/F/int as the 24-channel batch, 20 % integer mode, host pinned voltages",
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
             "deadline_ms": 1e3 * SUBOBS_S, "deadline_misses": st["deadline_misses"], "completed": done,
-            "sustained_channels": done * SUBOBS_S / wall, "wall_s": wall,
+            # channels kept in real time: the offered channels x the share of their requests
+            # that met the 8 s deadline; the completed sub-observations per wall second
+            # (which counts the last period's processing tail over a short run) beside it
+            "sustained_channels": len(chans) * (done - st["deadline_misses"]) / max(1, done),
+            "throughput_channels": done * SUBOBS_S / wall, "wall_s": wall,
             "latency_note": "percentiles include the warm-up requests (one per shape)",
             "lanes": 4, "hbm_budget_gb": 160}
 

@@ -47,9 +47,7 @@ WORKSPACE = 48 << 30
 # DRAM bytes (read + write) per integration slot of the dominant kernel, from an ncu
 # capture of the one-integration case (profiles/).  Reported only while the kernel's
 # source is byte-identical to the one captured (sha1 prefix of its .cu file).
-TRAFFIC = {"xstep_simt_kernel": ("paper_2303_11557_b300/csrc/xstep_simt.cu", "801bae888475", 6.645909e9 + 0.100315e9),
-           "xstep_tc_kernel<0> (fp16)": ("paper_2303_11557_b300/csrc/xstep_tc.cu", "afc1d7f6e301",
-                                             (5.340589e9 + 0.290356e9) / 3)}   # 3-slot capture
+TRAFFIC = {"xstep_simt_kernel": ("paper_2303_11557_b300/csrc/xstep_simt.cu", "801bae888475", 6.645909e9 + 0.100315e9)}
 
 
 def traffic_per_slot(kernel: str):

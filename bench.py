@@ -156,14 +156,14 @@ def algorithmic_work(T: int, N: int, F: int, K: int, n_ints: int, prec_bytes: in
 
 
 # ------------------------------------------------------------------------- cpu / oracle
-def oracle_sample_time(threads_note: dict):
-    """Time the FP64 oracle on a bounded sample of the workload: a 32-tile sub-array, one
+def oracle_sample_time(threads_note: dict, Ts: int = 32):
+    """Time the FP64 oracle on a bounded sample of the workload: a Ts-tile sub-array, one
     0.5 s integration (5000 frames), same N, F and delays.  Returns (seconds per 8 s
     256-tile sub-observation extrapolated, description, measured seconds)."""
     import oracle
     import synth
     W = WORKLOAD
-    Ts, N, F = 32, W["fft_len"], W["fine_avg"]
+    N, F = W["fft_len"], W["fine_avg"]
     K = int(W["int_time_s"] * FS) // N
     S = K * N
     d = synth.tile_delays_linear(W["seed"], Ts)
@@ -187,6 +187,22 @@ def oracle_sample_time(threads_note: dict):
               f"x{bp_f / bp_s:.1f} baselines, x{n_ints} integrations")
     threads_note["cores"] = int(os.environ.get("OMP_NUM_THREADS", 0)) or len(os.sched_getaffinity(0))
     return est, desc_s, t_all
+
+
+def oracle_one_core():
+    """The same oracle timing on one host core (a separate process with OMP_NUM_THREADS=1,
+    which the oracle's OpenMP runtime reads at start), on a 16-tile sub-array so that it
+    stays a bounded sample; extrapolated to the workload the same way."""
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; n = {}; "
+            "e, s, t = bench.oracle_sample_time(n, Ts=16); print(json.dumps([e, s, t]))" % ROOT)
+    try:
+        res = subprocess.run([sys.executable, "-c", code], env=dict(os.environ, OMP_NUM_THREADS="1"),
+                             capture_output=True, text=True, timeout=300)
+        est, sample, t = json.loads(res.stdout.strip().splitlines()[-1])
+    except (subprocess.SubprocessError, ValueError, IndexError, OSError) as e:
+        return {"unavailable": f"one-core oracle run failed: {type(e).__name__}"}
+    return {"value": SUBOBS_S / est, "unit": "channels", "cores": 1, "sample": sample, "measured_s": t,
+            "extrapolated_s_per_subobs": est}
 
 
 # ----------------------------------------------------------------------------- arms
@@ -681,6 +697,7 @@ def run_mine(args, world, rank, local):
         est, sample, _ = oracle_sample_time(note)
         cpu = {"value": SUBOBS_S / est, "unit": "channels", "cores": note["cores"], "kind": "oracle",
                "sample": sample, "extrapolated_s_per_subobs": est}
+        cpu["one_core"] = oracle_one_core()
 
     if rank != 0:
         return

@@ -189,6 +189,22 @@ def oracle_sample_time(threads_note: dict, Ts: int = 32):
     return est, desc_s, t_all
 
 
+def oracle_config0_time():
+    """Seconds the FP64 oracle takes (all host cores) for the whole parity workload of 16
+    tiles, 0.4 s, N = 128, no averaging (not extrapolated: it runs in full)."""
+    import oracle
+    import synth
+    T, N, S = 16, 128, 512_000
+    d = synth.tile_delays_fixed(T)
+    volt = synth.voltages(0x4D574158, 2 * T, S, tones=synth.point_source_tones(0x4D574158), delay_c01=d[:, :2],
+                          sky_freq_hz=WORKLOAD["sky_freq_hz"])
+    desc = oracle.Desc(n_tiles=T, fft_len=N, fine_avg=1, int_frames=S // N, n_samples=S,
+                       sky_freq_hz=WORKLOAD["sky_freq_hz"], dc_exclude=0)
+    t0 = time.perf_counter()
+    oracle.correlate(desc, volt, d)
+    return time.perf_counter() - t0
+
+
 def oracle_one_core():
     """The same oracle timing on one host core (a separate process with OMP_NUM_THREADS=1,
     which the oracle's OpenMP runtime reads at start), on a 16-tile sub-array so that it
@@ -698,6 +714,7 @@ def run_mine(args, world, rank, local):
         cpu = {"value": SUBOBS_S / est, "unit": "channels", "cores": note["cores"], "kind": "oracle",
                "sample": sample, "extrapolated_s_per_subobs": est}
         cpu["one_core"] = oracle_one_core()
+        cpu["config0_whole_run_s"] = oracle_config0_time()
 
     if rank != 0:
         return

@@ -354,12 +354,18 @@ mwax_status mwax_plan_autotune(mwax_plan* p, const int8_t* voltages, const doubl
     }
     // stage 2: tile window x run length, with that F-step variant
     if (st == MWAX_OK) p->fvariant = best.fstep_variant;
+    std::vector<std::pair<int, int>> tried;   // (window, run length) configured so far
+    tried.push_back({w0, rl0});               // measured in stage 1
     for (int w : windows)
         for (int rl : runs) {
             if (st != MWAX_OK) break;
-            if (w == w0 && rl != 0 && rl == rl0) continue;   // measured in stage 1
             st = configure_x(*p, rl, w);
             if (st != MWAX_OK) break;
+            // candidates that configure the same launches (run lengths clamped to the
+            // channel count, the pair form's fixed window) are timed once
+            const std::pair<int, int> got{p->window, p->run_len};
+            if (std::find(tried.begin(), tried.end(), got) != tried.end()) continue;
+            tried.push_back(got);
             float ms;
             time_call(ms);
             if (st != MWAX_OK) break;

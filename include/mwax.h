@@ -257,10 +257,10 @@ typedef struct {
  * three calls per candidate, timed with CUDA events on the plan's stream (the fastest of
  * the three counts).  First the F-step variant (radix-32 or generic, for N = 32..512) with
  * the plan's current X-step choice; then, with the faster variant, the tile window (256 or
- * 128, FP16 / FP8 forms; 128 only for MWAX_FP16X3) x the run length (the plan's modelled choice, 3, 5, 11 and all
- * output channels; candidates that configure the same launches are timed once).  Keeps the
- * fastest.  Synchronous.  vis_out is overwritten with a valid
- * result.  best (may be NULL) receives the choice and its time.
+ * 128 for the FP16 / FP8 forms; 128 only for MWAX_FP16X3) x the run length (the plan's
+ * modelled choice, 3, 5, 11 and all output channels; candidates that configure the same
+ * launches are timed once).  Keeps the fastest.  Synchronous.  vis_out is overwritten with
+ * a valid result.  best (may be NULL) receives the choice and its time.
  */
 mwax_status mwax_plan_autotune(mwax_plan* plan, const int8_t* voltages, const double* delay_poly, void* vis_out,
                                mwax_tuning* best);

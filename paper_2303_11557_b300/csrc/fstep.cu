@@ -335,6 +335,32 @@ __device__ __forceinline__ void store_frame_pair(const FArgs& a, long long at, l
     }
 }
 
+// Two neighbouring frames of one output channel (frame 0 at element `at`, an even index;
+// frame 1 at at + 1) written by one thread: each plane's two values as one word (FP32: 8
+// bytes, FP16: 4 bytes; FP16 pairs: hi and lo words, lo half a row further on).
+template <int OUTK>
+__device__ __forceinline__ void store_two_frames(const FArgs& a, long long at, long long ps, float2 y0, float2 y1)
+{
+    if (OUTK == FOUT_F32) {
+        float* Y = static_cast<float*>(a.Y);
+        *reinterpret_cast<float2*>(Y + at) = make_float2(y0.x, y1.x);
+        *reinterpret_cast<float2*>(Y + at + ps) = make_float2(y0.y, y1.y);
+    } else if (OUTK == FOUT_F16) {
+        __half* Y = static_cast<__half*>(a.Y);
+        *reinterpret_cast<__half2*>(Y + at) = __floats2half2_rn(y0.x, y1.x);
+        *reinterpret_cast<__half2*>(Y + at + ps) = __floats2half2_rn(y0.y, y1.y);
+    } else {
+        __half* Y = static_cast<__half*>(a.Y);
+        const long long lo = a.Kpad >> 1;
+        const __half2 hr = __floats2half2_rn(y0.x, y1.x), hi = __floats2half2_rn(y0.y, y1.y);
+        const float2 fr = __half22float2(hr), fi = __half22float2(hi);
+        *reinterpret_cast<__half2*>(Y + at) = hr;
+        *reinterpret_cast<__half2*>(Y + at + ps) = hi;
+        *reinterpret_cast<__half2*>(Y + at + lo) = __floats2half2_rn(y0.x - fr.x, y1.x - fr.y);
+        *reinterpret_cast<__half2*>(Y + at + ps + lo) = __floats2half2_rn(y0.y - fi.x, y1.y - fi.y);
+    }
+}
+
 // Delay phasor e^{2 pi i (phi0 + u d)} of ultrafine offset u (|u| < 4096), d = d_hi + d_lo
 // with d_hi holding 12 significant bits so that u * d_hi is exact in FP32.
 __device__ __forceinline__ float2 delay_phasor_u(float phi0, float d_hi, float d_lo, int u)
@@ -690,9 +716,17 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
         }
     }
 
+    // Two frames per pass-2 thread for N <= 128: frames 2i and 2i + 1 (neighbours along K)
+    // are stored as words.  Pass 1 writes frame f to row (f % 2) FB/2 + f / 2, so that the
+    // two rows a thread reads (i and i + FB/2) and the rows of a half-warp stay in distinct
+    // banks.
+    constexpr bool PAIRS2 = T <= 4;
+    static_assert(!PAIRS2 || FB % 2 == 0, "frame pairs");
+
     // ---- pass 1: 32-point DFTs of the T decimated sub-sequences of each frame
     for (int idx = threadIdx.x; idx < FB * T; idx += NT) {
-        const int t = idx % T, f = idx / T;
+        const int t = idx % T, row = idx / T;
+        const int f = PAIRS2 ? 2 * (row % (FB / 2)) + row / (FB / 2) : row;
         const long long fl = f0 + f;
         float2 v[32];
         if (fl < a.n_frames && !frame_zeroed(a, p, (a.m_begin + fl) * (long long)N)) {
@@ -710,9 +744,93 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
         }
         Dft<32>::run(v);
 #pragma unroll
-        for (int r = 0; r < 32; ++r) buf[f * ROW + SR * t + r] = v[r];
+        for (int r = 0; r < 32; ++r) buf[row * ROW + SR * t + r] = v[r];
     }
     __syncthreads();
+
+    if constexpr (PAIRS2) {
+        // ---- pass 2, frame pairs: radix-T butterflies j of frames 2i and 2i + 1 (rows i and
+        // i + FB/2), sharing the twiddle and gain loads; phasor per frame; word stores
+        constexpr int PP = FB / 2;
+        constexpr int JP = 32 * PP / NT;   // butterflies per thread
+        static_assert(JP * NT == 32 * PP, "whole butterflies per thread");
+        const int fp = threadIdx.x % PP;
+        const int jb = (threadIdx.x / PP) * JP;
+        const FrameR32 fi0 = finfo[2 * fp], fi1 = finfo[2 * fp + 1];
+        const bool live0 = fi0.slot >= 0, live1 = fi1.slot >= 0;
+        if (!live0 && !live1) return;
+        // both frames in one slot, frame 0 at an even index: one word per value
+        const bool paired = live0 && live1 && fi1.slot == fi0.slot && (fi0.k & 1) == 0;
+        const long long cs = 2LL * a.n * a.Kpad;
+        const long long ps = (long long)a.n * a.Kpad;
+        const long long base0 = (fi0.slot * N * 2LL * a.n + p) * a.Kpad + fi0.k;
+        const long long d1 = (fi1.slot * N * 2LL * a.n + p) * a.Kpad + fi1.k - base0;   // frame 1 - frame 0
+        long long at[T];
+#pragma unroll
+        for (int r = 0; r < T; ++r) {
+            const int k = jb + 32 * r;
+            const bool low = (T >= 2) ? (r < T / 2) : (k < N - N / 2);
+            at[r] = base0 + (long long)(low ? k + N / 2 : k - (N - N / 2)) * cs;
+        }
+        float2 Ej0 = make_float2(1.0f, 0.0f), Ej1 = Ej0;
+        if (fi0.delay) Ej0 = delay_phasor_u(fi0.phi0, fi0.d_hi, fi0.d_lo, jb);
+        if (fi1.delay) Ej1 = delay_phasor_u(fi1.phi0, fi1.d_hi, fi1.d_lo, jb);
+        for (int jj = 0; jj < JP; ++jj) {
+            const int j = jb + jj;
+            float2 v0[T], v1[T];
+#pragma unroll
+            for (int r = 0; r < T; ++r) {
+                v0[r] = buf[fp * ROW + SR * r + j];
+                v1[r] = buf[(fp + PP) * ROW + SR * r + j];
+                if (r > 0) {
+                    const float2 w = tw[j * r];
+                    v0[r] = c_mul(v0[r], w);
+                    v1[r] = c_mul(v1[r], w);
+                }
+            }
+            DftIf<T>::run(v0);
+            DftIf<T>::run(v1);
+            float2 E0 = Ej0, E1 = Ej1;
+#pragma unroll
+            for (int r = 0; r < T; ++r) {
+                const int k = j + 32 * r;
+                const bool low = (T >= 2) ? (r < T / 2) : (k < N - N / 2);
+                const int c = low ? k + N / 2 : k - (N - N / 2);
+                float2 y0 = v0[r], y1 = v1[r];
+                if (fi0.delay) {
+                    if (T >= 2) {
+                        if (r == T / 2) E0 = c_mul(E0, fi0.wrap);
+                        y0 = c_mul(y0, E0);
+                    } else {
+                        y0 = c_mul(y0, low ? E0 : c_mul(E0, fi0.wrap));
+                    }
+                    E0 = c_mul(E0, fi0.step32);
+                }
+                if (fi1.delay) {
+                    if (T >= 2) {
+                        if (r == T / 2) E1 = c_mul(E1, fi1.wrap);
+                        y1 = c_mul(y1, E1);
+                    } else {
+                        y1 = c_mul(y1, low ? E1 : c_mul(E1, fi1.wrap));
+                    }
+                    E1 = c_mul(E1, fi1.step32);
+                }
+                const float gn = gain[c];
+                y0 = make_float2(y0.x * gn, y0.y * gn);
+                y1 = make_float2(y1.x * gn, y1.y * gn);
+                if (paired) {
+                    store_two_frames<OUTK>(a, at[r], ps, y0, y1);
+                } else {
+                    if (live0) Store<N, OUTK>::run(a, at[r], ps, y0, fi0.slot, c, p);
+                    if (live1) Store<N, OUTK>::run(a, at[r] + d1, ps, y1, fi1.slot, c, p);
+                }
+                at[r] += cs;
+            }
+            if (fi0.delay) Ej0 = c_mul(Ej0, fi0.step1);
+            if (fi1.delay) Ej1 = c_mul(Ej1, fi1.step1);
+        }
+        return;
+    }
 
     // ---- pass 2: radix-T butterflies j = 0..31 of each frame, then phasor, gain, store
     const int f = threadIdx.x % FB;

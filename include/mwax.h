@@ -61,7 +61,7 @@ typedef enum {
     MWAX_INT8 = 3,  /* no FFT (N = 1, F = 1), exact integer sums, int64 output           */
     MWAX_FP16X3 = 4 /* FP32 FFT; each operand an FP16 hi/lo pair (22 significant bits),
                        three FP16 products per complex term on tcgen05 (the lo x lo term,
-                       2^-22 of the product, dropped), partial sums of 64 frames added in
+                       2^-22 of the product, dropped), partial sums of 128 frames added in
                        FP32: FP32-level error on the tensor cores; 128 x 128 tiles,
                        operands 8 B per sample and path like MWAX_FP32                  */
 } mwax_precision;

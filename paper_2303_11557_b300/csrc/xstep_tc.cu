@@ -763,6 +763,9 @@ cudaError_t launch_xstep_tc(const XLaunch& L, const XItem* items, int n_items, i
         if (mj == MODE_INT && (L.jobs[j].a.seg_frames <= 0 || L.jobs[j].a.seg_frames % 512 != 0 ||
                                L.jobs[j].a.seg_frames > 100 * 512))
             return cudaErrorInvalidValue;   // segments of whole exact chunks, int32-safe
+        if (mj == MODE_INT && (L.jobs[j].a.ktile <= 0 || L.jobs[j].a.ktile % 32 != 0 ||
+                               L.jobs[j].a.Kpad % L.jobs[j].a.ktile != 0))
+            return cudaErrorInvalidValue;   // K-tiled operands: whole k-blocks per tile
     }
     if (mode == MODE_PAIRS) return launch_tc_kernel<MODE_PAIRS>(L, items, n_items, counter, status, 1, s);
     if (mode == MODE_INT) return launch_tc_kernel<MODE_INT>(L, items, n_items, counter, status, 1, s);

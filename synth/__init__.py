@@ -65,13 +65,15 @@ def uniform(seed: int, n: int) -> np.ndarray:
 
 
 def voltages(seed: int, n_paths: int, n_samples: int, *, block_samples: int = BLOCK_SAMPLES,
-             sigma: float = 16.0, tones=None, delay_c01=None, sky_freq_hz: float = 0.0,
+             sigma: float = 16.0, tones=None, delay_c01=None, delay_poly=None, sky_freq_hz: float = 0.0,
              sample0: int = 0, out: np.ndarray | None = None) -> np.ndarray:
     """Synthetic int8 voltages, shape (n_blocks, n_paths, block_samples, 2).
 
     tones: list of (freq_hz, amplitude, phase_rad, path) with path = -1 for a signal
-    common to every path (delayed per path by delay_c01), else the one path carrying it.
-    delay_c01: float64 [n_paths, 2] of (c0 [s], c1 [s/s]) or None.
+    common to every path (delayed per path by its delay polynomial), else the one path
+    carrying it.
+    delay_poly: float64 [n_paths, 3] of (c0 [s], c1 [s/s], c2 [s/s^2]) or None;
+    delay_c01: float64 [n_paths, 2] of (c0, c1), the same with c2 = 0 (one of the two).
     """
     if n_samples % block_samples:
         raise ValueError("n_samples must be a whole number of blocks")
@@ -82,8 +84,13 @@ def voltages(seed: int, n_paths: int, n_samples: int, *, block_samples: int = BL
     ph = np.array([t[2] for t in tones] or [0.0], dtype=np.float64)
     pa = np.array([t[3] for t in tones] or [0], dtype=np.int32)
     d = None
+    if delay_c01 is not None and delay_poly is not None:
+        raise ValueError("give delay_c01 or delay_poly, not both")
     if delay_c01 is not None:
-        d = np.ascontiguousarray(np.asarray(delay_c01, dtype=np.float64).reshape(n_paths, 2))
+        d = np.zeros((n_paths, 3))
+        d[:, :2] = np.asarray(delay_c01, dtype=np.float64).reshape(n_paths, 2)
+    elif delay_poly is not None:
+        d = np.ascontiguousarray(np.asarray(delay_poly, dtype=np.float64).reshape(n_paths, 3))
     if out is None:
         out = np.empty((n_blocks, n_paths, block_samples, 2), dtype=np.int8)
     assert out.dtype == np.int8 and out.flags.c_contiguous and out.size == n_blocks * n_paths * block_samples * 2
@@ -120,4 +127,19 @@ def tile_delays_linear(seed: int, n_tiles: int, max_c0: float = 50e-9, max_c1: f
     for t in range(n_tiles):
         d[2 * t:2 * t + 2, 0] = max_c0 * u[2 * t]
         d[2 * t:2 * t + 2, 1] = max_c1 * (2 * u[2 * t + 1] - 1)
+    return d
+
+
+def path_delays_quadratic(seed: int, n_tiles: int, duration_s: float, max_c0: float = 50e-9,
+                          max_c1: float = 5e-9, end_c2: float = 20e-9) -> np.ndarray:
+    """Seeded quadratic delays, a different polynomial for every signal path (the x and
+    y pols of a tile included): c0 in U[0, max_c0], c1 in U[-max_c1, max_c1] and c2 in
+    U[-1, 1] * end_c2 / duration_s^2, so the quadratic term alone reaches up to end_c2
+    seconds by the end of a call of duration_s.  Returns float64 [n_paths, 3]."""
+    n = 2 * n_tiles
+    u = uniform(seed ^ 0x71756164, 3 * n).reshape(n, 3)
+    d = np.empty((n, 3))
+    d[:, 0] = max_c0 * u[:, 0]
+    d[:, 1] = max_c1 * (2 * u[:, 1] - 1)
+    d[:, 2] = end_c2 / (duration_s * duration_s) * (2 * u[:, 2] - 1)
     return d

@@ -14,11 +14,12 @@
  *   - tone t is either common to all paths (a point source seen by every
  *     signal path with that path's delay) or private to one path (the paper's
  *     hand-crafted digital-phase-rotator test vectors, Sec. 3.1);
- *   - tau_p(t) = c0 + c1 t (seconds), t_n = n / Fs, Fs = 1.28 MS/s;
+ *   - tau_p(t) = c0 + c1 t + c2 t^2 (seconds), t_n = n / Fs, Fs = 1.28 MS/s;
  *   - rint() rounds half to even; values are clipped to [-127, 127].
- * Each tone's phase is linear in n, so it is advanced by a fixed complex
- * rotation per sample and re-seeded from an exact FP64 phase at the start of
- * every 50 ms block (no drift across blocks).
+ * Each tone's phase is a quadratic A + B n + C n^2 in the sample index, so it is
+ * advanced per sample by a rotation whose angle B + C (2n + 1) itself grows by the
+ * fixed 2C per sample (one extra complex multiply when C != 0); both are re-seeded
+ * from exact FP64 phases at the start of every 50 ms block (no drift across blocks).
  *
  * Voltage layout: int8 [block][path][block_samples][2] (re, im), i.e. the
  * sub-observation is a sequence of data blocks, each holding every signal
@@ -77,45 +78,56 @@ void synth_gauss(uint64_t seed, uint64_t path, uint64_t sample, double sigma, do
  *   tone_amp[t]        : amplitude a_t
  *   tone_phase[t]      : starting phase phi_t (radians)
  *   tone_path[t]       : -1 = common to all paths, else the only path that carries it
- *   delay_c01          : [n_paths][2] (c0 s, c1 s/s) or NULL (no delay)
+ *   delay_poly         : [n_paths][3] (c0 s, c1 s/s, c2 s/s^2) or NULL (no delay)
  *   sky_freq_hz        : nu, sky frequency of the coarse-channel centre
  *   sample0            : absolute index of the first sample (lets callers make any window)
  */
 void synth_voltages(uint64_t seed, int n_paths, long long n_blocks, int block_samples, double sigma,
                     int n_tones, const double* tone_freq_hz, const double* tone_amp,
-                    const double* tone_phase, const int* tone_path, const double* delay_c01,
+                    const double* tone_phase, const int* tone_path, const double* delay_poly,
                     double sky_freq_hz, long long sample0, int8_t* out)
 {
     long long n_units = n_blocks * (long long)n_paths;
 #pragma omp parallel
     {
-        double* rot_re = (double*)malloc(sizeof(double) * (size_t)(2 * (n_tones > 0 ? n_tones : 1)));
-        double* rot_im = rot_re + (n_tones > 0 ? n_tones : 1);
-        double* cur_re = (double*)malloc(sizeof(double) * (size_t)(2 * (n_tones > 0 ? n_tones : 1)));
-        double* cur_im = cur_re + (n_tones > 0 ? n_tones : 1);
+        int nt_cap = n_tones > 0 ? n_tones : 1;
+        /* per tone: current value, per-sample rotation, and the rotation's own per-sample
+         * rotation (quadratic phase) */
+        double* buf = (double*)malloc(sizeof(double) * (size_t)(6 * nt_cap));
+        double *cur_re = buf, *cur_im = buf + nt_cap, *rot_re = buf + 2 * nt_cap, *rot_im = buf + 3 * nt_cap;
+        double *acc_re = buf + 4 * nt_cap, *acc_im = buf + 5 * nt_cap;
+        int* quad = (int*)malloc(sizeof(int) * (size_t)nt_cap);
 #pragma omp for schedule(dynamic, 4)
         for (long long unit = 0; unit < n_units; ++unit) {
             long long blk = unit / n_paths;
             int p = (int)(unit % n_paths);
             long long s0 = sample0 + blk * (long long)block_samples;
-            double c0 = delay_c01 ? delay_c01[2 * p] : 0.0;
-            double c1 = delay_c01 ? delay_c01[2 * p + 1] : 0.0;
-            /* phase(n) in cycles = phi/2pi + f (t - c0 - c1 t) - nu (c0 + c1 t), t = n/Fs
-             *                    = A + B n                                            */
+            double c0 = delay_poly ? delay_poly[3 * p] : 0.0;
+            double c1 = delay_poly ? delay_poly[3 * p + 1] : 0.0;
+            double c2 = delay_poly ? delay_poly[3 * p + 2] : 0.0;
+            /* phase(n) in cycles = phi/2pi + f (t - tau(t)) - nu tau(t), t = n/Fs,
+             * tau(t) = c0 + c1 t + c2 t^2, i.e.  A + B n + C n^2                     */
             int nt = 0;
             for (int t = 0; t < n_tones; ++t) {
                 if (tone_path[t] >= 0 && tone_path[t] != p) continue;
                 double f = tone_freq_hz[t];
                 double A = tone_phase[t] / SYNTH_TWO_PI - (f + sky_freq_hz) * c0;
                 double B = (f - (f + sky_freq_hz) * c1) / SYNTH_FS;
-                /* exact phase at s0, reduced to [0,1) cycles before the trig call */
-                double cyc = A + B * (double)s0;
+                double C = -(f + sky_freq_hz) * c2 / (SYNTH_FS * SYNTH_FS);
+                double sd = (double)s0;
+                /* exact phase at s0 and the step from s0 to s0 + 1, each reduced to [0,1)
+                 * cycles before the trig call */
+                double cyc = A + B * sd + C * sd * sd;
                 cyc -= floor(cyc);
-                double stp = B - floor(B);
+                double stp = B + C * (2.0 * sd + 1.0);
+                stp -= floor(stp);
                 cur_re[nt] = tone_amp[t] * cos(SYNTH_TWO_PI * cyc);
                 cur_im[nt] = tone_amp[t] * sin(SYNTH_TWO_PI * cyc);
                 rot_re[nt] = cos(SYNTH_TWO_PI * stp);
                 rot_im[nt] = sin(SYNTH_TWO_PI * stp);
+                quad[nt] = C != 0.0;
+                acc_re[nt] = cos(SYNTH_TWO_PI * 2.0 * C);   /* the step grows by 2C per sample */
+                acc_im[nt] = sin(SYNTH_TWO_PI * 2.0 * C);
                 ++nt;
             }
             int8_t* o = out + (size_t)unit * (size_t)block_samples * 2;
@@ -129,13 +141,19 @@ void synth_voltages(uint64_t seed, int n_paths, long long n_blocks, int block_sa
                     double ni = cur_re[k] * rot_im[k] + cur_im[k] * rot_re[k];
                     cur_re[k] = nr;
                     cur_im[k] = ni;
+                    if (quad[k]) {
+                        double rr = rot_re[k] * acc_re[k] - rot_im[k] * acc_im[k];
+                        double ri = rot_re[k] * acc_im[k] + rot_im[k] * acc_re[k];
+                        rot_re[k] = rr;
+                        rot_im[k] = ri;
+                    }
                 }
                 o[2 * i] = clip_round(re);
                 o[2 * i + 1] = clip_round(im);
             }
         }
-        free(rot_re);
-        free(cur_re);
+        free(buf);
+        free(quad);
     }
 }
 

@@ -25,17 +25,22 @@ def parity_error(vis_gpu, vis_ora, T):
 
 def workload(seed, T, n_samples, *, block_samples=64_000, delay="fixed", sky=synth.SKY_FREQ_HZ,
              sigma=16.0, rel_rms=0.3):
-    """Seeded noise + point-source voltages and the per-path delay polynomial."""
+    """Seeded noise + point-source voltages and the per-path delay polynomial.
+    delay: "fixed" (per tile, 0-50 ns), "linear" (per tile, c0 + c1 t), "quadratic" (a
+    different c0 + c1 t + c2 t^2 on every path, c2 t^2 reaching 20 ns by the end of the
+    call) or None (no correction; the source still carries the fixed delays)."""
     if delay == "fixed":
         dpoly = synth.tile_delays_fixed(T)
     elif delay == "linear":
         dpoly = synth.tile_delays_linear(seed, T)
+    elif delay == "quadratic":
+        dpoly = synth.path_delays_quadratic(seed, T, n_samples / synth.FS)
     else:
         dpoly = None
     src = dpoly if dpoly is not None else synth.tile_delays_fixed(T)
     volt = synth.voltages(seed, 2 * T, n_samples, block_samples=block_samples, sigma=sigma,
                           tones=synth.point_source_tones(seed, sigma=sigma, rel_rms=rel_rms),
-                          delay_c01=src[:, :2], sky_freq_hz=sky)
+                          delay_poly=src, sky_freq_hz=sky)
     return volt, dpoly
 
 

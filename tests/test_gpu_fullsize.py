@@ -1,7 +1,8 @@
 """Full-size parity: the 256-tile, 8 s sub-observation (512 signal paths, 10.24 M int8
 complex samples per path, 128-point FFT, 0.5 s integrations averaged by 4) run exactly
 as the benchmark runs it (same plan description and 48 GiB workspace, so the same
-launches), checked against the FP64 oracle on sampled outputs that the oracle computes one
+launches; the delays are a different quadratic polynomial on every signal path), checked
+against the FP64 oracle on sampled outputs that the oracle computes one
 by one: random (integration, baseline, channel, pol) entries plus the parallel-pol
 autocorrelations that the parity metric divides by.  Bars as in the small-case tests:
 FP32 and FP16 hi/lo pairs 1e-5, FP16 2e-3, FP8 3e-2 of the auto scale; the integer mode
@@ -24,9 +25,11 @@ TOL = {mw.MWAX_FP32: 1e-5, mw.MWAX_FP16: 2e-3, mw.MWAX_FP8: 3e-2, mw.MWAX_FP16X3
 
 @pytest.fixture(scope="module")
 def full_input():
-    delay = synth.tile_delays_linear(SEED, T)
+    # every signal path its own quadratic delay polynomial (c2 t^2 up to 20 ns by 8 s), the
+    # source delayed by the same polynomials
+    delay = synth.path_delays_quadratic(SEED, T, S / synth.FS)
     volt = np.empty((S // 64_000, 2 * T, 64_000, 2), dtype=np.int8)
-    synth.voltages(SEED, 2 * T, S, tones=synth.point_source_tones(SEED), delay_c01=delay[:, :2],
+    synth.voltages(SEED, 2 * T, S, tones=synth.point_source_tones(SEED), delay_poly=delay,
                    sky_freq_hz=synth.SKY_FREQ_HZ, out=volt)
     dev = torch.from_numpy(volt.reshape(-1)).cuda()
     yield volt, delay, dev

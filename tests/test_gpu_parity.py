@@ -109,6 +109,30 @@ def test_fft_lengths(N, F, prec):
     check(desc, volt, delay)
 
 
+@pytest.mark.parametrize("prec", FLOAT_PRECS)
+@pytest.mark.parametrize("N,F", [(128, 4), (1280, 10)])
+def test_quadratic_per_path_delays(prec, N, F):
+    # tau_p(t) = c0 + c1 t + c2 t^2 evaluated in FP64 at every frame centre (Sec. 4.3), a
+    # different polynomial on every signal path (x and y of one tile differ), through both
+    # FFT kernel families (two-pass radix-32 at N = 128, generic Stockham at N = 1280);
+    # 1.6 s of data so the c2 t^2 terms reach 20 ns, i.e. ~18 rad of fringe at 139.5 MHz
+    T, t_int, S = 24, 0.4, 2_048_000
+    if N not in _QUAD:   # one workload and oracle run per N, shared by the four forms
+        volt, delay = workload(0xC2 + N, T, S, delay="quadratic")
+        _QUAD[N] = (volt, delay, oracle.correlate(oracle_desc(T, N, F, t_int, S), volt, delay)[0])
+    volt, delay, ref = _QUAD[N]
+    assert np.all(delay[0::2] != delay[1::2]) and np.abs(delay[:, 2]).max() * 1.6 ** 2 > 10e-9
+    desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=t_int, samples_per_call=S,
+                       sky_freq_hz=synth.SKY_FREQ_HZ, precision=prec)
+    vis, _, plan = run_gpu(desc, volt, delay)
+    err = parity_error(vis, ref, T)
+    assert np.all(np.isfinite(vis)) and err.max() <= TOL[prec], f"max err {err.max():.3e}"
+    plan.close()
+
+
+_QUAD = {}
+
+
 @pytest.mark.parametrize("prec", [pytest.param(mw.MWAX_FP32, id="fp32"), pytest.param(mw.MWAX_FP16X3, id="fp16x3")])
 def test_one_8s_integration(prec):
     # the longest integration of the configurations: 80,000 frames of 128 points summed into

@@ -7,7 +7,8 @@ mathematics fix, never against a retyped copy of its own formulas:
   exactly representable in int8 give closed-form visibilities at the right channel,
   baseline and polarisation and zero elsewhere;
 * delay correction (Sec. 2.5.1, 4.3): closed-form fringe phase of a delayed tone,
-  and zero phase once corrected;
+  and zero phase once corrected, for static, linear and quadratic per-path delays
+  (the last through every oracle route that evaluates the polynomial);
 * a full cross-power matrix is Hermitian with real, non-negative autos;
 * closed-form expectation of a noise + point-source workload (statistical);
 * integer mode against numpy int64 brute force, and 2x input -> exactly 4x output.
@@ -162,6 +163,63 @@ def test_delay_tracking_frame_centre(N):
             for w in range(d.n_ints):
                 assert abs(np.angle(cor[w, b, c0, pol])) < 2e-3
                 assert abs(abs(cor[w, b, c0, pol]) - scale) < 2e-2 * scale
+
+
+@pytest.mark.parametrize("N", [16, 128])
+@pytest.mark.parametrize("route", ["correlate", "sampled", "ext"])
+def test_delay_quadratic_per_path_closed_form(N, route):
+    # Sec. 2.5.1 / 4.3 with the full delay polynomial tau_p(t) = c0 + c1 t + c2 t^2, a
+    # different one on each signal path (x and y of a tile differ too).  One frame per
+    # integration, so each visibility is a single frame's product: uncorrected, a common
+    # bin-centred tone shows the closed-form fringe -2 pi (nu + f)(tau_p(t_m) - tau_q(t_m))
+    # at the frame centre t_m = (m + 1/2) N / Fs; corrected, no phase is left.  Over the
+    # 6.4 ms call the c2 t^2 terms alone turn the fringe by up to ~1 rad, and c2 t (a
+    # dropped power) by ~100 rad.  Residual of the frame-centre sampling: the half-sample
+    # offset of the frame's mean time, 2 pi (nu + f) |tau_p' - tau_q'| / (2 Fs) < 1e-3 rad;
+    # int8 rounding (variance 1/12 per component) adds phase noise of rms
+    # sqrt(2) / (a sqrt(12 N)) per single-frame cross product, allowed 5 times over.
+    T, S = 2, 8192
+    nu = synth.SKY_FREQ_HZ
+    u0 = N // 4 - 1
+    f0 = u0 * FS / N
+    delay = np.array([[5e-9, 0.8e-6, 3e-5], [20e-9, -1.0e-6, -2.5e-5],
+                      [13e-9, 0.6e-6, 2e-5], [47e-9, -0.4e-6, -3e-5]])
+    d = oracle.Desc(n_tiles=T, fft_len=N, fine_avg=1, int_frames=1, n_samples=S, block_samples=S,
+                    sky_freq_hz=nu)
+    volt = synth.voltages(6, 4, S, block_samples=S, sigma=0.0, tones=[(f0, 100.0, 0.7, -1)],
+                          delay_poly=delay, sky_freq_hz=nu)
+    c0 = u0 + N // 2
+    frames = S // N
+    t = (np.arange(frames) + 0.5) * N / FS
+    tau = delay[:, 0][:, None] + delay[:, 1][:, None] * t + delay[:, 2][:, None] * t * t   # [path, frame]
+    if route == "correlate":
+        raw, _ = oracle.correlate(d, volt, None)
+        cor, _ = oracle.correlate(d, volt, delay)
+        pick = lambda v, w, b, pol: v[w, b, c0, pol]
+    elif route == "ext":
+        raw, _ = oracle.correlate_ext(d, oracle.Ext(), volt, None)
+        cor, _ = oracle.correlate_ext(d, oracle.Ext(), volt, delay)
+        pick = lambda v, w, b, pol: v[w, b, c0, pol]
+    else:
+        req = np.array([(w, b, c0, pol) for w in range(frames) for b in range(3) for pol in range(4)], dtype=np.int64)
+        look = {tuple(r): k for k, r in enumerate(req.tolist())}
+        raw = oracle.correlate_sampled(d, volt, None, req)
+        cor = oracle.correlate_sampled(d, volt, delay, req)
+        pick = lambda v, w, b, pol: v[look[(w, b, c0, pol)]]
+    scale = N * N * 1e4
+    tol = 1e-3 + 5 * np.sqrt(2) / (100.0 * np.sqrt(12 * N))
+    quad_turn = 0.0
+    for b, (i, j) in enumerate([(0, 0), (0, 1), (1, 1)]):
+        for pol in range(4):
+            p, q = 2 * i + (pol >> 1), 2 * j + (pol & 1)
+            for w in range(frames):
+                want = -2 * np.pi * (nu + f0) * (tau[p, w] - tau[q, w])
+                got = np.angle(pick(raw, w, b, pol))
+                assert abs(np.angle(np.exp(1j * (got - want)))) < tol
+                assert abs(np.angle(pick(cor, w, b, pol))) < tol
+                assert abs(abs(pick(cor, w, b, pol)) - scale) < 2e-2 * scale
+                quad_turn = max(quad_turn, abs(2 * np.pi * (nu + f0) * (delay[p, 2] - delay[q, 2]) * t[w] ** 2))
+    assert quad_turn > 0.5   # the quadratic term moves the fringe far beyond the tolerance
 
 
 def test_hermitian_full_matrix():

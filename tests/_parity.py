@@ -85,3 +85,25 @@ def sampled_error(got, want, req, n_main, tiles, T):
         aq = abs(want[look[(w, baseline_index(T, j, j), c, 3 * (pol & 1))]].real)
         err.append(abs(got[k] - want[k]) / np.sqrt(ap * aq))
     return np.array(err)
+
+
+# parity bars per precision (MWAX_* values: FP32 0, FP16 1, FP8 2, INT8 3, FP16X3 4)
+TOL_BY_PREC = {0: 1e-5, 1: 2e-3, 2: 3e-2, 4: 1e-5}
+
+
+def check_output_vs_oracle(T, N, F, int_time_s, n_samples, prec, volt, delay, vis, weights):
+    """A call's split output (vis, weights as numpy) against the full FP64 oracle on the
+    same inputs: integer mode bit-exact, float forms within their bar.  Returns the max
+    parity error (0 for the integer mode)."""
+    od = oracle_desc(T, N, F, int_time_s, n_samples, block_samples=volt.shape[2])
+    if prec == 3:
+        ref, rw = oracle.correlate_int(od, volt)
+        assert np.array_equal(vis, ref), "integer mode differs from the oracle"
+        assert np.array_equal(weights, rw.astype(np.float32))
+        return 0.0
+    ref, rw = oracle.correlate(od, volt, delay)
+    assert vis.shape == ref.shape and np.array_equal(weights, rw.astype(np.float32))
+    assert np.all(np.isfinite(vis))
+    err = parity_error(vis, ref, T).max()
+    assert err <= TOL_BY_PREC[prec], f"max err {err:.3e} (bar {TOL_BY_PREC[prec]:.0e})"
+    return err

@@ -1,13 +1,17 @@
 """Batched correlation (many coarse channels of mixed shapes and precisions in one
 schedule with one persistent X-step launch per round, CUDA-graph replay) and the
-autotuner.  Each plan's result in the batch must equal its result alone, bit for bit."""
+autotuner.  Each plan's result in the batch must equal its result alone, bit for bit,
+and that result must match the FP64 oracle at its precision's bar (integer mode bit-exact);
+the largest configuration shapes (512 tiles at N = 6400 and 1280) are checked on sampled
+outputs."""
 import numpy as np
 import pytest
 
 import oracle
 import paper_2303_11557_b300 as mw
 import synth
-from _parity import oracle_desc, parity_error, workload
+from _parity import (TOL_BY_PREC, check_output_vs_oracle, oracle_desc, parity_error, sample_requests,
+                     sampled_error, workload)
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -27,27 +31,33 @@ MIX = [
 
 
 def _inputs():
-    vs, ds, plans = [], [], []
+    vs, ds, plans, host = [], [], [], []
     for k, (T, N, F, t, S, prec, ws) in enumerate(MIX):
-        volt, delay = workload(500 + k, T, S, delay=None if prec == mw.MWAX_INT8 else "linear")
+        volt, delay = workload(500 + k, T, S, delay=None if prec == mw.MWAX_INT8 else "quadratic")
         plans.append(mw.mwax_plan_create_ex(mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=t,
                                                         samples_per_call=S, precision=prec,
                                                         sky_freq_hz=synth.SKY_FREQ_HZ,
                                                         workspace_limit=ws << 20)))
         vs.append(torch.from_numpy(volt.reshape(-1)).cuda())
         ds.append(None if delay is None else torch.from_numpy(delay).cuda())
-    return plans, vs, ds
+        host.append((volt, delay))
+    return plans, vs, ds, host
 
 
 def test_batch_equals_alone_and_graph_replay():
-    plans, vs, ds = _inputs()
+    plans, vs, ds, host = _inputs()
     alone = []
-    for p, v, d in zip(plans, vs, ds):
+    for k, (p, v, d) in enumerate(zip(plans, vs, ds)):
         mw.mwax_plan_set_stream(p)
         o = mw.empty_output(p)
+        o.fill_(0xAB)   # poison: every byte must be written
         mw.mwax_correlate(p, v, d, o)
         mw.mwax_plan_sync(p)
         alone.append(o.cpu().numpy().copy())
+        # the result alone against the FP64 oracle (so batch == alone == oracle)
+        T, N, F, t, S, prec, _ = MIX[k]
+        vis, w = mw.split_output(p, alone[-1])
+        check_output_vs_oracle(T, N, F, t, S, prec, host[k][0], host[k][1], vis, w)
     b = mw.Batch(plans)
     outs = [mw.empty_output(p) for p in plans]
     for call in range(3):                       # eager, capture + replay, replay
@@ -89,3 +99,44 @@ def test_autotune_keeps_parity():
                     mw.mwax_plan_sync(p)
                     vis, _ = mw.split_output(p, o)
                     assert parity_error(vis.cpu().numpy(), ref, T).max() <= tol
+
+
+# configuration-shaped channels of the 24-channel batch: 512 tiles at the two large FFT
+# lengths, 1 s of data each (0.5 / 0.25 s integrations), FP16 as the batch benchmark runs
+BIG = [
+    (512, 6400, 200, 0.5, 1_280_000, mw.MWAX_FP16),
+    (512, 1280, 40, 0.25, 1_280_000, mw.MWAX_FP16),
+    (128, 32, 1, 0.25, 1_280_000, mw.MWAX_FP16),
+]
+
+
+@pytest.mark.slow
+def test_batch_config_shapes_sampled_vs_oracle():
+    plans, vs, ds, host = [], [], [], []
+    for k, (T, N, F, t, S, prec) in enumerate(BIG):
+        volt, delay = workload(700 + k, T, S, delay="quadratic")
+        plans.append(mw.mwax_plan_create_ex(mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=t,
+                                                        samples_per_call=S, precision=prec,
+                                                        sky_freq_hz=synth.SKY_FREQ_HZ)))
+        vs.append(torch.from_numpy(volt.reshape(-1)).cuda())
+        ds.append(torch.from_numpy(delay).cuda())
+        host.append((volt, delay))
+    b = mw.Batch(plans)
+    outs = [mw.empty_output(p) for p in plans]
+    for o in outs:
+        o.fill_(0xAB)
+    b.correlate(vs, ds, outs)
+    b.sync()
+    for k, (T, N, F, t, S, prec) in enumerate(BIG):
+        vis, w = mw.split_output(plans[k], outs[k])
+        vis = vis.cpu().numpy()
+        assert np.all(w.cpu().numpy() == 1.0) and np.all(np.isfinite(vis))
+        n_ints, M = vis.shape[0], vis.shape[2]
+        req, n_main, tiles = sample_requests(0xB16 + k, T, [0, n_ints - 1], M, 16)
+        want = oracle.correlate_sampled(oracle_desc(T, N, F, t, S), host[k][0], host[k][1], req)
+        got = vis[req[:, 0], req[:, 1], req[:, 2], req[:, 3]]
+        err = sampled_error(got, want, req, n_main, tiles, T)
+        assert err.max() <= TOL_BY_PREC[prec], f"channel {k}: max err {err.max():.3e}"
+    b.close()
+    for p in plans:
+        p.close()

@@ -1,12 +1,13 @@
 """Serving loop: requests of mixed shapes and precisions (FP16 / FP8 / INT8 / FP32
 selectable per request) submitted while others run are admitted as lanes and HBM free up;
-every result must equal the same request run alone, bit for bit."""
+every result must equal the same request run alone, bit for bit, and each request's result
+alone must match the FP64 oracle at its precision's bar (integer mode bit-exact)."""
 import numpy as np
 import pytest
 
 import paper_2303_11557_b300 as mw
 import synth
-from _parity import workload
+from _parity import check_output_vs_oracle, workload
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -32,7 +33,7 @@ def _desc(T, N, F, t, S, prec):
 def test_server_mix_equals_alone(budget_mb, lanes):
     inputs, alone = [], []
     for k, (T, N, F, t, S, prec) in enumerate(REQS):
-        volt, delay = workload(900 + k, T, S, delay=None if prec == mw.MWAX_INT8 else "linear")
+        volt, delay = workload(900 + k, T, S, delay=None if prec == mw.MWAX_INT8 else "quadratic")
         hv = torch.from_numpy(volt.reshape(-1)).pin_memory()
         hd = None if delay is None else np.ascontiguousarray(delay)
         plan = mw.mwax_plan_create_ex(_desc(T, N, F, t, S, prec))
@@ -41,6 +42,8 @@ def test_server_mix_equals_alone(budget_mb, lanes):
         mw.mwax_correlate(plan, hv.cuda(), None if hd is None else torch.from_numpy(hd).cuda(), o)
         mw.mwax_plan_sync(plan)
         alone.append(o.cpu().numpy().copy())
+        vis, w = mw.split_output(plan, alone[-1])
+        check_output_vs_oracle(T, N, F, t, S, prec, volt, hd, vis, w)
         inputs.append((hv, hd, plan.output_bytes))
         plan.close()
     srv = mw.Server(hbm_budget=budget_mb << 20, n_lanes=lanes)

@@ -1,17 +1,28 @@
-// Allocation-free entry point: the FP32 correlation of a small plan with every piece of
-// device working memory (the X-step operand planes and the F/X tables) in fixed,
-// file-scope device arrays, for callers that cannot call cudaMalloc (for example code
-// that runs inside a CUDA-graph capture it does not control, in a process whose device
-// memory is owned by another allocator, or under a policy that forbids allocation after
-// start-up).  It reuses the library's F-step and CUDA-core X-step launchers unchanged.
+// Allocation-free entry point: the FP32 correlation of a small job with every piece of
+// device working memory (the X-step operand planes, the F/X tables and a status word) in
+// fixed, file-scope device arrays.  It serves callers that cannot call cudaMalloc: a
+// process whose device memory is owned by another allocator (a framework's caching pool
+// that has reserved the whole GPU), a plug-in whose host application forbids it to
+// allocate, or a real-time service that bans allocation after start-up because an
+// allocation can block or fail at an arbitrary time.  The F-step and the CUDA-core X-step
+// are the library's own launchers, unchanged.
 //
 // The arrays are part of the library image: every GPU that loads the library holds them
-// (about 33 MB) until the process exits.  Their host-side names are only stand-ins, so
-// their device addresses are looked up with cudaGetSymbolAddress once per device, with
-// that device current, on the first call made there.
+// (about 33.6 MB) until the process exits.  Their host-side names are only stand-ins, so
+// host code looks their device addresses up with cudaGetSymbolAddress, once per device and
+// context, with that device current, on the first call made there (under a lock; a new
+// context after cudaDeviceReset is looked up again).  Device code names them directly: a
+// one-block set-up kernel writes the tables from the job's shape passed by value, so no
+// host buffer is read after the call returns.
 #include <math.h>
+#include <stddef.h>
 #include <string.h>
 
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "avg_groups.cuh"
 #include "mwax_internal.cuh"
 #include "plan.cuh"
 
@@ -22,53 +33,140 @@ using namespace mwax;
 constexpr size_t kScratchBytes = (size_t)32 << 20;   // operand planes of one call
 constexpr int kMaxN = 512;
 constexpr int kMaxPaths = 64;                          // 32 tiles: one 64 x 64 X-step tile
-constexpr int kMaxGroups = 2 * kMaxN;
-constexpr int kMaxRuns = kMaxN;
+constexpr int kRunLen = 4;                             // output channels per X-step run
+constexpr int kMaxRuns = kMaxN / kRunLen;
 constexpr int kMaxDevices = 64;
 
+// Everything but the operands, in one array.
+struct Tables {
+    float2 tw[kMaxN];               // e^{-2 pi i k / N}
+    float gain[kMaxN];              // sqrt of each ultrafine channel's averaging weight
+    Group groups[kMaxN];            // at most one group per channel
+    RunInfo runs[kMaxRuns];
+    int4 tile;                      // the one 64 x 64 path-pair tile
+    double delay[3 * kMaxPaths];    // the caller's delay polynomial, when it was in host memory
+    int status;                     // 0, or the code of a bounded device wait that gave up
+    // scratch of the group builder (set-up kernel, thread 0): in the array rather than in
+    // per-thread local memory, which would make the driver grow its local-memory pool
+    double w[kMaxN], wsum[kMaxN];
+    int fa[kMaxN], fb[kMaxN];
+    char seen[kMaxN];
+};
+
 __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
-__device__ __align__(256) float2 g_tw[kMaxN];
-__device__ __align__(256) float g_gain[kMaxN];
-__device__ __align__(256) Group g_groups[kMaxGroups];
-__device__ __align__(256) RunInfo g_runs[kMaxRuns];
-__device__ __align__(256) int4 g_tiles[1];
-__device__ __align__(256) double g_delay[3 * kMaxPaths];
+__device__ __align__(256) Tables g_tab;
+
+// Shape of the job, and the delay polynomial by value when the caller's copy is in host
+// memory (the kernel parameters are captured at launch, so the host copy may go at once).
+struct SetupArgs {
+    int N, F, keep, dc_excl, n;
+    int copy_delay;
+    double delay[3 * kMaxPaths];
+};
+
+// One block: twiddles and the delay copy by all threads; averaging groups, runs and the
+// tile by thread 0 (N <= 512: microseconds); status cleared for this call.
+__global__ void __launch_bounds__(256) noalloc_setup_kernel(const SetupArgs a)
+{
+    for (int k = threadIdx.x; k < a.N; k += blockDim.x) {
+        double s, c;
+        sincospi(-2.0 * (double)k / (double)a.N, &s, &c);
+        g_tab.tw[k] = make_float2((float)c, (float)s);
+    }
+    if (a.copy_delay)
+        for (int i = threadIdx.x; i < 3 * a.n; i += blockDim.x) g_tab.delay[i] = a.delay[i];
+    if (threadIdx.x == 0) {
+        const int ng = build_avg_groups(a.N, a.keep, a.F, a.dc_excl, g_tab.gain, g_tab.groups, kMaxN, g_tab.w,
+                                        g_tab.fa, g_tab.fb, g_tab.wsum, g_tab.seen);
+        // the host ran the same builder on the same shape before launching: ng >= 0 here
+        const int M = a.keep / a.F;
+        for (int r = 0, j0 = 0; j0 < M; ++r, j0 += kRunLen) {
+            RunInfo& run = g_tab.runs[r];
+            run.j0 = j0;
+            run.j1 = j0 + kRunLen < M ? j0 + kRunLen : M;
+            run.g0 = ng;
+            run.g1 = 0;
+            for (int g = 0; g < ng; ++g) {
+                const Group& gr = g_tab.groups[g];
+                const bool in = (gr.ja >= run.j0 && gr.ja < run.j1) || (gr.jb >= run.j0 && gr.jb < run.j1);
+                if (in) {
+                    run.g0 = g < run.g0 ? g : run.g0;
+                    run.g1 = g + 1 > run.g1 ? g + 1 : run.g1;
+                }
+            }
+        }
+        g_tab.tile = make_int4(0, 0, 64, 1);
+        g_tab.status = ng >= 0 ? 0 : MWAX_EINVAL;
+    }
+}
+
+// After the X-step: if a bounded wait gave up (or the set-up failed), the call's
+// visibilities are incomplete, and every weight is set to 0 (no valid data) so the caller
+// can tell from the output alone.
+__global__ void noalloc_finish_kernel(char* out, long long n_ints, long long vis_set, long long n_weights,
+                                      long long stride)
+{
+    if (g_tab.status == 0) return;
+    const long long total = n_ints * n_weights;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const long long w = i / n_weights, k = i % n_weights;
+        reinterpret_cast<float*>(out + w * stride + vis_set)[k] = 0.0f;
+    }
+}
 
 struct DeviceArrays {
     bool ready;
+    unsigned long long ctx;   // the context the addresses belong to
     unsigned char* scratch;
-    float2* tw;
-    float* gain;
-    Group* groups;
-    RunInfo* runs;
-    int4* tiles;
-    double* delay;
+    Tables* tab;
 };
+
+// Device address of a member of the table array (host code must not dereference it).
+template <typename T>
+T* member(Tables* tab, size_t offset)
+{
+    return reinterpret_cast<T*>(reinterpret_cast<char*>(tab) + offset);
+}
+std::mutex g_mu;
 DeviceArrays g_dev[kMaxDevices];
 
-template <typename T>
-mwax_status symbol_address(T** dst, const void* symbol, const char* what)
+// Unique id of the calling thread's current context (0 if it cannot be read).
+unsigned long long current_context_id()
 {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, symbol);
-    if (e != cudaSuccess) return cuda_error(e, what);
-    *dst = static_cast<T*>(p);
-    return MWAX_OK;
+    static PFN_cuCtxGetCurrent_v4000 get_cur = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_cur = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(p);
+        tried = true;
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_cur && get_id && get_cur(&ctx) == CUDA_SUCCESS && ctx) get_id(ctx, &id);
+    return id;
 }
 
-// Device addresses of the arrays on device `dev` (looked up once, with `dev` current).
+// Device addresses of the arrays on device `dev` (current), looked up once per context.
 mwax_status lookup(int dev, DeviceArrays* out)
 {
+    std::lock_guard<std::mutex> lock(g_mu);   // also guards the driver entry points above
+    const unsigned long long ctx = current_context_id();
     DeviceArrays& d = g_dev[dev];
-    if (!d.ready) {
-        mwax_status st;
-        if ((st = symbol_address(&d.scratch, g_scratch, "scratch address")) != MWAX_OK) return st;
-        if ((st = symbol_address(&d.tw, g_tw, "twiddle address")) != MWAX_OK) return st;
-        if ((st = symbol_address(&d.gain, g_gain, "gain address")) != MWAX_OK) return st;
-        if ((st = symbol_address(&d.groups, g_groups, "group address")) != MWAX_OK) return st;
-        if ((st = symbol_address(&d.runs, g_runs, "run address")) != MWAX_OK) return st;
-        if ((st = symbol_address(&d.tiles, g_tiles, "tile address")) != MWAX_OK) return st;
-        if ((st = symbol_address(&d.delay, g_delay, "delay address")) != MWAX_OK) return st;
+    if (!d.ready || d.ctx != ctx) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess) return cuda_error(e, "scratch array address");
+        d.scratch = static_cast<unsigned char*>(p);
+        if ((e = cudaGetSymbolAddress(&p, g_tab)) != cudaSuccess) return cuda_error(e, "table array address");
+        d.tab = static_cast<Tables*>(p);
+        d.ctx = current_context_id();   // the look-up made the primary context current if it was not
         d.ready = true;
     }
     *out = d;
@@ -109,79 +207,39 @@ extern "C" mwax_status mwax_correlate_noalloc(const mwax_plan_desc* desc, const 
     if (need > kScratchBytes)
         return set_error(MWAX_EINVAL, "allocation-free call: operands exceed the 32 MiB device scratch array");
 
-    // averaging: gains sqrt(w) per ultrafine channel and groups (Sec. 2.6), in fixed arrays
-    const int M = N / F, jc = M / 2, half = F / 2, dc_excl = d.keep_dc ? 0 : 1;
-    float gain[kMaxN];
-    double w[kMaxN], wsum[kMaxN];
-    int fa[kMaxN], fb[kMaxN];
-    for (int c = 0; c < N; ++c) {
-        w[c] = 0.0;
-        fa[c] = fb[c] = -1;
+    // The averaging tables (Sec. 2.6) are validated here with the builder the set-up
+    // kernel runs, on stack arrays; only their group count leaves the host.
+    const int M = N / F, dc_excl = d.keep_dc ? 0 : 1;
+    int ng;
+    {
+        float gain[kMaxN];
+        Group groups[kMaxN];
+        double w[kMaxN], wsum[kMaxN];
+        int fa[kMaxN], fb[kMaxN];
+        char seen[kMaxN];
+        ng = build_avg_groups(N, N, F, dc_excl, gain, groups, kMaxN, w, fa, fb, wsum, seen);
+        if (ng < 0) return set_error(MWAX_EINVAL, "channel averaging leaves an empty channel");
     }
-    for (int j = 0; j < M; ++j) {
-        wsum[j] = 0.0;
-        const long long mid = (long long)(j - jc) * F;
-        for (long long u = mid - half; u <= mid + half; ++u) {
-            const long long c = u + N / 2;
-            if (c < 0 || c >= N) continue;
-            double wt = (F % 2 == 0 && (u == mid - half || u == mid + half)) ? 0.5 : 1.0;
-            if (dc_excl && F > 1 && u == 0) wt = 0.0;
-            if (wt == 0.0) continue;
-            w[c] = wt;
-            if (fa[c] < 0) fa[c] = j;
-            else fb[c] = j;
-            wsum[j] += wt;
+    const int nr = (M + kRunLen - 1) / kRunLen;
+
+    SetupArgs sa;
+    memset(&sa, 0, sizeof sa);
+    sa.N = N;
+    sa.F = F;
+    sa.keep = N;
+    sa.dc_excl = dc_excl;
+    sa.n = n;
+    bool delay_in_device_memory = false;
+    if (delay_poly) {
+        cudaPointerAttributes at;
+        cudaError_t e = cudaPointerGetAttributes(&at, delay_poly);
+        if (e != cudaSuccess) return cuda_error(e, "delay_poly attributes");
+        delay_in_device_memory = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+        if (!delay_in_device_memory) {   // host memory: read now, into the kernel parameters
+            memcpy(sa.delay, delay_poly, sizeof(double) * 3 * n);
+            sa.copy_delay = 1;
         }
     }
-    Group groups[kMaxGroups];
-    RunInfo runs[kMaxRuns];
-    int ng = 0;
-    bool seen[kMaxN];
-    for (int j = 0; j < M; ++j) seen[j] = false;
-    for (int c = 0; c < N; ++c) {
-        gain[c] = (float)sqrt(w[c]);
-        if (w[c] == 0.0) continue;
-        if (ng > 0 && groups[ng - 1].ja == fa[c] && groups[ng - 1].jb == fb[c]) {
-            groups[ng - 1].c1 = c + 1;
-            continue;
-        }
-        Group& g = groups[ng++];
-        g.c0 = c;
-        g.c1 = c + 1;
-        g.ja = fa[c];
-        g.jb = fb[c];
-        g.ca = (float)(1.0 / wsum[fa[c]]);
-        g.cb = fb[c] >= 0 ? (float)(1.0 / wsum[fb[c]]) : 0.0f;
-        g.first_a = !seen[g.ja];
-        seen[g.ja] = true;
-        g.first_b = 0;
-        if (g.jb >= 0) {
-            g.first_b = !seen[g.jb];
-            seen[g.jb] = true;
-        }
-    }
-    // runs of 4 output channels
-    int nr = 0;
-    for (int j0 = 0; j0 < M; j0 += 4) {
-        RunInfo& r = runs[nr++];
-        r.j0 = j0;
-        r.j1 = j0 + 4 < M ? j0 + 4 : M;
-        r.g0 = ng;
-        r.g1 = 0;
-        for (int g = 0; g < ng; ++g) {
-            const bool in = (groups[g].ja >= r.j0 && groups[g].ja < r.j1) || (groups[g].jb >= r.j0 && groups[g].jb < r.j1);
-            if (in) {
-                r.g0 = g < r.g0 ? g : r.g0;
-                r.g1 = g + 1 > r.g1 ? g + 1 : r.g1;
-            }
-        }
-    }
-    float2 tw[kMaxN];
-    for (int k = 0; k < N; ++k) {
-        const double a = -2.0 * M_PI * (double)k / (double)N;
-        tw[k] = make_float2((float)cos(a), (float)sin(a));
-    }
-    const int4 tile = make_int4(0, 0, 64, 1);
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -192,17 +250,11 @@ extern "C" mwax_status mwax_correlate_noalloc(const mwax_plan_desc* desc, const 
     if (st != MWAX_OK) return st;
     cudaStream_t s = (cudaStream_t)cuda_stream;
 
-    // tables (copied from host memory: the call returns once they are staged), delays,
-    // and the zero padding of the operand planes (the array keeps the previous call's data)
-    if ((e = cudaMemcpyAsync(A.tw, tw, sizeof(float2) * N, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(A.gain, gain, sizeof(float) * N, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(A.groups, groups, sizeof(Group) * ng, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(A.runs, runs, sizeof(RunInfo) * nr, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(A.tiles, &tile, sizeof(int4), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(A.scratch, 0, need, s)) != cudaSuccess)
-        return cuda_error(e, "table upload");
-    if (delay_poly && (e = cudaMemcpyAsync(A.delay, delay_poly, sizeof(double) * 3 * n, cudaMemcpyDefault, s)) != cudaSuccess)
-        return cuda_error(e, "delay upload");
+    // tables and status from the job's shape, then the zero padding of the operand planes
+    // (the array keeps the previous call's data)
+    noalloc_setup_kernel<<<1, 256, 0, s>>>(sa);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "set-up launch");
+    if ((e = cudaMemsetAsync(A.scratch, 0, need, s)) != cudaSuccess) return cuda_error(e, "operand clear");
 
     const long long B = (long long)T * (T + 1) / 2;
     const size_t vis_set = (size_t)B * M * 4 * 8, wts = (size_t)B * 4 * 4;
@@ -211,10 +263,10 @@ extern "C" mwax_status mwax_correlate_noalloc(const mwax_plan_desc* desc, const 
     FArgs fa_;
     memset(&fa_, 0, sizeof fa_);
     fa_.volt = voltages;
-    fa_.delay = delay_poly ? A.delay : nullptr;
+    fa_.delay = delay_poly ? (delay_in_device_memory ? delay_poly : member<double>(A.tab, offsetof(Tables, delay))) : nullptr;
     fa_.Y = A.scratch;
-    fa_.tw = A.tw;
-    fa_.gain = A.gain;
+    fa_.tw = member<float2>(A.tab, offsetof(Tables, tw));
+    fa_.gain = member<float>(A.tab, offsetof(Tables, gain));
     fa_.m_begin = 0;
     fa_.n_frames = n_ints * K;
     fa_.n_store = n_ints * K;
@@ -238,16 +290,20 @@ extern "C" mwax_status mwax_correlate_noalloc(const mwax_plan_desc* desc, const 
     xa.M = M;
     xa.n_groups = ng;
     xa.B = B;
-    xa.groups = A.groups;
-    xa.runs = A.runs;
-    xa.gain = A.gain;
-    xa.tiles = A.tiles;
+    xa.groups = member<Group>(A.tab, offsetof(Tables, groups));
+    xa.runs = member<RunInfo>(A.tab, offsetof(Tables, runs));
+    xa.gain = member<float>(A.tab, offsetof(Tables, gain));
+    xa.tiles = member<int4>(A.tab, offsetof(Tables, tile));
     xa.post_scale = 1.0f;
     xa.first_store = 1;
+    xa.status = member<int>(A.tab, offsetof(Tables, status));
     xa.spin_limit = 2000000;
     CUtensorMap map;   // encoded on the host into the launch parameters: no device memory
     if ((e = make_simt_tmap(&map, A.scratch, Kpad, n, n_ints * N * 2)) != cudaSuccess)
         return cuda_error(e, "operand tensor map");
     if ((e = launch_xstep_simt(map, xa, 1, nr, (int)n_ints, s)) != cudaSuccess) return cuda_error(e, "X-step launch");
+    noalloc_finish_kernel<<<8, 256, 0, s>>>(static_cast<char*>(vis_out), n_ints, (long long)vis_set, B * 4,
+                                            (long long)(vis_set + wts));
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "finish launch");
     return MWAX_OK;
 }

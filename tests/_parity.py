@@ -91,11 +91,11 @@ def sampled_error(got, want, req, n_main, tiles, T):
 TOL_BY_PREC = {0: 1e-5, 1: 2e-3, 2: 3e-2, 4: 1e-5}
 
 
-def check_output_vs_oracle(T, N, F, int_time_s, n_samples, prec, volt, delay, vis, weights):
+def check_output_vs_oracle(T, N, F, int_time_s, n_samples, prec, volt, delay, vis, weights, keep_dc=0):
     """A call's split output (vis, weights as numpy) against the full FP64 oracle on the
     same inputs: integer mode bit-exact, float forms within their bar.  Returns the max
     parity error (0 for the integer mode)."""
-    od = oracle_desc(T, N, F, int_time_s, n_samples, block_samples=volt.shape[2])
+    od = oracle_desc(T, N, F, int_time_s, n_samples, block_samples=volt.shape[2], keep_dc=keep_dc)
     if prec == 3:
         ref, rw = oracle.correlate_int(od, volt)
         assert np.array_equal(vis, ref), "integer mode differs from the oracle"

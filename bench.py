@@ -60,7 +60,64 @@ def traffic_per_slot(kernel: str):
     except OSError:
         return None
     return per_slot if h.startswith(sha) else None
-FP32_LANES_PER_SM, N_SM = 128, 148
+FP32_LANES_PER_SM = 128
+
+
+def sm_count(torch, dev: int = 0) -> int:
+    return torch.cuda.get_device_properties(dev).multi_processor_count
+
+
+def measure_peaks(mw, torch, dev: int, seconds: float = 2.0):
+    """Roofline denominators that MEASURED_PEAKS.json does not hold, measured here with CUDA
+    events (no clock or power setting touched), each as a burst (best of several short
+    runs) and sustained (back to back for `seconds`), with the SM clock sampled meanwhile:
+    - FP32 FMA: the library's FMA probe (16 independent chains per thread, full occupancy);
+    - FP8 e4m3 dense tensor: cuBLASLt through torch._scaled_mm at 8192^3, as the bf16 figure
+      of MEASURED_PEAKS.json is cuBLAS at 8192^3."""
+    res = {"sms": sm_count(torch, dev)}
+    clocks = ClockSampler(dev)
+    clocks.start()
+    stream = torch.cuda.current_stream()
+
+    def rate(fn, work, reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return work * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12
+
+    blocks = res["sms"] * 8
+    sink = torch.empty(blocks * 256, dtype=torch.float32, device="cuda")
+    iters = 4096
+    fmas = mw.mwax_probe_fma(blocks, iters, sink)
+    torch.cuda.synchronize()
+    one = rate(lambda: mw.mwax_probe_fma(blocks, iters, sink), 2.0 * fmas, 1)
+    reps = max(1, int(0.05 / max(2.0 * fmas / (one * 1e12), 1e-6)))   # ~50 ms per burst sample
+    burst = max(rate(lambda: mw.mwax_probe_fma(blocks, iters, sink), 2.0 * fmas, reps) for _ in range(5))
+    sus_reps = max(1, int(seconds / (2.0 * fmas / (burst * 1e12))))
+    sus = rate(lambda: mw.mwax_probe_fma(blocks, iters, sink), 2.0 * fmas, sus_reps)
+    res["fp32_fma_tflops"] = burst
+    res["fp32_fma_tflops_sustained"] = sus
+    res["fp32_fma_probe"] = f"mwax_probe_fma: {blocks} blocks x 256 threads x {iters * 8 * 16} FMA"
+    try:
+        n = 8192
+        a = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn)
+        b = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn).t()
+        one_s = torch.tensor(1.0, device="cuda")
+        mm = lambda: torch._scaled_mm(a, b, scale_a=one_s, scale_b=one_s, out_dtype=torch.bfloat16)
+        mm()
+        torch.cuda.synchronize()
+        flop = 2.0 * n ** 3
+        res["fp8_tflops"] = max(rate(mm, flop, 10) for _ in range(3))
+        res["fp8_tflops_sustained"] = rate(mm, flop, max(1, int(seconds / (flop / (res["fp8_tflops"] * 1e12)))))
+        res["fp8_how"] = "torch._scaled_mm e4m3 x e4m3 -> bf16, 8192^3 (cuBLASLt)"
+        del a, b
+    except Exception as e:   # no FP8 GEMM in this torch build: the nominal ratio is used instead
+        res["fp8_unavailable"] = f"{type(e).__name__}: {str(e)[:120]}"
+    res["clocks"] = clocks.stop()
+    return res
 
 
 def peaks():
@@ -266,6 +323,9 @@ def run_reference(args, world, rank):
             "warmup": args.warmup, "ms_per_step": 1e3 * est, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded noise + point source)",
             "impl": "reference",
+            # each step times a bounded sample (a 32-tile sub-array, one 0.5 s integration) and
+            # scales it to the 256-tile 8 s sub-observation: ms_per_step and value are extrapolated
+            "extrapolated": True, "measured_sample_s_per_step": statistics.median(meas),
             "config": {"workload": WORKLOAD["name"], "precision": "fp64 oracle on host cores"},
             "cpu_baseline": {"value": value, "unit": "channels", "cores": note.get("cores"), "kind": "oracle",
                              "sample": descs},
@@ -356,66 +416,94 @@ def run_batch24(mw, torch, dev_base, args):
             "input": "the 256-tile 8 s voltage bytes re-tiled per tile count (every channel computed in full)"}
 
 
-def run_serve(mw, torch, host_base, args, periods: int = 2):
-    """Real-time serving: 24 coarse channels each delivering an 8 s sub-observation every 8 s
+def run_serve(mw, torch, host_base, args, periods: int = 2, counts=(24, 32, 40, 48)):
+    """Real-time serving: n coarse channels each delivering an 8 s sub-observation every 8 s
     (seeded offsets within the period), FP16 or integer mode per request (80/20), host
-    pinned voltages; the server admits by HBM footprint; deadline = 8 s."""
-    chans = mixed_channels(0x4D57415C, int8_share=0.2)
-    hosts = {}
-    for c in chans:
-        T = c["T"]
-        if T in hosts:
-            continue
-        need = 160 * 2 * T * 64_000 * 2
-        if need <= host_base.numel():
-            hosts[T] = host_base[:need]
-        else:
-            h = torch.empty(need, dtype=torch.int8, pin_memory=True)
-            for k in range(need // host_base.numel()):
-                h[k * host_base.numel():(k + 1) * host_base.numel()].copy_(host_base)
-            hosts[T] = h
-    rng = np.random.default_rng(0x5E7E)
-    offsets = rng.uniform(0, SUBOBS_S, len(chans))
-    descs, outs = [], []
-    for c in chans:
+    pinned voltages; the server admits by HBM footprint; deadline = 8 s.  The 24-channel
+    load is measured first, then the offered count is raised until a deadline is missed:
+    the capacity is the largest count with no miss.  Warm-up requests (one per new shape,
+    which create the plans) run before each count's statistics are reset."""
+    chans_all = mixed_channels(0x4D57415C, n=max(counts), int8_share=0.2)
+    hosts, outs = {}, {}
+
+    def host_volt(T):
+        if T not in hosts:
+            need = 160 * 2 * T * 64_000 * 2
+            if need <= host_base.numel():
+                hosts[T] = host_base[:need]
+            else:
+                h = torch.empty(need, dtype=torch.int8, pin_memory=True)
+                for k in range(need // host_base.numel()):
+                    h[k * host_base.numel():(k + 1) * host_base.numel()].copy_(host_base)
+                hosts[T] = h
+        return hosts[T]
+
+    def desc_of(c):
         prec = mw.MWAX_INT8 if c["prec"] == "int8" else mw.MWAX_FP16
-        d = mw.PlanDesc(n_tiles=c["T"], fft_len=c["N"], fine_avg=c["F"], int_time_s=c["t"],
-                        samples_per_call=10_240_000, precision=prec, sky_freq_hz=0.0, workspace_limit=4 << 30)
-        descs.append(d)
-        p = mw.mwax_plan_create_ex(d)            # size of the output only
-        outs.append(torch.empty(p.output_bytes, dtype=torch.uint8, pin_memory=True))
-        p.close()
+        return mw.PlanDesc(n_tiles=c["T"], fft_len=c["N"], fine_avg=c["F"], int_time_s=c["t"],
+                           samples_per_call=10_240_000, precision=prec, sky_freq_hz=0.0, workspace_limit=4 << 30)
+
+    def key_of(d):
+        return (d.n_tiles, d.fft_len, d.fine_avg, d.int_time_s, d.precision)
+
+    def out_for(d):
+        # one pinned result buffer per shape, shared by that shape's requests: the read-back
+        # volume is the same, results are not inspected here (the tests compare them)
+        k = key_of(d)
+        if k not in outs:
+            p = mw.mwax_plan_create_ex(d)
+            outs[k] = torch.empty(p.output_bytes, dtype=torch.uint8, pin_memory=True)
+            p.close()
+        return outs[k]
+
     srv = mw.Server(hbm_budget=160 << 30, n_lanes=4)
-    # warm-up: one request of every distinct shape (plans created, kernels loaded)
-    seen = set()
-    for k, d in enumerate(descs):
-        key = (d.n_tiles, d.fft_len, d.fine_avg, d.int_time_s, d.precision)
-        if key not in seen:
-            seen.add(key)
-            srv.submit(d, hosts[d.n_tiles], None, outs[k])
-    srv.drain()
-    warm = srv.stats()["completed"]
-    t0 = time.perf_counter()
-    events = sorted((pp * SUBOBS_S + offsets[k], k) for pp in range(periods) for k in range(len(chans)))
-    for at, k in events:
-        while time.perf_counter() - t0 < at:
-            time.sleep(0.0005)
-        srv.submit(descs[k], hosts[descs[k].n_tiles], None, outs[k], deadline_s=SUBOBS_S)
-    srv.drain()
-    wall = time.perf_counter() - t0
-    st = srv.stats()
+    warmed, sweep, first = set(), [], None
+    for n in counts:
+        chans = chans_all[:n]
+        descs = [desc_of(c) for c in chans]
+        for d in descs:   # warm-up of the shapes not seen yet (plan creation, module loading)
+            if key_of(d) not in warmed:
+                warmed.add(key_of(d))
+                srv.submit(d, host_volt(d.n_tiles), None, out_for(d))
+        srv.drain()
+        srv.reset_stats()
+        rng = np.random.default_rng(0x5E7E + n)
+        offsets = rng.uniform(0, SUBOBS_S, n)
+        t0 = time.perf_counter()
+        events = sorted((pp * SUBOBS_S + offsets[k], k) for pp in range(periods) for k in range(n))
+        for at, k in events:
+            while time.perf_counter() - t0 < at:
+                time.sleep(0.0005)
+            srv.submit(descs[k], host_volt(descs[k].n_tiles), None, out_for(descs[k]), deadline_s=SUBOBS_S)
+        srv.drain()
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        up = sum(160 * 2 * d.n_tiles * 64_000 * 2 for d in descs) / SUBOBS_S / 1e9
+        row = {"channels": n, "completed": st["completed"], "deadline_misses": st["deadline_misses"],
+               "cold_starts": st["cold_starts"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+               "p50_warm_ms": st["p50_warm_ms"], "p99_warm_ms": st["p99_warm_ms"],
+               "throughput_channels": st["completed"] * SUBOBS_S / wall, "wall_s": wall,
+               "upload_gb_per_s_offered": up}
+        sweep.append(row)
+        if first is None:
+            first = row
+        if st["deadline_misses"] > 0:
+            break
     srv.close()
-    done = st["completed"] - warm
-    return {"workload": f"24 coarse channels x {periods} sub-observations of 8 s at wall-clock rate, tiles "
+    capacity = max([r["channels"] for r in sweep if r["deadline_misses"] == 0], default=0)
+    return {"workload": f"{counts[0]} coarse channels x {periods} sub-observations of 8 s at wall-clock rate, tiles "
                         "{128,256,512}, mixed N/F/int as the 24-channel batch, 20 % integer mode, host pinned voltages",
-            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
-            "deadline_ms": 1e3 * SUBOBS_S, "deadline_misses": st["deadline_misses"], "completed": done,
-            # channels kept in real time: the offered channels x the share of their requests
-            # that met the 8 s deadline; the completed sub-observations per wall second
-            # (which counts the last period's processing tail over a short run) beside it
-            "sustained_channels": len(chans) * (done - st["deadline_misses"]) / max(1, done),
-            "throughput_channels": done * SUBOBS_S / wall, "wall_s": wall,
-            "latency_note": "percentiles include the warm-up requests (one per shape)",
+            "p50_ms": first["p50_ms"], "p99_ms": first["p99_ms"], "max_ms": first["max_ms"],
+            "p50_warm_ms": first["p50_warm_ms"], "p99_warm_ms": first["p99_warm_ms"],
+            "cold_starts": first["cold_starts"],
+            "deadline_ms": 1e3 * SUBOBS_S, "deadline_misses": first["deadline_misses"], "completed": first["completed"],
+            "sustained_channels": counts[0] * (first["completed"] - first["deadline_misses"]) / max(1, first["completed"]),
+            "capacity_channels": capacity,
+            "capacity_note": "largest offered channel count (of the sweep) with no deadline miss over "
+                             f"{periods} periods; the sweep stops at the first count that misses",
+            "sweep": sweep,
+            "latency_note": "warm-up requests (one per new shape) excluded; p50/p99 over every timed request, "
+                            "*_warm over those whose lane already held the plan (no plan creation)",
             "lanes": 4, "hbm_budget_gb": 160}
 
 
@@ -464,7 +552,7 @@ def _time_calls(torch, fn, steps, warmup):
     return e0.elapsed_time(e1) / steps
 
 
-def run_extensions(mw, torch, W, dev_volt, delay, args):
+def run_extensions(mw, torch, W, dev_volt, delay, args, mpk):
     """The roadmap rows on the full 256-tile sub-observation (Sec. 2.4, 4.1-4.5): per-call
     device time of the plain FP16 call beside the same call with zeroing flags +
     normalisation, a 5 ms delay table, de-ripple gains; an oversampled channel (FP16);
@@ -524,10 +612,10 @@ def run_extensions(mw, torch, W, dev_volt, delay, args):
     incoh = torch.empty(bf.output_bytes(2), dtype=torch.uint8, device="cuda").view(torch.float32)
     bms = _time_calls(torch, lambda: bf.form(dev_volt, btab, beams, power, incoh), steps, warm)
     flops = 8.0 * nb * n * S
-    pk, pk_kind = peaks()
-    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    fp32_peak = mpk["fp32_fma_tflops_sustained"]
     res["beamformer"] = {"n_beams": nb, "ms_per_subobs": bms, "real_time_factor": SUBOBS_S / (bms * 1e-3),
                          "whole_call_tflops": flops / (bms * 1e-3) / 1e12, "fp32_peak_tflops": fp32_peak,
+                         "fp32_peak_kind": "measured FMA probe, sustained",
                          "whole_call_frac": flops / (bms * 1e-3) / 1e12 / fp32_peak,
                          "work": "8 flop per beam x path x sample (complex MAC); call includes the F-step"}
     del bf, beams, power, incoh
@@ -569,6 +657,7 @@ def run_mine(args, world, rank, local):
     dev_volt = host.cuda(non_blocking=False)
     dev_delay = torch.from_numpy(delay).cuda()
     pk, pk_kind = peaks()
+    mpk = measure_peaks(mw, torch, local)
     headline = args.precision
     forms = [headline] + ([] if args.no_forms else [f for f in ("fp32", "fp16x3", "fp16", "fp8", "int8")
                                                      if f != headline])
@@ -605,11 +694,18 @@ def run_mine(args, world, rank, local):
         x_per_launch = x_flops * args.steps / x_n
         x_avg_ms = x_ms / x_n
         x_achieved = x_per_launch / (x_avg_ms * 1e-3) / 1e12
+        nominal = None
         if form == "fp32":
             xkern, bound = "xstep_simt_kernel", "alu"
-            x_peak = N_SM * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
-            peak_kind = (f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {pk.get('sm_max_mhz')} MHz "
-                         f"({pk_kind} max clock)")
+            x_peak = mpk["fp32_fma_tflops_sustained"]
+            nominal = mpk["sms"] * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+            peak_kind = (f"measured FP32 FMA throughput, sustained ({mpk['fp32_fma_probe']}, "
+                         f"SM clock median {mpk['clocks'].get('sm_mhz')} MHz); nominal {mpk['sms']} SMs x "
+                         f"{FP32_LANES_PER_SM} lanes x 2 x {pk.get('sm_max_mhz')} MHz = {nominal:.1f} TFLOP/s")
+        elif form == "fp8" and "fp8_tflops_sustained" in mpk:
+            xkern, bound = "xstep_tc_kernel<0> (e4m3)", "tensor"
+            x_peak = mpk["fp8_tflops_sustained"]
+            peak_kind = f"measured dense e4m3, sustained ({mpk['fp8_how']})"
         else:
             xkern = {"fp16": "xstep_tc_kernel<0> (fp16)", "fp8": "xstep_tc_kernel<0> (e4m3)",
                      "fp16x3": "xstep_tc_kernel<1> (fp16 hi/lo pairs)",
@@ -631,7 +727,7 @@ def run_mine(args, world, rank, local):
              "roofline": {"bound": bound, "kernel": xkern, "achieved": x_achieved, "peak": x_peak, "unit": "TFLOP/s",
                           "frac": x_achieved / x_peak,
                           "traffic": None if tps is None else tps * n_ints * args.steps / x_n,
-                          "peak_kind": peak_kind,
+                          "peak_kind": peak_kind, "nominal_peak": nominal,
                           "per_launch": f"{x_per_launch:.4g} flop (8 x pairs x frames x {used} used bins)",
                           "avg_launch_ms": x_avg_ms,
                           # what the kernel executes with this tuning: whole tiles (pairs below
@@ -697,7 +793,7 @@ def run_mine(args, world, rank, local):
 
     ext = None
     if not args.no_ext and W is WORKLOAD:
-        ext = run_extensions(mw, torch, W, dev_volt, delay, args)
+        ext = run_extensions(mw, torch, W, dev_volt, delay, args, mpk)
 
     # 24 batched channels of mixed shapes, then real-time serving
     batch = serve = None
@@ -739,6 +835,7 @@ def run_mine(args, world, rank, local):
         "cpu_baseline": cpu,
         "precision_forms": {f: {k: v for k, v in r.items() if k != "gpu_launches"} for f, r in results.items()
                             if f != headline},
+        "measured_peaks": mpk,
         "batch": batch,
         "serving": serve,
         "extensions": ext,

@@ -227,6 +227,17 @@ mwax_status mwax_plan_set_passband(mwax_plan* plan, const float* gain);
 mwax_status mwax_plan_sync(mwax_plan* plan);
 
 /*
+ * Bound of every device-side wait of the plan's X-step kernels (an operational control,
+ * no counterpart in the paper): a wait gives up after kilocycles x 1000 SM clock cycles,
+ * raises the kernel's abort flag, lets its own TMA loads and MMAs in flight complete (a
+ * fixed bound of ~2 s that does not follow this limit), frees its tensor memory and
+ * returns; mwax_plan_sync() then reports MWAX_ETIMEOUT and the call's output is
+ * incomplete.  0 restores the default (2,000,000, about 1 s).  Applies to calls enqueued
+ * after it returns; in a batch a launch takes the largest limit of its plans.
+ */
+mwax_status mwax_plan_set_wait_limit(mwax_plan* plan, unsigned int kilocycles);
+
+/*
  * Per-stage device time (the paper's Table 2 breaks the FX-engine time down by
  * sub-function).  While enabled, CUDA events bracket each of the plan's kernel launches
  * on its stream.  mwax_plan_stage_times() waits for the stream and returns, per stage,
@@ -328,6 +339,11 @@ typedef struct {
     double p50_ms, p99_ms, max_ms;   /* latency from submission to result in host memory   */
     long long deadline_misses;       /* completed requests later than their deadline        */
     size_t hbm_in_use;               /* device bytes held by lanes (buffers and plans)       */
+    long long cold_starts;           /* admissions that created a plan (first request of a
+                                        shape on a lane, or after an eviction); their latency
+                                        includes plan creation                                */
+    double p50_warm_ms, p99_warm_ms; /* latency of the requests that found their plan cached
+                                        (steady state: no plan creation)                     */
 } mwax_server_stats;
 
 /* Start a server on the current device (NULL desc = defaults).  NULL on error. */
@@ -354,6 +370,11 @@ mwax_status mwax_server_drain(mwax_server* server);
 
 /* Counters and latency percentiles so far. */
 mwax_status mwax_server_get_stats(mwax_server* server, mwax_server_stats* stats);
+
+/* Start the statistics afresh (latencies, counts, misses, cold starts; requests already
+ * submitted still complete, and count if they complete after the reset), e.g. after
+ * warm-up requests that created the plans. */
+mwax_status mwax_server_reset_stats(mwax_server* server);
 
 /* Finish the queued requests, free everything.  NULL is a no-op. */
 void mwax_server_destroy(mwax_server* server);
@@ -409,24 +430,41 @@ mwax_status mwax_beam_sync(mwax_beamformer* bf);
 /* Waits for the beamformer's stream, frees everything.  NULL is a no-op. */
 void mwax_beam_destroy(mwax_beamformer* bf);
 
+/* ------------------------------------------------------------------ roofline probe */
+
+/*
+ * FP32 FMA throughput probe (no counterpart in the paper: it measures the denominator of
+ * the CUDA-core X-step's ALU roofline).  Enqueues `blocks` blocks of 256 threads, each
+ * thread running 16 independent FMA chains for iters x 8 steps, on cuda_stream; sink is a
+ * device buffer of blocks x 256 floats (written only in a case that does not occur).
+ * Returns the number of FMAs enqueued (2 flop each), or -1 on invalid arguments or a
+ * launch error.  Time it with events on the same stream.
+ */
+long long mwax_probe_fma(int blocks, int iters, float* sink, void* cuda_stream);
+
 /* ------------------------------------------------------------------ allocation-free call */
 
 /*
- * FP32 correlation of one small job that allocates no memory at all (the paper has no
- * counterpart; this is for callers that cannot allocate: code running inside a CUDA-graph
- * capture it does not control, processes whose device memory belongs to another
- * allocator, or services that forbid allocation after start-up).  desc as for
- * mwax_plan_create_ex with precision MWAX_FP32, 1..32 tiles, fft_len 32/64/128/256/512;
- * voltages and vis_out device pointers as for mwax_correlate (vis_out:
- * n_ints x (B M 4 complex64 + B 4 float32) bytes); delay_poly NULL, host or device;
+ * FP32 correlation of one small job that allocates no memory at all.  The paper has no
+ * counterpart.  It is for callers that cannot call cudaMalloc: processes whose device
+ * memory belongs to another allocator (a framework's caching pool that has reserved the
+ * GPU), plug-ins whose host application forbids them to allocate, and real-time services
+ * that ban allocation after start-up because an allocation may block or fail at any time.
+ * desc as for mwax_plan_create_ex with precision MWAX_FP32, 1..32 tiles, fft_len
+ * 32/64/128/256/512, all bins kept; voltages and vis_out device pointers as for
+ * mwax_correlate, 16-byte aligned (vis_out: n_ints x (B M 4 complex64 + B 4 float32)
+ * bytes); delay_poly NULL, host or device (host memory is read before the call returns);
  * cuda_stream a cudaStream_t (NULL = legacy default stream).
  * All device working memory is a fixed set of arrays inside the library image (a 32 MiB
- * operand array plus small tables, held on every GPU that loads the library until exit);
- * jobs whose operands exceed 32 MiB (n_ints x fft_len x 2 x 2T x K rounded up to 128
- * frames x 4 bytes) are rejected with MWAX_EINVAL.  The first call on a device looks up
- * the arrays' device addresses there; make it before any stream capture.  Every call uses
- * the same arrays (each call clears what must start at zero): calls that overlap on the
- * GPU, on any stream, race and corrupt each other.  Asynchronous on cuda_stream.
+ * operand array plus about 40 KB of tables and a status word, held on every GPU that
+ * loads the library until exit); jobs whose operands exceed 32 MiB (n_ints x fft_len x 2 x
+ * 2T x K rounded up to 128 frames x 4 bytes) are rejected with MWAX_EINVAL, as are
+ * misaligned pointers.  The first call on a device (and context) looks up the arrays'
+ * device addresses there, under a lock.  Every call uses the same arrays and rewrites
+ * what it needs (tables, status, zero padding): calls that overlap on the GPU, on any
+ * stream, race and corrupt each other.  Asynchronous on cuda_stream: errors found on the
+ * host are returned; if a bounded device wait gives up, every weight of the call's output
+ * is set to 0 (no valid data) instead, since no plan holds a status to query.
  */
 mwax_status mwax_correlate_noalloc(const mwax_plan_desc* desc, const int8_t* voltages, const double* delay_poly,
                                    void* vis_out, void* cuda_stream);

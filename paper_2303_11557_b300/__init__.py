@@ -83,7 +83,8 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong),
                 ("queued", ctypes.c_longlong), ("in_flight", ctypes.c_longlong), ("p50_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("deadline_misses", ctypes.c_longlong),
-                ("hbm_in_use", ctypes.c_size_t)]
+                ("hbm_in_use", ctypes.c_size_t), ("cold_starts", ctypes.c_longlong), ("p50_warm_ms", ctypes.c_double),
+                ("p99_warm_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -114,13 +115,16 @@ _lib = None
 SYMBOLS = ("mwax_plan_create", "mwax_plan_create_ex", "mwax_plan_get_info", "mwax_plan_output_bytes",
            "mwax_plan_input_bytes", "mwax_plan_set_stream", "mwax_correlate", "mwax_correlate_host",
            "mwax_correlate_host_async",
-           "mwax_plan_sync", "mwax_plan_destroy", "mwax_last_error", "mwax_version", "mwax_plan_enable_timing",
+           "mwax_plan_sync", "mwax_plan_set_wait_limit", "mwax_plan_destroy", "mwax_last_error", "mwax_version",
+           "mwax_plan_enable_timing",
            "mwax_plan_stage_times", "mwax_plan_autotune", "mwax_plan_set_tuning", "mwax_plan_get_tuning",
            "mwax_batch_create", "mwax_batch_set_stream", "mwax_batch_set_graphs", "mwax_batch_correlate",
            "mwax_batch_sync", "mwax_batch_destroy", "mwax_server_create", "mwax_server_submit", "mwax_server_poll",
-           "mwax_server_wait", "mwax_server_drain", "mwax_server_get_stats", "mwax_server_destroy",
+           "mwax_server_wait", "mwax_server_drain", "mwax_server_get_stats", "mwax_server_reset_stats",
+           "mwax_server_destroy",
            "mwax_correlate_noalloc", "mwax_correlate_ex", "mwax_plan_set_passband", "mwax_beam_create",
-           "mwax_beam_set_stream", "mwax_beam_output_bytes", "mwax_beam_form", "mwax_beam_sync", "mwax_beam_destroy")
+           "mwax_beam_set_stream", "mwax_beam_output_bytes", "mwax_beam_form", "mwax_beam_sync", "mwax_beam_destroy",
+           "mwax_probe_fma")
 
 
 def load_library(path: str | None = None):
@@ -159,6 +163,10 @@ def load_library(path: str | None = None):
     lib.mwax_correlate_host_async.restype = st
     lib.mwax_plan_sync.argtypes = [vp]
     lib.mwax_plan_sync.restype = st
+    lib.mwax_plan_set_wait_limit.argtypes = [vp, ctypes.c_uint]
+    lib.mwax_plan_set_wait_limit.restype = st
+    lib.mwax_probe_fma.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp]
+    lib.mwax_probe_fma.restype = ctypes.c_longlong
     lib.mwax_plan_destroy.argtypes = [vp]
     lib.mwax_plan_destroy.restype = None
     lib.mwax_last_error.argtypes = []
@@ -197,6 +205,8 @@ def load_library(path: str | None = None):
     lib.mwax_server_drain.restype = st
     lib.mwax_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
     lib.mwax_server_get_stats.restype = st
+    lib.mwax_server_reset_stats.argtypes = [vp]
+    lib.mwax_server_reset_stats.restype = st
     lib.mwax_server_destroy.argtypes = [vp]
     lib.mwax_server_destroy.restype = None
     lib.mwax_correlate_noalloc.argtypes = [ctypes.POINTER(_CDesc), vp, vp, vp, vp]
@@ -346,6 +356,21 @@ def mwax_plan_sync(plan: Plan):
     _check(load_library().mwax_plan_sync(plan.handle))
 
 
+def mwax_probe_fma(blocks: int, iters: int, sink, stream=None) -> int:
+    """Enqueue the FP32 FMA throughput probe on the stream; returns the FMAs enqueued."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    n = load_library().mwax_probe_fma(blocks, iters, _ptr(sink), ctypes.c_void_p(s.cuda_stream))
+    if n < 0:
+        raise MwaxError(MWAX_EINVAL, "FMA probe launch failed")
+    return n
+
+
+def mwax_plan_set_wait_limit(plan: Plan, kilocycles: int):
+    """Bound of the plan's device-side waits (x 1000 SM cycles; 0 = default ~1 s)."""
+    _check(load_library().mwax_plan_set_wait_limit(plan.handle, kilocycles))
+
+
 def mwax_plan_enable_timing(plan: Plan, enable: bool = True):
     _check(load_library().mwax_plan_enable_timing(plan.handle, int(bool(enable))))
 
@@ -450,6 +475,9 @@ class Server:
     def drain(self):
         _check(load_library().mwax_server_drain(self.handle))
         self._keep.clear()
+
+    def reset_stats(self):
+        _check(load_library().mwax_server_reset_stats(self.handle))
 
     def stats(self) -> dict:
         st = ServerStats()

@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include "avg_groups.cuh"
 #include "plan.cuh"
 
 using namespace mwax;
@@ -40,65 +41,19 @@ mwax_status fail(mwax_status st, const char* fmt, ...)
                         cudaGetErrorString(e_), __FILE__, __LINE__);                                     \
     } while (0)
 
-// Output channel j of M = keep/F: centred on ultrafine offset (j - floor(M/2)) F; odd F
-// takes F bins of weight 1, even F takes F+1 bins with the two ends at 1/2; the DC bin
-// is dropped from the centre channel when F > 1 (unless kept); bins beyond the kept band
-// (the coarse channel, or its central keep bins when oversampled, Sec. 4.5) do not exist
-// (Sec. 2.6).  Produces gain[c] = sqrt(w_c) and the groups of
-// consecutive channels that feed the same output channels, with coef = 1 / sum(w).
+// Channel-averaging gains and groups (Sec. 2.6) of a plan, from the shared builder.
 bool build_groups(int N, int keep, int F, int dc_excl, std::vector<float>& gain, std::vector<Group>& groups)
 {
-    const int M = keep / F, jc = M / 2, half = F / 2;
-    std::vector<double> w(N, 0.0), wsum(M, 0.0);
-    std::vector<std::vector<int>> feeds(N);
-    for (int j = 0; j < M; ++j) {
-        const long long mid = (long long)(j - jc) * F;
-        for (long long u = mid - half; u <= mid + half; ++u) {
-            const long long c = u + N / 2;
-            if (u < -(keep / 2) || u > keep - keep / 2 - 1) continue;   // outside the kept band
-            double wt = (F % 2 == 0 && (u == mid - half || u == mid + half)) ? 0.5 : 1.0;
-            if (dc_excl && F > 1 && u == 0) wt = 0.0;
-            if (wt == 0.0) continue;
-            if (w[c] != 0.0 && w[c] != wt) return false;   // a bin has one weight everywhere
-            w[c] = wt;
-            feeds[c].push_back(j);
-            wsum[j] += wt;
-        }
-    }
+    const int M = keep / F;
+    std::vector<double> w(N), wsum(M);
+    std::vector<int> fa(N), fb(N);
+    std::vector<char> seen(M);
     gain.assign(N, 0.0f);
-    for (int c = 0; c < N; ++c) gain[c] = (float)sqrt(w[c]);
-    for (int j = 0; j < M; ++j)
-        if (wsum[j] <= 0.0) return false;
-    groups.clear();
-    for (int c = 0; c < N; ++c) {
-        if (w[c] == 0.0) continue;
-        if (feeds[c].size() > 2) return false;
-        const int ja = feeds[c][0], jb = feeds[c].size() > 1 ? feeds[c][1] : -1;
-        if (!groups.empty() && groups.back().ja == ja && groups.back().jb == jb) {
-            groups.back().c1 = c + 1;   // zero-weight channels in between are skipped by the kernels
-            continue;
-        }
-        Group g;
-        g.c0 = c;
-        g.c1 = c + 1;
-        g.ja = ja;
-        g.jb = jb;
-        g.ca = (float)(1.0 / wsum[ja]);
-        g.cb = jb >= 0 ? (float)(1.0 / wsum[jb]) : 0.0f;
-        g.first_a = g.first_b = 0;
-        groups.push_back(g);
-    }
-    // Mark, per output channel, the first group feeding it (groups are in channel order
-    // and a run always starts at the first group of its first channel).
-    std::vector<char> seen(M, 0);
-    for (auto& g : groups) {
-        if (!seen[g.ja]) g.first_a = 1;
-        seen[g.ja] = 1;
-        if (g.jb >= 0) {
-            if (!seen[g.jb]) g.first_b = 1;
-            seen[g.jb] = 1;
-        }
-    }
+    groups.assign(N, Group{});
+    const int ng = build_avg_groups(N, keep, F, dc_excl, gain.data(), groups.data(), N, w.data(), fa.data(), fb.data(),
+                                    wsum.data(), seen.data());
+    if (ng < 0) return false;
+    groups.resize(ng);
     return true;
 }
 
@@ -797,6 +752,7 @@ mwax_status enqueue_fstep(mwax_plan* p, const LaunchGroup& g, const int8_t* volt
     fa.tab_steps = p->cur_steps;
     fa.tab_step = p->cur_step;
     fa.flags = p->cur_flags;
+    fa.status = p->status;
     if (p->prec == MWAX_FP8) {
         // FP16 operands, then per path and channel group the max magnitude, then e4m3
         fa.Y = p->Y16;
@@ -840,7 +796,7 @@ XArgs make_xargs(const mwax_plan* p, const LaunchGroup& g, char* out)
     xa.post_scale = p->post_scale;
     xa.first_store = (g.ch == 0) ? 1 : 0;
     xa.status = p->status;
-    xa.spin_limit = 2000000;   // x 1000 cycles: ~1 s per bounded wait
+    xa.spin_limit = p->spin_limit;   // x 1000 cycles; 0: the kernels' default (~1 s per wait)
     xa.scale = p->amax;
     return xa;
 }
@@ -1073,6 +1029,13 @@ mwax_status mwax_plan_sync(mwax_plan* p)
         MWAX_CUDA(cudaMemset(p->status, 0, sizeof(int)));
         return fail(MWAX_ETIMEOUT, "a device-side bounded wait gave up (status %d)", st);
     }
+    return MWAX_OK;
+}
+
+mwax_status mwax_plan_set_wait_limit(mwax_plan* p, unsigned int kilocycles)
+{
+    if (!p) return fail(MWAX_EINVAL, "plan is NULL");
+    p->spin_limit = kilocycles;
     return MWAX_OK;
 }
 

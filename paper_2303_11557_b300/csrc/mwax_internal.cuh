@@ -70,6 +70,8 @@ struct FArgs {
     // set by launch_fstep from fs and N (so no kernel divides in FP64 per frame)
     double frame_dt;           // N / fs: seconds per frame
     double fs_over_n;          // fs / N: frames per second
+    int* status;               // device status word of the kernels with bounded waits (tensor-core
+                               //   F-step), or nullptr
 };
 
 // Delay (s) of path p for frame m of the call (N samples from absolute sample m N): the

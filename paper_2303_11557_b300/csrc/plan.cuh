@@ -93,6 +93,7 @@ struct mwax_plan {
 
     cudaStream_t stream = nullptr;
     int device = 0;
+    unsigned int spin_limit = 0;   // bounded device waits, x 1000 cycles (0: the kernels' default)
 
     // stage timing: event pairs per launch, drained by mwax_plan_stage_times
     bool timing = false;

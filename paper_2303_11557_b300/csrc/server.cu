@@ -19,6 +19,7 @@
 #include <map>
 #include <mutex>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "plan.cuh"
@@ -38,11 +39,19 @@ struct Request {
     double deadline_s;
     Clock::time_point submitted;
     int status = 0;   // 0 pending, 1 done, <0 -error
+    bool cold = false;   // its admission created a plan
 };
 
+// Plans are cached per shape: ordered on the descriptor's fields (never on its bytes, so
+// padding a caller left uninitialised cannot create a new plan per request).
 struct PlanKey {
     mwax_plan_desc d;
-    bool operator<(const PlanKey& o) const { return memcmp(&d, &o.d, sizeof d) < 0; }
+    auto fields() const
+    {
+        return std::tie(d.n_tiles, d.fft_len, d.fine_avg, d.int_time_s, d.samples_per_call, d.block_samples,
+                        d.precision, d.sky_freq_hz, d.keep_dc, d.workspace_limit, d.sample_rate_hz, d.keep_bins);
+    }
+    bool operator<(const PlanKey& o) const { return fields() < o.fields(); }
 };
 
 struct Lane {
@@ -72,7 +81,10 @@ struct mwax_server {
     std::thread thr;
     size_t hbm_in_use = 0;
     std::vector<double> latencies_ms;
+    std::vector<double> warm_latencies_ms;   // requests whose lane already held their plan
     long long completed = 0, failed = 0, misses = 0, submitted = 0;
+    long long cold = 0;   // admissions that had to create a plan
+    long long reset_completed = 0, reset_failed = 0;   // counts at the last statistics reset
     std::string init_error;
     bool ready = false;
 };
@@ -179,6 +191,8 @@ bool try_admit(mwax_server* S)
         }
     }
     S->queue.pop_front();
+    if (!has_plan) S->cold += 1;
+    r->cold = !has_plan;
     mwax_plan* p = lane_plan(S, *lane, d);
     bool ok = p && grow(S, reinterpret_cast<void**>(&lane->dvolt), &lane->dvolt_bytes, mwax_plan_input_bytes(p)) &&
               grow(S, reinterpret_cast<void**>(&lane->dout), &lane->dout_bytes, mwax_plan_output_bytes(p));
@@ -214,6 +228,7 @@ void reap(mwax_server* S)
             r->status = 1;
             S->completed += 1;
             S->latencies_ms.push_back(ms);
+            if (!r->cold) S->warm_latencies_ms.push_back(ms);
             if (r->deadline_s > 0 && ms > 1e3 * r->deadline_s) S->misses += 1;
         } else {
             r->status = -MWAX_ECUDA;
@@ -356,15 +371,27 @@ mwax_status mwax_server_drain(mwax_server* S)
 {
     if (!S) return set_error(MWAX_EINVAL, "server is NULL");
     std::unique_lock<std::mutex> lk(S->mu);
-    S->done_cv.wait(lk, [&] { return S->completed + S->failed == S->submitted; });
+    S->done_cv.wait(lk, [&] { return S->completed + S->failed + S->reset_completed + S->reset_failed == S->submitted; });
     return S->failed ? set_error(MWAX_ECUDA, "some requests failed") : MWAX_OK;
+}
+
+mwax_status mwax_server_reset_stats(mwax_server* S)
+{
+    if (!S) return set_error(MWAX_EINVAL, "server is NULL");
+    std::lock_guard<std::mutex> g(S->mu);
+    S->reset_completed += S->completed;
+    S->reset_failed += S->failed;
+    S->completed = S->failed = S->misses = S->cold = 0;
+    S->latencies_ms.clear();
+    S->warm_latencies_ms.clear();
+    return MWAX_OK;
 }
 
 mwax_status mwax_server_get_stats(mwax_server* S, mwax_server_stats* st)
 {
     if (!S || !st) return set_error(MWAX_EINVAL, "NULL argument");
     std::lock_guard<std::mutex> g(S->mu);
-    st->submitted = S->submitted;
+    st->submitted = S->submitted - S->reset_completed - S->reset_failed;
     st->completed = S->completed;
     st->failed = S->failed;
     st->queued = (long long)S->queue.size();
@@ -375,6 +402,9 @@ mwax_status mwax_server_get_stats(mwax_server* S, mwax_server_stats* st)
     st->max_ms = S->latencies_ms.empty() ? 0.0 : *std::max_element(S->latencies_ms.begin(), S->latencies_ms.end());
     st->deadline_misses = S->misses;
     st->hbm_in_use = S->hbm_in_use;
+    st->cold_starts = S->cold;
+    st->p50_warm_ms = percentile(S->warm_latencies_ms, 0.50);
+    st->p99_warm_ms = percentile(S->warm_latencies_ms, 0.99);
     return MWAX_OK;
 }
 

@@ -68,6 +68,24 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
     return true;
 }
 
+// Default bound of a wait, in units of 1000 SM clock cycles (~1 s at 2 GHz).
+constexpr unsigned int kDefaultSpin = 2000000u;
+// Bound of the waits after an abort for a kernel's own TMA loads and MMAs in flight.  Those
+// always complete (valid addresses, issued instructions), so this bound does not follow the
+// (possibly tiny) spin limit that fired; it only keeps a dead device from hanging the CTA.
+constexpr long long kDrainCycles = 4000000000LL;
+// Status bit recorded when even that drain bound ran out.
+constexpr int kDrainGaveUp = 256;
+
+// Wait for the phase of `parity` to complete, at most `limit` cycles; false on expiry.
+__device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, long long limit)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > limit) return false;
+    return true;
+}
+
 // ------------------------------------------------------------------ TMA
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2)
 {

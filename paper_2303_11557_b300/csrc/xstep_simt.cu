@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const long long nchunks = (a.klen + KT - 1) / KT;
-    const long long lim = (long long)(a.spin_limit > 0 ? a.spin_limit : 2000000) * 1000LL;
+    const long long lim = (long long)(a.spin_limit > 0 ? a.spin_limit : tc::kDefaultSpin) * 1000LL;
     volatile int* abort = &S.abort;
     int* status = a.status ? a.status : &S.local_status;
 
@@ -328,19 +328,16 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     }
 
     // Drain: the last copy issued into each stage has landed before the CTA exits (already
-    // true unless a wait gave up).
+    // true unless a wait gave up; copies from valid addresses always land, so the bound is
+    // the fixed drain bound, not the spin limit that may have fired).
     __syncthreads();
     if (tid == 0) {
         const long long issued = S.issued;
         for (int st = 0; st < STAGES; ++st) {
             if (issued <= st) continue;
             const long long last = issued - 1 - ((issued - 1 - st) % STAGES);   // last chunk copied into st
-            const long long t0 = clock64();
-            while (!tc::mbar_try_wait(&S.full[st], (uint32_t)((last / STAGES) & 1)))
-                if (clock64() - t0 > lim) {
-                    atomicOr(status, 64);
-                    break;
-                }
+            if (!tc::wait_bounded(&S.full[st], (uint32_t)((last / STAGES) & 1), tc::kDrainCycles))
+                atomicOr(status, tc::kDrainGaveUp);
         }
     }
 }

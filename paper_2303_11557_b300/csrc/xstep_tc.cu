@@ -104,6 +104,7 @@ struct TcSmem {
     uint64_t item_full[IRING];    // producer -> MMA + epilogue: item index published
     uint64_t item_empty[IRING];   // MMA + epilogue -> producer: slot free again
     int item[IRING];              // claimed item index, -1 = no more work
+    uint64_t drained;             // after an abort: the MMA issuer's last commit (all its MMAs done)
     uint32_t tmem_base;
     int abort;
 };
@@ -253,6 +254,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             tc::mbar_init(&S.item_full[r], 1);
             tc::mbar_init(&S.item_empty[r], 1 + EPI_THREADS);
         }
+        tc::mbar_init(&S.drained, 1);
         S.abort = 0;
         tc::fence_mbar_init();
     }
@@ -355,12 +357,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             if (*abort) {
                 // let the last load issued into each stage land before the CTA can exit
-                for (int s = 0; s < STAGES; ++s) {
-                    if (issued_phase[s] < 0) continue;
-                    const long long t0 = clock64();
-                    while (!tc::mbar_try_wait(&S.full[s], (uint32_t)issued_phase[s]) && clock64() - t0 < lim) {
-                    }
-                }
+                // (loads from valid addresses always land: the bound is not the spin limit)
+                for (int s = 0; s < STAGES; ++s)
+                    if (issued_phase[s] >= 0 && !tc::wait_bounded(&S.full[s], (uint32_t)issued_phase[s], tc::kDrainCycles))
+                        atomicOr(status, tc::kDrainGaveUp);
             }
         }
     } else if (warp == 1) {
@@ -524,11 +524,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
             }
             if (*abort && issued) {
-                // wait for the MMAs in flight before TMEM is released
-                tc::mma_commit(&S.acc_full[cur_b]);
-                const long long t0 = clock64();
-                while (!tc::mbar_try_wait(&S.acc_full[cur_b], cur_ph) && clock64() - t0 < lim) {
-                }
+                // wait for the MMAs in flight before TMEM is released: a commit on a barrier
+                // of its own arrives once every MMA issued so far has completed
+                tc::mma_commit(&S.drained);
+                if (!tc::wait_bounded(&S.drained, 0u, tc::kDrainCycles)) atomicOr(status, tc::kDrainGaveUp);
             }
         }
     } else {
@@ -743,8 +742,10 @@ cudaError_t launch_tc_kernel(const XLaunch& L, const XItem* items, int n_items, 
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
+    unsigned int spin = 0;   // x 1000 cycles per bounded wait: the largest of the jobs' limits
+    for (int j = 0; j < L.n_jobs; ++j) spin = L.jobs[j].a.spin_limit > spin ? L.jobs[j].a.spin_limit : spin;
     xstep_tc_kernel<MODE><<<n_items < sms ? n_items : sms, NTHREADS, smem, s>>>(L, items, n_items, counter, status,
-                                                                                 2000000u, dbuf);
+                                                                                 spin ? spin : tc::kDefaultSpin, dbuf);
     return cudaGetLastError();
 }
 

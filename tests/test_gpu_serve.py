@@ -60,3 +60,38 @@ def test_server_mix_equals_alone(budget_mb, lanes):
         assert srv.poll(ids[k]) == 1
         assert np.array_equal(o.numpy(), ref), f"request {k} differs"
     srv.close()
+
+
+def test_plan_cache_ignores_descriptor_padding():
+    # The server caches plans per shape.  Three requests of one shape whose descriptors
+    # differ only in their padding bytes (a C caller need not initialise those) must share
+    # one plan: one cold start, the rest served from the cache.
+    import ctypes
+    T, N, F, t, S = 8, 128, 4, 0.05, 64_000
+    desc = _desc(T, N, F, t, S, mw.MWAX_FP16)
+    volt, _ = workload(990, T, S, delay=None)
+    hv = torch.from_numpy(volt.reshape(-1)).pin_memory()
+    plan = mw.mwax_plan_create_ex(desc)
+    nbytes = plan.output_bytes
+    plan.close()
+    out = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    srv = mw.Server(n_lanes=1)
+    lib = mw.load_library()
+    src = desc.c()
+    size = ctypes.sizeof(type(src))
+    assert size > sum(ctypes.sizeof(ty) for _, ty in type(src)._fields_)   # the struct has padding
+    keep = []
+    for fill in (0x00, 0xFF, 0x5A):
+        raw = (ctypes.c_ubyte * size)(*([fill] * size))
+        cd = type(src).from_buffer(raw)
+        for name, _ in type(src)._fields_:
+            setattr(cd, name, getattr(src, name))
+        keep.append(raw)
+        rid = lib.mwax_server_submit(srv.handle, ctypes.byref(cd), ctypes.c_void_p(hv.data_ptr()), None,
+                                     ctypes.c_void_p(out.data_ptr()), ctypes.c_double(8.0))
+        assert rid >= 0
+        srv.wait(rid)
+    st = srv.stats()
+    assert st["completed"] == 3 and st["failed"] == 0
+    assert st["cold_starts"] == 1, st
+    srv.close()

@@ -252,7 +252,9 @@ mwax_status mwax_plan_stage_times(mwax_plan* plan, double ms[3], long long launc
 
 /* Launch choices of a plan.  fstep_variant: 0 = two-pass radix-32 F-step kernel (built
  * for N = 32..512; the generic kernel elsewhere), 1 = generic shared-memory Stockham
- * kernel.  run_len: output channels per X-step work item (0 = the plan's own choice: the
+ * kernel, 2 = tensor-core four-step DFT (the fine-channel FFT as two DFT-matrix products
+ * on tcgen05, N = 80 x 80 or 80 x 16: built for N = 6400 and 1280 with FP16 operands out,
+ * i.e. the MWAX_FP16 and MWAX_FP8 forms; variant 0 elsewhere).  run_len: output channels per X-step work item (0 = the plan's own choice: the
  * run length whose longest-first schedule of the work items on the GPU's resident CTA
  * slots is shortest).  window: column width of a tensor-core X-step tile, 128 or 256
  * (MWAX_FP16X3 always runs 128).  ms: device time of one call measured by the autotuner. */
@@ -266,7 +268,8 @@ typedef struct {
 /*
  * Autotuner: runs the plan on the caller's buffers (same arguments as mwax_correlate),
  * three calls per candidate, timed with CUDA events on the plan's stream (the fastest of
- * the three counts).  First the F-step variant (radix-32 or generic, for N = 32..512) with
+ * the three counts).  First the F-step variant (radix-32 or generic, for N = 32..512;
+ * generic or tensor-core four-step for N = 1280 and 6400 in the FP16 and FP8 forms) with
  * the plan's current X-step choice; then, with the faster variant, the tile window (256 or
  * 128 for the FP16 / FP8 forms; 128 only for MWAX_FP16X3) x the run length (the plan's
  * modelled choice, 3, 5, 11 and all output channels; candidates that configure the same
@@ -390,7 +393,8 @@ void mwax_server_destroy(mwax_server* server);
  * (f_u = (c - N/2) Fs / N; a frame takes the table step that holds its centre sample).
  * Optional detected outputs per interval of int_frames frames: Stokes I of each beam,
  * sum over the interval of |B_x|^2 + |B_y|^2, and the incoherent beam, sum over the
- * interval and the tiles of |Y|^2 per polarisation.  FP32 throughout.
+ * interval and the tiles of |Y|^2 per polarisation.  FP32 spectra; the beam sums on the
+ * tensor cores from FP16 hi/lo pairs (default) or in FP32 on the CUDA cores (engine 1).
  */
 typedef struct mwax_beamformer mwax_beamformer;
 
@@ -405,6 +409,10 @@ typedef struct {
     long long table_step_samples; /* samples per delay-table entry; 0 = 6,400 (5 ms)          */
     int int_frames;               /* frames per detected sample; 0 = no detected outputs      */
     size_t workspace_limit;       /* device bytes for one chunk's spectra; 0 = 4 GiB          */
+    int engine;                   /* 0 = tcgen05 tensor cores: per (5 ms step, 4 channels, pol,
+                                     16 beams) the beams x tiles by tiles x frames product from
+                                     FP16 hi/lo operand pairs, three products per term (FP32-
+                                     level error); 1 = FP32 CUDA cores                        */
 } mwax_beam_desc;
 
 /* NULL on error (mwax_last_error()); allocates the spectra workspace on the current device. */
@@ -425,6 +433,8 @@ size_t mwax_beam_output_bytes(const mwax_beamformer* bf, int which);
  */
 mwax_status mwax_beam_form(mwax_beamformer* bf, const int8_t* voltages, const double* beam_delay,
                            long long table_steps, void* beams_out, float* power_out, float* incoh_out);
+/* Waits for the beamformer's stream; MWAX_ETIMEOUT if a bounded device wait of the
+ * tensor-core engine gave up (the call's beams are then incomplete). */
 mwax_status mwax_beam_sync(mwax_beamformer* bf);
 
 /* Waits for the beamformer's stream, frees everything.  NULL is a no-op. */

@@ -48,7 +48,7 @@ class _BeamDesc(ctypes.Structure):
                 ("samples_per_call", ctypes.c_longlong), ("block_samples", ctypes.c_int),
                 ("sky_freq_hz", ctypes.c_double), ("sample_rate_hz", ctypes.c_double),
                 ("table_step_samples", ctypes.c_longlong), ("int_frames", ctypes.c_int),
-                ("workspace_limit", ctypes.c_size_t)]
+                ("workspace_limit", ctypes.c_size_t), ("engine", ctypes.c_int)]
 
 
 class _Call(ctypes.Structure):
@@ -554,10 +554,11 @@ class Beamformer:
 
     def __init__(self, n_tiles: int, fft_len: int, n_beams: int, samples_per_call: int, *, block_samples: int = 0,
                  sky_freq_hz: float = 0.0, sample_rate_hz: float = 0.0, table_step_samples: int = 0,
-                 int_frames: int = 0, workspace_limit: int = 0):
+                 int_frames: int = 0, workspace_limit: int = 0, engine: int = 0):
+        """engine: 0 = tensor cores (FP16 hi/lo pairs, FP32-level error), 1 = FP32 CUDA cores."""
         lib = load_library()
         self.desc = _BeamDesc(n_tiles, fft_len, n_beams, samples_per_call, block_samples, sky_freq_hz, sample_rate_hz,
-                              table_step_samples, int_frames, workspace_limit)
+                              table_step_samples, int_frames, workspace_limit, engine)
         h = lib.mwax_beam_create(ctypes.byref(self.desc))
         if not h:
             raise MwaxError(MWAX_EINVAL, mwax_last_error())

@@ -310,6 +310,8 @@ mwax_status mwax_plan_autotune(mwax_plan* p, const int8_t* voltages, const doubl
     BCUDA(cudaSetDevice(p->device));
     std::vector<int> fvars = {0};
     if (p->N >= 32 && p->N <= 512) fvars.push_back(1);
+    // tensor-core four-step DFT: FP16 operands out (the FP16 and FP8 forms), N = 1280, 6400
+    if ((p->prec == MWAX_FP16 || p->prec == MWAX_FP8) && fstep_tc_supported(p->N)) fvars.push_back(2);
     std::vector<int> windows = {p->window};
     if (tc_plan(p)) windows = {256, 128};
     std::vector<int> runs = {0};   // 0: the plan's modelled run length
@@ -385,7 +387,7 @@ mwax_status mwax_plan_autotune(mwax_plan* p, const int8_t* voltages, const doubl
 mwax_status mwax_plan_set_tuning(mwax_plan* p, const mwax_tuning* t)
 {
     if (!p || !t) return set_error(MWAX_EINVAL, "NULL argument");
-    if (t->fstep_variant < 0 || t->fstep_variant > 1 || (t->window != 128 && t->window != 256) || t->run_len < 0)
+    if (t->fstep_variant < 0 || t->fstep_variant > 2 || (t->window != 128 && t->window != 256) || t->run_len < 0)
         return set_error(MWAX_EINVAL, "invalid tuning");
     BCUDA(cudaSetDevice(p->device));
     BCUDA(cudaStreamSynchronize(p->stream));

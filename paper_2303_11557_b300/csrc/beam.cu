@@ -14,7 +14,9 @@
 // spectra stream in by asynchronous copies (two stages), and each thread accumulates an
 // 8-beam x 2-frame complex register tile.  The
 // incoherent beam (sum over tiles of |Y|^2) is accumulated from the same staged spectra.
-// Detected Stokes I is formed afterwards from the coherent beams.
+// Detected Stokes I is formed afterwards from the coherent beams.  That CUDA-core engine
+// (FP32) is engine 1; engine 0, the default, runs the same products on the tensor cores
+// (below).
 #include <math.h>
 #include <string.h>
 
@@ -22,6 +24,7 @@
 #include <vector>
 
 #include "plan.cuh"
+#include "tc_ptx.cuh"
 
 namespace mwax {
 namespace {
@@ -206,6 +209,299 @@ __global__ void __launch_bounds__(NT) beam_kernel(const BeamArgs a)
     }
 }
 
+// ------------------------------------------------------------------ tensor-core engine
+// The same product on tcgen05: per (step unit of <= 128 frames, 4 consecutive channels, one
+// polarisation, 16 beams) a CTA accumulates, channel by channel, D[m][b] = sum_t Y[t][m]
+// W[b][t] in tensor memory (M = frames, N = beams, K = tiles in chunks of 64).  Both
+// operands are staged by the CUDA cores into shared memory in the no-swizzle K-major layout
+// as FP16 hi/lo pairs (v = hi + lo, 22 significant bits; the spectra pre-scaled by a power
+// of two that keeps them in FP16 range, undone exactly at the end), and each complex term
+// takes three FP16 products per real product (hi hi, hi lo, lo hi; the dropped lo lo is
+// 2^-22 of it): the FP32 engine's accuracy on the tensor cores.  The steering phasors of
+// a chunk are made once per (beam, tile) at the first channel and advanced to the next
+// channel by the exact ratio e^{2 pi i tau Fs / N}.
+constexpr int TM = 128;                 // frames per unit (MMA M)
+constexpr int TNB = 16;                 // beams per CTA (MMA N)
+constexpr int TCQ = 4;                  // channels per CTA
+constexpr int TKC = 64;                 // tiles per K chunk
+constexpr int TNT = 256;                // threads per CTA
+constexpr uint32_t T_LBO_A = 16 * 128 + 16;   // A: 128 frame rows; K core stride (+16 B: bank spread)
+constexpr uint32_t T_APLANE = (TKC / 8) * T_LBO_A;
+constexpr uint32_t T_LBO_B = 2 * 128 + 16;    // B: 16 beam rows
+constexpr uint32_t T_BPLANE = (TKC / 8) * T_LBO_B;
+constexpr size_t kBeamTcSmem = 4 * T_APLANE + 6 * T_BPLANE + sizeof(float) * TCQ * TM + 1024;
+
+struct BeamTcShared {
+    uint64_t bar;       // MMA completion
+    uint64_t drained;   // after an abort: every MMA issued has completed
+    uint32_t tmem;
+    int abort;
+};
+
+__device__ __forceinline__ uint64_t plain_desc(uint32_t saddr, uint32_t lbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)(128u >> 4) << 32;   // SBO: next 8-row group
+    d |= (uint64_t)1 << 46;             // tcgen05 descriptor; no swizzle
+    return d;
+}
+
+__device__ __forceinline__ uint32_t plain_at(int r, int k, uint32_t lbo)
+{
+    return (uint32_t)(k >> 3) * lbo + (uint32_t)(r >> 3) * 128u + (uint32_t)(r & 7) * 16u + (uint32_t)(k & 7) * 2u;
+}
+
+__device__ __forceinline__ void split_half(float v, __half& hi, __half& lo)
+{
+    hi = __float2half_rn(v);
+    lo = __float2half_rn(v - __half2float(hi));   // the difference is exact in FP32
+}
+
+__device__ __forceinline__ void beam_tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(TNT, 2) beam_tc_kernel(const BeamArgs a, float prescale, float unscale, int* status)
+{
+    extern __shared__ __align__(1024) unsigned char beam_tc_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(beam_tc_raw) + 127) & ~(uintptr_t)127);
+    unsigned char* Ap[4];   // yr hi, yr lo, yi hi, yi lo
+    for (int i = 0; i < 4; ++i) Ap[i] = sm + i * T_APLANE;
+    unsigned char* Bp[6];   // wr hi, wr lo, wi hi, wi lo, -wi hi, -wi lo
+    for (int i = 0; i < 6; ++i) Bp[i] = sm + 4 * T_APLANE + i * T_BPLANE;
+    float* inc = reinterpret_cast<float*>(sm + 4 * T_APLANE + 6 * T_BPLANE);   // [TCQ][TM]
+    BeamTcShared& S = *reinterpret_cast<BeamTcShared*>(inc + TCQ * TM);
+
+    const BeamUnit un = a.units[blockIdx.x];
+    const int c0 = blockIdx.y * TCQ;
+    const int pol = blockIdx.z & 1, bg = blockIdx.z >> 1;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nfr = un.m_hi - un.m_lo;
+    const bool want_incoh = a.incoh != nullptr && bg == 0;
+    const int n_kc = (a.T + TKC - 1) / TKC;
+
+    for (int i = tid; i < TCQ * TM; i += TNT) inc[i] = 0.0f;
+    if (tid == 0) {
+        tc::mbar_init(&S.bar, 1);
+        tc::mbar_init(&S.drained, 1);
+        S.abort = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(&S.tmem, 128);   // D of the 4 channels: (16 re + 16 im) columns each
+        tc::tmem_relinquish();
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = S.tmem;
+    const uint32_t idesc = tc::idesc(0, TM, TNB, false);
+    const long long lim = (long long)tc::kDefaultSpin * 1000LL;
+    uint32_t parity = 0;
+    bool issued = false, waiting = false;
+    // a thread's own timeout (bad) decides nothing alone: every exit is taken by all threads
+    // at the same barrier, from __syncthreads_or of the threads' flags (stop)
+    bool bad = false, stop = false;
+
+    // steering role of this thread: beam b = tid / 16, tiles 4 (tid % 16) .. + 3 of a chunk
+    const int wb = tid >> 4, wt4 = tid & 15;
+    const int bb = bg * TNB + wb;
+    for (int kc = 0; kc < n_kc && !stop; ++kc) {
+        float2 w[4], R[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int tt = kc * TKC + 4 * wt4 + j;
+            w[j] = R[j] = make_float2(0.0f, 0.0f);
+            if (tt < a.T && bb < a.nb) {
+                const float4 pr = __ldg(a.params + ((long long)bb * a.n + 2 * tt + pol) * a.steps + un.step);
+                const int u0 = c0 - a.N / 2;
+                float x = (float)u0 * pr.y;
+                x -= rintf(x);
+                float y = pr.x + x + (float)u0 * pr.z;
+                y -= rintf(y);
+                float sn, cs;
+                sincospif(2.0f * y, &sn, &cs);
+                w[j] = make_float2(cs, sn);
+                const float dd = pr.y - rintf(pr.y) + pr.z;
+                sincospif(2.0f * dd, &sn, &cs);
+                R[j] = make_float2(cs, sn);
+            }
+        }
+        for (int ci = 0; ci < TCQ; ++ci) {
+            const int c = c0 + ci;
+            // the previous MMAs read the operands about to be overwritten
+            if (waiting) {
+                const long long t0 = clock64();
+                bool ok = true;
+                while (!tc::mbar_try_wait(&S.bar, parity)) {
+                    if (*reinterpret_cast<volatile int*>(&S.abort) || clock64() - t0 > lim) {
+                        ok = false;
+                        break;
+                    }
+                }
+                if (ok) {
+                    parity ^= 1u;
+                } else {
+                    bad = true;
+                    S.abort = 1;   // lets the other threads' waits give up early
+                    if (status) atomicOr(status, 4096);
+                }
+                waiting = false;
+            }
+            // A: Y^T (rows = frames, K = tiles), FP32 -> pre-scaled FP16 hi/lo; tiles past T
+            // are zero (K padding), frames past the unit are never read back
+            for (int e = tid; e < TKC * nfr; e += TNT) {
+                const int tl = e % TKC, m = e / TKC;
+                const int tt = kc * TKC + tl;
+                float yr = 0.0f, yi = 0.0f;
+                if (tt < a.T) {
+                    const long long row = ((long long)c * 2 * a.n + 2 * tt + pol) * a.Kpad + un.m_lo + m;
+                    yr = __ldg(a.Y + row);
+                    yi = __ldg(a.Y + row + (long long)a.n * a.Kpad);
+                }
+                if (want_incoh) {
+                    float pw = fmaf(yr, yr, yi * yi);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) pw += __shfl_xor_sync(0xffffffffu, pw, o);
+                    if (lane == 0) atomicAdd(&inc[ci * TM + m], pw);   // a warp holds 32 tiles of one frame
+                }
+                __half h[4];
+                split_half(yr * prescale, h[0], h[1]);
+                split_half(yi * prescale, h[2], h[3]);
+                const uint32_t o = plain_at(m, tl, T_LBO_A);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) *reinterpret_cast<__half*>(Ap[i] + o) = h[i];
+            }
+            // B: the steering phasors of this channel (rows = beams, K = tiles)
+            {
+                __half hr[2][4], hi[2][4], hn[2][4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    split_half(w[j].x, hr[0][j], hr[1][j]);
+                    split_half(w[j].y, hi[0][j], hi[1][j]);
+                    split_half(-w[j].y, hn[0][j], hn[1][j]);
+                    w[j] = cmul(w[j], R[j]);   // next channel
+                }
+                const uint32_t o = plain_at(wb, 4 * wt4, T_LBO_B);
+#pragma unroll
+                for (int l = 0; l < 2; ++l) {
+                    *reinterpret_cast<uint2*>(Bp[0 + l] + o) = *reinterpret_cast<const uint2*>(hr[l]);
+                    *reinterpret_cast<uint2*>(Bp[2 + l] + o) = *reinterpret_cast<const uint2*>(hi[l]);
+                    *reinterpret_cast<uint2*>(Bp[4 + l] + o) = *reinterpret_cast<const uint2*>(hn[l]);
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tc::fence_before();
+            if ((stop = __syncthreads_or(bad))) break;
+            if (tid == 0) {
+                tc::fence_after();
+                const uint32_t dre = tmem + 32u * ci, dim = dre + 16u;
+                uint32_t A0[4], B0[6];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) A0[i] = tc::smem_u32(Ap[i]);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) B0[i] = tc::smem_u32(Bp[i]);
+#pragma unroll
+                for (int ks = 0; ks < TKC / 16; ++ks) {
+                    const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+                    uint64_t da[4], db[6];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) da[i] = plain_desc(A0[i] + ks * 2u * T_LBO_A, T_LBO_A);
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) db[i] = plain_desc(B0[i] + ks * 2u * T_LBO_B, T_LBO_B);
+                    // re: yr wr - yi wi;  im: yr wi + yi wr  (hi hi, hi lo, lo hi of each)
+                    tc::mma_f16(dre, da[0], db[0], idesc, acc);
+                    tc::mma_f16(dre, da[0], db[1], idesc, 1u);
+                    tc::mma_f16(dre, da[1], db[0], idesc, 1u);
+                    tc::mma_f16(dre, da[2], db[4], idesc, 1u);
+                    tc::mma_f16(dre, da[2], db[5], idesc, 1u);
+                    tc::mma_f16(dre, da[3], db[4], idesc, 1u);
+                    tc::mma_f16(dim, da[0], db[2], idesc, acc);
+                    tc::mma_f16(dim, da[0], db[3], idesc, 1u);
+                    tc::mma_f16(dim, da[1], db[2], idesc, 1u);
+                    tc::mma_f16(dim, da[2], db[0], idesc, 1u);
+                    tc::mma_f16(dim, da[2], db[1], idesc, 1u);
+                    tc::mma_f16(dim, da[3], db[0], idesc, 1u);
+                }
+                tc::mma_commit(&S.bar);
+                issued = true;
+            }
+            waiting = true;
+        }
+    }
+    if (waiting && !stop) {
+        const long long t0 = clock64();
+        bool ok = true;
+        while (!tc::mbar_try_wait(&S.bar, parity)) {
+            if (*reinterpret_cast<volatile int*>(&S.abort) || clock64() - t0 > lim) {
+                ok = false;
+                break;
+            }
+        }
+        if (!ok) {
+            bad = true;
+            S.abort = 1;
+            if (status) atomicOr(status, 4096);
+        }
+    }
+    tc::fence_after();
+    stop = __syncthreads_or(bad);
+
+    // epilogue: row m = 32 (warp % 4) + lane, beams 8 (warp / 4) .. + 7; four channels per
+    // beam and frame are one 32-byte store
+    if (!stop) {
+        const int q = warp & 3, h = warp >> 2;
+        const int m = 32 * q + lane;
+        const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16);
+        float2 v[TCQ][8];
+#pragma unroll
+        for (int ci = 0; ci < TCQ; ++ci) {
+            uint32_t re[8], im[8];
+            beam_tmem_ld8(tq + 32u * ci + 8u * h, re);
+            beam_tmem_ld8(tq + 32u * ci + 16u + 8u * h, im);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int b = 0; b < 8; ++b)
+                v[ci][b] = make_float2(__uint_as_float(re[b]) * unscale, __uint_as_float(im[b]) * unscale);
+        }
+        if (m < nfr) {
+            const long long fr = a.f0 + un.m_lo + m;   // frame in the call
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const int beam = bg * TNB + 8 * h + b;
+                if (beam >= a.nb) continue;
+                float4* dst = reinterpret_cast<float4*>(a.beams + (((long long)beam * 2 + pol) * a.frames + fr) * a.N + c0);
+                dst[0] = make_float4(v[0][b].x, v[0][b].y, v[1][b].x, v[1][b].y);
+                dst[1] = make_float4(v[2][b].x, v[2][b].y, v[3][b].x, v[3][b].y);
+            }
+        }
+    }
+    if (!stop && want_incoh && a.int_frames > 0)
+        for (int i = tid; i < TCQ * nfr; i += TNT) {
+            const int ci = i / nfr, m = i % nfr;
+            const long long fr = a.f0 + un.m_lo + m;
+            const long long wdet = fr / a.int_frames;
+            if (wdet < a.n_det) atomicAdd(a.incoh + (wdet * 2 + pol) * a.N + c0 + ci, inc[ci * TM + m]);
+        }
+
+    if (tid == 0 && stop && issued) {
+        tc::mma_commit(&S.drained);
+        if (!tc::wait_bounded(&S.drained, 0u, tc::kDrainCycles) && status) atomicOr(status, tc::kDrainGaveUp);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after();
+        tc::tmem_dealloc(tmem, 128);
+    }
+}
+
 // Stokes I of each beam summed over the frames of each detection interval.
 __global__ void detect_kernel(const float2* __restrict__ beams, float* __restrict__ power, int nb, long long frames,
                               int N, int int_frames, long long n_det)
@@ -249,6 +545,9 @@ struct mwax_beamformer {
     BeamUnit* units = nullptr;
     long long units_cap = 0;
     std::vector<BeamUnit> h_units;
+    int* status = nullptr;    // bounded waits of the tensor-core engine
+    int engine = 0;           // 0: tcgen05 (FP16 hi/lo pairs), 1: FP32 CUDA cores
+    float prescale = 1.0f;    // power of two keeping the spectra in FP16 range (engine 0)
     cudaStream_t stream = nullptr;
     int device = 0;
     long long launches = 0;
@@ -265,6 +564,7 @@ void free_beam(mwax_beamformer* b)
     cudaFree(b->params);
     cudaFree(b->d_tab);
     cudaFree(b->units);
+    cudaFree(b->status);
     delete b;
 }
 
@@ -286,6 +586,7 @@ mwax_status beam_setup(mwax_beamformer* b, const mwax_beam_desc& d)
         return set_error(MWAX_EINVAL, "samples_per_call must be a whole number of blocks");
     if (d.sample_rate_hz < 0.0) return set_error(MWAX_EINVAL, "sample_rate_hz must be >= 0");
     if (d.table_step_samples < 0 || d.int_frames < 0) return set_error(MWAX_EINVAL, "negative table step or int_frames");
+    if (d.engine != 0 && d.engine != 1) return set_error(MWAX_EINVAL, "engine must be 0 (tensor cores) or 1 (CUDA cores)");
     b->desc = d;
     b->T = d.n_tiles;
     b->n = 2 * d.n_tiles;
@@ -299,7 +600,12 @@ mwax_status beam_setup(mwax_beamformer* b, const mwax_beam_desc& d)
     b->tab_step = d.table_step_samples ? d.table_step_samples : 6400;
     b->int_frames = d.int_frames;
     b->n_det = d.int_frames > 0 ? b->frames / d.int_frames : 0;
+    b->engine = d.engine;
+    // |Re Y|, |Im Y| <= 128 sqrt(2) N: scaled by 2^-k below 2^15 for the FP16 operands
+    while (181.0 * b->N * b->prescale > 32768.0) b->prescale *= 0.5f;
     BEAM_CUDA(cudaGetDevice(&b->device));
+    BEAM_CUDA(cudaMalloc(&b->status, sizeof(int)));
+    BEAM_CUDA(cudaMemset(b->status, 0, sizeof(int)));
 
     // spectra of a chunk of frames: workspace_limit (default 4 GiB) of FP32 operands
     const size_t limit = d.workspace_limit ? d.workspace_limit : ((size_t)4 << 30);
@@ -326,8 +632,10 @@ mwax_status beam_setup(mwax_beamformer* b, const mwax_beam_desc& d)
     return MWAX_OK;
 }
 
-// Work units of frames [f0, f0 + nfr): per table step, its frames in pieces of FMAX.
-void build_units(const mwax_beamformer* b, long long f0, long long nfr, long long steps, std::vector<BeamUnit>& u)
+// Work units of frames [f0, f0 + nfr): per table step, its frames in pieces of at most
+// fmax (32 for the CUDA-core engine, 128 = the MMA rows for the tensor-core engine).
+void build_units(const mwax_beamformer* b, long long f0, long long nfr, long long steps, int fmax,
+                 std::vector<BeamUnit>& u)
 {
     u.clear();
     long long m = 0;
@@ -336,7 +644,7 @@ void build_units(const mwax_beamformer* b, long long f0, long long nfr, long lon
         long long step = (2 * fr * b->N + b->N) / (2 * b->tab_step);
         if (step >= steps) step = steps - 1;
         long long e = m + 1;
-        while (e < nfr && e - m < FMAX) {
+        while (e < nfr && e - m < fmax) {
             long long s2 = (2 * (f0 + e) * b->N + b->N) / (2 * b->tab_step);
             if (s2 >= steps) s2 = steps - 1;
             if (s2 != step) break;
@@ -434,7 +742,7 @@ mwax_status mwax_beam_form(mwax_beamformer* b, const int8_t* volt, const double*
         fa.nu = b->nu;
         fa.fs = b->fs;
         BEAM_CUDA(launch_fstep(b->N, FOUT_F32, fa, s, 0));
-        build_units(b, f0, nfr, steps, b->h_units);
+        build_units(b, f0, nfr, steps, b->engine == 0 ? TM : FMAX, b->h_units);
         BEAM_CUDA(cudaMemcpyAsync(b->units, b->h_units.data(), sizeof(BeamUnit) * b->h_units.size(),
                                   cudaMemcpyHostToDevice, s));
         BeamArgs ba;
@@ -453,13 +761,24 @@ mwax_status mwax_beam_form(mwax_beamformer* b, const int8_t* volt, const double*
         ba.nb = b->nb;
         ba.int_frames = b->int_frames;
         ba.n_det = b->n_det;
-        dim3 grid((unsigned)b->h_units.size(), (unsigned)(b->N / CB), (unsigned)(2 * ((b->nb + BG - 1) / BG)));
-        static bool attr_done = false;
-        if (!attr_done) {
-            BEAM_CUDA(cudaFuncSetAttribute(beam_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBeamSmem));
-            attr_done = true;
+        if (b->engine == 0) {
+            dim3 grid((unsigned)b->h_units.size(), (unsigned)(b->N / TCQ), (unsigned)(2 * ((b->nb + TNB - 1) / TNB)));
+            static bool tc_attr_done = false;
+            if (!tc_attr_done) {
+                BEAM_CUDA(cudaFuncSetAttribute(beam_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)kBeamTcSmem));
+                tc_attr_done = true;
+            }
+            beam_tc_kernel<<<grid, TNT, kBeamTcSmem, s>>>(ba, b->prescale, 1.0f / b->prescale, b->status);
+        } else {
+            dim3 grid((unsigned)b->h_units.size(), (unsigned)(b->N / CB), (unsigned)(2 * ((b->nb + BG - 1) / BG)));
+            static bool attr_done = false;
+            if (!attr_done) {
+                BEAM_CUDA(cudaFuncSetAttribute(beam_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBeamSmem));
+                attr_done = true;
+            }
+            beam_kernel<<<grid, NT, kBeamSmem, s>>>(ba);
         }
-        beam_kernel<<<grid, NT, kBeamSmem, s>>>(ba);
         BEAM_CUDA(cudaGetLastError());
         b->launches += 2;
     }
@@ -477,6 +796,12 @@ mwax_status mwax_beam_sync(mwax_beamformer* b)
     if (!b) return set_error(MWAX_EINVAL, "beamformer is NULL");
     BEAM_CUDA(cudaSetDevice(b->device));
     BEAM_CUDA(cudaStreamSynchronize(b->stream));
+    int st = 0;
+    BEAM_CUDA(cudaMemcpy(&st, b->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st != 0) {
+        BEAM_CUDA(cudaMemset(b->status, 0, sizeof(int)));
+        return set_error(MWAX_ETIMEOUT, "a device-side bounded wait of the beamformer gave up");
+    }
     return MWAX_OK;
 }
 

@@ -1150,6 +1150,10 @@ cudaError_t launch_fstep(int N, int out_kind, const FArgs& a_in, cudaStream_t s,
     FArgs a = a_in;
     a.frame_dt = (double)N / a.fs;
     a.fs_over_n = a.fs / (double)N;
+    if (variant == 2) {
+        if (out_kind == FOUT_F16 && fstep_tc_supported(N)) return launch_fstep_tc(N, a, s);
+        variant = 0;
+    }
     switch (out_kind) {
         case FOUT_F32: return launch_kind<FOUT_F32>(N, a, s, variant);
         case FOUT_F16: return launch_kind<FOUT_F16>(N, a, s, variant);

@@ -1,0 +1,76 @@
+"""The tensor-core F-step (F-step variant 2: the fine-channel FFT as two DFT-matrix products
+on tcgen05, N = 80 x 80 = 6400 and 80 x 16 = 1280, FP16 operands out) against the FP64
+oracle, at the FP16 and FP8 bars: frame counts that leave ragged frame groups and groups
+that straddle two integrations, per-path quadratic delays, zeroed data blocks, and the
+same plan with the CUDA-core F-step for comparison."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2303_11557_b300 as mw
+import synth
+from _parity import oracle_desc, parity_error, workload
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = {mw.MWAX_FP16: 2e-3, mw.MWAX_FP8: 3e-2}
+PRECS = [pytest.param(mw.MWAX_FP16, id="fp16"), pytest.param(mw.MWAX_FP8, id="fp8")]
+
+
+def _run(desc, volt, delay, variant, flags=None):
+    plan = mw.mwax_plan_create_ex(desc)
+    mw.mwax_plan_set_stream(plan)
+    t = mw.mwax_plan_get_tuning(plan)
+    mw.mwax_plan_set_tuning(plan, mw.Tuning(variant, t.run_len, t.window, 0.0))
+    out = mw.empty_output(plan)
+    out.fill_(0xAB)
+    dv = torch.from_numpy(volt.reshape(-1)).cuda()
+    dd = None if delay is None else torch.from_numpy(delay).cuda()
+    if flags is None:
+        mw.mwax_correlate(plan, dv, dd, out)
+    else:
+        mw.mwax_correlate_ex(plan, dv, out, delay_poly=dd, zero_flags=torch.from_numpy(flags).cuda())
+    mw.mwax_plan_sync(plan)
+    vis, w = mw.split_output(plan, out)
+    res = vis.cpu().numpy(), w.cpu().numpy()
+    plan.close()
+    return res
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("N,F,K", [(6400, 50, 203), (1280, 10, 203), (1280, 40, 250)])
+def test_tensor_core_fstep_parity(prec, N, F, K):
+    # K frames per integration, 2 integrations: odd K leaves a frame pair (6400) split across
+    # the integrations, K not a multiple of 8 leaves 8-frame groups (1280) that straddle them
+    T = 6
+    bs = K * N
+    volt, delay = workload(0x7C + N + K, T, 2 * bs, block_samples=bs, delay="quadratic")
+    desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=K * N / synth.FS, samples_per_call=2 * bs,
+                       block_samples=bs, sky_freq_hz=synth.SKY_FREQ_HZ, precision=prec)
+    vis, w = _run(desc, volt, delay, 2)
+    ref, rw = oracle.correlate(oracle_desc(T, N, F, K * N / synth.FS, 2 * bs, block_samples=bs), volt, delay)
+    assert np.array_equal(w, rw.astype(np.float32))
+    err = parity_error(vis, ref, T)
+    assert np.all(np.isfinite(vis)) and err.max() <= TOL[prec], f"max err {err.max():.3e}"
+    # the CUDA-core F-step on the same plan: both within the bar, and close to each other
+    vis0, _ = _run(desc, volt, delay, 0)
+    assert parity_error(vis0, ref, T).max() <= TOL[prec]
+    assert parity_error(vis, vis0.astype(np.complex128), T).max() <= TOL[prec]
+
+
+def test_tensor_core_fstep_zeroed_blocks_and_many_paths():
+    # 40 tiles (80 paths: several path items per CTA), 10 blocks of 5 frames (N = 6400), a
+    # seeded tenth of the blocks flagged as zeroed: the F-step reads them as zero
+    T, N, F, K, bs = 40, 6400, 200, 50, 32_000
+    S = 2 * K * N
+    volt, delay = workload(0x7D, T, S, block_samples=bs, delay="quadratic")
+    flags = (np.random.default_rng(7).random((S // bs, 2 * T)) < 0.1).astype(np.uint8)
+    desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=K * N / synth.FS, samples_per_call=S,
+                       block_samples=bs, sky_freq_hz=synth.SKY_FREQ_HZ, precision=mw.MWAX_FP16)
+    vis, w = _run(desc, volt, delay, 2, flags=flags)
+    ref, rw = oracle.correlate_ext(oracle_desc(T, N, F, K * N / synth.FS, S, block_samples=bs),
+                                   oracle.Ext(zero_flags=flags), volt, delay)
+    assert np.allclose(w, rw, atol=1e-6)
+    err = parity_error(vis, ref, T)
+    assert np.all(np.isfinite(vis)) and err.max() <= 2e-3, f"max err {err.max():.3e}"

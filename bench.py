@@ -600,25 +600,34 @@ def run_extensions(mw, torch, W, dev_volt, delay, args, mpk):
                                 "n_chan_out": op.info["n_chan_out"]}
     op.close()
     del oo
-    # tied-array beams: 8 beams, 5 ms steering tables, 10 ms detected Stokes I + incoherent
+    # tied-array beams: 8 beams, 5 ms steering tables, 10 ms detected Stokes I + incoherent;
+    # both engines (0: tensor cores from FP16 hi/lo pairs, 1: FP32 CUDA cores)
     nb = 8
-    bf = mw.Beamformer(T, N, nb, S, sky_freq_hz=W["sky_freq_hz"], int_frames=100)
-    bf.set_stream()
     rng = np.random.default_rng(W["seed"] + 4)
     btab = torch.from_numpy(delay[None, :, :1] + rng.uniform(-200e-9, 200e-9, (nb, n, 1)) +
                             delay[None, :, 1:2] * t_mid[None, None, :]).cuda()
-    beams = torch.empty(bf.output_bytes(0), dtype=torch.uint8, device="cuda")
-    power = torch.empty(bf.output_bytes(1), dtype=torch.uint8, device="cuda").view(torch.float32)
-    incoh = torch.empty(bf.output_bytes(2), dtype=torch.uint8, device="cuda").view(torch.float32)
-    bms = _time_calls(torch, lambda: bf.form(dev_volt, btab, beams, power, incoh), steps, warm)
     flops = 8.0 * nb * n * S
     fp32_peak = mpk["fp32_fma_tflops_sustained"]
-    res["beamformer"] = {"n_beams": nb, "ms_per_subobs": bms, "real_time_factor": SUBOBS_S / (bms * 1e-3),
-                         "whole_call_tflops": flops / (bms * 1e-3) / 1e12, "fp32_peak_tflops": fp32_peak,
-                         "fp32_peak_kind": "measured FMA probe, sustained",
-                         "whole_call_frac": flops / (bms * 1e-3) / 1e12 / fp32_peak,
-                         "work": "8 flop per beam x path x sample (complex MAC); call includes the F-step"}
-    del bf, beams, power, incoh
+    beam = {"n_beams": nb, "work": "8 flop per beam x path x sample (complex MAC); calls include the F-step",
+            "fp32_peak_tflops": fp32_peak, "fp32_peak_kind": "measured FMA probe, sustained"}
+    for engine, name in ((0, "tensor_cores"), (1, "cuda_cores")):
+        bf = mw.Beamformer(T, N, nb, S, sky_freq_hz=W["sky_freq_hz"], int_frames=100, engine=engine)
+        bf.set_stream()
+        beams = torch.empty(bf.output_bytes(0), dtype=torch.uint8, device="cuda")
+        power = torch.empty(bf.output_bytes(1), dtype=torch.uint8, device="cuda").view(torch.float32)
+        incoh = torch.empty(bf.output_bytes(2), dtype=torch.uint8, device="cuda").view(torch.float32)
+        bms = _time_calls(torch, lambda: bf.form(dev_volt, btab, beams, power, incoh), steps, warm)
+        beam[name] = {"ms_per_subobs": bms, "real_time_factor": SUBOBS_S / (bms * 1e-3),
+                      "whole_call_tflops": flops / (bms * 1e-3) / 1e12}
+        del bf, beams, power, incoh
+    beam["cuda_cores"]["whole_call_frac_fp32"] = beam["cuda_cores"]["whole_call_tflops"] / fp32_peak
+    # the tensor-core engine issues 12 FP16 products of M 128 x N 16 per 16 tiles, channel, pol
+    # and 16 beams over units of at most 128 frames: at 50 frames per 5 ms step and 8 beams,
+    # issued / algorithmic = (128 / 50) (16 / 8) x 3 (hi/lo products)
+    beam["tensor_cores"]["issued_tflops_fp16"] = beam["tensor_cores"]["whole_call_tflops"] * (128 / 50) * 2 * 3
+    bf16_sus = peaks()[0].get("bf16_tflops_sustained", 1400.0)
+    beam["tensor_cores"]["issued_frac_of_tensor_peak"] = beam["tensor_cores"]["issued_tflops_fp16"] / bf16_sus
+    res["beamformer"] = beam
     return res
 
 

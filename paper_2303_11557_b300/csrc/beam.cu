@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(NT) beam_kernel(const BeamArgs a)
 }
 
 // ------------------------------------------------------------------ tensor-core engine
-// The same product on tcgen05: per (step unit of <= 128 frames, 4 consecutive channels, one
+// The same product on tcgen05: per (step unit of <= 64 frames, 4 consecutive channels, one
 // polarisation, 16 beams) a CTA accumulates, channel by channel, D[m][b] = sum_t Y[t][m]
 // W[b][t] in tensor memory (M = frames, N = beams, K = tiles in chunks of 64).  Both
 // operands are staged by the CUDA cores into shared memory in the no-swizzle K-major layout
@@ -220,7 +220,8 @@ __global__ void __launch_bounds__(NT) beam_kernel(const BeamArgs a)
 // 2^-22 of it): the FP32 engine's accuracy on the tensor cores.  The steering phasors of
 // a chunk are made once per (beam, tile) at the first channel and advanced to the next
 // channel by the exact ratio e^{2 pi i tau Fs / N}.
-constexpr int TM = 128;                 // frames per unit (MMA M)
+constexpr int TM = 128;                 // MMA M (rows = frames)
+constexpr int TMU = 64;                 // frames per unit (rows past it are never read back)
 constexpr int TNB = 16;                 // beams per CTA (MMA N)
 constexpr int TCQ = 4;                  // channels per CTA
 constexpr int TKC = 64;                 // tiles per K chunk
@@ -302,12 +303,44 @@ __global__ void __launch_bounds__(TNT, 2) beam_tc_kernel(const BeamArgs a, float
     tc::fence_after();
     const uint32_t tmem = S.tmem;
     const uint32_t idesc = tc::idesc(0, TM, TNB, false);
+    uint64_t desc_a[4], desc_b[6];   // operand planes at K step 0
+#pragma unroll
+    for (int i = 0; i < 4; ++i) desc_a[i] = plain_desc(tc::smem_u32(Ap[i]), T_LBO_A);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) desc_b[i] = plain_desc(tc::smem_u32(Bp[i]), T_LBO_B);
     const long long lim = (long long)tc::kDefaultSpin * 1000LL;
     uint32_t parity = 0;
     bool issued = false, waiting = false;
     // a thread's own timeout (bad) decides nothing alone: every exit is taken by all threads
     // at the same barrier, from __syncthreads_or of the threads' flags (stop)
     bool bad = false, stop = false;
+
+    // spectra loaded one (chunk, channel) step ahead: a thread takes frames mh + 16 j of
+    // the tile pairs tp0 and tp0 + 16 of the chunk, so a warp reads 64-byte runs of 4 tile
+    // rows per plane; frames past the unit and tiles past T read as zero
+    const int nj = (nfr + 15) >> 4;
+    float yv[TMU / 16][2][2][2];   // [j][pair][tile of the pair][re, im]
+    auto load_step = [&](int kc, int ci) {
+        const int mh = tid & 15, tp0 = tid >> 4;
+        const int c = c0 + ci;
+#pragma unroll
+        for (int j = 0; j < TMU / 16; ++j) {
+            const int m = mh + 16 * j;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int tt = kc * TKC + 2 * (tp0 + 16 * h) + e;
+                    yv[j][h][e][0] = yv[j][h][e][1] = 0.0f;
+                    if (j < nj && m < nfr && tt < a.T) {
+                        const long long row = ((long long)c * 2 * a.n + 2 * tt + pol) * a.Kpad + un.m_lo + m;
+                        yv[j][h][e][0] = __ldg(a.Y + row);
+                        yv[j][h][e][1] = __ldg(a.Y + row + (long long)a.n * a.Kpad);
+                    }
+                }
+        }
+    };
+    load_step(0, 0);
 
     // steering role of this thread: beam b = tid / 16, tiles 4 (tid % 16) .. + 3 of a chunk
     const int wb = tid >> 4, wt4 = tid & 15;
@@ -354,29 +387,40 @@ __global__ void __launch_bounds__(TNT, 2) beam_tc_kernel(const BeamArgs a, float
                 }
                 waiting = false;
             }
-            // A: Y^T (rows = frames, K = tiles), FP32 -> pre-scaled FP16 hi/lo; tiles past T
-            // are zero (K padding), frames past the unit are never read back
-            for (int e = tid; e < TKC * nfr; e += TNT) {
-                const int tl = e % TKC, m = e / TKC;
-                const int tt = kc * TKC + tl;
-                float yr = 0.0f, yi = 0.0f;
-                if (tt < a.T) {
-                    const long long row = ((long long)c * 2 * a.n + 2 * tt + pol) * a.Kpad + un.m_lo + m;
-                    yr = __ldg(a.Y + row);
-                    yi = __ldg(a.Y + row + (long long)a.n * a.Kpad);
-                }
-                if (want_incoh) {
-                    float pw = fmaf(yr, yr, yi * yi);
+            // A: Y^T (rows = frames, K = tiles) from the values loaded one step ahead, FP32 ->
+            // pre-scaled FP16 hi/lo; both tiles of a pair as one 4-byte word
+            {
+                const int mh = tid & 15, tp0 = tid >> 4;
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) pw += __shfl_xor_sync(0xffffffffu, pw, o);
-                    if (lane == 0) atomicAdd(&inc[ci * TM + m], pw);   // a warp holds 32 tiles of one frame
-                }
-                __half h[4];
-                split_half(yr * prescale, h[0], h[1]);
-                split_half(yi * prescale, h[2], h[3]);
-                const uint32_t o = plain_at(m, tl, T_LBO_A);
+                for (int j = 0; j < TMU / 16; ++j) {
+                    if (j >= nj) break;
+                    const int m = mh + 16 * j;
+                    const bool mok = m < nfr;
+                    if (want_incoh) {
+                        float pw = 0.0f;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) *reinterpret_cast<__half*>(Ap[i] + o) = h[i];
+                        for (int h = 0; h < 2; ++h)
+#pragma unroll
+                            for (int e = 0; e < 2; ++e)
+                                pw = fmaf(yv[j][h][e][0], yv[j][h][e][0], fmaf(yv[j][h][e][1], yv[j][h][e][1], pw));
+                        pw += __shfl_xor_sync(0xffffffffu, pw, 16);   // lanes L, L + 16: same frame
+                        if (lane < 16 && mok) atomicAdd(&inc[ci * TM + m], pw);
+                    }
+                    if (!mok) continue;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        __half hv[4][2];   // [yr hi, yr lo, yi hi, yi lo][tile of the pair]
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            split_half(yv[j][h][e][0] * prescale, hv[0][e], hv[1][e]);
+                            split_half(yv[j][h][e][1] * prescale, hv[2][e], hv[3][e]);
+                        }
+                        const uint32_t o = plain_at(m, 2 * (tp0 + 16 * h), T_LBO_A);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            *reinterpret_cast<__half2*>(Ap[i] + o) = __halves2half2(hv[i][0], hv[i][1]);
+                    }
+                }
             }
             // B: the steering phasors of this channel (rows = beams, K = tiles)
             {
@@ -402,19 +446,15 @@ __global__ void __launch_bounds__(TNT, 2) beam_tc_kernel(const BeamArgs a, float
             if (tid == 0) {
                 tc::fence_after();
                 const uint32_t dre = tmem + 32u * ci, dim = dre + 16u;
-                uint32_t A0[4], B0[6];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) A0[i] = tc::smem_u32(Ap[i]);
-#pragma unroll
-                for (int i = 0; i < 6; ++i) B0[i] = tc::smem_u32(Bp[i]);
 #pragma unroll
                 for (int ks = 0; ks < TKC / 16; ++ks) {
                     const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+                    // the start address field counts 16-byte units: step ks is 2 K core columns on
                     uint64_t da[4], db[6];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) da[i] = plain_desc(A0[i] + ks * 2u * T_LBO_A, T_LBO_A);
+                    for (int i = 0; i < 4; ++i) da[i] = desc_a[i] + (uint64_t)((ks * 2u * T_LBO_A) >> 4);
 #pragma unroll
-                    for (int i = 0; i < 6; ++i) db[i] = plain_desc(B0[i] + ks * 2u * T_LBO_B, T_LBO_B);
+                    for (int i = 0; i < 6; ++i) db[i] = desc_b[i] + (uint64_t)((ks * 2u * T_LBO_B) >> 4);
                     // re: yr wr - yi wi;  im: yr wi + yi wr  (hi hi, hi lo, lo hi of each)
                     tc::mma_f16(dre, da[0], db[0], idesc, acc);
                     tc::mma_f16(dre, da[0], db[1], idesc, 1u);
@@ -433,6 +473,9 @@ __global__ void __launch_bounds__(TNT, 2) beam_tc_kernel(const BeamArgs a, float
                 issued = true;
             }
             waiting = true;
+            // the next step's spectra load while these MMAs run
+            if (ci + 1 < TCQ) load_step(kc, ci + 1);
+            else if (kc + 1 < n_kc) load_step(kc + 1, 0);
         }
     }
     if (waiting && !stop) {
@@ -633,7 +676,7 @@ mwax_status beam_setup(mwax_beamformer* b, const mwax_beam_desc& d)
 }
 
 // Work units of frames [f0, f0 + nfr): per table step, its frames in pieces of at most
-// fmax (32 for the CUDA-core engine, 128 = the MMA rows for the tensor-core engine).
+// fmax (32 for the CUDA-core engine, 64 for the tensor-core engine).
 void build_units(const mwax_beamformer* b, long long f0, long long nfr, long long steps, int fmax,
                  std::vector<BeamUnit>& u)
 {
@@ -742,7 +785,7 @@ mwax_status mwax_beam_form(mwax_beamformer* b, const int8_t* volt, const double*
         fa.nu = b->nu;
         fa.fs = b->fs;
         BEAM_CUDA(launch_fstep(b->N, FOUT_F32, fa, s, 0));
-        build_units(b, f0, nfr, steps, b->engine == 0 ? TM : FMAX, b->h_units);
+        build_units(b, f0, nfr, steps, b->engine == 0 ? TMU : FMAX, b->h_units);
         BEAM_CUDA(cudaMemcpyAsync(b->units, b->h_units.data(), sizeof(BeamUnit) * b->h_units.size(),
                                   cudaMemcpyHostToDevice, s));
         BeamArgs ba;

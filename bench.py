@@ -513,13 +513,16 @@ def time_plan(mw, torch, plan, dev_volt, dev_delay, steps, warmup, world, clocks
     stream = torch.cuda.current_stream()
     mw.mwax_plan_set_stream(plan, stream)
     out = mw.empty_output(plan)
+    # the clock sampler (nvidia-smi) starts, and the library's stage events are created,
+    # before the warm-up: neither start-up happens inside the timed region
+    if clocks:
+        clocks.start()
+        time.sleep(1.0)
+    mw.mwax_plan_enable_timing(plan, True)
     for _ in range(warmup):
         mw.mwax_correlate(plan, dev_volt, dev_delay, out)
     mw.mwax_plan_sync(plan)
     mw.mwax_plan_stage_times(plan)          # reset counters
-    mw.mwax_plan_enable_timing(plan, True)
-    if clocks:
-        clocks.start()
     barrier(world)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -665,6 +668,25 @@ def run_mine(args, world, rank, local):
     host, delay = make_inputs(W, pin=not args.no_e2e)
     dev_volt = host.cuda(non_blocking=False)
     dev_delay = torch.from_numpy(delay).cuda()
+    if args.beam_only:
+        # the beamformer alone on this workload (profiler captures): 8 beams, one engine
+        import synth
+        T, S, N, n = W["n_tiles"], W["samples"], W["fft_len"], 2 * W["n_tiles"]
+        nb = 8
+        t_mid = (np.arange(S // 6400) + 0.5) * 6400 / synth.FS
+        rng = np.random.default_rng(W["seed"] + 4)
+        btab = torch.from_numpy(delay[None, :, :1] + rng.uniform(-200e-9, 200e-9, (nb, n, 1)) +
+                                delay[None, :, 1:2] * t_mid[None, None, :]).cuda()
+        bf = mw.Beamformer(T, N, nb, S, sky_freq_hz=W["sky_freq_hz"], int_frames=100, engine=args.beam_engine)
+        bf.set_stream()
+        beams = torch.empty(bf.output_bytes(0), dtype=torch.uint8, device="cuda")
+        power = torch.empty(bf.output_bytes(1), dtype=torch.uint8, device="cuda").view(torch.float32)
+        incoh = torch.empty(bf.output_bytes(2), dtype=torch.uint8, device="cuda").view(torch.float32)
+        ms = _time_calls(torch, lambda: bf.form(dev_volt, btab, beams, power, incoh), args.steps, args.warmup)
+        if rank == 0:
+            print(json.dumps({"beam_only": True, "engine": args.beam_engine, "workload": W["name"], "n_beams": nb,
+                              "ms_per_call": ms, "tflops_whole_call": 8.0 * nb * n * S / (ms * 1e-3) / 1e12}), flush=True)
+        return
     pk, pk_kind = peaks()
     mpk = measure_peaks(mw, torch, local)
     headline = args.precision
@@ -688,6 +710,9 @@ def run_mine(args, world, rank, local):
         # as a user does once per shape; the timed steps below run the chosen tuning
         tuning = (mw.mwax_plan_get_tuning(plan) if args.no_tune
                   else mw.mwax_plan_autotune(plan, dev_volt, ddelay, mw.empty_output(plan)))
+        if args.fstep_variant is not None:   # a fixed F-step kernel (profiler captures)
+            tuning = mw.Tuning(args.fstep_variant, tuning.run_len, tuning.window, 0.0)
+            mw.mwax_plan_set_tuning(plan, tuning)
         torch.cuda.empty_cache()
         clocks = ClockSampler(local) if form == headline else None
         ms, stages, out, ck = time_plan(mw, torch, plan, dev_volt, ddelay, args.steps, args.warmup, world, clocks)
@@ -875,6 +900,11 @@ def main():
     ap.add_argument("--fine-avg", type=int, default=0, help="fscrunch with --fft-len")
     ap.add_argument("--workload", default="full", choices=["full", "small"],
                     help="small = one 0.5 s integration (for profiler captures)")
+    ap.add_argument("--fstep-variant", type=int, default=None, choices=[0, 1, 2],
+                    help="fix the F-step kernel (0 radix-32 / generic, 1 generic, 2 tensor-core) after tuning")
+    ap.add_argument("--beam-only", action="store_true", help="time the beamformer alone (profiler captures)")
+    ap.add_argument("--beam-engine", type=int, default=0, choices=[0, 1],
+                    help="with --beam-only: 0 tensor cores, 1 CUDA cores")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":

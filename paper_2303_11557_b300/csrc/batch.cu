@@ -310,8 +310,10 @@ mwax_status mwax_plan_autotune(mwax_plan* p, const int8_t* voltages, const doubl
     BCUDA(cudaSetDevice(p->device));
     std::vector<int> fvars = {0};
     if (p->N >= 32 && p->N <= 512) fvars.push_back(1);
-    // tensor-core four-step DFT: FP16 operands out (the FP16 and FP8 forms), N = 1280, 6400
+    // tensor-core F-steps: the four-step DFT for FP16 operands out (the FP16 and FP8 forms)
+    // at N = 1280, 6400; the direct DFT product at N = 32, 64, 128 (every float form)
     if ((p->prec == MWAX_FP16 || p->prec == MWAX_FP8) && fstep_tc_supported(p->N)) fvars.push_back(2);
+    if (p->prec != MWAX_INT8 && (p->N == 32 || p->N == 64 || p->N == 128)) fvars.push_back(2);
     std::vector<int> windows = {p->window};
     if (tc_plan(p)) windows = {256, 128};
     std::vector<int> runs = {0};   // 0: the plan's modelled run length

@@ -1152,6 +1152,7 @@ cudaError_t launch_fstep(int N, int out_kind, const FArgs& a_in, cudaStream_t s,
     a.fs_over_n = a.fs / (double)N;
     if (variant == 2) {
         if (out_kind == FOUT_F16 && fstep_tc_supported(N)) return launch_fstep_tc(N, a, s);
+        if (fstep_dft_supported(N, out_kind) && a.ktile == 0) return launch_fstep_dft(N, out_kind, a, s);
         variant = 0;
     }
     switch (out_kind) {

@@ -145,12 +145,16 @@ struct XLaunch {
 
 // Launchers (each returns the cudaError_t of its launch).
 // variant 0: two-pass radix-32 kernel for N = 32..512 (generic elsewhere); 1: generic
-// Stockham passes for every N; 2: the tensor-core four-step DFT for FP16 output at
-// N = 1280 and 6400 (variant 0 elsewhere).
+// Stockham passes for every N; 2: a tensor-core F-step where one is built (the direct DFT
+// product for N = 32, 64, 128, every output kind; the four-step DFT for FP16 output at
+// N = 1280 and 6400), variant 0 elsewhere.
 cudaError_t launch_fstep(int N, int out_kind, const FArgs& a, cudaStream_t s, int variant);
 // The tensor-core four-step F-step (FP16 output), N = 1280 or 6400.
 bool fstep_tc_supported(int N);
 cudaError_t launch_fstep_tc(int N, const FArgs& a, cudaStream_t s);
+// The tensor-core direct-DFT F-step, N = 32, 64, 128 (FP32, FP16 or FP16 hi/lo output).
+bool fstep_dft_supported(int N, int out_kind);
+cudaError_t launch_fstep_dft(int N, int out_kind, const FArgs& a, cudaStream_t s);
 
 // e4m3 scale of a path's spectra from their max magnitude: 448 is e4m3's largest finite.
 __host__ __device__ __forceinline__ float e4m3_scale(float amax) { return amax > 0.0f ? amax * (1.0f / 448.0f) : 1.0f; }

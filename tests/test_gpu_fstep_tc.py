@@ -1,8 +1,9 @@
-"""The tensor-core F-step (F-step variant 2: the fine-channel FFT as two DFT-matrix products
-on tcgen05, N = 80 x 80 = 6400 and 80 x 16 = 1280, FP16 operands out) against the FP64
-oracle, at the FP16 and FP8 bars: frame counts that leave ragged frame groups and groups
-that straddle two integrations, per-path quadratic delays, zeroed data blocks, and the
-same plan with the CUDA-core F-step for comparison."""
+"""The tensor-core F-steps (F-step variant 2) against the FP64 oracle: the four-step DFT
+(two DFT-matrix products on tcgen05, N = 80 x 80 = 6400 and 80 x 16 = 1280, FP16 operands
+out) at the FP16 and FP8 bars, and the direct DFT product (N = 32, 64, 128) in every float
+form at its bar: frame counts that leave ragged items and items that straddle two
+integrations or data blocks, per-path quadratic delays, zeroed data blocks, and the same
+plan with the CUDA-core F-step for comparison."""
 import numpy as np
 import pytest
 
@@ -74,3 +75,44 @@ def test_tensor_core_fstep_zeroed_blocks_and_many_paths():
     assert np.allclose(w, rw, atol=1e-6)
     err = parity_error(vis, ref, T)
     assert np.all(np.isfinite(vis)) and err.max() <= 2e-3, f"max err {err.max():.3e}"
+
+
+# ---------------------------------------------------------------- direct-DFT tensor-core F-step
+TOL_ALL = {mw.MWAX_FP32: 1e-5, mw.MWAX_FP16: 2e-3, mw.MWAX_FP8: 3e-2, mw.MWAX_FP16X3: 1e-5}
+ALL_FLOAT = [pytest.param(mw.MWAX_FP32, id="fp32"), pytest.param(mw.MWAX_FP16, id="fp16"),
+             pytest.param(mw.MWAX_FP8, id="fp8"), pytest.param(mw.MWAX_FP16X3, id="fp16x3")]
+
+
+@pytest.mark.parametrize("prec", ALL_FLOAT)
+@pytest.mark.parametrize("N,F,K,bs", [(128, 4, 200, 6400), (64, 2, 250, 16_000), (32, 1, 250, 8000)])
+def test_direct_dft_fstep_parity(prec, N, F, K, bs):
+    # 128-frame items straddle the two integrations (K is not a multiple of 128) and data
+    # blocks smaller than an item (bulk copies split at block boundaries); per-path
+    # quadratic delays; every float form (FP16 DFT matrix for FP16 / FP8 operands, an FP16
+    # hi/lo pair for FP32 and hi/lo operands)
+    T = 7
+    S = 2 * K * N
+    assert S % bs == 0
+    volt, delay = workload(0x7E + N + prec, T, S, block_samples=bs, delay="quadratic")
+    desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=K * N / synth.FS, samples_per_call=S,
+                       block_samples=bs, sky_freq_hz=synth.SKY_FREQ_HZ, precision=prec)
+    vis, w = _run(desc, volt, delay, 2)
+    ref, rw = oracle.correlate(oracle_desc(T, N, F, K * N / synth.FS, S, block_samples=bs), volt, delay)
+    assert np.array_equal(w, rw.astype(np.float32))
+    err = parity_error(vis, ref, T)
+    assert np.all(np.isfinite(vis)) and err.max() <= TOL_ALL[prec], f"max err {err.max():.3e}"
+
+
+def test_direct_dft_fstep_zeroed_blocks_fp32():
+    T, N, F, K, bs = 9, 128, 4, 400, 6400
+    S = 2 * K * N
+    volt, delay = workload(0x7F, T, S, block_samples=bs, delay="quadratic")
+    flags = (np.random.default_rng(8).random((S // bs, 2 * T)) < 0.15).astype(np.uint8)
+    desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=K * N / synth.FS, samples_per_call=S,
+                       block_samples=bs, sky_freq_hz=synth.SKY_FREQ_HZ, precision=mw.MWAX_FP32)
+    vis, w = _run(desc, volt, delay, 2, flags=flags)
+    ref, rw = oracle.correlate_ext(oracle_desc(T, N, F, K * N / synth.FS, S, block_samples=bs),
+                                   oracle.Ext(zero_flags=flags), volt, delay)
+    assert np.allclose(w, rw, atol=1e-6)
+    err = parity_error(vis, ref, T)
+    assert np.all(np.isfinite(vis)) and err.max() <= 1e-5, f"max err {err.max():.3e}"

@@ -252,9 +252,12 @@ mwax_status mwax_plan_stage_times(mwax_plan* plan, double ms[3], long long launc
 
 /* Launch choices of a plan.  fstep_variant: 0 = two-pass radix-32 F-step kernel (built
  * for N = 32..512; the generic kernel elsewhere), 1 = generic shared-memory Stockham
- * kernel, 2 = tensor-core four-step DFT (the fine-channel FFT as two DFT-matrix products
- * on tcgen05, N = 80 x 80 or 80 x 16: built for N = 6400 and 1280 with FP16 operands out,
- * i.e. the MWAX_FP16 and MWAX_FP8 forms; variant 0 elsewhere).  run_len: output channels per X-step work item (0 = the plan's own choice: the
+ * kernel, 2 = tensor-core DFT products (N = 1280, 6400 with FP16 operands out, i.e. the
+ * MWAX_FP16 and MWAX_FP8 forms: the four-step DFT N = 80 x 16, 80 x 80 with both stages on
+ * tcgen05; N = 32, 64, 128 in every float form: the direct DFT as one product; variant 0
+ * elsewhere), 3 = 128-row tensor-core F-step (N = 128 x 10, 128 x 50 with FP16 operands
+ * out: stage A on tcgen05 with every accumulator lane a bin, stage B a radix-5/2 DFT in
+ * registers; variant 2 elsewhere).  run_len: output channels per X-step work item (0 = the plan's own choice: the
  * run length whose longest-first schedule of the work items on the GPU's resident CTA
  * slots is shortest).  window: column width of a tensor-core X-step tile, 128 or 256
  * (MWAX_FP16X3 always runs 128).  ms: device time of one call measured by the autotuner. */
@@ -269,7 +272,8 @@ typedef struct {
  * Autotuner: runs the plan on the caller's buffers (same arguments as mwax_correlate),
  * three calls per candidate, timed with CUDA events on the plan's stream (the fastest of
  * the three counts).  First the F-step variant (radix-32 or generic, for N = 32..512;
- * generic or tensor-core four-step for N = 1280 and 6400 in the FP16 and FP8 forms) with
+ * the tensor-core direct DFT for N = 32, 64, 128 in the float forms; generic and both
+ * tensor-core F-steps for N = 1280 and 6400 in the FP16 and FP8 forms) with
  * the plan's current X-step choice; then, with the faster variant, the tile window (256 or
  * 128 for the FP16 / FP8 forms; 128 only for MWAX_FP16X3) x the run length (the plan's
  * modelled choice, 3, 5, 11 and all output channels; candidates that configure the same
@@ -287,10 +291,11 @@ mwax_status mwax_plan_get_tuning(const mwax_plan* plan, mwax_tuning* tuning);
 /*
  * Batch of plans (e.g. many coarse channels of mixed tile counts, FFT lengths,
  * integration times and precisions) correlated together on one stream.  Each call runs
- * every plan once: per round, the plans' F-steps on auxiliary streams, then ONE
- * persistent tcgen05 X-step launch over all FP16 / FP8 plans' work (one job per plan,
- * work items claimed dynamically, most expensive first); FP32, FP16X3 and integer-mode
- * plans run their own X-steps.  The paper processes one coarse channel per server (Sec. 2.1); a
+ * every plan once: per round, the plans' F-steps on auxiliary streams, then one
+ * persistent tcgen05 X-step launch per tensor-core kernel mode (all FP16 / FP8 plans; all
+ * FP16X3 plans; all integer-mode plans), each over the merged work of its plans (one job
+ * per plan, work items claimed dynamically, most expensive first); FP32 plans run their
+ * own CUDA-core X-steps.  The paper processes one coarse channel per server (Sec. 2.1); a
  * batch processes many on one GPU.  The batch references the plans (they must outlive it,
  * stay on one device and not be used on their own while the batch runs) and uses the
  * plans' workspaces.  Returns NULL on error.

@@ -74,6 +74,7 @@ void free_plan(mwax_plan* p)
     if (!p) return;
     cudaFree(p->Y);
     cudaFree(p->Y16);
+    cudaFree(p->Yt);
     cudaFree(p->tw);
     cudaFree(p->delay);
     cudaFree(p->groups);
@@ -753,6 +754,8 @@ mwax_status enqueue_fstep(mwax_plan* p, const LaunchGroup& g, const int8_t* volt
     fa.tab_step = p->cur_step;
     fa.flags = p->cur_flags;
     fa.status = p->status;
+    fa.Yt = p->Yt;
+    fa.Yt_bytes = (long long)p->Yt_bytes;
     if (p->prec == MWAX_FP8) {
         // FP16 operands, then per path and channel group the max magnitude, then e4m3
         fa.Y = p->Y16;

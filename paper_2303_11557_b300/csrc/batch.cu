@@ -3,9 +3,10 @@
 //
 // Schedule of one batch call: every plan's output is initialised; then, round by round,
 // the F-steps of each plan's r-th launch group run on auxiliary streams (fork/join), and
-// ONE persistent tcgen05 X launch covers the r-th groups of all FP16 / FP8 plans (their
-// work items merged into one cost-sorted list; each plan is one job of the launch).
-// CUDA-core FP32 and integer-mode plans run their X-steps in the same round after it.
+// one persistent tcgen05 X launch per kernel mode covers the r-th groups of all plans of
+// that mode (FP16 / FP8 plans; FP16 hi/lo-pair plans; integer-mode plans): their work
+// items are merged into one cost-sorted list and each plan is one job of the launch.
+// CUDA-core FP32 plans run their own X-steps in the same round after them.
 // The paper runs one coarse channel per server (Sec. 2.1); here one GPU takes many.
 #include <math.h>
 #include <string.h>
@@ -32,7 +33,7 @@ struct mwax_batch {
         XItem* items = nullptr;
         int n_items = 0;
     };
-    std::vector<RoundX> rx;
+    std::vector<std::vector<RoundX>> rx;   // [round][kernel mode]
     int* counter = nullptr;
     int* status = nullptr;
     bool graphs = true;
@@ -53,11 +54,30 @@ constexpr int kAuxStreams = 4;
 
 bool tc_plan(const mwax_plan* p) { return p->prec == MWAX_FP16 || p->prec == MWAX_FP8; }
 
+// Kernel mode of a plan's tensor-core X-step: 0 FP16 / FP8, 1 FP16 hi/lo pairs, 2 integer
+// mode; -1 for the CUDA-core FP32 X-step.  One persistent launch serves one mode.
+constexpr int kModes = 3;
+int x_mode(const mwax_plan* p)
+{
+    switch (p->prec) {
+        case MWAX_FP16: case MWAX_FP8: return 0;
+        case MWAX_FP16X3: return 1;
+        case MWAX_INT8: return 2;
+        default: return -1;
+    }
+}
+
+int x_op(const mwax_plan* p)
+{
+    return p->prec == MWAX_FP8 ? 1 : (p->prec == MWAX_FP16X3 ? 2 : (p->prec == MWAX_INT8 ? 3 : 0));
+}
+
 void free_batch(mwax_batch* b)
 {
     if (!b) return;
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
-    for (auto& r : b->rx) cudaFree(r.items);
+    for (auto& r : b->rx)
+        for (auto& m : r) cudaFree(m.items);
     cudaFree(b->counter);
     cudaFree(b->status);
     for (auto s : b->aux) cudaStreamDestroy(s);
@@ -78,26 +98,31 @@ mwax_status build(mwax_batch* b)
         n_rounds = std::max(n_rounds, groups.back().size());
     }
     b->rounds.assign(n_rounds, {});
-    b->rx.assign(n_rounds, {});
+    b->rx.assign(n_rounds, std::vector<mwax_batch::RoundX>(kModes));
     for (size_t r = 0; r < n_rounds; ++r) {
-        std::vector<std::pair<double, XItem>> items;
+        std::vector<std::pair<double, XItem>> items[kModes];
         for (size_t i = 0; i < b->plans.size(); ++i) {
             if (r >= groups[i].size()) continue;
             const LaunchGroup& g = groups[i][r];
             b->rounds[r].push_back({(int)i, g});
             mwax_plan* p = b->plans[i];
-            if (!tc_plan(p)) continue;
-            const int job = (int)b->rx[r].jobs.size();
-            if (job >= kMaxJobs) return set_error(MWAX_EUNSUPPORTED, "more tensor-core plans in a batch than kMaxJobs");
-            b->rx[r].jobs.push_back((int)i);
-            plan_items(*p, job, g.nslots, g.klen, items);
+            const int m = x_mode(p);
+            if (m < 0) continue;
+            mwax_batch::RoundX& R = b->rx[r][m];
+            const int job = (int)R.jobs.size();
+            if (job >= kMaxJobs) return set_error(MWAX_EUNSUPPORTED, "more tensor-core plans of one mode than kMaxJobs");
+            R.jobs.push_back((int)i);
+            plan_items(*p, job, g.nslots, g.klen, items[m]);
         }
-        std::vector<XItem> order;
-        sort_items(items, order);
-        b->rx[r].n_items = (int)order.size();
-        if (!order.empty()) {
-            BCUDA(cudaMalloc(&b->rx[r].items, sizeof(XItem) * order.size()));
-            BCUDA(cudaMemcpy(b->rx[r].items, order.data(), sizeof(XItem) * order.size(), cudaMemcpyHostToDevice));
+        for (int m = 0; m < kModes; ++m) {
+            std::vector<XItem> order;
+            sort_items(items[m], order);
+            mwax_batch::RoundX& R = b->rx[r][m];
+            R.n_items = (int)order.size();
+            if (!order.empty()) {
+                BCUDA(cudaMalloc(&R.items, sizeof(XItem) * order.size()));
+                BCUDA(cudaMemcpy(R.items, order.data(), sizeof(XItem) * order.size(), cudaMemcpyHostToDevice));
+            }
         }
     }
     BCUDA(cudaMalloc(&b->counter, sizeof(int)));
@@ -145,9 +170,10 @@ mwax_status enqueue_batch(mwax_batch* b, const int8_t* const* volt, const double
             BCUDA(cudaEventRecord(b->joins[a], b->aux[a]));
             BCUDA(cudaStreamWaitEvent(s, b->joins[a], 0));
         }
-        // one persistent tensor-core X launch for every FP16 / FP8 plan of the round
-        const auto& R = b->rx[r];
-        if (!R.jobs.empty()) {
+        // one persistent tensor-core X launch per kernel mode for the round's plans
+        for (int m = 0; m < kModes; ++m) {
+            const auto& R = b->rx[r][m];
+            if (R.jobs.empty()) continue;
             L.n_jobs = (int)R.jobs.size();
             for (size_t j = 0; j < R.jobs.size(); ++j) {
                 const int i = R.jobs[j];
@@ -158,16 +184,17 @@ mwax_status enqueue_batch(mwax_batch* b, const int8_t* const* volt, const double
                 L.jobs[j].tmap = p->tmap;
                 L.jobs[j].a = make_xargs(p, *g, static_cast<char*>(out[i]));
                 L.jobs[j].a.status = b->status;
-                L.jobs[j].op = (p->prec == MWAX_FP8) ? 1 : 0;
+                if (p->prec == MWAX_INT8) L.jobs[j].a.seg_frames = int8_seg_frames(g->klen);
+                L.jobs[j].op = x_op(p);
                 L.jobs[j].max_cols = 0;
                 for (const int4& tl : p->h_tiles) L.jobs[j].max_cols = std::max(L.jobs[j].max_cols, tl.z);
             }
             BCUDA(launch_xstep_tc(L, R.items, R.n_items, b->counter, b->status, s));
         }
-        // the other plans' X-steps
+        // the CUDA-core FP32 plans' X-steps
         for (auto& e : b->rounds[r]) {
             mwax_plan* p = b->plans[e.first];
-            if (tc_plan(p)) continue;
+            if (x_mode(p) >= 0) continue;
             mwax_status st = enqueue_xstep_single(p, e.second, make_xargs(p, e.second, static_cast<char*>(out[e.first])), s);
             if (st != MWAX_OK) return st;
         }
@@ -176,6 +203,24 @@ mwax_status enqueue_batch(mwax_batch* b, const int8_t* const* volt, const double
 }
 
 }  // namespace
+
+namespace mwax {
+mwax_status ensure_f128_scratch(mwax_plan* p)
+{
+    if (!fstep_f128_supported(p->N) || (p->prec != MWAX_FP16 && p->prec != MWAX_FP8)) return MWAX_OK;
+    const size_t need = fstep_f128_scratch_bytes(p->N, p->n, p->Kc);
+    if (p->Yt_bytes >= need) return MWAX_OK;
+    BCUDA(cudaSetDevice(p->device));
+    BCUDA(cudaStreamSynchronize(p->stream));
+    cudaFree(p->Yt);
+    p->Yt = nullptr;
+    p->Yt_bytes = 0;
+    BCUDA(cudaMalloc(&p->Yt, need));
+    p->Yt_bytes = need;
+    return MWAX_OK;
+}
+
+}  // namespace mwax
 
 extern "C" {
 
@@ -313,6 +358,7 @@ mwax_status mwax_plan_autotune(mwax_plan* p, const int8_t* voltages, const doubl
     // tensor-core F-steps: the four-step DFT for FP16 operands out (the FP16 and FP8 forms)
     // at N = 1280, 6400; the direct DFT product at N = 32, 64, 128 (every float form)
     if ((p->prec == MWAX_FP16 || p->prec == MWAX_FP8) && fstep_tc_supported(p->N)) fvars.push_back(2);
+    if ((p->prec == MWAX_FP16 || p->prec == MWAX_FP8) && fstep_f128_supported(p->N)) fvars.push_back(3);
     if (p->prec != MWAX_INT8 && (p->N == 32 || p->N == 64 || p->N == 128)) fvars.push_back(2);
     std::vector<int> windows = {p->window};
     if (tc_plan(p)) windows = {256, 128};
@@ -344,6 +390,7 @@ mwax_status mwax_plan_autotune(mwax_plan* p, const int8_t* voltages, const doubl
     // stage 1: the F-step variant, with the plan's own X-step choice
     const int rl0 = p->run_len, w0 = p->window;
     for (int fv : fvars) {
+        if (fv == 3 && (st = ensure_f128_scratch(p)) != MWAX_OK) break;
         p->fvariant = fv;
         st = configure_x(*p, rl0, w0);
         if (st != MWAX_OK) break;
@@ -389,10 +436,14 @@ mwax_status mwax_plan_autotune(mwax_plan* p, const int8_t* voltages, const doubl
 mwax_status mwax_plan_set_tuning(mwax_plan* p, const mwax_tuning* t)
 {
     if (!p || !t) return set_error(MWAX_EINVAL, "NULL argument");
-    if (t->fstep_variant < 0 || t->fstep_variant > 2 || (t->window != 128 && t->window != 256) || t->run_len < 0)
+    if (t->fstep_variant < 0 || t->fstep_variant > 3 || (t->window != 128 && t->window != 256) || t->run_len < 0)
         return set_error(MWAX_EINVAL, "invalid tuning");
     BCUDA(cudaSetDevice(p->device));
     BCUDA(cudaStreamSynchronize(p->stream));
+    if (t->fstep_variant == 3) {
+        const mwax_status st = ensure_f128_scratch(p);
+        if (st != MWAX_OK) return st;
+    }
     p->fvariant = t->fstep_variant;
     return configure_x(*p, t->run_len, tc_plan(p) ? t->window : p->window);
 }

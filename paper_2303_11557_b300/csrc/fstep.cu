@@ -1150,6 +1150,10 @@ cudaError_t launch_fstep(int N, int out_kind, const FArgs& a_in, cudaStream_t s,
     FArgs a = a_in;
     a.frame_dt = (double)N / a.fs;
     a.fs_over_n = a.fs / (double)N;
+    if (variant == 3) {
+        if (out_kind == FOUT_F16 && fstep_f128_supported(N) && a.Yt) return launch_fstep_f128(N, a, s);
+        variant = 2;
+    }
     if (variant == 2) {
         if (out_kind == FOUT_F16 && fstep_tc_supported(N)) return launch_fstep_tc(N, a, s);
         if (fstep_dft_supported(N, out_kind) && a.ktile == 0) return launch_fstep_dft(N, out_kind, a, s);

@@ -1,0 +1,681 @@
+// Tensor-core F-step for the long fine-channel FFTs with full 128-row MMAs (Sec. 2.5.1:
+// N = 128 N2, here 1280 = 128 x 10 and 6400 = 128 x 50), FP16 operands out (the FP16 and
+// FP8 forms).  Four-step decomposition with the 128-point DFT on the tensor cores:
+//   sample n = n1 + 128 n2, bin k = N2 k1 + k2,
+//   stage P (CUDA cores, one thread per n1 of a frame, in registers):
+//       Z[n1, k2] = e^{-2 pi i n1 k2 / N} sum_n2 x[n1 + 128 n2] e^{-2 pi i n2 k2 / N2}
+//   stage A (tcgen05, both operands in shared memory, M = 128 bins k1, K = 128 samples n1):
+//       X[N2 k1 + k2] = sum_n1 e^{-2 pi i k1 n1 / 128} Z[n1, k2]
+//   stage E (CUDA cores, one lane per k1): the delay phasor (Sec. 4.3), the channel gain,
+//       FP16 (re, im) into a frame-major scratch tile of the item, Yt[p][group][c][g],
+//       c = fftshift(k): one 2 MB page per item, whole sectors;
+//   transpose (one launch per slot after the F-step's): Yt to the K-major operand planes
+//       Y[slot][c][plane][p][Kpad], a warp writing 64 contiguous bytes of a row at a time.
+// Writing the K-major rows straight from the bins (each item holds only G frames, so each
+// lane's store lands in its own row and 2 MB page) measured several times slower than
+// the whole F-step: the address translation of scattered rows, not DRAM, bounds it.
+// Every accumulator lane is a bin row k1.  The B operand's rows are ordered (half of k2,
+// k2 within the half, frame): a warp's lanes read the G frames of one bin from adjacent
+// tensor-memory columns and store them with one 2G-byte store per plane.  Z is rounded to
+// FP16 once and the 128-point DFT matrix is FP16 (2^-12 per entry): the FP16 form's error
+// bar holds widely.
+//
+// A persistent CTA (one per SM: 8 worker warps and a control warp) loops over the items (G
+// frames of one path) of one integration slot, software-pipelined: while the worker warps run
+// stage E of item j, the tensor cores run stage A of item j + 1 into the other half of
+// tensor memory and the bulk copy of item j + 2's int8 samples lands; the control warp
+// issues both and computes the frame terms; one CTA barrier per item.  Every wait is bounded (status
+// word); loop exits are taken by all threads at that barrier.
+#include "mwax_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace mwax {
+namespace {
+
+constexpr int kM = 128;                 // bins k1 (MMA rows), samples n1 (MMA K)
+constexpr int kW = 256;                 // worker threads (stages P and E)
+constexpr int kT = kW + 32;             // plus one control warp (copies, MMAs, frame terms)
+constexpr uint32_t kLboF = 16 * 128;    // DFT matrix: 128 rows per K core column
+constexpr uint32_t kFPlane = 16 * kLboF;
+constexpr uint32_t kBufCols = 256;      // tensor-memory columns per accumulator buffer
+
+template <int N2, int G>
+struct F128 {
+    static constexpr int N = kM * N2;
+    static constexpr int H = N2 / 2;                          // bins k2 per warp half
+    static constexpr int HS = (H * G + 7) / 8 * 8;            // B rows per half (padded)
+    static constexpr int NA = 2 * HS;                         // MMA N
+    static_assert(N2 % 2 == 0 && NA % 16 == 0 && 2 * NA <= (int)kBufCols, "MMA shape");
+    static_assert(G == 2 || G == 4 || G == 8, "frames per item");
+    // K core-column stride padded by 16 B: the 2- and 4-byte stores of stage P, whose
+    // lanes walk along K, spread over all banks
+    static constexpr uint32_t LBO_X = NA * 16 + 16;
+    static constexpr uint32_t XPLANE = 16 * LBO_X;
+    static constexpr uint32_t STAGE = G * 2 * N;              // int8 (re, im) of the item's frames
+    // stage P: one thread per sample n1 of a frame, or per pair (n1, n1 + 1) when there
+    // are enough pairs for every thread (4-byte stores)
+    static constexpr bool PAIR = G * kM / 2 >= kW;
+    static constexpr int TASKS = PAIR ? G * kM / 2 : G * kM;
+    static_assert(TASKS % kW == 0, "whole tasks per thread");
+    static constexpr int PER = TASKS / kW;
+    static constexpr int CB = 8 / G;                          // bins per 8-column load
+    static constexpr int NCH = (H + CB - 1) / CB;             // loads per half and plane
+    static_assert((NCH * CB - 1) * G + G <= HS, "loads stay inside the half's columns");
+};
+
+struct F128Frame {
+    long long slot, k;       // operand slot and frame within it (slot -1: not stored)
+    float phi0, d_hi, d_lo;  // delay terms: the phasor of bin offset u is e^{2 pi i (phi0 + u d)}
+    int delay;
+    float2 step;             // e^{2 pi i d}: phasor ratio between bins k and k + 1
+};
+
+// Items of one launch: one integration slot, path-major, groups of G frames.
+struct F128Items {
+    unsigned n_items;    // paths x groups
+    unsigned groups;     // groups of G frames per slot: ceil(Kc / G)
+    unsigned slot;       // slot of the launch group
+};
+
+// Path, first frame (of the call) and frames in the slot (at most G) of an item.
+template <int G>
+__device__ __forceinline__ void item_pos(const F128Items& m, long long Kc, unsigned item, unsigned& p, long long& f0,
+                                         int& nv)
+{
+    p = item / m.groups;
+    const unsigned fg = item - p * m.groups;
+    f0 = (long long)m.slot * Kc + (long long)fg * G;
+    const long long left = Kc - (long long)fg * G;
+    nv = left < G ? (int)left : G;
+}
+
+struct F128Shared {
+    uint64_t ld_bar;         // an item's int8 frames staged
+    uint64_t bar;            // an item's stage-A MMAs complete
+    uint64_t drained;        // after an abort: every MMA issued has completed
+    unsigned ld_mask;        // frames of the staged item with data
+    uint32_t tmem;
+    int abort;
+};
+
+__device__ __forceinline__ uint64_t desc_plain(uint32_t saddr, uint32_t lbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)(128u >> 4) << 32;   // SBO: next 8-row group
+    d |= (uint64_t)1 << 46;             // tcgen05 descriptor, no swizzle
+    return d;
+}
+
+// Byte offset of element (row r, K index k) of a K-major no-swizzle operand: 8-row x 16-byte
+// core matrices, 8-row groups 128 B apart, K core columns lbo apart.
+__device__ __forceinline__ uint32_t plain_off(int r, int k, uint32_t lbo)
+{
+    return (uint32_t)(k >> 3) * lbo + (uint32_t)(r >> 3) * 128u + (uint32_t)(r & 7) * 16u + (uint32_t)(k & 7) * 2u;
+}
+
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     tc::smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void ld8(uint32_t taddr, uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+}
+
+// Bounded wait on an mbarrier phase; on a timeout or another thread's abort: false.
+__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, const int* abort)
+{
+    const long long lim = (long long)tc::kDefaultSpin * 1000LL, t0 = clock64();
+    while (!tc::mbar_try_wait(bar, parity))
+        if (*reinterpret_cast<const volatile int*>(abort) || clock64() - t0 > lim) return false;
+    return true;
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+// e^{2 pi i (phi0 + u d)}, d = d_hi + d_lo with d_hi holding 12 significant bits (|u| < 4096).
+__device__ __forceinline__ float2 phasor_u(float phi0, float d_hi, float d_lo, int u)
+{
+    const float uf = (float)u;
+    float x = uf * d_hi;
+    x -= rintf(x);
+    float y = phi0 + x + uf * d_lo;
+    y -= rintf(y);
+    float s, c;
+    sincospif(2.0f * y, &s, &c);
+    return make_float2(c, s);
+}
+
+// Forward DFTs X[k] = sum_n x[n] e^{-2 pi i n k / L} in registers, in place, natural order.
+__device__ __forceinline__ void dft5(float2& x0, float2& x1, float2& x2, float2& x3, float2& x4)
+{
+    const float c1 = 0.30901699437494745f, s1 = 0.9510565162951535f;   // cos, sin 2 pi / 5
+    const float c2 = -0.8090169943749473f, s2 = 0.5877852522924732f;   // cos, sin 4 pi / 5
+    const float2 a1 = cadd(x1, x4), b1 = csub(x1, x4), a2 = cadd(x2, x3), b2 = csub(x2, x3);
+    const float2 p1 = make_float2(x0.x + c1 * a1.x + c2 * a2.x, x0.y + c1 * a1.y + c2 * a2.y);
+    const float2 p2 = make_float2(x0.x + c2 * a1.x + c1 * a2.x, x0.y + c2 * a1.y + c1 * a2.y);
+    // X1 = p1 - i (s1 b1 + s2 b2), X2 = p2 - i (s2 b1 - s1 b2); X4, X3 their mirrors
+    const float2 q1 = make_float2(s1 * b1.y + s2 * b2.y, -(s1 * b1.x + s2 * b2.x));
+    const float2 q2 = make_float2(s2 * b1.y - s1 * b2.y, -(s2 * b1.x - s1 * b2.x));
+    x0 = make_float2(x0.x + a1.x + a2.x, x0.y + a1.y + a2.y);
+    x1 = cadd(p1, q1);
+    x4 = csub(p1, q1);
+    x2 = cadd(p2, q2);
+    x3 = csub(p2, q2);
+}
+
+// Length 10 = 5 x 2: n = 2 a + b, k = k' + 5 k'': X = sum_b W10^{b k'} (-1)^{b k''} DFT5_a(x[2a+b])
+__device__ __forceinline__ void dft10(float2 (&x)[10])
+{
+    const float2 e0[5] = {x[0], x[2], x[4], x[6], x[8]};
+    float2 o[5] = {x[1], x[3], x[5], x[7], x[9]};
+    float2 e[5] = {e0[0], e0[1], e0[2], e0[3], e0[4]};
+    dft5(e[0], e[1], e[2], e[3], e[4]);
+    dft5(o[0], o[1], o[2], o[3], o[4]);
+    // W10^k' = e^{-2 pi i k' / 10}: cos / sin of 36 and 72 degrees
+    const float ca = 0.8090169943749475f, sa = 0.5877852522924731f, cb = 0.30901699437494745f,
+                sb = 0.9510565162951535f;
+    o[1] = cmul(o[1], make_float2(ca, -sa));
+    o[2] = cmul(o[2], make_float2(cb, -sb));
+    o[3] = cmul(o[3], make_float2(-cb, -sb));
+    o[4] = cmul(o[4], make_float2(-ca, -sa));
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        x[k] = cadd(e[k], o[k]);
+        x[k + 5] = csub(e[k], o[k]);
+    }
+}
+
+// Length 50 = 5 x 10: n = 10 a + b, k = k' + 5 k'': a length-5 DFT over a for each b, the
+// twiddles W50^{b k'} (table w[j] = W50^j), then a length-10 DFT over b for each k', in
+// place: bin k ends in slot 10 (k mod 5) + k / 5 (bin_slot).
+__device__ __forceinline__ void dft50(float2 (&x)[50], const float2* w)
+{
+#pragma unroll
+    for (int b = 0; b < 10; ++b) dft5(x[b], x[10 + b], x[20 + b], x[30 + b], x[40 + b]);
+#pragma unroll
+    for (int kp = 0; kp < 5; ++kp) {
+        float2 z[10];
+#pragma unroll
+        for (int b = 0; b < 10; ++b) z[b] = (b * kp == 0) ? x[10 * kp + b] : cmul(x[10 * kp + b], w[b * kp]);
+        dft10(z);
+#pragma unroll
+        for (int kk = 0; kk < 10; ++kk) x[10 * kp + kk] = z[kk];
+    }
+}
+
+template <int L>
+__host__ __device__ constexpr int bin_slot(int k)
+{
+    return L == 50 ? 10 * (k % 5) + k / 5 : k;
+}
+
+template <int L>
+__device__ __forceinline__ void dft_n2(float2 (&x)[L], const float2* w)
+{
+    static_assert(L == 10 || L == 50, "stage-B lengths");
+    if constexpr (L == 10) dft10(x);
+    else dft50(x, w);
+}
+
+
+// Issue the copies of an item's frames (2N bytes each, one bulk copy per frame with data; a
+// frame never straddles a data block, whose length is a multiple of N) and publish the
+// mask of frames copied (the others are read as zero: past the call's data or the slot, or a
+// zeroed block).  One thread.
+template <int N2, int G>
+__device__ __forceinline__ void issue_item(const FArgs& a, const F128Items& m, unsigned item, int8_t* stage,
+                                               uint64_t* bar, unsigned* mask_out)
+{
+    constexpr int N = kM * N2;
+    unsigned p;
+    long long f0;
+    int nv;
+    item_pos<G>(m, a.Kc, item, p, f0, nv);
+    const unsigned fpb = (unsigned)(a.bs / N);   // frames per data block
+    unsigned mask = 0;
+    long long srcs[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const long long f = f0 + g;
+        srcs[g] = 0;
+        if (g >= nv || f >= a.n_frames) continue;
+        const unsigned mf = (unsigned)(a.m_begin + f), blk = mf / fpb, fb = mf - blk * fpb;
+        if (a.flags != nullptr && a.flags[(long long)blk * a.n + p] != 0) continue;
+        srcs[g] = (((long long)blk * a.n + p) * (long long)a.bs + (long long)fb * N) * 2;
+        mask |= 1u << g;
+    }
+    // the mask is published before the arrive (release): a waiter that sees the phase
+    // complete (at once when no frame is copied) reads this item's mask
+    *mask_out = mask;
+    tc::mbar_arrive_expect_tx(bar, (uint32_t)(__popc(mask) * 2 * N));
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+        if (mask & (1u << g)) bulk_copy(stage + g * 2 * N, a.volt + srcs[g], 2u * N, bar);
+}
+
+// B-operand row of bin k2 of frame g: rows grouped by half of k2, then bin, then frame.
+template <int N2, int G>
+__host__ __device__ constexpr int z_row(int k2, int g)
+{
+    return (k2 >= N2 / 2 ? F128<N2, G>::HS : 0) + (k2 % (N2 / 2)) * G + g;
+}
+
+// Stage P of one task: the length-N2 DFT over n2 of sample n1 of frame g (two samples n1,
+// n1 + 1 with PAIR), the twiddles e^{-2 pi i n1 k2 / N}, FP16 rows of the B operand.
+template <int N2, int G, bool PAIR>
+__device__ __forceinline__ void stage_p_task(const int8_t* stage, bool live, int g, int n1, const float2* tw,
+                                             const float2* w2, unsigned char* xre, unsigned char* xim)
+{
+    using C = F128<N2, G>;
+    constexpr int N = C::N;
+    constexpr int NS = PAIR ? 2 : 1;
+    float2 x[NS][N2];
+    const int8_t* src = stage + g * 2 * N + 2 * n1;
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) {
+        if constexpr (PAIR) {
+            const char4 v = live ? *reinterpret_cast<const char4*>(src + 2 * kM * n2) : make_char4(0, 0, 0, 0);
+            x[0][n2] = make_float2((float)v.x, (float)v.y);
+            x[1][n2] = make_float2((float)v.z, (float)v.w);
+        } else {
+            const char2 v = live ? *reinterpret_cast<const char2*>(src + 2 * kM * n2) : make_char2(0, 0);
+            x[0][n2] = make_float2((float)v.x, (float)v.y);
+        }
+    }
+    float2 w[NS], E[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        dft_n2<N2>(x[s], w2);
+        w[s] = __ldg(&tw[n1 + s]);   // e^{-2 pi i (n1 + s) / N}
+        E[s] = w[s];
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) {
+        float2 z[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            z[s] = x[s][bin_slot<N2>(k2)];
+            if (k2 > 0) {
+                z[s] = cmul(z[s], E[s]);
+                E[s] = cmul(E[s], w[s]);
+            }
+        }
+        const uint32_t o = plain_off(z_row<N2, G>(k2, g), n1, C::LBO_X);
+        if constexpr (PAIR) {
+            const __half2 r2 = __floats2half2_rn(z[0].x, z[1].x), i2 = __floats2half2_rn(z[0].y, z[1].y);
+            *reinterpret_cast<__half2*>(xre + o) = r2;
+            *reinterpret_cast<__half2*>(xim + o) = i2;
+        } else {
+            *reinterpret_cast<__half*>(xre + o) = __float2half_rn(z[0].x);
+            *reinterpret_cast<__half*>(xim + o) = __float2half_rn(z[0].y);
+        }
+    }
+}
+
+// Frame terms of an item's frame g: operand slot and position, delay phasor terms (the FP64
+// delay polynomial or table, Sec. 4.3).
+template <int N2, int G>
+__device__ __forceinline__ F128Frame frame_terms(const FArgs& a, const F128Items& m, unsigned item, int g)
+{
+    constexpr int N = kM * N2;
+    unsigned p;
+    long long f0;
+    int nv;
+    item_pos<G>(m, a.Kc, item, p, f0, nv);
+    const long long f = f0 + g;
+    F128Frame fi;
+    const bool stored = g < nv && f < a.n_store;
+    fi.slot = stored ? f / a.Kc : -1;
+    fi.k = stored ? f % a.Kc : 0;
+    fi.delay = 0;
+    fi.phi0 = fi.d_hi = fi.d_lo = 0.0f;
+    fi.step = make_float2(1.0f, 0.0f);
+    if ((a.delay != nullptr || a.delay_tab != nullptr) && g < nv && f < a.n_frames) {
+        const double tau = frame_delay(a, (int)p, a.m_begin + f, N);
+        const double ph = a.nu * tau;
+        fi.phi0 = (float)(ph - floor(ph));
+        const double d = tau * a.fs_over_n;
+        const float dh = __uint_as_float(__float_as_uint((float)d) & 0xFFFFF000u);
+        fi.d_hi = dh;
+        fi.d_lo = (float)(d - (double)dh);
+        fi.delay = 1;
+        float sn, cs;
+        sincospif(2.0f * (float)(d - rint(d)), &sn, &cs);
+        fi.step = make_float2(cs, sn);
+    }
+    return fi;
+}
+
+template <int N2, int G>
+__global__ void __launch_bounds__(kT, 1) fstep_f128_kernel(const FArgs a, const F128Items m)
+{
+    using C = F128<N2, G>;
+    constexpr int N = C::N, H = C::H, HS = C::HS, NA = C::NA;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
+    unsigned char* f_re = sm;
+    unsigned char* f_im = f_re + kFPlane;
+    unsigned char* x_re = f_im + kFPlane;
+    unsigned char* x_im = x_re + C::XPLANE;
+    int8_t* stage = reinterpret_cast<int8_t*>(x_im + C::XPLANE);
+    float2* w2 = reinterpret_cast<float2*>(stage + C::STAGE);     // W_N2^j, j < N2 (64 slots)
+    F128Frame* frs = reinterpret_cast<F128Frame*>(w2 + 64);      // frame terms, 3 items x G
+    F128Shared& S = *reinterpret_cast<F128Shared*>(frs + 3 * G);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool worker = tid < kW, ctl = tid == kW;   // ctl: lane 0 of the control warp
+    int* status = a.status;
+
+    // ---- set-up: the 128-point DFT matrix (A: rows k1, K = n1), the B operand zeroed (its
+    // padding rows stay zero), the length-N2 twiddles, barriers, tensor memory
+    for (int e = tid; e < kM * kM; e += kT) {
+        const int k = e / kM, n = e % kM;
+        float s, c;
+        sincospif(-2.0f * (float)((k * n) % kM) / (float)kM, &s, &c);   // argument exact
+        const uint32_t o = plain_off(k, n, kLboF);
+        *reinterpret_cast<__half*>(f_re + o) = __float2half_rn(c);
+        *reinterpret_cast<__half*>(f_im + o) = __float2half_rn(s);
+    }
+    for (uint32_t i = tid; i < 2 * C::XPLANE / 16; i += kT) reinterpret_cast<uint4*>(x_re)[i] = make_uint4(0, 0, 0, 0);
+    for (int j = tid; j < N2; j += kT) w2[j] = __ldg(&a.tw[j * kM]);   // e^{-2 pi i 128 j / N} = W_N2^j
+    unsigned cur = blockIdx.x;
+    if (ctl) {
+        tc::mbar_init(&S.ld_bar, 1);
+        tc::mbar_init(&S.bar, 1);
+        tc::mbar_init(&S.drained, 1);
+        S.abort = 0;
+        tc::fence_mbar_init();
+        if (cur < m.n_items) issue_item<N2, G>(a, m, cur, stage, &S.ld_bar, &S.ld_mask);
+    }
+    if (tid >= kW && tid < kW + G && cur < m.n_items) frs[tid - kW] = frame_terms<N2, G>(a, m, cur, tid - kW);
+    if (warp == 0) {
+        tc::tmem_alloc(&S.tmem, 2 * kBufCols);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = S.tmem;
+    const int q = warp & 3, h = (warp >> 2) & 1;
+    const int k1 = 32 * q + lane;                  // a worker lane's bin row
+    uint32_t ld_par = 0, mma_par = 0;
+    unsigned n_copies = cur < m.n_items ? 1u : 0u;   // copies issued (control thread)
+    bool bad = false, stop = false, issued = false;
+
+    // stage P of an item (worker threads): its staged samples to the B operand
+    auto stage_p = [&]() {
+        if (!wait_phase(&S.ld_bar, ld_par, &S.abort)) {
+            bad = true;
+            S.abort = 1;   // lets the other threads' waits give up early
+            if (status) atomicOr(status, 2048);
+            return;
+        }
+        ld_par ^= 1u;
+        const unsigned mask = S.ld_mask;
+#pragma unroll
+        for (int i = 0; i < C::PER; ++i) {
+            const int t = tid + kW * i;
+            const int g = C::PAIR ? t / (kM / 2) : t / kM;
+            const int n1 = C::PAIR ? 2 * (t % (kM / 2)) : t % kM;
+            stage_p_task<N2, G, C::PAIR>(stage, (mask >> g) & 1u, g, n1, a.tw, w2, x_re, x_im);
+        }
+    };
+
+    // stage A of the item staged in the B operand, into accumulator buffer `buf` (control
+    // thread): re = Fr Zr - Fi Zi, im = Fr Zi + Fi Zr
+    auto stage_a = [&](int buf) {
+        const uint32_t id = tc::idesc(0, kM, NA, false), id_neg = tc::idesc(0, kM, NA, true);
+        const uint64_t ar = desc_plain(tc::smem_u32(f_re), kLboF), ai = desc_plain(tc::smem_u32(f_im), kLboF);
+        const uint64_t br = desc_plain(tc::smem_u32(x_re), C::LBO_X), bi = desc_plain(tc::smem_u32(x_im), C::LBO_X);
+        const uint32_t dre = tmem + (uint32_t)buf * kBufCols, dim = dre + NA;
+#pragma unroll
+        for (int ks = 0; ks < kM / 16; ++ks) {
+            const uint32_t acc = ks > 0 ? 1u : 0u;
+            const uint64_t oa = (uint64_t)((ks * 2u * kLboF) >> 4), ob = (uint64_t)((ks * 2u * C::LBO_X) >> 4);
+            tc::mma_f16(dre, ar + oa, br + ob, id, acc);
+            tc::mma_f16(dre, ai + oa, bi + ob, id_neg, 1u);
+            tc::mma_f16(dim, ar + oa, bi + ob, id, acc);
+            tc::mma_f16(dim, ai + oa, br + ob, id, 1u);
+        }
+        tc::mma_commit(&S.bar);
+        issued = true;
+    };
+
+    // stage E of an item from accumulator buffer `buf` (worker threads): bins
+    // k = N2 k1 + k2, k2 in this warp's half; phasor, gain, FP16 (re, im) of the G frames
+    // into the item's scratch tile Yt[c][g]
+    auto stage_e = [&](unsigned item, int buf, const F128Frame* fr) {
+        const bool lowk = k1 < kM / 2;                  // k < N/2: u = k; else u = k - N
+        const int k0 = N2 * k1 + H * h;                 // this lane's first bin
+        float2 P[G], st[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const F128Frame& fi = fr[g];
+            P[g] = fi.delay ? phasor_u(fi.phi0, fi.d_hi, fi.d_lo, lowk ? k0 : k0 - N) : make_float2(1.0f, 0.0f);
+            st[g] = fi.step;
+        }
+        uint32_t* T = static_cast<uint32_t*>(a.Yt) + (size_t)item * N * G;
+        const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * kBufCols + (uint32_t)(h * HS);
+#pragma unroll 1
+        for (int ch = 0; ch < C::NCH; ++ch) {
+            uint32_t vr[8], vi[8];
+            ld8(tb + (uint32_t)(8 * ch), vr);
+            ld8(tb + (uint32_t)(NA + 8 * ch), vi);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int b = 0; b < C::CB; ++b) {
+                const int kk = ch * C::CB + b;
+                if (kk >= H) break;
+                const int k = k0 + kk;
+                const int c = lowk ? k + N / 2 : k - N / 2;   // fftshift
+                const float gn = __ldg(&a.gain[c]);
+                uint32_t hv[G];
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    float2 y = make_float2(__uint_as_float(vr[b * G + g]), __uint_as_float(vi[b * G + g]));
+                    y = cmul(y, P[g]);
+                    P[g] = cmul(P[g], st[g]);
+                    const __half2 v = __floats2half2_rn(y.x * gn, y.y * gn);
+                    hv[g] = *reinterpret_cast<const uint32_t*>(&v);
+                }
+                uint32_t* t = T + (size_t)c * G;
+                if constexpr (G == 8) {
+                    reinterpret_cast<uint4*>(t)[0] = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                    reinterpret_cast<uint4*>(t)[1] = make_uint4(hv[4], hv[5], hv[6], hv[7]);
+                } else if constexpr (G == 4) {
+                    *reinterpret_cast<uint4*>(t) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                } else {
+                    *reinterpret_cast<uint2*>(t) = make_uint2(hv[0], hv[1]);
+                }
+            }
+        }
+    };
+
+    // ---- prologue: stage P and stage A of the first item, the copy of the second
+    if (worker && cur < m.n_items) stage_p();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // B operand: generic writes, MMA reads
+    tc::fence_before();
+    stop = __syncthreads_or(bad);
+    if (!stop && ctl && cur < m.n_items) {
+        tc::fence_after();
+        stage_a(0);
+        const unsigned nxt = cur + gridDim.x;
+        if (nxt < m.n_items) {
+            issue_item<N2, G>(a, m, nxt, stage, &S.ld_bar, &S.ld_mask);
+            ++n_copies;
+        }
+    }
+
+    // ---- steady state, item `cur` in buffer it & 1.  Workers: wait for its MMAs, stage P
+    // of the next item.  Control warp: the next item's frame terms.  Barrier.  Then the
+    // control thread issues stage A of the next item and the copy of the one after, and the
+    // workers run stage E of `cur`.
+    int it = 0;
+    for (; !stop && cur < m.n_items; cur += gridDim.x, ++it) {
+        const unsigned nxt = cur + gridDim.x;
+        if (worker) {
+            if (wait_phase(&S.bar, mma_par, &S.abort)) {
+                mma_par ^= 1u;
+            } else {
+                bad = true;
+                S.abort = 1;
+                if (status) atomicOr(status, 1024);
+            }
+            tc::fence_after();
+            if (!bad && nxt < m.n_items) stage_p();
+        } else if (lane < G && nxt < m.n_items) {
+            frs[((it + 1) % 3) * G + lane] = frame_terms<N2, G>(a, m, nxt, lane);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc::fence_before();
+        if ((stop = __syncthreads_or(bad))) break;
+        tc::fence_after();
+        if (ctl && nxt < m.n_items) {
+            stage_a((it + 1) & 1);
+            const unsigned nn = nxt + gridDim.x;
+            if (nn < m.n_items) {
+                issue_item<N2, G>(a, m, nn, stage, &S.ld_bar, &S.ld_mask);
+                ++n_copies;
+            }
+        }
+        if (worker) stage_e(cur, it & 1, frs + (it % 3) * G);
+    }
+
+    // ---- wind-down: after an abort the MMAs and the bulk copy in flight finish before the
+    // CTA releases its tensor memory and exits (at most one copy is ever in flight)
+    if (ctl && stop) {
+        if (issued) {
+            tc::mma_commit(&S.drained);
+            if (!tc::wait_bounded(&S.drained, 0u, tc::kDrainCycles) && status) atomicOr(status, tc::kDrainGaveUp);
+        }
+        if (n_copies > 0 && !tc::wait_bounded(&S.ld_bar, (n_copies - 1) & 1u, tc::kDrainCycles) && status)
+            atomicOr(status, tc::kDrainGaveUp);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after();
+        tc::tmem_dealloc(tmem, 2 * kBufCols);
+    }
+}
+
+// Transpose of one slot's scratch tiles Yt[p][group][c][g] (FP16 re, im) into the K-major
+// operand planes of that slot, Y[c][plane][p][Kpad]: a CTA takes one path, 32 channels and
+// up to 256 frames; it reads the groups' 32-channel runs (whole sectors), turns them in
+// shared memory and writes 64 rows of up to 512 contiguous bytes.
+constexpr int kTrC = 32, kTrK = 256;
+template <int G>
+__global__ void __launch_bounds__(256) f128_transpose_kernel(const uint32_t* __restrict__ Yt, __half* __restrict__ Y,
+                                                             int N, int n, long long Kpad, unsigned groups, int kn)
+{
+    __shared__ uint32_t S[kTrC][kTrK + 4];
+    const int cblocks = N / kTrC, kblocks = (kn + kTrK - 1) / kTrK;
+    const long long b = blockIdx.x;
+    const int kb = (int)(b % kblocks), cb = (int)((b / kblocks) % cblocks), p = (int)(b / ((long long)kblocks * cblocks));
+    const int c0 = cb * kTrC, k0 = kb * kTrK, kt = min(kTrK, kn - k0);
+    const int ng = (kt + G - 1) / G;   // groups in this tile
+    // read: group fg's words (c0 .. c0 + 31) x G, contiguous
+    for (int e = threadIdx.x; e < ng * kTrC * G; e += blockDim.x) {
+        const int fg = e / (kTrC * G), r = e % (kTrC * G), c = r / G, g = r % G;
+        S[c][fg * G + g] = __ldg(Yt + ((size_t)(p * (size_t)groups + k0 / G + fg) * N + c0) * G + r);
+    }
+    __syncthreads();
+    // write: row (c, plane), frames k0 .. k0 + kt - 1, 8 frames (16 bytes) per thread step
+    const long long ps = (long long)n * Kpad;
+    const int segs = (kt + 7) / 8;
+    for (int e = threadIdx.x; e < kTrC * 2 * segs; e += blockDim.x) {
+        const int j = e % segs, row = e / segs, c = row >> 1, plane = row & 1;
+        __half* dst = Y + ((long long)(c0 + c) * 2 * n + p) * Kpad + plane * ps + k0 + 8 * j;
+        const uint32_t* src = &S[c][8 * j];
+        const int sh = plane ? 16 : 0;
+        if (8 * j + 8 <= kt) {
+            uint32_t w[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                w[i] = ((src[2 * i] >> sh) & 0xFFFFu) | (((src[2 * i + 1] >> sh) & 0xFFFFu) << 16);
+            *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+        } else {
+            for (int i = 0; 8 * j + i < kt; ++i) dst[i] = __ushort_as_half((unsigned short)((src[i] >> sh) & 0xFFFFu));
+        }
+    }
+}
+
+template <int N2, int G>
+cudaError_t launch_f128(const FArgs& a, cudaStream_t s)
+{
+    using C = F128<N2, G>;
+    constexpr size_t smem = 2 * kFPlane + 2 * C::XPLANE + C::STAGE + sizeof(float2) * 64 +
+                            3 * G * sizeof(F128Frame) + sizeof(F128Shared) + 128;
+    static_assert(smem <= 227 * 1024, "shared memory");
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(fstep_f128_kernel<N2, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    if (a.bs % C::N != 0 || a.Kc <= 0 || a.m_begin + a.n_frames >= (1LL << 31)) return cudaErrorInvalidValue;
+    if (a.n_store <= 0 || a.n <= 0) return cudaSuccess;
+    const long long groups = (a.Kc + G - 1) / G, slots = (a.n_store + a.Kc - 1) / a.Kc;
+    const long long n_items = (long long)a.n * groups;
+    if (n_items >= (1LL << 31) || (size_t)a.Yt_bytes < fstep_f128_scratch_bytes(C::N, a.n, a.Kc))
+        return cudaErrorInvalidValue;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long grid = n_items < sms ? n_items : sms;
+    const long long slot_elems = (long long)C::N * 2 * a.n * a.Kpad;
+    for (long long sl = 0; sl < slots; ++sl) {
+        F128Items m;
+        m.n_items = (unsigned)n_items;
+        m.groups = (unsigned)groups;
+        m.slot = (unsigned)sl;
+        fstep_f128_kernel<N2, G><<<(unsigned)grid, kT, smem, s>>>(a, m);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const long long left = a.n_store - sl * a.Kc;
+        const int kn = (int)(left < a.Kc ? left : a.Kc);   // frames stored in this slot
+        const long long tblocks = (long long)a.n * (C::N / kTrC) * ((kn + kTrK - 1) / kTrK);
+        f128_transpose_kernel<G><<<(unsigned)tblocks, 256, 0, s>>>(
+            static_cast<const uint32_t*>(a.Yt), static_cast<__half*>(a.Y) + sl * slot_elems, C::N, a.n, a.Kpad,
+            (unsigned)groups, kn);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+bool fstep_f128_supported(int N) { return N == 1280 || N == 6400; }
+
+size_t fstep_f128_scratch_bytes(int N, int n, long long Kc)
+{
+    const int G = N == 1280 ? 8 : 2;
+    return (size_t)n * (size_t)((Kc + G - 1) / G) * G * (size_t)N * 4;
+}
+
+cudaError_t launch_fstep_f128(int N, const FArgs& a, cudaStream_t s)
+{
+    switch (N) {
+        case 1280: return launch_f128<10, 8>(a, s);
+        case 6400: return launch_f128<50, 2>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace mwax

@@ -193,10 +193,10 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t b
 }
 
 // Issue the copies of an item's frames (2N bytes each, one bulk copy per frame with data)
-// into the int8 stage and return the mask of frames copied (the others are read as zero:
+// into the int8 stage and publish the mask of frames copied (the others are read as zero:
 // past the call's data, or a zeroed block).  One thread.
 template <int N2, int G>
-__device__ __forceinline__ unsigned issue_item(const FArgs& a, long long item, unsigned char* stage, uint64_t* bar)
+__device__ __forceinline__ void issue_item(const FArgs& a, long long item, unsigned char* stage, uint64_t* bar, unsigned* mask_out)
 {
     constexpr int N = kN1 * N2;
     const long long n_fg = (a.n_store + G - 1) / G;
@@ -215,11 +215,13 @@ __device__ __forceinline__ unsigned issue_item(const FArgs& a, long long item, u
         srcs[g] = ((blk * a.n + p) * (long long)a.bs + off) * 2;
         mask |= 1u << g;
     }
+    // the mask is published before the arrive (release): a waiter that sees the phase
+    // complete (at once when no frame is copied) reads this item's mask
+    *mask_out = mask;
     tc::mbar_arrive_expect_tx(bar, (uint32_t)(__popc(mask) * 2 * N));
 #pragma unroll
     for (int g = 0; g < G; ++g)
         if (mask & (1u << g)) bulk_copy(stage + g * 2 * N, a.volt + srcs[g], 2u * N, bar);
-    return mask;
 }
 
 // Transpose one 8 x 8 block of staged int8 samples (rows n1 = 8 b1 + i, samples n2 = 8 b2 ..
@@ -317,7 +319,7 @@ __global__ void __launch_bounds__(kNT, CTAS) fstep_tc_kernel(const FArgs a, long
         tc::mbar_init(&S.ld_bar, 1);
         S.abort = 0;
         tc::fence_mbar_init();
-        if (item < n_items) S.ld_mask = issue_item<N2, G>(a, item, stage, &S.ld_bar);   // first item
+        if (item < n_items) issue_item<N2, G>(a, item, stage, &S.ld_bar, &S.ld_mask);   // first item
     }
     if (warp == 0) {
         tc::tmem_alloc(&S.tmem, C::TMEM);
@@ -407,7 +409,7 @@ __global__ void __launch_bounds__(kNT, CTAS) fstep_tc_kernel(const FArgs a, long
         {
             const long long next = item + gridDim.x;
             if (tid == 0 && next < n_items) {
-                S.ld_mask = issue_item<N2, G>(a, next, stage, &S.ld_bar);
+                issue_item<N2, G>(a, next, stage, &S.ld_bar, &S.ld_mask);
                 ld_pending = true;
             }
         }

@@ -72,6 +72,9 @@ struct FArgs {
     double fs_over_n;          // fs / N: frames per second
     int* status;               // device status word of the kernels with bounded waits (tensor-core
                                //   F-step), or nullptr
+    void* Yt;                  // 128-row tensor-core F-step: frame-major scratch of one slot
+                               //   (fstep_f128_scratch_bytes), or nullptr
+    long long Yt_bytes;
 };
 
 // Delay (s) of path p for frame m of the call (N samples from absolute sample m N): the
@@ -147,11 +150,17 @@ struct XLaunch {
 // variant 0: two-pass radix-32 kernel for N = 32..512 (generic elsewhere); 1: generic
 // Stockham passes for every N; 2: a tensor-core F-step where one is built (the direct DFT
 // product for N = 32, 64, 128, every output kind; the four-step DFT for FP16 output at
-// N = 1280 and 6400), variant 0 elsewhere.
+// N = 1280 and 6400), variant 0 elsewhere; 3: the 128-row tensor-core F-step (FP16 output,
+// N = 1280 and 6400), variant 2 elsewhere.
 cudaError_t launch_fstep(int N, int out_kind, const FArgs& a, cudaStream_t s, int variant);
 // The tensor-core four-step F-step (FP16 output), N = 1280 or 6400.
 bool fstep_tc_supported(int N);
 cudaError_t launch_fstep_tc(int N, const FArgs& a, cudaStream_t s);
+// The 128-row tensor-core F-step (FP16 output), N = 1280 or 6400; it needs the scratch
+// a.Yt of fstep_f128_scratch_bytes (one slot of frame-major spectra).
+bool fstep_f128_supported(int N);
+size_t fstep_f128_scratch_bytes(int N, int n, long long Kc);
+cudaError_t launch_fstep_f128(int N, const FArgs& a, cudaStream_t s);
 // The tensor-core direct-DFT F-step, N = 32, 64, 128 (FP32, FP16 or FP16 hi/lo output).
 bool fstep_dft_supported(int N, int out_kind);
 cudaError_t launch_fstep_dft(int N, int out_kind, const FArgs& a, cudaStream_t s);

@@ -1,6 +1,6 @@
 """Batched correlation (many coarse channels of mixed shapes and precisions in one
-schedule with one persistent X-step launch per round, CUDA-graph replay) and the
-autotuner.  Each plan's result in the batch must equal its result alone, bit for bit,
+schedule with one persistent X-step launch per round and tensor-core kernel mode,
+CUDA-graph replay) and the autotuner.  Each plan's result in the batch must equal its result alone, bit for bit,
 and that result must match the FP64 oracle at its precision's bar (integer mode bit-exact);
 the largest configuration shapes (512 tiles at N = 6400 and 1280) are checked on sampled
 outputs."""
@@ -27,6 +27,8 @@ MIX = [
     (30, 1, 1, 0.025, 64_000, mw.MWAX_INT8, 1024),
     (70, 6400, 50, 0.05, 64_000, mw.MWAX_FP8, 1024),
     (24, 128, 4, 0.05, 128_000, mw.MWAX_FP16X3, 16),
+    (16, 64, 2, 0.05, 64_000, mw.MWAX_FP16X3, 1024),   # two hi/lo plans: one launch, two jobs
+    (20, 1, 1, 0.05, 64_000, mw.MWAX_INT8, 1024),      # two integer-mode plans likewise
 ]
 
 

@@ -1,6 +1,7 @@
-"""The tensor-core F-steps (F-step variant 2) against the FP64 oracle: the four-step DFT
-(two DFT-matrix products on tcgen05, N = 80 x 80 = 6400 and 80 x 16 = 1280, FP16 operands
-out) at the FP16 and FP8 bars, and the direct DFT product (N = 32, 64, 128) in every float
+"""The tensor-core F-steps (F-step variants 2 and 3) against the FP64 oracle: the four-step
+DFT (two DFT-matrix products on tcgen05, N = 80 x 80 = 6400 and 80 x 16 = 1280, FP16
+operands out) and the 128-row F-step (stage A on tcgen05, a radix-5/2 stage B in registers,
+N = 128 x 50 and 128 x 10) at the FP16 and FP8 bars, and the direct DFT product (N = 32, 64, 128) in every float
 form at its bar: frame counts that leave ragged items and items that straddle two
 integrations or data blocks, per-path quadratic delays, zeroed data blocks, and the same
 plan with the CUDA-core F-step for comparison."""
@@ -39,9 +40,13 @@ def _run(desc, volt, delay, variant, flags=None):
     return res
 
 
+VARIANTS = [pytest.param(2, id="fourstep"), pytest.param(3, id="row128")]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("N,F,K", [(6400, 50, 203), (1280, 10, 203), (1280, 40, 250)])
-def test_tensor_core_fstep_parity(prec, N, F, K):
+def test_tensor_core_fstep_parity(variant, prec, N, F, K):
     # K frames per integration, 2 integrations: odd K leaves a frame pair (6400) split across
     # the integrations, K not a multiple of 8 leaves 8-frame groups (1280) that straddle them
     T = 6
@@ -49,7 +54,7 @@ def test_tensor_core_fstep_parity(prec, N, F, K):
     volt, delay = workload(0x7C + N + K, T, 2 * bs, block_samples=bs, delay="quadratic")
     desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=K * N / synth.FS, samples_per_call=2 * bs,
                        block_samples=bs, sky_freq_hz=synth.SKY_FREQ_HZ, precision=prec)
-    vis, w = _run(desc, volt, delay, 2)
+    vis, w = _run(desc, volt, delay, variant)
     ref, rw = oracle.correlate(oracle_desc(T, N, F, K * N / synth.FS, 2 * bs, block_samples=bs), volt, delay)
     assert np.array_equal(w, rw.astype(np.float32))
     err = parity_error(vis, ref, T)
@@ -60,7 +65,8 @@ def test_tensor_core_fstep_parity(prec, N, F, K):
     assert parity_error(vis, vis0.astype(np.complex128), T).max() <= TOL[prec]
 
 
-def test_tensor_core_fstep_zeroed_blocks_and_many_paths():
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_tensor_core_fstep_zeroed_blocks_and_many_paths(variant):
     # 40 tiles (80 paths: several path items per CTA), 10 blocks of 5 frames (N = 6400), a
     # seeded tenth of the blocks flagged as zeroed: the F-step reads them as zero
     T, N, F, K, bs = 40, 6400, 200, 50, 32_000
@@ -69,7 +75,7 @@ def test_tensor_core_fstep_zeroed_blocks_and_many_paths():
     flags = (np.random.default_rng(7).random((S // bs, 2 * T)) < 0.1).astype(np.uint8)
     desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=K * N / synth.FS, samples_per_call=S,
                        block_samples=bs, sky_freq_hz=synth.SKY_FREQ_HZ, precision=mw.MWAX_FP16)
-    vis, w = _run(desc, volt, delay, 2, flags=flags)
+    vis, w = _run(desc, volt, delay, variant, flags=flags)
     ref, rw = oracle.correlate_ext(oracle_desc(T, N, F, K * N / synth.FS, S, block_samples=bs),
                                    oracle.Ext(zero_flags=flags), volt, delay)
     assert np.allclose(w, rw, atol=1e-6)

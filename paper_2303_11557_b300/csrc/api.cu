@@ -391,6 +391,13 @@ mwax_status setup(mwax_plan& p)
         MWAX_CUDA(cudaMalloc(&p.Y, p.Y_bytes));
         MWAX_CUDA(cudaMemset(p.Y, 0, p.Y_bytes));
     }
+    // N = 1280, 6400 with FP16 operands out: the 128-row tensor-core F-step by default (the
+    // fastest measured there), with its one-slot scratch
+    if (fstep_f128_supported(p.N) && (p.prec == MWAX_FP16 || p.prec == MWAX_FP8)) {
+        const mwax_status st = ensure_f128_scratch(&p);
+        if (st != MWAX_OK) return st;
+        p.fvariant = 3;
+    }
 
     // twiddles e^{-2 pi i k / N}, rounded from FP64
     std::vector<float2> tw(p.N);

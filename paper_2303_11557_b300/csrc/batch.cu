@@ -211,7 +211,7 @@ mwax_status ensure_f128_scratch(mwax_plan* p)
     const size_t need = fstep_f128_scratch_bytes(p->N, p->n, p->Kc);
     if (p->Yt_bytes >= need) return MWAX_OK;
     BCUDA(cudaSetDevice(p->device));
-    BCUDA(cudaStreamSynchronize(p->stream));
+    if (p->stream) BCUDA(cudaStreamSynchronize(p->stream));
     cudaFree(p->Yt);
     p->Yt = nullptr;
     p->Yt_bytes = 0;

@@ -7,8 +7,8 @@
 //   stage A (tcgen05, both operands in shared memory, M = 128 bins k1, K = 128 samples n1):
 //       X[N2 k1 + k2] = sum_n1 e^{-2 pi i k1 n1 / 128} Z[n1, k2]
 //   stage E (CUDA cores, one lane per k1): the delay phasor (Sec. 4.3), the channel gain,
-//       FP16 (re, im) into a frame-major scratch tile of the item, Yt[p][group][c][g],
-//       c = fftshift(k): one 2 MB page per item, whole sectors;
+//       FP16 (re, im) into a shared-memory tile, then copied whole (coalesced) into the
+//       item's frame-major scratch tile Yt[p][group][c][g], c = fftshift(k);
 //   transpose (one launch per slot after the F-step's): Yt to the K-major operand planes
 //       Y[slot][c][plane][p][Kpad], a warp writing 64 contiguous bytes of a row at a time.
 // Writing the K-major rows straight from the bins (each item holds only G frames, so each
@@ -28,6 +28,8 @@
 // word); loop exits are taken by all threads at that barrier.
 #include "mwax_internal.cuh"
 #include "tc_ptx.cuh"
+
+#include <algorithm>
 
 namespace mwax {
 namespace {
@@ -60,6 +62,10 @@ struct F128 {
     static constexpr int PER = TASKS / kW;
     static constexpr int CB = 8 / G;                          // bins per 8-column load
     static constexpr int NCH = (H + CB - 1) / CB;             // loads per half and plane
+    // stage E's tile in shared memory: channel c's G words at c * TS (16-byte rows padded so
+    // that the lanes of a store phase, N2 channels apart, spread over the banks)
+    static constexpr int TS = G == 8 ? 12 : G;
+    static constexpr uint32_t TILE = (uint32_t)N * TS * 4;
     static_assert((NCH * CB - 1) * G + G <= HS, "loads stay inside the half's columns");
 };
 
@@ -373,7 +379,8 @@ __global__ void __launch_bounds__(kT, 1) fstep_f128_kernel(const FArgs a, const 
     unsigned char* x_re = f_im + kFPlane;
     unsigned char* x_im = x_re + C::XPLANE;
     int8_t* stage = reinterpret_cast<int8_t*>(x_im + C::XPLANE);
-    float2* w2 = reinterpret_cast<float2*>(stage + C::STAGE);     // W_N2^j, j < N2 (64 slots)
+    uint32_t* T = reinterpret_cast<uint32_t*>(stage + C::STAGE);  // stage E tile [c][TS]
+    float2* w2 = reinterpret_cast<float2*>(stage + C::STAGE + C::TILE);   // W_N2^j, j < N2 (64 slots)
     F128Frame* frs = reinterpret_cast<F128Frame*>(w2 + 64);      // frame terms, 3 items x G
     F128Shared& S = *reinterpret_cast<F128Shared*>(frs + 3 * G);
 
@@ -458,8 +465,8 @@ __global__ void __launch_bounds__(kT, 1) fstep_f128_kernel(const FArgs a, const 
 
     // stage E of an item from accumulator buffer `buf` (worker threads): bins
     // k = N2 k1 + k2, k2 in this warp's half; phasor, gain, FP16 (re, im) of the G frames
-    // into the item's scratch tile Yt[c][g]
-    auto stage_e = [&](unsigned item, int buf, const F128Frame* fr) {
+    // into the shared-memory tile T
+    auto stage_e = [&](int buf, const F128Frame* fr) {
         const bool lowk = k1 < kM / 2;                  // k < N/2: u = k; else u = k - N
         const int k0 = N2 * k1 + H * h;                 // this lane's first bin
         float2 P[G], st[G];
@@ -469,21 +476,35 @@ __global__ void __launch_bounds__(kT, 1) fstep_f128_kernel(const FArgs a, const 
             P[g] = fi.delay ? phasor_u(fi.phi0, fi.d_hi, fi.d_lo, lowk ? k0 : k0 - N) : make_float2(1.0f, 0.0f);
             st[g] = fi.step;
         }
-        uint32_t* T = static_cast<uint32_t*>(a.Yt) + (size_t)item * N * G;
         const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * kBufCols + (uint32_t)(h * HS);
-#pragma unroll 1
+        // chunk ch + 1's tensor-memory columns and gains load while chunk ch is processed
+        uint32_t vr[8], vi[8], nr[8], ni[8];
+        float gc[C::CB], gnx[C::CB];
+        auto gains = [&](int ch, float (&gv)[C::CB]) {
+#pragma unroll
+            for (int b = 0; b < C::CB; ++b) {
+                const int k = k0 + min(ch * C::CB + b, H - 1);
+                gv[b] = __ldg(&a.gain[lowk ? k + N / 2 : k - N / 2]);
+            }
+        };
+        ld8(tb, vr);
+        ld8(tb + (uint32_t)NA, vi);
+        gains(0, gc);
+        tc::tmem_wait_ld();
+#pragma unroll
         for (int ch = 0; ch < C::NCH; ++ch) {
-            uint32_t vr[8], vi[8];
-            ld8(tb + (uint32_t)(8 * ch), vr);
-            ld8(tb + (uint32_t)(NA + 8 * ch), vi);
-            tc::tmem_wait_ld();
+            if (ch + 1 < C::NCH) {
+                ld8(tb + (uint32_t)(8 * (ch + 1)), nr);
+                ld8(tb + (uint32_t)(NA + 8 * (ch + 1)), ni);
+                gains(ch + 1, gnx);
+            }
 #pragma unroll
             for (int b = 0; b < C::CB; ++b) {
                 const int kk = ch * C::CB + b;
                 if (kk >= H) break;
                 const int k = k0 + kk;
                 const int c = lowk ? k + N / 2 : k - N / 2;   // fftshift
-                const float gn = __ldg(&a.gain[c]);
+                const float gn = gc[b];
                 uint32_t hv[G];
 #pragma unroll
                 for (int g = 0; g < G; ++g) {
@@ -493,7 +514,7 @@ __global__ void __launch_bounds__(kT, 1) fstep_f128_kernel(const FArgs a, const 
                     const __half2 v = __floats2half2_rn(y.x * gn, y.y * gn);
                     hv[g] = *reinterpret_cast<const uint32_t*>(&v);
                 }
-                uint32_t* t = T + (size_t)c * G;
+                uint32_t* t = T + c * C::TS;
                 if constexpr (G == 8) {
                     reinterpret_cast<uint4*>(t)[0] = make_uint4(hv[0], hv[1], hv[2], hv[3]);
                     reinterpret_cast<uint4*>(t)[1] = make_uint4(hv[4], hv[5], hv[6], hv[7]);
@@ -503,6 +524,35 @@ __global__ void __launch_bounds__(kT, 1) fstep_f128_kernel(const FArgs a, const 
                     *reinterpret_cast<uint2*>(t) = make_uint2(hv[0], hv[1]);
                 }
             }
+            if (ch + 1 < C::NCH) {
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    vr[i] = nr[i];
+                    vi[i] = ni[i];
+                }
+#pragma unroll
+                for (int b = 0; b < C::CB; ++b) gc[b] = gnx[b];
+            }
+        }
+    };
+
+    // the tile of an item into its scratch tile Yt[c][g] (worker threads; 16-byte copies,
+    // a warp writing 512 contiguous bytes)
+    auto copy_out = [&](unsigned item) {
+        uint4* dst = reinterpret_cast<uint4*>(static_cast<uint32_t*>(a.Yt) + (size_t)item * N * G);
+        for (int q = tid; q < N * G / 4; q += kW) {
+            const int c = q / (G / 4 > 0 ? G / 4 : 1);
+            uint4 v;
+            if constexpr (G >= 4) {
+                v = *reinterpret_cast<const uint4*>(T + c * C::TS + 4 * (q % (G / 4)));
+            } else {
+                // G = 2: two channels per 16 bytes
+                const uint2 lo = *reinterpret_cast<const uint2*>(T + (2 * q) * C::TS);
+                const uint2 hi = *reinterpret_cast<const uint2*>(T + (2 * q + 1) * C::TS);
+                v = make_uint4(lo.x, lo.y, hi.x, hi.y);
+            }
+            dst[q] = v;
         }
     };
 
@@ -553,7 +603,11 @@ __global__ void __launch_bounds__(kT, 1) fstep_f128_kernel(const FArgs a, const 
                 ++n_copies;
             }
         }
-        if (worker) stage_e(cur, it & 1, frs + (it % 3) * G);
+        if (worker) {
+            stage_e(it & 1, frs + (it % 3) * G);
+            asm volatile("bar.sync 1, %0;" ::"n"(kW) : "memory");   // the worker warps' tile complete
+            copy_out(cur);
+        }
     }
 
     // ---- wind-down: after an abort the MMAs and the bulk copy in flight finish before the
@@ -575,24 +629,39 @@ __global__ void __launch_bounds__(kT, 1) fstep_f128_kernel(const FArgs a, const 
 }
 
 // Transpose of one slot's scratch tiles Yt[p][group][c][g] (FP16 re, im) into the K-major
-// operand planes of that slot, Y[c][plane][p][Kpad]: a CTA takes one path, 32 channels and
-// up to 256 frames; it reads the groups' 32-channel runs (whole sectors), turns them in
-// shared memory and writes 64 rows of up to 512 contiguous bytes.
-constexpr int kTrC = 32, kTrK = 256;
-template <int G>
+// operand planes of that slot, Y[c][plane][p][Kpad]: a CTA takes one path, kTrC channels
+// and up to 8192 / kTrC frames; it reads the groups' kTrC-channel runs (whole sectors),
+// turns them in shared memory and writes 2 kTrC rows of up to 16384 / kTrC bytes.  (Run
+// beside the next slot's F-step on a second stream it gained little: the F-step's CTAs
+// fill the SMs, and a transpose thin enough to fit beside them is latency-bound.)
+constexpr int kTrWords = 8192;   // 32 KB tile
+template <int G, int kTrC>
 __global__ void __launch_bounds__(256) f128_transpose_kernel(const uint32_t* __restrict__ Yt, __half* __restrict__ Y,
                                                              int N, int n, long long Kpad, unsigned groups, int kn)
 {
-    __shared__ uint32_t S[kTrC][kTrK + 4];
+    constexpr int kTrK = kTrWords / kTrC;
+    __shared__ __align__(16) uint32_t S[kTrC][kTrK + 4];
     const int cblocks = N / kTrC, kblocks = (kn + kTrK - 1) / kTrK;
-    const long long b = blockIdx.x;
+    const long long tiles = (long long)n * cblocks * kblocks;
+    for (long long b = blockIdx.x; b < tiles; b += gridDim.x) {
     const int kb = (int)(b % kblocks), cb = (int)((b / kblocks) % cblocks), p = (int)(b / ((long long)kblocks * cblocks));
     const int c0 = cb * kTrC, k0 = kb * kTrK, kt = min(kTrK, kn - k0);
     const int ng = (kt + G - 1) / G;   // groups in this tile
-    // read: group fg's words (c0 .. c0 + 31) x G, contiguous
-    for (int e = threadIdx.x; e < ng * kTrC * G; e += blockDim.x) {
-        const int fg = e / (kTrC * G), r = e % (kTrC * G), c = r / G, g = r % G;
-        S[c][fg * G + g] = __ldg(Yt + ((size_t)(p * (size_t)groups + k0 / G + fg) * N + c0) * G + r);
+    // read: group fg's words (c0 .. c0 + kTrC - 1) x G are contiguous 16-byte chunks
+    constexpr int CH = kTrC * G / 4;
+    const uint4* src = reinterpret_cast<const uint4*>(Yt + ((size_t)p * groups + k0 / G) * N * G + (size_t)c0 * G);
+#pragma unroll 4
+    for (int e = threadIdx.x; e < ng * CH; e += blockDim.x) {
+        const int fg = e / CH, r4 = e % CH;
+        const uint4 v = __ldg(src + (size_t)fg * (N * G / 4) + r4);
+        if constexpr (G >= 4) {
+            const int c = 4 * r4 / G, g = 4 * r4 % G;
+            *reinterpret_cast<uint4*>(&S[c][fg * G + g]) = v;
+        } else {
+            const int c = 2 * r4;   // G = 2: two channels per chunk
+            *reinterpret_cast<uint2*>(&S[c][fg * 2]) = make_uint2(v.x, v.y);
+            *reinterpret_cast<uint2*>(&S[c + 1][fg * 2]) = make_uint2(v.z, v.w);
+        }
     }
     __syncthreads();
     // write: row (c, plane), frames k0 .. k0 + kt - 1, 8 frames (16 bytes) per thread step
@@ -601,17 +670,18 @@ __global__ void __launch_bounds__(256) f128_transpose_kernel(const uint32_t* __r
     for (int e = threadIdx.x; e < kTrC * 2 * segs; e += blockDim.x) {
         const int j = e % segs, row = e / segs, c = row >> 1, plane = row & 1;
         __half* dst = Y + ((long long)(c0 + c) * 2 * n + p) * Kpad + plane * ps + k0 + 8 * j;
-        const uint32_t* src = &S[c][8 * j];
         const int sh = plane ? 16 : 0;
         if (8 * j + 8 <= kt) {
-            uint32_t w[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                w[i] = ((src[2 * i] >> sh) & 0xFFFFu) | (((src[2 * i + 1] >> sh) & 0xFFFFu) << 16);
-            *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+            const uint4 a0 = *reinterpret_cast<const uint4*>(&S[c][8 * j]);
+            const uint4 a1 = *reinterpret_cast<const uint4*>(&S[c][8 * j + 4]);
+            const uint32_t sel = plane ? 0x7632u : 0x5410u;   // the re (low) or im (high) halves
+            *reinterpret_cast<uint4*>(dst) = make_uint4(__byte_perm(a0.x, a0.y, sel), __byte_perm(a0.z, a0.w, sel),
+                                                        __byte_perm(a1.x, a1.y, sel), __byte_perm(a1.z, a1.w, sel));
         } else {
-            for (int i = 0; 8 * j + i < kt; ++i) dst[i] = __ushort_as_half((unsigned short)((src[i] >> sh) & 0xFFFFu));
+            for (int i = 0; 8 * j + i < kt; ++i) dst[i] = __ushort_as_half((unsigned short)((S[c][8 * j + i] >> sh) & 0xFFFFu));
         }
+    }
+    __syncthreads();   // S is refilled by the next tile
     }
 }
 
@@ -619,7 +689,7 @@ template <int N2, int G>
 cudaError_t launch_f128(const FArgs& a, cudaStream_t s)
 {
     using C = F128<N2, G>;
-    constexpr size_t smem = 2 * kFPlane + 2 * C::XPLANE + C::STAGE + sizeof(float2) * 64 +
+    constexpr size_t smem = 2 * kFPlane + 2 * C::XPLANE + C::STAGE + C::TILE + sizeof(float2) * 64 +
                             3 * G * sizeof(F128Frame) + sizeof(F128Shared) + 128;
     static_assert(smem <= 227 * 1024, "shared memory");
     static bool attr_done = false;
@@ -650,8 +720,9 @@ cudaError_t launch_f128(const FArgs& a, cudaStream_t s)
         if (e != cudaSuccess) return e;
         const long long left = a.n_store - sl * a.Kc;
         const int kn = (int)(left < a.Kc ? left : a.Kc);   // frames stored in this slot
-        const long long tblocks = (long long)a.n * (C::N / kTrC) * ((kn + kTrK - 1) / kTrK);
-        f128_transpose_kernel<G><<<(unsigned)tblocks, 256, 0, s>>>(
+        constexpr int TRC = G >= 8 ? 32 : 64, TRK = kTrWords / TRC;   // channels, frames per transpose tile
+        const long long tiles = (long long)a.n * (C::N / TRC) * ((kn + TRK - 1) / TRK);
+        f128_transpose_kernel<G, TRC><<<(unsigned)tiles, 256, 0, s>>>(
             static_cast<const uint32_t*>(a.Yt), static_cast<__half*>(a.Y) + sl * slot_elems, C::N, a.n, a.Kpad,
             (unsigned)groups, kn);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

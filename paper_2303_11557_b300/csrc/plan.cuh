@@ -52,7 +52,8 @@ struct mwax_plan {
     int tile = 64;               // paths per tile side of the X-step
     int run_len = 0;             // output channels per X work item (autotuned)
     int window = 256;            // tensor-core tile column window (autotuned: 128 or 256)
-    int fvariant = 0;            // F-step kernel: 0 = two-pass radix-32 where built, 1 = generic
+    int fvariant = 0;            // F-step kernel: 0 = two-pass radix-32 where built, 1 = generic,
+                                 //   2 = tensor-core DFT products, 3 = 128-row tensor-core
     CUtensorMap tmap;            // operand planes, for the tcgen05 X-step
 
     // host copies of the tables (work-item costs) and the tcgen05 item lists by slot count

@@ -83,7 +83,7 @@ def test_autotune_keeps_parity():
         d = torch.from_numpy(delay).cuda()
         o = mw.empty_output(p)
         best = mw.mwax_plan_autotune(p, v, d, o)
-        assert best.ms > 0 and best.fstep_variant in (0, 1) and best.window in (128, 256)
+        assert best.ms > 0 and best.fstep_variant in (0, 1, 2) and best.window in (128, 256)
         got = mw.mwax_plan_get_tuning(p)
         assert (got.fstep_variant, got.run_len, got.window) == (best.fstep_variant, best.run_len, best.window)
         o.fill_(0)
@@ -93,7 +93,7 @@ def test_autotune_keeps_parity():
         ref, _ = oracle.correlate(oracle_desc(T, N, F, t, S), volt, delay)
         assert parity_error(vis.cpu().numpy(), ref, T).max() <= tol
         # every candidate choice is correct, not just the fastest
-        for fv in (0, 1):
+        for fv in (0, 1, 2):
             for w in (128, 256):
                 for rl in (1, 3, 32):
                     mw.mwax_plan_set_tuning(p, mw.Tuning(fv, rl, w, 0.0))

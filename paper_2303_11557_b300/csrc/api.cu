@@ -81,6 +81,8 @@ void free_plan(mwax_plan* p)
     cudaFree(p->gain);
     cudaFree(p->chan_group);
     cudaFree(p->amax);
+    cudaFree(p->gain8);
+    cudaFree(p->amax_static);
     cudaFree(p->runs);
     cudaFree(p->tiles);
     cudaFree(p->status);
@@ -325,11 +327,32 @@ constexpr double kMaxPassband = 2.0;
 
 // The F-step's per-channel gains as the device holds them: sqrt(w_c) x passband gain x the
 // power-of-two pre-scale of the FP16 operand forms (1 otherwise), one multiply per value.
+//
+// FP8 form: the F-step writes e4m3 directly with a static scale per channel group g,
+// s_g = A_g / 448 with A_g = 181.02 N max_{c in g} gain_c (pre-scaled), the bound on any
+// |Re X|, |Im X| of the group: no value saturates, and the values of an ordinary sky sit
+// well inside e4m3's normal range, whose relative step (2^-3) is the same at any scale.
 mwax_status upload_gains(mwax_plan& p)
 {
     std::vector<float> g(p.N);
     for (int c = 0; c < p.N; ++c) g[c] = p.h_gain[c] * p.out_scale;   // exact: a power of two
     MWAX_CUDA(cudaMemcpy(p.gain, g.data(), sizeof(float) * p.N, cudaMemcpyHostToDevice));
+    if (p.prec == MWAX_FP8) {
+        std::vector<float> g8(p.N, 0.0f), a8(p.n_groups, 448.0f);
+        for (int gi = 0; gi < p.n_groups; ++gi) {
+            const Group& gr = p.h_groups[gi];
+            double gmax = 0.0;
+            for (int c = gr.c0; c < gr.c1; ++c) gmax = std::max(gmax, (double)g[c]);
+            if (gmax <= 0.0) continue;
+            const double A = 181.02 * p.N * gmax;
+            a8[gi] = (float)A;
+            for (int c = gr.c0; c < gr.c1; ++c) g8[c] = (float)((double)g[c] * 448.0 / A);
+        }
+        if (!p.gain8) MWAX_CUDA(cudaMalloc(&p.gain8, sizeof(float) * p.N));
+        if (!p.amax_static) MWAX_CUDA(cudaMalloc(&p.amax_static, sizeof(float) * std::max(1, p.n_groups)));
+        MWAX_CUDA(cudaMemcpy(p.gain8, g8.data(), sizeof(float) * p.N, cudaMemcpyHostToDevice));
+        MWAX_CUDA(cudaMemcpy(p.amax_static, a8.data(), sizeof(float) * p.n_groups, cudaMemcpyHostToDevice));
+    }
     return MWAX_OK;
 }
 
@@ -763,8 +786,14 @@ mwax_status enqueue_fstep(mwax_plan* p, const LaunchGroup& g, const int8_t* volt
     fa.status = p->status;
     fa.Yt = p->Yt;
     fa.Yt_bytes = (long long)p->Yt_bytes;
-    if (p->prec == MWAX_FP8) {
-        // FP16 operands, then per path and channel group the max magnitude, then e4m3
+    if (p->prec == MWAX_FP8 && p->fvariant != 2) {
+        // e4m3 straight from the F-step, with the plan's static per-group scales
+        fa.gain = p->gain8;
+        MWAX_CUDA(timed(p, 1, s, [&] { return launch_fstep(p->N, FOUT_E4M3, fa, s, p->fvariant); }));
+        MWAX_CUDA(timed(p, 1, s, [&] { return launch_fill_amax(p->amax, p->amax_static, p->n_groups, p->n, g.nslots, s); }));
+    } else if (p->prec == MWAX_FP8) {
+        // the tensor-core DFT-product F-steps write FP16: then per path and channel group
+        // the max magnitude, then e4m3
         fa.Y = p->Y16;
         MWAX_CUDA(timed(p, 1, s, [&] { return launch_fstep(p->N, FOUT_F16, fa, s, p->fvariant); }));
         MWAX_CUDA(timed(p, 1, s, [&] {

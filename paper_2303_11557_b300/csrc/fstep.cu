@@ -264,6 +264,11 @@ struct Store {
             Y[at + plane_stride] = hi;
             Y[at + lo] = __float2half_rn(xr - __half2float(hr));
             Y[at + plane_stride + lo] = __float2half_rn(xi - __half2float(hi));
+        } else if (OUTK == FOUT_E4M3) {
+            uint8_t* Y = static_cast<uint8_t*>(a.Y);
+            const uint32_t q = e4m3x2(v);
+            Y[at] = (uint8_t)(q & 0xFFu);
+            Y[at + plane_stride] = (uint8_t)(q >> 8);
         } else {
             __half* Y = static_cast<__half*>(a.Y);
             Y[at] = __float2half_rn(v.x);
@@ -304,6 +309,18 @@ __device__ __forceinline__ void store_frame_pair(const FArgs& a, long long at, l
         } else if (live) {
             Y[at] = __low2half(h2);
             Y[at + ps] = __high2half(h2);
+        }
+    } else if (OUTK == FOUT_E4M3) {
+        const uint32_t q = e4m3x2(y);   // (re, im) bytes
+        const uint32_t other = __shfl_xor_sync(0xffffffffu, q, 1);
+        uint8_t* Y = static_cast<uint8_t*>(a.Y);
+        if (paired) {
+            // even lane: (frame 0 re, frame 1 re); odd lane: (frame 0 im, frame 1 im)
+            if (odd) *reinterpret_cast<uint16_t*>(Y + at - 1 + ps) = (uint16_t)__byte_perm(other, q, 0x0051);
+            else *reinterpret_cast<uint16_t*>(Y + at) = (uint16_t)__byte_perm(q, other, 0x0040);
+        } else if (live) {
+            Y[at] = (uint8_t)(q & 0xFFu);
+            Y[at + ps] = (uint8_t)(q >> 8);
         }
     } else {   // FP16 hi/lo pairs: lo values half a row further on
         const float xr = y.x, xi = y.y;
@@ -349,6 +366,10 @@ __device__ __forceinline__ void store_two_frames(const FArgs& a, long long at, l
         __half* Y = static_cast<__half*>(a.Y);
         *reinterpret_cast<__half2*>(Y + at) = __floats2half2_rn(y0.x, y1.x);
         *reinterpret_cast<__half2*>(Y + at + ps) = __floats2half2_rn(y0.y, y1.y);
+    } else if (OUTK == FOUT_E4M3) {
+        uint8_t* Y = static_cast<uint8_t*>(a.Y);
+        *reinterpret_cast<uint16_t*>(Y + at) = (uint16_t)e4m3x2(make_float2(y0.x, y1.x));
+        *reinterpret_cast<uint16_t*>(Y + at + ps) = (uint16_t)e4m3x2(make_float2(y0.y, y1.y));
     } else {
         __half* Y = static_cast<__half*>(a.Y);
         const long long lo = a.Kpad >> 1;
@@ -1151,7 +1172,8 @@ cudaError_t launch_fstep(int N, int out_kind, const FArgs& a_in, cudaStream_t s,
     a.frame_dt = (double)N / a.fs;
     a.fs_over_n = a.fs / (double)N;
     if (variant == 3) {
-        if (out_kind == FOUT_F16 && fstep_f128_supported(N) && a.Yt) return launch_fstep_f128(N, a, s);
+        if ((out_kind == FOUT_F16 || out_kind == FOUT_E4M3) && fstep_f128_supported(N) && a.Yt)
+            return launch_fstep_f128(N, out_kind, a, s);
         variant = 2;
     }
     if (variant == 2) {
@@ -1163,6 +1185,7 @@ cudaError_t launch_fstep(int N, int out_kind, const FArgs& a_in, cudaStream_t s,
         case FOUT_F32: return launch_kind<FOUT_F32>(N, a, s, variant);
         case FOUT_F16: return launch_kind<FOUT_F16>(N, a, s, variant);
         case FOUT_F16X3: return launch_kind<FOUT_F16X3>(N, a, s, variant);
+        case FOUT_E4M3: return launch_kind<FOUT_E4M3>(N, a, s, variant);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1209,6 +1232,23 @@ __global__ void __launch_bounds__(256) amax_e4m3_kernel(const __half* __restrict
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (lane == 0) amax[(slot * n_groups + g) * (long long)n + p] = m;
     }
+}
+
+__global__ void __launch_bounds__(256) fill_amax_kernel(float* __restrict__ amax, const float* __restrict__ amax_static,
+                                                        int n_groups, int n, long long total)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
+        amax[i] = __ldg(&amax_static[(i / n) % n_groups]);
+}
+
+cudaError_t launch_fill_amax(float* amax, const float* amax_static, int n_groups, int n, long long slots,
+                             cudaStream_t s)
+{
+    const long long total = slots * n_groups * (long long)n;
+    if (total <= 0) return cudaSuccess;
+    fill_amax_kernel<<<(unsigned)std::min<long long>((total + 255) / 256, 148LL * 8), 256, 0, s>>>(amax, amax_static,
+                                                                                                  n_groups, n, total);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_amax_e4m3(const __half* Y16, float* amax, const int* chan_group, const Group* groups, int n_groups,

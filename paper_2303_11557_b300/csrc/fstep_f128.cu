@@ -1,6 +1,6 @@
 // Tensor-core F-step for the long fine-channel FFTs with full 128-row MMAs (Sec. 2.5.1:
-// N = 128 N2, here 1280 = 128 x 10 and 6400 = 128 x 50), FP16 operands out (the FP16 and
-// FP8 forms).  Four-step decomposition with the 128-point DFT on the tensor cores:
+// N = 128 N2, here 1280 = 128 x 10 and 6400 = 128 x 50), FP16 or e4m3 operands out (the
+// FP16 and FP8 forms).  Four-step decomposition with the 128-point DFT on the tensor cores:
 //   sample n = n1 + 128 n2, bin k = N2 k1 + k2,
 //   stage P (CUDA cores, one thread per n1 of a frame, in registers):
 //       Z[n1, k2] = e^{-2 pi i n1 k2 / N} sum_n2 x[n1 + 128 n2] e^{-2 pi i n2 k2 / N2}
@@ -10,7 +10,7 @@
 //       FP16 (re, im) into a shared-memory tile, then copied whole (coalesced) into the
 //       item's frame-major scratch tile Yt[p][group][c][g], c = fftshift(k);
 //   transpose (one launch per slot after the F-step's): Yt to the K-major operand planes
-//       Y[slot][c][plane][p][Kpad], a warp writing 64 contiguous bytes of a row at a time.
+//       Y[slot][c][plane][p][Kpad] (FP16, or e4m3 when the gains carry the FP8 scales).
 // Writing the K-major rows straight from the bins (each item holds only G frames, so each
 // lane's store lands in its own row and 2 MB page) measured several times slower than
 // the whole F-step: the address translation of scattered rows, not DRAM, bounds it.
@@ -635,8 +635,8 @@ __global__ void __launch_bounds__(kT, 1) fstep_f128_kernel(const FArgs a, const 
 // beside the next slot's F-step on a second stream it gained little: the F-step's CTAs
 // fill the SMs, and a transpose thin enough to fit beside them is latency-bound.)
 constexpr int kTrWords = 8192;   // 32 KB tile
-template <int G, int kTrC>
-__global__ void __launch_bounds__(256) f128_transpose_kernel(const uint32_t* __restrict__ Yt, __half* __restrict__ Y,
+template <int G, int kTrC, bool E4M3>
+__global__ void __launch_bounds__(256) f128_transpose_kernel(const uint32_t* __restrict__ Yt, void* __restrict__ Yv,
                                                              int N, int n, long long Kpad, unsigned groups, int kn)
 {
     constexpr int kTrK = kTrWords / kTrC;
@@ -669,23 +669,46 @@ __global__ void __launch_bounds__(256) f128_transpose_kernel(const uint32_t* __r
     const int segs = (kt + 7) / 8;
     for (int e = threadIdx.x; e < kTrC * 2 * segs; e += blockDim.x) {
         const int j = e % segs, row = e / segs, c = row >> 1, plane = row & 1;
-        __half* dst = Y + ((long long)(c0 + c) * 2 * n + p) * Kpad + plane * ps + k0 + 8 * j;
+        const long long at = ((long long)(c0 + c) * 2 * n + p) * Kpad + plane * ps + k0 + 8 * j;
         const int sh = plane ? 16 : 0;
-        if (8 * j + 8 <= kt) {
-            const uint4 a0 = *reinterpret_cast<const uint4*>(&S[c][8 * j]);
-            const uint4 a1 = *reinterpret_cast<const uint4*>(&S[c][8 * j + 4]);
-            const uint32_t sel = plane ? 0x7632u : 0x5410u;   // the re (low) or im (high) halves
-            *reinterpret_cast<uint4*>(dst) = make_uint4(__byte_perm(a0.x, a0.y, sel), __byte_perm(a0.z, a0.w, sel),
-                                                        __byte_perm(a1.x, a1.y, sel), __byte_perm(a1.z, a1.w, sel));
+        if constexpr (E4M3) {
+            // the FP8 form: the tile holds v / s as FP16; e4m3 bytes, 8 frames per 8 bytes
+            uint8_t* dst = static_cast<uint8_t*>(Yv) + at;
+            if (8 * j + 8 <= kt) {
+                uint32_t w[2];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    float f[4];
+#pragma unroll
+                    for (int e2 = 0; e2 < 4; ++e2)
+                        f[e2] = __half2float(__ushort_as_half((unsigned short)((S[c][8 * j + 4 * i + e2] >> sh) & 0xFFFFu)));
+                    w[i] = e4m3x2(make_float2(f[0], f[1])) | (e4m3x2(make_float2(f[2], f[3])) << 16);
+                }
+                *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
+            } else {
+                for (int i = 0; 8 * j + i < kt; ++i) {
+                    const float f = __half2float(__ushort_as_half((unsigned short)((S[c][8 * j + i] >> sh) & 0xFFFFu)));
+                    dst[i] = (uint8_t)(e4m3x2(make_float2(f, 0.0f)) & 0xFFu);
+                }
+            }
         } else {
-            for (int i = 0; 8 * j + i < kt; ++i) dst[i] = __ushort_as_half((unsigned short)((S[c][8 * j + i] >> sh) & 0xFFFFu));
+            __half* dst = static_cast<__half*>(Yv) + at;
+            if (8 * j + 8 <= kt) {
+                const uint4 a0 = *reinterpret_cast<const uint4*>(&S[c][8 * j]);
+                const uint4 a1 = *reinterpret_cast<const uint4*>(&S[c][8 * j + 4]);
+                const uint32_t sel = plane ? 0x7632u : 0x5410u;   // the re (low) or im (high) halves
+                *reinterpret_cast<uint4*>(dst) = make_uint4(__byte_perm(a0.x, a0.y, sel), __byte_perm(a0.z, a0.w, sel),
+                                                            __byte_perm(a1.x, a1.y, sel), __byte_perm(a1.z, a1.w, sel));
+            } else {
+                for (int i = 0; 8 * j + i < kt; ++i) dst[i] = __ushort_as_half((unsigned short)((S[c][8 * j + i] >> sh) & 0xFFFFu));
+            }
         }
     }
     __syncthreads();   // S is refilled by the next tile
     }
 }
 
-template <int N2, int G>
+template <int N2, int G, bool E4M3>
 cudaError_t launch_f128(const FArgs& a, cudaStream_t s)
 {
     using C = F128<N2, G>;
@@ -722,9 +745,9 @@ cudaError_t launch_f128(const FArgs& a, cudaStream_t s)
         const int kn = (int)(left < a.Kc ? left : a.Kc);   // frames stored in this slot
         constexpr int TRC = G >= 8 ? 32 : 64, TRK = kTrWords / TRC;   // channels, frames per transpose tile
         const long long tiles = (long long)a.n * (C::N / TRC) * ((kn + TRK - 1) / TRK);
-        f128_transpose_kernel<G, TRC><<<(unsigned)tiles, 256, 0, s>>>(
-            static_cast<const uint32_t*>(a.Yt), static_cast<__half*>(a.Y) + sl * slot_elems, C::N, a.n, a.Kpad,
-            (unsigned)groups, kn);
+        void* ys = static_cast<char*>(a.Y) + sl * slot_elems * (E4M3 ? 1 : 2);
+        f128_transpose_kernel<G, TRC, E4M3><<<(unsigned)tiles, 256, 0, s>>>(static_cast<const uint32_t*>(a.Yt), ys, C::N,
+                                                                           a.n, a.Kpad, (unsigned)groups, kn);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -740,11 +763,13 @@ size_t fstep_f128_scratch_bytes(int N, int n, long long Kc)
     return (size_t)n * (size_t)((Kc + G - 1) / G) * G * (size_t)N * 4;
 }
 
-cudaError_t launch_fstep_f128(int N, const FArgs& a, cudaStream_t s)
+cudaError_t launch_fstep_f128(int N, int out_kind, const FArgs& a, cudaStream_t s)
 {
+    const bool e4m3 = out_kind == FOUT_E4M3;
+    if (!e4m3 && out_kind != FOUT_F16) return cudaErrorInvalidValue;
     switch (N) {
-        case 1280: return launch_f128<10, 8>(a, s);
-        case 6400: return launch_f128<50, 2>(a, s);
+        case 1280: return e4m3 ? launch_f128<10, 8, true>(a, s) : launch_f128<10, 8, false>(a, s);
+        case 6400: return e4m3 ? launch_f128<50, 2, true>(a, s) : launch_f128<50, 2, false>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -19,11 +19,20 @@ constexpr int kKAlign = 128;             // frames per operand row are padded to
 // 512 KB (a whole 1 s row per path would put them 2.56 MB apart, one memory page each).
 constexpr int kIntKTile = 2048;
 
-// Output-type selector of the F-step (the FP8 form quantises the FP16 output afterwards).
+// Output-type selector of the F-step.
 // FOUT_F16X3: each value v (pre-scaled) as an FP16 pair hi = fp16(v), lo = fp16(v - hi),
 // hi in the first half of the operand row and lo in the second (the launch's Kpad is then
 // the row length, twice the frame capacity).
-enum FOut : int { FOUT_F32 = 0, FOUT_F16 = 1, FOUT_F16X3 = 2 };
+// FOUT_E4M3: the FP8 form written directly, v / s rounded to e4m3 (saturating), with the
+// plan's per-channel-group scale s folded into the gains (fp8_static_amax); otherwise the
+// FP8 form quantises an FP16 F-step's output with measured maxima afterwards.
+enum FOut : int { FOUT_F32 = 0, FOUT_F16 = 1, FOUT_F16X3 = 2, FOUT_E4M3 = 3 };
+
+// e4m3 bytes of (v.x, v.y), saturating: x in the low byte.
+__device__ __forceinline__ uint32_t e4m3x2(float2 v)
+{
+    return (uint32_t)__nv_cvt_float2_to_fp8x2(v, __NV_SATFINITE, __NV_E4M3);
+}
 
 // Channel averaging (Sec. 2.6) is split in two: the F-step multiplies ultrafine channel
 // c by gain[c] = sqrt(w_c) (w_c = 1, 1/2 for the end bins of an even fscrunch, 0 for an
@@ -156,11 +165,11 @@ cudaError_t launch_fstep(int N, int out_kind, const FArgs& a, cudaStream_t s, in
 // The tensor-core four-step F-step (FP16 output), N = 1280 or 6400.
 bool fstep_tc_supported(int N);
 cudaError_t launch_fstep_tc(int N, const FArgs& a, cudaStream_t s);
-// The 128-row tensor-core F-step (FP16 output), N = 1280 or 6400; it needs the scratch
-// a.Yt of fstep_f128_scratch_bytes (one slot of frame-major spectra).
+// The 128-row tensor-core F-step (FP16 or e4m3 output), N = 1280 or 6400; it needs the
+// scratch a.Yt of fstep_f128_scratch_bytes (one slot of frame-major spectra).
 bool fstep_f128_supported(int N);
 size_t fstep_f128_scratch_bytes(int N, int n, long long Kc);
-cudaError_t launch_fstep_f128(int N, const FArgs& a, cudaStream_t s);
+cudaError_t launch_fstep_f128(int N, int out_kind, const FArgs& a, cudaStream_t s);
 // The tensor-core direct-DFT F-step, N = 32, 64, 128 (FP32, FP16 or FP16 hi/lo output).
 bool fstep_dft_supported(int N, int out_kind);
 cudaError_t launch_fstep_dft(int N, int out_kind, const FArgs& a, cudaStream_t s);
@@ -174,6 +183,10 @@ cudaError_t launch_quantise_e4m3(const __half* Y16, __nv_fp8_storage_t* Y8, cons
 // values over frames [0, kvalid) into amax (then launch_quantise_e4m3).
 cudaError_t launch_amax_e4m3(const __half* Y16, float* amax, const int* chan_group, const Group* groups, int n_groups,
                              long long slots, int N, int n, long long Kpad, long long kvalid, cudaStream_t s);
+// FP8 form written by the F-step (FOUT_E4M3): the scales are static per channel group,
+// amax[slot][g][p] = amax_static[g] for the launch's slots.
+cudaError_t launch_fill_amax(float* amax, const float* amax_static, int n_groups, int n, long long slots,
+                             cudaStream_t s);
 cudaError_t launch_init_output(char* out, long long n_ints, long long vis_set_bytes, long long weights_bytes,
                                cudaStream_t s);
 // Occupancy weights from zeroing flags (Sec. 4.1) over each integration's weights table;

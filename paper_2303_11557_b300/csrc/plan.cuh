@@ -41,6 +41,8 @@ struct mwax_plan {
     int* chan_group = nullptr;   // FP8: group of each ultrafine channel
     float* amax = nullptr;       // FP8: [slots][groups][n] per-path max magnitude
     size_t amax_bytes = 0;
+    float* gain8 = nullptr;      // FP8, e4m3 from the F-step: gains carrying 1 / (static scale)
+    float* amax_static = nullptr;   // FP8: [groups] bound on the group's magnitudes
     RunInfo* runs = nullptr;
     int n_runs = 0;
     int4* tiles = nullptr;

@@ -900,9 +900,9 @@ def main():
     ap.add_argument("--fine-avg", type=int, default=0, help="fscrunch with --fft-len")
     ap.add_argument("--workload", default="full", choices=["full", "small"],
                     help="small = one 0.5 s integration (for profiler captures)")
-    ap.add_argument("--fstep-variant", type=int, default=None, choices=[0, 1, 2, 3],
+    ap.add_argument("--fstep-variant", type=int, default=None, choices=[0, 1, 2, 3, 4],
                     help="fix the F-step kernel (0 radix-32 / generic, 1 generic, 2 tensor-core DFT "
-                         "products, 3 128-row tensor-core) after tuning")
+                         "products, 3 128-row tensor-core, 4 frames-on-lanes direct DFT) after tuning")
     ap.add_argument("--beam-only", action="store_true", help="time the beamformer alone (profiler captures)")
     ap.add_argument("--beam-engine", type=int, default=0, choices=[0, 1],
                     help="with --beam-only: 0 tensor cores, 1 CUDA cores")

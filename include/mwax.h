@@ -257,7 +257,9 @@ mwax_status mwax_plan_stage_times(mwax_plan* plan, double ms[3], long long launc
  * tcgen05; N = 32, 64, 128 in every float form: the direct DFT as one product; variant 0
  * elsewhere), 3 = 128-row tensor-core F-step (N = 128 x 10, 128 x 50 with FP16 operands
  * out: stage A on tcgen05 with every accumulator lane a bin, stage B a radix-5/2 DFT in
- * registers; variant 2 elsewhere).  run_len: output channels per X-step work item (0 = the plan's own choice: the
+ * registers; variant 2 elsewhere), 4 = direct DFT with the frames on the accumulator lanes
+ * (N = 32, 64, 128 with FP16 operands out: one tcgen05 product per 128 frames, each warp
+ * store writing 32 consecutive frames of an operand row; variant 0 elsewhere).  run_len: output channels per X-step work item (0 = the plan's own choice: the
  * run length whose longest-first schedule of the work items on the GPU's resident CTA
  * slots is shortest).  window: column width of a tensor-core X-step tile, 128 or 256
  * (MWAX_FP16X3 always runs 128).  ms: device time of one call measured by the autotuner. */

@@ -360,6 +360,7 @@ mwax_status mwax_plan_autotune(mwax_plan* p, const int8_t* voltages, const doubl
     if ((p->prec == MWAX_FP16 || p->prec == MWAX_FP8) && fstep_tc_supported(p->N)) fvars.push_back(2);
     if ((p->prec == MWAX_FP16 || p->prec == MWAX_FP8) && fstep_f128_supported(p->N)) fvars.push_back(3);
     if (p->prec != MWAX_INT8 && (p->N == 32 || p->N == 64 || p->N == 128)) fvars.push_back(2);
+    if ((p->prec == MWAX_FP16 || p->prec == MWAX_FP8) && fstep_fd_supported(p->N, FOUT_F16)) fvars.push_back(4);
     std::vector<int> windows = {p->window};
     if (tc_plan(p)) windows = {256, 128};
     std::vector<int> runs = {0};   // 0: the plan's modelled run length
@@ -436,7 +437,7 @@ mwax_status mwax_plan_autotune(mwax_plan* p, const int8_t* voltages, const doubl
 mwax_status mwax_plan_set_tuning(mwax_plan* p, const mwax_tuning* t)
 {
     if (!p || !t) return set_error(MWAX_EINVAL, "NULL argument");
-    if (t->fstep_variant < 0 || t->fstep_variant > 3 || (t->window != 128 && t->window != 256) || t->run_len < 0)
+    if (t->fstep_variant < 0 || t->fstep_variant > 4 || (t->window != 128 && t->window != 256) || t->run_len < 0)
         return set_error(MWAX_EINVAL, "invalid tuning");
     BCUDA(cudaSetDevice(p->device));
     BCUDA(cudaStreamSynchronize(p->stream));

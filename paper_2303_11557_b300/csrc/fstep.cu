@@ -711,29 +711,30 @@ __global__ void __launch_bounds__(128) fstep_r32_kernel(const FArgs a)
         tw[i] = __ldg(&a.tw[i]);
         gain[i] = __ldg(&a.gain[i]);
     }
-    // Per-frame delay terms (Sec. 4.3), four roles per frame spread over the CTA's threads
-    // so that no warp carries all of the FP64 work into the barrier after pass 1.
-    {
-        const int f = threadIdx.x % FB, role = threadIdx.x / FB;
+    // Per-frame delay terms (Sec. 4.3): the FP64 polynomial once per frame (the FP64 pipe is
+    // narrow on this GPU), the phasor ratios from its FP32 split d_hi + d_lo (u d_hi exact
+    // for |u| < 4096: u = 1, 32, -N).
+    if (threadIdx.x < FB) {
+        const int f = threadIdx.x;
         const long long fl = f0 + f;
         const bool live = (a.delay != nullptr || a.delay_tab != nullptr) && fl < a.n_frames;
-        const double tau = live ? frame_delay(a, p, a.m_begin + fl, N) : 0.0;
-        const double d = tau * a.fs_over_n;
         FrameR32& fi = finfo[f];
-        if (role == 0) {
-            fi.slot = (fl < a.n_store) ? fl / a.Kc : -1;
-            fi.k = (fl < a.n_store) ? fl % a.Kc : 0;
-            fi.delay = live ? 1 : 0;
+        fi.slot = (fl < a.n_store) ? fl / a.Kc : -1;
+        fi.k = (fl < a.n_store) ? fl % a.Kc : 0;
+        fi.delay = live ? 1 : 0;
+        fi.phi0 = fi.d_hi = fi.d_lo = 0.0f;
+        fi.step1 = fi.step32 = fi.wrap = make_float2(1.0f, 0.0f);
+        if (live) {
+            const double tau = frame_delay(a, p, a.m_begin + fl, N);
+            const double d = tau * a.fs_over_n;
             const double ph = a.nu * tau;
-            fi.phi0 = live ? (float)(ph - floor(ph)) : 0.0f;
+            fi.phi0 = (float)(ph - floor(ph));
             const float dh = __uint_as_float(__float_as_uint((float)d) & 0xFFFFF000u);
-            fi.d_hi = live ? dh : 0.0f;
-            fi.d_lo = live ? (float)(d - (double)dh) : 0.0f;
-        } else if (role == 1 || role == 2 || role == 3) {
-            const double x = (role == 1) ? d : (role == 2 ? 32.0 * d : -(double)N * d);
-            float sn = 0.0f, cs = 1.0f;
-            if (live) sincospif(2.0f * (float)(x - rint(x)), &sn, &cs);
-            (role == 1 ? fi.step1 : (role == 2 ? fi.step32 : fi.wrap)) = make_float2(cs, sn);
+            fi.d_hi = dh;
+            fi.d_lo = (float)(d - (double)dh);
+            fi.step1 = delay_phasor_u(0.0f, fi.d_hi, fi.d_lo, 1);
+            fi.step32 = delay_phasor_u(0.0f, fi.d_hi, fi.d_lo, 32);
+            fi.wrap = delay_phasor_u(0.0f, fi.d_hi, fi.d_lo, -N);
         }
     }
 
@@ -1171,6 +1172,10 @@ cudaError_t launch_fstep(int N, int out_kind, const FArgs& a_in, cudaStream_t s,
     FArgs a = a_in;
     a.frame_dt = (double)N / a.fs;
     a.fs_over_n = a.fs / (double)N;
+    if (variant == 4) {
+        if (fstep_fd_supported(N, out_kind) && a.ktile == 0) return launch_fstep_fd(N, out_kind, a, s);
+        variant = 0;
+    }
     if (variant == 3) {
         if ((out_kind == FOUT_F16 || out_kind == FOUT_E4M3) && fstep_f128_supported(N) && a.Yt)
             return launch_fstep_f128(N, out_kind, a, s);

@@ -159,8 +159,9 @@ struct XLaunch {
 // variant 0: two-pass radix-32 kernel for N = 32..512 (generic elsewhere); 1: generic
 // Stockham passes for every N; 2: a tensor-core F-step where one is built (the direct DFT
 // product for N = 32, 64, 128, every output kind; the four-step DFT for FP16 output at
-// N = 1280 and 6400), variant 0 elsewhere; 3: the 128-row tensor-core F-step (FP16 output,
-// N = 1280 and 6400), variant 2 elsewhere.
+// N = 1280 and 6400), variant 0 elsewhere; 3: the 128-row tensor-core F-step (FP16 or e4m3
+// output, N = 1280 and 6400), variant 2 elsewhere; 4: the direct DFT with the frames on
+// the accumulator lanes (FP16 or e4m3 output, N = 32, 64, 128), variant 0 elsewhere.
 cudaError_t launch_fstep(int N, int out_kind, const FArgs& a, cudaStream_t s, int variant);
 // The tensor-core four-step F-step (FP16 output), N = 1280 or 6400.
 bool fstep_tc_supported(int N);
@@ -170,6 +171,10 @@ cudaError_t launch_fstep_tc(int N, const FArgs& a, cudaStream_t s);
 bool fstep_f128_supported(int N);
 size_t fstep_f128_scratch_bytes(int N, int n, long long Kc);
 cudaError_t launch_fstep_f128(int N, int out_kind, const FArgs& a, cudaStream_t s);
+// The tensor-core direct-DFT F-step with the frames on the accumulator lanes (variant 4),
+// N = 32, 64, 128, FP16 or e4m3 output.
+bool fstep_fd_supported(int N, int out_kind);
+cudaError_t launch_fstep_fd(int N, int out_kind, const FArgs& a, cudaStream_t s);
 // The tensor-core direct-DFT F-step, N = 32, 64, 128 (FP32, FP16 or FP16 hi/lo output).
 bool fstep_dft_supported(int N, int out_kind);
 cudaError_t launch_fstep_dft(int N, int out_kind, const FArgs& a, cudaStream_t s);

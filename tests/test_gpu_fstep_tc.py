@@ -1,8 +1,9 @@
-"""The tensor-core F-steps (F-step variants 2 and 3) against the FP64 oracle: the four-step
+"""The tensor-core F-steps (F-step variants 2, 3 and 4) against the FP64 oracle: the four-step
 DFT (two DFT-matrix products on tcgen05, N = 80 x 80 = 6400 and 80 x 16 = 1280, FP16
 operands out) and the 128-row F-step (stage A on tcgen05, a radix-5/2 stage B in registers,
-N = 128 x 50 and 128 x 10) at the FP16 and FP8 bars, and the direct DFT product (N = 32, 64, 128) in every float
-form at its bar: frame counts that leave ragged items and items that straddle two
+N = 128 x 50 and 128 x 10) at the FP16 and FP8 bars, the direct DFT product (N = 32, 64,
+128) in every float form at its bar, and the direct DFT with the frames on the accumulator
+lanes (N = 32, 64, 128) at the FP16 and FP8 bars: frame counts that leave ragged items and items that straddle two
 integrations or data blocks, per-path quadratic delays, zeroed data blocks, and the same
 plan with the CUDA-core F-step for comparison."""
 import numpy as np
@@ -122,3 +123,39 @@ def test_direct_dft_fstep_zeroed_blocks_fp32():
     assert np.allclose(w, rw, atol=1e-6)
     err = parity_error(vis, ref, T)
     assert np.all(np.isfinite(vis)) and err.max() <= 1e-5, f"max err {err.max():.3e}"
+
+
+# ---------------------------------------------------------------- frames-on-lanes direct DFT
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("N,F,K,bs", [(128, 4, 200, 6400), (64, 2, 250, 16_000), (32, 1, 250, 8000),
+                                      (128, 4, 500, 64_000)])
+def test_frames_on_lanes_fstep_parity(prec, N, F, K, bs):
+    # F-step variant 4: 128-frame items straddle the two integrations and data blocks of
+    # fewer than 128 frames (several copies per item); per-path quadratic delays
+    T = 7
+    S = 2 * K * N
+    assert S % bs == 0
+    volt, delay = workload(0x80 + N + prec + K, T, S, block_samples=bs, delay="quadratic")
+    desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=K * N / synth.FS, samples_per_call=S,
+                       block_samples=bs, sky_freq_hz=synth.SKY_FREQ_HZ, precision=prec)
+    vis, w = _run(desc, volt, delay, 4)
+    ref, rw = oracle.correlate(oracle_desc(T, N, F, K * N / synth.FS, S, block_samples=bs), volt, delay)
+    assert np.array_equal(w, rw.astype(np.float32))
+    err = parity_error(vis, ref, T)
+    assert np.all(np.isfinite(vis)) and err.max() <= TOL[prec], f"max err {err.max():.3e}"
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_frames_on_lanes_fstep_zeroed_blocks(prec):
+    T, N, F, K, bs = 9, 128, 4, 400, 6400
+    S = 2 * K * N
+    volt, delay = workload(0x81, T, S, block_samples=bs, delay="quadratic")
+    flags = (np.random.default_rng(9).random((S // bs, 2 * T)) < 0.15).astype(np.uint8)
+    desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=K * N / synth.FS, samples_per_call=S,
+                       block_samples=bs, sky_freq_hz=synth.SKY_FREQ_HZ, precision=prec)
+    vis, w = _run(desc, volt, delay, 4, flags=flags)
+    ref, rw = oracle.correlate_ext(oracle_desc(T, N, F, K * N / synth.FS, S, block_samples=bs),
+                                   oracle.Ext(zero_flags=flags), volt, delay)
+    assert np.allclose(w, rw, atol=1e-6)
+    err = parity_error(vis, ref, T)
+    assert np.all(np.isfinite(vis)) and err.max() <= TOL[prec], f"max err {err.max():.3e}"

@@ -47,7 +47,7 @@ WORKSPACE = 48 << 30
 # DRAM bytes (read + write) per integration slot of the dominant kernel, from an ncu
 # capture of the one-integration case (profiles/).  Reported only while the kernel's
 # source is byte-identical to the one captured (sha1 prefix of its .cu file).
-TRAFFIC = {"xstep_simt_kernel": ("paper_2303_11557_b300/csrc/xstep_simt.cu", "801bae888475", 6.645909e9 + 0.100315e9)}
+TRAFFIC = {"xstep_simt_kernel": ("paper_2303_11557_b300/csrc/xstep_simt.cu", "4aed89a75fb5", 6.595614e9 + 0.098705e9)}
 
 
 def traffic_per_slot(kernel: str):
@@ -721,8 +721,9 @@ def run_mine(args, world, rank, local):
         N, F = desc.fft_len, desc.fine_avg
         elem = {"fp32": 4, "fp16": 2, "fp8": 1, "int8": 2, "fp16x3": 4}[form]
         x_flops, f_bytes, used = algorithmic_work(W["n_tiles"], N, F, K, n_ints, elem)
-        if form == "fp8":
-            f_bytes += 2.0 * 2 * W["n_tiles"] * K * N * n_ints   # the amax pass reads the voltages again
+        if form == "fp8" and tuning.fstep_variant == 2:
+            # the DFT-product F-steps write FP16: a maxima pass and a quantisation pass follow
+            f_bytes += 2.0 * 2 * W["n_tiles"] * K * N * n_ints
         x_ms, x_n = stages["xstep"]
         f_ms, f_n = stages["fstep"]
         x_per_launch = x_flops * args.steps / x_n

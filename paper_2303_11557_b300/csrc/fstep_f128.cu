@@ -16,7 +16,7 @@
 // the whole F-step: the address translation of scattered rows, not DRAM, bounds it.
 // Every accumulator lane is a bin row k1.  The B operand's rows are ordered (half of k2,
 // k2 within the half, frame): a warp's lanes read the G frames of one bin from adjacent
-// tensor-memory columns and store them with one 2G-byte store per plane.  Z is rounded to
+// tensor-memory columns and write them as one row of the shared tile.  Z is rounded to
 // FP16 once and the 128-point DFT matrix is FP16 (2^-12 per entry): the FP16 form's error
 // bar holds widely.
 //
@@ -24,8 +24,8 @@
 // frames of one path) of one integration slot, software-pipelined: while the worker warps run
 // stage E of item j, the tensor cores run stage A of item j + 1 into the other half of
 // tensor memory and the bulk copy of item j + 2's int8 samples lands; the control warp
-// issues both and computes the frame terms; one CTA barrier per item.  Every wait is bounded (status
-// word); loop exits are taken by all threads at that barrier.
+// issues both and computes the frame terms; one CTA barrier per item.  Every wait is
+// bounded (status word); loop exits are taken by all threads at that barrier.
 #include "mwax_internal.cuh"
 #include "tc_ptx.cuh"
 

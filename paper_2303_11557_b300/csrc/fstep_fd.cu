@@ -6,9 +6,9 @@
 // matrix F_N[k, n] = e^{-2 pi i k n / N}, each row scaled by its channel's gain, rounded to
 // FP16 (2^-12 per entry).  Then per lane (one frame) and bin: the delay phasor (Sec. 4.3; a
 // ratio recurrence along the bins from one sincospi per frame and warp) and the store of
-// the K-major operand planes Y[slot][c][plane][p][Kpad], c = fftshift(k): a warp's 32 lanes are 32 consecutive
-// frames, so each store instruction writes 64 (FP16) or 32 (e4m3) contiguous bytes of one
-// operand row.
+// the K-major operand planes Y[slot][c][plane][p][Kpad], c = fftshift(k): a warp's 32
+// lanes are 32 consecutive frames, so each store instruction writes 64 (FP16) or 32 (e4m3)
+// contiguous bytes of one operand row.
 //
 // A persistent CTA (16 worker warps and a control warp, one CTA per SM) loops over the items,
 // software-pipelined as the 128-row F-step: the control warp copies item j + 2's samples in

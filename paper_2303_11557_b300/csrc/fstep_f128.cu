@@ -20,12 +20,12 @@
 // FP16 once and the 128-point DFT matrix is FP16 (2^-12 per entry): the FP16 form's error
 // bar holds widely.
 //
-// A persistent CTA (one per SM: 8 worker warps and a control warp) loops over the items (G
+// A persistent CTA (one per SM: 8 or 16 worker warps and a control warp) loops over the items (G
 // frames of one path) of one integration slot, software-pipelined: while the worker warps run
 // stage E of item j, the tensor cores run stage A of item j + 1 into the other half of
-// tensor memory and the bulk copy of item j + 2's int8 samples lands; the control warp
-// issues both and computes the frame terms; one CTA barrier per item.  Every wait is
-// bounded (status word); loop exits are taken by all threads at that barrier.
+// tensor memory and the bulk copies of later items' int8 samples land; the control warp
+// issues both; one CTA barrier per item.  Every
+// wait is bounded (status word); loop exits are taken by all threads at that barrier.
 #include "mwax_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -35,8 +35,10 @@ namespace mwax {
 namespace {
 
 constexpr int kM = 128;                 // bins k1 (MMA rows), samples n1 (MMA K)
-constexpr int kW = 256;                 // worker threads (stages P and E)
-constexpr int kT = kW + 32;             // plus one control warp (copies, MMAs, frame terms)
+// Worker threads (stages P and E) per length: 16 warps at N = 1280 (registers allow it),
+// 8 at N = 6400 (the length-50 DFT holds 100 registers per thread); plus one control warp
+// (copies, MMAs).
+__host__ __device__ constexpr int f128_workers(int N2) { return N2 == 10 ? 512 : 256; }
 constexpr uint32_t kLboF = 16 * 128;    // DFT matrix: 128 rows per K core column
 constexpr uint32_t kFPlane = 16 * kLboF;
 constexpr uint32_t kBufCols = 256;      // tensor-memory columns per accumulator buffer
@@ -54,12 +56,21 @@ struct F128 {
     static constexpr uint32_t LBO_X = NA * 16 + 16;
     static constexpr uint32_t XPLANE = 16 * LBO_X;
     static constexpr uint32_t STAGE = G * 2 * N;              // int8 (re, im) of the item's frames
+    // int8 stage buffers: two at N = 1280 (a short item's copy, issued one item ahead, did
+    // not land in time: the workers waited on it for a third of the item), one at N = 6400
+    // (its longer items hide the copy; shared memory is full)
+    static constexpr int ST = N2 == 10 ? 2 : 1;
     // stage P: one thread per sample n1 of a frame, or per pair (n1, n1 + 1) when there
     // are enough pairs for every thread (4-byte stores)
-    static constexpr bool PAIR = G * kM / 2 >= kW;
+    static constexpr int W = f128_workers(N2);                // worker threads
+    static constexpr int T = W + 32;                          // plus the control warp
+    static constexpr int FS = W / 256;                        // frame groups of stage E
+    static constexpr int FG = G / FS;                         // frames per stage-E warp
+    static_assert(FG == G || FG == 4, "stage-E frame split");
+    static constexpr bool PAIR = G * kM / 2 >= W;
     static constexpr int TASKS = PAIR ? G * kM / 2 : G * kM;
-    static_assert(TASKS % kW == 0, "whole tasks per thread");
-    static constexpr int PER = TASKS / kW;
+    static_assert(TASKS % W == 0, "whole tasks per thread");
+    static constexpr int PER = TASKS / W;
     static constexpr int CB = 8 / G;                          // bins per 8-column load
     static constexpr int NCH = (H + CB - 1) / CB;             // loads per half and plane
     // stage E's tile in shared memory: channel c's G words at c * TS (16-byte rows padded so
@@ -96,10 +107,10 @@ __device__ __forceinline__ void item_pos(const F128Items& m, long long Kc, unsig
 }
 
 struct F128Shared {
-    uint64_t ld_bar;         // an item's int8 frames staged
+    uint64_t ld_bar[2];      // an item's int8 frames staged, per stage buffer
     uint64_t bar;            // an item's stage-A MMAs complete
     uint64_t drained;        // after an abort: every MMA issued has completed
-    unsigned ld_mask;        // frames of the staged item with data
+    unsigned ld_mask[2];     // frames of the staged item with data, per stage buffer
     uint32_t tmem;
     int abort;
 };
@@ -133,6 +144,14 @@ __device__ __forceinline__ void ld8(uint32_t taddr, uint32_t (&r)[8])
 {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+}
+
+__device__ __forceinline__ void ld4(uint32_t taddr, uint32_t (&r)[4])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                  : "r"(taddr)
                  : "memory");
 }
@@ -239,9 +258,9 @@ __device__ __forceinline__ void dft_n2(float2 (&x)[L], const float2* w)
 }
 
 
-// Issue the copies of an item's frames (2N bytes each, one bulk copy per frame with data; a
-// frame never straddles a data block, whose length is a multiple of N) and publish the
-// mask of frames copied (the others are read as zero: past the call's data or the slot, or a
+// Issue the copies of an item's frames (one bulk copy per run of consecutive frames with
+// data in one data block; a frame never straddles a block, whose length is a multiple of
+// N) and publish the mask of frames copied (the others are read as zero: past the call's data or the slot, or a
 // zeroed block).  One thread.
 template <int N2, int G>
 __device__ __forceinline__ void issue_item(const FArgs& a, const F128Items& m, unsigned item, int8_t* stage,
@@ -253,25 +272,47 @@ __device__ __forceinline__ void issue_item(const FArgs& a, const F128Items& m, u
     int nv;
     item_pos<G>(m, a.Kc, item, p, f0, nv);
     const unsigned fpb = (unsigned)(a.bs / N);   // frames per data block
+    const unsigned mf0 = (unsigned)(a.m_begin + f0), blk0 = mf0 / fpb, fb0 = mf0 - blk0 * fpb;
+    // frame g lies in block blk0 + (fb0 + g) / fpb: stepped, not divided
+    auto valid = [&](int g, unsigned blk) {
+        return g < nv && f0 + g < a.n_frames && (a.flags == nullptr || a.flags[(long long)blk * a.n + p] == 0);
+    };
     unsigned mask = 0;
-    long long srcs[G];
+    {
+        unsigned blk = blk0, fb = fb0;
 #pragma unroll
-    for (int g = 0; g < G; ++g) {
-        const long long f = f0 + g;
-        srcs[g] = 0;
-        if (g >= nv || f >= a.n_frames) continue;
-        const unsigned mf = (unsigned)(a.m_begin + f), blk = mf / fpb, fb = mf - blk * fpb;
-        if (a.flags != nullptr && a.flags[(long long)blk * a.n + p] != 0) continue;
-        srcs[g] = (((long long)blk * a.n + p) * (long long)a.bs + (long long)fb * N) * 2;
-        mask |= 1u << g;
+        for (int g = 0; g < G; ++g) {
+            if (valid(g, blk)) mask |= 1u << g;
+            if (++fb == fpb) {
+                fb = 0;
+                ++blk;
+            }
+        }
     }
     // the mask is published before the arrive (release): a waiter that sees the phase
     // complete (at once when no frame is copied) reads this item's mask
     *mask_out = mask;
     tc::mbar_arrive_expect_tx(bar, (uint32_t)(__popc(mask) * 2 * N));
+    // one copy per run of consecutive frames with data inside one block (contiguous there)
+    unsigned blk = blk0, fb = fb0;
+    int g_run = -1;
+    long long src_run = 0;
 #pragma unroll
-    for (int g = 0; g < G; ++g)
-        if (mask & (1u << g)) bulk_copy(stage + g * 2 * N, a.volt + srcs[g], 2u * N, bar);
+    for (int g = 0; g <= G; ++g) {
+        const bool in = g < G && ((mask >> g) & 1u);
+        if (g_run >= 0 && (!in || fb == 0)) {   // close the open run at a gap or a block edge
+            bulk_copy(stage + g_run * 2 * N, a.volt + src_run, (uint32_t)((g - g_run) * 2 * N), bar);
+            g_run = -1;
+        }
+        if (in && g_run < 0) {
+            g_run = g;
+            src_run = (((long long)blk * a.n + p) * (long long)a.bs + (long long)fb * N) * 2;
+        }
+        if (g < G && ++fb == fpb) {
+            fb = 0;
+            ++blk;
+        }
+    }
 }
 
 // B-operand row of bin k2 of frame g: rows grouped by half of k2, then bin, then frame.
@@ -368,7 +409,7 @@ __device__ __forceinline__ F128Frame frame_terms(const FArgs& a, const F128Items
 }
 
 template <int N2, int G>
-__global__ void __launch_bounds__(kT, 1) fstep_f128_kernel(const FArgs a, const F128Items m)
+__global__ void __launch_bounds__(F128<N2, G>::T, 1) fstep_f128_kernel(const FArgs a, const F128Items m)
 {
     using C = F128<N2, G>;
     constexpr int N = C::N, H = C::H, HS = C::HS, NA = C::NA;
@@ -379,14 +420,22 @@ __global__ void __launch_bounds__(kT, 1) fstep_f128_kernel(const FArgs a, const 
     unsigned char* x_re = f_im + kFPlane;
     unsigned char* x_im = x_re + C::XPLANE;
     int8_t* stage = reinterpret_cast<int8_t*>(x_im + C::XPLANE);
-    uint32_t* T = reinterpret_cast<uint32_t*>(stage + C::STAGE);  // stage E tile [c][TS]
-    float2* w2 = reinterpret_cast<float2*>(stage + C::STAGE + C::TILE);   // W_N2^j, j < N2 (64 slots)
+    uint32_t* T = reinterpret_cast<uint32_t*>(stage + C::ST * C::STAGE);  // stage E tile [c][TS]
+    float2* w2 = reinterpret_cast<float2*>(stage + C::ST * C::STAGE + C::TILE);   // W_N2^j, j < N2 (64 slots)
     F128Frame* frs = reinterpret_cast<F128Frame*>(w2 + 64);      // frame terms, 3 items x G
     F128Shared& S = *reinterpret_cast<F128Shared*>(frs + 3 * G);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr int kW = C::W, kT = C::T;
     const bool worker = tid < kW, ctl = tid == kW;   // ctl: lane 0 of the control warp
     int* status = a.status;
+    unsigned n_cp[2] = {0u, 0u};   // copies issued per stage buffer (control thread)
+    // copy item `itj`, the j-th of this CTA, into stage buffer j mod ST
+    auto issue_copy = [&](int j, unsigned itj) {
+        const int b = j % C::ST;
+        issue_item<N2, G>(a, m, itj, stage + b * C::STAGE, &S.ld_bar[b], &S.ld_mask[b]);
+        ++n_cp[b];
+    };
 
     // ---- set-up: the 128-point DFT matrix (A: rows k1, K = n1), the B operand zeroed (its
     // padding rows stay zero), the length-N2 twiddles, barriers, tensor memory
@@ -402,12 +451,17 @@ __global__ void __launch_bounds__(kT, 1) fstep_f128_kernel(const FArgs a, const 
     for (int j = tid; j < N2; j += kT) w2[j] = __ldg(&a.tw[j * kM]);   // e^{-2 pi i 128 j / N} = W_N2^j
     unsigned cur = blockIdx.x;
     if (ctl) {
-        tc::mbar_init(&S.ld_bar, 1);
+        tc::mbar_init(&S.ld_bar[0], 1);
+        tc::mbar_init(&S.ld_bar[1], 1);
         tc::mbar_init(&S.bar, 1);
         tc::mbar_init(&S.drained, 1);
         S.abort = 0;
         tc::fence_mbar_init();
-        if (cur < m.n_items) issue_item<N2, G>(a, m, cur, stage, &S.ld_bar, &S.ld_mask);
+        // the first ST items' copies, one per stage buffer
+        for (int j = 0; j < C::ST; ++j) {
+            const unsigned itj = cur + (unsigned)j * gridDim.x;
+            if (itj < m.n_items) issue_copy(j, itj);
+        }
     }
     if (tid >= kW && tid < kW + G && cur < m.n_items) frs[tid - kW] = frame_terms<N2, G>(a, m, cur, tid - kW);
     if (warp == 0) {
@@ -418,28 +472,28 @@ __global__ void __launch_bounds__(kT, 1) fstep_f128_kernel(const FArgs a, const 
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = S.tmem;
-    const int q = warp & 3, h = (warp >> 2) & 1;
+    const int q = warp & 3, h = (warp >> 2) & 1, fq = warp >> 3;   // lane quarter, bin half, frame group
     const int k1 = 32 * q + lane;                  // a worker lane's bin row
-    uint32_t ld_par = 0, mma_par = 0;
-    unsigned n_copies = cur < m.n_items ? 1u : 0u;   // copies issued (control thread)
+    uint32_t mma_par = 0;
     bool bad = false, stop = false, issued = false;
 
     // stage P of an item (worker threads): its staged samples to the B operand
-    auto stage_p = [&]() {
-        if (!wait_phase(&S.ld_bar, ld_par, &S.abort)) {
+    auto stage_p = [&](int j) {   // the CTA's j-th item: stage buffer j mod ST, its (j / ST)-th copy
+        const int b = j % C::ST;
+        if (!wait_phase(&S.ld_bar[b], (uint32_t)(j / C::ST) & 1u, &S.abort)) {
             bad = true;
             S.abort = 1;   // lets the other threads' waits give up early
             if (status) atomicOr(status, 2048);
             return;
         }
-        ld_par ^= 1u;
-        const unsigned mask = S.ld_mask;
+        const unsigned mask = S.ld_mask[b];
+        const int8_t* sb = stage + b * C::STAGE;
 #pragma unroll
         for (int i = 0; i < C::PER; ++i) {
             const int t = tid + kW * i;
             const int g = C::PAIR ? t / (kM / 2) : t / kM;
             const int n1 = C::PAIR ? 2 * (t % (kM / 2)) : t % kM;
-            stage_p_task<N2, G, C::PAIR>(stage, (mask >> g) & 1u, g, n1, a.tw, w2, x_re, x_im);
+            stage_p_task<N2, G, C::PAIR>(sb, (mask >> g) & 1u, g, n1, a.tw, w2, x_re, x_im);
         }
     };
 
@@ -466,7 +520,7 @@ __global__ void __launch_bounds__(kT, 1) fstep_f128_kernel(const FArgs a, const 
     // stage E of an item from accumulator buffer `buf` (worker threads): bins
     // k = N2 k1 + k2, k2 in this warp's half; phasor, gain, FP16 (re, im) of the G frames
     // into the shared-memory tile T
-    auto stage_e = [&](int buf, const F128Frame* fr) {
+    auto stage_e_all = [&](int buf, const F128Frame* fr) {
         const bool lowk = k1 < kM / 2;                  // k < N/2: u = k; else u = k - N
         const int k0 = N2 * k1 + H * h;                 // this lane's first bin
         float2 P[G], st[G];
@@ -537,6 +591,66 @@ __global__ void __launch_bounds__(kT, 1) fstep_f128_kernel(const FArgs a, const 
         }
     };
 
+    // stage E with the frames split over two warp groups (16 worker warps): warp group fq
+    // takes frames FG fq .. FG fq + FG - 1 of every bin of its half; per bin one 4-column
+    // tensor-memory load per plane, the next bin's loads and gain in flight
+    auto stage_e_split = [&](int buf, const F128Frame* fr) {
+        constexpr int FG = C::FG;
+        const int g0 = fq * FG;
+        const bool lowk = k1 < kM / 2;
+        const int k0 = N2 * k1 + H * h;
+        float2 P[FG], st[FG];
+#pragma unroll
+        for (int j = 0; j < FG; ++j) {
+            const F128Frame& fi = fr[g0 + j];
+            P[j] = fi.delay ? phasor_u(fi.phi0, fi.d_hi, fi.d_lo, lowk ? k0 : k0 - N) : make_float2(1.0f, 0.0f);
+            st[j] = fi.step;
+        }
+        const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)buf * kBufCols + (uint32_t)(h * HS + g0);
+        auto gain_of = [&](int kk) {
+            const int k = k0 + kk;
+            return __ldg(&a.gain[lowk ? k + N / 2 : k - N / 2]);
+        };
+        uint32_t vr[4], vi[4], nr[4], ni[4];
+        ld4(tb, vr);
+        ld4(tb + (uint32_t)NA, vi);
+        float gc = gain_of(0), gnx = 0.0f;
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int kk = 0; kk < H; ++kk) {
+            if (kk + 1 < H) {
+                ld4(tb + (uint32_t)((kk + 1) * G), nr);
+                ld4(tb + (uint32_t)(NA + (kk + 1) * G), ni);
+                gnx = gain_of(kk + 1);
+            }
+            const int k = k0 + kk;
+            const int c = lowk ? k + N / 2 : k - N / 2;   // fftshift
+            uint32_t hv[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float2 y = make_float2(__uint_as_float(vr[j]), __uint_as_float(vi[j]));
+                y = cmul(y, P[j]);
+                P[j] = cmul(P[j], st[j]);
+                const __half2 v = __floats2half2_rn(y.x * gc, y.y * gc);
+                hv[j] = *reinterpret_cast<const uint32_t*>(&v);
+            }
+            *reinterpret_cast<uint4*>(T + c * C::TS + g0) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+            if (kk + 1 < H) {
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    vr[i] = nr[i];
+                    vi[i] = ni[i];
+                }
+                gc = gnx;
+            }
+        }
+    };
+    auto stage_e = [&](int buf, const F128Frame* fr) {
+        if constexpr (C::FS == 1) stage_e_all(buf, fr);
+        else stage_e_split(buf, fr);
+    };
+
     // the tile of an item into its scratch tile Yt[c][g] (worker threads; 16-byte copies,
     // a warp writing 512 contiguous bytes)
     auto copy_out = [&](unsigned item) {
@@ -557,24 +671,22 @@ __global__ void __launch_bounds__(kT, 1) fstep_f128_kernel(const FArgs a, const 
     };
 
     // ---- prologue: stage P and stage A of the first item, the copy of the second
-    if (worker && cur < m.n_items) stage_p();
+    if (worker && cur < m.n_items) stage_p(0);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // B operand: generic writes, MMA reads
     tc::fence_before();
     stop = __syncthreads_or(bad);
     if (!stop && ctl && cur < m.n_items) {
         tc::fence_after();
         stage_a(0);
-        const unsigned nxt = cur + gridDim.x;
-        if (nxt < m.n_items) {
-            issue_item<N2, G>(a, m, nxt, stage, &S.ld_bar, &S.ld_mask);
-            ++n_copies;
-        }
+        const unsigned itj = cur + (unsigned)C::ST * gridDim.x;   // item ST, into buffer 0
+        if (itj < m.n_items) issue_copy(C::ST, itj);
     }
 
-    // ---- steady state, item `cur` in buffer it & 1.  Workers: wait for its MMAs, stage P
-    // of the next item.  Control warp: the next item's frame terms.  Barrier.  Then the
-    // control thread issues stage A of the next item and the copy of the one after, and the
-    // workers run stage E of `cur`.
+    // ---- steady state, item `cur` in buffer it & 1.  Workers: wait for its MMAs, stage P of
+    // the next item; its frame terms on the workers or the control warp.  Barrier.  Then the control thread issues stage A of
+    // the next item and the copy of a later one (the control warp shares its scheduler with
+    // four worker warps, so its own work is kept short), and the workers run stage E of
+    // `cur`.
     int it = 0;
     for (; !stop && cur < m.n_items; cur += gridDim.x, ++it) {
         const unsigned nxt = cur + gridDim.x;
@@ -587,8 +699,15 @@ __global__ void __launch_bounds__(kT, 1) fstep_f128_kernel(const FArgs a, const 
                 if (status) atomicOr(status, 1024);
             }
             tc::fence_after();
-            if (!bad && nxt < m.n_items) stage_p();
-        } else if (lane < G && nxt < m.n_items) {
+            if (!bad && nxt < m.n_items) {
+                // the next item's frame terms (FP64): with 16 worker warps one frame per warp on
+                // its lane 0 (the control warp shares its scheduler with four worker warps);
+                // with 8, on the control warp
+                if (C::W == 512 && lane == 0 && warp < G)
+                    frs[((it + 1) % 3) * G + warp] = frame_terms<N2, G>(a, m, nxt, warp);
+                stage_p(it + 1);
+            }
+        } else if (C::W != 512 && lane < G && nxt < m.n_items) {
             frs[((it + 1) % 3) * G + lane] = frame_terms<N2, G>(a, m, nxt, lane);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -597,11 +716,9 @@ __global__ void __launch_bounds__(kT, 1) fstep_f128_kernel(const FArgs a, const 
         tc::fence_after();
         if (ctl && nxt < m.n_items) {
             stage_a((it + 1) & 1);
-            const unsigned nn = nxt + gridDim.x;
-            if (nn < m.n_items) {
-                issue_item<N2, G>(a, m, nn, stage, &S.ld_bar, &S.ld_mask);
-                ++n_copies;
-            }
+            // item it + 1 + ST into the buffer item it + 1 has just left
+            const unsigned itj = nxt + (unsigned)C::ST * gridDim.x;
+            if (itj < m.n_items) issue_copy(it + 1 + C::ST, itj);
         }
         if (worker) {
             stage_e(it & 1, frs + (it % 3) * G);
@@ -610,15 +727,16 @@ __global__ void __launch_bounds__(kT, 1) fstep_f128_kernel(const FArgs a, const 
         }
     }
 
-    // ---- wind-down: after an abort the MMAs and the bulk copy in flight finish before the
-    // CTA releases its tensor memory and exits (at most one copy is ever in flight)
+    // ---- wind-down: after an abort the MMAs and the bulk copies in flight finish before the
+    // CTA releases its tensor memory and exits (at most one copy per stage buffer)
     if (ctl && stop) {
         if (issued) {
             tc::mma_commit(&S.drained);
             if (!tc::wait_bounded(&S.drained, 0u, tc::kDrainCycles) && status) atomicOr(status, tc::kDrainGaveUp);
         }
-        if (n_copies > 0 && !tc::wait_bounded(&S.ld_bar, (n_copies - 1) & 1u, tc::kDrainCycles) && status)
-            atomicOr(status, tc::kDrainGaveUp);
+        for (int b = 0; b < C::ST; ++b)
+            if (n_cp[b] > 0 && !tc::wait_bounded(&S.ld_bar[b], (n_cp[b] - 1) & 1u, tc::kDrainCycles) && status)
+                atomicOr(status, tc::kDrainGaveUp);
     }
     tc::fence_before();
     __syncthreads();
@@ -712,7 +830,7 @@ template <int N2, int G, bool E4M3>
 cudaError_t launch_f128(const FArgs& a, cudaStream_t s)
 {
     using C = F128<N2, G>;
-    constexpr size_t smem = 2 * kFPlane + 2 * C::XPLANE + C::STAGE + C::TILE + sizeof(float2) * 64 +
+    constexpr size_t smem = 2 * kFPlane + 2 * C::XPLANE + C::ST * C::STAGE + C::TILE + sizeof(float2) * 64 +
                             3 * G * sizeof(F128Frame) + sizeof(F128Shared) + 128;
     static_assert(smem <= 227 * 1024, "shared memory");
     static bool attr_done = false;
@@ -738,7 +856,7 @@ cudaError_t launch_f128(const FArgs& a, cudaStream_t s)
         m.n_items = (unsigned)n_items;
         m.groups = (unsigned)groups;
         m.slot = (unsigned)sl;
-        fstep_f128_kernel<N2, G><<<(unsigned)grid, kT, smem, s>>>(a, m);
+        fstep_f128_kernel<N2, G><<<(unsigned)grid, C::T, smem, s>>>(a, m);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         const long long left = a.n_store - sl * a.Kc;

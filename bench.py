@@ -416,7 +416,7 @@ def run_batch24(mw, torch, dev_base, args):
             "input": "the 256-tile 8 s voltage bytes re-tiled per tile count (every channel computed in full)"}
 
 
-def run_serve(mw, torch, host_base, args, periods: int = 2, counts=(24, 32, 40, 48)):
+def run_serve(mw, torch, host_base, args, periods: int = 2, counts=(24, 32, 40, 48, 56, 64)):
     """Real-time serving: n coarse channels each delivering an 8 s sub-observation every 8 s
     (seeded offsets within the period), FP16 or integer mode per request (80/20), host
     pinned voltages; the server admits by HBM footprint; deadline = 8 s.  The 24-channel

@@ -759,11 +759,13 @@ __global__ void __launch_bounds__(256) f128_transpose_kernel(const uint32_t* __r
 {
     constexpr int kTrK = kTrWords / kTrC;
     __shared__ __align__(16) uint32_t S[kTrC][kTrK + 4];
-    const int cblocks = N / kTrC, kblocks = (kn + kTrK - 1) / kTrK;
+    const int cblocks = N / kTrC, kblocks = (int)((Kpad + kTrK - 1) / kTrK);
     const long long tiles = (long long)n * cblocks * kblocks;
     for (long long b = blockIdx.x; b < tiles; b += gridDim.x) {
     const int kb = (int)(b % kblocks), cb = (int)((b / kblocks) % cblocks), p = (int)(b / ((long long)kblocks * cblocks));
-    const int c0 = cb * kTrC, k0 = kb * kTrK, kt = min(kTrK, kn - k0);
+    const int c0 = cb * kTrC, k0 = kb * kTrK;
+    const int kt = max(0, min(kTrK, kn - k0));              // frames with data in this tile
+    const int kw = (int)min((long long)kTrK, Kpad - k0);    // frames written: whole rows to Kpad
     const int ng = (kt + G - 1) / G;   // groups in this tile
     // read: group fg's words (c0 .. c0 + kTrC - 1) x G are contiguous 16-byte chunks
     constexpr int CH = kTrC * G / 4;
@@ -782,44 +784,40 @@ __global__ void __launch_bounds__(256) f128_transpose_kernel(const uint32_t* __r
         }
     }
     __syncthreads();
-    // write: row (c, plane), frames k0 .. k0 + kt - 1, 8 frames (16 bytes) per thread step
+    // write: row (c, plane), frames k0 .. k0 + kw - 1 (zeros past the data: whole rows up to
+    // Kpad, so every store fills its sectors), 8 frames per thread step
     const long long ps = (long long)n * Kpad;
-    const int segs = (kt + 7) / 8;
+    const int segs = kw / 8;   // Kpad is a multiple of 8
     for (int e = threadIdx.x; e < kTrC * 2 * segs; e += blockDim.x) {
         const int j = e % segs, row = e / segs, c = row >> 1, plane = row & 1;
         const long long at = ((long long)(c0 + c) * 2 * n + p) * Kpad + plane * ps + k0 + 8 * j;
-        const int sh = plane ? 16 : 0;
+        uint32_t w8[8];   // the tile's (re, im) words of the 8 frames, 0 past the data
+        if (8 * j + 8 <= kt) {
+            const uint4 a0 = *reinterpret_cast<const uint4*>(&S[c][8 * j]);
+            const uint4 a1 = *reinterpret_cast<const uint4*>(&S[c][8 * j + 4]);
+            w8[0] = a0.x; w8[1] = a0.y; w8[2] = a0.z; w8[3] = a0.w;
+            w8[4] = a1.x; w8[5] = a1.y; w8[6] = a1.z; w8[7] = a1.w;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) w8[i] = 8 * j + i < kt ? S[c][8 * j + i] : 0u;
+        }
+        const uint32_t sel = plane ? 0x7632u : 0x5410u;   // the re (low) or im (high) halves
         if constexpr (E4M3) {
             // the FP8 form: the tile holds v / s as FP16; e4m3 bytes, 8 frames per 8 bytes
-            uint8_t* dst = static_cast<uint8_t*>(Yv) + at;
-            if (8 * j + 8 <= kt) {
-                uint32_t w[2];
+            uint32_t w[2];
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    float f[4];
-#pragma unroll
-                    for (int e2 = 0; e2 < 4; ++e2)
-                        f[e2] = __half2float(__ushort_as_half((unsigned short)((S[c][8 * j + 4 * i + e2] >> sh) & 0xFFFFu)));
-                    w[i] = e4m3x2(make_float2(f[0], f[1])) | (e4m3x2(make_float2(f[2], f[3])) << 16);
-                }
-                *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
-            } else {
-                for (int i = 0; 8 * j + i < kt; ++i) {
-                    const float f = __half2float(__ushort_as_half((unsigned short)((S[c][8 * j + i] >> sh) & 0xFFFFu)));
-                    dst[i] = (uint8_t)(e4m3x2(make_float2(f, 0.0f)) & 0xFFu);
-                }
+            for (int i = 0; i < 2; ++i) {
+                const uint32_t h01 = __byte_perm(w8[4 * i], w8[4 * i + 1], sel);
+                const uint32_t h23 = __byte_perm(w8[4 * i + 2], w8[4 * i + 3], sel);
+                const float2 f01 = __half22float2(*reinterpret_cast<const __half2*>(&h01));
+                const float2 f23 = __half22float2(*reinterpret_cast<const __half2*>(&h23));
+                w[i] = e4m3x2(f01) | (e4m3x2(f23) << 16);
             }
+            *reinterpret_cast<uint2*>(static_cast<uint8_t*>(Yv) + at) = make_uint2(w[0], w[1]);
         } else {
-            __half* dst = static_cast<__half*>(Yv) + at;
-            if (8 * j + 8 <= kt) {
-                const uint4 a0 = *reinterpret_cast<const uint4*>(&S[c][8 * j]);
-                const uint4 a1 = *reinterpret_cast<const uint4*>(&S[c][8 * j + 4]);
-                const uint32_t sel = plane ? 0x7632u : 0x5410u;   // the re (low) or im (high) halves
-                *reinterpret_cast<uint4*>(dst) = make_uint4(__byte_perm(a0.x, a0.y, sel), __byte_perm(a0.z, a0.w, sel),
-                                                            __byte_perm(a1.x, a1.y, sel), __byte_perm(a1.z, a1.w, sel));
-            } else {
-                for (int i = 0; 8 * j + i < kt; ++i) dst[i] = __ushort_as_half((unsigned short)((S[c][8 * j + i] >> sh) & 0xFFFFu));
-            }
+            *reinterpret_cast<uint4*>(static_cast<__half*>(Yv) + at) =
+                make_uint4(__byte_perm(w8[0], w8[1], sel), __byte_perm(w8[2], w8[3], sel),
+                           __byte_perm(w8[4], w8[5], sel), __byte_perm(w8[6], w8[7], sel));
         }
     }
     __syncthreads();   // S is refilled by the next tile
@@ -862,7 +860,7 @@ cudaError_t launch_f128(const FArgs& a, cudaStream_t s)
         const long long left = a.n_store - sl * a.Kc;
         const int kn = (int)(left < a.Kc ? left : a.Kc);   // frames stored in this slot
         constexpr int TRC = G >= 8 ? 32 : 64, TRK = kTrWords / TRC;   // channels, frames per transpose tile
-        const long long tiles = (long long)a.n * (C::N / TRC) * ((kn + TRK - 1) / TRK);
+        const long long tiles = (long long)a.n * (C::N / TRC) * ((a.Kpad + TRK - 1) / TRK);
         void* ys = static_cast<char*>(a.Y) + sl * slot_elems * (E4M3 ? 1 : 2);
         f128_transpose_kernel<G, TRC, E4M3><<<(unsigned)tiles, 256, 0, s>>>(static_cast<const uint32_t*>(a.Yt), ys, C::N,
                                                                            a.n, a.Kpad, (unsigned)groups, kn);

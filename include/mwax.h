@@ -284,7 +284,10 @@ typedef struct {
  */
 mwax_status mwax_plan_autotune(mwax_plan* plan, const int8_t* voltages, const double* delay_poly, void* vis_out,
                                mwax_tuning* best);
-/* Set or read a plan's launch choices (waits for the plan's stream before changing). */
+/* Set or read a plan's launch choices (waits for the plan's stream before changing).
+ * Choosing F-step variant 3 or 4 allocates its device scratch once if the plan has none
+ * (the frames' delay terms, written by a small kernel before each F-step launch; variant 3
+ * also one slot of frame-major spectra); MWAX_ENOMEM if that fails. */
 mwax_status mwax_plan_set_tuning(mwax_plan* plan, const mwax_tuning* tuning);
 mwax_status mwax_plan_get_tuning(const mwax_plan* plan, mwax_tuning* tuning);
 

@@ -417,7 +417,7 @@ mwax_status setup(mwax_plan& p)
     // N = 1280, 6400 with FP16 operands out: the 128-row tensor-core F-step by default (the
     // fastest measured there), with its one-slot scratch
     if (fstep_f128_supported(p.N) && (p.prec == MWAX_FP16 || p.prec == MWAX_FP8)) {
-        const mwax_status st = ensure_f128_scratch(&p);
+        const mwax_status st = ensure_fstep_scratch(&p, 3);
         if (st != MWAX_OK) return st;
         p.fvariant = 3;
     }

@@ -205,10 +205,18 @@ mwax_status enqueue_batch(mwax_batch* b, const int8_t* const* volt, const double
 }  // namespace
 
 namespace mwax {
-mwax_status ensure_f128_scratch(mwax_plan* p)
+mwax_status ensure_fstep_scratch(mwax_plan* p, int variant)
 {
-    if (!fstep_f128_supported(p->N) || (p->prec != MWAX_FP16 && p->prec != MWAX_FP8)) return MWAX_OK;
-    const size_t need = fstep_f128_scratch_bytes(p->N, p->n, p->Kc);
+    if (p->prec != MWAX_FP16 && p->prec != MWAX_FP8) return MWAX_OK;
+    size_t need = 0;
+    if (variant == 3 && fstep_f128_supported(p->N)) {
+        need = fstep_f128_scratch_bytes(p->N, p->n, p->Kc);
+    } else if (variant == 4 && fstep_fd_supported(p->N, FOUT_F16)) {
+        // the most frames one F-step launch stores: a launch group of whole integrations, or
+        // one chunk of a split integration
+        const long long max_store = p->chunks == 1 ? p->slots * p->K : p->Kpad;
+        need = fstep_fd_scratch_bytes(p->N, p->n, max_store);
+    }
     if (p->Yt_bytes >= need) return MWAX_OK;
     BCUDA(cudaSetDevice(p->device));
     if (p->stream) BCUDA(cudaStreamSynchronize(p->stream));
@@ -391,7 +399,7 @@ mwax_status mwax_plan_autotune(mwax_plan* p, const int8_t* voltages, const doubl
     // stage 1: the F-step variant, with the plan's own X-step choice
     const int rl0 = p->run_len, w0 = p->window;
     for (int fv : fvars) {
-        if (fv == 3 && (st = ensure_f128_scratch(p)) != MWAX_OK) break;
+        if ((fv == 3 || fv == 4) && (st = ensure_fstep_scratch(p, fv)) != MWAX_OK) break;
         p->fvariant = fv;
         st = configure_x(*p, rl0, w0);
         if (st != MWAX_OK) break;
@@ -441,8 +449,8 @@ mwax_status mwax_plan_set_tuning(mwax_plan* p, const mwax_tuning* t)
         return set_error(MWAX_EINVAL, "invalid tuning");
     BCUDA(cudaSetDevice(p->device));
     BCUDA(cudaStreamSynchronize(p->stream));
-    if (t->fstep_variant == 3) {
-        const mwax_status st = ensure_f128_scratch(p);
+    if (t->fstep_variant == 3 || t->fstep_variant == 4) {
+        const mwax_status st = ensure_fstep_scratch(p, t->fstep_variant);
         if (st != MWAX_OK) return st;
     }
     p->fvariant = t->fstep_variant;

@@ -11,6 +11,9 @@
 //       item's frame-major scratch tile Yt[p][group][c][g], c = fftshift(k);
 //   transpose (one launch per slot after the F-step's): Yt to the K-major operand planes
 //       Y[slot][c][plane][p][Kpad] (FP16, or e4m3 when the gains carry the FP8 scales).
+// Each frame's delay terms (FP64) and each item's mask of frames with data come from a small
+// kernel launched before the F kernel: on this GPU's narrow FP64 pipe one lane's FP64 work
+// costs a whole warp's issue time, and inside the F kernel it held every item's barrier.
 // Writing the K-major rows straight from the bins (each item holds only G frames, so each
 // lane's store lands in its own row and 2 MB page) measured several times slower than
 // the whole F-step: the address translation of scattered rows, not DRAM, bounds it.
@@ -81,17 +84,28 @@ struct F128 {
 };
 
 struct F128Frame {
-    long long slot, k;       // operand slot and frame within it (slot -1: not stored)
     float phi0, d_hi, d_lo;  // delay terms: the phasor of bin offset u is e^{2 pi i (phi0 + u d)}
     int delay;
     float2 step;             // e^{2 pi i d}: phasor ratio between bins k and k + 1
 };
+// an item's G frame terms travel by bulk copy (16-byte multiples)
+static_assert(sizeof(F128Frame) == 24, "frame terms: 24 bytes");
+
+// Frames per item, and the bytes of one launch's scratch tiles (FP16 re, im words [item][c][g]).
+constexpr int f128_frames(int N) { return N == 1280 ? 8 : 2; }
+inline size_t f128_tiles_bytes(int N, int n, long long Kc)
+{
+    const int G = f128_frames(N);
+    return (size_t)n * (size_t)((Kc + G - 1) / G) * G * (size_t)N * 4;
+}
 
 // Items of one launch: one integration slot, path-major, groups of G frames.
 struct F128Items {
     unsigned n_items;    // paths x groups
     unsigned groups;     // groups of G frames per slot: ceil(Kc / G)
     unsigned slot;       // slot of the launch group
+    F128Frame* tab;      // frame terms [item][G] (f128_terms_kernel)
+    unsigned* masks;     // frames with data per item (f128_terms_kernel)
 };
 
 // Path, first frame (of the call) and frames in the slot (at most G) of an item.
@@ -257,14 +271,39 @@ __device__ __forceinline__ void dft_n2(float2 (&x)[L], const float2* w)
     else dft50(x, w);
 }
 
+// The frames of an item with data: the others are read as zero (past the call's data or the
+// slot, or in a zeroed block).  A frame never straddles a data block, whose length is a
+// multiple of N.
+template <int N2, int G>
+__device__ __forceinline__ unsigned item_mask(const FArgs& a, const F128Items& m, unsigned item)
+{
+    constexpr int N = kM * N2;
+    unsigned p;
+    long long f0;
+    int nv;
+    item_pos<G>(m, a.Kc, item, p, f0, nv);
+    const unsigned fpb = (unsigned)(a.bs / N);   // frames per data block
+    const unsigned mf0 = (unsigned)(a.m_begin + f0), blk0 = mf0 / fpb;
+    unsigned blk = blk0, fb = mf0 - blk0 * fpb, mask = 0;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        if (g < nv && f0 + g < a.n_frames && (a.flags == nullptr || a.flags[(long long)blk * a.n + p] == 0))
+            mask |= 1u << g;
+        if (++fb == fpb) {   // frame g + 1 lies in the next block
+            fb = 0;
+            ++blk;
+        }
+    }
+    return mask;
+}
 
-// Issue the copies of an item's frames (one bulk copy per run of consecutive frames with
-// data in one data block; a frame never straddles a block, whose length is a multiple of
-// N) and publish the mask of frames copied (the others are read as zero: past the call's data or the slot, or a
-// zeroed block).  One thread.
+// Stage an item: its frames with data (the mask of f128_terms_kernel; one bulk copy per run
+// of consecutive frames with data in one data block) and its G frame terms, on one mbarrier
+// transaction; publish the mask.  One thread.
 template <int N2, int G>
 __device__ __forceinline__ void issue_item(const FArgs& a, const F128Items& m, unsigned item, int8_t* stage,
-                                               uint64_t* bar, unsigned* mask_out)
+                                               uint64_t* bar, unsigned* mask_out, const unsigned* masks,
+                                               const F128Frame* tab, F128Frame* terms)
 {
     constexpr int N = kM * N2;
     unsigned p;
@@ -273,26 +312,12 @@ __device__ __forceinline__ void issue_item(const FArgs& a, const F128Items& m, u
     item_pos<G>(m, a.Kc, item, p, f0, nv);
     const unsigned fpb = (unsigned)(a.bs / N);   // frames per data block
     const unsigned mf0 = (unsigned)(a.m_begin + f0), blk0 = mf0 / fpb, fb0 = mf0 - blk0 * fpb;
-    // frame g lies in block blk0 + (fb0 + g) / fpb: stepped, not divided
-    auto valid = [&](int g, unsigned blk) {
-        return g < nv && f0 + g < a.n_frames && (a.flags == nullptr || a.flags[(long long)blk * a.n + p] == 0);
-    };
-    unsigned mask = 0;
-    {
-        unsigned blk = blk0, fb = fb0;
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            if (valid(g, blk)) mask |= 1u << g;
-            if (++fb == fpb) {
-                fb = 0;
-                ++blk;
-            }
-        }
-    }
+    const unsigned mask = __ldg(&masks[item]);
     // the mask is published before the arrive (release): a waiter that sees the phase
-    // complete (at once when no frame is copied) reads this item's mask
+    // complete reads this item's mask
     *mask_out = mask;
-    tc::mbar_arrive_expect_tx(bar, (uint32_t)(__popc(mask) * 2 * N));
+    tc::mbar_arrive_expect_tx(bar, (uint32_t)(__popc(mask) * 2 * N) + (uint32_t)(G * sizeof(F128Frame)));
+    bulk_copy(terms, tab + (size_t)item * G, (uint32_t)(G * sizeof(F128Frame)), bar);
     // one copy per run of consecutive frames with data inside one block (contiguous there)
     unsigned blk = blk0, fb = fb0;
     int g_run = -1;
@@ -374,8 +399,8 @@ __device__ __forceinline__ void stage_p_task(const int8_t* stage, bool live, int
     }
 }
 
-// Frame terms of an item's frame g: operand slot and position, delay phasor terms (the FP64
-// delay polynomial or table, Sec. 4.3).
+// Frame terms of an item's frame g: the delay phasor terms (the FP64 delay polynomial or
+// table, Sec. 4.3).
 template <int N2, int G>
 __device__ __forceinline__ F128Frame frame_terms(const FArgs& a, const F128Items& m, unsigned item, int g)
 {
@@ -386,9 +411,6 @@ __device__ __forceinline__ F128Frame frame_terms(const FArgs& a, const F128Items
     item_pos<G>(m, a.Kc, item, p, f0, nv);
     const long long f = f0 + g;
     F128Frame fi;
-    const bool stored = g < nv && f < a.n_store;
-    fi.slot = stored ? f / a.Kc : -1;
-    fi.k = stored ? f % a.Kc : 0;
     fi.delay = 0;
     fi.phi0 = fi.d_hi = fi.d_lo = 0.0f;
     fi.step = make_float2(1.0f, 0.0f);
@@ -408,6 +430,20 @@ __device__ __forceinline__ F128Frame frame_terms(const FArgs& a, const F128Items
     return fi;
 }
 
+// Per launch, before the F kernel: every item's frame terms and mask, one thread per frame.
+// The FP64 work runs here at full occupancy; the F kernel's control thread copies an item's
+// terms into shared memory with its samples.
+template <int N2, int G>
+__global__ void __launch_bounds__(256) f128_terms_kernel(const FArgs a, const F128Items m)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)m.n_items * G) return;
+    const unsigned item = (unsigned)(e / G);
+    const int g = (int)(e - (long long)item * G);
+    m.tab[e] = frame_terms<N2, G>(a, m, item, g);
+    if (g == 0) m.masks[item] = item_mask<N2, G>(a, m, item);
+}
+
 template <int N2, int G>
 __global__ void __launch_bounds__(F128<N2, G>::T, 1) fstep_f128_kernel(const FArgs a, const F128Items m)
 {
@@ -422,8 +458,11 @@ __global__ void __launch_bounds__(F128<N2, G>::T, 1) fstep_f128_kernel(const FAr
     int8_t* stage = reinterpret_cast<int8_t*>(x_im + C::XPLANE);
     uint32_t* T = reinterpret_cast<uint32_t*>(stage + C::ST * C::STAGE);  // stage E tile [c][TS]
     float2* w2 = reinterpret_cast<float2*>(stage + C::ST * C::STAGE + C::TILE);   // W_N2^j, j < N2 (64 slots)
-    F128Frame* frs = reinterpret_cast<F128Frame*>(w2 + 64);      // frame terms, 3 items x G
-    F128Shared& S = *reinterpret_cast<F128Shared*>(frs + 3 * G);
+    // frame terms of ST + 2 items x G: items j .. j + ST + 1 are staged or in use while the
+    // CTA's j-th item is in stage E
+    F128Frame* frs = reinterpret_cast<F128Frame*>(w2 + 64);
+    constexpr int NFR = C::ST + 2;
+    F128Shared& S = *reinterpret_cast<F128Shared*>(frs + NFR * G);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr int kW = C::W, kT = C::T;
@@ -433,7 +472,8 @@ __global__ void __launch_bounds__(F128<N2, G>::T, 1) fstep_f128_kernel(const FAr
     // copy item `itj`, the j-th of this CTA, into stage buffer j mod ST
     auto issue_copy = [&](int j, unsigned itj) {
         const int b = j % C::ST;
-        issue_item<N2, G>(a, m, itj, stage + b * C::STAGE, &S.ld_bar[b], &S.ld_mask[b]);
+        issue_item<N2, G>(a, m, itj, stage + b * C::STAGE, &S.ld_bar[b], &S.ld_mask[b], m.masks, m.tab,
+                          frs + (j % NFR) * G);
         ++n_cp[b];
     };
 
@@ -463,7 +503,6 @@ __global__ void __launch_bounds__(F128<N2, G>::T, 1) fstep_f128_kernel(const FAr
             if (itj < m.n_items) issue_copy(j, itj);
         }
     }
-    if (tid >= kW && tid < kW + G && cur < m.n_items) frs[tid - kW] = frame_terms<N2, G>(a, m, cur, tid - kW);
     if (warp == 0) {
         tc::tmem_alloc(&S.tmem, 2 * kBufCols);
         tc::tmem_relinquish();
@@ -683,9 +722,9 @@ __global__ void __launch_bounds__(F128<N2, G>::T, 1) fstep_f128_kernel(const FAr
     }
 
     // ---- steady state, item `cur` in buffer it & 1.  Workers: wait for its MMAs, stage P of
-    // the next item; its frame terms on the workers or the control warp.  Barrier.  Then the control thread issues stage A of
-    // the next item and the copy of a later one (the control warp shares its scheduler with
-    // four worker warps, so its own work is kept short), and the workers run stage E of
+    // the next item.  Barrier.  Then the control thread issues stage A of the next item and
+    // the copy of a later one (samples and frame terms; the control warp shares its scheduler
+    // with four worker warps, so its own work is kept short), and the workers run stage E of
     // `cur`.
     int it = 0;
     for (; !stop && cur < m.n_items; cur += gridDim.x, ++it) {
@@ -699,16 +738,7 @@ __global__ void __launch_bounds__(F128<N2, G>::T, 1) fstep_f128_kernel(const FAr
                 if (status) atomicOr(status, 1024);
             }
             tc::fence_after();
-            if (!bad && nxt < m.n_items) {
-                // the next item's frame terms (FP64): with 16 worker warps one frame per warp on
-                // its lane 0 (the control warp shares its scheduler with four worker warps);
-                // with 8, on the control warp
-                if (C::W == 512 && lane == 0 && warp < G)
-                    frs[((it + 1) % 3) * G + warp] = frame_terms<N2, G>(a, m, nxt, warp);
-                stage_p(it + 1);
-            }
-        } else if (C::W != 512 && lane < G && nxt < m.n_items) {
-            frs[((it + 1) % 3) * G + lane] = frame_terms<N2, G>(a, m, nxt, lane);
+            if (!bad && nxt < m.n_items) stage_p(it + 1);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         tc::fence_before();
@@ -721,7 +751,7 @@ __global__ void __launch_bounds__(F128<N2, G>::T, 1) fstep_f128_kernel(const FAr
             if (itj < m.n_items) issue_copy(it + 1 + C::ST, itj);
         }
         if (worker) {
-            stage_e(it & 1, frs + (it % 3) * G);
+            stage_e(it & 1, frs + (it % NFR) * G);
             asm volatile("bar.sync 1, %0;" ::"n"(kW) : "memory");   // the worker warps' tile complete
             copy_out(cur);
         }
@@ -829,8 +859,9 @@ cudaError_t launch_f128(const FArgs& a, cudaStream_t s)
 {
     using C = F128<N2, G>;
     constexpr size_t smem = 2 * kFPlane + 2 * C::XPLANE + C::ST * C::STAGE + C::TILE + sizeof(float2) * 64 +
-                            3 * G * sizeof(F128Frame) + sizeof(F128Shared) + 128;
+                            (C::ST + 2) * G * sizeof(F128Frame) + sizeof(F128Shared) + 128;
     static_assert(smem <= 227 * 1024, "shared memory");
+    static_assert(G == f128_frames(C::N), "frames per item");
     static bool attr_done = false;
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(fstep_f128_kernel<N2, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -849,14 +880,20 @@ cudaError_t launch_f128(const FArgs& a, cudaStream_t s)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long grid = n_items < sms ? n_items : sms;
     const long long slot_elems = (long long)C::N * 2 * a.n * a.Kpad;
+    // behind the scratch tiles: the frame terms and masks of one launch
+    char* tail = static_cast<char*>(a.Yt) + f128_tiles_bytes(C::N, a.n, a.Kc);
     for (long long sl = 0; sl < slots; ++sl) {
         F128Items m;
         m.n_items = (unsigned)n_items;
         m.groups = (unsigned)groups;
         m.slot = (unsigned)sl;
-        fstep_f128_kernel<N2, G><<<(unsigned)grid, C::T, smem, s>>>(a, m);
+        m.tab = reinterpret_cast<F128Frame*>(tail);
+        m.masks = reinterpret_cast<unsigned*>(tail + (size_t)n_items * G * sizeof(F128Frame));
+        f128_terms_kernel<N2, G><<<(unsigned)((n_items * G + 255) / 256), 256, 0, s>>>(a, m);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
+        fstep_f128_kernel<N2, G><<<(unsigned)grid, C::T, smem, s>>>(a, m);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const long long left = a.n_store - sl * a.Kc;
         const int kn = (int)(left < a.Kc ? left : a.Kc);   // frames stored in this slot
         constexpr int TRC = G >= 8 ? 32 : 64, TRK = kTrWords / TRC;   // channels, frames per transpose tile
@@ -875,8 +912,9 @@ bool fstep_f128_supported(int N) { return N == 1280 || N == 6400; }
 
 size_t fstep_f128_scratch_bytes(int N, int n, long long Kc)
 {
-    const int G = N == 1280 ? 8 : 2;
-    return (size_t)n * (size_t)((Kc + G - 1) / G) * G * (size_t)N * 4;
+    const int G = f128_frames(N);
+    const size_t items = (size_t)n * (size_t)((Kc + G - 1) / G);
+    return f128_tiles_bytes(N, n, Kc) + items * (G * sizeof(F128Frame) + sizeof(unsigned));
 }
 
 cudaError_t launch_fstep_f128(int N, int out_kind, const FArgs& a, cudaStream_t s)

@@ -11,11 +11,14 @@
 // contiguous bytes of one operand row.
 //
 // A persistent CTA (16 worker warps and a control warp, one CTA per SM) loops over the items,
-// software-pipelined as the 128-row F-step: the control warp copies item j + 2's samples in
-// (bulk copies, one per run of frames within a data block) and issues item j + 1's MMAs
-// into the other half of tensor memory while the workers compute item j + 1's frame terms
-// and convert its samples, then run the epilogue of item j; one CTA barrier per item.  Every
-// wait is bounded.
+// software-pipelined as the 128-row F-step: the control warp copies item j + 3's samples
+// and frame terms in (bulk copies, one per run of frames within a data block; two stage
+// buffers, so each copy has two items' time to land) and issues item j + 1's MMAs into the
+// other half of tensor memory while the workers convert item j + 1's samples, then run the
+// epilogue of item j; one CTA barrier per item.  Every wait is
+// bounded.  The frames' delay terms (FP64) come from a small kernel launched first: inside
+// this one they held every item's barrier (one warp's FP64 sequence on this GPU's narrow
+// FP64 pipe).
 #include "mwax_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -25,6 +28,10 @@ namespace mwax {
 namespace {
 
 constexpr int kF = 128;              // frames per item (MMA M, tensor-memory lanes)
+// int8 stage buffers: with one, each copy was issued one item ahead and the workers waited
+// on it for over a third of the item
+constexpr int kST = 2;
+constexpr int kNFR = kST + 2;        // frame-term slots: items j .. j + kST + 1
 constexpr int kW = 512;              // worker threads (4 warps per lane quarter)
 constexpr int kT = kW + 32;          // plus the control warp
 
@@ -44,18 +51,19 @@ struct FD {
     static_assert(TASKS % kW == 0, "whole conversion tasks per thread");
 };
 
-struct FDFrame {
+struct FDTerm {
     long long base;          // element of (slot, c = 0, re plane, p, k) or -1: not stored
     float phi0, d_hi, d_lo;  // delay terms: the phasor of bin offset u is e^{2 pi i (phi0 + u d)}
     int delay;
     float2 step;             // e^{2 pi i d}: phasor ratio between bins k and k + 1
 };
+static_assert(sizeof(FDTerm) == 32, "frame terms: 32 bytes (an item's 128 travel by bulk copy)");
 
 struct FDShared {
-    uint64_t ld_bar;         // an item's int8 frames staged
+    uint64_t ld_bar[kST];    // an item's int8 frames staged, per stage buffer
     uint64_t bar;            // an item's MMAs complete
     uint64_t drained;        // after an abort: every MMA issued has completed
-    unsigned mask[kF / 32];  // frames of the staged item with data
+    unsigned mask[kST][kF / 32];   // frames of the staged item with data, per stage buffer
     uint32_t tmem;
     int abort;
 };
@@ -120,25 +128,27 @@ __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, const
 }
 
 // Issue the copies of an item's frames: one bulk copy per run of frames with data inside
-// one data block (frames never straddle blocks: a block is a multiple of N samples).  The
-// mask of frames copied is published before the arrive (a waiter that sees the phase
-// complete reads this item's mask); the other frames are read as zero.  One thread.
+// one data block (frames never straddle blocks: a block is a multiple of N samples), and of
+// its 128 frame terms (fd_terms_kernel), on one mbarrier transaction.  The mask of frames
+// copied is published before the arrive (a waiter that sees the phase complete reads this
+// item's mask); the other frames are read as zero.  One thread.
 template <int N>
 __device__ __forceinline__ void issue_item(const FArgs& a, unsigned item, unsigned n_fg, int8_t* stage,
-                                           uint64_t* bar, unsigned* mask_out)
+                                           uint64_t* bar, unsigned* mask_out, const FDTerm* tab, FDTerm* terms)
 {
+    // frame numbers below 2^31 (launcher): 32-bit division
     const unsigned p = item / n_fg;
-    const long long f0 = (long long)(item - p * n_fg) * kF;
-    const long long fpb = a.bs / N;   // frames per data block
-    long long fend = f0 + kF < a.n_frames ? f0 + kF : a.n_frames;
+    const unsigned f0 = (item - p * n_fg) * (unsigned)kF, mb = (unsigned)a.m_begin;
+    const unsigned fpb = (unsigned)(a.bs / N);   // frames per data block
+    const unsigned fend = (long long)f0 + kF < a.n_frames ? f0 + kF : (unsigned)a.n_frames;
     unsigned m0 = 0u, m1 = 0u, m2 = 0u, m3 = 0u;   // frames with data (bits of frames 0..127)
     uint32_t bytes = 0;
     // first pass: the runs and the mask; second pass: the copies (after the arrive)
-    for (long long f = f0; f < fend;) {
-        const long long mf = a.m_begin + f, blk = mf / fpb;
-        long long run = (blk + 1) * fpb - a.m_begin;   // first frame of the next block
+    for (unsigned f = f0; f < fend;) {
+        const unsigned mf = mb + f, blk = mf / fpb;
+        unsigned run = (blk + 1) * fpb - mb;   // first frame of the next block
         if (run > fend) run = fend;
-        if (a.flags == nullptr || a.flags[blk * a.n + p] == 0) {
+        if (a.flags == nullptr || a.flags[(long long)blk * a.n + p] == 0) {
             const int lo = (int)(f - f0), hi = (int)(run - f0);   // frames [lo, hi) of the item
             auto bits = [&](int w) {
                 const int a0 = max(lo - 32 * w, 0), a1 = min(hi - 32 * w, 32);
@@ -155,13 +165,14 @@ __device__ __forceinline__ void issue_item(const FArgs& a, unsigned item, unsign
     const unsigned mask[kF / 32] = {m0, m1, m2, m3};
 #pragma unroll
     for (int i = 0; i < kF / 32; ++i) mask_out[i] = mask[i];
-    tc::mbar_arrive_expect_tx(bar, bytes);
-    for (long long f = f0; f < fend;) {
-        const long long mf = a.m_begin + f, blk = mf / fpb;
-        long long run = (blk + 1) * fpb - a.m_begin;
+    tc::mbar_arrive_expect_tx(bar, bytes + (uint32_t)(kF * sizeof(FDTerm)));
+    bulk_copy(terms, tab + (size_t)item * kF, (uint32_t)(kF * sizeof(FDTerm)), bar);
+    for (unsigned f = f0; f < fend;) {
+        const unsigned mf = mb + f, blk = mf / fpb;
+        unsigned run = (blk + 1) * fpb - mb;
         if (run > fend) run = fend;
-        if (a.flags == nullptr || a.flags[blk * a.n + p] == 0) {
-            const long long src = ((blk * a.n + p) * (long long)a.bs + (mf - blk * fpb) * N) * 2;
+        if (a.flags == nullptr || a.flags[(long long)blk * a.n + p] == 0) {
+            const long long src = (((long long)blk * a.n + p) * (long long)a.bs + (long long)(mf - blk * fpb) * N) * 2;
             bulk_copy(stage + (f - f0) * 2 * N, a.volt + src, (uint32_t)((run - f) * 2 * N), bar);
         }
         f = run;
@@ -171,19 +182,19 @@ __device__ __forceinline__ void issue_item(const FArgs& a, unsigned item, unsign
 // Frame terms of frame g of an item: its operand position and delay phasor terms (the FP64
 // delay polynomial or table, Sec. 4.3).
 template <int N>
-__device__ __forceinline__ FDFrame frame_terms(const FArgs& a, unsigned item, unsigned n_fg, int g)
+__device__ __forceinline__ FDTerm frame_terms(const FArgs& a, unsigned item, unsigned n_fg, int g)
 {
     const unsigned p = item / n_fg;
     const long long f = (long long)(item - p * n_fg) * kF + g;
-    FDFrame fi;
+    FDTerm fi;
     fi.base = -1;
     if (f < a.n_store) {
         const long long slot = f / a.Kc, k = f % a.Kc;
         fi.base = (slot * N * 2LL * a.n + p) * a.Kpad + k;
     }
+    fi.step = make_float2(1.0f, 0.0f);
     fi.delay = 0;
     fi.phi0 = fi.d_hi = fi.d_lo = 0.0f;
-    fi.step = make_float2(1.0f, 0.0f);
     if ((a.delay != nullptr || a.delay_tab != nullptr) && f < a.n_frames) {
         const double tau = frame_delay(a, (int)p, a.m_begin + f, N);
         const double ph = a.nu * tau;
@@ -198,6 +209,17 @@ __device__ __forceinline__ FDFrame frame_terms(const FArgs& a, unsigned item, un
     return fi;
 }
 
+// Before the F kernel: the delay terms of every frame of the launch, one thread per frame,
+// into the table a.Yt [item][128].
+template <int N>
+__global__ void __launch_bounds__(256) fd_terms_kernel(const FArgs a, unsigned n_items, unsigned n_fg)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)n_items * kF) return;
+    const unsigned item = (unsigned)(e / kF);
+    static_cast<FDTerm*>(a.Yt)[e] = frame_terms<N>(a, item, n_fg, (int)(e - (long long)item * kF));
+}
+
 template <int N, bool E4M3>
 __global__ void __launch_bounds__(kT, 1) fstep_fd_kernel(const FArgs a, unsigned n_items, unsigned n_fg)
 {
@@ -208,16 +230,25 @@ __global__ void __launch_bounds__(kT, 1) fstep_fd_kernel(const FArgs a, unsigned
     unsigned char* f_im = f_re + C::BPLANE;
     unsigned char* x_re = f_im + C::BPLANE;      // the item's samples (A: rows g, K = n)
     unsigned char* x_im = x_re + C::APLANE;
-    int8_t* stage = reinterpret_cast<int8_t*>(x_im + C::APLANE);
-    FDFrame* frs = reinterpret_cast<FDFrame*>(stage + C::STAGE);   // frame terms, 3 items x 128
-    FDShared& S = *reinterpret_cast<FDShared*>(frs + 3 * kF);
+    int8_t* stage = reinterpret_cast<int8_t*>(x_im + C::APLANE);   // kST buffers
+    // frame terms of kNFR items x 128: the CTA's j-th item in slot j mod kNFR (item j in
+    // stage E, j + 1 converted, j + 2 and j + 3 staged or being copied)
+    FDTerm* frs = reinterpret_cast<FDTerm*>(stage + kST * C::STAGE);
+    const FDTerm* tab = static_cast<const FDTerm*>(a.Yt);
+    FDShared& S = *reinterpret_cast<FDShared*>(frs + kNFR * kF);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool worker = tid < kW, ctl = tid == kW;
     int* status = a.status;
+    unsigned n_cp[kST] = {0u, 0u};   // copies issued per stage buffer (control thread)
+    // copy the CTA's j-th item `itj` into stage buffer j mod kST
+    auto issue_copy = [&](int j, unsigned itj) {
+        const int b = j % kST;
+        issue_item<N>(a, itj, n_fg, stage + b * C::STAGE, &S.ld_bar[b], S.mask[b], tab, frs + (j % kNFR) * kF);
+        ++n_cp[b];
+    };
 
-    // ---- set-up: the DFT matrix, barriers, tensor memory, the first item's copy and frame
-    // terms
+    // ---- set-up: the DFT matrix, barriers, tensor memory, the first kST items' copies
     // row k carries the gain of its output channel c(k) = fftshift(k): the product is the
     // gained spectrum
     for (int e = tid; e < N * N; e += kT) {
@@ -231,14 +262,16 @@ __global__ void __launch_bounds__(kT, 1) fstep_fd_kernel(const FArgs a, unsigned
     }
     unsigned cur = blockIdx.x;
     if (ctl) {
-        tc::mbar_init(&S.ld_bar, 1);
+        for (int b = 0; b < kST; ++b) tc::mbar_init(&S.ld_bar[b], 1);
         tc::mbar_init(&S.bar, 1);
         tc::mbar_init(&S.drained, 1);
         S.abort = 0;
         tc::fence_mbar_init();
-        if (cur < n_items) issue_item<N>(a, cur, n_fg, stage, &S.ld_bar, S.mask);
+        for (int j = 0; j < kST; ++j) {
+            const unsigned itj = cur + (unsigned)j * gridDim.x;
+            if (itj < n_items) issue_copy(j, itj);
+        }
     }
-    if (tid < kF && cur < n_items) frs[tid] = frame_terms<N>(a, cur, n_fg, tid);
     if (warp == 0) {
         tc::tmem_alloc(&S.tmem, C::TMEM);
         tc::tmem_relinquish();
@@ -249,26 +282,28 @@ __global__ void __launch_bounds__(kT, 1) fstep_fd_kernel(const FArgs a, unsigned
     const uint32_t tmem = S.tmem;
     const int q = warp & 3, h = (warp >> 2) & 3;   // lane quarter; quarter of the bins
     const int g = 32 * q + lane;                   // a worker lane's frame
-    uint32_t ld_par = 0, mma_par = 0;
-    unsigned n_copies = cur < n_items ? 1u : 0u;   // copies issued (control thread)
+    uint32_t mma_par = 0;
     bool bad = false, stop = false, issued = false;
 
-    // conversion of the staged item (workers): 8 samples of one frame per task, FP16 rows
-    auto stage_p = [&]() {
-        if (!wait_phase(&S.ld_bar, ld_par, &S.abort)) {
+    // conversion of the CTA's j-th item (workers; stage buffer j mod kST, its (j / kST)-th
+    // copy): 8 samples of one frame per task, FP16 rows
+    auto stage_p = [&](int ji) {
+        const int bs = ji % kST;
+        if (!wait_phase(&S.ld_bar[bs], (uint32_t)(ji / kST) & 1u, &S.abort)) {
             bad = true;
             S.abort = 1;
             if (status) atomicOr(status, 2048);
             return;
         }
-        ld_par ^= 1u;
+        const unsigned* mk = S.mask[bs];
+        const int8_t* sb = stage + bs * C::STAGE;
 #pragma unroll
         for (int i = 0; i < C::TASKS / kW; ++i) {
             const int t = tid + kW * i;
             const int j = t % (N / 8), fr = t / (N / 8);
             uint32_t wr[4] = {0u, 0u, 0u, 0u}, wi[4] = {0u, 0u, 0u, 0u};
-            if ((S.mask[fr >> 5] >> (fr & 31)) & 1u) {
-                const uint4 raw = *reinterpret_cast<const uint4*>(stage + fr * 2 * N + 16 * j);
+            if ((mk[fr >> 5] >> (fr & 31)) & 1u) {
+                const uint4 raw = *reinterpret_cast<const uint4*>(sb + fr * 2 * N + 16 * j);
                 const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};   // (re, im) int8 of 2 samples each
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
@@ -309,9 +344,9 @@ __global__ void __launch_bounds__(kT, 1) fstep_fd_kernel(const FArgs a, unsigned
     // the epilogue of an item (workers): lane = frame g, bins k of this warp's quarter (the
     // upper half is u = k - N); phasor recurrence along the bins, conversion, stores
     // (the bins of a quarter are consecutive channels: one pointer step per bin)
-    auto stage_e = [&](int buf, const FDFrame* fr) {
+    auto stage_e = [&](int buf, const FDTerm* fr) {
         constexpr int QB = C::QB;
-        const FDFrame fi = fr[g];
+        const FDTerm fi = fr[g];
         const bool live = fi.base >= 0;
         const bool upper = h >= 2;                       // k >= N/2: u = k - N, c = k - N/2
         const int k0 = h * QB;
@@ -360,19 +395,17 @@ __global__ void __launch_bounds__(kT, 1) fstep_fd_kernel(const FArgs a, unsigned
         }
     };
 
-    // ---- prologue: conversion and MMAs of the first item, the copy of the second
-    if (worker && cur < n_items) stage_p();
+    // ---- prologue: conversion and MMAs of the first item, the copy of item kST into the
+    // buffer the first has left
+    if (worker && cur < n_items) stage_p(0);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // A operand: generic writes, MMA reads
     tc::fence_before();
     stop = __syncthreads_or(bad);
     if (!stop && ctl && cur < n_items) {
         tc::fence_after();
         stage_a(0);
-        const unsigned nxt = cur + gridDim.x;
-        if (nxt < n_items) {
-            issue_item<N>(a, nxt, n_fg, stage, &S.ld_bar, S.mask);
-            ++n_copies;
-        }
+        const unsigned itj = cur + (unsigned)kST * gridDim.x;
+        if (itj < n_items) issue_copy(kST, itj);
     }
 
     // ---- steady state, item `cur` in buffer it & 1 (as the 128-row F-step)
@@ -388,12 +421,7 @@ __global__ void __launch_bounds__(kT, 1) fstep_fd_kernel(const FArgs a, unsigned
                 if (status) atomicOr(status, 1024);
             }
             tc::fence_after();
-            if (!bad && nxt < n_items) {
-                // the next item's frame terms (FP64 delay polynomial: one frame per thread of
-                // the first four warps), then its conversion
-                if (tid < kF) frs[((it + 1) % 3) * kF + tid] = frame_terms<N>(a, nxt, n_fg, tid);
-                stage_p();
-            }
+            if (!bad && nxt < n_items) stage_p(it + 1);   // the next item's conversion
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         tc::fence_before();
@@ -401,24 +429,23 @@ __global__ void __launch_bounds__(kT, 1) fstep_fd_kernel(const FArgs a, unsigned
         tc::fence_after();
         if (ctl && nxt < n_items) {
             stage_a((it + 1) & 1);
-            const unsigned nn = nxt + gridDim.x;
-            if (nn < n_items) {
-                issue_item<N>(a, nn, n_fg, stage, &S.ld_bar, S.mask);
-                ++n_copies;
-            }
+            // item it + 1 + kST into the buffer item it + 1 has just left
+            const unsigned itj = nxt + (unsigned)kST * gridDim.x;
+            if (itj < n_items) issue_copy(it + 1 + kST, itj);
         }
-        if (worker) stage_e(it & 1, frs + (it % 3) * kF);
+        if (worker) stage_e(it & 1, frs + (it % kNFR) * kF);
     }
 
-    // ---- wind-down: after an abort the MMAs and the bulk copy in flight finish before the
-    // CTA releases its tensor memory and exits (at most one copy is ever in flight)
+    // ---- wind-down: after an abort the MMAs and the bulk copies in flight finish before the
+    // CTA releases its tensor memory and exits (at most one copy per stage buffer)
     if (ctl && stop) {
         if (issued) {
             tc::mma_commit(&S.drained);
             if (!tc::wait_bounded(&S.drained, 0u, tc::kDrainCycles) && status) atomicOr(status, tc::kDrainGaveUp);
         }
-        if (n_copies > 0 && !tc::wait_bounded(&S.ld_bar, (n_copies - 1) & 1u, tc::kDrainCycles) && status)
-            atomicOr(status, tc::kDrainGaveUp);
+        for (int b = 0; b < kST; ++b)
+            if (n_cp[b] > 0 && !tc::wait_bounded(&S.ld_bar[b], (n_cp[b] - 1) & 1u, tc::kDrainCycles) && status)
+                atomicOr(status, tc::kDrainGaveUp);
     }
     tc::fence_before();
     __syncthreads();
@@ -432,7 +459,7 @@ template <int N, bool E4M3>
 cudaError_t launch_fd(const FArgs& a, cudaStream_t s)
 {
     using C = FD<N>;
-    constexpr size_t smem = 2 * C::BPLANE + 2 * C::APLANE + C::STAGE + 3 * kF * sizeof(FDFrame) +
+    constexpr size_t smem = 2 * C::BPLANE + 2 * C::APLANE + kST * C::STAGE + kNFR * kF * sizeof(FDTerm) +
                             sizeof(FDShared) + 128;
     static_assert(smem <= 227 * 1024, "shared memory");
     static bool attr_done = false;
@@ -445,16 +472,29 @@ cudaError_t launch_fd(const FArgs& a, cudaStream_t s)
     if (a.bs % N != 0 || a.ktile != 0) return cudaErrorInvalidValue;
     const long long n_fg = (a.n_store + kF - 1) / kF, n_items = (long long)a.n * n_fg;
     if (n_items <= 0) return cudaSuccess;
-    if (n_items >= (1LL << 31)) return cudaErrorInvalidValue;
+    // the frame-term table in the scratch; frame numbers below 2^31 (32-bit block arithmetic)
+    if (n_items >= (1LL << 31) || a.Kc <= 0 || a.Yt == nullptr || a.m_begin + a.n_frames >= (1LL << 31) ||
+        n_fg * kF >= (1LL << 31) ||
+        (size_t)a.Yt_bytes < fstep_fd_scratch_bytes(N, a.n, a.n_store))
+        return cudaErrorInvalidValue;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long grid = n_items < sms ? n_items : sms;
+    fd_terms_kernel<N><<<(unsigned)((n_items * kF + 255) / 256), 256, 0, s>>>(a, (unsigned)n_items, (unsigned)n_fg);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     fstep_fd_kernel<N, E4M3><<<(unsigned)grid, kT, smem, s>>>(a, (unsigned)n_items, (unsigned)n_fg);
     return cudaGetLastError();
 }
 
 }  // namespace
+
+size_t fstep_fd_scratch_bytes(int N, int n, long long n_store)
+{
+    (void)N;
+    return (size_t)n * (size_t)((n_store + kF - 1) / kF) * kF * sizeof(FDTerm);
+}
 
 bool fstep_fd_supported(int N, int out_kind)
 {

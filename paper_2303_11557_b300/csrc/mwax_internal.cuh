@@ -81,8 +81,9 @@ struct FArgs {
     double fs_over_n;          // fs / N: frames per second
     int* status;               // device status word of the kernels with bounded waits (tensor-core
                                //   F-step), or nullptr
-    void* Yt;                  // 128-row tensor-core F-step: frame-major scratch of one slot
-                               //   (fstep_f128_scratch_bytes), or nullptr
+    void* Yt;                  // F-step scratch: variant 3, frame-major spectra of one slot and
+                               //   the frame terms (fstep_f128_scratch_bytes); variant 4, the
+                               //   frame terms (fstep_fd_scratch_bytes); or nullptr
     long long Yt_bytes;
 };
 
@@ -172,8 +173,10 @@ bool fstep_f128_supported(int N);
 size_t fstep_f128_scratch_bytes(int N, int n, long long Kc);
 cudaError_t launch_fstep_f128(int N, int out_kind, const FArgs& a, cudaStream_t s);
 // The tensor-core direct-DFT F-step with the frames on the accumulator lanes (variant 4),
-// N = 32, 64, 128, FP16 or e4m3 output.
+// N = 32, 64, 128, FP16 or e4m3 output; it needs the scratch a.Yt of fstep_fd_scratch_bytes
+// for a launch of n_store frames (the frames' delay terms).
 bool fstep_fd_supported(int N, int out_kind);
+size_t fstep_fd_scratch_bytes(int N, int n, long long n_store);
 cudaError_t launch_fstep_fd(int N, int out_kind, const FArgs& a, cudaStream_t s);
 // The tensor-core direct-DFT F-step, N = 32, 64, 128 (FP32, FP16 or FP16 hi/lo output).
 bool fstep_dft_supported(int N, int out_kind);

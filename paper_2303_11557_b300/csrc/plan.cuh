@@ -30,7 +30,8 @@ struct mwax_plan {
     // device memory
     void* Y = nullptr;      // X-step operands (FP8: e4m3)
     void* Y16 = nullptr;    // FP8 only: the FP16 operands the e4m3 ones are quantised from
-    void* Yt = nullptr;     // F-step variant 3 only: frame-major scratch of one slot
+    void* Yt = nullptr;     // F-step variants 3 and 4: their scratch (frame terms; variant 3
+                            //   also the frame-major spectra of one slot)
     size_t Yt_bytes = 0;
     size_t Y_bytes = 0;
     float2* tw = nullptr;
@@ -124,7 +125,7 @@ mwax_status enqueue_xstep_single(mwax_plan* p, const LaunchGroup& g, const XArgs
 void plan_items(const mwax_plan& p, int job, long long nslots, long long klen,
                 std::vector<std::pair<double, XItem>>& out);
 // F-step variant 3: allocate its scratch (once; set-up time, never inside a call).
-mwax_status ensure_f128_scratch(mwax_plan* p);
+mwax_status ensure_fstep_scratch(mwax_plan* p, int variant);
 // Integer mode: samples per K segment of the tensor-core X-step (one work item each).
 long long int8_seg_frames(long long klen);
 void sort_items(std::vector<std::pair<double, XItem>>& v, std::vector<XItem>& order);

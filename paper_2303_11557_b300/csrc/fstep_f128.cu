@@ -33,6 +33,7 @@
 #include "tc_ptx.cuh"
 
 #include <algorithm>
+#include <cstring>
 
 namespace mwax {
 namespace {
@@ -61,7 +62,7 @@ struct F128 {
     static constexpr uint32_t STAGE = G * 2 * N;              // int8 (re, im) of the item's frames
     // int8 stage buffers: two at N = 1280 (a short item's copy, issued one item ahead, did
     // not land in time: the workers waited on it for a third of the item), one at N = 6400
-    // (its longer items hide the copy; shared memory is full)
+    // (its longer items hide the copy: a second buffer measured 3 % slower)
     static constexpr int ST = N2 == 10 ? 2 : 1;
     // stage P: one thread per sample n1 of a frame, or per pair (n1, n1 + 1) when there
     // are enough pairs for every thread (4-byte stores)
@@ -444,8 +445,12 @@ __global__ void __launch_bounds__(256) f128_terms_kernel(const FArgs a, const F1
     if (g == 0) m.masks[item] = item_mask<N2, G>(a, m, item);
 }
 
+// Rows (channels) per tensor-store box of an item's tile (padded tiles, N = 1280).
+constexpr int kTileRows = 256;
+
 template <int N2, int G>
-__global__ void __launch_bounds__(F128<N2, G>::T, 1) fstep_f128_kernel(const FArgs a, const F128Items m)
+__global__ void __launch_bounds__(F128<N2, G>::T, 1)
+    fstep_f128_kernel(const FArgs a, const F128Items m, const __grid_constant__ CUtensorMap tm_tile)
 {
     using C = F128<N2, G>;
     constexpr int N = C::N, H = C::H, HS = C::HS, NA = C::NA;
@@ -690,8 +695,19 @@ __global__ void __launch_bounds__(F128<N2, G>::T, 1) fstep_f128_kernel(const FAr
         else stage_e_split(buf, fr);
     };
 
-    // the tile of an item into its scratch tile Yt[c][g] (worker threads; 16-byte copies,
-    // a warp writing 512 contiguous bytes)
+    // the tile of an item into its scratch tile Yt[c][g].  The padded tile (N = 1280): tensor
+    // stores by the bulk-copy engine (one worker thread, after the workers' fence and
+    // barrier) whose boxes end past the rows, so the padding is not written; the workers go
+    // on to the next item.  The dense tile (N = 6400): the worker threads, 16-byte copies, a
+    // warp writing 512 contiguous bytes (one 51 KB bulk store per item measured 9 % slower over
+    // the F-step, the stores draining long after the item loop; 16 bulk stores of 3.2 KB, 1.5 %).
+    constexpr bool kTmaTile = C::TS != G;
+    auto store_tile = [&](unsigned item) {
+#pragma unroll
+        for (int i = 0; i < N / kTileRows; ++i)
+            tc::tma_store_2d(&tm_tile, T + i * kTileRows * C::TS, 0, (int)(item * (unsigned)N) + i * kTileRows);
+        tc::bulk_commit();
+    };
     auto copy_out = [&](unsigned item) {
         uint4* dst = reinterpret_cast<uint4*>(static_cast<uint32_t*>(a.Yt) + (size_t)item * N * G);
         for (int q = tid; q < N * G / 4; q += kW) {
@@ -741,6 +757,7 @@ __global__ void __launch_bounds__(F128<N2, G>::T, 1) fstep_f128_kernel(const FAr
             if (!bad && nxt < m.n_items) stage_p(it + 1);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (kTmaTile && tid == 0) tc::bulk_wait_read_all();   // the last tile read out: stage E may rewrite it
         tc::fence_before();
         if ((stop = __syncthreads_or(bad))) break;
         tc::fence_after();
@@ -752,8 +769,13 @@ __global__ void __launch_bounds__(F128<N2, G>::T, 1) fstep_f128_kernel(const FAr
         }
         if (worker) {
             stage_e(it & 1, frs + (it % NFR) * G);
+            if constexpr (kTmaTile) tc::fence_proxy_async();
             asm volatile("bar.sync 1, %0;" ::"n"(kW) : "memory");   // the worker warps' tile complete
-            copy_out(cur);
+            if constexpr (kTmaTile) {
+                if (tid == 0) store_tile(cur);
+            } else {
+                copy_out(cur);
+            }
         }
     }
 
@@ -768,6 +790,7 @@ __global__ void __launch_bounds__(F128<N2, G>::T, 1) fstep_f128_kernel(const FAr
             if (n_cp[b] > 0 && !tc::wait_bounded(&S.ld_bar[b], (n_cp[b] - 1) & 1u, tc::kDrainCycles) && status)
                 atomicOr(status, tc::kDrainGaveUp);
     }
+    if (kTmaTile && tid == 0) tc::bulk_wait_all();   // the tile stores complete before the CTA exits
     tc::fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -873,8 +896,16 @@ cudaError_t launch_f128(const FArgs& a, cudaStream_t s)
     if (a.n_store <= 0 || a.n <= 0) return cudaSuccess;
     const long long groups = (a.Kc + G - 1) / G, slots = (a.n_store + a.Kc - 1) / a.Kc;
     const long long n_items = (long long)a.n * groups;
-    if (n_items >= (1LL << 31) || (size_t)a.Yt_bytes < fstep_f128_scratch_bytes(C::N, a.n, a.Kc))
+    // tile rows (item x N) are 32-bit tensor coordinates
+    if (n_items * C::N >= (1LL << 31) || (size_t)a.Yt_bytes < fstep_f128_scratch_bytes(C::N, a.n, a.Kc))
         return cudaErrorInvalidValue;
+    CUtensorMap tm_tile;
+    memset(&tm_tile, 0, sizeof tm_tile);
+    if constexpr (C::TS != G) {
+        static_assert(C::N % kTileRows == 0 && (C::TS * 4) % 16 == 0, "tile boxes");
+        cudaError_t e = make_rows_tmap(&tm_tile, a.Yt, G, n_items * C::N, C::TS, kTileRows);
+        if (e != cudaSuccess) return e;
+    }
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -892,7 +923,7 @@ cudaError_t launch_f128(const FArgs& a, cudaStream_t s)
         f128_terms_kernel<N2, G><<<(unsigned)((n_items * G + 255) / 256), 256, 0, s>>>(a, m);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        fstep_f128_kernel<N2, G><<<(unsigned)grid, C::T, smem, s>>>(a, m);
+        fstep_f128_kernel<N2, G><<<(unsigned)grid, C::T, smem, s>>>(a, m, tm_tile);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const long long left = a.n_store - sl * a.Kc;
         const int kn = (int)(left < a.Kc ? left : a.Kc);   // frames stored in this slot

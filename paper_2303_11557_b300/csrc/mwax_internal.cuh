@@ -210,6 +210,8 @@ int simt_resident_ctas();   // CTAs of the FP32 X-step resident per SM
 // FP32 operand planes for the CUDA-core X-step: 32 frames x 64 rows x both planes per box,
 // 128-byte swizzle.
 cudaError_t make_simt_tmap(CUtensorMap* map, const void* Y, long long Kpad, int n, long long planes);
+cudaError_t make_rows_tmap(CUtensorMap* map, const void* base, int row_words, long long rows, int box_words,
+                           int box_rows);
 cudaError_t make_operand_tmap(CUtensorMap* map, const void* Y, int elem_bytes, long long Kpad, int n,
                               long long planes);
 cudaError_t launch_xstep_tc(const XLaunch& L, const XItem* items, int n_items, int* counter, int* status,

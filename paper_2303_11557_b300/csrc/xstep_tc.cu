@@ -710,6 +710,25 @@ cudaError_t make_operand_tmap(CUtensorMap* map, const void* Y, int elem_bytes, l
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// Tensor map over `rows` rows of `row_words` 32-bit words (rows contiguous), box
+// (box_words, box_rows), no swizzle.  A box wider than the rows is allowed for stores: the
+// words past a row's end are outside the tensor and not written (a padded shared tile
+// stored into dense rows).
+cudaError_t make_rows_tmap(CUtensorMap* map, const void* base, int row_words, long long rows, int box_words,
+                           int box_rows)
+{
+    auto fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    cuuint64_t dims[2] = {(cuuint64_t)row_words, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)row_words * 4};
+    cuuint32_t box[2] = {(cuuint32_t)box_words, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 cudaError_t make_simt_tmap(CUtensorMap* map, const void* Y, long long Kpad, int n, long long planes)
 {
     auto fn = encode_fn();

@@ -605,17 +605,22 @@ cudaEvent_t take_event(mwax_plan* p)
     return e;
 }
 
-// Bracket one launch of `stage` with events when timing is on; count it either way.
+// Bracket one launch of `stage` with events when timing is on; count its kernels either way.
 template <typename F>
 cudaError_t timed(mwax_plan* p, int stage, cudaStream_t s, F&& launch)
 {
-    p->launches[stage] += 1;
-    if (!p->timing) return launch();
-    cudaEvent_t a = take_event(p), b = take_event(p);
-    cudaEventRecord(a, s);
-    cudaError_t e = launch();
-    cudaEventRecord(b, s);
-    p->ev_used.push_back({stage, {a, b}});
+    const long long x0 = extra_launches();
+    cudaError_t e;
+    if (!p->timing) {
+        e = launch();
+    } else {
+        cudaEvent_t a = take_event(p), b = take_event(p);
+        cudaEventRecord(a, s);
+        e = launch();
+        cudaEventRecord(b, s);
+        p->ev_used.push_back({stage, {a, b}});
+    }
+    p->launches[stage] += 1 + (extra_launches() - x0);
     return e;
 }
 
@@ -723,6 +728,13 @@ mwax_status host_call(mwax_plan* p, const int8_t* volt, const double* delay_poly
 namespace mwax {
 
 mwax_status set_error(mwax_status st, const char* msg) { return fail(st, "%s", msg); }
+
+namespace {
+thread_local long long t_extra_launches = 0;
+}
+
+void count_extra_launches(long long k) { t_extra_launches += k; }
+long long extra_launches() { return t_extra_launches; }
 
 mwax_status cuda_error(cudaError_t e, const char* what)
 {

@@ -933,6 +933,7 @@ cudaError_t launch_f128(const FArgs& a, cudaStream_t s)
         f128_transpose_kernel<G, TRC, E4M3><<<(unsigned)tiles, 256, 0, s>>>(static_cast<const uint32_t*>(a.Yt), ys, C::N,
                                                                            a.n, a.Kpad, (unsigned)groups, kn);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        count_extra_launches(sl == 0 ? 2 : 3);   // frame terms, F kernel, transpose per slot
     }
     return cudaSuccess;
 }

@@ -179,19 +179,25 @@ __device__ __forceinline__ void issue_item(const FArgs& a, unsigned item, unsign
     }
 }
 
+// Operand position of frame g of an item (frame numbers below 2^31: 32-bit division).
+template <int N>
+__device__ __forceinline__ long long frame_base(const FArgs& a, unsigned item, unsigned n_fg, int g)
+{
+    const unsigned p = item / n_fg, f = (item - p * n_fg) * (unsigned)kF + (unsigned)g;
+    if ((long long)f >= a.n_store) return -1;
+    const unsigned kc = (unsigned)a.Kc, slot = f / kc, k = f - slot * kc;
+    return ((long long)slot * N * 2LL * a.n + p) * a.Kpad + k;
+}
+
 // Frame terms of frame g of an item: its operand position and delay phasor terms (the FP64
-// delay polynomial or table, Sec. 4.3).
+// delay polynomial or table, Sec. 4.3), one frame at a time.
 template <int N>
 __device__ __forceinline__ FDTerm frame_terms(const FArgs& a, unsigned item, unsigned n_fg, int g)
 {
     const unsigned p = item / n_fg;
     const long long f = (long long)(item - p * n_fg) * kF + g;
     FDTerm fi;
-    fi.base = -1;
-    if (f < a.n_store) {
-        const long long slot = f / a.Kc, k = f % a.Kc;
-        fi.base = (slot * N * 2LL * a.n + p) * a.Kpad + k;
-    }
+    fi.base = frame_base<N>(a, item, n_fg, g);
     fi.step = make_float2(1.0f, 0.0f);
     fi.delay = 0;
     fi.phi0 = fi.d_hi = fi.d_lo = 0.0f;
@@ -209,15 +215,102 @@ __device__ __forceinline__ FDTerm frame_terms(const FArgs& a, unsigned item, uns
     return fi;
 }
 
-// Before the F kernel: the delay terms of every frame of the launch, one thread per frame,
-// into the table a.Yt [item][128].
+// x rounded toward zero to `bits` significant bits: products with integers of up to 24 - bits
+// bits are exact in FP32.
+__device__ __forceinline__ float sig_bits(float x, int bits)
+{
+    return __uint_as_float(__float_as_uint(x) & (0xFFFFFFFFu << (24 - bits)));
+}
+
+// The delay polynomial along an item's frames (Sec. 4.3): with t_j = t_0 + j dt,
+//   tau_j = tau_0 + j rate + j^2 acc,  rate = dt (c1 + 2 c2 t_0),  acc = c2 dt^2,
+// so the phase nu tau_j (cycles) is nu tau_0 + j (nu rate) + j^2 (nu acc) and only its value
+// mod 1 matters: one FP64 evaluation per item gives frac(nu tau_0) and the two differences
+// reduced mod 1 (j, j^2 integers), each split hi + lo with hi short enough that j hi and
+// j^2 hi are exact in FP32; every frame then adds them in FP32.  The bin slope
+// d_j = tau_j fs / N likewise: d_0 split as the per-frame terms do, plus FP32 increments.
+struct FDBase {
+    float P0, Rh, Rl, Ah, Al;   // phase: frac(nu tau_0), nu rate mod 1 (hi, lo), nu acc mod 1 (hi, lo)
+    float dh, dl0, ddr, dda;    // slope: d_0 = dh + dl0; per frame and per frame^2
+};
+
+template <int N>
+__device__ __forceinline__ FDBase item_base(const FArgs& a, unsigned item, unsigned n_fg)
+{
+    const unsigned p = item / n_fg;
+    const long long f0 = (long long)(item - p * n_fg) * kF;
+    const double dt = a.frame_dt;
+    const double t0 = ((double)(a.m_begin + f0) + 0.5) * dt;
+    const double c0 = a.delay[3 * p], c1 = a.delay[3 * p + 1], c2 = a.delay[3 * p + 2];
+    const double tau0 = fma(t0, fma(t0, c2, c1), c0);
+    const double rate = fma(2.0 * c2, t0, c1) * dt, acc = c2 * dt * dt;
+    FDBase B;
+    const double ph = a.nu * tau0;
+    B.P0 = (float)(ph - floor(ph));
+    double r = a.nu * rate;
+    r -= rint(r);
+    B.Rh = sig_bits((float)r, 12);   // j < 2^7
+    B.Rl = (float)(r - (double)B.Rh);
+    double q = a.nu * acc;
+    q -= rint(q);
+    B.Ah = sig_bits((float)q, 8);    // j^2 < 2^14
+    B.Al = (float)(q - (double)B.Ah);
+    const double d0 = tau0 * a.fs_over_n;
+    B.dh = sig_bits((float)d0, 12);
+    B.dl0 = (float)(d0 - (double)B.dh);
+    B.ddr = (float)(rate * a.fs_over_n);
+    B.dda = (float)(acc * a.fs_over_n);
+    return B;
+}
+
+template <int N>
+__device__ __forceinline__ FDTerm frame_from_base(const FArgs& a, const FDBase& B, unsigned item, unsigned n_fg, int g)
+{
+    const unsigned p = item / n_fg;
+    const long long f = (long long)(item - p * n_fg) * kF + g;
+    FDTerm fi;
+    fi.base = frame_base<N>(a, item, n_fg, g);
+    fi.step = make_float2(1.0f, 0.0f);
+    fi.delay = 0;
+    fi.phi0 = fi.d_hi = fi.d_lo = 0.0f;
+    if (f < a.n_frames) {
+        const float jf = (float)g, j2 = (float)(g * g);
+        float x1 = jf * B.Rh, x2 = j2 * B.Ah;   // exact
+        x1 -= rintf(x1);
+        x2 -= rintf(x2);
+        float ph = B.P0 + x1 + x2 + fmaf(jf, B.Rl, j2 * B.Al);
+        fi.phi0 = ph - floorf(ph);
+        fi.d_hi = B.dh;
+        fi.d_lo = B.dl0 + fmaf(jf, B.ddr, j2 * B.dda);
+        fi.delay = 1;
+        fi.step = phasor_u(0.0f, fi.d_hi, fi.d_lo, 1);
+    }
+    return fi;
+}
+
+// Before the F kernel: the terms of every frame of the launch into the table a.Yt
+// [item][128].  A block takes 32 items: with a delay polynomial, lane i of the first warp
+// evaluates item i's FP64 base (one FP64 sequence per 32 items: this GPU's FP64 pipe is
+// narrow), then every thread derives frames from it in FP32; with a delay table (or none),
+// frame by frame.
+constexpr int kTermItems = 32;
 template <int N>
 __global__ void __launch_bounds__(256) fd_terms_kernel(const FArgs a, unsigned n_items, unsigned n_fg)
 {
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (long long)n_items * kF) return;
-    const unsigned item = (unsigned)(e / kF);
-    static_cast<FDTerm*>(a.Yt)[e] = frame_terms<N>(a, item, n_fg, (int)(e - (long long)item * kF));
+    __shared__ FDBase base[kTermItems];
+    const unsigned item0 = blockIdx.x * (unsigned)kTermItems;
+    const bool poly = a.delay != nullptr && a.delay_tab == nullptr;
+    if (poly && threadIdx.x < kTermItems && item0 + threadIdx.x < n_items)
+        base[threadIdx.x] = item_base<N>(a, item0 + threadIdx.x, n_fg);
+    __syncthreads();
+    FDTerm* tab = static_cast<FDTerm*>(a.Yt);
+    for (int e = threadIdx.x; e < kTermItems * kF; e += blockDim.x) {
+        const unsigned item = item0 + (unsigned)(e / kF);
+        const int g = e % kF;
+        if (item >= n_items) break;   // e rises: so does item
+        tab[(size_t)item * kF + g] = poly ? frame_from_base<N>(a, base[e / kF], item, n_fg, g)
+                                          : frame_terms<N>(a, item, n_fg, g);
+    }
 }
 
 template <int N, bool E4M3>
@@ -473,7 +566,8 @@ cudaError_t launch_fd(const FArgs& a, cudaStream_t s)
     const long long n_fg = (a.n_store + kF - 1) / kF, n_items = (long long)a.n * n_fg;
     if (n_items <= 0) return cudaSuccess;
     // the frame-term table in the scratch; frame numbers below 2^31 (32-bit block arithmetic)
-    if (n_items >= (1LL << 31) || a.Kc <= 0 || a.Yt == nullptr || a.m_begin + a.n_frames >= (1LL << 31) ||
+    if (n_items >= (1LL << 31) || a.Kc <= 0 || a.Kc >= (1LL << 31) || a.Yt == nullptr ||
+        a.m_begin + a.n_frames >= (1LL << 31) ||
         n_fg * kF >= (1LL << 31) ||
         (size_t)a.Yt_bytes < fstep_fd_scratch_bytes(N, a.n, a.n_store))
         return cudaErrorInvalidValue;
@@ -481,10 +575,12 @@ cudaError_t launch_fd(const FArgs& a, cudaStream_t s)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long grid = n_items < sms ? n_items : sms;
-    fd_terms_kernel<N><<<(unsigned)((n_items * kF + 255) / 256), 256, 0, s>>>(a, (unsigned)n_items, (unsigned)n_fg);
+    fd_terms_kernel<N><<<(unsigned)((n_items + kTermItems - 1) / kTermItems), 256, 0, s>>>(a, (unsigned)n_items,
+                                                                                          (unsigned)n_fg);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     fstep_fd_kernel<N, E4M3><<<(unsigned)grid, kT, smem, s>>>(a, (unsigned)n_items, (unsigned)n_fg);
+    count_extra_launches(1);   // the frame-term kernel
     return cudaGetLastError();
 }
 

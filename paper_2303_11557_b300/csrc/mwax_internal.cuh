@@ -164,6 +164,11 @@ struct XLaunch {
 // output, N = 1280 and 6400), variant 2 elsewhere; 4: the direct DFT with the frames on
 // the accumulator lanes (FP16 or e4m3 output, N = 32, 64, 128), variant 0 elsewhere.
 cudaError_t launch_fstep(int N, int out_kind, const FArgs& a, cudaStream_t s, int variant);
+// Kernels launched beyond the first by a launcher that issues several (the F-step variants
+// with a frame-term kernel and a transpose), counted per host thread: a plan's launch count
+// is the number of kernels.
+void count_extra_launches(long long k);
+long long extra_launches();
 // The tensor-core four-step F-step (FP16 output), N = 1280 or 6400.
 bool fstep_tc_supported(int N);
 cudaError_t launch_fstep_tc(int N, const FArgs& a, cudaStream_t s);

@@ -159,3 +159,27 @@ def test_frames_on_lanes_fstep_zeroed_blocks(prec):
     assert np.allclose(w, rw, atol=1e-6)
     err = parity_error(vis, ref, T)
     assert np.all(np.isfinite(vis)) and err.max() <= TOL[prec], f"max err {err.max():.3e}"
+
+
+@pytest.mark.parametrize("N,F,variant,per_call", [(128, 4, 0, lambda slots: 1), (128, 4, 4, lambda slots: 2),
+                                                   (1280, 10, 3, lambda slots: 3 * slots)],
+                         ids=["radix32", "frames-on-lanes", "row128"])
+def test_fstep_kernel_count_per_call(N, F, variant, per_call):
+    """The plan's launch count is the number of kernels: the frames-on-lanes F-step launches
+    its frame-term kernel too, the 128-row F-step a frame-term kernel, the F kernel and the
+    transpose per integration slot (two slots per call here, one launch group)."""
+    T, bs = 4, 64_000
+    S = 2 * bs
+    desc = mw.PlanDesc(n_tiles=T, fft_len=N, fine_avg=F, int_time_s=bs / synth.FS, samples_per_call=S,
+                       block_samples=bs, sky_freq_hz=synth.SKY_FREQ_HZ, precision=mw.MWAX_FP16)
+    plan = mw.mwax_plan_create_ex(desc)
+    mw.mwax_plan_set_stream(plan)
+    t = mw.mwax_plan_get_tuning(plan)
+    mw.mwax_plan_set_tuning(plan, mw.Tuning(variant, t.run_len, t.window, 0.0))
+    out = mw.empty_output(plan)
+    volt = torch.from_numpy(synth.voltages(5, 2 * T, S, block_samples=bs).reshape(-1)).cuda()
+    mw.mwax_plan_stage_times(plan)
+    mw.mwax_correlate(plan, volt, None, out)
+    counts = mw.mwax_plan_stage_times(plan)
+    plan.close()
+    assert counts["fstep"][1] == per_call(2)

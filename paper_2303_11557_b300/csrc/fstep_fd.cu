@@ -232,7 +232,22 @@ __device__ __forceinline__ float sig_bits(float x, int bits)
 struct FDBase {
     float P0, Rh, Rl, Ah, Al;   // phase: frac(nu tau_0), nu rate mod 1 (hi, lo), nu acc mod 1 (hi, lo)
     float dh, dl0, ddr, dda;    // slope: d_0 = dh + dl0; per frame and per frame^2
+    long long row0;             // operand element of (slot of frame 0, c = 0, re, p, k = 0)
+    unsigned f0, k0;            // the item's first frame in the launch, and within its slot
 };
+
+// The item's position terms (any delay model): its first frame, that frame's slot and
+// place in it, so that each frame's operand position takes no division by the slot length
+// unless the item runs into the next slot.
+template <int N>
+__device__ __forceinline__ void item_position(const FArgs& a, unsigned item, unsigned n_fg, FDBase& B)
+{
+    const unsigned p = item / n_fg, kc = (unsigned)a.Kc;
+    B.f0 = (item - p * n_fg) * (unsigned)kF;
+    const unsigned slot = B.f0 / kc;
+    B.k0 = B.f0 - slot * kc;
+    B.row0 = ((long long)slot * N * 2LL * a.n + p) * a.Kpad;
+}
 
 template <int N>
 __device__ __forceinline__ FDBase item_base(const FArgs& a, unsigned item, unsigned n_fg)
@@ -264,12 +279,16 @@ __device__ __forceinline__ FDBase item_base(const FArgs& a, unsigned item, unsig
 }
 
 template <int N>
-__device__ __forceinline__ FDTerm frame_from_base(const FArgs& a, const FDBase& B, unsigned item, unsigned n_fg, int g)
+__device__ __forceinline__ FDTerm frame_from_base(const FArgs& a, const FDBase& B, int g)
 {
-    const unsigned p = item / n_fg;
-    const long long f = (long long)(item - p * n_fg) * kF + g;
+    const long long f = (long long)B.f0 + g;
     FDTerm fi;
-    fi.base = frame_base<N>(a, item, n_fg, g);
+    fi.base = -1;
+    if (f < a.n_store) {
+        const unsigned kc = (unsigned)a.Kc, kk = B.k0 + (unsigned)g;
+        const unsigned ds = kk < kc ? 0u : kk / kc;   // slots past the item's first
+        fi.base = B.row0 + (long long)ds * N * 2LL * a.n * a.Kpad + (kk - ds * kc);
+    }
     fi.step = make_float2(1.0f, 0.0f);
     fi.delay = 0;
     fi.phi0 = fi.d_hi = fi.d_lo = 0.0f;
@@ -300,16 +319,18 @@ __global__ void __launch_bounds__(256) fd_terms_kernel(const FArgs a, unsigned n
     __shared__ FDBase base[kTermItems];
     const unsigned item0 = blockIdx.x * (unsigned)kTermItems;
     const bool poly = a.delay != nullptr && a.delay_tab == nullptr;
-    if (poly && threadIdx.x < kTermItems && item0 + threadIdx.x < n_items)
-        base[threadIdx.x] = item_base<N>(a, item0 + threadIdx.x, n_fg);
+    if (poly && threadIdx.x < kTermItems && item0 + threadIdx.x < n_items) {
+        FDBase B = item_base<N>(a, item0 + threadIdx.x, n_fg);
+        item_position<N>(a, item0 + threadIdx.x, n_fg, B);
+        base[threadIdx.x] = B;
+    }
     __syncthreads();
     FDTerm* tab = static_cast<FDTerm*>(a.Yt);
     for (int e = threadIdx.x; e < kTermItems * kF; e += blockDim.x) {
         const unsigned item = item0 + (unsigned)(e / kF);
         const int g = e % kF;
         if (item >= n_items) break;   // e rises: so does item
-        tab[(size_t)item * kF + g] = poly ? frame_from_base<N>(a, base[e / kF], item, n_fg, g)
-                                          : frame_terms<N>(a, item, n_fg, g);
+        tab[(size_t)item * kF + g] = poly ? frame_from_base<N>(a, base[e / kF], g) : frame_terms<N>(a, item, n_fg, g);
     }
 }
 

@@ -51,7 +51,7 @@ struct FD {
     static_assert(TASKS % kW == 0, "whole conversion tasks per thread");
 };
 
-struct FDTerm {
+struct __align__(16) FDTerm {   // two 16-byte stores
     long long base;          // element of (slot, c = 0, re plane, p, k) or -1: not stored
     float phi0, d_hi, d_lo;  // delay terms: the phasor of bin offset u is e^{2 pi i (phi0 + u d)}
     int delay;
@@ -310,8 +310,9 @@ __device__ __forceinline__ FDTerm frame_from_base(const FArgs& a, const FDBase& 
 // Before the F kernel: the terms of every frame of the launch into the table a.Yt
 // [item][128].  A block takes 32 items: with a delay polynomial, lane i of the first warp
 // evaluates item i's FP64 base (one FP64 sequence per 32 items: this GPU's FP64 pipe is
-// narrow), then every thread derives frames from it in FP32; with a delay table (or none),
-// frame by frame.
+// narrow), then 8 threads per item derive its frames from it in FP32, the base held in
+// registers (read once per thread: per frame, its fields' shared-memory loads throttled
+// the kernel); with a delay table (or none), frame by frame.
 constexpr int kTermItems = 32;
 template <int N>
 __global__ void __launch_bounds__(256) fd_terms_kernel(const FArgs a, unsigned n_items, unsigned n_fg)
@@ -325,12 +326,18 @@ __global__ void __launch_bounds__(256) fd_terms_kernel(const FArgs a, unsigned n
         base[threadIdx.x] = B;
     }
     __syncthreads();
+    static_assert(kTermItems * 8 == 256, "8 threads per item");
     FDTerm* tab = static_cast<FDTerm*>(a.Yt);
-    for (int e = threadIdx.x; e < kTermItems * kF; e += blockDim.x) {
-        const unsigned item = item0 + (unsigned)(e / kF);
-        const int g = e % kF;
-        if (item >= n_items) break;   // e rises: so does item
-        tab[(size_t)item * kF + g] = poly ? frame_from_base<N>(a, base[e / kF], g) : frame_terms<N>(a, item, n_fg, g);
+    const int ii = threadIdx.x >> 3, sub = threadIdx.x & 7;
+    const unsigned item = item0 + (unsigned)ii;
+    if (item >= n_items) return;
+    FDTerm* out = tab + (size_t)item * kF;
+    if (poly) {
+        const FDBase B = base[ii];
+#pragma unroll 4
+        for (int g = sub; g < kF; g += 8) out[g] = frame_from_base<N>(a, B, g);
+    } else {
+        for (int g = sub; g < kF; g += 8) out[g] = frame_terms<N>(a, item, n_fg, g);
     }
 }
 

@@ -97,7 +97,8 @@ typedef struct {
     size_t vis_set_bytes;        /* one integration's visibilities            */
     size_t weights_bytes;        /* one integration's weights table           */
     size_t output_bytes;         /* n_ints * (vis_set_bytes + weights_bytes)  */
-    size_t workspace_bytes;      /* device memory the plan holds              */
+    size_t workspace_bytes;      /* device memory the plan holds: operand planes and
+                                    F-step scratch (which a tuning choice may grow) */
     int precision;
     double x_flop_alg;           /* X-step work per call: 8 flop per complex multiply-
                                     accumulate over the n (n + 1) / 2 unique path pairs,

@@ -953,7 +953,7 @@ mwax_status mwax_plan_get_info(const mwax_plan* p, mwax_plan_info* info)
     info->vis_set_bytes = p->vis_set_bytes;
     info->weights_bytes = p->weights_bytes;
     info->output_bytes = (size_t)p->n_ints * p->int_stride;
-    info->workspace_bytes = p->Y_bytes;
+    info->workspace_bytes = p->Y_bytes + p->Yt_bytes;   // operands (FP8: with its FP16 staging) + F-step scratch
     info->precision = p->prec;
     mwax::x_flops(*p, &info->x_flop_alg, &info->x_flop_issued);
     return MWAX_OK;

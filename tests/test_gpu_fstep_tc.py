@@ -183,3 +183,30 @@ def test_fstep_kernel_count_per_call(N, F, variant, per_call):
     counts = mw.mwax_plan_stage_times(plan)
     plan.close()
     assert counts["fstep"][1] == per_call(2)
+
+
+def test_workspace_bytes_count_fstep_scratch():
+    """The plan's reported device memory includes the F-step scratch: choosing the
+    frames-on-lanes F-step adds its frame-term table (32 bytes per frame of a launch), and
+    the 128-row F-step's plans hold theirs from creation."""
+    T, bs = 4, 64_000
+    S = 2 * bs
+    desc = mw.PlanDesc(n_tiles=T, fft_len=128, fine_avg=4, int_time_s=bs / synth.FS, samples_per_call=S,
+                       block_samples=bs, sky_freq_hz=synth.SKY_FREQ_HZ, precision=mw.MWAX_FP16)
+    plan = mw.mwax_plan_create_ex(desc)
+    w0 = plan.info["workspace_bytes"]
+    t = mw.mwax_plan_get_tuning(plan)
+    mw.mwax_plan_set_tuning(plan, mw.Tuning(4, t.run_len, t.window, 0.0))
+    w1 = plan.info["workspace_bytes"]
+    plan.close()
+    frames = S // 128   # every frame of the call in one launch group
+    assert w1 - w0 == 2 * T * ((frames + 127) // 128) * 128 * 32
+    d2 = mw.PlanDesc(n_tiles=T, fft_len=1280, fine_avg=10, int_time_s=bs / synth.FS, samples_per_call=S,
+                     block_samples=bs, sky_freq_hz=synth.SKY_FREQ_HZ, precision=mw.MWAX_FP16)
+    p2 = mw.mwax_plan_create_ex(d2)
+    info = p2.info
+    p2.close()
+    # operands: 2 slots x N x 2 planes x paths x Kpad (50 frames -> 128) x 2 bytes; the
+    # scratch: one slot of frame-major tiles, 7 groups of 8 frames x N words per path
+    operands = 2 * 1280 * 2 * (2 * T) * 128 * 2
+    assert info["workspace_bytes"] >= operands + (2 * T) * 7 * 8 * 1280 * 4

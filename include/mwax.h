@@ -304,7 +304,9 @@ mwax_status mwax_plan_get_tuning(const mwax_plan* plan, mwax_tuning* tuning);
  * own CUDA-core X-steps.  The paper processes one coarse channel per server (Sec. 2.1); a
  * batch processes many on one GPU.  The batch references the plans (they must outlive it,
  * stay on one device and not be used on their own while the batch runs) and uses the
- * plans' workspaces.  Returns NULL on error.
+ * plans' workspaces.  The plans' launch choices (mwax_plan_set_tuning, mwax_plan_autotune,
+ * which may also allocate or release F-step scratch) are read when the batch is created:
+ * change them only before.  Returns NULL on error.
  */
 typedef struct mwax_batch mwax_batch;
 mwax_batch* mwax_batch_create(mwax_plan* const* plans, int n_plans);

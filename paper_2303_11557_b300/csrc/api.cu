@@ -62,7 +62,7 @@ int prec_elem_bytes(int prec)
     switch (prec) {
         case MWAX_FP32: return 4;
         case MWAX_FP16: return 2;
-        case MWAX_FP8: return 3;   // FP16 staging (2) + e4m3 operands (1)
+        case MWAX_FP8: return 1;   // e4m3 operands (F-step variant 2's FP16 staging comes with that variant)
         case MWAX_INT8: return 2;   // int8 held exactly in FP16 operands
         case MWAX_FP16X3: return 4;   // an FP16 hi/lo pair per value
         default: return 0;
@@ -405,15 +405,8 @@ mwax_status setup(mwax_plan& p)
     }
     const size_t elems = (size_t)p.slots * p.N * 2 * p.n * p.Kpad;
     p.Y_bytes = elems * p.elem_bytes;
-    if (p.prec == MWAX_FP8) {
-        MWAX_CUDA(cudaMalloc(&p.Y16, elems * 2));
-        MWAX_CUDA(cudaMemset(p.Y16, 0, elems * 2));
-        MWAX_CUDA(cudaMalloc(&p.Y, elems));
-        MWAX_CUDA(cudaMemset(p.Y, 0, elems));
-    } else {
-        MWAX_CUDA(cudaMalloc(&p.Y, p.Y_bytes));
-        MWAX_CUDA(cudaMemset(p.Y, 0, p.Y_bytes));
-    }
+    MWAX_CUDA(cudaMalloc(&p.Y, p.Y_bytes));
+    MWAX_CUDA(cudaMemset(p.Y, 0, p.Y_bytes));
     // N = 1280, 6400 with FP16 operands out: the 128-row tensor-core F-step by default (the
     // fastest measured there), with its one-slot scratch
     if (fstep_f128_supported(p.N) && (p.prec == MWAX_FP16 || p.prec == MWAX_FP8)) {
@@ -805,7 +798,8 @@ mwax_status enqueue_fstep(mwax_plan* p, const LaunchGroup& g, const int8_t* volt
         MWAX_CUDA(timed(p, 1, s, [&] { return launch_fill_amax(p->amax, p->amax_static, p->n_groups, p->n, g.nslots, s); }));
     } else if (p->prec == MWAX_FP8) {
         // the tensor-core DFT-product F-steps write FP16: then per path and channel group
-        // the max magnitude, then e4m3
+        // the max magnitude, then e4m3 (the FP16 staging is allocated with the variant)
+        if (!p->Y16) return fail(MWAX_EINVAL, "FP8 plan with F-step variant 2 and no FP16 staging");
         fa.Y = p->Y16;
         MWAX_CUDA(timed(p, 1, s, [&] { return launch_fstep(p->N, FOUT_F16, fa, s, p->fvariant); }));
         MWAX_CUDA(timed(p, 1, s, [&] {
@@ -953,7 +947,8 @@ mwax_status mwax_plan_get_info(const mwax_plan* p, mwax_plan_info* info)
     info->vis_set_bytes = p->vis_set_bytes;
     info->weights_bytes = p->weights_bytes;
     info->output_bytes = (size_t)p->n_ints * p->int_stride;
-    info->workspace_bytes = p->Y_bytes + p->Yt_bytes;   // operands (FP8: with its FP16 staging) + F-step scratch
+    // operands, FP8 variant 2's FP16 staging, F-step scratch
+    info->workspace_bytes = p->Y_bytes + (p->Y16 ? 2 * p->Y_bytes : 0) + p->Yt_bytes;
     info->precision = p->prec;
     mwax::x_flops(*p, &info->x_flop_alg, &info->x_flop_issued);
     return MWAX_OK;

@@ -208,6 +208,14 @@ namespace mwax {
 mwax_status ensure_fstep_scratch(mwax_plan* p, int variant)
 {
     if (p->prec != MWAX_FP16 && p->prec != MWAX_FP8) return MWAX_OK;
+    if (variant == 2 && p->prec == MWAX_FP8 && !p->Y16) {
+        // the DFT-product F-steps write FP16 operands, quantised to e4m3 afterwards
+        BCUDA(cudaSetDevice(p->device));
+        if (p->stream) BCUDA(cudaStreamSynchronize(p->stream));
+        BCUDA(cudaMalloc(&p->Y16, 2 * p->Y_bytes));
+        BCUDA(cudaMemset(p->Y16, 0, 2 * p->Y_bytes));
+        return MWAX_OK;
+    }
     size_t need = 0;
     if (variant == 3 && fstep_f128_supported(p->N)) {
         need = fstep_f128_scratch_bytes(p->N, p->n, p->Kc);
@@ -399,7 +407,7 @@ mwax_status mwax_plan_autotune(mwax_plan* p, const int8_t* voltages, const doubl
     // stage 1: the F-step variant, with the plan's own X-step choice
     const int rl0 = p->run_len, w0 = p->window;
     for (int fv : fvars) {
-        if ((fv == 3 || fv == 4) && (st = ensure_fstep_scratch(p, fv)) != MWAX_OK) break;
+        if (fv >= 2 && (st = ensure_fstep_scratch(p, fv)) != MWAX_OK) break;
         p->fvariant = fv;
         st = configure_x(*p, rl0, w0);
         if (st != MWAX_OK) break;
@@ -436,6 +444,16 @@ mwax_status mwax_plan_autotune(mwax_plan* p, const int8_t* voltages, const doubl
     cudaEventDestroy(e1);
     if (st != MWAX_OK) return st;
     p->fvariant = best.fstep_variant;
+    // release the scratch of the variants not kept (the stream is idle: the timing synced)
+    if (p->Y16 && best.fstep_variant != 2) {
+        cudaFree(p->Y16);
+        p->Y16 = nullptr;
+    }
+    if (p->Yt && best.fstep_variant != 3 && best.fstep_variant != 4) {
+        cudaFree(p->Yt);
+        p->Yt = nullptr;
+        p->Yt_bytes = 0;
+    }
     st = configure_x(*p, best.run_len, best.window);
     if (st != MWAX_OK) return st;
     if (best_out) *best_out = best;
@@ -449,7 +467,7 @@ mwax_status mwax_plan_set_tuning(mwax_plan* p, const mwax_tuning* t)
         return set_error(MWAX_EINVAL, "invalid tuning");
     BCUDA(cudaSetDevice(p->device));
     BCUDA(cudaStreamSynchronize(p->stream));
-    if (t->fstep_variant == 3 || t->fstep_variant == 4) {
+    if (t->fstep_variant >= 2) {
         const mwax_status st = ensure_fstep_scratch(p, t->fstep_variant);
         if (st != MWAX_OK) return st;
     }

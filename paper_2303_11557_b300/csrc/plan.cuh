@@ -29,7 +29,8 @@ struct mwax_plan {
 
     // device memory
     void* Y = nullptr;      // X-step operands (FP8: e4m3)
-    void* Y16 = nullptr;    // FP8 only: the FP16 operands the e4m3 ones are quantised from
+    void* Y16 = nullptr;    // FP8 with F-step variant 2 only: the FP16 operands the e4m3 ones
+                            //   are quantised from (2 x Y_bytes), allocated with the variant
     void* Yt = nullptr;     // F-step variants 3 and 4: their scratch (frame terms; variant 3
                             //   also the frame-major spectra of one slot)
     size_t Yt_bytes = 0;
